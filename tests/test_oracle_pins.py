@@ -1,0 +1,519 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed-form
+colours, hand-composited pixels, brute-force enumeration, library routines,
+finite differences, and the second-order statements of Theorems 1 and 2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+SQRT_PI = math.sqrt(math.pi)
+
+
+def _one_gaussian(mean, log_scale, logit, dc, quat=(1.0, 0.0, 0.0, 0.0)):
+    n = np.asarray(mean).reshape(-1, 3).shape[0]
+    return synth.Scene(np.asarray(mean, np.float32).reshape(n, 3),
+                       np.asarray(log_scale, np.float32).reshape(n, 3),
+                       np.broadcast_to(np.asarray(quat, np.float32).reshape(-1, 4), (n, 4)).copy(),
+                       np.asarray(logit, np.float32).reshape(n),
+                       np.asarray(dc, np.float32).reshape(n, 1, 3), 0)
+
+
+# --------------------------------------------------------------------------
+# Building blocks
+# --------------------------------------------------------------------------
+
+def test_exp_f32_within_two_ulp():
+    """The float32 exponential of the integer stage is accurate (Cody-Waite +
+    Taylor): within 2 ulp of the correctly rounded value."""
+    x = np.concatenate([np.linspace(-20, 5, 20001), np.random.default_rng(0).normal(-9, 2, 5000)])
+    x = x.astype(np.float32)
+    got = oracle.exp_f32(x)
+    ref = np.exp(x.astype(np.float64)).astype(np.float32)
+    ulp = np.abs(got.view(np.int32).astype(np.int64) - ref.view(np.int32).astype(np.int64))
+    assert ulp.max() <= 2
+
+
+def test_sh_basis_orthonormal_and_gradient():
+    """Real SH basis up to degree 3 is orthonormal on the sphere (Gauss-Legendre
+    x uniform-phi quadrature, exact for these polynomial degrees) and its
+    gradient matches central differences."""
+    ct, wt = np.polynomial.legendre.leggauss(12)
+    phis = np.linspace(0, 2 * np.pi, 24, endpoint=False)
+    st = np.sqrt(1 - ct ** 2)
+    dirs = np.stack([np.outer(st, np.cos(phis)).ravel(), np.outer(st, np.sin(phis)).ravel(),
+                     np.repeat(ct, phis.size)], 1)
+    w = np.repeat(wt, phis.size) * (2 * np.pi / phis.size)
+    Y, _ = oracle.sh_basis(3, dirs)
+    gram = (Y * w[:, None]).T @ Y
+    assert np.abs(gram - np.eye(16)).max() < 1e-12
+    rng = np.random.default_rng(1)
+    d = rng.normal(size=(20, 3))
+    _, dY = oracle.sh_basis(3, d)
+    h = 1e-6
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        Yp, _ = oracle.sh_basis(3, d + e)
+        Ym, _ = oracle.sh_basis(3, d - e)
+        assert np.abs((Yp - Ym) / (2 * h) - dY[:, :, a]).max() < 1e-7
+
+
+# --------------------------------------------------------------------------
+# Forward colour: closed forms (Section 3, Eq. alpha_blend / sigma_2D)
+# --------------------------------------------------------------------------
+
+def test_single_opaque_gaussian_centre_pixel():
+    """o -> 0.999 on the optical axis: alpha is clamped at 0.99, so the centre
+    pixel is exactly 0.99 c + 0.01 bg."""
+    c0 = 0.5 / SQRT_PI
+    dc = np.array([0.6, -0.4, 0.0]) / c0      # colour c = 0.5 + c0 dc
+    colour = 0.5 + c0 * dc.astype(np.float32).astype(np.float64)
+    sc = _one_gaussian([0, 0, 3.0], [-3.0, -3.0, -3.0], math.log(0.999 / 0.001), dc)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings(bg=(0.2, 0.3, 0.4))
+    r = oracle.render(sc, cam, st)
+    a = float(np.float32(0.99))
+    expect = a * colour + (1 - a) * np.array(st.bg, dtype=np.float32).astype(np.float64)
+    assert np.abs(r["image"][32, 32] - expect).max() < 1e-12
+    assert r["n_contrib"][32, 32] == 1
+
+
+def test_single_gaussian_off_centre_closed_form():
+    """Axis-aligned Gaussian on the optical axis: J is diagonal, so
+    Sigma2D = diag(fx^2 sx^2/z^2 + 0.3, fy^2 sy^2/z^2 + 0.3) and
+    C(x) = c o exp(-dx^2/(2 sx'^2) - dy^2/(2 sy'^2)) where composited."""
+    sx, sy, z, o = 0.05, 0.03, 3.0, 0.5
+    sc = _one_gaussian([0, 0, z], [math.log(sx), math.log(sy), -3.0], 0.0, [0.0, 0.0, 0.0])
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings()
+    r = oracle.render(sc, cam, st)
+    fx = 64.0
+    s32x = math.exp(float(np.float32(math.log(sx))))   # the stored log-scale is float32
+    s32y = math.exp(float(np.float32(math.log(sy))))
+    vx = fx * fx * s32x ** 2 / z ** 2 + float(np.float32(0.3))
+    vy = fx * fx * s32y ** 2 / z ** 2 + float(np.float32(0.3))
+    checked = 0
+    for py in range(26, 39):
+        for px in range(26, 39):
+            dx, dy = px - 32.0, py - 32.0
+            a = o * math.exp(-0.5 * (dx * dx / vx + dy * dy / vy))
+            if a < 1 / 255 * 1.001:
+                continue
+            assert abs(r["image"][py, px, 0] - 0.5 * a) < 1e-12
+            checked += 1
+    assert checked > 20
+
+
+def test_two_gaussians_composite_by_hand():
+    """Two Gaussians at distinct depths on the axis: C = c1 a1 + c2 a2 (1 - a1)
+    + bg (1 - a1)(1 - a2) at the centre, whatever their input order."""
+    c0 = 0.5 / SQRT_PI
+    cols = np.array([[0.9, 0.2, 0.1], [0.1, 0.7, 0.4]])
+    dcs = (cols - 0.5) / c0
+    for order in ([0, 1], [1, 0]):
+        means = np.array([[0, 0, 2.0], [0, 0, 3.5]])[order]
+        logits = np.array([0.3, -0.2])[order]
+        sc = _one_gaussian(means, [[-3.0] * 3] * 2, logits, dcs[order])
+        cam = synth.camera_identity(64, 64, 64.0)
+        st = synth.Settings(bg=(0.25, 0.5, 0.75))
+        r = oracle.render(sc, cam, st)
+        o = 1 / (1 + np.exp(-np.array([0.3, -0.2], dtype=np.float32).astype(np.float64)))
+        bg = np.array(st.bg, dtype=np.float32).astype(np.float64)
+        cc = 0.5 + c0 * dcs.astype(np.float32).astype(np.float64)
+        expect = cc[0] * o[0] + cc[1] * o[1] * (1 - o[0]) + bg * (1 - o[0]) * (1 - o[1])
+        assert np.abs(r["image"][32, 32] - expect).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Integer stages: brute force (binning, sort, ranges, rect coverage)
+# --------------------------------------------------------------------------
+
+def _brute_bins(scene, cam, st):
+    isg = oracle.integer_stage(scene, cam, st)
+    gx, gy = oracle.n_tiles(cam, st)
+    inst = []
+    for i in range(scene.n):
+        if isg["tiles"][i] == 0:
+            continue
+        xl, xh, yl, yh = isg["rect"][i]
+        db = int(isg["depth"][i:i + 1].view(np.uint32)[0])
+        for ty in range(gy):
+            for tx in range(gx):
+                if xl <= tx <= xh and yl <= ty <= yh:
+                    inst.append((ty * gx + tx, db, i))
+    inst.sort()
+    return isg, inst, gx * gy
+
+
+@pytest.mark.parametrize("seed", [0, 5, 11])
+def test_binning_sort_ranges_brute_force(seed):
+    sc = synth.tiny_scene(seed)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings()
+    keys, gids, ranges = oracle.bin_sort(sc, cam, st)
+    isg, inst, T = _brute_bins(sc, cam, st)
+    assert len(inst) == len(keys) == int(isg["tiles"].sum())
+    assert [t for t, _, _ in inst] == [int(k >> np.uint64(32)) for k in keys]
+    assert [d for _, d, _ in inst] == [int(k & np.uint64(0xFFFFFFFF)) for k in keys]
+    assert [g for _, _, g in inst] == gids.tolist()
+    for t in range(T):
+        idx = [k for k, x in enumerate(inst) if x[0] == t]
+        if idx:
+            assert ranges[t].tolist() == [idx[0], idx[-1] + 1]
+        else:
+            assert ranges[t, 0] == ranges[t, 1]
+
+
+def test_rect_covers_three_sigma_ellipse_and_is_tight():
+    """Every pixel within radius_sigma Mahalanobis distance of a visible
+    Gaussian lies in a tile of its rect; every tile of the rect meets the
+    square [mu - r, mu + r]."""
+    sc = synth.tiny_scene(3)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings()
+    isg = oracle.integer_stage(sc, cam, st)
+    pr = oracle.project(sc, cam, st)
+    ys, xs = np.mgrid[0:64, 0:64]
+    for i in range(sc.n):
+        if isg["tiles"][i] == 0:
+            continue
+        q = pr["conic"][i]
+        dx, dy = xs - pr["mean2d"][i, 0], ys - pr["mean2d"][i, 1]
+        maha = q[0] * dx * dx + 2 * q[1] * dx * dy + q[2] * dy * dy
+        inside = maha <= st.radius_sigma ** 2 * (1 - 1e-6)
+        xl, xh, yl, yh = isg["rect"][i]
+        tx, ty = xs // st.tile_w, ys // st.tile_h
+        in_rect = (tx >= xl) & (tx <= xh) & (ty >= yl) & (ty <= yh)
+        assert not np.any(inside & ~in_rect)
+        # tightness: the rect is the set of tiles meeting the bounding square
+        Sig = np.linalg.inv(np.array([[q[0], q[1]], [q[1], q[2]]]))
+        m, det = 0.5 * (Sig[0, 0] + Sig[1, 1]), np.linalg.det(Sig)
+        r = math.ceil(st.radius_sigma * math.sqrt(m + math.sqrt(max(0.1, m * m - det))))
+        mx, my = isg["mean2d"][i]
+        assert xl == max(0, math.floor((mx - r) / 16)) and xh == min(3, math.floor((mx + r) / 16))
+        assert yl == max(0, math.floor((my - r) / 16)) and yh == min(3, math.floor((my + r) / 16))
+
+
+# --------------------------------------------------------------------------
+# Gradients: central finite differences on the full model (smooth mode)
+# --------------------------------------------------------------------------
+
+FIELDS = ("means", "log_scales", "quats", "opacity_logit", "sh")
+
+
+def _lin_loss(scene, cam, st, g):
+    return float(np.sum(oracle.render(scene, cam, st)["image"] * g))
+
+
+def _fd_check(scene, cam, st, g, gauss_idx, h=1e-4):
+    ana = oracle.backward(scene, cam, st, g)
+    base_keys = oracle.bin_sort(scene, cam, st)[1]
+    fd_all, an_all = [], []
+    for i in gauss_idx:
+        for f in FIELDS:
+            arr = getattr(scene, f)
+            flat = arr.reshape(scene.n, -1)
+            for k in range(flat.shape[1]):
+                x0 = flat[i, k]
+                vals = []
+                ok = True
+                for s in (+1, -1):
+                    sc2 = scene.copy()
+                    a2 = getattr(sc2, f).reshape(scene.n, -1)
+                    a2[i, k] = np.float32(x0 + s * h)
+                    if not np.array_equal(oracle.bin_sort(sc2, cam, st)[1], base_keys):
+                        ok = False
+                        break
+                    vals.append((_lin_loss(sc2, cam, st, g), float(a2[i, k])))
+                if not ok:
+                    continue
+                (lp, xp), (lm, xm) = vals
+                fd_all.append((lp - lm) / (xp - xm))
+                an_all.append(ana[f if f != "opacity_logit" else "opacity_logit"].reshape(scene.n, -1)[i, k])
+    return np.array(fd_all), np.array(an_all)
+
+
+def test_gradient_matches_central_differences_sh0():
+    sc = synth.tiny_scene(0)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings().smooth()
+    g = np.random.default_rng(7).normal(size=(64, 64, 3)) / (64 * 64)
+    vis = np.nonzero(oracle.integer_stage(sc, cam, st)["tiles"])[0]
+    idx = np.random.default_rng(3).choice(vis, 16, replace=False)
+    fd, an = _fd_check(sc, cam, st, g, idx)
+    assert fd.size > 150
+    err = np.linalg.norm(fd - an) / np.linalg.norm(an)
+    assert err < 1e-5, err
+    assert np.abs(fd - an).max() < 1e-4 * np.abs(an).max()
+
+
+def test_gradient_matches_central_differences_sh3_offaxis():
+    """Degree-3 SH (view-dependent colour depends on p) and an off-axis,
+    rotated camera with Gaussians near the Jacobian clamp."""
+    sc = synth.cluster_scene(4, 96, sh_degree=3)
+    sc.log_scales[:] = sc.log_scales + 2.0          # a few pixels wide at this distance
+    cam = synth.camera_lookat((1.0, -0.5, -6.0), (0.3, 0.2, 0.0), 48, 40, 48.0)
+    st = synth.Settings().smooth()
+    st.fov_clamp = 1.05
+    g = np.random.default_rng(8).normal(size=(40, 48, 3)) / (48 * 40)
+    vis = np.nonzero(oracle.integer_stage(sc, cam, st)["tiles"])[0]
+    idx = np.random.default_rng(4).choice(vis, min(6, vis.size), replace=False)
+    fd, an = _fd_check(sc, cam, st, g, idx)
+    assert fd.size > 200
+    err = np.linalg.norm(fd - an) / np.linalg.norm(an)
+    assert err < 1e-5, err
+
+
+def test_gradient_with_active_alpha_clamp():
+    """Where o G > alpha_max the composited alpha is the constant alpha_max: its
+    derivative is zero, which central differences confirm away from the kink."""
+    sc = synth.tiny_scene(2, 32)
+    sc.opacity_logit[:] = 6.0                      # o ~ 0.9975: clamp active near centres
+    cam = synth.camera_identity(32, 32, 32.0)
+    st = synth.Settings().smooth()
+    st.alpha_max = 0.99
+    g = np.random.default_rng(9).normal(size=(32, 32, 3)) / (32 * 32)
+    vis = np.nonzero(oracle.integer_stage(sc, cam, st)["tiles"])[0]
+    fd, an = _fd_check(sc, cam, st, g, vis[:8], h=1e-4)
+    err = np.linalg.norm(fd - an) / np.linalg.norm(an)
+    assert err < 1e-3, err
+
+
+def test_l1_loss_gradient():
+    rng = np.random.default_rng(0)
+    img = rng.uniform(size=(8, 9, 3))
+    tgt = rng.uniform(size=(8, 9, 3)).astype(np.float32)
+    L, g = oracle.l1_loss_grad(img, tgt, n_views=2)
+    assert abs(L - np.mean(np.abs(img - tgt.astype(np.float64))) / 2) < 1e-15
+    h = 1e-7
+    for k in range(10):
+        idx = tuple(rng.integers(0, s) for s in img.shape)
+        e = np.zeros_like(img)
+        e[idx] = h
+        fd = (oracle.l1_loss_grad(img + e, tgt, 2)[0] - oracle.l1_loss_grad(img - e, tgt, 2)[0]) / (2 * h)
+        assert abs(fd - g[idx]) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Splitting matrix = Hessian of the loss w.r.t. p_i in the frozen model
+# (Theorem 1 with T^(i) = 0 for a loss affine in each alpha, Lemma on the
+# decomposition of the Hessian, and the Appendix's closed-form Hessian).
+# --------------------------------------------------------------------------
+
+def _frozen_hessian(sc, cam, st, i, g, h):
+    H = np.zeros((3, 3))
+    f0 = oracle.frozen_eval(sc, cam, st, i, dp=np.zeros(3), g=g)
+    for a in range(3):
+        for b in range(a, 3):
+            def f(sa, sb):
+                d = np.zeros(3)
+                d[a] += sa * h
+                d[b] += sb * h
+                return oracle.frozen_eval(sc, cam, st, i, dp=d, g=g)
+            if a == b:
+                v = (f(1, 0) - 2 * f0 + f(-1, 0)) / h ** 2
+            else:
+                v = (f(1, 1) - f(1, -1) - f(-1, 1) + f(-1, -1)) / (4 * h * h)
+            H[a, b] = H[b, a] = v
+    return H
+
+
+def test_splitting_matrix_equals_frozen_hessian():
+    sc = synth.tiny_scene(0)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings().smooth()
+    g = np.random.default_rng(11).normal(size=(64, 64, 3)) / (64 * 64)
+    S = oracle.backward(sc, cam, st, g)["S"]
+    vis = np.nonzero(oracle.integer_stage(sc, cam, st)["tiles"])[0]
+    for i in np.random.default_rng(5).choice(vis, 8, replace=False):
+        # Richardson: H(h) = H + c h^2 + ..., so (4 H(h/2) - H(h)) / 3 = H + O(h^4)
+        h = 2e-3
+        H1 = _frozen_hessian(sc, cam, st, i, g, h)
+        H2 = _frozen_hessian(sc, cam, st, i, g, h / 2)
+        Hr = (4 * H2 - H1) / 3
+        rel = np.linalg.norm(Hr - S[i]) / np.linalg.norm(S[i])
+        assert rel < 1e-6, (i, rel)
+
+
+def test_splitting_matrix_symmetric():
+    sc = synth.tiny_scene(1)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings()
+    r = oracle.render(sc, cam, st)
+    _, g = oracle.l1_loss_grad(r["image"], synth.target_image(2, 64, 64))
+    S = oracle.backward(sc, cam, st, g)["S"]
+    assert np.array_equal(S, np.transpose(S, (0, 2, 1)))
+    assert np.abs(S).max() > 0
+
+
+# --------------------------------------------------------------------------
+# Theorems 1 and 2: sign of lambda_min decides; predicted decrease; optimality
+# --------------------------------------------------------------------------
+
+def _setup_l1(seed=0):
+    sc = synth.tiny_scene(seed)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings().smooth()
+    r = oracle.render(sc, cam, st)
+    tgt = synth.target_image(2, 64, 64)
+    _, g = oracle.l1_loss_grad(r["image"], tgt)
+    S = oracle.backward(sc, cam, st, g)["S"]
+    return sc, cam, st, g, tgt, S
+
+
+def test_split_sign_and_predicted_decrease():
+    """Mixture split of Gaussian i along +-eps v (w = 1/2):
+    L(split) - L(theta) = eps^2 v^T S v / 2 + O(eps^4); with v = v_min the change
+    is negative iff lambda_min < 0.  Checked on the linear functional (exact
+    second order) and on the real L1 loss."""
+    sc, cam, st, g, tgt, S = _setup_l1(0)
+    lam, v = oracle.eig3_min(S)
+    ev, V = oracle.jacobi3(S)
+    base_lin = oracle.frozen_eval(sc, cam, st, 0, dp=np.zeros(3), g=g)
+    base_l1 = oracle.frozen_eval(sc, cam, st, 0, dp=np.zeros(3), target=tgt)
+    scale = np.abs(S).reshape(len(S), -1).max(1)
+    cand = [i for i in np.argsort(-scale)[:12]]
+    n_neg = n_pos = 0
+    for i in cand:
+        s_max = float(np.exp(sc.log_scales[i].astype(np.float64)).max())
+        errs = []
+        for frac in (1e-1, 3e-2, 1e-2):
+            eps = frac * s_max
+            pred = 0.5 * eps * eps * lam[i]
+            meas = oracle.frozen_eval(sc, cam, st, i, mix_v=eps * v[i], g=g) - base_lin
+            errs.append(abs(meas - pred))
+            if frac == 1e-2:
+                assert abs(meas - pred) <= 1e-3 * abs(pred) + 1e-15
+                assert (meas < 0) == (lam[i] < 0)
+                meas1 = oracle.frozen_eval(sc, cam, st, i, mix_v=eps * v[i], target=tgt) - base_l1
+                assert (meas1 < 0) == (lam[i] < 0)
+                # the largest eigenvector direction gives the largest eigenvalue's change
+                pmax = 0.5 * eps * eps * ev[i, 2]
+                mmax = oracle.frozen_eval(sc, cam, st, i, mix_v=eps * V[i, 2], g=g) - base_lin
+                assert abs(mmax - pmax) <= 1e-3 * abs(pmax) + 1e-15
+        # remainder is higher order (symmetric split => odd orders cancel)
+        slope = np.log(errs[0] / errs[2]) / np.log(10.0)
+        assert slope > 2.9, slope
+        n_neg += lam[i] < 0
+        n_pos += ev[i, 2] > 0
+    assert n_neg > 0 and n_pos > 0
+
+
+def test_split_along_v_min_is_optimal():
+    """No direction beats +-v_min (Theorem 2): over random unit directions the
+    second-order change never goes below eps^2 lambda_min / 2."""
+    sc, cam, st, g, tgt, S = _setup_l1(1)
+    lam, v = oracle.eig3_min(S)
+    i = int(np.argmin(lam))
+    eps = 1e-2 * float(np.exp(sc.log_scales[i].astype(np.float64)).max())
+    base = oracle.frozen_eval(sc, cam, st, i, dp=np.zeros(3), g=g)
+    best = oracle.frozen_eval(sc, cam, st, i, mix_v=eps * v[i], g=g) - base
+    rng = np.random.default_rng(0)
+    for _ in range(300):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        dv = oracle.frozen_eval(sc, cam, st, i, mix_v=eps * d, g=g) - base
+        assert dv >= best - 1e-6 * abs(best)
+
+
+# --------------------------------------------------------------------------
+# Eigen-solve: trig formula vs Jacobi vs LAPACK, identities, degenerate cases
+# --------------------------------------------------------------------------
+
+def _rand_sym(rng, n):
+    A = rng.normal(size=(n, 3, 3))
+    return A + np.transpose(A, (0, 2, 1))
+
+
+def test_eig_trig_matches_jacobi_and_lapack():
+    rng = np.random.default_rng(0)
+    A = _rand_sym(rng, 2000)
+    # known spectra: U diag(l) U^T with repeated and near-repeated eigenvalues
+    U = np.linalg.qr(rng.normal(size=(300, 3, 3)))[0]
+    ls = rng.normal(size=(300, 3))
+    ls[:100, 1] = ls[:100, 0]
+    ls[100:150, 1] = ls[100:150, 0] + 1e-9
+    B = np.einsum("nij,nj,nkj->nik", U, ls, U)
+    A = np.concatenate([A, B])
+    lam, v = oracle.eig3_min(A)
+    ev, V = oracle.jacobi3(A)
+    ref = np.linalg.eigvalsh(A)
+    nrm = np.linalg.norm(A.reshape(len(A), -1), axis=1)
+    sep = (ref[:, 1] - ref[:, 0]) > 1e-6 * nrm
+    # arccos near +-1 loses half the digits at a repeated minimum eigenvalue
+    assert np.all(np.abs(lam - ref[:, 0])[sep] <= 1e-12 * nrm[sep])
+    assert np.all(np.abs(lam - ref[:, 0]) <= 1e-7 * nrm)
+    assert np.all(np.abs(ev - ref) <= 1e-12 * nrm[:, None])
+    res = np.linalg.norm(np.einsum("nij,nj->ni", A, v) - lam[:, None] * v, axis=1)
+    gap = ref[:, 1] - ref[:, 0]
+    ok = gap > 1e-6 * nrm
+    assert np.all(res[ok] <= 1e-10 * nrm[ok])
+    assert np.allclose(np.linalg.norm(v, axis=1), 1.0, atol=1e-14)
+    # trace and determinant identities (Jacobi's full spectrum)
+    assert np.all(np.abs(ev.sum(1) - np.trace(A, axis1=1, axis2=2)) <= 1e-12 * nrm)
+    assert np.all(np.abs(ev.prod(1) - np.linalg.det(A)) <= 1e-11 * nrm ** 3)
+    # agreement of eigenvectors where the gap is clear
+    cosang = np.abs(np.einsum("ni,ni->n", v, V[:, 0, :]))
+    assert np.all(1 - cosang[ok & (gap > 1e-3 * nrm)] < 1e-10)
+
+
+def test_eig_degenerate_cases():
+    # zero and scalar matrices: lambda = q, v = e_x
+    lam, v = oracle.eig3_min(np.stack([np.zeros((3, 3)), 2.5 * np.eye(3)]))
+    assert lam.tolist() == [0.0, 2.5]
+    assert v.tolist() == [[1, 0, 0], [1, 0, 0]]
+    # diagonal: exact minimum and axis
+    lam, v = oracle.eig3_min(np.diag([3.0, -1.0, 2.0])[None])
+    assert abs(lam[0] + 1.0) < 1e-14 and np.allclose(v[0], [0, 1, 0], atol=1e-12)
+    # rank-one negative: double zero eigenvalue above a negative one
+    u = np.array([1.0, 2.0, -2.0]) / 3.0
+    lam, v = oracle.eig3_min((-4.0 * np.outer(u, u))[None])
+    assert abs(lam[0] + 4.0) < 1e-12 and abs(abs(v[0] @ u) - 1) < 1e-12
+    # repeated minimum: v is any unit vector of the eigenspace, canonical sign
+    lam, v = oracle.eig3_min(np.diag([-1.0, -1.0, 5.0])[None])
+    assert abs(lam[0] + 1.0) < 1e-12 and abs(v[0, 2]) < 1e-12
+    assert abs(np.linalg.norm(v[0]) - 1) < 1e-12
+    k = int(np.argmax(np.abs(v[0])))
+    assert v[0, k] > 0
+
+
+# --------------------------------------------------------------------------
+# Split output (Theorem 2, Algorithm 1)
+# --------------------------------------------------------------------------
+
+def test_split_output_invariants():
+    sc, cam, st, g, tgt, S = _setup_l1(0)
+    lam, v = oracle.eig3_min(S)
+    out = oracle.split(sc, lam, v, eps_split=-1e-6, step_scale=0.5)
+    flags = lam < -1e-6
+    n = sc.n
+    assert out["n_out"] == n + flags.sum()
+    assert np.array_equal(out["flags"], flags)
+    par = out["parent"]
+    assert np.array_equal(par[:n], np.arange(n))
+    assert np.array_equal(par[n:], np.nonzero(flags)[0])
+    o = 1 / (1 + np.exp(-sc.opacity_logit.astype(np.float64)))
+    for row2, i in enumerate(np.nonzero(flags)[0]):
+        j = n + row2
+        m1, m2 = out["means"][i], out["means"][j]
+        assert np.allclose(0.5 * (m1 + m2), sc.means[i].astype(np.float64), atol=1e-12)
+        eps = 0.5 * np.exp(sc.log_scales[i].astype(np.float64)).max()
+        assert np.allclose(m1 - m2, 2 * eps * v[i], atol=1e-12)
+        o1 = 1 / (1 + np.exp(-out["opacity_logit"][i]))
+        o2 = 1 / (1 + np.exp(-out["opacity_logit"][j]))
+        assert abs(o1 + o2 - o[i]) < 1e-12 and abs(o1 - o2) < 1e-15
+        for f in ("log_scales", "quats", "sh"):
+            assert np.array_equal(out[f][j], getattr(sc, f)[i].astype(np.float64))
+    keep = ~flags
+    assert np.array_equal(out["means"][:n][keep], sc.means[keep].astype(np.float64))
+    assert np.array_equal(out["opacity_logit"][:n][keep], sc.opacity_logit[keep].astype(np.float64))
+    # gradient gate (compactest condition)
+    gn = np.random.default_rng(0).uniform(size=n)
+    out2 = oracle.split(sc, lam, v, -1e-6, 0.5, grad_norm=gn, eps_grad=0.5)
+    assert np.array_equal(out2["flags"], flags & (gn <= 0.5))
