@@ -1,0 +1,238 @@
+/*
+ * steepgs.h -- C ABI of the GB300 (sm_103a) SteepGS splitting path.
+ *
+ * The path follows "Steepest Descent Density Control for Compact 3D Gaussian
+ * Splatting" (arXiv 2505.05587):
+ *   sgs_project                    Section 3, Eq. sigma_3D / sigma_2D and the
+ *                                  affine-projection footnote: EWA projection.
+ *   sgs_bin_sort                   Section 3 ("sorts points according to
+ *                                  view-dependent depth"): tile binning and
+ *                                  (tile, depth) radix sort.
+ *   sgs_render_fwd                 Section 3, Eq. alpha_blend.
+ *   sgs_l1_loss_grad               Section 3, Eq. loss with the L1 error.
+ *   sgs_render_bwd_with_splitting  Section 4.4 and Algorithm 1 (accumulate
+ *                                  gradients and S^(i) = E[dl/dsigma Hess sigma])
+ *                                  with the Appendix's closed-form Hessian.
+ *   sgs_densify_split              Theorem 2, Algorithm 1 and the Appendix
+ *                                  "Eigendecomposition": minimum eigenpair of
+ *                                  S/T_split, split into p +- eps v_min with
+ *                                  opacity o/2, prefix-sum compaction.
+ *
+ * Conventions shared by every call
+ *   - Every array pointer is a DEVICE pointer owned by the caller, unless a
+ *     field says otherwise.  The library never allocates device memory: scratch
+ *     comes from a caller workspace sized by the matching *_workspace_size.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream) and returns an int status (SGS_OK or an SGS_ERR_*
+ *     code).  Argument errors are detected on the host before any launch and
+ *     leave every output untouched.  SGS_ERR_CUDA means a launch failed; the
+ *     CUDA error code is kept for sgs_get_last_cuda_error().
+ *   - Data-dependent sizes (instance count M, split count) are written to
+ *     caller-owned device integers.  When a size exceeds the caller's capacity
+ *     the kernels write only within capacity (never out of bounds) and the
+ *     caller sees the overflow by comparing the count it reads back with the
+ *     capacity it passed.
+ *   - Layouts are structure-of-arrays, float32, row-major:
+ *       means [N,3], log_scales [N,3], quats [N,4] as (w,x,y,z) (need not be
+ *       unit: the rotation uses q/|q|), opacity_logit [N] (opacity =
+ *       sigmoid), sh [N,K,3] with K = (sh_degree+1)^2 and sh_degree <= 3;
+ *       images [H,W,3]; per-pixel maps [H,W].
+ *   - Cameras: x_cam = R x_world + t, OpenCV axes (x right, y down, z
+ *     forward), pinhole intrinsics fx, fy, cx, cy; pixel (px,py) is sampled at
+ *     its integer coordinates.
+ */
+#ifndef STEEPGS_H
+#define STEEPGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SGS_OK 0
+#define SGS_ERR_INVALID_ARG 1
+#define SGS_ERR_WORKSPACE 2
+#define SGS_ERR_CAPACITY 3
+#define SGS_ERR_CUDA 4
+#define SGS_ERR_TIMEOUT 5
+#define SGS_ERR_UNSUPPORTED 6
+
+/* Gaussian parameters theta^(i) = (p, Sigma via quaternion + log-scale, o, SH
+ * colour) (Section 3, "Scene Representation").  Read-only input. */
+typedef struct sgs_gaussians {
+    const float *means;
+    const float *log_scales;
+    const float *quats;
+    const float *opacity_logit;
+    const float *sh;
+    int32_t n;
+    int32_t sh_degree;
+} sgs_gaussians;
+
+/* Writable Gaussian arrays (output of sgs_densify_split), same layouts. */
+typedef struct sgs_gaussians_mut {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logit;
+    float *sh;
+} sgs_gaussians_mut;
+
+/* Pinhole camera, host struct passed by pointer (copied at the call). */
+typedef struct sgs_camera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_z;       /* Gaussians with camera z <= near_z are culled */
+} sgs_camera;
+
+/* Rasterisation constants, host struct passed by pointer.
+ * tile_w x tile_h must be one of 16x16, 16x8, 8x8, 32x8.
+ * alpha = min(alpha_max, o G); a pair is skipped when alpha < alpha_min; the
+ * walk of a pixel stops before the Gaussian that would bring transmittance
+ * below T_min; the support is the radius_sigma-sigma bounding square of the
+ * 2-D covariance (dilated by `dilation` on its diagonal); the Jacobian's
+ * tx/tz, ty/tz are clamped to +-fov_clamp * (W/2)/fx, (H/2)/fy. */
+typedef struct sgs_settings {
+    int32_t tile_w, tile_h;
+    float alpha_min, alpha_max, T_min, radius_sigma, dilation, fov_clamp;
+    float bg[3];
+} sgs_settings;
+
+/* Per-view projected state written by sgs_project, capacity >= n rows.
+ *   xy          [N,4] (mu_x, mu_y, mu_x_lo, mu_y_lo): 2-D mean in pixels as an
+ *               unevaluated float pair mu = hi + lo (about 44 bits).
+ *   conic_opac  [N,4] (Q00, Q01, Q11, opacity), Q = Sigma2D^-1.
+ *   rgb         [N,4] (r, g, b, 0) after the SH evaluation and the clamp at 0.
+ *   depth       [N]   camera-space z, float32 (the depth sort key).
+ *   rect        [N,4] int16 (x_lo, y_lo, x_hi, y_hi), inclusive tile rect;
+ *               (0,0,-1,-1) for a culled Gaussian.
+ *   tiles_touched [N] number of tiles in rect (0 = culled). */
+typedef struct sgs_proj {
+    float *xy;
+    float *conic_opac;
+    float *rgb;
+    float *depth;
+    int16_t *rect;
+    uint32_t *tiles_touched;
+} sgs_proj;
+
+/* Binned, sorted instances written by sgs_bin_sort.
+ *   gids     [capacity]  Gaussian id of each (Gaussian, tile) instance, in
+ *                        (tile id, float32 depth bits, Gaussian id) order.
+ *   keys     [capacity]  optional (NULL to skip): (tile id << 32) | depth bits.
+ *   ranges   [T,2]       per tile [start, end) into gids, T = tiles_x*tiles_y,
+ *                        tile id = ty * tiles_x + tx.
+ *   count    [1] int32   M, the number of instances (may exceed capacity).
+ *   capacity             rows available in gids / keys. */
+typedef struct sgs_bins {
+    uint32_t *gids;
+    uint64_t *keys;
+    uint32_t *ranges;
+    int32_t *count;
+    int64_t capacity;
+} sgs_bins;
+
+/* Parameter gradients, accumulated (+=) by sgs_render_bwd_with_splitting. */
+typedef struct sgs_grads {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logit;
+    float *sh;
+} sgs_grads;
+
+/* Human-readable name of a status code (static storage). */
+const char *sgs_error_string(int status);
+/* CUDA error code behind the last SGS_ERR_CUDA returned on this thread. */
+int sgs_get_last_cuda_error(void);
+/* Library version, major*10000 + minor*100 + patch. */
+int sgs_version(void);
+
+/* Projection (Section 3, Eq. sigma_2D and the affine-Pi footnote; Pi is the
+ * pinhole map, linearised at p as P = J W for the 2-D covariance).
+ * Writes `out` rows [0, g->n).  The integer stage (depth, tile rect) uses a
+ * fixed sequence of IEEE float32 operations so that it is reproducible
+ * bit-for-bit.  Errors: SGS_ERR_INVALID_ARG on NULL arrays, n < 0,
+ * sh_degree outside [0,3], non-positive image size or unsupported tile. */
+int sgs_project(const sgs_gaussians *g, const sgs_camera *cam, const sgs_settings *st,
+                const sgs_proj *out, void *stream);
+
+/* Workspace bytes needed by sgs_bin_sort for n Gaussians, `capacity`
+ * instances and `num_tiles` tiles.  Returns SGS_OK or SGS_ERR_INVALID_ARG. */
+int sgs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t num_tiles, size_t *bytes);
+
+/* Binning and depth sort (Section 3): a stable radix sort of the Gaussians by
+ * float32 depth bits, emission of one instance per covered tile in that order,
+ * then a stable radix sort of the instances by tile id; equivalent to one
+ * stable sort on the key (tile << 32 | depth bits) of instances emitted in
+ * Gaussian order.  Reads proj->depth, proj->rect, proj->tiles_touched.
+ * Errors: SGS_ERR_INVALID_ARG, SGS_ERR_WORKSPACE when ws_bytes is too small. */
+int sgs_bin_sort(const sgs_proj *proj, int32_t n, const sgs_camera *cam, const sgs_settings *st,
+                 const sgs_bins *out, void *ws, size_t ws_bytes, void *stream);
+
+/* Forward compositing (Section 3, Eq. alpha_blend), front to back over each
+ * tile's list: C = sum c_i alpha_i T_i + T_final bg.
+ * Outputs image [H,W,3], final_T [H,W] (transmittance after the last
+ * composited Gaussian) and n_contrib [H,W] (1 + list position of the last
+ * composited Gaussian, 0 if none), the two maps the backward pass needs. */
+int sgs_render_fwd(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
+                   const sgs_settings *st, float *image, float *final_T, uint32_t *n_contrib,
+                   void *stream);
+
+/* L1 photometric loss (Section 3, Eq. loss, l = |.|):
+ * loss += mean over pixels and channels of |image - target| / n_views and
+ * dL_dimage = sign(image - target) / (3 H W n_views).  loss is one device
+ * float, accumulated (+=); dL_dimage [H,W,3] is overwritten. */
+int sgs_l1_loss_grad(const float *image, const float *target, int32_t height, int32_t width,
+                     int32_t n_views, float *dL_dimage, float *loss, void *stream);
+
+/* Workspace bytes for sgs_render_bwd_with_splitting with n Gaussians. */
+int sgs_render_bwd_workspace_size(int32_t n, size_t *bytes);
+
+/* Backward pass fused with the splitting-matrix accumulation (Section 4.4,
+ * Algorithm 1).  Back to front over each pixel's list, recomputing the
+ * transmittance by division; dL/dalpha is reduced per Gaussian with warp
+ * shuffles and one atomic per warp.  With w = dL/dalpha * alpha and
+ * u = Q (x - mu) per composited, unclamped pair, the splitting matrix of this
+ * view is S += P^T (sum w u u^T - (sum w) Q) P (the Appendix's Hessian
+ * sigma (Y Y^T - P^T Q P), Y = P^T u, summed over pixels).
+ * grads are accumulated (+=); S_accum [N,6] = (xx, xy, xz, yy, yz, zz) is
+ * accumulated (+=), so calling once per view sums over views.
+ * Errors: SGS_ERR_INVALID_ARG, SGS_ERR_WORKSPACE. */
+int sgs_render_bwd_with_splitting(const sgs_gaussians *g, const sgs_proj *proj, const sgs_bins *bins,
+                                  const sgs_camera *cam, const sgs_settings *st,
+                                  const float *final_T, const uint32_t *n_contrib,
+                                  const float *dL_dimage, const sgs_grads *grads, float *S_accum,
+                                  void *ws, size_t ws_bytes, void *stream);
+
+/* Workspace bytes for sgs_densify_split with n Gaussians. */
+int sgs_densify_split_workspace_size(int32_t n, size_t *bytes);
+
+/* Steepest density control (Theorem 2, Algorithm 1, Appendix
+ * "Eigendecomposition").  For each Gaussian: S_bar = S_accum * inv_T_split;
+ * lambda_min, v_min by the trigonometric root formula (float32) refined by
+ * one Rayleigh quotient; flag = lambda_min < eps_split, and, when grad_norm is
+ * not NULL, grad_norm[i] <= eps_grad (the "compactest" condition).
+ * Output rows: row i = Gaussian i, moved to p + eps_i v_min with opacity o/2
+ * when flagged; row N + excl[i] = its second offspring p - eps_i v_min with
+ * opacity o/2 (excl = exclusive prefix sum of the flags); scales, rotation and
+ * SH are copied; eps_i = step_scale * max_k exp(log_scale_ik).
+ * d_n_out (device int32) receives N + number of flags; rows at or beyond
+ * `capacity` are not written.  parent_index [capacity] (int32, may be NULL),
+ * lam_min_out [N] and v_min_out [N,3] (may be NULL) are written.
+ * `out` must not alias `in`.  Errors: SGS_ERR_INVALID_ARG, SGS_ERR_WORKSPACE. */
+int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, float inv_T_split,
+                      float eps_split, float step_scale, const float *grad_norm, float eps_grad,
+                      const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
+                      int32_t *parent_index, float *lam_min_out, float *v_min_out,
+                      void *ws, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STEEPGS_H */

@@ -1,0 +1,314 @@
+"""Thin Python binding of libsteepgs (include/steepgs.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch provides device memory and the stream.  There is no CPU
+fallback: if the library is missing, importing this module raises.
+
+Functions keep the C names without the ``sgs_`` prefix: project, bin_sort,
+render_fwd, l1_loss_grad, render_bwd_with_splitting, densify_split, and the
+workspace-size queries.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsteepgs.so")
+
+SGS_OK = 0
+ERRORS = {1: "invalid argument", 2: "workspace too small", 3: "capacity exceeded", 4: "CUDA error",
+          5: "timeout", 6: "unsupported"}
+
+
+class SteepGSError(RuntimeError):
+    def __init__(self, fn: str, status: int, cuda: int = 0):
+        msg = f"{fn}: {ERRORS.get(status, 'unknown')} (status {status})"
+        if status == 4:
+            msg += f", cudaError {cuda}"
+        super().__init__(msg)
+        self.status = status
+
+
+# --------------------------------------------------------------------------
+# ctypes mirrors of the C structs
+# --------------------------------------------------------------------------
+class Gaussians(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int32),
+                ("sh_degree", C.c_int32)]
+
+
+class GaussiansMut(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("near_z", C.c_float)]
+
+
+class Settings(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("alpha_min", C.c_float),
+                ("alpha_max", C.c_float), ("T_min", C.c_float), ("radius_sigma", C.c_float),
+                ("dilation", C.c_float), ("fov_clamp", C.c_float), ("bg", C.c_float * 3)]
+
+
+class Proj(C.Structure):
+    _fields_ = [("xy", C.c_void_p), ("conic_opac", C.c_void_p), ("rgb", C.c_void_p),
+                ("depth", C.c_void_p), ("rect", C.c_void_p), ("tiles_touched", C.c_void_p)]
+
+
+class Bins(C.Structure):
+    _fields_ = [("gids", C.c_void_p), ("keys", C.c_void_p), ("ranges", C.c_void_p),
+                ("count", C.c_void_p), ("capacity", C.c_int64)]
+
+
+class Grads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libsteepgs.so; raises (no fallback) when it is not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libsteepgs.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P, I32, I64, F, SZ = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_size_t
+        L.sgs_error_string.restype = C.c_char_p
+        L.sgs_error_string.argtypes = [C.c_int]
+        L.sgs_get_last_cuda_error.restype = C.c_int
+        L.sgs_version.restype = C.c_int
+        L.sgs_project.argtypes = [P, P, P, P, P]
+        L.sgs_bin_sort_workspace_size.argtypes = [I32, I64, I32, C.POINTER(SZ)]
+        L.sgs_bin_sort.argtypes = [P, I32, P, P, P, P, SZ, P]
+        L.sgs_render_fwd.argtypes = [P, P, P, P, P, P, P, P]
+        L.sgs_l1_loss_grad.argtypes = [P, P, I32, I32, I32, P, P, P]
+        L.sgs_render_bwd_workspace_size.argtypes = [I32, C.POINTER(SZ)]
+        L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, P, P, SZ, P]
+        L.sgs_densify_split_workspace_size.argtypes = [I32, C.POINTER(SZ)]
+        L.sgs_densify_split.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P, SZ, P]
+        for name in ("sgs_project", "sgs_bin_sort_workspace_size", "sgs_bin_sort", "sgs_render_fwd",
+                     "sgs_l1_loss_grad", "sgs_render_bwd_workspace_size", "sgs_render_bwd_with_splitting",
+                     "sgs_densify_split_workspace_size", "sgs_densify_split"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(fn: str, status: int):
+    if status != SGS_OK:
+        raise SteepGSError(fn, status, lib().sgs_get_last_cuda_error())
+
+
+def _p(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+# --------------------------------------------------------------------------
+# Tensor bundles
+# --------------------------------------------------------------------------
+@dataclass
+class GaussianTensors:
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logit: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    def c(self) -> Gaussians:
+        for t in (self.means, self.log_scales, self.quats, self.opacity_logit, self.sh):
+            if t.dtype != torch.float32:
+                raise TypeError("Gaussian parameters must be float32")
+        return Gaussians(_p(self.means), _p(self.log_scales), _p(self.quats), _p(self.opacity_logit),
+                         _p(self.sh), self.n, self.sh_degree)
+
+    def c_mut(self) -> GaussiansMut:
+        return GaussiansMut(_p(self.means), _p(self.log_scales), _p(self.quats), _p(self.opacity_logit),
+                            _p(self.sh))
+
+    @staticmethod
+    def empty(n: int, sh_degree: int, device="cuda") -> "GaussianTensors":
+        K = (sh_degree + 1) ** 2
+        f = dict(device=device, dtype=torch.float32)
+        return GaussianTensors(torch.empty(n, 3, **f), torch.empty(n, 3, **f), torch.empty(n, 4, **f),
+                               torch.empty(n, **f), torch.empty(n, K, 3, **f), sh_degree)
+
+    @staticmethod
+    def from_scene(scene, device="cuda") -> "GaussianTensors":
+        f = dict(device=device, dtype=torch.float32)
+        return GaussianTensors(torch.as_tensor(scene.means).to(**f).contiguous(),
+                               torch.as_tensor(scene.log_scales).to(**f).contiguous(),
+                               torch.as_tensor(scene.quats).to(**f).contiguous(),
+                               torch.as_tensor(scene.opacity_logit).to(**f).contiguous(),
+                               torch.as_tensor(scene.sh).to(**f).contiguous(), int(scene.sh_degree))
+
+    def zeros_like(self) -> "GaussianTensors":
+        return GaussianTensors(torch.zeros_like(self.means), torch.zeros_like(self.log_scales),
+                               torch.zeros_like(self.quats), torch.zeros_like(self.opacity_logit),
+                               torch.zeros_like(self.sh), self.sh_degree)
+
+    def narrow(self, n: int) -> "GaussianTensors":
+        return GaussianTensors(self.means[:n], self.log_scales[:n], self.quats[:n], self.opacity_logit[:n],
+                               self.sh[:n], self.sh_degree)
+
+    def tensors(self):
+        return (self.means, self.log_scales, self.quats, self.opacity_logit, self.sh)
+
+
+@dataclass
+class ProjBuffers:
+    xy: torch.Tensor           # [N,4] f32
+    conic_opac: torch.Tensor   # [N,4] f32
+    rgb: torch.Tensor          # [N,4] f32
+    depth: torch.Tensor        # [N]   f32
+    rect: torch.Tensor         # [N,4] i16
+    tiles_touched: torch.Tensor  # [N] i32 (uint32 in C)
+
+    @staticmethod
+    def alloc(n: int, device="cuda") -> "ProjBuffers":
+        f = dict(device=device, dtype=torch.float32)
+        return ProjBuffers(torch.empty(n, 4, **f), torch.empty(n, 4, **f), torch.empty(n, 4, **f),
+                           torch.empty(n, **f), torch.empty(n, 4, device=device, dtype=torch.int16),
+                           torch.empty(n, device=device, dtype=torch.int32))
+
+    def c(self) -> Proj:
+        return Proj(_p(self.xy), _p(self.conic_opac), _p(self.rgb), _p(self.depth), _p(self.rect),
+                    _p(self.tiles_touched))
+
+
+@dataclass
+class BinBuffers:
+    gids: torch.Tensor     # [cap] i32 (uint32 in C)
+    keys: torch.Tensor | None  # [cap] i64 (uint64 in C) or None
+    ranges: torch.Tensor   # [T,2] i32 (uint32 in C)
+    count: torch.Tensor    # [1] i32
+    capacity: int
+
+    @staticmethod
+    def alloc(capacity: int, num_tiles: int, with_keys=False, device="cuda") -> "BinBuffers":
+        i32 = dict(device=device, dtype=torch.int32)
+        return BinBuffers(torch.empty(max(capacity, 1), **i32),
+                          torch.empty(max(capacity, 1), device=device, dtype=torch.int64) if with_keys else None,
+                          torch.empty(num_tiles, 2, **i32), torch.zeros(1, **i32), capacity)
+
+    def c(self) -> Bins:
+        return Bins(_p(self.gids), _p(self.keys), _p(self.ranges), _p(self.count), self.capacity)
+
+
+def camera_c(cam) -> Camera:
+    """Marshals a camera with fields R (3x3), t (3), fx, fy, cx, cy, width, height, near_z."""
+    R = [float(x) for x in torch.as_tensor(cam.R, dtype=torch.float32).reshape(-1).tolist()]
+    t = [float(x) for x in torch.as_tensor(cam.t, dtype=torch.float32).reshape(-1).tolist()]
+    return Camera((C.c_float * 9)(*R), (C.c_float * 3)(*t), cam.fx, cam.fy, cam.cx, cam.cy,
+                  int(cam.width), int(cam.height), getattr(cam, "near_z", 0.2))
+
+
+def settings_c(st) -> Settings:
+    return Settings(st.tile_w, st.tile_h, st.alpha_min, st.alpha_max, st.T_min, st.radius_sigma,
+                    st.dilation, st.fov_clamp, (C.c_float * 3)(*[float(x) for x in st.bg]))
+
+
+def num_tiles(cam, st) -> int:
+    return ((cam.width + st.tile_w - 1) // st.tile_w) * ((cam.height + st.tile_h - 1) // st.tile_h)
+
+
+# --------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# --------------------------------------------------------------------------
+def project(g: GaussianTensors, cam, st, out: ProjBuffers, stream=None):
+    gc, cc, sc, oc = g.c(), camera_c(cam), settings_c(st), out.c()
+    _check("sgs_project", lib().sgs_project(C.byref(gc), C.byref(cc), C.byref(sc), C.byref(oc), _stream(stream)))
+
+
+def bin_sort_workspace_size(n: int, capacity: int, tiles: int) -> int:
+    b = C.c_size_t()
+    _check("sgs_bin_sort_workspace_size", lib().sgs_bin_sort_workspace_size(n, capacity, tiles, C.byref(b)))
+    return b.value
+
+
+def bin_sort(proj: ProjBuffers, n: int, cam, st, out: BinBuffers, ws: torch.Tensor, stream=None):
+    pc, cc, sc, oc = proj.c(), camera_c(cam), settings_c(st), out.c()
+    _check("sgs_bin_sort", lib().sgs_bin_sort(C.byref(pc), n, C.byref(cc), C.byref(sc), C.byref(oc), _p(ws),
+                                               ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def render_fwd(proj: ProjBuffers, bins: BinBuffers, cam, st, image, final_T, n_contrib, stream=None):
+    pc, bc, cc, sc = proj.c(), bins.c(), camera_c(cam), settings_c(st)
+    _check("sgs_render_fwd", lib().sgs_render_fwd(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc), _p(image),
+                                                   _p(final_T), _p(n_contrib), _stream(stream)))
+
+
+def l1_loss_grad(image, target, n_views: int, dL_dimage, loss, stream=None):
+    H, W = int(image.shape[0]), int(image.shape[1])
+    _check("sgs_l1_loss_grad", lib().sgs_l1_loss_grad(_p(image), _p(target), H, W, n_views, _p(dL_dimage),
+                                                       _p(loss), _stream(stream)))
+
+
+def render_bwd_workspace_size(n: int) -> int:
+    b = C.c_size_t()
+    _check("sgs_render_bwd_workspace_size", lib().sgs_render_bwd_workspace_size(n, C.byref(b)))
+    return b.value
+
+
+def render_bwd_with_splitting(g: GaussianTensors, proj: ProjBuffers, bins: BinBuffers, cam, st, final_T,
+                              n_contrib, dL_dimage, grads: GaussianTensors, S_accum, ws, stream=None):
+    gc, pc, bc, cc, sc = g.c(), proj.c(), bins.c(), camera_c(cam), settings_c(st)
+    grc = Grads(*[_p(t) for t in grads.tensors()])
+    _check("sgs_render_bwd_with_splitting",
+           lib().sgs_render_bwd_with_splitting(C.byref(gc), C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
+                                               _p(final_T), _p(n_contrib), _p(dL_dimage), C.byref(grc),
+                                               _p(S_accum), _p(ws), ws.numel() * ws.element_size(),
+                                               _stream(stream)))
+
+
+def densify_split_workspace_size(n: int) -> int:
+    b = C.c_size_t()
+    _check("sgs_densify_split_workspace_size", lib().sgs_densify_split_workspace_size(n, C.byref(b)))
+    return b.value
+
+
+def densify_split(g: GaussianTensors, S_accum, inv_T_split: float, eps_split: float, step_scale: float,
+                  grad_norm, eps_grad: float, out: GaussianTensors, capacity: int, d_n_out, parent_index,
+                  lam_min_out, v_min_out, ws, stream=None):
+    gc, oc = g.c(), out.c_mut()
+    _check("sgs_densify_split",
+           lib().sgs_densify_split(C.byref(gc), _p(S_accum), inv_T_split, eps_split, step_scale, _p(grad_norm),
+                                   eps_grad, C.byref(oc), capacity, _p(d_n_out), _p(parent_index),
+                                   _p(lam_min_out), _p(v_min_out), _p(ws), ws.numel() * ws.element_size(),
+                                   _stream(stream)))
+
+
+def workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)

@@ -1,0 +1,194 @@
+// C ABI of libsteepgs (declarations and contracts: include/steepgs.h).
+// Host-side argument checks, workspace carving and kernel launches only.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace sgs {
+
+bool tile_supported(int tw, int th) {
+    return (tw == 16 && th == 16) || (tw == 16 && th == 8) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
+}
+
+CamDev make_cam(const sgs_camera& c, const sgs_settings& s) {
+    CamDev d;
+    memcpy(d.R, c.R, sizeof(d.R));
+    memcpy(d.t, c.t, sizeof(d.t));
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    d.width = c.width; d.height = c.height;
+    d.near_z = c.near_z;
+    d.limx = d.limy = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+        double v = -((double)c.R[k] * c.t[0] + (double)c.R[3 + k] * c.t[1] + (double)c.R[6 + k] * c.t[2]);
+        d.cc[k] = (float)v;
+    }
+    d.gx = (c.width + s.tile_w - 1) / s.tile_w;
+    d.gy = (c.height + s.tile_h - 1) / s.tile_h;
+    return d;
+}
+
+SetDev make_set(const sgs_settings& s) {
+    SetDev d;
+    d.tile_w = s.tile_w; d.tile_h = s.tile_h;
+    d.alpha_min = s.alpha_min; d.alpha_max = s.alpha_max; d.T_min = s.T_min;
+    d.radius_sigma = s.radius_sigma; d.dilation = s.dilation; d.fov_clamp = s.fov_clamp;
+    d.bg[0] = s.bg[0]; d.bg[1] = s.bg[1]; d.bg[2] = s.bg[2];
+    return d;
+}
+
+static thread_local int g_last_cuda = 0;
+
+static int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SGS_OK;
+    g_last_cuda = (int)e;
+    return SGS_ERR_CUDA;
+}
+
+static bool valid_cam(const sgs_camera* c) {
+    return c && c->width > 0 && c->height > 0 && c->width <= 32767 * 8 && c->height <= 32767 * 8 &&
+           isfinite(c->fx) && isfinite(c->fy) && c->fx > 0.0f && c->fy > 0.0f;
+}
+
+static bool valid_settings(const sgs_settings* s) {
+    return s && tile_supported(s->tile_w, s->tile_h) && s->alpha_max > 0.0f && s->alpha_max <= 1.0f &&
+           s->alpha_min >= 0.0f && s->T_min >= 0.0f && s->radius_sigma > 0.0f && s->dilation >= 0.0f &&
+           s->fov_clamp > 0.0f;
+}
+
+static bool valid_gaussians(const sgs_gaussians* g) {
+    if (!g || g->n < 0 || g->sh_degree < 0 || g->sh_degree > kMaxShDegree) return false;
+    if (g->n == 0) return true;
+    return g->means && g->log_scales && g->quats && g->opacity_logit && g->sh;
+}
+
+static bool tiles_fit(const sgs_camera* c, const sgs_settings* s) {
+    int64_t gx = (c->width + s->tile_w - 1) / s->tile_w;
+    int64_t gy = (c->height + s->tile_h - 1) / s->tile_h;
+    return gx <= 32767 && gy <= 32767 && gx * gy < (int64_t)1 << 31;
+}
+
+}  // namespace sgs
+
+using namespace sgs;
+
+extern "C" {
+
+const char* sgs_error_string(int status) {
+    switch (status) {
+        case SGS_OK: return "ok";
+        case SGS_ERR_INVALID_ARG: return "invalid argument";
+        case SGS_ERR_WORKSPACE: return "workspace too small";
+        case SGS_ERR_CAPACITY: return "capacity exceeded";
+        case SGS_ERR_CUDA: return "CUDA error";
+        case SGS_ERR_TIMEOUT: return "timeout";
+        case SGS_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+int sgs_get_last_cuda_error(void) { return g_last_cuda; }
+
+int sgs_version(void) { return 100; }
+
+int sgs_project(const sgs_gaussians* g, const sgs_camera* cam, const sgs_settings* st, const sgs_proj* out,
+                void* stream) {
+    if (!valid_gaussians(g) || !valid_cam(cam) || !valid_settings(st) || !out || !tiles_fit(cam, st))
+        return SGS_ERR_INVALID_ARG;
+    if (g->n > 0 && (!out->xy || !out->conic_opac || !out->rgb || !out->depth || !out->rect || !out->tiles_touched))
+        return SGS_ERR_INVALID_ARG;
+    return cuda_status(launch_project(*g, make_cam(*cam, *st), make_set(*st), *out, (cudaStream_t)stream));
+}
+
+int sgs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t num_tiles, size_t* bytes) {
+    if (n < 0 || capacity < 0 || num_tiles <= 0 || !bytes || capacity > ((int64_t)1 << 31) - 1)
+        return SGS_ERR_INVALID_ARG;
+    *bytes = bin_sort_ws_bytes(n, capacity, num_tiles);
+    return SGS_OK;
+}
+
+int sgs_bin_sort(const sgs_proj* proj, int32_t n, const sgs_camera* cam, const sgs_settings* st,
+                 const sgs_bins* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!proj || n < 0 || !valid_cam(cam) || !valid_settings(st) || !out || !tiles_fit(cam, st))
+        return SGS_ERR_INVALID_ARG;
+    if (!out->ranges || !out->count || out->capacity < 0 || out->capacity > ((int64_t)1 << 31) - 1)
+        return SGS_ERR_INVALID_ARG;
+    if (out->capacity > 0 && !out->gids) return SGS_ERR_INVALID_ARG;
+    if (n > 0 && (!proj->depth || !proj->rect || !proj->tiles_touched)) return SGS_ERR_INVALID_ARG;
+    CamDev cd = make_cam(*cam, *st);
+    if (!ws || ws_bytes < bin_sort_ws_bytes(n, out->capacity, cd.gx * cd.gy)) return SGS_ERR_WORKSPACE;
+    return cuda_status(launch_bin_sort(*proj, n, cd, make_set(*st), *out, ws, (cudaStream_t)stream));
+}
+
+int sgs_render_fwd(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,
+                   float* image, float* final_T, uint32_t* n_contrib, void* stream) {
+    if (!proj || !bins || !valid_cam(cam) || !valid_settings(st) || !image || !final_T || !n_contrib ||
+        !tiles_fit(cam, st) || !bins->ranges)
+        return SGS_ERR_INVALID_ARG;
+    return cuda_status(launch_render_fwd(*proj, *bins, make_cam(*cam, *st), make_set(*st), image, final_T,
+                                         n_contrib, (cudaStream_t)stream));
+}
+
+int sgs_l1_loss_grad(const float* image, const float* target, int32_t height, int32_t width, int32_t n_views,
+                     float* dL_dimage, float* loss, void* stream) {
+    if (!image || !target || height <= 0 || width <= 0 || n_views <= 0 || !dL_dimage || !loss)
+        return SGS_ERR_INVALID_ARG;
+    return cuda_status(launch_l1(image, target, height, width, n_views, dL_dimage, loss, (cudaStream_t)stream));
+}
+
+int sgs_render_bwd_workspace_size(int32_t n, size_t* bytes) {
+    if (n < 0 || !bytes) return SGS_ERR_INVALID_ARG;
+    *bytes = sizeof(float) * 16 * (size_t)(n > 0 ? n : 1) + 256;
+    return SGS_OK;
+}
+
+int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, const sgs_bins* bins,
+                                  const sgs_camera* cam, const sgs_settings* st, const float* final_T,
+                                  const uint32_t* n_contrib, const float* dL_dimage, const sgs_grads* grads,
+                                  float* S_accum, void* ws, size_t ws_bytes, void* stream) {
+    if (!valid_gaussians(g) || !proj || !bins || !valid_cam(cam) || !valid_settings(st) || !final_T ||
+        !n_contrib || !dL_dimage || !grads || !tiles_fit(cam, st) || !bins->ranges)
+        return SGS_ERR_INVALID_ARG;
+    if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit ||
+                     !grads->sh || !S_accum))
+        return SGS_ERR_INVALID_ARG;
+    size_t need = 0;
+    sgs_render_bwd_workspace_size(g->n, &need);
+    if (!ws || ws_bytes < need) return SGS_ERR_WORKSPACE;
+    if (g->n == 0) return SGS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* g2d = reinterpret_cast<float*>(align_up(reinterpret_cast<uintptr_t>(ws), 256));
+    if ((char*)g2d + sizeof(float) * 16 * (size_t)g->n > (char*)ws + ws_bytes) return SGS_ERR_WORKSPACE;
+    CamDev cd = make_cam(*cam, *st);
+    SetDev sd = make_set(*st);
+    cudaError_t e = cudaMemsetAsync(g2d, 0, sizeof(float) * 16 * (size_t)g->n, s);
+    if (e == cudaSuccess) e = launch_render_bwd(*proj, *bins, cd, sd, final_T, n_contrib, dL_dimage, g2d, s);
+    if (e == cudaSuccess) e = launch_project_bwd(*g, cd, sd, g2d, *grads, S_accum, s);
+    return cuda_status(e);
+}
+
+int sgs_densify_split_workspace_size(int32_t n, size_t* bytes) {
+    if (n < 0 || !bytes) return SGS_ERR_INVALID_ARG;
+    *bytes = densify_ws_bytes(n);
+    return SGS_OK;
+}
+
+int sgs_densify_split(const sgs_gaussians* in, const float* S_accum, float inv_T_split, float eps_split,
+                      float step_scale, const float* grad_norm, float eps_grad, const sgs_gaussians_mut* out,
+                      int64_t capacity, int32_t* d_n_out, int32_t* parent_index, float* lam_min_out,
+                      float* v_min_out, void* ws, size_t ws_bytes, void* stream) {
+    if (!valid_gaussians(in) || !out || !d_n_out || capacity < in->n || !isfinite(inv_T_split) ||
+        !isfinite(step_scale))
+        return SGS_ERR_INVALID_ARG;
+    if (in->n > 0 && (!S_accum || !out->means || !out->log_scales || !out->quats || !out->opacity_logit ||
+                      !out->sh))
+        return SGS_ERR_INVALID_ARG;
+    if (in->n > 0 && (out->means == in->means || out->sh == in->sh || out->opacity_logit == in->opacity_logit))
+        return SGS_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < densify_ws_bytes(in->n)) return SGS_ERR_WORKSPACE;
+    return cuda_status(launch_densify(*in, S_accum, inv_T_split, eps_split, step_scale, grad_norm, eps_grad, *out,
+                                      capacity, d_n_out, parent_index, lam_min_out, v_min_out, ws,
+                                      (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Internal declarations shared by the CUDA translation units of libsteepgs.
+// Not part of the public ABI (include/steepgs.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "steepgs.h"
+
+namespace sgs {
+
+constexpr int kMaxShDegree = 3;
+
+// ---------------------------------------------------------------------------
+// IEEE float32 operations that the compiler never contracts into FMA.  The
+// integer stage (depth key, tile rect) is written with these so that every
+// build produces the same bits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+// a*b + c with two roundings
+__device__ __forceinline__ float mad_rn(float a, float b, float c) { return __fadd_rn(__fmul_rn(a, b), c); }
+
+// Float32 state of one Gaussian in one view, produced by the integer stage.
+struct Stage {
+    bool culled;
+    float tx, ty, tz;      // camera-space mean
+    float ux, uy;          // clamped tx/tz, ty/tz
+    bool clx, cly;         // clamp active
+    float T[6];            // P = J W (2x3)
+    float Rq[9];           // rotation of the unit quaternion
+    float qn;              // |q|
+    float s[3];            // exp(log_scale)
+    float V[6];            // P Rq diag(s)
+    float a, b, c;         // Sigma2D with dilation
+    int x_lo, x_hi, y_lo, y_hi;
+};
+
+struct CamDev {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int width, height;
+    float near_z;
+    float limx, limy;       // Jacobian clamp limits
+    float cc[3];            // camera centre -R^T t
+    int gx, gy;             // tiles
+};
+
+struct SetDev {
+    int tile_w, tile_h;
+    float alpha_min, alpha_max, T_min, radius_sigma, dilation, fov_clamp;
+    float bg[3];
+};
+
+__device__ Stage integer_stage(const float* __restrict__ means, const float* __restrict__ log_scales,
+                               const float* __restrict__ quats, int i, const CamDev& cam,
+                               const SetDev& st);
+
+// Host helpers (defined in api.cu)
+CamDev make_cam(const sgs_camera& c, const sgs_settings& s);
+SetDev make_set(const sgs_settings& s);
+bool tile_supported(int tw, int th);
+
+// Launchers (host functions, enqueue on `stream`).
+cudaError_t launch_project(const sgs_gaussians& g, const CamDev& cam, const SetDev& st,
+                           const sgs_proj& out, cudaStream_t stream);
+cudaError_t launch_project_bwd(const sgs_gaussians& g, const CamDev& cam, const SetDev& st,
+                               const float* g2d, const sgs_grads& grads, float* S_accum,
+                               cudaStream_t stream);
+
+size_t bin_sort_ws_bytes(int n, int64_t capacity, int num_tiles);
+cudaError_t launch_bin_sort(const sgs_proj& proj, int n, const CamDev& cam, const SetDev& st,
+                            const sgs_bins& out, void* ws, cudaStream_t stream);
+
+cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
+                              const SetDev& st, float* image, float* final_T, uint32_t* n_contrib,
+                              cudaStream_t stream);
+cudaError_t launch_render_bwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
+                              const SetDev& st, const float* final_T, const uint32_t* n_contrib,
+                              const float* dL_dimage, float* g2d, cudaStream_t stream);
+
+cudaError_t launch_l1(const float* image, const float* target, int H, int W, int n_views,
+                      float* dL, float* loss, cudaStream_t stream);
+
+size_t densify_ws_bytes(int n);
+cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T, float eps_split,
+                           float step_scale, const float* grad_norm, float eps_grad,
+                           const sgs_gaussians_mut& out, int64_t capacity, int32_t* d_n_out,
+                           int32_t* parent, float* lam_out, float* v_out, void* ws,
+                           cudaStream_t stream);
+
+// Generic device-side primitives (sort.cu)
+// Exclusive scan of n uint32 values (n read from *d_n when d_n != nullptr,
+// else n_host), writing out[i] and *d_total.  `tmp` needs scan_tmp_bytes(n_max).
+size_t scan_tmp_bytes(int64_t n_max);
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* d_total,
+                                  int64_t n_max, const int32_t* d_n, void* tmp, cudaStream_t stream);
+
+constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves aligned sub-buffers out of one workspace.
+struct Carver {
+    char* base;
+    size_t off;
+    template <class T>
+    T* take(size_t count) {
+        off = align_up(off, 256);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += sizeof(T) * count;
+        return p;
+    }
+};
+
+}  // namespace sgs

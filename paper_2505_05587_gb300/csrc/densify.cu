@@ -1,0 +1,243 @@
+// Steepest density control: minimum eigenpair of the averaged splitting
+// matrices, split decision, offspring generation and prefix-sum compaction;
+// plus the L1 photometric loss and its gradient.
+//
+// Paper: Theorem 2 (m = 2, w = 1/2, delta = +-v_min when lambda_min < 0),
+// Algorithm 1 (S /= T_split; replace theta by (theta +- eps delta, o/2)),
+// Appendix "Eigendecomposition" (A = p B + q I, beta = 2 cos(arccos(det B / 2)
+// / 3 + 2 k pi / 3)), the "Compactest Splitting Strategy" variant (gradient
+// gate), Section 3 Eq. loss (L1).
+#include "common.cuh"
+
+namespace sgs {
+
+struct Eig {
+    float lam;
+    float v[3];
+};
+
+__device__ __forceinline__ void cross3(const float* a, const float* b, float* c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Minimum eigenpair of the symmetric matrix (xx, xy, xz, yy, yz, zz).
+// Trigonometric root formula for lambda; eigenvector from the largest cross
+// product of two rows of A - lambda I (with a repeated-root fallback); then one
+// Rayleigh quotient v^T A v, which restores full float32 accuracy of lambda
+// where the arccos loses digits (a near-repeated minimum root).
+__device__ Eig eig3_min(const float* s6, float scale) {
+    const float a00 = s6[0] * scale, a01 = s6[1] * scale, a02 = s6[2] * scale;
+    const float a11 = s6[3] * scale, a12 = s6[4] * scale, a22 = s6[5] * scale;
+    Eig e;
+    const float q = (a00 + a11 + a22) * (1.0f / 3.0f);
+    const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    const float p2 = (b00 * b00 + b11 * b11 + b22 * b22 + 2.0f * (a01 * a01 + a02 * a02 + a12 * a12)) *
+                     (1.0f / 6.0f);
+    if (!(p2 > 0.0f)) {
+        e.lam = q;
+        e.v[0] = 1.0f; e.v[1] = 0.0f; e.v[2] = 0.0f;
+        return e;
+    }
+    const float p = sqrtf(p2);
+    const float ip = 1.0f / p;
+    const float B00 = b00 * ip, B11 = b11 * ip, B22 = b22 * ip;
+    const float B01 = a01 * ip, B02 = a02 * ip, B12 = a12 * ip;
+    const float detB = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) +
+                       B02 * (B01 * B12 - B11 * B02);
+    const float r = fminf(fmaxf(0.5f * detB, -1.0f), 1.0f);
+    const float phi = acosf(r) * (1.0f / 3.0f);
+    const float lam0 = q + 2.0f * p * cosf(phi + 2.0943951023931953f);
+    const float r0[3] = {a00 - lam0, a01, a02};
+    const float r1[3] = {a01, a11 - lam0, a12};
+    const float r2[3] = {a02, a12, a22 - lam0};
+    float c[3][3];
+    cross3(r0, r1, c[0]);
+    cross3(r0, r2, c[1]);
+    cross3(r1, r2, c[2]);
+    float n2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n2[k] = c[k][0] * c[k][0] + c[k][1] * c[k][1] + c[k][2] * c[k][2];
+    int best = 0;
+    if (n2[1] > n2[best]) best = 1;
+    if (n2[2] > n2[best]) best = 2;
+    float v[3];
+    if (n2[best] > 0.0f) {
+        const float in = rsqrtf(n2[best]);
+        v[0] = c[best][0] * in; v[1] = c[best][1] * in; v[2] = c[best][2] * in;
+    } else {
+        // repeated minimum root: any unit vector orthogonal to the largest row
+        const float rn0 = r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2];
+        const float rn1 = r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2];
+        const float rn2 = r2[0] * r2[0] + r2[1] * r2[1] + r2[2] * r2[2];
+        const float* row = r0;
+        float rb = rn0;
+        if (rn1 > rb) { row = r1; rb = rn1; }
+        if (rn2 > rb) { row = r2; rb = rn2; }
+        int ax = 0;
+        if (fabsf(row[1]) < fabsf(row[ax])) ax = 1;
+        if (fabsf(row[2]) < fabsf(row[ax])) ax = 2;
+        float ev[3] = {0.0f, 0.0f, 0.0f};
+        ev[ax] = 1.0f;
+        cross3(row, ev, v);
+        const float in = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        v[0] *= in; v[1] *= in; v[2] *= in;
+    }
+    // canonical sign: largest-magnitude component positive (lowest index on ties)
+    int k = 0;
+    if (fabsf(v[1]) > fabsf(v[k])) k = 1;
+    if (fabsf(v[2]) > fabsf(v[k])) k = 2;
+    if (v[k] < 0.0f) { v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2]; }
+    const float Av0 = a00 * v[0] + a01 * v[1] + a02 * v[2];
+    const float Av1 = a01 * v[0] + a11 * v[1] + a12 * v[2];
+    const float Av2 = a02 * v[0] + a12 * v[1] + a22 * v[2];
+    e.lam = v[0] * Av0 + v[1] * Av1 + v[2] * Av2;
+    e.v[0] = v[0]; e.v[1] = v[1]; e.v[2] = v[2];
+    return e;
+}
+
+__global__ void __launch_bounds__(256) eig_flag_kernel(const float* __restrict__ S, int n, float inv_T,
+                                                       float eps_split, const float* __restrict__ grad_norm,
+                                                       float eps_grad, float* __restrict__ lam_out,
+                                                       float* __restrict__ v_out, uint32_t* __restrict__ flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s6[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s6[k] = S[(size_t)i * 6 + k];
+    Eig e = eig3_min(s6, inv_T);
+    lam_out[i] = e.lam;
+    v_out[3 * (size_t)i] = e.v[0];
+    v_out[3 * (size_t)i + 1] = e.v[1];
+    v_out[3 * (size_t)i + 2] = e.v[2];
+    bool f = e.lam < eps_split;
+    if (grad_norm) f = f && (grad_norm[i] <= eps_grad);
+    flags[i] = f ? 1u : 0u;
+}
+
+__global__ void n_out_kernel(const uint32_t* __restrict__ total, int n, int32_t* __restrict__ d_n_out) {
+    *d_n_out = n + (int32_t)(*total);
+}
+
+// logit(sigmoid(x) / 2) = -log(1 + 2 exp(-x)), evaluated without overflow.
+__device__ __forceinline__ float half_opacity_logit(float x) {
+    return x > 0.0f ? -log1pf(2.0f * expf(-x)) : x - logf(expf(x) + 2.0f);
+}
+
+__global__ void __launch_bounds__(256) split_kernel(
+    const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
+    const float* __restrict__ logit, const float* __restrict__ sh, int n, int K3, const float* __restrict__ v,
+    const uint32_t* __restrict__ flags, const uint32_t* __restrict__ excl, float step_scale, int64_t cap,
+    float* __restrict__ o_means, float* __restrict__ o_ls, float* __restrict__ o_quats,
+    float* __restrict__ o_logit, float* __restrict__ o_sh, int32_t* __restrict__ parent) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool f = flags[i] != 0u;
+    const float l0 = log_scales[3 * i], l1 = log_scales[3 * i + 1], l2 = log_scales[3 * i + 2];
+    const float x = logit[i];
+    const float p0 = means[3 * i], p1 = means[3 * i + 1], p2 = means[3 * i + 2];
+    int64_t rows[2] = {i, f ? (int64_t)n + (int64_t)excl[i] : -1};
+    float eps = 0.0f, lg = x;
+    if (f) {
+        eps = step_scale * expf(fmaxf(l0, fmaxf(l1, l2)));
+        lg = half_opacity_logit(x);
+    }
+    const float v0 = f ? v[3 * i] : 0.0f, v1 = f ? v[3 * i + 1] : 0.0f, v2 = f ? v[3 * i + 2] : 0.0f;
+    for (int r = 0; r < 2; ++r) {
+        const int64_t row = rows[r];
+        if (row < 0 || row >= cap) continue;
+        const float sg = r == 0 ? eps : -eps;
+        o_means[3 * row] = p0 + sg * v0;
+        o_means[3 * row + 1] = p1 + sg * v1;
+        o_means[3 * row + 2] = p2 + sg * v2;
+        o_ls[3 * row] = l0;
+        o_ls[3 * row + 1] = l1;
+        o_ls[3 * row + 2] = l2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o_quats[4 * row + k] = quats[4 * i + k];
+        o_logit[row] = lg;
+        const float* src = sh + (size_t)i * K3;
+        float* dst = o_sh + (size_t)row * K3;
+        for (int k = 0; k < K3; ++k) dst[k] = src[k];
+        if (parent) parent[row] = i;
+    }
+}
+
+size_t densify_ws_bytes(int n) {
+    Carver c{nullptr, 0};
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    c.take<uint32_t>(nn);       // flags
+    c.take<uint32_t>(nn);       // excl
+    c.take<uint32_t>(1);        // total
+    c.take<float>(nn);          // lam (when the caller passes none)
+    c.take<float>(3 * nn);      // v
+    c.take<char>(scan_tmp_bytes(n));
+    return c.off + 256;
+}
+
+cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T, float eps_split,
+                           float step_scale, const float* grad_norm, float eps_grad,
+                           const sgs_gaussians_mut& out, int64_t capacity, int32_t* d_n_out, int32_t* parent,
+                           float* lam_out, float* v_out, void* ws, cudaStream_t stream) {
+    const int n = in.n;
+    Carver c{reinterpret_cast<char*>(ws), 0};
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    uint32_t* flags = c.take<uint32_t>(nn);
+    uint32_t* excl = c.take<uint32_t>(nn);
+    uint32_t* total = c.take<uint32_t>(1);
+    float* lam_ws = c.take<float>(nn);
+    float* v_ws = c.take<float>(3 * nn);
+    void* scan_tmp = c.take<char>(scan_tmp_bytes(n));
+    float* lam = lam_out ? lam_out : lam_ws;
+    float* v = v_out ? v_out : v_ws;
+    if (n == 0) return cudaMemsetAsync(d_n_out, 0, sizeof(int32_t), stream);
+    const int nb = (n + 255) / 256;
+    eig_flag_kernel<<<nb, 256, 0, stream>>>(S, n, inv_T, eps_split, grad_norm, eps_grad, lam, v, flags);
+    cudaError_t e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
+    if (e != cudaSuccess) return e;
+    n_out_kernel<<<1, 1, 0, stream>>>(total, n, d_n_out);
+    const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;
+    split_kernel<<<nb, 256, 0, stream>>>(in.means, in.log_scales, in.quats, in.opacity_logit, in.sh, n, K3, v,
+                                         flags, excl, step_scale, capacity, out.means, out.log_scales,
+                                         out.quats, out.opacity_logit, out.sh, parent);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// L1 loss: loss += sum |C - Chat| / (3 H W V); dL/dC = sign(C - Chat) / (3 H W V)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ image, const float* __restrict__ target,
+                                                 int64_t count, float norm, float* __restrict__ dL,
+                                                 float* __restrict__ loss) {
+    __shared__ float s_part[8];
+    float acc = 0.0f;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float r = image[k] - target[k];
+        acc += fabsf(r);
+        dL[k] = r > 0.0f ? norm : (r < 0.0f ? -norm : 0.0f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_part[w];
+        atomicAdd(loss, s * norm);
+    }
+}
+
+cudaError_t launch_l1(const float* image, const float* target, int H, int W, int n_views, float* dL, float* loss,
+                      cudaStream_t stream) {
+    const int64_t count = (int64_t)H * W * 3;
+    if (count == 0) return cudaSuccess;
+    const float norm = (float)(1.0 / (3.0 * (double)H * (double)W * (double)n_views));
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    l1_kernel<<<(int)blocks, 256, 0, stream>>>(image, target, count, norm, dL, loss);
+    return cudaGetLastError();
+}
+
+}  // namespace sgs

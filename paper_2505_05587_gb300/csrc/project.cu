@@ -1,0 +1,486 @@
+// Projection of the Gaussians into one view and its adjoint with the lift of
+// the 2-D splitting accumulators to the 3x3 splitting matrix.
+//
+// Paper: Section 3, Eq. sigma_3D (sigma = o N(xi; p, Sigma)), Eq. sigma_2D and
+// the affine-Pi footnote (Sigma2D = P Sigma P^T); Appendix "Deriving Hessian of
+// Gaussian" (Hess_p sigma = sigma (Y Y^T - P^T Sigma2D^-1 P), Y = P^T
+// Sigma2D^-1 (x - Pi(p)), with P, Sigma2D and colour frozen).
+#include "common.cuh"
+
+namespace sgs {
+
+// ---------------------------------------------------------------------------
+// float32 exponential used by the integer stage: Cody-Waite range reduction
+// (x = k ln2 + r, ln2 split so that k*ln2_hi is exact) and the degree-7 Taylor
+// polynomial of e^r in Horner form, each step rounded separately, then the
+// exact scaling by 2^k.  Within 2 ulp of exp for |x| <= 87.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float exp_stage(float x) {
+    x = fminf(fmaxf(x, -87.0f), 88.0f);
+    float k = rintf(mul_rn(x, 0x1.715476p+0f));
+    float r = sub_rn(sub_rn(x, mul_rn(k, 0x1.62e4p-1f)), mul_rn(k, 0x1.7f7d1cp-20f));
+    float p = 0x1.a01a02p-13f;
+    p = mad_rn(p, r, 0x1.6c16c2p-10f);
+    p = mad_rn(p, r, 0x1.111112p-7f);
+    p = mad_rn(p, r, 0x1.555556p-5f);
+    p = mad_rn(p, r, 0x1.555556p-3f);
+    p = mad_rn(p, r, 0.5f);
+    p = mad_rn(p, r, 1.0f);
+    p = mad_rn(p, r, 1.0f);
+    int ki = (int)k;
+    return mul_rn(p, __int_as_float((ki + 127) << 23));
+}
+
+// Integer stage: camera-space mean, clamped Jacobian, rotation, scales and the
+// dilated 2-D covariance in float32 with a fixed operation order; radius
+// ceil(radius_sigma sqrt(lambda_max)); inclusive tile rect of the bounding
+// square.  Sums are left to right.
+__device__ Stage integer_stage(const float* __restrict__ means, const float* __restrict__ log_scales,
+                               const float* __restrict__ quats, int i, const CamDev& cam,
+                               const SetDev& st) {
+    Stage o;
+    o.culled = true;
+    o.x_lo = 0; o.x_hi = -1; o.y_lo = 0; o.y_hi = -1;
+    const float p0 = means[3 * i], p1 = means[3 * i + 1], p2 = means[3 * i + 2];
+    const float* R = cam.R;
+    o.tx = add_rn(add_rn(add_rn(mul_rn(R[0], p0), mul_rn(R[1], p1)), mul_rn(R[2], p2)), cam.t[0]);
+    o.ty = add_rn(add_rn(add_rn(mul_rn(R[3], p0), mul_rn(R[4], p1)), mul_rn(R[5], p2)), cam.t[1]);
+    o.tz = add_rn(add_rn(add_rn(mul_rn(R[6], p0), mul_rn(R[7], p1)), mul_rn(R[8], p2)), cam.t[2]);
+    if (!(o.tz > cam.near_z)) return o;
+    const float tz = o.tz;
+    float mx = add_rn(div_rn(mul_rn(cam.fx, o.tx), tz), cam.cx);
+    float my = add_rn(div_rn(mul_rn(cam.fy, o.ty), tz), cam.cy);
+    float limx = div_rn(mul_rn(st.fov_clamp, mul_rn(0.5f, (float)cam.width)), cam.fx);
+    float limy = div_rn(mul_rn(st.fov_clamp, mul_rn(0.5f, (float)cam.height)), cam.fy);
+    float rx = div_rn(o.tx, tz), ry = div_rn(o.ty, tz);
+    o.clx = (rx < -limx) || (rx > limx);
+    o.cly = (ry < -limy) || (ry > limy);
+    o.ux = fminf(fmaxf(rx, -limx), limx);
+    o.uy = fminf(fmaxf(ry, -limy), limy);
+    float J00 = div_rn(cam.fx, tz), J02 = div_rn(-mul_rn(cam.fx, o.ux), tz);
+    float J11 = div_rn(cam.fy, tz), J12 = div_rn(-mul_rn(cam.fy, o.uy), tz);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        o.T[j] = add_rn(mul_rn(J00, R[j]), mul_rn(J02, R[6 + j]));
+        o.T[3 + j] = add_rn(mul_rn(J11, R[3 + j]), mul_rn(J12, R[6 + j]));
+    }
+    const float q0 = quats[4 * i], q1 = quats[4 * i + 1], q2 = quats[4 * i + 2], q3 = quats[4 * i + 3];
+    float qn = sqrt_rn(add_rn(add_rn(add_rn(mul_rn(q0, q0), mul_rn(q1, q1)), mul_rn(q2, q2)), mul_rn(q3, q3)));
+    o.qn = qn;
+    if (!(qn > 0.0f)) return o;
+    float w = div_rn(q0, qn), x = div_rn(q1, qn), y = div_rn(q2, qn), z = div_rn(q3, qn);
+    float* Rq = o.Rq;
+    Rq[0] = sub_rn(1.0f, mul_rn(2.0f, add_rn(mul_rn(y, y), mul_rn(z, z))));
+    Rq[1] = mul_rn(2.0f, sub_rn(mul_rn(x, y), mul_rn(w, z)));
+    Rq[2] = mul_rn(2.0f, add_rn(mul_rn(x, z), mul_rn(w, y)));
+    Rq[3] = mul_rn(2.0f, add_rn(mul_rn(x, y), mul_rn(w, z)));
+    Rq[4] = sub_rn(1.0f, mul_rn(2.0f, add_rn(mul_rn(x, x), mul_rn(z, z))));
+    Rq[5] = mul_rn(2.0f, sub_rn(mul_rn(y, z), mul_rn(w, x)));
+    Rq[6] = mul_rn(2.0f, sub_rn(mul_rn(x, z), mul_rn(w, y)));
+    Rq[7] = mul_rn(2.0f, add_rn(mul_rn(y, z), mul_rn(w, x)));
+    Rq[8] = sub_rn(1.0f, mul_rn(2.0f, add_rn(mul_rn(x, x), mul_rn(y, y))));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o.s[k] = exp_stage(log_scales[3 * i + k]);
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = mul_rn(Rq[3 * r + c], o.s[c]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            o.V[3 * a + j] = add_rn(add_rn(mul_rn(o.T[3 * a], M[j]), mul_rn(o.T[3 * a + 1], M[3 + j])),
+                                    mul_rn(o.T[3 * a + 2], M[6 + j]));
+    const float* V = o.V;
+    o.a = add_rn(add_rn(add_rn(mul_rn(V[0], V[0]), mul_rn(V[1], V[1])), mul_rn(V[2], V[2])), st.dilation);
+    o.b = add_rn(add_rn(mul_rn(V[0], V[3]), mul_rn(V[1], V[4])), mul_rn(V[2], V[5]));
+    o.c = add_rn(add_rn(add_rn(mul_rn(V[3], V[3]), mul_rn(V[4], V[4])), mul_rn(V[5], V[5])), st.dilation);
+    float det = sub_rn(mul_rn(o.a, o.c), mul_rn(o.b, o.b));
+    if (!(det > 0.0f)) return o;
+    float mid = mul_rn(0.5f, add_rn(o.a, o.c));
+    float lam = add_rn(mid, sqrt_rn(fmaxf(0.1f, sub_rn(mul_rn(mid, mid), det))));
+    float rad = ceilf(mul_rn(st.radius_sigma, sqrt_rn(lam)));
+    float fxlo = floorf(div_rn(sub_rn(mx, rad), (float)st.tile_w));
+    float fxhi = floorf(div_rn(add_rn(mx, rad), (float)st.tile_w));
+    float fylo = floorf(div_rn(sub_rn(my, rad), (float)st.tile_h));
+    float fyhi = floorf(div_rn(add_rn(my, rad), (float)st.tile_h));
+    if (!(fxhi >= 0.0f && fxlo <= (float)(cam.gx - 1) && fyhi >= 0.0f && fylo <= (float)(cam.gy - 1)))
+        return o;
+    o.x_lo = (int)fmaxf(fxlo, 0.0f);
+    o.x_hi = (int)fminf(fxhi, (float)(cam.gx - 1));
+    o.y_lo = (int)fmaxf(fylo, 0.0f);
+    o.y_hi = (int)fminf(fyhi, (float)(cam.gy - 1));
+    o.culled = false;
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// Unevaluated float pairs (hi + lo) for the 2-D mean: error-free transforms
+// (Knuth two-sum, FMA two-product).
+// ---------------------------------------------------------------------------
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+    F2 s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ F2 f2_mul(F2 x, float b) {
+    F2 p = two_prod(x.hi, b);
+    return fast_two_sum(p.hi, __fmaf_rn(x.lo, b, p.lo));
+}
+__device__ __forceinline__ F2 f2_div(F2 x, F2 y) {
+    float q1 = __fdiv_rn(x.hi, y.hi);
+    F2 p = f2_mul(y, q1);
+    F2 r = f2_add(x, F2{-p.hi, -p.lo});
+    float q2 = __fdiv_rn(r.hi, y.hi);
+    return fast_two_sum(q1, q2);
+}
+__device__ __forceinline__ F2 dot3_plus(const float* R, float p0, float p1, float p2, float t) {
+    F2 acc = two_prod(R[0], p0);
+    acc = f2_add(acc, two_prod(R[1], p1));
+    acc = f2_add(acc, two_prod(R[2], p2));
+    return f2_add(acc, F2{t, 0.0f});
+}
+
+// ---------------------------------------------------------------------------
+// Real spherical harmonics, degree <= 3, orthonormal on the sphere, with the
+// sign pattern of the common graphics convention.  Coefficients are
+// 1/(2 sqrt(pi)), sqrt(3/(4 pi)), (1/2) sqrt(15/pi), (1/4) sqrt(5/pi),
+// (1/4) sqrt(15/pi), (1/4) sqrt(35/(2 pi)), (1/2) sqrt(105/pi),
+// (1/4) sqrt(21/(2 pi)), (1/4) sqrt(7/pi), (1/4) sqrt(105/pi).
+// ---------------------------------------------------------------------------
+constexpr float kC0 = 2.8209479177e-01f;
+constexpr float kC1 = 4.8860251190e-01f;
+constexpr float kC2a = 1.0925484306e+00f;
+constexpr float kC2b = 3.1539156525e-01f;
+constexpr float kC2c = 5.4627421530e-01f;
+constexpr float kC3a = 5.9004358993e-01f;
+constexpr float kC3b = 2.8906114426e+00f;
+constexpr float kC3c = 4.5704579946e-01f;
+constexpr float kC3d = 3.7317633259e-01f;
+constexpr float kC3e = 1.4453057213e+00f;
+
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float* Y) {
+    Y[0] = kC0;
+    if (deg < 1) return;
+    Y[1] = -kC1 * y; Y[2] = kC1 * z; Y[3] = -kC1 * x;
+    if (deg < 2) return;
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kC2a * x * y;
+    Y[5] = -kC2a * y * z;
+    Y[6] = kC2b * (2.0f * zz - xx - yy);
+    Y[7] = -kC2a * x * z;
+    Y[8] = kC2c * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -kC3a * y * (3.0f * xx - yy);
+    Y[10] = kC3b * x * y * z;
+    Y[11] = -kC3c * y * (4.0f * zz - xx - yy);
+    Y[12] = kC3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -kC3c * x * (4.0f * zz - xx - yy);
+    Y[14] = kC3e * z * (xx - yy);
+    Y[15] = -kC3a * x * (xx - 3.0f * yy);
+}
+
+// Gradient of the basis polynomials, dY[k][axis].
+__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float (*dY)[3]) {
+    dY[0][0] = dY[0][1] = dY[0][2] = 0.0f;
+    if (deg < 1) return;
+    dY[1][0] = 0.0f; dY[1][1] = -kC1; dY[1][2] = 0.0f;
+    dY[2][0] = 0.0f; dY[2][1] = 0.0f; dY[2][2] = kC1;
+    dY[3][0] = -kC1; dY[3][1] = 0.0f; dY[3][2] = 0.0f;
+    if (deg < 2) return;
+    float xx = x * x, yy = y * y, zz = z * z;
+    dY[4][0] = kC2a * y; dY[4][1] = kC2a * x; dY[4][2] = 0.0f;
+    dY[5][0] = 0.0f; dY[5][1] = -kC2a * z; dY[5][2] = -kC2a * y;
+    dY[6][0] = -2.0f * kC2b * x; dY[6][1] = -2.0f * kC2b * y; dY[6][2] = 4.0f * kC2b * z;
+    dY[7][0] = -kC2a * z; dY[7][1] = 0.0f; dY[7][2] = -kC2a * x;
+    dY[8][0] = 2.0f * kC2c * x; dY[8][1] = -2.0f * kC2c * y; dY[8][2] = 0.0f;
+    if (deg < 3) return;
+    dY[9][0] = -6.0f * kC3a * x * y; dY[9][1] = -kC3a * (3.0f * xx - 3.0f * yy); dY[9][2] = 0.0f;
+    dY[10][0] = kC3b * y * z; dY[10][1] = kC3b * x * z; dY[10][2] = kC3b * x * y;
+    dY[11][0] = 2.0f * kC3c * x * y; dY[11][1] = -kC3c * (4.0f * zz - xx - 3.0f * yy); dY[11][2] = -8.0f * kC3c * y * z;
+    dY[12][0] = -6.0f * kC3d * x * z; dY[12][1] = -6.0f * kC3d * y * z; dY[12][2] = kC3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+    dY[13][0] = -kC3c * (4.0f * zz - 3.0f * xx - yy); dY[13][1] = 2.0f * kC3c * x * y; dY[13][2] = -8.0f * kC3c * x * z;
+    dY[14][0] = 2.0f * kC3e * x * z; dY[14][1] = -2.0f * kC3e * y * z; dY[14][2] = kC3e * (xx - yy);
+    dY[15][0] = -kC3a * (3.0f * xx - 3.0f * yy); dY[15][1] = 6.0f * kC3a * x * y; dY[15][2] = 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Forward projection: one thread per Gaussian.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) project_kernel(
+    const float* __restrict__ means, const float* __restrict__ log_scales,
+    const float* __restrict__ quats, const float* __restrict__ opacity_logit,
+    const float* __restrict__ sh, int n, int sh_degree, CamDev cam, SetDev st,
+    float4* __restrict__ xy, float4* __restrict__ conic_opac, float4* __restrict__ rgb_out,
+    float* __restrict__ depth, short4* __restrict__ rect, uint32_t* __restrict__ tiles) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Stage s = integer_stage(means, log_scales, quats, i, cam, st);
+    depth[i] = s.tz;
+    if (s.culled) {
+        tiles[i] = 0;
+        rect[i] = make_short4(0, 0, -1, -1);
+        xy[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        conic_opac[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rgb_out[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    tiles[i] = (uint32_t)((s.x_hi - s.x_lo + 1) * (s.y_hi - s.y_lo + 1));
+    rect[i] = make_short4((short)s.x_lo, (short)s.y_lo, (short)s.x_hi, (short)s.y_hi);
+    // 2-D mean as a float pair: mu = f (t_xy / t_z) + c
+    const float p0 = means[3 * i], p1 = means[3 * i + 1], p2 = means[3 * i + 2];
+    F2 tx = dot3_plus(cam.R, p0, p1, p2, cam.t[0]);
+    F2 ty = dot3_plus(cam.R + 3, p0, p1, p2, cam.t[1]);
+    F2 tz = dot3_plus(cam.R + 6, p0, p1, p2, cam.t[2]);
+    F2 mx = f2_add(f2_mul(f2_div(tx, tz), cam.fx), F2{cam.cx, 0.0f});
+    F2 my = f2_add(f2_mul(f2_div(ty, tz), cam.fy), F2{cam.cy, 0.0f});
+    xy[i] = make_float4(mx.hi, my.hi, mx.lo, my.lo);
+    float det = s.a * s.c - s.b * s.b;
+    float inv = 1.0f / det;
+    float o = 1.0f / (1.0f + expf(-opacity_logit[i]));
+    conic_opac[i] = make_float4(s.c * inv, -s.b * inv, s.a * inv, o);
+    // view-dependent colour
+    float d0 = p0 - cam.cc[0], d1 = p1 - cam.cc[1], d2 = p2 - cam.cc[2];
+    float dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    float inv_dn = 1.0f / dn;
+    float Y[16];
+    sh_basis(sh_degree, d0 * inv_dn, d1 * inv_dn, d2 * inv_dn, Y);
+    const int K = (sh_degree + 1) * (sh_degree + 1);
+    const float* c = sh + (size_t)i * K * 3;
+    float r = 0.5f, g = 0.5f, b = 0.5f;
+    for (int k = 0; k < K; ++k) {
+        r += Y[k] * c[3 * k];
+        g += Y[k] * c[3 * k + 1];
+        b += Y[k] * c[3 * k + 2];
+    }
+    rgb_out[i] = make_float4(fmaxf(r, 0.0f), fmaxf(g, 0.0f), fmaxf(b, 0.0f), 0.0f);
+}
+
+cudaError_t launch_project(const sgs_gaussians& g, const CamDev& cam, const SetDev& st,
+                           const sgs_proj& out, cudaStream_t stream) {
+    if (g.n == 0) return cudaSuccess;
+    int blocks = (g.n + 255) / 256;
+    project_kernel<<<blocks, 256, 0, stream>>>(
+        g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, g.sh_degree, cam, st,
+        reinterpret_cast<float4*>(out.xy), reinterpret_cast<float4*>(out.conic_opac),
+        reinterpret_cast<float4*>(out.rgb), out.depth, reinterpret_cast<short4*>(out.rect),
+        out.tiles_touched);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the projection plus the lift of the splitting accumulators.
+// g2d row (16 floats, the last 3 unused): dL/dmu (2), dL/dQ (Q00, Q01 as the shared off-diagonal
+// value, Q11), dL/dopacity, dL/drgb (3), a0 = sum w, A2 = sum w u u^T (xx, xy,
+// yy) with w = dL/dalpha alpha and u = Q (x - mu).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) project_bwd_kernel(
+    const float* __restrict__ means, const float* __restrict__ log_scales,
+    const float* __restrict__ quats, const float* __restrict__ opacity_logit,
+    const float* __restrict__ sh, int n, int sh_degree, CamDev cam, SetDev st,
+    const float* __restrict__ g2d, float* __restrict__ g_means, float* __restrict__ g_ls,
+    float* __restrict__ g_quats, float* __restrict__ g_logit, float* __restrict__ g_sh,
+    float* __restrict__ S_accum) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Stage s = integer_stage(means, log_scales, quats, i, cam, st);
+    if (s.culled) return;
+    const float* gg = g2d + (size_t)i * 16;
+    const float dmx = gg[0], dmy = gg[1], dQa = gg[2], dQb = gg[3], dQc = gg[4];
+    const float dop = gg[5], dr = gg[6], dgc = gg[7], db = gg[8];
+    const float a0 = gg[9], A2xx = gg[10], A2xy = gg[11], A2yy = gg[12];
+    const float fx = cam.fx, fy = cam.fy, tx = s.tx, ty = s.ty, tz = s.tz;
+    const float* R = cam.R;
+
+    // conic Q = Sigma2D^-1 (float32 from the integer-stage covariance)
+    float det = s.a * s.c - s.b * s.b;
+    float inv = 1.0f / det;
+    float Qa = s.c * inv, Qb = -s.b * inv, Qc = s.a * inv;
+
+    // --- splitting matrix of this view: S += P^T (A2 - a0 Q) P ---------------
+    {
+        float K00 = A2xx - a0 * Qa, K01 = A2xy - a0 * Qb, K11 = A2yy - a0 * Qc;
+        const float* P = s.T;
+        float Sv[6];
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b) {
+                Sv[k++] = K00 * P[a] * P[b] + K01 * (P[a] * P[3 + b] + P[3 + a] * P[b]) +
+                          K11 * P[3 + a] * P[3 + b];
+            }
+        float* So = S_accum + (size_t)i * 6;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) So[j] += Sv[j];
+    }
+
+    // --- opacity -----------------------------------------------------------
+    float o = 1.0f / (1.0f + expf(-opacity_logit[i]));
+    g_logit[i] += dop * o * (1.0f - o);
+
+    // --- colour (SH) -------------------------------------------------------
+    float dp0 = 0.0f, dp1 = 0.0f, dp2 = 0.0f;
+    {
+        const float p0 = means[3 * i], p1 = means[3 * i + 1], p2 = means[3 * i + 2];
+        float d0 = p0 - cam.cc[0], d1 = p1 - cam.cc[1], d2 = p2 - cam.cc[2];
+        float dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+        float inv_dn = 1.0f / dn;
+        float h0 = d0 * inv_dn, h1 = d1 * inv_dn, h2 = d2 * inv_dn;
+        float Y[16];
+        sh_basis(sh_degree, h0, h1, h2, Y);
+        const int K = (sh_degree + 1) * (sh_degree + 1);
+        const float* c = sh + (size_t)i * K * 3;
+        float raw[3] = {0.5f, 0.5f, 0.5f};
+        for (int k = 0; k < K; ++k) {
+            raw[0] += Y[k] * c[3 * k];
+            raw[1] += Y[k] * c[3 * k + 1];
+            raw[2] += Y[k] * c[3 * k + 2];
+        }
+        float gc[3] = {raw[0] > 0.0f ? dr : 0.0f, raw[1] > 0.0f ? dgc : 0.0f, raw[2] > 0.0f ? db : 0.0f};
+        float* gs = g_sh + (size_t)i * K * 3;
+        for (int k = 0; k < K; ++k) {
+            gs[3 * k] += Y[k] * gc[0];
+            gs[3 * k + 1] += Y[k] * gc[1];
+            gs[3 * k + 2] += Y[k] * gc[2];
+        }
+        if (sh_degree > 0) {
+            float dY[16][3];
+            sh_basis_grad(sh_degree, h0, h1, h2, dY);
+            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
+            for (int k = 1; k < K; ++k) {
+                float w = gc[0] * c[3 * k] + gc[1] * c[3 * k + 1] + gc[2] * c[3 * k + 2];
+                e0 += w * dY[k][0];
+                e1 += w * dY[k][1];
+                e2 += w * dY[k][2];
+            }
+            float pr = e0 * h0 + e1 * h1 + e2 * h2;
+            dp0 += (e0 - pr * h0) * inv_dn;
+            dp1 += (e1 - pr * h1) * inv_dn;
+            dp2 += (e2 - pr * h2) * inv_dn;
+        }
+    }
+
+    // --- 2-D mean ------------------------------------------------------------
+    float itz = 1.0f / tz, itz2 = itz * itz;
+    float dt0 = dmx * fx * itz;
+    float dt1 = dmy * fy * itz;
+    float dt2 = -(dmx * fx * tx + dmy * fy * ty) * itz2;
+
+    // --- conic -> Sigma2D: G2 = -Q GQ Q, GQ = [[dQa, dQb/2], [dQb/2, dQc]] ---
+    float h = 0.5f * dQb;
+    float t00 = Qa * dQa + Qb * h, t01 = Qa * h + Qb * dQc;
+    float t10 = Qb * dQa + Qc * h, t11 = Qb * h + Qc * dQc;
+    float G00 = -(t00 * Qa + t01 * Qb);
+    float G01 = -(t00 * Qb + t01 * Qc);
+    float G10 = -(t10 * Qa + t11 * Qb);
+    float G11 = -(t10 * Qb + t11 * Qc);
+    float Gs01 = 0.5f * (G01 + G10);
+
+    // --- Sigma2D = V V^T, V = P M (M = Rq diag(s)): dV = 2 G2 V ----------------
+    const float* V = s.V;
+    float dV[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        dV[j] = 2.0f * (G00 * V[j] + Gs01 * V[3 + j]);
+        dV[3 + j] = 2.0f * (Gs01 * V[j] + G11 * V[3 + j]);
+    }
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = s.Rq[3 * r + c] * s.s[c];
+    // dP = dV M^T ; dM = P^T dV
+    float dP[6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            dP[3 * a + j] = dV[3 * a] * M[3 * j] + dV[3 * a + 1] * M[3 * j + 1] + dV[3 * a + 2] * M[3 * j + 2];
+    float dM[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dM[3 * r + c] = s.T[r] * dV[c] + s.T[3 + r] * dV[3 + c];
+
+    // --- P = J W: dJ = dP W^T --------------------------------------------------
+    float dJ[6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            dJ[3 * a + k] = dP[3 * a] * R[3 * k] + dP[3 * a + 1] * R[3 * k + 1] + dP[3 * a + 2] * R[3 * k + 2];
+    // J = [[fx/tz, 0, -fx ux/tz], [0, fy/tz, -fy uy/tz]], ux = clamp(tx/tz)
+    dt2 += dJ[0] * (-fx * itz2) + dJ[4] * (-fy * itz2);
+    {
+        float dux_dtx = s.clx ? 0.0f : itz;
+        float dux_dtz = s.clx ? 0.0f : -tx * itz2;
+        dt0 += dJ[2] * (-fx * itz) * dux_dtx;
+        dt2 += dJ[2] * ((-fx * itz) * dux_dtz + fx * s.ux * itz2);
+        float duy_dty = s.cly ? 0.0f : itz;
+        float duy_dtz = s.cly ? 0.0f : -ty * itz2;
+        dt1 += dJ[5] * (-fy * itz) * duy_dty;
+        dt2 += dJ[5] * ((-fy * itz) * duy_dtz + fy * s.uy * itz2);
+    }
+    // t = W p + t_w
+    dp0 += R[0] * dt0 + R[3] * dt1 + R[6] * dt2;
+    dp1 += R[1] * dt0 + R[4] * dt1 + R[7] * dt2;
+    dp2 += R[2] * dt0 + R[5] * dt1 + R[8] * dt2;
+    g_means[3 * i] += dp0;
+    g_means[3 * i + 1] += dp1;
+    g_means[3 * i + 2] += dp2;
+
+    // --- scales and rotation ---------------------------------------------------
+    float dRq[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        float ds = dM[b] * s.Rq[b] + dM[3 + b] * s.Rq[3 + b] + dM[6 + b] * s.Rq[6 + b];
+        g_ls[3 * i + b] += ds * s.s[b];
+        dRq[b] = dM[b] * s.s[b];
+        dRq[3 + b] = dM[3 + b] * s.s[b];
+        dRq[6 + b] = dM[6 + b] * s.s[b];
+    }
+    float inv_qn = 1.0f / s.qn;
+    float w = quats[4 * i] * inv_qn, x = quats[4 * i + 1] * inv_qn;
+    float y = quats[4 * i + 2] * inv_qn, z = quats[4 * i + 3] * inv_qn;
+    const float* d = dRq;
+    float dw = 2.0f * (-z * d[1] + y * d[2] + z * d[3] - x * d[5] - y * d[6] + x * d[7]);
+    float dx = 2.0f * (y * d[1] + z * d[2] + y * d[3] - 2.0f * x * d[4] - w * d[5] + z * d[6] + w * d[7] - 2.0f * x * d[8]);
+    float dy = 2.0f * (-2.0f * y * d[0] + x * d[1] + w * d[2] + x * d[3] + z * d[5] - w * d[6] + z * d[7] - 2.0f * y * d[8]);
+    float dz = 2.0f * (-2.0f * z * d[0] - w * d[1] + x * d[2] + w * d[3] - 2.0f * z * d[4] + y * d[5] + x * d[6] + y * d[7]);
+    float dot = dw * w + dx * x + dy * y + dz * z;
+    g_quats[4 * i] += (dw - dot * w) * inv_qn;
+    g_quats[4 * i + 1] += (dx - dot * x) * inv_qn;
+    g_quats[4 * i + 2] += (dy - dot * y) * inv_qn;
+    g_quats[4 * i + 3] += (dz - dot * z) * inv_qn;
+}
+
+cudaError_t launch_project_bwd(const sgs_gaussians& g, const CamDev& cam, const SetDev& st,
+                               const float* g2d, const sgs_grads& grads, float* S_accum,
+                               cudaStream_t stream) {
+    if (g.n == 0) return cudaSuccess;
+    int blocks = (g.n + 127) / 128;
+    project_bwd_kernel<<<blocks, 128, 0, stream>>>(
+        g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, g.sh_degree, cam, st, g2d,
+        grads.means, grads.log_scales, grads.quats, grads.opacity_logit, grads.sh, S_accum);
+    return cudaGetLastError();
+}
+
+}  // namespace sgs

@@ -1,0 +1,125 @@
+"""Buffers and the fused densification iteration on one GPU.
+
+Every step runs in libsteepgs through the binding; this module only owns the
+device buffers (allocated once, reused across iterations) and orders the
+calls on one stream:
+
+    project -> bin_sort -> render_fwd -> l1_loss_grad
+            -> render_bwd_with_splitting (S += P^T(...)P per view)
+            -> densify_split (lambda_min, v_min, split, compaction)
+
+The instance count M is data dependent.  Buffers are sized with headroom; when
+a view needs more, the pipeline reads M back once, grows the buffers and
+re-runs the sort (never silently truncates).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import binding as B
+
+
+@dataclass
+class ViewBuffers:
+    """Per-view buffers: projection, bins, image maps and the L1 gradient."""
+    cam: object
+    st: object
+    n: int
+    proj: B.ProjBuffers
+    bins: B.BinBuffers
+    image: torch.Tensor
+    final_T: torch.Tensor
+    n_contrib: torch.Tensor
+    dL: torch.Tensor
+    sort_ws: torch.Tensor
+    with_keys: bool = False
+
+    @staticmethod
+    def alloc(n: int, cam, st, capacity: int | None = None, with_keys=False, device="cuda") -> "ViewBuffers":
+        T = B.num_tiles(cam, st)
+        cap = capacity if capacity is not None else max(4 * n, 1024)
+        H, W = cam.height, cam.width
+        f = dict(device=device, dtype=torch.float32)
+        return ViewBuffers(cam, st, n, B.ProjBuffers.alloc(n, device), B.BinBuffers.alloc(cap, T, with_keys, device),
+                           torch.empty(H, W, 3, **f), torch.empty(H, W, **f),
+                           torch.empty(H, W, device=device, dtype=torch.int32), torch.empty(H, W, 3, **f),
+                           B.workspace(B.bin_sort_workspace_size(n, cap, T), device), with_keys)
+
+    def grow(self, capacity: int):
+        T = B.num_tiles(self.cam, self.st)
+        dev = self.image.device
+        self.bins = B.BinBuffers.alloc(capacity, T, self.with_keys, dev)
+        self.sort_ws = B.workspace(B.bin_sort_workspace_size(self.n, capacity, T), dev)
+
+
+def project_and_sort(g: B.GaussianTensors, vb: ViewBuffers, stream=None, check_capacity=True) -> int | None:
+    """Runs project + bin_sort; grows the instance buffers when M exceeds them.
+    Returns M when it was read back (check_capacity=True), else None."""
+    B.project(g, vb.cam, vb.st, vb.proj, stream)
+    B.bin_sort(vb.proj, g.n, vb.cam, vb.st, vb.bins, vb.sort_ws, stream)
+    if not check_capacity:
+        return None
+    M = int(vb.bins.count.item())
+    if M > vb.bins.capacity:
+        vb.grow(int(M * 1.25) + 1024)
+        B.bin_sort(vb.proj, g.n, vb.cam, vb.st, vb.bins, vb.sort_ws, stream)
+    return M
+
+
+def render(g: B.GaussianTensors, vb: ViewBuffers, stream=None):
+    project_and_sort(g, vb, stream)
+    B.render_fwd(vb.proj, vb.bins, vb.cam, vb.st, vb.image, vb.final_T, vb.n_contrib, stream)
+    return vb.image
+
+
+@dataclass
+class DensifyBuffers:
+    """Accumulators and outputs of the densification step."""
+    grads: B.GaussianTensors
+    S: torch.Tensor
+    bwd_ws: torch.Tensor
+    loss: torch.Tensor
+    out: B.GaussianTensors
+    parent: torch.Tensor
+    lam: torch.Tensor
+    v: torch.Tensor
+    n_out: torch.Tensor
+    split_ws: torch.Tensor
+    capacity: int
+
+    @staticmethod
+    def alloc(g: B.GaussianTensors, capacity: int | None = None) -> "DensifyBuffers":
+        n = g.n
+        dev = g.means.device
+        cap = capacity if capacity is not None else 2 * n
+        return DensifyBuffers(g.zeros_like(), torch.zeros(n, 6, device=dev),
+                              B.workspace(B.render_bwd_workspace_size(n), dev), torch.zeros(1, device=dev),
+                              B.GaussianTensors.empty(cap, g.sh_degree, dev),
+                              torch.empty(cap, device=dev, dtype=torch.int32), torch.empty(n, device=dev),
+                              torch.empty(n, 3, device=dev), torch.zeros(1, device=dev, dtype=torch.int32),
+                              B.workspace(B.densify_split_workspace_size(n), dev), cap)
+
+    def zero_(self):
+        for t in self.grads.tensors():
+            t.zero_()
+        self.S.zero_()
+        self.loss.zero_()
+
+
+def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: list[torch.Tensor],
+                    db: DensifyBuffers, T_split: float = 1.0, eps_split: float = 0.0, step_scale: float = 1.0,
+                    grad_norm=None, eps_grad: float = 0.0, stream=None, check_capacity=True):
+    """One fused fwd+bwd+splitting iteration over the views (Algorithm 1 with
+    the split step taken right after accumulation)."""
+    db.zero_()
+    V = len(views)
+    for vb, tgt in zip(views, targets):
+        project_and_sort(g, vb, stream, check_capacity)
+        B.render_fwd(vb.proj, vb.bins, vb.cam, vb.st, vb.image, vb.final_T, vb.n_contrib, stream)
+        B.l1_loss_grad(vb.image, tgt, V, vb.dL, db.loss, stream)
+        B.render_bwd_with_splitting(g, vb.proj, vb.bins, vb.cam, vb.st, vb.final_T, vb.n_contrib, vb.dL,
+                                    db.grads, db.S, db.bwd_ws, stream)
+    B.densify_split(g, db.S, 1.0 / T_split, eps_split, step_scale, grad_norm, eps_grad, db.out, db.capacity,
+                    db.n_out, db.parent, db.lam, db.v, db.split_ws, stream)

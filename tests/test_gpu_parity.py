@@ -1,0 +1,287 @@
+"""GPU path vs CPU oracle, element by element, through the C ABI.
+
+Bars: bit-exact integer work (tile rects, keys, sort order, ranges, split
+indices); colour within 1e-5 absolute; gradients and splitting matrices
+within 1e-4 relative (Frobenius); eigenvalues within 1e-4 |S_bar|_F with
+identical split decisions wherever |lambda_min| > 1e-6.  Pixels whose
+compositing decisions lie within a relative 1e-5 of a threshold (the oracle's
+band mask) are excluded from colour comparisons.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+from paper_2505_05587_gb300 import binding as B  # noqa: E402
+from paper_2505_05587_gb300 import pipeline as PL  # noqa: E402
+
+FIELDS = ("means", "log_scales", "quats", "opacity_logit", "sh")
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / den if den > 0 else np.linalg.norm(a - b)
+
+
+def _upper6(S):
+    return np.stack([S[:, 0, 0], S[:, 0, 1], S[:, 0, 2], S[:, 1, 1], S[:, 1, 2], S[:, 2, 2]], 1)
+
+
+def _gpu_view(scene, cam, st, capacity=None, with_keys=True):
+    g = B.GaussianTensors.from_scene(scene)
+    vb = PL.ViewBuffers.alloc(scene.n, cam, st, capacity=capacity, with_keys=with_keys)
+    M = PL.project_and_sort(g, vb)
+    torch.cuda.synchronize()
+    return g, vb, M
+
+
+CASES = [
+    ("tiny", lambda: synth.tiny_scene(0), lambda: synth.camera_identity(64, 64, 64.0), synth.Settings()),
+    ("tiny_seed7_ragged", lambda: synth.tiny_scene(7, 300), lambda: synth.camera_identity(70, 45, 60.0),
+     synth.Settings()),
+    ("cluster_sh3_lookat", lambda: synth.cluster_scene(3, 3000, 3),
+     lambda: synth.camera_lookat((1.0, 0.5, -6.0), (0, 0, 0), 150, 101, 150.0), synth.Settings()),
+    ("tile16x8", lambda: synth.tiny_scene(1), lambda: synth.camera_identity(64, 48, 64.0),
+     synth.Settings(tile_w=16, tile_h=8)),
+    ("tile8x8_sh1", lambda: synth.cluster_scene(5, 800, 1),
+     lambda: synth.camera_lookat((0.0, -1.0, -6.0), (0, 0, 0), 77, 59, 77.0), synth.Settings(tile_w=8, tile_h=8)),
+    ("tile32x8_sh2_bg", lambda: synth.cluster_scene(6, 1500, 2),
+     lambda: synth.camera_lookat((2.0, 0.0, -5.5), (0, 0, 0), 96, 64, 96.0),
+     synth.Settings(tile_w=32, tile_h=8, bg=(0.1, 0.2, 0.3))),
+]
+
+
+@pytest.mark.parametrize("name,mk_scene,mk_cam,st", CASES, ids=[c[0] for c in CASES])
+def test_integer_stage_and_sort_bit_exact(name, mk_scene, mk_cam, st):
+    scene, cam = mk_scene(), mk_cam()
+    g, vb, M = _gpu_view(scene, cam, st)
+    isg = oracle.integer_stage(scene, cam, st)
+    keys, gids, ranges = oracle.bin_sort(scene, cam, st)
+    assert M == len(keys)
+    tiles = vb.proj.tiles_touched.cpu().numpy()
+    assert np.array_equal(tiles, isg["tiles"])
+    rect = vb.proj.rect.cpu().numpy().astype(np.int32)
+    vis = isg["tiles"] > 0
+    assert np.array_equal(rect[vis][:, [0, 2, 1, 3]], isg["rect"][vis])
+    depth = vb.proj.depth.cpu().numpy()
+    assert np.array_equal(depth[vis].view(np.uint32), isg["depth"][vis].view(np.uint32))
+    assert np.array_equal(vb.bins.gids[:M].cpu().numpy().view(np.uint32), gids)
+    assert np.array_equal(vb.bins.keys[:M].cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(vb.bins.ranges.cpu().numpy().view(np.uint32), ranges)
+
+
+def _render_gpu(scene, cam, st):
+    g, vb, M = _gpu_view(scene, cam, st)
+    B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib)
+    torch.cuda.synchronize()
+    return g, vb
+
+
+@pytest.mark.parametrize("name,mk_scene,mk_cam,st", CASES, ids=[c[0] for c in CASES])
+def test_render_fwd_parity(name, mk_scene, mk_cam, st):
+    scene, cam = mk_scene(), mk_cam()
+    g, vb = _render_gpu(scene, cam, st)
+    ref = oracle.render(scene, cam, st)
+    ok = ~ref["band"]
+    assert ok.mean() > 0.999
+    img = vb.image.cpu().numpy().astype(np.float64)
+    assert np.abs(img - ref["image"])[ok].max() < 1e-5
+    assert np.array_equal(vb.n_contrib.cpu().numpy()[ok], ref["n_contrib"][ok])
+    assert np.abs(vb.final_T.cpu().numpy() - ref["final_T"])[ok].max() < 1e-5
+
+
+def test_single_opaque_gaussian_exact_colour():
+    c0 = 0.5 / np.sqrt(np.pi)
+    sc = synth.Scene(np.array([[0, 0, 3.0]], np.float32), np.full((1, 3), -3.0, np.float32),
+                     np.array([[1, 0, 0, 0]], np.float32), np.array([np.log(0.999 / 0.001)], np.float32),
+                     (np.array([[[0.6, -0.4, 0.0]]]) / c0).astype(np.float32), 0)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings(bg=(0.2, 0.3, 0.4))
+    g, vb = _render_gpu(sc, cam, st)
+    ref = oracle.render(sc, cam, st)
+    assert np.abs(vb.image.cpu().numpy()[32, 32] - ref["image"][32, 32]).max() < 1e-6
+
+
+def _backward_both(scene, cam, st, target_seed=2):
+    g, vb = _render_gpu(scene, cam, st)
+    ref = oracle.render(scene, cam, st)
+    tgt = synth.target_image(target_seed, cam.height, cam.width)
+    L_ref, dL_ref = oracle.l1_loss_grad(ref["image"], tgt)
+    # the backward is compared on the same dL/dC (the oracle's, as float32)
+    dL = torch.as_tensor(dL_ref.astype(np.float32)).cuda().contiguous()
+    grads = g.zeros_like()
+    S = torch.zeros(scene.n, 6, device="cuda")
+    ws = B.workspace(B.render_bwd_workspace_size(scene.n))
+    B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, dL, grads, S, ws)
+    torch.cuda.synchronize()
+    acc = oracle.backward(scene, cam, st, dL_ref.astype(np.float32).astype(np.float64))
+    return grads, S, acc, ref, tgt
+
+
+@pytest.mark.parametrize("name,mk_scene,mk_cam,st", CASES, ids=[c[0] for c in CASES])
+def test_backward_with_splitting_parity(name, mk_scene, mk_cam, st):
+    scene, cam = mk_scene(), mk_cam()
+    grads, S, acc, ref, _ = _backward_both(scene, cam, st)
+    assert ref["band"].mean() < 1e-3
+    for f, t in zip(FIELDS, grads.tensors()):
+        r = _rel(t.cpu().numpy(), acc[f])
+        assert r < 1e-4, (f, r)
+    Sg = S.cpu().numpy()
+    So = _upper6(acc["S"])
+    assert _rel(Sg, So) < 1e-4
+
+
+def test_l1_loss_grad_parity():
+    rng = np.random.default_rng(0)
+    img = rng.uniform(size=(37, 53, 3)).astype(np.float32)
+    tgt = synth.target_image(1, 37, 53)
+    L_ref, g_ref = oracle.l1_loss_grad(img.astype(np.float64), tgt, n_views=3)
+    ti, tt = torch.as_tensor(img).cuda(), torch.as_tensor(tgt).cuda()
+    dL = torch.empty_like(ti)
+    loss = torch.zeros(1, device="cuda")
+    B.l1_loss_grad(ti, tt, 3, dL, loss)
+    torch.cuda.synchronize()
+    assert np.array_equal(np.sign(dL.cpu().numpy()), np.sign(g_ref))
+    assert np.abs(dL.cpu().numpy() - g_ref).max() < 1e-6 * np.abs(g_ref).max()
+    assert abs(loss.item() - L_ref) < 1e-5 * L_ref
+
+
+def _densify_both(scene, S_or, S_gpu, eps_split, step_scale=1.0, inv_T=1.0, grad_norm=None, eps_grad=0.0):
+    g = B.GaussianTensors.from_scene(scene)
+    db = PL.DensifyBuffers.alloc(g)
+    gn = None if grad_norm is None else torch.as_tensor(grad_norm.astype(np.float32)).cuda()
+    B.densify_split(g, S_gpu, inv_T, eps_split, step_scale, gn, eps_grad, db.out, db.capacity, db.n_out, db.parent,
+                    db.lam, db.v, db.split_ws)
+    torch.cuda.synchronize()
+    lam_o, v_o = oracle.eig3_min(S_or, inv_T)
+    sp = oracle.split(scene, lam_o, v_o, eps_split, step_scale, grad_norm, eps_grad)
+    return db, lam_o, v_o, sp
+
+
+@pytest.mark.parametrize("name,mk_scene,mk_cam,st", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_densify_split_parity(name, mk_scene, mk_cam, st):
+    scene, cam = mk_scene(), mk_cam()
+    grads, S, acc, ref, _ = _backward_both(scene, cam, st)
+    # the densify step reads the oracle's S (as float32), so its checks are independent of the backward's
+    S_or = acc["S"].astype(np.float32).astype(np.float64)
+    S_gpu = torch.as_tensor(_upper6(acc["S"]).astype(np.float32)).cuda().contiguous()
+    for eps_split in (0.0, -1e-6):
+        db, lam_o, v_o, sp = _densify_both(scene, S_or, S_gpu, eps_split, step_scale=0.5, inv_T=0.5)
+        lam_g = db.lam.cpu().numpy()
+        v_g = db.v.cpu().numpy()
+        nrm = np.linalg.norm(S_or.reshape(-1, 9), axis=1) * 0.5
+        assert np.all(np.abs(lam_g - lam_o) <= 1e-4 * np.maximum(nrm, 1e-30))
+        ev = np.linalg.eigvalsh(S_or * 0.5)
+        gap = (ev[:, 1] - ev[:, 0]) > 1e-3 * nrm
+        cosang = np.abs(np.sum(v_g * v_o, 1))
+        assert np.all(1 - cosang[gap] <= 1e-4)
+        decided = np.abs(lam_o - eps_split) > max(1e-6, 0.0)
+        flags_g = np.zeros(scene.n, bool)
+        n_out = int(db.n_out.item())
+        par = db.parent.cpu().numpy()[:n_out]
+        flags_g[par[scene.n:]] = True
+        assert np.array_equal(flags_g[decided], sp["flags"][decided])
+        if np.array_equal(flags_g, sp["flags"]):
+            assert n_out == sp["n_out"]
+            assert np.array_equal(par, sp["parent"])
+            om = db.out.means[:n_out].cpu().numpy()
+            assert np.abs(om - sp["means"]).max() < 1e-4 * 0.5 * np.exp(scene.log_scales.max()) + 1e-6
+            ol = db.out.opacity_logit[:n_out].cpu().numpy()
+            assert np.abs(ol - sp["opacity_logit"]).max() < 1e-5
+            for f in ("log_scales", "quats", "sh"):
+                assert np.array_equal(getattr(db.out, f)[:n_out].cpu().numpy(), sp[f].astype(np.float32))
+
+
+def test_densify_gradient_gate_parity():
+    scene = synth.tiny_scene(0)
+    cam = synth.camera_identity(64, 64, 64.0)
+    _, _, acc, _, _ = _backward_both(scene, cam, synth.Settings())
+    S_or = acc["S"].astype(np.float32).astype(np.float64)
+    S_gpu = torch.as_tensor(_upper6(acc["S"]).astype(np.float32)).cuda().contiguous()
+    gn = np.random.default_rng(3).uniform(size=scene.n).astype(np.float32).astype(np.float64)
+    db, lam_o, v_o, sp = _densify_both(scene, S_or, S_gpu, -1e-6, grad_norm=gn, eps_grad=0.4)
+    n_out = int(db.n_out.item())
+    decided = np.abs(lam_o + 1e-6) > 1e-6
+    flags_g = np.zeros(scene.n, bool)
+    flags_g[db.parent.cpu().numpy()[scene.n:n_out]] = True
+    assert np.array_equal(flags_g[decided], sp["flags"][decided])
+
+
+def test_fused_iteration_end_to_end():
+    """The whole pipeline (both views summed) against the oracle iteration."""
+    scene = synth.tiny_scene(0)
+    cams = [synth.camera_identity(64, 64, 64.0), synth.camera_identity(64, 64, 64.0, centre=(0.2, -0.1, 0.0))]
+    st = synth.Settings()
+    tg = [synth.target_image(2, 64, 64), synth.target_image(3, 64, 64)]
+    g = B.GaussianTensors.from_scene(scene)
+    views = [PL.ViewBuffers.alloc(scene.n, c, st) for c in cams]
+    db = PL.DensifyBuffers.alloc(g)
+    targets = [torch.as_tensor(t).cuda() for t in tg]
+    PL.fused_iteration(g, views, targets, db, eps_split=-1e-6)
+    torch.cuda.synchronize()
+    ref = oracle.densify_iteration(scene, cams, st, tg, eps_split=-1e-6)
+    assert abs(db.loss.item() - ref["loss"]) < 1e-5 * ref["loss"]
+    assert _rel(db.S.cpu().numpy(), _upper6(ref["grads"]["S"])) < 1e-4
+    for f, t in zip(FIELDS, db.grads.tensors()):
+        assert _rel(t.cpu().numpy(), ref["grads"][f]) < 1e-4, f
+
+
+def test_empty_and_fully_culled_scenes():
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings()
+    empty = synth.subset(synth.tiny_scene(0), slice(0, 0))
+    g, vb = _render_gpu(empty, cam, st)
+    assert int(vb.bins.count.item()) == 0
+    assert np.all(vb.image.cpu().numpy() == 0.0) and np.all(vb.final_T.cpu().numpy() == 1.0)
+    behind = synth.tiny_scene(1)
+    behind.means[:, 2] = -behind.means[:, 2]
+    g, vb = _render_gpu(behind, cam, st)
+    assert int(vb.bins.count.item()) == 0
+    assert np.all(vb.proj.tiles_touched.cpu().numpy() == 0)
+    grads = g.zeros_like()
+    S = torch.zeros(behind.n, 6, device="cuda")
+    dL = torch.ones(64, 64, 3, device="cuda")
+    B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, dL, grads, S,
+                                B.workspace(B.render_bwd_workspace_size(behind.n)))
+    torch.cuda.synchronize()
+    assert float(S.abs().max()) == 0.0 and float(grads.means.abs().max()) == 0.0
+
+
+def test_capacity_overflow_reported_and_regrown():
+    scene = synth.tiny_scene(0)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings()
+    g = B.GaussianTensors.from_scene(scene)
+    vb = PL.ViewBuffers.alloc(scene.n, cam, st, capacity=16, with_keys=True)
+    B.project(g, cam, st, vb.proj)
+    B.bin_sort(vb.proj, scene.n, cam, st, vb.bins, vb.sort_ws)
+    torch.cuda.synchronize()
+    M = int(vb.bins.count.item())
+    keys, gids, ranges = oracle.bin_sort(scene, cam, st)
+    assert M == len(keys) > 16
+    M2 = PL.project_and_sort(g, vb)
+    torch.cuda.synchronize()
+    assert M2 == M and vb.bins.capacity >= M
+    assert np.array_equal(vb.bins.gids[:M].cpu().numpy().view(np.uint32), gids)
+
+
+def test_invalid_arguments_rejected_on_host():
+    scene = synth.tiny_scene(0)
+    cam = synth.camera_identity(64, 64, 64.0)
+    g = B.GaussianTensors.from_scene(scene)
+    vb = PL.ViewBuffers.alloc(scene.n, cam, synth.Settings())
+    with pytest.raises(B.SteepGSError) as e:
+        B.project(g, cam, synth.Settings(tile_w=12, tile_h=12), vb.proj)
+    assert e.value.status == 1
+    with pytest.raises(B.SteepGSError) as e:
+        B.bin_sort(vb.proj, scene.n, cam, synth.Settings(), vb.bins, B.workspace(16))
+    assert e.value.status == 2
