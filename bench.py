@@ -1,0 +1,375 @@
+"""Benchmark of the fused SteepGS fwd+bwd+splitting iteration on GB300.
+
+Workload: scene-scale single view -- 1,000,000 Gaussians from the 64-cluster
+mixture (SH degree 3), one 1237x822 view at distance 6, 16x16 tiles, L1 loss
+to a uniform-random target, then the minimum-eigenpair split at
+lambda_min < 0.  A step = one fused iteration: project, bin_sort, render_fwd,
+l1_loss_grad, render_bwd_with_splitting, densify_split (all in libsteepgs).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Prints one JSON line (rank 0).  N>1 (torchrun) runs N independent replicas
+("replicas only": the path has no exchange step on one view).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "fwd+bwd+splitting ms/iter @1M Gaussians; render frames/s + p50/p99 ms"
+N_GAUSS = 1_000_000
+WIDTH, HEIGHT = 1237, 822
+SCENE_SEED, TARGET_SEED = 0, 1
+EPS_SPLIT = 0.0
+WORKLOAD = "scene-scale single view: 1M Gaussians (64-cluster mixture, SH3), 1237x822, 16x16 tiles"
+
+# FP32 operations per pixel-Gaussian pair, counted from render.cu (FMA = 2).
+OPS_FWD_COMPOSITED = 28      # offset, quadratic form, exp, alpha, T update, 3 colour FMAs
+OPS_FWD_SKIPPED = 17         # offset, quadratic form, exp, alpha, threshold test
+OPS_BWD_COMPOSITED = 68      # + T division, dL/dalpha, colour behind, 9 gradient and 4 split terms
+OPS_BWD_SKIPPED = 19
+OPS_PROJ_BWD = 420           # projection adjoint + S lift per visible Gaussian (counted)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the GPU works."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, period_ms: int = 20):
+        self.index, self.period = index, period_ms
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", f"-lms={self.period}"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        busy = [s for s in sm if mx is None or s > 0.3 * mx] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(n, m, p, t):
+    """Bytes each array of the iteration is read or written once (SH degree 3)."""
+    return 932 * n + 124 * m + 88 * p + 8 * t
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_05587_gb300 import binding as B
+    from paper_2505_05587_gb300 import pipeline as PL
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.lib()
+
+    scene = synth.cluster_scene(SCENE_SEED, N_GAUSS, 3)
+    cam = synth.scene_camera(WIDTH, HEIGHT)
+    st = synth.Settings()
+    target_np = synth.target_image(TARGET_SEED, HEIGHT, WIDTH)
+    g = B.GaussianTensors.from_scene(scene, dev)
+    target = torch.as_tensor(target_np).to(dev)
+    vb = PL.ViewBuffers.alloc(g.n, cam, st, capacity=4 * g.n, device=dev)
+    db = PL.DensifyBuffers.alloc(g)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # warm-up (the first call also sizes the instance buffers)
+    PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=True)
+    for _ in range(max(args.warmup - 1, 0)):
+        PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=False)
+    torch.cuda.synchronize(dev)
+    M = int(vb.bins.count.item())
+    n_out = int(db.n_out.item())
+
+    names = ["zero_accumulators", "project", "bin_sort", "render_fwd", "l1_loss_grad",
+             "render_bwd_with_splitting", "densify_split"]
+    NC = len(names)
+
+    def one_step(ev):
+        """One fused iteration with events around each call (on the launching stream)."""
+        ev[0].record(stream)
+        db.zero_()
+        ev[1].record(stream)
+        B.project(g, cam, st, vb.proj, stream)
+        ev[2].record(stream)
+        B.bin_sort(vb.proj, g.n, cam, st, vb.bins, vb.sort_ws, stream)
+        ev[3].record(stream)
+        B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib, stream)
+        ev[4].record(stream)
+        B.l1_loss_grad(vb.image, target, 1, vb.dL, db.loss, stream)
+        ev[5].record(stream)
+        B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, vb.dL, db.grads,
+                                    db.S, db.bwd_ws, stream)
+        ev[6].record(stream)
+        B.densify_split(g, db.S, 1.0, EPS_SPLIT, 1.0, None, 0.0, db.out, db.capacity, db.n_out, db.parent, db.lam,
+                        db.v, db.split_ws, stream)
+        ev[7].record(stream)
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(NC + 1)] for _ in range(K)]
+    sampler = ClockSampler(local)
+    with sampler:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        launches0 = B.kernel_launches()
+        wall0 = time.perf_counter()
+        for k in range(K):
+            flush.zero_()                     # L2 flush between iterations, outside the events
+            one_step(evs[k])
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - wall0
+        launches = B.kernel_launches() - launches0
+        if world > 1:
+            dist.barrier()
+
+        # end-to-end through the public API: pinned host inputs in, loss and count out
+        host = [t.detach().cpu().pin_memory() for t in g.tensors()]
+        host_tgt = target.detach().cpu().pin_memory()
+        loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+        nout_host = torch.empty(1, dtype=torch.int32).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host) + host_tgt.numel() * 4
+        e2e_ms = []
+        for k in range(max(K // 2, 3)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for dst, src in zip(g.tensors(), host):
+                dst.copy_(src, non_blocking=True)
+            target.copy_(host_tgt, non_blocking=True)
+            PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=False)
+            loss_host.copy_(db.loss, non_blocking=True)
+            nout_host.copy_(db.n_out, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+    clocks = sampler.summary()
+
+    per_call = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(NC)] for k in range(K)])
+    step_ms = per_call.sum(1)
+    ms_iter = float(step_ms.mean())
+    e2e = float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([ms_iter, e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_iter, e2e = float(t[0]), float(t[1])
+
+    # work units of the dominant launch (outside the timed region)
+    counts = torch.empty(HEIGHT, WIDTH, 2, dtype=torch.int32, device=dev)
+    B.render_stats(vb.proj, vb.bins, cam, st, counts, stream)
+    torch.cuda.synchronize(dev)
+    c = counts.to(torch.int64)
+    ev_fwd, comp = int(c[..., 0].sum()), int(c[..., 1].sum())
+    ev_bwd = int(vb.n_contrib.to(torch.int64).sum())
+    n_vis = int((vb.proj.tiles_touched > 0).sum())
+    call_ms = per_call.mean(0)
+    dom = int(np.argmax(call_ms))
+    flops_bwd = comp * OPS_BWD_COMPOSITED + (ev_bwd - comp) * OPS_BWD_SKIPPED + n_vis * OPS_PROJ_BWD
+    flops_fwd = comp * OPS_FWD_COMPOSITED + (ev_fwd - comp) * OPS_FWD_SKIPPED
+    hbm_peak, peak_kind = _peaks()
+    T = B.num_tiles(cam, st)
+    P = WIDTH * HEIGHT
+    alg_bytes = algorithmic_bytes(N_GAUSS, M, P, T)
+    if names[dom] == "render_fwd":
+        achieved = flops_fwd / (call_ms[dom] * 1e-3) / 1e12
+    else:
+        dom = names.index("render_bwd_with_splitting")
+        achieved = flops_bwd / (call_ms[dom] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": names[dom], "achieved": round(achieved, 3),
+                "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "traffic": args.traffic if args.traffic is not None else None,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "work": {"pairs_evaluated_fwd": ev_fwd, "pairs_evaluated_bwd": ev_bwd,
+                         "pairs_composited": comp, "visible_gaussians": n_vis}}
+    hbm = {"bytes_per_iter": alg_bytes, "achieved": round(alg_bytes / (ms_iter * 1e-3) / 1e9, 1),
+           "peak": hbm_peak, "unit": "GB/s", "frac": round(alg_bytes / (ms_iter * 1e-3) / 1e9 / hbm_peak, 4),
+           "peak_kind": peak_kind}
+
+    result = {
+        "metric": METRIC, "value": round(ms_iter / world, 4), "unit": "ms/iter", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(ms_iter, 4), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
+                   "sh_degree": 3, "tile": "16x16", "instances_M": M, "n_out": n_out,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "256 MiB buffer written between iterations, outside the timed events"},
+        "per_call_ms": {nm: round(float(v), 4) for nm, v in zip(names, call_ms)},
+        "wall_ms_per_step": round(wall * 1e3 / K, 4),
+        "roofline": roofline, "hbm_roofline": hbm,
+        "e2e": {"value": round(e2e / world, 4), "unit": "ms/iter", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": 8},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_full()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timings
+# ---------------------------------------------------------------------------
+def _oracle_iteration(scene, cam, st, target):
+    import oracle
+    r = oracle.render(scene, cam, st)
+    _, g = oracle.l1_loss_grad(r["image"], target)
+    acc = oracle.backward(scene, cam, st, g)
+    lam, v = oracle.eig3_min(acc["S"])
+    oracle.split(scene, lam, v, EPS_SPLIT, 1.0)
+
+
+def cpu_baseline_full():
+    """The oracle, as it stands (single thread, float64), on one full iteration."""
+    scene = synth.cluster_scene(SCENE_SEED, N_GAUSS, 3)
+    cam = synth.scene_camera(WIDTH, HEIGHT)
+    tgt = synth.target_image(TARGET_SEED, HEIGHT, WIDTH)
+    t0 = time.perf_counter()
+    _oracle_iteration(scene, cam, synth.Settings(), tgt)
+    dt = time.perf_counter() - t0
+    return {"value": round(dt * 1e3, 1), "unit": "ms/iter", "cores": 1, "kind": "oracle",
+            "sample": "one full fused iteration of the same workload (float64 C oracle, 1 thread)"}
+
+
+def _strip_camera(cam, y0, h):
+    return synth.Camera(cam.R, cam.t, cam.fx, cam.fy, cam.cx, cam.cy - y0, cam.width, h, cam.near_z)
+
+
+def run_reference(args):
+    """Oracle arm: each step runs the oracle's fused iteration on the full scene
+    for a horizontal strip of rows; the per-iteration time is extrapolated with
+    a linear model t(rows) = a + b rows, a measured on a one-row strip."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    scene = synth.cluster_scene(SCENE_SEED, N_GAUSS, 3)
+    cam = synth.scene_camera(WIDTH, HEIGHT)
+    st = synth.Settings()
+    tgt = synth.target_image(TARGET_SEED, HEIGHT, WIDTH)
+    t0 = time.perf_counter()
+    _oracle_iteration(scene, _strip_camera(cam, 400, 1), st, tgt[400:401])
+    a = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _oracle_iteration(scene, _strip_camera(cam, 400, 16), st, tgt[400:416])
+    b16 = max(time.perf_counter() - t0 - a, 1e-3) / 16.0
+    budget = 150.0
+    steps = args.steps + args.warmup
+    rows = int((budget / steps - a) / b16) // 16 * 16
+    rows = max(16, min(HEIGHT // 16 * 16, rows))
+    est = []
+    for k in range(steps):
+        y0 = (k * rows) % (HEIGHT - rows + 1) // 16 * 16
+        t0 = time.perf_counter()
+        _oracle_iteration(scene, _strip_camera(cam, y0, rows), st, tgt[y0:y0 + rows])
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            est.append(a + (dt - a) * HEIGHT / rows)
+    v = float(np.mean(est)) * 1e3
+    out = {"metric": METRIC, "value": round(v, 1), "unit": "ms/iter", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
+                      "sh_degree": 3, "tile": "16x16"},
+           "cpu_baseline": {"value": round(v, 1), "unit": "ms/iter", "cores": 1, "kind": "oracle",
+                            "sample": f"per step: full scene, a {rows}-row strip of the view (rotating); "
+                                      f"t(rows) = a + b rows extrapolated to {HEIGHT} rows, a = "
+                                      f"{a:.2f} s from a one-row strip"},
+           "e2e": {"value": round(v, 1), "unit": "ms/iter", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the dominant kernel from an ncu capture")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -151,6 +151,9 @@ const char *sgs_error_string(int status);
 int sgs_get_last_cuda_error(void);
 /* Library version, major*10000 + minor*100 + patch. */
 int sgs_version(void);
+/* Number of CUDA kernel launches this library has issued since it was loaded
+ * (all threads), for measurement reports.  Memsets are not counted. */
+uint64_t sgs_kernel_launches(void);
 
 /* Projection (Section 3, Eq. sigma_2D and the affine-Pi footnote; Pi is the
  * pinhole map, linearised at p as P = J W for the 2-D covariance).
@@ -182,6 +185,12 @@ int sgs_bin_sort(const sgs_proj *proj, int32_t n, const sgs_camera *cam, const s
 int sgs_render_fwd(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
                    const sgs_settings *st, float *image, float *final_T, uint32_t *n_contrib,
                    void *stream);
+
+/* Pair counts of the forward walk (a measurement aid, not on the path):
+ * counts [H,W,2] uint32 = (pairs evaluated, pairs composited) per pixel, the
+ * work units behind the rasteriser's algorithmic FLOP count. */
+int sgs_render_stats(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
+                     const sgs_settings *st, uint32_t *counts, void *stream);
 
 /* L1 photometric loss (Section 3, Eq. loss, l = |.|):
  * loss += mean over pixels and channels of |image - target| / n_views and

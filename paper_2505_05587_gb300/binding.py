@@ -89,17 +89,19 @@ def lib():
         L.sgs_error_string.argtypes = [C.c_int]
         L.sgs_get_last_cuda_error.restype = C.c_int
         L.sgs_version.restype = C.c_int
+        L.sgs_kernel_launches.restype = C.c_uint64
         L.sgs_project.argtypes = [P, P, P, P, P]
         L.sgs_bin_sort_workspace_size.argtypes = [I32, I64, I32, C.POINTER(SZ)]
         L.sgs_bin_sort.argtypes = [P, I32, P, P, P, P, SZ, P]
         L.sgs_render_fwd.argtypes = [P, P, P, P, P, P, P, P]
         L.sgs_l1_loss_grad.argtypes = [P, P, I32, I32, I32, P, P, P]
+        L.sgs_render_stats.argtypes = [P, P, P, P, P, P]
         L.sgs_render_bwd_workspace_size.argtypes = [I32, C.POINTER(SZ)]
         L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, P, P, SZ, P]
         L.sgs_densify_split_workspace_size.argtypes = [I32, C.POINTER(SZ)]
         L.sgs_densify_split.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P, SZ, P]
         for name in ("sgs_project", "sgs_bin_sort_workspace_size", "sgs_bin_sort", "sgs_render_fwd",
-                     "sgs_l1_loss_grad", "sgs_render_bwd_workspace_size", "sgs_render_bwd_with_splitting",
+                     "sgs_l1_loss_grad", "sgs_render_stats", "sgs_render_bwd_workspace_size", "sgs_render_bwd_with_splitting",
                      "sgs_densify_split_workspace_size", "sgs_densify_split"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -270,6 +272,13 @@ def render_fwd(proj: ProjBuffers, bins: BinBuffers, cam, st, image, final_T, n_c
                                                    _p(final_T), _p(n_contrib), _stream(stream)))
 
 
+def render_stats(proj: ProjBuffers, bins: BinBuffers, cam, st, counts, stream=None):
+    """counts: int32 [H,W,2] <- (pairs evaluated, pairs composited) per pixel."""
+    pc, bc, cc, sc = proj.c(), bins.c(), camera_c(cam), settings_c(st)
+    _check("sgs_render_stats", lib().sgs_render_stats(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
+                                                       _p(counts), _stream(stream)))
+
+
 def l1_loss_grad(image, target, n_views: int, dL_dimage, loss, stream=None):
     H, W = int(image.shape[0]), int(image.shape[1])
     _check("sgs_l1_loss_grad", lib().sgs_l1_loss_grad(_p(image), _p(target), H, W, n_views, _p(dL_dimage),
@@ -308,6 +317,11 @@ def densify_split(g: GaussianTensors, S_accum, inv_T_split: float, eps_split: fl
                                    eps_grad, C.byref(oc), capacity, _p(d_n_out), _p(parent_index),
                                    _p(lam_min_out), _p(v_min_out), _p(ws), ws.numel() * ws.element_size(),
                                    _stream(stream)))
+
+
+def kernel_launches() -> int:
+    """Kernel launches issued by the library so far (process-wide)."""
+    return int(lib().sgs_kernel_launches())
 
 
 def workspace(nbytes: int, device="cuda") -> torch.Tensor:

@@ -3,6 +3,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace sgs {
@@ -38,6 +40,9 @@ SetDev make_set(const sgs_settings& s) {
 }
 
 static thread_local int g_last_cuda = 0;
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 
 static int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SGS_OK;
@@ -91,6 +96,8 @@ int sgs_get_last_cuda_error(void) { return g_last_cuda; }
 
 int sgs_version(void) { return 100; }
 
+uint64_t sgs_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
+
 int sgs_project(const sgs_gaussians* g, const sgs_camera* cam, const sgs_settings* st, const sgs_proj* out,
                 void* stream) {
     if (!valid_gaussians(g) || !valid_cam(cam) || !valid_settings(st) || !out || !tiles_fit(cam, st))
@@ -127,6 +134,15 @@ int sgs_render_fwd(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera*
         return SGS_ERR_INVALID_ARG;
     return cuda_status(launch_render_fwd(*proj, *bins, make_cam(*cam, *st), make_set(*st), image, final_T,
                                          n_contrib, (cudaStream_t)stream));
+}
+
+int sgs_render_stats(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,
+                     uint32_t* counts, void* stream) {
+    if (!proj || !bins || !valid_cam(cam) || !valid_settings(st) || !counts || !tiles_fit(cam, st) ||
+        !bins->ranges)
+        return SGS_ERR_INVALID_ARG;
+    return cuda_status(launch_render_stats(*proj, *bins, make_cam(*cam, *st), make_set(*st), counts,
+                                           (cudaStream_t)stream));
 }
 
 int sgs_l1_loss_grad(const float* image, const float* target, int32_t height, int32_t width, int32_t n_views,

@@ -61,6 +61,8 @@ __device__ Stage integer_stage(const float* __restrict__ means, const float* __r
                                const SetDev& st);
 
 // Host helpers (defined in api.cu)
+// Counts kernel launches issued by the library (for measurement reports).
+void note_launch(int k = 1);
 CamDev make_cam(const sgs_camera& c, const sgs_settings& s);
 SetDev make_set(const sgs_settings& s);
 bool tile_supported(int tw, int th);
@@ -82,6 +84,9 @@ cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const 
 cudaError_t launch_render_bwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
                               const SetDev& st, const float* final_T, const uint32_t* n_contrib,
                               const float* dL_dimage, float* g2d, cudaStream_t stream);
+
+cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
+                                const SetDev& st, uint32_t* counts, cudaStream_t stream);
 
 cudaError_t launch_l1(const float* image, const float* target, int H, int W, int n_views,
                       float* dL, float* loss, cudaStream_t stream);

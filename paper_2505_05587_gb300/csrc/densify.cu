@@ -194,13 +194,16 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T,
     if (n == 0) return cudaMemsetAsync(d_n_out, 0, sizeof(int32_t), stream);
     const int nb = (n + 255) / 256;
     eig_flag_kernel<<<nb, 256, 0, stream>>>(S, n, inv_T, eps_split, grad_norm, eps_grad, lam, v, flags);
+    note_launch();
     cudaError_t e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
     if (e != cudaSuccess) return e;
     n_out_kernel<<<1, 1, 0, stream>>>(total, n, d_n_out);
+    note_launch();
     const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;
     split_kernel<<<nb, 256, 0, stream>>>(in.means, in.log_scales, in.quats, in.opacity_logit, in.sh, n, K3, v,
                                          flags, excl, step_scale, capacity, out.means, out.log_scales,
                                          out.quats, out.opacity_logit, out.sh, parent);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -237,6 +240,7 @@ cudaError_t launch_l1(const float* image, const float* target, int H, int W, int
     int64_t blocks = (count + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     l1_kernel<<<(int)blocks, 256, 0, stream>>>(image, target, count, norm, dL, loss);
+    note_launch();
     return cudaGetLastError();
 }
 

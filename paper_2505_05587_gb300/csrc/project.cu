@@ -282,6 +282,7 @@ cudaError_t launch_project(const sgs_gaussians& g, const CamDev& cam, const SetD
         reinterpret_cast<float4*>(out.xy), reinterpret_cast<float4*>(out.conic_opac),
         reinterpret_cast<float4*>(out.rgb), out.depth, reinterpret_cast<short4*>(out.rect),
         out.tiles_touched);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -480,6 +481,7 @@ cudaError_t launch_project_bwd(const sgs_gaussians& g, const CamDev& cam, const 
     project_bwd_kernel<<<blocks, 128, 0, stream>>>(
         g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, g.sh_degree, cam, st, g2d,
         grads.means, grads.log_scales, grads.quats, grads.opacity_logit, grads.sh, S_accum);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -81,6 +81,37 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
     }
 }
 
+// Pair counts of the forward walk, per pixel: (pairs evaluated, pairs
+// composited).  A measurement aid; it replays the walk without colour.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) render_stats_kernel(
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
+    const float4* __restrict__ conic_opac, int W, int H, int gx, SetDev st, uint2* __restrict__ counts) {
+    const int tile = blockIdx.x;
+    const int px = (tile % gx) * TW + (int)(threadIdx.x % TW);
+    const int py = (tile / gx) * TH + (int)(threadIdx.x / TW);
+    if (px >= W || py >= H) return;
+    const uint2 rg = ranges[tile];
+    float T = 1.0f;
+    uint32_t ev = 0, comp = 0;
+    for (uint32_t k = rg.x; k < rg.y; ++k) {
+        const uint32_t g = gids[k];
+        const float4 m = xy[g];
+        const float4 co = conic_opac[g];
+        const float dx = ((float)px - m.x) - m.z;
+        const float dy = ((float)py - m.y) - m.w;
+        const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+        const float alpha = fminf(st.alpha_max, co.w * __expf(power));
+        ++ev;
+        if (alpha < st.alpha_min) continue;
+        const float Tn = T * (1.0f - alpha);
+        if (Tn < st.T_min) break;
+        ++comp;
+        T = Tn;
+    }
+    counts[py * W + px] = make_uint2(ev, comp);
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -200,6 +231,27 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
 }
 
 template <int TW, int TH>
+static cudaError_t stats_tmpl(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
+                              uint32_t* counts, cudaStream_t stream) {
+    const int T = cam.gx * cam.gy;
+    render_stats_kernel<TW, TH><<<T, TW * TH, 0, stream>>>(
+        reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
+        reinterpret_cast<const float4*>(proj.conic_opac), cam.width, cam.height, cam.gx, st,
+        reinterpret_cast<uint2*>(counts));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
+                                uint32_t* counts, cudaStream_t stream) {
+    if (st.tile_w == 16 && st.tile_h == 16) return stats_tmpl<16, 16>(proj, bins, cam, st, counts, stream);
+    if (st.tile_w == 16 && st.tile_h == 8) return stats_tmpl<16, 8>(proj, bins, cam, st, counts, stream);
+    if (st.tile_w == 8 && st.tile_h == 8) return stats_tmpl<8, 8>(proj, bins, cam, st, counts, stream);
+    if (st.tile_w == 32 && st.tile_h == 8) return stats_tmpl<32, 8>(proj, bins, cam, st, counts, stream);
+    return cudaErrorInvalidValue;
+}
+
+template <int TW, int TH>
 static cudaError_t fwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
                             float* image, float* final_T, uint32_t* n_contrib, cudaStream_t stream) {
     const int T = cam.gx * cam.gy;
@@ -207,6 +259,7 @@ static cudaError_t fwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const Ca
         reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
         reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
         cam.width, cam.height, cam.gx, st, image, final_T, n_contrib);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -219,6 +272,7 @@ static cudaError_t bwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const Ca
         reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
         reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
         cam.width, cam.height, cam.gx, st, final_T, n_contrib, dL, g2d);
+    note_launch();
     return cudaGetLastError();
 }
 

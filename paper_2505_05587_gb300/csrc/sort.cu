@@ -123,8 +123,11 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* d
     int nb = scan_blocks(n_max);
     uint32_t* partial = reinterpret_cast<uint32_t*>(tmp);
     scan_reduce_kernel<<<nb, SCAN_THREADS, 0, stream>>>(in, d_n, n_max, partial);
+    note_launch();
     scan_partials_kernel<<<1, SCAN_THREADS, 0, stream>>>(partial, nb, d_total);
+    note_launch();
     scan_downsweep_kernel<<<nb, SCAN_THREADS, 0, stream>>>(in, out, d_n, n_max, partial);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -309,9 +312,12 @@ static cudaError_t radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], const int32_
         int bits = min(bits_per, total_bits - shift);
         int src = p & 1, dst = src ^ 1;
         radix_hist_kernel<<<G, RS_THREADS, 0, stream>>>(k[src], d_n, n_host, n_max, shift, bits, rb.hist);
+        note_launch();
         radix_scan_kernel<<<1 << bits, 1024, 0, stream>>>(rb.hist, G, rb.digit_tot);
+        note_launch();
         radix_scatter_kernel<<<G, RS_THREADS, 0, stream>>>(k[src], v[src], k[dst], v[dst], d_n, n_host,
                                                            n_max, shift, bits, rb.hist, rb.digit_tot);
+        note_launch();
         shift += bits;
     }
     return cudaGetLastError();
@@ -427,11 +433,13 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, int n, const CamDev& cam, cons
     const int nb = (n + 255) / 256;
     // 1. stable sort of the Gaussians by depth bits (culled ones last)
     depth_keys_kernel<<<nb, 256, 0, stream>>>(proj.depth, proj.tiles_touched, n, w.dkey[0], w.perm[0]);
+    note_launch();
     e = radix_sort_pairs(w.dkey, w.perm, nullptr, n, n, 32, w.rb, stream);
     if (e != cudaSuccess) return e;
     const uint32_t* perm = w.perm[rs_passes(32) & 1];
     // 2. instance offsets in depth order, M
     gather_counts_kernel<<<nb, 256, 0, stream>>>(perm, proj.tiles_touched, n, w.cnt);
+    note_launch();
     e = launch_exclusive_scan(w.cnt, w.offs, reinterpret_cast<uint32_t*>(out.count), n, nullptr,
                               w.scan_tmp, stream);
     if (e != cudaSuccess) return e;
@@ -452,6 +460,7 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, int n, const CamDev& cam, cons
     }
     emit_kernel<<<nb, 256, 0, stream>>>(perm, w.cnt, w.offs, reinterpret_cast<const short4*>(proj.rect), n,
                                         cam.gx, out.capacity, gk[0], gv[0]);
+    note_launch();
     // 4. stable sort of the instances by tile id
     e = radix_sort_pairs(gk, gv, out.count, 0, out.capacity, tile_bits, w.rb, stream);
     if (e != cudaSuccess) return e;
@@ -460,9 +469,11 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, int n, const CamDev& cam, cons
     int rb = 152 * 8;
     ranges_kernel<<<rb, 256, 0, stream>>>(tile_sorted, out.count, out.capacity,
                                           reinterpret_cast<uint2*>(out.ranges));
+    note_launch();
     if (out.keys)
         keys_kernel<<<rb, 256, 0, stream>>>(tile_sorted, out.gids, proj.depth, out.count, out.capacity,
                                             out.keys);
+        note_launch();
     return cudaGetLastError();
 }
 
