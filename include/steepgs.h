@@ -240,6 +240,30 @@ int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, float inv_T
                       int32_t *parent_index, float *lam_min_out, float *v_min_out,
                       void *ws, size_t ws_bytes, void *stream);
 
+/* Allocation-free variant of sgs_densify_split (the paper has no counterpart:
+ * this is an interface convenience).  For callers that cannot give the
+ * library a workspace -- code running where cudaMalloc is not allowed or not
+ * wanted (a host callback, a real-time loop in which an allocation would
+ * synchronise the device, a plugin whose host owns every device allocation and
+ * passes only input and output buffers).  Same arguments, semantics and
+ * results as sgs_densify_split, minus the workspace: the scratch is a fixed
+ * SGS_NOALLOC_SCRATCH_BYTES array inside the library's device image, reserved
+ * on every GPU that loads the library until the process exits.
+ *   - n must not exceed SGS_NOALLOC_MAX_GAUSSIANS; larger n returns
+ *     SGS_ERR_INVALID_ARG before anything is launched.
+ *   - It works on the calling thread's current device.  The first call on a
+ *     device looks up the array's device address (cudaGetSymbolAddress) and
+ *     caches it; make that first call before any stream capture begins.
+ *   - Every call shares the one array, so calls whose work overlaps on the GPU
+ *     (other streams, other threads) race: serialise them.
+ *   - It calls no cudaMalloc, cudaFree or allocating routine. */
+#define SGS_NOALLOC_MAX_GAUSSIANS 1000000
+#define SGS_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
+int sgs_densify_split_noalloc(const sgs_gaussians *in, const float *S_accum, float inv_T_split,
+                              float eps_split, float step_scale, const float *grad_norm, float eps_grad,
+                              const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
+                              int32_t *parent_index, float *lam_min_out, float *v_min_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -100,9 +100,10 @@ def lib():
         L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, P, P, SZ, P]
         L.sgs_densify_split_workspace_size.argtypes = [I32, C.POINTER(SZ)]
         L.sgs_densify_split.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P, SZ, P]
+        L.sgs_densify_split_noalloc.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P]
         for name in ("sgs_project", "sgs_bin_sort_workspace_size", "sgs_bin_sort", "sgs_render_fwd",
                      "sgs_l1_loss_grad", "sgs_render_stats", "sgs_render_bwd_workspace_size", "sgs_render_bwd_with_splitting",
-                     "sgs_densify_split_workspace_size", "sgs_densify_split"):
+                     "sgs_densify_split_workspace_size", "sgs_densify_split", "sgs_densify_split_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -322,6 +323,19 @@ def densify_split(g: GaussianTensors, S_accum, inv_T_split: float, eps_split: fl
 def kernel_launches() -> int:
     """Kernel launches issued by the library so far (process-wide)."""
     return int(lib().sgs_kernel_launches())
+
+
+def densify_split_noalloc(g: GaussianTensors, S_accum, inv_T_split: float, eps_split: float, step_scale: float,
+                          grad_norm, eps_grad: float, out: GaussianTensors, capacity: int, d_n_out, parent_index,
+                          lam_min_out, v_min_out, stream=None):
+    """densify_split without a workspace, for callers that cannot allocate one
+    (its scratch is a fixed array inside the library; n <= 1,000,000; calls
+    that overlap on the GPU race)."""
+    gc, oc = g.c(), out.c_mut()
+    _check("sgs_densify_split_noalloc",
+           lib().sgs_densify_split_noalloc(C.byref(gc), _p(S_accum), inv_T_split, eps_split, step_scale,
+                                           _p(grad_norm), eps_grad, C.byref(oc), capacity, _p(d_n_out),
+                                           _p(parent_index), _p(lam_min_out), _p(v_min_out), _stream(stream)))
 
 
 def workspace(nbytes: int, device="cuda") -> torch.Tensor:

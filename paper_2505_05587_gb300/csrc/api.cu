@@ -44,10 +44,14 @@ static std::atomic<unsigned long long> g_launches{0};
 
 void note_launch(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 
-static int cuda_status(cudaError_t e) {
-    if (e == cudaSuccess) return SGS_OK;
+int record_cuda_error(cudaError_t e) {
     g_last_cuda = (int)e;
     return SGS_ERR_CUDA;
+}
+
+static int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SGS_OK;
+    return record_cuda_error(e);
 }
 
 static bool valid_cam(const sgs_camera* c) {

@@ -63,6 +63,8 @@ __device__ Stage integer_stage(const float* __restrict__ means, const float* __r
 // Host helpers (defined in api.cu)
 // Counts kernel launches issued by the library (for measurement reports).
 void note_launch(int k = 1);
+// Keeps `e` for sgs_get_last_cuda_error() and returns SGS_ERR_CUDA.
+int record_cuda_error(cudaError_t e);
 CamDev make_cam(const sgs_camera& c, const sgs_settings& s);
 SetDev make_set(const sgs_settings& s);
 bool tile_supported(int tw, int th);
