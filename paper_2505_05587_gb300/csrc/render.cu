@@ -6,18 +6,69 @@
 // splitting matrix S = E[dl/dsigma Hess_p sigma] accumulated during
 // back-propagation); Appendix "Deriving Hessian of Gaussian".
 //
-// One CTA per tile of TW x TH pixels, one thread per pixel.  Gaussian records
-// of the tile's depth-sorted list are staged in shared memory in batches of
-// TW*TH (one coalesced 16-byte load per field per thread).
+// One CTA per tile of TW x TH pixels, one thread per pixel, warps on 8x4 pixel
+// blocks.  Gaussian records of the tile's depth-sorted list are staged in
+// shared memory in batches of TW*TH (one coalesced 16-byte load per field per
+// thread); each warp then walks only the batch entries whose alpha support
+// meets its block (an exact skip: outside that support alpha < alpha_min).
 #include "common.cuh"
 
 namespace sgs {
 
-// Row of the per-Gaussian 2-D accumulator buffer (16 floats, 4 float4 atomics):
+// Row of the per-Gaussian 2-D accumulator buffer (16 floats; one 13-lane
+// vector of atomics per warp and Gaussian):
 //  0 dL/dmu_x   1 dL/dmu_y   2 dL/dQ00   3 dL/dQ01 (shared off-diagonal)
 //  4 dL/dQ11    5 dL/do      6..8 dL/drgb
 //  9 a0 = sum w   10..12 A2 = sum w u u^T (xx, xy, yy)   13..15 unused
 constexpr int kG2dStride = 16;
+
+// Pixel of a thread: warps cover 8x4 pixel blocks of the tile (lane -> 8
+// columns x 4 rows), so that a warp can skip, as a whole, every Gaussian whose
+// alpha support misses its block.
+template <int TW>
+__device__ __forceinline__ void warp_block_origin(int tile, int gx, int TH_, int* bx, int* by) {
+    const int warp = threadIdx.x >> 5;
+    *bx = (tile % gx) * TW + (warp % (TW / 8)) * 8;
+    *by = (tile / gx) * TH_ + (warp / (TW / 8)) * 4;
+}
+
+// Axis-aligned box of the region where alpha = o G can reach alpha_min:
+// d^T Q d <= 2 ln(o / alpha_min) (widened by a small safety margin, so the box
+// is conservative against float rounding).  Empty when o < alpha_min; the
+// whole plane when alpha_min = 0.
+__device__ __forceinline__ float4 alpha_support_box(float4 m, float4 co, float alpha_min) {
+    const float o = co.w;
+    if (!(o >= alpha_min)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);
+    if (!(alpha_min > 0.0f)) return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);
+    const float m2 = 2.0f * logf(o / alpha_min) * 1.001f + 1e-3f;
+    const float det = co.x * co.z - co.y * co.y;
+    const float ex = sqrtf(m2 * co.z / det) + 0.01f;
+    const float ey = sqrtf(m2 * co.x / det) + 0.01f;
+    const float cx = m.x + m.z, cy = m.y + m.w;
+    return make_float4(cx - ex, cx + ex, cy - ey, cy + ey);
+}
+
+// Order-preserving list of the batch entries whose support box meets the
+// warp's pixel block [bx, bx+7] x [by, by+3].  Returns the list length.
+__device__ __forceinline__ int build_warp_list(const float4* s_box, int cnt, float bx, float by,
+                                               uint8_t* list) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int nl = 0;
+    for (int c = 0; c < cnt; c += 32) {
+        const int e = c + lane;
+        bool hit = false;
+        if (e < cnt) {
+            const float4 b = s_box[e];
+            hit = b.y >= bx && b.x <= bx + 7.0f && b.w >= by && b.z <= by + 3.0f;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) list[nl + __popc(m & lt)] = (uint8_t)e;
+        nl += __popc(m);
+    }
+    __syncwarp();
+    return nl;
+}
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
@@ -25,12 +76,18 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
     float* __restrict__ image, float* __restrict__ final_T, uint32_t* __restrict__ n_contrib) {
     constexpr int BS = TW * TH;
+    constexpr int NW = BS / 32;
     __shared__ float4 s_xy[BS];
     __shared__ float4 s_co[BS];
     __shared__ float4 s_rgb[BS];
+    __shared__ float4 s_box[BS];
+    __shared__ uint8_t s_list[NW][BS];
     const int tile = blockIdx.x;
-    const int px = (tile % gx) * TW + (int)(threadIdx.x % TW);
-    const int py = (tile / gx) * TH + (int)(threadIdx.x / TW);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int bx, by;
+    warp_block_origin<TW>(tile, gx, TH, &bx, &by);
+    const int px = bx + (lane & 7);
+    const int py = by + (lane >> 3);
     const bool inside = px < W && py < H;
     const float fpx = (float)px, fpy = (float)py;
     const uint2 rg = ranges[tile];
@@ -40,16 +97,21 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
     uint32_t last = 0;
     for (int base = 0; base < n; base += BS) {
         if (__syncthreads_count(done) == BS) break;
-        const int k = base + (int)threadIdx.x;
-        if (k < n) {
-            const uint32_t g = gids[rg.x + k];
-            s_xy[threadIdx.x] = xy[g];
-            s_co[threadIdx.x] = conic_opac[g];
+        const int cnt = min(BS, n - base);
+        if ((int)threadIdx.x < cnt) {
+            const uint32_t g = gids[rg.x + base + threadIdx.x];
+            const float4 m = xy[g];
+            const float4 co = conic_opac[g];
+            s_xy[threadIdx.x] = m;
+            s_co[threadIdx.x] = co;
             s_rgb[threadIdx.x] = rgb[g];
+            s_box[threadIdx.x] = alpha_support_box(m, co, st.alpha_min);
         }
         __syncthreads();
-        const int cnt = min(BS, n - base);
-        for (int j = 0; !done && j < cnt; ++j) {
+        if (__all_sync(0xffffffffu, done)) continue;
+        const int nl = build_warp_list(s_box, cnt, (float)bx, (float)by, s_list[warp]);
+        for (int k = 0; k < nl && !done; ++k) {
+            const int j = s_list[warp][k];
             const float4 m = s_xy[j];
             const float4 co = s_co[j];
             const float dx = (fpx - m.x) - m.z;
@@ -112,10 +174,36 @@ __global__ void __launch_bounds__(TW * TH) render_stats_kernel(
     counts[py * W + px] = make_uint2(ev, comp);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Reduce-scatter of 16 per-lane values across the warp in 16 shuffles
+// (halving exchanges at strides 16, 8, 4, 2, then a final pair sum).  Lane l
+// returns the warp total of slot (l >> 1) & 15.
+__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int k = 0; k < 8; ++k) {
+        const float send = b4 ? v[k] : v[k + 8];
+        const float keep = b4 ? v[k + 8] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = b3 ? v[k] : v[k + 4];
+        const float keep = b3 ? v[k + 4] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = b2 ? v[k] : v[k + 2];
+        const float keep = b2 ? v[k + 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const float send = b1 ? v[0] : v[1];
+        const float keep = b1 ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 template <int TW, int TH>
@@ -125,19 +213,25 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
     const float* __restrict__ dL_dimage, float* __restrict__ g2d) {
     constexpr int BS = TW * TH;
+    constexpr int NW = BS / 32;
     __shared__ uint32_t s_gid[BS];
     __shared__ float4 s_xy[BS];
     __shared__ float4 s_co[BS];
     __shared__ float4 s_rgb[BS];
+    __shared__ float4 s_box[BS];
+    __shared__ uint8_t s_list[NW][BS];
     __shared__ uint32_t s_max;
     const int tile = blockIdx.x;
-    const int px = (tile % gx) * TW + (int)(threadIdx.x % TW);
-    const int py = (tile / gx) * TH + (int)(threadIdx.x / TW);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int bx, by;
+    warp_block_origin<TW>(tile, gx, TH, &bx, &by);
+    const int px = bx + (lane & 7);
+    const int py = by + (lane >> 3);
     const bool inside = px < W && py < H;
     const float fpx = (float)px, fpy = (float)py;
     const int pix = py * W + px;
     const uint2 rg = ranges[tile];
-    const int lane = threadIdx.x & 31;
+    const int slot = (lane >> 1) & 15;
 
     float T = inside ? final_T[pix] : 1.0f;
     const uint32_t last = inside ? n_contrib[pix] : 0u;
@@ -149,7 +243,7 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
     if (threadIdx.x == 0) s_max = 0u;
     __syncthreads();
     {
-        uint32_t m = __reduce_max_sync(0xffffffffu, last);
+        const uint32_t m = __reduce_max_sync(0xffffffffu, last);
         if (lane == 0) atomicMax(&s_max, m);
     }
     __syncthreads();
@@ -157,24 +251,29 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
 
     for (int end = maxl; end > 0; end -= BS) {
         const int start = max(0, end - BS);
+        const int cnt = end - start;
         __syncthreads();
-        const int k = start + (int)threadIdx.x;
-        if (k < end) {
-            const uint32_t g = gids[rg.x + k];
+        if ((int)threadIdx.x < cnt) {
+            const uint32_t g = gids[rg.x + start + threadIdx.x];
+            const float4 m = xy[g];
+            const float4 co = conic_opac[g];
             s_gid[threadIdx.x] = g;
-            s_xy[threadIdx.x] = xy[g];
-            s_co[threadIdx.x] = conic_opac[g];
+            s_xy[threadIdx.x] = m;
+            s_co[threadIdx.x] = co;
             s_rgb[threadIdx.x] = rgb[g];
+            s_box[threadIdx.x] = alpha_support_box(m, co, st.alpha_min);
         }
         __syncthreads();
-        for (int j = end - 1; j >= start; --j) {
-            const int jj = j - start;
-            bool valid = inside && (uint32_t)j < last;
-            float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f;
-            float v8 = 0.f, v9 = 0.f, v10 = 0.f, v11 = 0.f, v12 = 0.f;
+        const int nl = build_warp_list(s_box, cnt, (float)bx, (float)by, s_list[warp]);
+        for (int k = nl - 1; k >= 0; --k) {
+            const int e = s_list[warp][k];
+            bool valid = inside && (uint32_t)(start + e) < last;
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = 0.0f;
             if (valid) {
-                const float4 m = s_xy[jj];
-                const float4 co = s_co[jj];
+                const float4 m = s_xy[e];
+                const float4 co = s_co[e];
                 const float dx = (fpx - m.x) - m.z;
                 const float dy = (fpy - m.y) - m.w;
                 const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
@@ -185,7 +284,7 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
                 if (alpha < st.alpha_min) {
                     valid = false;
                 } else {
-                    const float4 c = s_rgb[jj];
+                    const float4 c = s_rgb[e];
                     const float one_m = 1.0f - alpha;
                     T = __fdividef(T, one_m);            // transmittance in front of this Gaussian
                     const float dLda = T * (g0 * (c.x - acc0) + g1 * (c.y - acc1) + g2 * (c.z - acc2));
@@ -193,38 +292,30 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
                     acc1 = alpha * c.y + one_m * acc1;
                     acc2 = alpha * c.z + one_m * acc2;
                     const float aT = alpha * T;
-                    v6 = g0 * aT;
-                    v7 = g1 * aT;
-                    v8 = g2 * aT;
+                    v[6] = g0 * aT;
+                    v[7] = g1 * aT;
+                    v[8] = g2 * aT;
                     if (!clamped) {
                         const float w = dLda * alpha;          // dL/dsigma * sigma
                         const float ux = co.x * dx + co.y * dy;  // u = Q (x - mu)
                         const float uy = co.y * dx + co.z * dy;
-                        v0 = w * ux;
-                        v1 = w * uy;
-                        v2 = -0.5f * w * dx * dx;
-                        v3 = -w * dx * dy;
-                        v4 = -0.5f * w * dy * dy;
-                        v5 = dLda * G;
-                        v9 = w;
-                        v10 = w * ux * ux;
-                        v11 = w * ux * uy;
-                        v12 = w * uy * uy;
+                        v[0] = w * ux;
+                        v[1] = w * uy;
+                        v[2] = -0.5f * w * dx * dx;
+                        v[3] = -w * dx * dy;
+                        v[4] = -0.5f * w * dy * dy;
+                        v[5] = dLda * G;
+                        v[9] = w;
+                        v[10] = w * ux * ux;
+                        v[11] = w * ux * uy;
+                        v[12] = w * uy * uy;
                     }
                 }
             }
             if (__any_sync(0xffffffffu, valid)) {
-                v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2); v3 = warp_sum(v3);
-                v4 = warp_sum(v4); v5 = warp_sum(v5); v6 = warp_sum(v6); v7 = warp_sum(v7);
-                v8 = warp_sum(v8); v9 = warp_sum(v9); v10 = warp_sum(v10); v11 = warp_sum(v11);
-                v12 = warp_sum(v12);
-                if (lane == 0) {
-                    float4* row = reinterpret_cast<float4*>(g2d + (size_t)s_gid[jj] * kG2dStride);
-                    atomicAdd(row, make_float4(v0, v1, v2, v3));
-                    atomicAdd(row + 1, make_float4(v4, v5, v6, v7));
-                    atomicAdd(row + 2, make_float4(v8, v9, v10, v11));
-                    atomicAdd(row + 3, make_float4(v12, 0.f, 0.f, 0.f));
-                }
+                const float tot = warp_reduce_scatter16(v);
+                if ((lane & 1) == 0 && slot < 13)
+                    atomicAdd(g2d + (size_t)s_gid[e] * kG2dStride + slot, tot);
             }
         }
     }
