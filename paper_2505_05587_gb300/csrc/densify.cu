@@ -7,6 +7,9 @@
 // Appendix "Eigendecomposition" (A = p B + q I, beta = 2 cos(arccos(det B / 2)
 // / 3 + 2 k pi / 3)), the "Compactest Splitting Strategy" variant (gradient
 // gate), Section 3 Eq. loss (L1).
+#include <algorithm>
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sgs {
@@ -59,36 +62,36 @@ __device__ Eig eig3_min(const float* s6, float scale) {
     float n2[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) n2[k] = c[k][0] * c[k][0] + c[k][1] * c[k][1] + c[k][2] * c[k][2];
-    int best = 0;
-    if (n2[1] > n2[best]) best = 1;
-    if (n2[2] > n2[best]) best = 2;
+    float bn = n2[0], bc0 = c[0][0], bc1 = c[0][1], bc2 = c[0][2];
+    if (n2[1] > bn) { bn = n2[1]; bc0 = c[1][0]; bc1 = c[1][1]; bc2 = c[1][2]; }
+    if (n2[2] > bn) { bn = n2[2]; bc0 = c[2][0]; bc1 = c[2][1]; bc2 = c[2][2]; }
     float v[3];
-    if (n2[best] > 0.0f) {
-        const float in = rsqrtf(n2[best]);
-        v[0] = c[best][0] * in; v[1] = c[best][1] * in; v[2] = c[best][2] * in;
+    if (bn > 0.0f) {
+        const float in = rsqrtf(bn);
+        v[0] = bc0 * in; v[1] = bc1 * in; v[2] = bc2 * in;
     } else {
         // repeated minimum root: any unit vector orthogonal to the largest row
         const float rn0 = r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2];
         const float rn1 = r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2];
         const float rn2 = r2[0] * r2[0] + r2[1] * r2[1] + r2[2] * r2[2];
-        const float* row = r0;
+        float row[3] = {r0[0], r0[1], r0[2]};
         float rb = rn0;
-        if (rn1 > rb) { row = r1; rb = rn1; }
-        if (rn2 > rb) { row = r2; rb = rn2; }
-        int ax = 0;
-        if (fabsf(row[1]) < fabsf(row[ax])) ax = 1;
-        if (fabsf(row[2]) < fabsf(row[ax])) ax = 2;
-        float ev[3] = {0.0f, 0.0f, 0.0f};
-        ev[ax] = 1.0f;
+        if (rn1 > rb) { row[0] = r1[0]; row[1] = r1[1]; row[2] = r1[2]; rb = rn1; }
+        if (rn2 > rb) { row[0] = r2[0]; row[1] = r2[1]; row[2] = r2[2]; rb = rn2; }
+        const float a0 = fabsf(row[0]), a1 = fabsf(row[1]), a2 = fabsf(row[2]);
+        float ev[3];
+        ev[0] = (a0 <= a1 && a0 <= a2) ? 1.0f : 0.0f;
+        ev[1] = (ev[0] == 0.0f && a1 <= a2) ? 1.0f : 0.0f;
+        ev[2] = (ev[0] == 0.0f && ev[1] == 0.0f) ? 1.0f : 0.0f;
         cross3(row, ev, v);
         const float in = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         v[0] *= in; v[1] *= in; v[2] *= in;
     }
     // canonical sign: largest-magnitude component positive (lowest index on ties)
-    int k = 0;
-    if (fabsf(v[1]) > fabsf(v[k])) k = 1;
-    if (fabsf(v[2]) > fabsf(v[k])) k = 2;
-    if (v[k] < 0.0f) { v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2]; }
+    float big = v[0];
+    if (fabsf(v[1]) > fabsf(big)) big = v[1];
+    if (fabsf(v[2]) > fabsf(big)) big = v[2];
+    if (big < 0.0f) { v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2]; }
     const float Av0 = a00 * v[0] + a01 * v[1] + a02 * v[2];
     const float Av1 = a01 * v[0] + a11 * v[1] + a12 * v[2];
     const float Av2 = a02 * v[0] + a12 * v[1] + a22 * v[2];
@@ -125,27 +128,31 @@ __device__ __forceinline__ float half_opacity_logit(float x) {
     return x > 0.0f ? -log1pf(2.0f * expf(-x)) : x - logf(expf(x) + 2.0f);
 }
 
-__global__ void __launch_bounds__(256) split_kernel(
+// Per-Gaussian fields of the output rows: mean, scales, rotation, opacity,
+// parent index.  Row i holds Gaussian i (moved to p + eps v with o/2 when
+// flagged); row N + excl[i] holds the second offspring p - eps v.
+__global__ void __launch_bounds__(256) split_fields_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
-    const float* __restrict__ logit, const float* __restrict__ sh, int n, int K3, const float* __restrict__ v,
-    const uint32_t* __restrict__ flags, const uint32_t* __restrict__ excl, float step_scale, int64_t cap,
-    float* __restrict__ o_means, float* __restrict__ o_ls, float* __restrict__ o_quats,
-    float* __restrict__ o_logit, float* __restrict__ o_sh, int32_t* __restrict__ parent) {
+    const float* __restrict__ logit, int n, const float* __restrict__ v, const uint32_t* __restrict__ flags,
+    const uint32_t* __restrict__ excl, float step_scale, int64_t cap, float* __restrict__ o_means,
+    float* __restrict__ o_ls, float* __restrict__ o_quats, float* __restrict__ o_logit,
+    int32_t* __restrict__ parent) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const bool f = flags[i] != 0u;
     const float l0 = log_scales[3 * i], l1 = log_scales[3 * i + 1], l2 = log_scales[3 * i + 2];
     const float x = logit[i];
     const float p0 = means[3 * i], p1 = means[3 * i + 1], p2 = means[3 * i + 2];
-    int64_t rows[2] = {i, f ? (int64_t)n + (int64_t)excl[i] : -1};
+    const float4 q = reinterpret_cast<const float4*>(quats)[i];
     float eps = 0.0f, lg = x;
     if (f) {
         eps = step_scale * expf(fmaxf(l0, fmaxf(l1, l2)));
         lg = half_opacity_logit(x);
     }
     const float v0 = f ? v[3 * i] : 0.0f, v1 = f ? v[3 * i + 1] : 0.0f, v2 = f ? v[3 * i + 2] : 0.0f;
+#pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const int64_t row = rows[r];
+        const int64_t row = r == 0 ? (int64_t)i : (f ? (int64_t)n + (int64_t)excl[i] : -1);
         if (row < 0 || row >= cap) continue;
         const float sg = r == 0 ? eps : -eps;
         o_means[3 * row] = p0 + sg * v0;
@@ -154,13 +161,32 @@ __global__ void __launch_bounds__(256) split_kernel(
         o_ls[3 * row] = l0;
         o_ls[3 * row + 1] = l1;
         o_ls[3 * row + 2] = l2;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) o_quats[4 * row + k] = quats[4 * i + k];
+        reinterpret_cast<float4*>(o_quats)[row] = q;
         o_logit[row] = lg;
-        const float* src = sh + (size_t)i * K3;
-        float* dst = o_sh + (size_t)row * K3;
-        for (int k = 0; k < K3; ++k) dst[k] = src[k];
         if (parent) parent[row] = i;
+    }
+}
+
+// SH rows of the output, one thread per vector unit of a row (U units of
+// VEC floats): reads and the writes of row i are coalesced, and the second
+// offspring of consecutive flagged Gaussians land in consecutive rows.
+template <int VEC>
+__global__ void __launch_bounds__(256) split_sh_kernel(const float* __restrict__ sh, int n, int U,
+                                                       const uint32_t* __restrict__ flags,
+                                                       const uint32_t* __restrict__ excl, int64_t cap,
+                                                       float* __restrict__ o_sh) {
+    using V = typename std::conditional<VEC == 4, float4, float>::type;
+    const int64_t total = (int64_t)n * U;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / U;
+        const int u = (int)(t - i * U);
+        const V val = reinterpret_cast<const V*>(sh)[t];
+        reinterpret_cast<V*>(o_sh)[t] = val;
+        if (flags[i]) {
+            const int64_t row = (int64_t)n + (int64_t)excl[i];
+            if (row < cap) reinterpret_cast<V*>(o_sh)[row * U + u] = val;
+        }
     }
 }
 
@@ -200,9 +226,19 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T,
     n_out_kernel<<<1, 1, 0, stream>>>(total, n, d_n_out);
     note_launch();
     const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;
-    split_kernel<<<nb, 256, 0, stream>>>(in.means, in.log_scales, in.quats, in.opacity_logit, in.sh, n, K3, v,
-                                         flags, excl, step_scale, capacity, out.means, out.log_scales,
-                                         out.quats, out.opacity_logit, out.sh, parent);
+    split_fields_kernel<<<nb, 256, 0, stream>>>(in.means, in.log_scales, in.quats, in.opacity_logit, n, v, flags,
+                                                excl, step_scale, capacity, out.means, out.log_scales, out.quats,
+                                                out.opacity_logit, parent);
+    note_launch();
+    const bool vec4 = K3 % 4 == 0 && (reinterpret_cast<uintptr_t>(in.sh) % 16) == 0 &&
+                      (reinterpret_cast<uintptr_t>(out.sh) % 16) == 0;
+    const int U = vec4 ? K3 / 4 : K3;
+    const int64_t units = (int64_t)n * U;
+    const int sb = (int)std::min<int64_t>((units + 255) / 256, 152 * 16);
+    if (vec4)
+        split_sh_kernel<4><<<sb, 256, 0, stream>>>(in.sh, n, U, flags, excl, capacity, out.sh);
+    else
+        split_sh_kernel<1><<<sb, 256, 0, stream>>>(in.sh, n, U, flags, excl, capacity, out.sh);
     note_launch();
     return cudaGetLastError();
 }

@@ -221,13 +221,33 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
     dY[15][0] = -kC3a * (3.0f * xx - 3.0f * yy); dY[15][1] = 6.0f * kC3a * x * y; dY[15][2] = 0.0f;
 }
 
+// Loads the 3K SH coefficients of Gaussian i (16-byte loads when 3K is a
+// multiple of 4; rows of 3K floats start 16-byte aligned then).
+template <int DEG>
+__device__ __forceinline__ void load_sh(const float* __restrict__ sh, int i, float (&c)[3 * (DEG + 1) * (DEG + 1)]) {
+    constexpr int K3 = 3 * (DEG + 1) * (DEG + 1);
+    const float* src = sh + (size_t)i * K3;
+    if constexpr (K3 % 4 == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+        for (int q = 0; q < K3 / 4; ++q) {
+            const float4 t = __ldg(s4 + q);
+            c[4 * q] = t.x; c[4 * q + 1] = t.y; c[4 * q + 2] = t.z; c[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < K3; ++q) c[q] = __ldg(src + q);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Forward projection: one thread per Gaussian.
 // ---------------------------------------------------------------------------
+template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logit,
-    const float* __restrict__ sh, int n, int sh_degree, CamDev cam, SetDev st,
+    const float* __restrict__ sh, int n, CamDev cam, SetDev st,
     float4* __restrict__ xy, float4* __restrict__ conic_opac, float4* __restrict__ rgb_out,
     float* __restrict__ depth, short4* __restrict__ rect, uint32_t* __restrict__ tiles) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -260,11 +280,13 @@ __global__ void __launch_bounds__(256) project_kernel(
     float d0 = p0 - cam.cc[0], d1 = p1 - cam.cc[1], d2 = p2 - cam.cc[2];
     float dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
     float inv_dn = 1.0f / dn;
+    constexpr int K = (DEG + 1) * (DEG + 1);
     float Y[16];
-    sh_basis(sh_degree, d0 * inv_dn, d1 * inv_dn, d2 * inv_dn, Y);
-    const int K = (sh_degree + 1) * (sh_degree + 1);
-    const float* c = sh + (size_t)i * K * 3;
+    sh_basis(DEG, d0 * inv_dn, d1 * inv_dn, d2 * inv_dn, Y);
+    float c[3 * K];
+    load_sh<DEG>(sh, i, c);
     float r = 0.5f, g = 0.5f, b = 0.5f;
+#pragma unroll
     for (int k = 0; k < K; ++k) {
         r += Y[k] * c[3 * k];
         g += Y[k] * c[3 * k + 1];
@@ -277,8 +299,11 @@ cudaError_t launch_project(const sgs_gaussians& g, const CamDev& cam, const SetD
                            const sgs_proj& out, cudaStream_t stream) {
     if (g.n == 0) return cudaSuccess;
     int blocks = (g.n + 255) / 256;
-    project_kernel<<<blocks, 256, 0, stream>>>(
-        g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, g.sh_degree, cam, st,
+    auto kern = g.sh_degree == 0 ? project_kernel<0>
+              : g.sh_degree == 1 ? project_kernel<1>
+              : g.sh_degree == 2 ? project_kernel<2> : project_kernel<3>;
+    kern<<<blocks, 256, 0, stream>>>(
+        g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, cam, st,
         reinterpret_cast<float4*>(out.xy), reinterpret_cast<float4*>(out.conic_opac),
         reinterpret_cast<float4*>(out.rgb), out.depth, reinterpret_cast<short4*>(out.rect),
         out.tiles_touched);
@@ -292,10 +317,11 @@ cudaError_t launch_project(const sgs_gaussians& g, const CamDev& cam, const SetD
 // value, Q11), dL/dopacity, dL/drgb (3), a0 = sum w, A2 = sum w u u^T (xx, xy,
 // yy) with w = dL/dalpha alpha and u = Q (x - mu).
 // ---------------------------------------------------------------------------
+template <int DEG>
 __global__ void __launch_bounds__(128) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logit,
-    const float* __restrict__ sh, int n, int sh_degree, CamDev cam, SetDev st,
+    const float* __restrict__ sh, int n, CamDev cam, SetDev st,
     const float* __restrict__ g2d, float* __restrict__ g_means, float* __restrict__ g_ls,
     float* __restrict__ g_quats, float* __restrict__ g_logit, float* __restrict__ g_sh,
     float* __restrict__ S_accum) {
@@ -345,11 +371,13 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(
         float dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
         float inv_dn = 1.0f / dn;
         float h0 = d0 * inv_dn, h1 = d1 * inv_dn, h2 = d2 * inv_dn;
+        constexpr int K = (DEG + 1) * (DEG + 1);
         float Y[16];
-        sh_basis(sh_degree, h0, h1, h2, Y);
-        const int K = (sh_degree + 1) * (sh_degree + 1);
-        const float* c = sh + (size_t)i * K * 3;
+        sh_basis(DEG, h0, h1, h2, Y);
+        float c[3 * K];
+        load_sh<DEG>(sh, i, c);
         float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
         for (int k = 0; k < K; ++k) {
             raw[0] += Y[k] * c[3 * k];
             raw[1] += Y[k] * c[3 * k + 1];
@@ -357,15 +385,31 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(
         }
         float gc[3] = {raw[0] > 0.0f ? dr : 0.0f, raw[1] > 0.0f ? dgc : 0.0f, raw[2] > 0.0f ? db : 0.0f};
         float* gs = g_sh + (size_t)i * K * 3;
-        for (int k = 0; k < K; ++k) {
-            gs[3 * k] += Y[k] * gc[0];
-            gs[3 * k + 1] += Y[k] * gc[1];
-            gs[3 * k + 2] += Y[k] * gc[2];
+        if constexpr ((3 * K) % 4 == 0) {
+            float4* g4 = reinterpret_cast<float4*>(gs);
+#pragma unroll
+            for (int q = 0; q < 3 * K / 4; ++q) {
+                float4 t = g4[q];
+                const int f = 4 * q;
+                t.x += Y[f / 3] * gc[f % 3];
+                t.y += Y[(f + 1) / 3] * gc[(f + 1) % 3];
+                t.z += Y[(f + 2) / 3] * gc[(f + 2) % 3];
+                t.w += Y[(f + 3) / 3] * gc[(f + 3) % 3];
+                g4[q] = t;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                gs[3 * k] += Y[k] * gc[0];
+                gs[3 * k + 1] += Y[k] * gc[1];
+                gs[3 * k + 2] += Y[k] * gc[2];
+            }
         }
-        if (sh_degree > 0) {
+        if constexpr (DEG > 0) {
             float dY[16][3];
-            sh_basis_grad(sh_degree, h0, h1, h2, dY);
+            sh_basis_grad(DEG, h0, h1, h2, dY);
             float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
+#pragma unroll
             for (int k = 1; k < K; ++k) {
                 float w = gc[0] * c[3 * k] + gc[1] * c[3 * k + 1] + gc[2] * c[3 * k + 2];
                 e0 += w * dY[k][0];
@@ -478,8 +522,11 @@ cudaError_t launch_project_bwd(const sgs_gaussians& g, const CamDev& cam, const 
                                cudaStream_t stream) {
     if (g.n == 0) return cudaSuccess;
     int blocks = (g.n + 127) / 128;
-    project_bwd_kernel<<<blocks, 128, 0, stream>>>(
-        g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, g.sh_degree, cam, st, g2d,
+    auto kern = g.sh_degree == 0 ? project_bwd_kernel<0>
+              : g.sh_degree == 1 ? project_bwd_kernel<1>
+              : g.sh_degree == 2 ? project_bwd_kernel<2> : project_bwd_kernel<3>;
+    kern<<<blocks, 128, 0, stream>>>(
+        g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, cam, st, g2d,
         grads.means, grads.log_scales, grads.quats, grads.opacity_logit, grads.sh, S_accum);
     note_launch();
     return cudaGetLastError();
