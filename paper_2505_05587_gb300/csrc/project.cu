@@ -240,6 +240,37 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, int i, flo
     }
 }
 
+// e = sum_k w_k grad Y_k (the gradient of the polynomials, k >= 1), without
+// materialising the 16 x 3 table of basis gradients.
+template <int DEG>
+__device__ __forceinline__ void sh_weighted_grad(float x, float y, float z, const float* w, float& e0, float& e1,
+                                                 float& e2) {
+    e0 = 0.0f; e1 = 0.0f; e2 = 0.0f;
+    if constexpr (DEG >= 1) {
+        e0 += -kC1 * w[3];
+        e1 += -kC1 * w[1];
+        e2 += kC1 * w[2];
+    }
+    if constexpr (DEG >= 2) {
+        const float xx = x * x, yy = y * y;
+        e0 += kC2a * (y * w[4] - z * w[7]) - 2.0f * kC2b * x * w[6] + 2.0f * kC2c * x * w[8];
+        e1 += kC2a * (x * w[4] - z * w[5]) - 2.0f * kC2b * y * w[6] - 2.0f * kC2c * y * w[8];
+        e2 += -kC2a * (y * w[5] + x * w[7]) + 4.0f * kC2b * z * w[6];
+        (void)xx; (void)yy;
+    }
+    if constexpr (DEG >= 3) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        e0 += -6.0f * kC3a * x * y * w[9] + kC3b * y * z * w[10] + 2.0f * kC3c * x * y * w[11] -
+              6.0f * kC3d * x * z * w[12] - kC3c * (4.0f * zz - 3.0f * xx - yy) * w[13] +
+              2.0f * kC3e * x * z * w[14] - kC3a * (3.0f * xx - 3.0f * yy) * w[15];
+        e1 += -kC3a * (3.0f * xx - 3.0f * yy) * w[9] + kC3b * x * z * w[10] -
+              kC3c * (4.0f * zz - xx - 3.0f * yy) * w[11] - 6.0f * kC3d * y * z * w[12] +
+              2.0f * kC3c * x * y * w[13] - 2.0f * kC3e * y * z * w[14] + 6.0f * kC3a * x * y * w[15];
+        e2 += kC3b * x * y * w[10] - 8.0f * kC3c * y * z * w[11] + kC3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * w[12] -
+              8.0f * kC3c * x * z * w[13] + kC3e * (xx - yy) * w[14];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Forward projection: one thread per Gaussian.
 // ---------------------------------------------------------------------------
@@ -313,219 +344,254 @@ cudaError_t launch_project(const sgs_gaussians& g, const CamDev& cam, const SetD
 
 // ---------------------------------------------------------------------------
 // Adjoint of the projection plus the lift of the splitting accumulators.
-// g2d row (16 floats, the last 3 unused): dL/dmu (2), dL/dQ (Q00, Q01 as the shared off-diagonal
-// value, Q11), dL/dopacity, dL/drgb (3), a0 = sum w, A2 = sum w u u^T (xx, xy,
-// yy) with w = dL/dalpha alpha and u = Q (x - mu).
+// g2d row (16 floats; 9 used), from the rasteriser's backward pass, with
+// w = dL/dalpha * alpha and d = x - mu per composited, unclamped pair:
+//   0..1 sum w d,  2..4 D = sum w d d^T (xx, xy, yy),  5 a0 = sum w,
+//   6..8 dL/drgb.
+// Then dL/dmu = Q sum w d, dL/dQ = -D/2 (the off-diagonal value counted once:
+// -D_xy), dL/dopacity = a0 / o, and the splitting accumulator
+// A2 = sum w u u^T = Q D Q (u = Q d), so this view adds
+// S += P^T (A2 - a0 Q) P.
+//
+// One thread per Gaussian; each warp stages its 32 Gaussians' SH rows through
+// shared memory so that the 3K-float rows are read and updated with coalesced
+// accesses.
 // ---------------------------------------------------------------------------
+constexpr int kBwdThreads = 128;
+
 template <int DEG>
-__global__ void __launch_bounds__(128) project_bwd_kernel(
+__global__ void __launch_bounds__(kBwdThreads) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logit,
     const float* __restrict__ sh, int n, CamDev cam, SetDev st,
     const float* __restrict__ g2d, float* __restrict__ g_means, float* __restrict__ g_ls,
     float* __restrict__ g_quats, float* __restrict__ g_logit, float* __restrict__ g_sh,
     float* __restrict__ S_accum) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    Stage s = integer_stage(means, log_scales, quats, i, cam, st);
-    if (s.culled) return;
-    const float* gg = g2d + (size_t)i * 16;
-    const float dmx = gg[0], dmy = gg[1], dQa = gg[2], dQb = gg[3], dQc = gg[4];
-    const float dop = gg[5], dr = gg[6], dgc = gg[7], db = gg[8];
-    const float a0 = gg[9], A2xx = gg[10], A2xy = gg[11], A2yy = gg[12];
-    const float fx = cam.fx, fy = cam.fy, tx = s.tx, ty = s.ty, tz = s.tz;
-    const float* R = cam.R;
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int K3 = 3 * K;
+    constexpr int ROW = K3 + 1;                      // padded row: conflict-free per-thread access
+    __shared__ float s_sh[kBwdThreads / 32][32 * ROW];
+    __shared__ uint32_t s_need[kBwdThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int base = blockIdx.x * kBwdThreads + warp * 32;
+    const int i = base + lane;
+    float* ws = s_sh[warp];
 
-    // conic Q = Sigma2D^-1 (float32 from the integer-stage covariance)
-    float det = s.a * s.c - s.b * s.b;
-    float inv = 1.0f / det;
-    float Qa = s.c * inv, Qb = -s.b * inv, Qc = s.a * inv;
-
-    // --- splitting matrix of this view: S += P^T (A2 - a0 Q) P ---------------
-    {
-        float K00 = A2xx - a0 * Qa, K01 = A2xy - a0 * Qb, K11 = A2yy - a0 * Qc;
-        const float* P = s.T;
-        float Sv[6];
-        int k = 0;
+    bool work = false;
+    Stage s;
+    float gg[9];
+    if (i < n) {
+        const float4* r4 = reinterpret_cast<const float4*>(g2d + (size_t)i * 16);
+        const float4 a = r4[0], b = r4[1], c = r4[2];
+        gg[0] = a.x; gg[1] = a.y; gg[2] = a.z; gg[3] = a.w;
+        gg[4] = b.x; gg[5] = b.y; gg[6] = b.z; gg[7] = b.w; gg[8] = c.x;
+        bool any = false;
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = a; b < 3; ++b) {
-                Sv[k++] = K00 * P[a] * P[b] + K01 * (P[a] * P[3 + b] + P[3 + a] * P[b]) +
-                          K11 * P[3 + a] * P[3 + b];
-            }
-        float* So = S_accum + (size_t)i * 6;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) So[j] += Sv[j];
-    }
-
-    // --- opacity -----------------------------------------------------------
-    float o = 1.0f / (1.0f + expf(-opacity_logit[i]));
-    g_logit[i] += dop * o * (1.0f - o);
-
-    // --- colour (SH) -------------------------------------------------------
-    float dp0 = 0.0f, dp1 = 0.0f, dp2 = 0.0f;
-    {
-        const float p0 = means[3 * i], p1 = means[3 * i + 1], p2 = means[3 * i + 2];
-        float d0 = p0 - cam.cc[0], d1 = p1 - cam.cc[1], d2 = p2 - cam.cc[2];
-        float dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-        float inv_dn = 1.0f / dn;
-        float h0 = d0 * inv_dn, h1 = d1 * inv_dn, h2 = d2 * inv_dn;
-        constexpr int K = (DEG + 1) * (DEG + 1);
-        float Y[16];
-        sh_basis(DEG, h0, h1, h2, Y);
-        float c[3 * K];
-        load_sh<DEG>(sh, i, c);
-        float raw[3] = {0.5f, 0.5f, 0.5f};
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            raw[0] += Y[k] * c[3 * k];
-            raw[1] += Y[k] * c[3 * k + 1];
-            raw[2] += Y[k] * c[3 * k + 2];
+        for (int q = 0; q < 9; ++q) any |= gg[q] != 0.0f;
+        if (any) {
+            s = integer_stage(means, log_scales, quats, i, cam, st);
+            work = !s.culled;
         }
-        float gc[3] = {raw[0] > 0.0f ? dr : 0.0f, raw[1] > 0.0f ? dgc : 0.0f, raw[2] > 0.0f ? db : 0.0f};
-        float* gs = g_sh + (size_t)i * K * 3;
-        if constexpr ((3 * K) % 4 == 0) {
-            float4* g4 = reinterpret_cast<float4*>(gs);
+    }
+    const uint32_t need = __ballot_sync(0xffffffffu, work);
+    if (need == 0u) return;                          // nothing in this warp touched any pixel
+    if (lane == 0) s_need[warp] = need;
+    const int rows = min(32, n - base);
+
+    // stage the SH rows of the warp's Gaussians (coalesced)
+    for (int f = lane; f < rows * K3; f += 32) {
+        const int r = f / K3;
+        ws[r * ROW + (f - r * K3)] = ((need >> r) & 1u) ? sh[(size_t)base * K3 + f] : 0.0f;
+    }
+    __syncwarp();
+
+    if (work) {
+        const float fx = cam.fx, fy = cam.fy, tx = s.tx, ty = s.ty, tz = s.tz;
+        const float* R = cam.R;
+        const float det = s.a * s.c - s.b * s.b;
+        const float inv = 1.0f / det;
+        const float Qa = s.c * inv, Qb = -s.b * inv, Qc = s.a * inv;
+        const float sx = gg[0], sy = gg[1], D00 = gg[2], D01 = gg[3], D11 = gg[4], a0 = gg[5];
+        const float dmx = Qa * sx + Qb * sy, dmy = Qb * sx + Qc * sy;
+        const float dQa = -0.5f * D00, dQb = -D01, dQc = -0.5f * D11;
+
+        // --- splitting matrix of this view: S += P^T (Q D Q - a0 Q) P -------------
+        {
+            const float m00 = Qa * D00 + Qb * D01, m01 = Qa * D01 + Qb * D11;
+            const float m10 = Qb * D00 + Qc * D01, m11 = Qb * D01 + Qc * D11;
+            const float K00 = (m00 * Qa + m01 * Qb) - a0 * Qa;
+            const float K01 = (m00 * Qb + m01 * Qc) - a0 * Qb;
+            const float K11 = (m10 * Qb + m11 * Qc) - a0 * Qc;
+            const float* P = s.T;
+            float* So = S_accum + (size_t)i * 6;
+            int k = 0;
 #pragma unroll
-            for (int q = 0; q < 3 * K / 4; ++q) {
-                float4 t = g4[q];
-                const int f = 4 * q;
-                t.x += Y[f / 3] * gc[f % 3];
-                t.y += Y[(f + 1) / 3] * gc[(f + 1) % 3];
-                t.z += Y[(f + 2) / 3] * gc[(f + 2) % 3];
-                t.w += Y[(f + 3) / 3] * gc[(f + 3) % 3];
-                g4[q] = t;
-            }
-        } else {
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = a; b < 3; ++b) {
+                    So[k++] += K00 * P[a] * P[b] + K01 * (P[a] * P[3 + b] + P[3 + a] * P[b]) +
+                               K11 * P[3 + a] * P[3 + b];
+                }
+        }
+
+        // --- opacity: dL/do = a0 / o (unclamped pairs carry alpha = o G) ----------
+        const float o = 1.0f / (1.0f + expf(-opacity_logit[i]));
+        const float dop = o > 0.0f ? a0 / o : 0.0f;
+        g_logit[i] += dop * o * (1.0f - o);
+
+        // --- colour (SH) ----------------------------------------------------------
+        float dp0 = 0.0f, dp1 = 0.0f, dp2 = 0.0f;
+        {
+            const float p0 = means[3 * i], p1 = means[3 * i + 1], p2 = means[3 * i + 2];
+            const float d0 = p0 - cam.cc[0], d1 = p1 - cam.cc[1], d2 = p2 - cam.cc[2];
+            const float inv_dn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            const float h0 = d0 * inv_dn, h1 = d1 * inv_dn, h2 = d2 * inv_dn;
+            float Y[16];
+            sh_basis(DEG, h0, h1, h2, Y);
+            float* row = ws + lane * ROW;
+            float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                gs[3 * k] += Y[k] * gc[0];
-                gs[3 * k + 1] += Y[k] * gc[1];
-                gs[3 * k + 2] += Y[k] * gc[2];
+                raw0 += Y[k] * row[3 * k];
+                raw1 += Y[k] * row[3 * k + 1];
+                raw2 += Y[k] * row[3 * k + 2];
+            }
+            const float gc0 = raw0 > 0.0f ? gg[6] : 0.0f;
+            const float gc1 = raw1 > 0.0f ? gg[7] : 0.0f;
+            const float gc2 = raw2 > 0.0f ? gg[8] : 0.0f;
+            if constexpr (DEG > 0) {
+                float wk[16];
+#pragma unroll
+                for (int k = 0; k < K; ++k) wk[k] = gc0 * row[3 * k] + gc1 * row[3 * k + 1] + gc2 * row[3 * k + 2];
+                float e0, e1, e2;
+                sh_weighted_grad<DEG>(h0, h1, h2, wk, e0, e1, e2);
+                const float pr = e0 * h0 + e1 * h1 + e2 * h2;
+                dp0 += (e0 - pr * h0) * inv_dn;
+                dp1 += (e1 - pr * h1) * inv_dn;
+                dp2 += (e2 - pr * h2) * inv_dn;
+            }
+            // the row now receives this Gaussian's SH gradient increments
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                row[3 * k] = Y[k] * gc0;
+                row[3 * k + 1] = Y[k] * gc1;
+                row[3 * k + 2] = Y[k] * gc2;
             }
         }
-        if constexpr (DEG > 0) {
-            float dY[16][3];
-            sh_basis_grad(DEG, h0, h1, h2, dY);
-            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
+
+        // --- 2-D mean ---------------------------------------------------------------
+        const float itz = 1.0f / tz, itz2 = itz * itz;
+        float dt0 = dmx * fx * itz;
+        float dt1 = dmy * fy * itz;
+        float dt2 = -(dmx * fx * tx + dmy * fy * ty) * itz2;
+
+        // --- conic -> Sigma2D: G2 = -Q GQ Q, GQ = [[dQa, dQb/2], [dQb/2, dQc]] ------
+        const float h = 0.5f * dQb;
+        const float t00 = Qa * dQa + Qb * h, t01 = Qa * h + Qb * dQc;
+        const float t10 = Qb * dQa + Qc * h, t11 = Qb * h + Qc * dQc;
+        const float G00 = -(t00 * Qa + t01 * Qb);
+        const float G01 = -(t00 * Qb + t01 * Qc);
+        const float G10 = -(t10 * Qa + t11 * Qb);
+        const float G11 = -(t10 * Qb + t11 * Qc);
+        const float Gs01 = 0.5f * (G01 + G10);
+
+        // --- Sigma2D = V V^T, V = P M (M = Rq diag(s)): dV = 2 G2 V ------------------
+        const float* V = s.V;
+        float dV[6];
 #pragma unroll
-            for (int k = 1; k < K; ++k) {
-                float w = gc[0] * c[3 * k] + gc[1] * c[3 * k + 1] + gc[2] * c[3 * k + 2];
-                e0 += w * dY[k][0];
-                e1 += w * dY[k][1];
-                e2 += w * dY[k][2];
-            }
-            float pr = e0 * h0 + e1 * h1 + e2 * h2;
-            dp0 += (e0 - pr * h0) * inv_dn;
-            dp1 += (e1 - pr * h1) * inv_dn;
-            dp2 += (e2 - pr * h2) * inv_dn;
+        for (int j = 0; j < 3; ++j) {
+            dV[j] = 2.0f * (G00 * V[j] + Gs01 * V[3 + j]);
+            dV[3 + j] = 2.0f * (Gs01 * V[j] + G11 * V[3 + j]);
         }
+        float M[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) M[3 * r + c] = s.Rq[3 * r + c] * s.s[c];
+        float dP[6];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                dP[3 * a + j] = dV[3 * a] * M[3 * j] + dV[3 * a + 1] * M[3 * j + 1] + dV[3 * a + 2] * M[3 * j + 2];
+        float dM[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dM[3 * r + c] = s.T[r] * dV[c] + s.T[3 + r] * dV[3 + c];
+
+        // --- P = J W: dJ = dP W^T ------------------------------------------------------
+        float dJ[6];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                dJ[3 * a + k] = dP[3 * a] * R[3 * k] + dP[3 * a + 1] * R[3 * k + 1] + dP[3 * a + 2] * R[3 * k + 2];
+        // J = [[fx/tz, 0, -fx ux/tz], [0, fy/tz, -fy uy/tz]], ux = clamp(tx/tz)
+        dt2 += dJ[0] * (-fx * itz2) + dJ[4] * (-fy * itz2);
+        {
+            const float dux_dtx = s.clx ? 0.0f : itz;
+            const float dux_dtz = s.clx ? 0.0f : -tx * itz2;
+            dt0 += dJ[2] * (-fx * itz) * dux_dtx;
+            dt2 += dJ[2] * ((-fx * itz) * dux_dtz + fx * s.ux * itz2);
+            const float duy_dty = s.cly ? 0.0f : itz;
+            const float duy_dtz = s.cly ? 0.0f : -ty * itz2;
+            dt1 += dJ[5] * (-fy * itz) * duy_dty;
+            dt2 += dJ[5] * ((-fy * itz) * duy_dtz + fy * s.uy * itz2);
+        }
+        // t = W p + t_w
+        dp0 += R[0] * dt0 + R[3] * dt1 + R[6] * dt2;
+        dp1 += R[1] * dt0 + R[4] * dt1 + R[7] * dt2;
+        dp2 += R[2] * dt0 + R[5] * dt1 + R[8] * dt2;
+        g_means[3 * i] += dp0;
+        g_means[3 * i + 1] += dp1;
+        g_means[3 * i + 2] += dp2;
+
+        // --- scales and rotation --------------------------------------------------------
+        float dRq[9];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float ds = dM[b] * s.Rq[b] + dM[3 + b] * s.Rq[3 + b] + dM[6 + b] * s.Rq[6 + b];
+            g_ls[3 * i + b] += ds * s.s[b];
+            dRq[b] = dM[b] * s.s[b];
+            dRq[3 + b] = dM[3 + b] * s.s[b];
+            dRq[6 + b] = dM[6 + b] * s.s[b];
+        }
+        const float inv_qn = 1.0f / s.qn;
+        const float4 q4 = reinterpret_cast<const float4*>(quats)[i];
+        const float w = q4.x * inv_qn, x = q4.y * inv_qn, y = q4.z * inv_qn, z = q4.w * inv_qn;
+        const float* d = dRq;
+        const float dw = 2.0f * (-z * d[1] + y * d[2] + z * d[3] - x * d[5] - y * d[6] + x * d[7]);
+        const float dx = 2.0f * (y * d[1] + z * d[2] + y * d[3] - 2.0f * x * d[4] - w * d[5] + z * d[6] + w * d[7] - 2.0f * x * d[8]);
+        const float dy = 2.0f * (-2.0f * y * d[0] + x * d[1] + w * d[2] + x * d[3] + z * d[5] - w * d[6] + z * d[7] - 2.0f * y * d[8]);
+        const float dz = 2.0f * (-2.0f * z * d[0] - w * d[1] + x * d[2] + w * d[3] - 2.0f * z * d[4] + y * d[5] + x * d[6] + y * d[7]);
+        const float dot = dw * w + dx * x + dy * y + dz * z;
+        float4* gq = reinterpret_cast<float4*>(g_quats) + i;
+        float4 gqv = *gq;
+        gqv.x += (dw - dot * w) * inv_qn;
+        gqv.y += (dx - dot * x) * inv_qn;
+        gqv.z += (dy - dot * y) * inv_qn;
+        gqv.w += (dz - dot * z) * inv_qn;
+        *gq = gqv;
     }
+    __syncwarp();
 
-    // --- 2-D mean ------------------------------------------------------------
-    float itz = 1.0f / tz, itz2 = itz * itz;
-    float dt0 = dmx * fx * itz;
-    float dt1 = dmy * fy * itz;
-    float dt2 = -(dmx * fx * tx + dmy * fy * ty) * itz2;
-
-    // --- conic -> Sigma2D: G2 = -Q GQ Q, GQ = [[dQa, dQb/2], [dQb/2, dQc]] ---
-    float h = 0.5f * dQb;
-    float t00 = Qa * dQa + Qb * h, t01 = Qa * h + Qb * dQc;
-    float t10 = Qb * dQa + Qc * h, t11 = Qb * h + Qc * dQc;
-    float G00 = -(t00 * Qa + t01 * Qb);
-    float G01 = -(t00 * Qb + t01 * Qc);
-    float G10 = -(t10 * Qa + t11 * Qb);
-    float G11 = -(t10 * Qb + t11 * Qc);
-    float Gs01 = 0.5f * (G01 + G10);
-
-    // --- Sigma2D = V V^T, V = P M (M = Rq diag(s)): dV = 2 G2 V ----------------
-    const float* V = s.V;
-    float dV[6];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        dV[j] = 2.0f * (G00 * V[j] + Gs01 * V[3 + j]);
-        dV[3 + j] = 2.0f * (Gs01 * V[j] + G11 * V[3 + j]);
+    // add the staged SH gradient increments (coalesced read-modify-write)
+    for (int f = lane; f < rows * K3; f += 32) {
+        const int r = f / K3;
+        if ((need >> r) & 1u) g_sh[(size_t)base * K3 + f] += ws[r * ROW + (f - r * K3)];
     }
-    float M[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) M[3 * r + c] = s.Rq[3 * r + c] * s.s[c];
-    // dP = dV M^T ; dM = P^T dV
-    float dP[6];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            dP[3 * a + j] = dV[3 * a] * M[3 * j] + dV[3 * a + 1] * M[3 * j + 1] + dV[3 * a + 2] * M[3 * j + 2];
-    float dM[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dM[3 * r + c] = s.T[r] * dV[c] + s.T[3 + r] * dV[3 + c];
-
-    // --- P = J W: dJ = dP W^T --------------------------------------------------
-    float dJ[6];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            dJ[3 * a + k] = dP[3 * a] * R[3 * k] + dP[3 * a + 1] * R[3 * k + 1] + dP[3 * a + 2] * R[3 * k + 2];
-    // J = [[fx/tz, 0, -fx ux/tz], [0, fy/tz, -fy uy/tz]], ux = clamp(tx/tz)
-    dt2 += dJ[0] * (-fx * itz2) + dJ[4] * (-fy * itz2);
-    {
-        float dux_dtx = s.clx ? 0.0f : itz;
-        float dux_dtz = s.clx ? 0.0f : -tx * itz2;
-        dt0 += dJ[2] * (-fx * itz) * dux_dtx;
-        dt2 += dJ[2] * ((-fx * itz) * dux_dtz + fx * s.ux * itz2);
-        float duy_dty = s.cly ? 0.0f : itz;
-        float duy_dtz = s.cly ? 0.0f : -ty * itz2;
-        dt1 += dJ[5] * (-fy * itz) * duy_dty;
-        dt2 += dJ[5] * ((-fy * itz) * duy_dtz + fy * s.uy * itz2);
-    }
-    // t = W p + t_w
-    dp0 += R[0] * dt0 + R[3] * dt1 + R[6] * dt2;
-    dp1 += R[1] * dt0 + R[4] * dt1 + R[7] * dt2;
-    dp2 += R[2] * dt0 + R[5] * dt1 + R[8] * dt2;
-    g_means[3 * i] += dp0;
-    g_means[3 * i + 1] += dp1;
-    g_means[3 * i + 2] += dp2;
-
-    // --- scales and rotation ---------------------------------------------------
-    float dRq[9];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        float ds = dM[b] * s.Rq[b] + dM[3 + b] * s.Rq[3 + b] + dM[6 + b] * s.Rq[6 + b];
-        g_ls[3 * i + b] += ds * s.s[b];
-        dRq[b] = dM[b] * s.s[b];
-        dRq[3 + b] = dM[3 + b] * s.s[b];
-        dRq[6 + b] = dM[6 + b] * s.s[b];
-    }
-    float inv_qn = 1.0f / s.qn;
-    float w = quats[4 * i] * inv_qn, x = quats[4 * i + 1] * inv_qn;
-    float y = quats[4 * i + 2] * inv_qn, z = quats[4 * i + 3] * inv_qn;
-    const float* d = dRq;
-    float dw = 2.0f * (-z * d[1] + y * d[2] + z * d[3] - x * d[5] - y * d[6] + x * d[7]);
-    float dx = 2.0f * (y * d[1] + z * d[2] + y * d[3] - 2.0f * x * d[4] - w * d[5] + z * d[6] + w * d[7] - 2.0f * x * d[8]);
-    float dy = 2.0f * (-2.0f * y * d[0] + x * d[1] + w * d[2] + x * d[3] + z * d[5] - w * d[6] + z * d[7] - 2.0f * y * d[8]);
-    float dz = 2.0f * (-2.0f * z * d[0] - w * d[1] + x * d[2] + w * d[3] - 2.0f * z * d[4] + y * d[5] + x * d[6] + y * d[7]);
-    float dot = dw * w + dx * x + dy * y + dz * z;
-    g_quats[4 * i] += (dw - dot * w) * inv_qn;
-    g_quats[4 * i + 1] += (dx - dot * x) * inv_qn;
-    g_quats[4 * i + 2] += (dy - dot * y) * inv_qn;
-    g_quats[4 * i + 3] += (dz - dot * z) * inv_qn;
 }
 
 cudaError_t launch_project_bwd(const sgs_gaussians& g, const CamDev& cam, const SetDev& st,
                                const float* g2d, const sgs_grads& grads, float* S_accum,
                                cudaStream_t stream) {
     if (g.n == 0) return cudaSuccess;
-    int blocks = (g.n + 127) / 128;
+    int blocks = (g.n + kBwdThreads - 1) / kBwdThreads;
     auto kern = g.sh_degree == 0 ? project_bwd_kernel<0>
               : g.sh_degree == 1 ? project_bwd_kernel<1>
               : g.sh_degree == 2 ? project_bwd_kernel<2> : project_bwd_kernel<3>;
-    kern<<<blocks, 128, 0, stream>>>(
+    kern<<<blocks, kBwdThreads, 0, stream>>>(
         g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, cam, st, g2d,
         grads.means, grads.log_scales, grads.quats, grads.opacity_logit, grads.sh, S_accum);
     note_launch();

@@ -15,12 +15,37 @@
 
 namespace sgs {
 
-// Row of the per-Gaussian 2-D accumulator buffer (16 floats; one 13-lane
-// vector of atomics per warp and Gaussian):
-//  0 dL/dmu_x   1 dL/dmu_y   2 dL/dQ00   3 dL/dQ01 (shared off-diagonal)
-//  4 dL/dQ11    5 dL/do      6..8 dL/drgb
-//  9 a0 = sum w   10..12 A2 = sum w u u^T (xx, xy, yy)   13..15 unused
+// Row of the per-Gaussian 2-D accumulator buffer (16 floats, slots 9..15
+// unused; one 9-lane vector of atomics per warp and Gaussian).  With
+// w = dL/dalpha * alpha for unclamped composited pairs (0 otherwise) and
+// d = x - mu:
+//  0..1 sum w d            (dL/dmu = Q sum w d)
+//  2..4 D = sum w d d^T    (xx, xy, yy): dL/dQ = -D/2, and the splitting
+//                          accumulator sum w u u^T = Q D Q with u = Q d
+//  5    a0 = sum w         (dL/do = a0 / o)
+//  6..8 dL/drgb = sum g alpha T
 constexpr int kG2dStride = 16;
+
+// Staged conic in base-2 exponent form: G = 2^(dx (A dx + B dy) + C dy^2)
+// with (A, B, C) = -log2(e) (Q00/2, Q01, Q11/2); w = opacity.
+__device__ __forceinline__ float4 conic_exp2(float4 co) {
+    constexpr float L2E = 1.4426950408889634f;
+    return make_float4(-0.5f * L2E * co.x, -L2E * co.y, -0.5f * L2E * co.z, co.w);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 2-D Gaussian value at offset (dx, dy) from the staged exponent form.  The
+// operations are spelled out so that the forward and backward kernels compute
+// the same bits (their skip and clamp decisions must agree).
+__device__ __forceinline__ float gauss2(float4 cp, float dx, float dy) {
+    const float t = __fmaf_rn(cp.y, dy, __fmul_rn(cp.x, dx));
+    return ex2_approx(__fmaf_rn(dx, t, __fmul_rn(__fmul_rn(cp.z, dy), dy)));
+}
 
 // Pixel of a thread: warps cover 8x4 pixel blocks of the tile (lane -> 8
 // columns x 4 rows), so that a warp can skip, as a whole, every Gaussian whose
@@ -103,7 +128,7 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
             const float4 m = xy[g];
             const float4 co = conic_opac[g];
             s_xy[threadIdx.x] = m;
-            s_co[threadIdx.x] = co;
+            s_co[threadIdx.x] = conic_exp2(co);
             s_rgb[threadIdx.x] = rgb[g];
             s_box[threadIdx.x] = alpha_support_box(m, co, st.alpha_min);
         }
@@ -113,11 +138,10 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
         for (int k = 0; k < nl && !done; ++k) {
             const int j = s_list[warp][k];
             const float4 m = s_xy[j];
-            const float4 co = s_co[j];
+            const float4 cp = s_co[j];
             const float dx = (fpx - m.x) - m.z;
             const float dy = (fpy - m.y) - m.w;
-            const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-            const float alpha = fminf(st.alpha_max, co.w * __expf(power));
+            const float alpha = fminf(st.alpha_max, __fmul_rn(cp.w, gauss2(cp, dx, dy)));
             if (alpha < st.alpha_min) continue;
             const float Tn = T * (1.0f - alpha);
             if (Tn < st.T_min) {
@@ -159,11 +183,10 @@ __global__ void __launch_bounds__(TW * TH) render_stats_kernel(
     for (uint32_t k = rg.x; k < rg.y; ++k) {
         const uint32_t g = gids[k];
         const float4 m = xy[g];
-        const float4 co = conic_opac[g];
+        const float4 cp = conic_exp2(conic_opac[g]);
         const float dx = ((float)px - m.x) - m.z;
         const float dy = ((float)py - m.y) - m.w;
-        const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-        const float alpha = fminf(st.alpha_max, co.w * __expf(power));
+        const float alpha = fminf(st.alpha_max, __fmul_rn(cp.w, gauss2(cp, dx, dy)));
         ++ev;
         if (alpha < st.alpha_min) continue;
         const float Tn = T * (1.0f - alpha);
@@ -174,36 +197,37 @@ __global__ void __launch_bounds__(TW * TH) render_stats_kernel(
     counts[py * W + px] = make_uint2(ev, comp);
 }
 
-// Reduce-scatter of 16 per-lane values across the warp in 16 shuffles
-// (halving exchanges at strides 16, 8, 4, 2, then a final pair sum).  Lane l
-// returns the warp total of slot (l >> 1) & 15.
-__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16]) {
+// Reduce-scatter of 8 per-lane values across the warp in 9 shuffles (halving
+// exchanges at strides 16, 8, 4, then pair sums at 2 and 1).  Lane l returns
+// the warp total of slot (l >> 2) & 7.
+__device__ __forceinline__ float warp_reduce_scatter8(float (&v)[8]) {
     const int lane = threadIdx.x & 31;
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const float send = b4 ? v[k] : v[k + 8];
-        const float keep = b4 ? v[k + 8] : v[k];
+    for (int k = 0; k < 4; ++k) {
+        const float send = b4 ? v[k] : v[k + 4];
+        const float keep = b4 ? v[k + 4] : v[k];
         v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float send = b3 ? v[k] : v[k + 4];
-        const float keep = b3 ? v[k + 4] : v[k];
+    for (int k = 0; k < 2; ++k) {
+        const float send = b3 ? v[k] : v[k + 2];
+        const float keep = b3 ? v[k + 2] : v[k];
         v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
     }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float send = b2 ? v[k] : v[k + 2];
-        const float keep = b2 ? v[k + 2] : v[k];
-        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
     {
-        const float send = b1 ? v[0] : v[1];
-        const float keep = b1 ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        const float send = b2 ? v[0] : v[1];
+        const float keep = b2 ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
     }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 template <int TW, int TH>
@@ -231,7 +255,8 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
     const float fpx = (float)px, fpy = (float)py;
     const int pix = py * W + px;
     const uint2 rg = ranges[tile];
-    const int slot = (lane >> 1) & 15;
+    // atomics: lanes 0,4,...,28 carry slots 0..7 of the reduce-scatter, lane 1 slot 8
+    const int slot = ((lane & 3) == 0) ? (lane >> 2) : (lane == 1 ? 8 : -1);
 
     float T = inside ? final_T[pix] : 1.0f;
     const uint32_t last = inside ? n_contrib[pix] : 0u;
@@ -259,7 +284,7 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
             const float4 co = conic_opac[g];
             s_gid[threadIdx.x] = g;
             s_xy[threadIdx.x] = m;
-            s_co[threadIdx.x] = co;
+            s_co[threadIdx.x] = conic_exp2(co);
             s_rgb[threadIdx.x] = rgb[g];
             s_box[threadIdx.x] = alpha_support_box(m, co, st.alpha_min);
         }
@@ -267,55 +292,33 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
         const int nl = build_warp_list(s_box, cnt, (float)bx, (float)by, s_list[warp]);
         for (int k = nl - 1; k >= 0; --k) {
             const int e = s_list[warp][k];
-            bool valid = inside && (uint32_t)(start + e) < last;
-            float v[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = 0.0f;
-            if (valid) {
-                const float4 m = s_xy[e];
-                const float4 co = s_co[e];
-                const float dx = (fpx - m.x) - m.z;
-                const float dy = (fpy - m.y) - m.w;
-                const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-                const float G = __expf(power);
-                const float araw = co.w * G;
-                const bool clamped = !(araw < st.alpha_max);
-                const float alpha = clamped ? st.alpha_max : araw;
-                if (alpha < st.alpha_min) {
-                    valid = false;
-                } else {
-                    const float4 c = s_rgb[e];
-                    const float one_m = 1.0f - alpha;
-                    T = __fdividef(T, one_m);            // transmittance in front of this Gaussian
-                    const float dLda = T * (g0 * (c.x - acc0) + g1 * (c.y - acc1) + g2 * (c.z - acc2));
-                    acc0 = alpha * c.x + one_m * acc0;
-                    acc1 = alpha * c.y + one_m * acc1;
-                    acc2 = alpha * c.z + one_m * acc2;
-                    const float aT = alpha * T;
-                    v[6] = g0 * aT;
-                    v[7] = g1 * aT;
-                    v[8] = g2 * aT;
-                    if (!clamped) {
-                        const float w = dLda * alpha;          // dL/dsigma * sigma
-                        const float ux = co.x * dx + co.y * dy;  // u = Q (x - mu)
-                        const float uy = co.y * dx + co.z * dy;
-                        v[0] = w * ux;
-                        v[1] = w * uy;
-                        v[2] = -0.5f * w * dx * dx;
-                        v[3] = -w * dx * dy;
-                        v[4] = -0.5f * w * dy * dy;
-                        v[5] = dLda * G;
-                        v[9] = w;
-                        v[10] = w * ux * ux;
-                        v[11] = w * ux * uy;
-                        v[12] = w * uy * uy;
-                    }
-                }
-            }
+            const float4 m = s_xy[e];
+            const float4 cp = s_co[e];
+            const float4 c = s_rgb[e];
+            const float dx = (fpx - m.x) - m.z;
+            const float dy = (fpy - m.y) - m.w;
+            const float araw = __fmul_rn(cp.w, gauss2(cp, dx, dy));
+            const bool valid = inside && (uint32_t)(start + e) < last && araw >= st.alpha_min;
+            const bool clamped = araw >= st.alpha_max;
+            // branch-free: an invalid pair has alpha 0, leaving T, the colour
+            // behind and every accumulated term unchanged
+            const float ae = valid ? (clamped ? st.alpha_max : araw) : 0.0f;
+            const float one_m = 1.0f - ae;
+            T = __fdividef(T, one_m);                 // transmittance in front of this Gaussian
+            const float dLda = T * (g0 * (c.x - acc0) + g1 * (c.y - acc1) + g2 * (c.z - acc2));
+            acc0 += ae * (c.x - acc0);
+            acc1 += ae * (c.y - acc1);
+            acc2 += ae * (c.z - acc2);
+            const float aT = ae * T;
+            const float w = (clamped ? 0.0f : ae) * dLda;   // dL/dsigma * sigma
+            const float wdx = w * dx, wdy = w * dy;
+            float v[8] = {wdx, wdy, wdx * dx, wdx * dy, wdy * dy, w, g0 * aT, g1 * aT};
+            const float v8 = g2 * aT;
             if (__any_sync(0xffffffffu, valid)) {
-                const float tot = warp_reduce_scatter16(v);
-                if ((lane & 1) == 0 && slot < 13)
-                    atomicAdd(g2d + (size_t)s_gid[e] * kG2dStride + slot, tot);
+                const float tot8 = warp_reduce_scatter8(v);
+                const float tot1 = warp_sum(v8);
+                if (slot >= 0)
+                    atomicAdd(g2d + (size_t)s_gid[e] * kG2dStride + slot, slot == 8 ? tot1 : tot8);
             }
         }
     }
