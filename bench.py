@@ -158,7 +158,7 @@ def run_gpu(args):
     def one_step(ev):
         """One fused iteration with events around each call (on the launching stream)."""
         ev[0].record(stream)
-        db.zero_()
+        db.zero_(grads=False)               # S and loss; the backward overwrites the gradients
         ev[1].record(stream)
         B.project(g, cam, st, vb.proj, stream)
         ev[2].record(stream)
@@ -169,7 +169,7 @@ def run_gpu(args):
         B.l1_loss_grad(vb.image, target, 1, vb.dL, db.loss, stream)
         ev[5].record(stream)
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, vb.dL, db.grads,
-                                    db.S, db.bwd_ws, stream)
+                                    db.S, db.bwd_ws, stream, accumulate=False)
         ev[6].record(stream)
         B.densify_split(g, db.S, 1.0, EPS_SPLIT, 1.0, None, 0.0, db.out, db.capacity, db.n_out, db.parent, db.lam,
                         db.v, db.split_ws, stream)

@@ -136,7 +136,7 @@ typedef struct sgs_bins {
     int64_t capacity;
 } sgs_bins;
 
-/* Parameter gradients, accumulated (+=) by sgs_render_bwd_with_splitting. */
+/* Parameter gradients written by sgs_render_bwd_with_splitting. */
 typedef struct sgs_grads {
     float *means;
     float *log_scales;
@@ -209,14 +209,16 @@ int sgs_render_bwd_workspace_size(int32_t n, size_t *bytes);
  * u = Q (x - mu) per composited, unclamped pair, the splitting matrix of this
  * view is S += P^T (sum w u u^T - (sum w) Q) P (the Appendix's Hessian
  * sigma (Y Y^T - P^T Q P), Y = P^T u, summed over pixels).
- * grads are accumulated (+=); S_accum [N,6] = (xx, xy, xz, yy, yz, zz) is
- * accumulated (+=), so calling once per view sums over views.
+ * grads are accumulated (+=) when accumulate_grads != 0, else overwritten
+ * (every row, zeros for Gaussians this view does not reach; no prior zeroing
+ * needed).  S_accum [N,6] = (xx, xy, xz, yy, yz, zz) is always accumulated
+ * (+=), so calling once per view (or per training step) sums over them.
  * Errors: SGS_ERR_INVALID_ARG, SGS_ERR_WORKSPACE. */
 int sgs_render_bwd_with_splitting(const sgs_gaussians *g, const sgs_proj *proj, const sgs_bins *bins,
                                   const sgs_camera *cam, const sgs_settings *st,
                                   const float *final_T, const uint32_t *n_contrib,
-                                  const float *dL_dimage, const sgs_grads *grads, float *S_accum,
-                                  void *ws, size_t ws_bytes, void *stream);
+                                  const float *dL_dimage, const sgs_grads *grads, int32_t accumulate_grads,
+                                  float *S_accum, void *ws, size_t ws_bytes, void *stream);
 
 /* Workspace bytes for sgs_densify_split with n Gaussians. */
 int sgs_densify_split_workspace_size(int32_t n, size_t *bytes);

@@ -97,7 +97,7 @@ def lib():
         L.sgs_l1_loss_grad.argtypes = [P, P, I32, I32, I32, P, P, P]
         L.sgs_render_stats.argtypes = [P, P, P, P, P, P]
         L.sgs_render_bwd_workspace_size.argtypes = [I32, C.POINTER(SZ)]
-        L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, P, P, SZ, P]
+        L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, I32, P, P, SZ, P]
         L.sgs_densify_split_workspace_size.argtypes = [I32, C.POINTER(SZ)]
         L.sgs_densify_split.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P, SZ, P]
         L.sgs_densify_split_noalloc.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P]
@@ -293,13 +293,15 @@ def render_bwd_workspace_size(n: int) -> int:
 
 
 def render_bwd_with_splitting(g: GaussianTensors, proj: ProjBuffers, bins: BinBuffers, cam, st, final_T,
-                              n_contrib, dL_dimage, grads: GaussianTensors, S_accum, ws, stream=None):
+                              n_contrib, dL_dimage, grads: GaussianTensors, S_accum, ws, stream=None,
+                              accumulate: bool = True):
     gc, pc, bc, cc, sc = g.c(), proj.c(), bins.c(), camera_c(cam), settings_c(st)
     grc = Grads(*[_p(t) for t in grads.tensors()])
     _check("sgs_render_bwd_with_splitting",
            lib().sgs_render_bwd_with_splitting(C.byref(gc), C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
                                                _p(final_T), _p(n_contrib), _p(dL_dimage), C.byref(grc),
-                                               _p(S_accum), _p(ws), ws.numel() * ws.element_size(),
+                                               1 if accumulate else 0, _p(S_accum), _p(ws),
+                                               ws.numel() * ws.element_size(),
                                                _stream(stream)))
 
 

@@ -20,7 +20,8 @@ CamDev make_cam(const sgs_camera& c, const sgs_settings& s) {
     d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
     d.width = c.width; d.height = c.height;
     d.near_z = c.near_z;
-    d.limx = d.limy = 0.0f;
+    d.limx = (s.fov_clamp * (0.5f * (float)c.width)) / c.fx;
+    d.limy = (s.fov_clamp * (0.5f * (float)c.height)) / c.fy;
     for (int k = 0; k < 3; ++k) {
         double v = -((double)c.R[k] * c.t[0] + (double)c.R[3 + k] * c.t[1] + (double)c.R[6 + k] * c.t[2]);
         d.cc[k] = (float)v;
@@ -165,7 +166,7 @@ int sgs_render_bwd_workspace_size(int32_t n, size_t* bytes) {
 int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, const sgs_bins* bins,
                                   const sgs_camera* cam, const sgs_settings* st, const float* final_T,
                                   const uint32_t* n_contrib, const float* dL_dimage, const sgs_grads* grads,
-                                  float* S_accum, void* ws, size_t ws_bytes, void* stream) {
+                                  int32_t accumulate_grads, float* S_accum, void* ws, size_t ws_bytes, void* stream) {
     if (!valid_gaussians(g) || !proj || !bins || !valid_cam(cam) || !valid_settings(st) || !final_T ||
         !n_contrib || !dL_dimage || !grads || !tiles_fit(cam, st) || !bins->ranges)
         return SGS_ERR_INVALID_ARG;
@@ -183,7 +184,7 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
     SetDev sd = make_set(*st);
     cudaError_t e = cudaMemsetAsync(g2d, 0, sizeof(float) * 16 * (size_t)g->n, s);
     if (e == cudaSuccess) e = launch_render_bwd(*proj, *bins, cd, sd, final_T, n_contrib, dL_dimage, g2d, s);
-    if (e == cudaSuccess) e = launch_project_bwd(*g, cd, sd, g2d, *grads, S_accum, s);
+    if (e == cudaSuccess) e = launch_project_bwd(*g, *proj, cd, g2d, accumulate_grads != 0, *grads, S_accum, s);
     return cuda_status(e);
 }
 

@@ -72,9 +72,8 @@ bool tile_supported(int tw, int th);
 // Launchers (host functions, enqueue on `stream`).
 cudaError_t launch_project(const sgs_gaussians& g, const CamDev& cam, const SetDev& st,
                            const sgs_proj& out, cudaStream_t stream);
-cudaError_t launch_project_bwd(const sgs_gaussians& g, const CamDev& cam, const SetDev& st,
-                               const float* g2d, const sgs_grads& grads, float* S_accum,
-                               cudaStream_t stream);
+cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const CamDev& cam, const float* g2d,
+                               bool accumulate, const sgs_grads& grads, float* S_accum, cudaStream_t stream);
 
 size_t bin_sort_ws_bytes(int n, int64_t capacity, int num_tiles);
 cudaError_t launch_bin_sort(const sgs_proj& proj, int n, const CamDev& cam, const SetDev& st,

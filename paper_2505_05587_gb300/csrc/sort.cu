@@ -326,20 +326,30 @@ static cudaError_t radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], const int32_
 // ---------------------------------------------------------------------------
 // Binning kernels
 // ---------------------------------------------------------------------------
-__global__ void depth_keys_kernel(const float* __restrict__ depth, const uint32_t* __restrict__ tiles, int n,
-                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+__global__ void visible_flags_kernel(const uint32_t* __restrict__ tiles, int n, uint32_t* __restrict__ flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    // depth > near_z > 0 for every visible Gaussian, so its bits order like the value.
-    keys[i] = tiles[i] ? __float_as_uint(depth[i]) : 0xffffffffu;
-    vals[i] = (uint32_t)i;
+    flag[i] = tiles[i] ? 1u : 0u;
+}
+
+// Compacts the visible Gaussians (in index order) into (depth bits, index)
+// pairs.  depth > near_z > 0 for every visible Gaussian, so its bits order like
+// the value.
+__global__ void depth_keys_kernel(const float* __restrict__ depth, const uint32_t* __restrict__ tiles,
+                                  const uint32_t* __restrict__ pos, int n, uint32_t* __restrict__ keys,
+                                  uint32_t* __restrict__ vals) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || tiles[i] == 0u) return;
+    const uint32_t p = pos[i];
+    keys[p] = __float_as_uint(depth[i]);
+    vals[p] = (uint32_t)i;
 }
 
 __global__ void gather_counts_kernel(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ tiles,
-                                     int n, uint32_t* __restrict__ cnt) {
+                                     const int32_t* __restrict__ d_n, int n_max, uint32_t* __restrict__ cnt) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    cnt[j] = tiles[perm[j]];
+    if (j >= n_max) return;
+    cnt[j] = j < *d_n ? tiles[perm[j]] : 0u;
 }
 
 __global__ void emit_kernel(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cnt,
@@ -390,7 +400,7 @@ static int ceil_log2(int64_t x) {
 }
 
 struct BinWs {
-    uint32_t *dkey[2], *perm[2], *cnt, *offs, *inst_tile[2], *inst_gid_tmp;
+    uint32_t *dkey[2], *perm[2], *cnt, *offs, *inst_tile[2], *inst_gid_tmp, *n_vis;
     void* scan_tmp;
     RadixBufs rb;
     size_t bytes;
@@ -410,6 +420,7 @@ static BinWs carve_bin_ws(void* base, int n, int64_t cap) {
     w.inst_tile[0] = c.take<uint32_t>(cc);
     w.inst_tile[1] = c.take<uint32_t>(cc);
     w.inst_gid_tmp = c.take<uint32_t>(cc);
+    w.n_vis = c.take<uint32_t>(1);
     w.scan_tmp = c.take<char>(scan_tmp_bytes(n));
     w.rb.hist = c.take<uint32_t>((size_t)RS_RADIX_MAX * RS_MAX_BLOCKS);
     w.rb.digit_tot = c.take<uint32_t>(RS_RADIX_MAX);
@@ -431,14 +442,19 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, int n, const CamDev& cam, cons
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaMemsetAsync(out.count, 0, sizeof(int32_t), stream);
     const int nb = (n + 255) / 256;
-    // 1. stable sort of the Gaussians by depth bits (culled ones last)
-    depth_keys_kernel<<<nb, 256, 0, stream>>>(proj.depth, proj.tiles_touched, n, w.dkey[0], w.perm[0]);
+    const int32_t* d_nvis = reinterpret_cast<const int32_t*>(w.n_vis);
+    // 1. compact the visible Gaussians, then a stable sort of them by depth bits
+    visible_flags_kernel<<<nb, 256, 0, stream>>>(proj.tiles_touched, n, w.cnt);
     note_launch();
-    e = radix_sort_pairs(w.dkey, w.perm, nullptr, n, n, 32, w.rb, stream);
+    e = launch_exclusive_scan(w.cnt, w.offs, w.n_vis, n, nullptr, w.scan_tmp, stream);
+    if (e != cudaSuccess) return e;
+    depth_keys_kernel<<<nb, 256, 0, stream>>>(proj.depth, proj.tiles_touched, w.offs, n, w.dkey[0], w.perm[0]);
+    note_launch();
+    e = radix_sort_pairs(w.dkey, w.perm, d_nvis, 0, n, 32, w.rb, stream);
     if (e != cudaSuccess) return e;
     const uint32_t* perm = w.perm[rs_passes(32) & 1];
     // 2. instance offsets in depth order, M
-    gather_counts_kernel<<<nb, 256, 0, stream>>>(perm, proj.tiles_touched, n, w.cnt);
+    gather_counts_kernel<<<nb, 256, 0, stream>>>(perm, proj.tiles_touched, d_nvis, n, w.cnt);
     note_launch();
     e = launch_exclusive_scan(w.cnt, w.offs, reinterpret_cast<uint32_t*>(out.count), n, nullptr,
                               w.scan_tmp, stream);

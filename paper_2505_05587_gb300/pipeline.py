@@ -101,9 +101,12 @@ class DensifyBuffers:
                               torch.empty(n, 3, device=dev), torch.zeros(1, device=dev, dtype=torch.int32),
                               B.workspace(B.densify_split_workspace_size(n), dev), cap)
 
-    def zero_(self):
-        for t in self.grads.tensors():
-            t.zero_()
+    def zero_(self, grads: bool = True):
+        """Resets the accumulators; the gradients need no reset when the first
+        backward call of an iteration overwrites them."""
+        if grads:
+            for t in self.grads.tensors():
+                t.zero_()
         self.S.zero_()
         self.loss.zero_()
 
@@ -113,13 +116,14 @@ def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: lis
                     grad_norm=None, eps_grad: float = 0.0, stream=None, check_capacity=True):
     """One fused fwd+bwd+splitting iteration over the views (Algorithm 1 with
     the split step taken right after accumulation)."""
-    db.zero_()
+    db.zero_(grads=False)
     V = len(views)
-    for vb, tgt in zip(views, targets):
+    for k, (vb, tgt) in enumerate(zip(views, targets)):
         project_and_sort(g, vb, stream, check_capacity)
         B.render_fwd(vb.proj, vb.bins, vb.cam, vb.st, vb.image, vb.final_T, vb.n_contrib, stream)
         B.l1_loss_grad(vb.image, tgt, V, vb.dL, db.loss, stream)
+        # the first view overwrites the gradients, later views add to them
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, vb.cam, vb.st, vb.final_T, vb.n_contrib, vb.dL,
-                                    db.grads, db.S, db.bwd_ws, stream)
+                                    db.grads, db.S, db.bwd_ws, stream, accumulate=k > 0)
     B.densify_split(g, db.S, 1.0 / T_split, eps_split, step_scale, grad_norm, eps_grad, db.out, db.capacity,
                     db.n_out, db.parent, db.lam, db.v, db.split_ws, stream)

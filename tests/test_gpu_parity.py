@@ -140,6 +140,32 @@ def test_backward_with_splitting_parity(name, mk_scene, mk_cam, st):
     assert _rel(Sg, So) < 1e-4
 
 
+def test_backward_overwrite_and_accumulate_modes():
+    """accumulate_grads = 0 overwrites every row (stale contents do not leak);
+    = 1 adds; S always adds."""
+    scene = synth.cluster_scene(3, 3000, 3)
+    cam = synth.camera_lookat((1.0, 0.5, -6.0), (0, 0, 0), 150, 101, 150.0)
+    st = synth.Settings()
+    grads_ref, S_ref, acc, _, _ = _backward_both(scene, cam, st)
+    g, vb = _render_gpu(scene, cam, st)
+    ref = oracle.render(scene, cam, st)
+    _, dL_ref = oracle.l1_loss_grad(ref["image"], synth.target_image(2, cam.height, cam.width))
+    dL = torch.as_tensor(dL_ref.astype(np.float32)).cuda().contiguous()
+    grads = g.zeros_like()
+    for t in grads.tensors():
+        t.fill_(1234.5)                      # stale contents must be overwritten
+    S = torch.zeros(scene.n, 6, device="cuda")
+    ws = B.workspace(B.render_bwd_workspace_size(scene.n))
+    B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, dL, grads, S, ws,
+                                accumulate=False)
+    B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, dL, grads, S, ws,
+                                accumulate=True)
+    torch.cuda.synchronize()
+    for f, t in zip(FIELDS, grads.tensors()):
+        assert _rel(t.cpu().numpy(), 2.0 * acc[f]) < 1e-4, f
+    assert _rel(S.cpu().numpy(), 2.0 * _upper6(acc["S"])) < 1e-4
+
+
 def test_l1_loss_grad_parity():
     rng = np.random.default_rng(0)
     img = rng.uniform(size=(37, 53, 3)).astype(np.float32)
@@ -251,7 +277,7 @@ def test_empty_and_fully_culled_scenes():
     S = torch.zeros(behind.n, 6, device="cuda")
     dL = torch.ones(64, 64, 3, device="cuda")
     B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, dL, grads, S,
-                                B.workspace(B.render_bwd_workspace_size(behind.n)))
+                                B.workspace(B.render_bwd_workspace_size(behind.n)), accumulate=False)
     torch.cuda.synchronize()
     assert float(S.abs().max()) == 0.0 and float(grads.means.abs().max()) == 0.0
 
