@@ -220,6 +220,15 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians *g, const sgs_proj *proj, 
                                   const float *dL_dimage, const sgs_grads *grads, int32_t accumulate_grads,
                                   float *S_accum, void *ws, size_t ws_bytes, void *stream);
 
+/* Adam step on one parameter array of `count` floats (the optimiser of the
+ * training loop around the path; Algorithm 1's "standard gradient descent"
+ * step): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * When grad_accum is not NULL it also adds g into it (Algorithm 1's
+ * G <- G + grad).  step >= 1. */
+int sgs_adam_step(float *param, const float *grad, float *m, float *v, int64_t count, float lr, float beta1,
+                  float beta2, float eps, int32_t step, float *grad_accum, void *stream);
+
 /* Workspace bytes for sgs_densify_split with n Gaussians. */
 int sgs_densify_split_workspace_size(int32_t n, size_t *bytes);
 

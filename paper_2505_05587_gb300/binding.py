@@ -100,6 +100,8 @@ def lib():
         L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, I32, P, P, SZ, P]
         L.sgs_densify_split_workspace_size.argtypes = [I32, C.POINTER(SZ)]
         L.sgs_densify_split.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P, SZ, P]
+        L.sgs_adam_step.argtypes = [P, P, P, P, I64, F, F, F, F, I32, P, P]
+        L.sgs_adam_step.restype = C.c_int
         L.sgs_densify_split_noalloc.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P]
         for name in ("sgs_project", "sgs_bin_sort_workspace_size", "sgs_bin_sort", "sgs_render_fwd",
                      "sgs_l1_loss_grad", "sgs_render_stats", "sgs_render_bwd_workspace_size", "sgs_render_bwd_with_splitting",
@@ -303,6 +305,13 @@ def render_bwd_with_splitting(g: GaussianTensors, proj: ProjBuffers, bins: BinBu
                                                1 if accumulate else 0, _p(S_accum), _p(ws),
                                                ws.numel() * ws.element_size(),
                                                _stream(stream)))
+
+
+def adam_step(param, grad, m, v, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, grad_accum=None,
+              stream=None):
+    """In-place Adam update of one float32 parameter tensor."""
+    _check("sgs_adam_step", lib().sgs_adam_step(_p(param), _p(grad), _p(m), _p(v), param.numel(), lr, beta1, beta2,
+                                                 eps, step, _p(grad_accum), _stream(stream)))
 
 
 def densify_split_workspace_size(n: int) -> int:

@@ -188,6 +188,16 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
     return cuda_status(e);
 }
 
+int sgs_adam_step(float* param, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
+                  float beta2, float eps, int32_t step, float* grad_accum, void* stream) {
+    if (count < 0 || step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return SGS_ERR_INVALID_ARG;
+    if (count > 0 && (!param || !grad || !m || !v)) return SGS_ERR_INVALID_ARG;
+    return cuda_status(launch_adam(param, grad, m, v, count, lr, beta1, beta2, eps, step, grad_accum,
+                                   (cudaStream_t)stream));
+}
+
 int sgs_densify_split_workspace_size(int32_t n, size_t* bytes) {
     if (n < 0 || !bytes) return SGS_ERR_INVALID_ARG;
     *bytes = densify_ws_bytes(n);

@@ -92,6 +92,9 @@ cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, cons
 cudaError_t launch_l1(const float* image, const float* target, int H, int W, int n_views,
                       float* dL, float* loss, cudaStream_t stream);
 
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, float lr, float b1, float b2,
+                        float eps, int step, float* G, cudaStream_t stream);
+
 size_t densify_ws_bytes(int n);
 cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T, float eps_split,
                            float step_scale, const float* grad_norm, float eps_grad,

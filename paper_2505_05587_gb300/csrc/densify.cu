@@ -244,6 +244,38 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T,
 }
 
 // ---------------------------------------------------------------------------
+// Adam update of one parameter array (the optimiser of the training loop
+// around the splitting path), optionally accumulating the raw gradient into
+// G (Algorithm 1's G <- G + grad).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, const float* __restrict__ g,
+                                                   float* __restrict__ m, float* __restrict__ v, int64_t count,
+                                                   float lr, float b1, float b2, float eps, float bc1, float bc2,
+                                                   float* __restrict__ G) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float gk = g[k];
+        const float mk = b1 * m[k] + (1.0f - b1) * gk;
+        const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
+        m[k] = mk;
+        v[k] = vk;
+        p[k] -= lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+        if (G) G[k] += gk;
+    }
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, float lr, float b1, float b2,
+                        float eps, int step, float* G, cudaStream_t stream) {
+    if (count == 0) return cudaSuccess;
+    const float bc1 = 1.0f - powf(b1, (float)step), bc2 = 1.0f - powf(b2, (float)step);
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    adam_kernel<<<(int)blocks, 256, 0, stream>>>(p, g, m, v, count, lr, b1, b2, eps, bc1, bc2, G);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // L1 loss: loss += sum |C - Chat| / (3 H W V); dL/dC = sign(C - Chat) / (3 H W V)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ image, const float* __restrict__ target,
