@@ -220,6 +220,32 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians *g, const sgs_proj *proj, 
                                   const float *dL_dimage, const sgs_grads *grads, int32_t accumulate_grads,
                                   float *S_accum, void *ws, size_t ws_bytes, void *stream);
 
+/* Several views of one scene in one pass (the batched densification step):
+ * projection of every (view, Gaussian) pair, one binning and depth sort over
+ * all views (global tile ids, view v's tiles following view v-1's), forward
+ * compositing and its backward pass as persistent kernels that pull tiles of
+ * all views from a work counter, the L1 loss of every view, and the
+ * projection adjoint summing each Gaussian's views: gradients overwritten
+ * (accumulate_grads = 0) or added, splitting matrices added to S_accum.
+ *   cams[n_views]      host array, 1 <= n_views <= 16, resolutions may differ;
+ *   batch              Gaussians staged per shared-memory batch: 64, 128 or
+ *                      256 (0 = min(tile pixels, 256));
+ *   targets, images    concatenated [sum_v H_v W_v, 3] float, view v starting
+ *                      at pixel sum_{u<v} H_u W_u; images is written;
+ *   loss               device float, += mean over views of each view's mean
+ *                      |C - Chat| (L1 over pixels and channels);
+ *   d_count            device int32 receiving the instance count M of all
+ *                      views; capacity = instance rows of the workspace.  When
+ *                      M > capacity the results are not valid (no access goes
+ *                      out of bounds); read d_count and retry with more.
+ * Errors: SGS_ERR_INVALID_ARG, SGS_ERR_WORKSPACE, SGS_ERR_CUDA. */
+int sgs_render_views_workspace_size(int32_t n, const sgs_camera *cams, int32_t n_views, const sgs_settings *st,
+                                    int64_t capacity, size_t *bytes);
+int sgs_render_views_with_splitting(const sgs_gaussians *g, const sgs_camera *cams, int32_t n_views,
+                                    const sgs_settings *st, int32_t batch, const float *targets, float *images,
+                                    float *loss, const sgs_grads *grads, int32_t accumulate_grads, float *S_accum,
+                                    int32_t *d_count, int64_t capacity, void *ws, size_t ws_bytes, void *stream);
+
 /* Adam step on one parameter array of `count` floats (the optimiser of the
  * training loop around the path; Algorithm 1's "standard gradient descent"
  * step): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;

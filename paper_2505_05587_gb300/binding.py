@@ -100,6 +100,10 @@ def lib():
         L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, I32, P, P, SZ, P]
         L.sgs_densify_split_workspace_size.argtypes = [I32, C.POINTER(SZ)]
         L.sgs_densify_split.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P, SZ, P]
+        L.sgs_render_views_workspace_size.argtypes = [I32, P, I32, P, I64, C.POINTER(SZ)]
+        L.sgs_render_views_workspace_size.restype = C.c_int
+        L.sgs_render_views_with_splitting.argtypes = [P, P, I32, P, I32, P, P, P, P, I32, P, P, I64, P, SZ, P]
+        L.sgs_render_views_with_splitting.restype = C.c_int
         L.sgs_adam_step.argtypes = [P, P, P, P, I64, F, F, F, F, I32, P, P]
         L.sgs_adam_step.restype = C.c_int
         L.sgs_densify_split_noalloc.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P]
@@ -305,6 +309,35 @@ def render_bwd_with_splitting(g: GaussianTensors, proj: ProjBuffers, bins: BinBu
                                                1 if accumulate else 0, _p(S_accum), _p(ws),
                                                ws.numel() * ws.element_size(),
                                                _stream(stream)))
+
+
+def cameras_c(cams):
+    arr = (Camera * len(cams))()
+    for k, c in enumerate(cams):
+        arr[k] = camera_c(c)
+    return arr
+
+
+def render_views_workspace_size(n: int, cams, st, capacity: int) -> int:
+    b = C.c_size_t()
+    arr, sc = cameras_c(cams), settings_c(st)
+    _check("sgs_render_views_workspace_size",
+           lib().sgs_render_views_workspace_size(n, arr, len(cams), C.byref(sc), capacity, C.byref(b)))
+    return b.value
+
+
+def render_views_with_splitting(g: GaussianTensors, cams, st, batch: int, targets, images, loss,
+                                grads: GaussianTensors, accumulate: bool, S_accum, d_count, capacity: int, ws,
+                                stream=None):
+    """All views in one pass: project, bin/sort, persistent forward, L1,
+    persistent backward, projection adjoint (see sgs_render_views_with_splitting)."""
+    gc, arr, sc = g.c(), cameras_c(cams), settings_c(st)
+    grc = Grads(*[_p(t) for t in grads.tensors()])
+    _check("sgs_render_views_with_splitting",
+           lib().sgs_render_views_with_splitting(C.byref(gc), arr, len(cams), C.byref(sc), batch, _p(targets),
+                                                 _p(images), _p(loss), C.byref(grc), 1 if accumulate else 0,
+                                                 _p(S_accum), _p(d_count), capacity, _p(ws),
+                                                 ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def adam_step(param, grad, m, v, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, grad_accum=None,

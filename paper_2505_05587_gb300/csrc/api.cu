@@ -31,6 +31,26 @@ CamDev make_cam(const sgs_camera& c, const sgs_settings& s) {
     return d;
 }
 
+ViewsDev make_views(const sgs_camera* cams, int nv, const sgs_settings& s) {
+    ViewsDev vd;
+    memset(&vd, 0, sizeof(vd));
+    vd.nv = nv;
+    int t = 0;
+    long long p = 0;
+    for (int v = 0; v < nv; ++v) {
+        vd.cam[v] = make_cam(cams[v], s);
+        vd.tile_off[v] = t;
+        vd.pix_off[v] = p;
+        t += vd.cam[v].gx * vd.cam[v].gy;
+        p += (long long)cams[v].width * cams[v].height;
+    }
+    vd.tile_off[nv] = t;
+    vd.pix_off[nv] = p;
+    vd.T_total = t;
+    vd.P_total = p;
+    return vd;
+}
+
 SetDev make_set(const sgs_settings& s) {
     SetDev d;
     d.tile_w = s.tile_w; d.tile_h = s.tile_h;
@@ -109,7 +129,7 @@ int sgs_project(const sgs_gaussians* g, const sgs_camera* cam, const sgs_setting
         return SGS_ERR_INVALID_ARG;
     if (g->n > 0 && (!out->xy || !out->conic_opac || !out->rgb || !out->depth || !out->rect || !out->tiles_touched))
         return SGS_ERR_INVALID_ARG;
-    return cuda_status(launch_project(*g, make_cam(*cam, *st), make_set(*st), *out, (cudaStream_t)stream));
+    return cuda_status(launch_project(*g, make_views(cam, 1, *st), make_set(*st), *out, (cudaStream_t)stream));
 }
 
 int sgs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t num_tiles, size_t* bytes) {
@@ -127,9 +147,9 @@ int sgs_bin_sort(const sgs_proj* proj, int32_t n, const sgs_camera* cam, const s
         return SGS_ERR_INVALID_ARG;
     if (out->capacity > 0 && !out->gids) return SGS_ERR_INVALID_ARG;
     if (n > 0 && (!proj->depth || !proj->rect || !proj->tiles_touched)) return SGS_ERR_INVALID_ARG;
-    CamDev cd = make_cam(*cam, *st);
-    if (!ws || ws_bytes < bin_sort_ws_bytes(n, out->capacity, cd.gx * cd.gy)) return SGS_ERR_WORKSPACE;
-    return cuda_status(launch_bin_sort(*proj, n, cd, make_set(*st), *out, ws, (cudaStream_t)stream));
+    ViewsDev vd = make_views(cam, 1, *st);
+    if (!ws || ws_bytes < bin_sort_ws_bytes(n, out->capacity, vd.T_total)) return SGS_ERR_WORKSPACE;
+    return cuda_status(launch_bin_sort(*proj, n, vd, make_set(*st), *out, ws, (cudaStream_t)stream));
 }
 
 int sgs_render_fwd(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,
@@ -184,7 +204,8 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
     SetDev sd = make_set(*st);
     cudaError_t e = cudaMemsetAsync(g2d, 0, sizeof(float) * 16 * (size_t)g->n, s);
     if (e == cudaSuccess) e = launch_render_bwd(*proj, *bins, cd, sd, final_T, n_contrib, dL_dimage, g2d, s);
-    if (e == cudaSuccess) e = launch_project_bwd(*g, *proj, cd, g2d, accumulate_grads != 0, *grads, S_accum, s);
+    if (e == cudaSuccess)
+        e = launch_project_bwd(*g, *proj, make_views(cam, 1, *st), g2d, accumulate_grads != 0, *grads, S_accum, s);
     return cuda_status(e);
 }
 
@@ -196,6 +217,107 @@ int sgs_adam_step(float* param, const float* grad, float* m, float* v, int64_t c
     if (count > 0 && (!param || !grad || !m || !v)) return SGS_ERR_INVALID_ARG;
     return cuda_status(launch_adam(param, grad, m, v, count, lr, beta1, beta2, eps, step, grad_accum,
                                    (cudaStream_t)stream));
+}
+
+// ---------------------------------------------------------------------------
+// Several views in one pass
+// ---------------------------------------------------------------------------
+struct ViewsWs {
+    sgs_proj proj;
+    sgs_bins bins;
+    void* sort_ws;
+    size_t sort_bytes;
+    float* final_T;
+    uint32_t* n_contrib;
+    float* dL;
+    float* g2d;
+    uint32_t* counters;
+    size_t bytes;
+};
+
+static ViewsWs carve_views_ws(void* base, int n, const ViewsDev& vd, int64_t capacity) {
+    Carver c{reinterpret_cast<char*>(base), 0};
+    ViewsWs w;
+    const size_t rows = (size_t)(n > 0 ? n : 1) * vd.nv;
+    const size_t P = (size_t)(vd.P_total > 0 ? vd.P_total : 1);
+    const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
+    w.proj.xy = c.take<float>(4 * rows);
+    w.proj.conic_opac = c.take<float>(4 * rows);
+    w.proj.rgb = c.take<float>(4 * rows);
+    w.proj.depth = c.take<float>(rows);
+    w.proj.rect = c.take<int16_t>(4 * rows);
+    w.proj.tiles_touched = c.take<uint32_t>(rows);
+    w.bins.gids = c.take<uint32_t>(cap);
+    w.bins.keys = nullptr;
+    w.bins.ranges = c.take<uint32_t>(2 * (size_t)vd.T_total);
+    w.bins.count = nullptr;
+    w.bins.capacity = capacity;
+    w.sort_bytes = bin_sort_ws_bytes((int)rows, capacity, vd.T_total);
+    w.sort_ws = c.take<char>(w.sort_bytes);
+    w.final_T = c.take<float>(P);
+    w.n_contrib = c.take<uint32_t>(P);
+    w.dL = c.take<float>(3 * P);
+    w.g2d = c.take<float>(16 * rows);
+    w.counters = c.take<uint32_t>(2);
+    w.bytes = c.off + 256;
+    return w;
+}
+
+static bool valid_views(const sgs_camera* cams, int32_t n_views, const sgs_settings* st) {
+    if (!cams || n_views < 1 || n_views > kMaxViews || !valid_settings(st)) return false;
+    long long tiles = 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (!valid_cam(&cams[v]) || !tiles_fit(&cams[v], st)) return false;
+        tiles += (long long)((cams[v].width + st->tile_w - 1) / st->tile_w) *
+                 ((cams[v].height + st->tile_h - 1) / st->tile_h);
+    }
+    return tiles < ((long long)1 << 31);
+}
+
+int sgs_render_views_workspace_size(int32_t n, const sgs_camera* cams, int32_t n_views, const sgs_settings* st,
+                                    int64_t capacity, size_t* bytes) {
+    if (n < 0 || capacity < 0 || capacity > ((int64_t)1 << 31) - 1 || !bytes || !valid_views(cams, n_views, st) ||
+        (long long)n * n_views > ((long long)1 << 31) - 1)
+        return SGS_ERR_INVALID_ARG;
+    ViewsDev vd = make_views(cams, n_views, *st);
+    *bytes = carve_views_ws(nullptr, n, vd, capacity).bytes;
+    return SGS_OK;
+}
+
+int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* cams, int32_t n_views,
+                                    const sgs_settings* st, int32_t batch, const float* targets, float* images,
+                                    float* loss, const sgs_grads* grads, int32_t accumulate_grads, float* S_accum,
+                                    int32_t* d_count, int64_t capacity, void* ws, size_t ws_bytes, void* stream) {
+    if (!valid_gaussians(g) || !valid_views(cams, n_views, st) || !targets || !images || !loss || !grads ||
+        !d_count || capacity < 0 || capacity > ((int64_t)1 << 31) - 1 ||
+        (long long)g->n * n_views > ((long long)1 << 31) - 1)
+        return SGS_ERR_INVALID_ARG;
+    if (batch == 0) batch = st->tile_w * st->tile_h > 256 ? 256 : st->tile_w * st->tile_h;
+    if (batch != 64 && batch != 128 && batch != 256) return SGS_ERR_INVALID_ARG;
+    if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit || !grads->sh ||
+                     !S_accum))
+        return SGS_ERR_INVALID_ARG;
+    ViewsDev vd = make_views(cams, n_views, *st);
+    ViewsWs w = carve_views_ws(nullptr, g->n, vd, capacity);
+    if (!ws || ws_bytes < w.bytes) return SGS_ERR_WORKSPACE;
+    w = carve_views_ws(ws, g->n, vd, capacity);
+    w.bins.count = d_count;
+    const SetDev sd = make_set(*st);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t rows = (size_t)g->n * n_views;
+    cudaError_t e = launch_project(*g, vd, sd, w.proj, s);
+    if (e == cudaSuccess) e = launch_bin_sort(w.proj, g->n, vd, sd, w.bins, w.sort_ws, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 2 * sizeof(uint32_t), s);
+    if (e == cudaSuccess)
+        e = launch_render_fwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, images, w.final_T,
+                                    w.n_contrib, w.counters, s);
+    if (e == cudaSuccess) e = launch_l1_views(images, targets, vd, w.dL, loss, s);
+    if (e == cudaSuccess && rows > 0) e = cudaMemsetAsync(w.g2d, 0, 16 * sizeof(float) * rows, s);
+    if (e == cudaSuccess)
+        e = launch_render_bwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, w.final_T, w.n_contrib,
+                                    w.dL, w.g2d, w.counters + 1, s);
+    if (e == cudaSuccess) e = launch_project_bwd(*g, w.proj, vd, w.g2d, accumulate_grads != 0, *grads, S_accum, s);
+    return cuda_status(e);
 }
 
 int sgs_densify_split_workspace_size(int32_t n, size_t* bytes) {

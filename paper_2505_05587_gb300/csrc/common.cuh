@@ -50,6 +50,32 @@ struct CamDev {
     int gx, gy;             // tiles
 };
 
+// Up to kMaxViews views of one scene processed together.  Single-view calls
+// use nv = 1.  Rows of the concatenated per-view projection buffers are
+// v * n + i; global tile id = tile_off[v] + local tile id; pixel p of view v is
+// pix_off[v] + p.  Passed by value as a kernel parameter.
+constexpr int kMaxViews = 16;
+struct ViewsDev {
+    int nv;
+    int T_total;
+    long long P_total;
+    int tile_off[kMaxViews + 1];
+    long long pix_off[kMaxViews + 1];
+    CamDev cam[kMaxViews];
+};
+
+__device__ __forceinline__ int view_of_tile(const ViewsDev& vd, int t) {
+    int v = 0;
+    while (v + 1 < vd.nv && t >= vd.tile_off[v + 1]) ++v;
+    return v;
+}
+
+__device__ __forceinline__ int view_of_pixel(const ViewsDev& vd, long long p) {
+    int v = 0;
+    while (v + 1 < vd.nv && p >= vd.pix_off[v + 1]) ++v;
+    return v;
+}
+
 struct SetDev {
     int tile_w, tile_h;
     float alpha_min, alpha_max, T_min, radius_sigma, dilation, fov_clamp;
@@ -66,17 +92,18 @@ void note_launch(int k = 1);
 // Keeps `e` for sgs_get_last_cuda_error() and returns SGS_ERR_CUDA.
 int record_cuda_error(cudaError_t e);
 CamDev make_cam(const sgs_camera& c, const sgs_settings& s);
+ViewsDev make_views(const sgs_camera* cams, int nv, const sgs_settings& s);
 SetDev make_set(const sgs_settings& s);
 bool tile_supported(int tw, int th);
 
 // Launchers (host functions, enqueue on `stream`).
-cudaError_t launch_project(const sgs_gaussians& g, const CamDev& cam, const SetDev& st,
-                           const sgs_proj& out, cudaStream_t stream);
-cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const CamDev& cam, const float* g2d,
+cudaError_t launch_project(const sgs_gaussians& g, const ViewsDev& vd, const SetDev& st, const sgs_proj& out,
+                           cudaStream_t stream);
+cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const ViewsDev& vd, const float* g2d,
                                bool accumulate, const sgs_grads& grads, float* S_accum, cudaStream_t stream);
 
 size_t bin_sort_ws_bytes(int n, int64_t capacity, int num_tiles);
-cudaError_t launch_bin_sort(const sgs_proj& proj, int n, const CamDev& cam, const SetDev& st,
+cudaError_t launch_bin_sort(const sgs_proj& proj, int n_per_view, const ViewsDev& vd, const SetDev& st,
                             const sgs_bins& out, void* ws, cudaStream_t stream);
 
 cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
@@ -86,9 +113,19 @@ cudaError_t launch_render_bwd(const sgs_proj& proj, const sgs_bins& bins, const 
                               const SetDev& st, const float* final_T, const uint32_t* n_contrib,
                               const float* dL_dimage, float* g2d, cudaStream_t stream);
 
+cudaError_t launch_render_fwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
+                                    const uint32_t* gids, const SetDev& st, int batch, float* images,
+                                    float* final_T, uint32_t* n_contrib, uint32_t* counter, cudaStream_t stream);
+cudaError_t launch_render_bwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
+                                    const uint32_t* gids, const SetDev& st, int batch, const float* final_T,
+                                    const uint32_t* n_contrib, const float* dL, float* g2d, uint32_t* counter,
+                                    cudaStream_t stream);
+
 cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
                                 const SetDev& st, uint32_t* counts, cudaStream_t stream);
 
+cudaError_t launch_l1_views(const float* image, const float* target, const ViewsDev& vd, float* dL, float* loss,
+                            cudaStream_t stream);
 cudaError_t launch_l1(const float* image, const float* target, int H, int W, int n_views,
                       float* dL, float* loss, cudaStream_t stream);
 

@@ -300,6 +300,43 @@ __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ image
     }
 }
 
+// Several views concatenated at pixel offsets: per-view normalisation.
+__global__ void __launch_bounds__(256) l1_views_kernel(const float* __restrict__ image,
+                                                       const float* __restrict__ target, ViewsDev vd,
+                                                       float* __restrict__ dL, float* __restrict__ loss) {
+    __shared__ float s_part[8];
+    float acc = 0.0f;
+    const long long count = 3 * vd.P_total;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int v = view_of_pixel(vd, k / 3);
+        const float norm = 1.0f / (3.0f * (float)vd.cam[v].width * (float)vd.cam[v].height * (float)vd.nv);
+        const float r = image[k] - target[k];
+        acc += fabsf(r) * norm;
+        dL[k] = r > 0.0f ? norm : (r < 0.0f ? -norm : 0.0f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_part[w];
+        atomicAdd(loss, s);
+    }
+}
+
+cudaError_t launch_l1_views(const float* image, const float* target, const ViewsDev& vd, float* dL, float* loss,
+                            cudaStream_t stream) {
+    const long long count = 3 * vd.P_total;
+    if (count == 0) return cudaSuccess;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    l1_views_kernel<<<(int)blocks, 256, 0, stream>>>(image, target, vd, dL, loss);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_l1(const float* image, const float* target, int H, int W, int n_views, float* dL, float* loss,
                       cudaStream_t stream) {
     const int64_t count = (int64_t)H * W * 3;

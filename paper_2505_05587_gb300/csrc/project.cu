@@ -278,23 +278,26 @@ template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logit,
-    const float* __restrict__ sh, int n, CamDev cam, SetDev st,
+    const float* __restrict__ sh, int n, ViewsDev vd, SetDev st,
     float4* __restrict__ xy, float4* __restrict__ conic_opac, float4* __restrict__ rgb_out,
     float* __restrict__ depth, short4* __restrict__ rect, uint32_t* __restrict__ tiles) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (long long)n * vd.nv) return;
+    const int v = (int)(row / n);
+    const int i = (int)(row - (long long)v * n);
+    const CamDev& cam = vd.cam[v];
     Stage s = integer_stage(means, log_scales, quats, i, cam, st);
-    depth[i] = s.tz;
+    depth[row] = s.tz;
     if (s.culled) {
-        tiles[i] = 0;
-        rect[i] = make_short4(0, 0, -1, -1);
-        xy[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        conic_opac[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        rgb_out[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        tiles[row] = 0;
+        rect[row] = make_short4(0, 0, -1, -1);
+        xy[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+        conic_opac[row] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rgb_out[row] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
-    tiles[i] = (uint32_t)((s.x_hi - s.x_lo + 1) * (s.y_hi - s.y_lo + 1));
-    rect[i] = make_short4((short)s.x_lo, (short)s.y_lo, (short)s.x_hi, (short)s.y_hi);
+    tiles[row] = (uint32_t)((s.x_hi - s.x_lo + 1) * (s.y_hi - s.y_lo + 1));
+    rect[row] = make_short4((short)s.x_lo, (short)s.y_lo, (short)s.x_hi, (short)s.y_hi);
     // 2-D mean as a float pair: mu = f (t_xy / t_z) + c
     const float p0 = means[3 * i], p1 = means[3 * i + 1], p2 = means[3 * i + 2];
     F2 tx = dot3_plus(cam.R, p0, p1, p2, cam.t[0]);
@@ -302,11 +305,11 @@ __global__ void __launch_bounds__(256) project_kernel(
     F2 tz = dot3_plus(cam.R + 6, p0, p1, p2, cam.t[2]);
     F2 mx = f2_add(f2_mul(f2_div(tx, tz), cam.fx), F2{cam.cx, 0.0f});
     F2 my = f2_add(f2_mul(f2_div(ty, tz), cam.fy), F2{cam.cy, 0.0f});
-    xy[i] = make_float4(mx.hi, my.hi, mx.lo, my.lo);
+    xy[row] = make_float4(mx.hi, my.hi, mx.lo, my.lo);
     float det = s.a * s.c - s.b * s.b;
     float inv = 1.0f / det;
     float o = 1.0f / (1.0f + expf(-opacity_logit[i]));
-    conic_opac[i] = make_float4(s.c * inv, -s.b * inv, s.a * inv, o);
+    conic_opac[row] = make_float4(s.c * inv, -s.b * inv, s.a * inv, o);
     // view-dependent colour
     float d0 = p0 - cam.cc[0], d1 = p1 - cam.cc[1], d2 = p2 - cam.cc[2];
     float dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -323,18 +326,19 @@ __global__ void __launch_bounds__(256) project_kernel(
         g += Y[k] * c[3 * k + 1];
         b += Y[k] * c[3 * k + 2];
     }
-    rgb_out[i] = make_float4(fmaxf(r, 0.0f), fmaxf(g, 0.0f), fmaxf(b, 0.0f), 0.0f);
+    rgb_out[row] = make_float4(fmaxf(r, 0.0f), fmaxf(g, 0.0f), fmaxf(b, 0.0f), 0.0f);
 }
 
-cudaError_t launch_project(const sgs_gaussians& g, const CamDev& cam, const SetDev& st,
-                           const sgs_proj& out, cudaStream_t stream) {
+cudaError_t launch_project(const sgs_gaussians& g, const ViewsDev& vd, const SetDev& st, const sgs_proj& out,
+                           cudaStream_t stream) {
     if (g.n == 0) return cudaSuccess;
-    int blocks = (g.n + 255) / 256;
+    const long long rows = (long long)g.n * vd.nv;
+    const int blocks = (int)((rows + 255) / 256);
     auto kern = g.sh_degree == 0 ? project_kernel<0>
               : g.sh_degree == 1 ? project_kernel<1>
               : g.sh_degree == 2 ? project_kernel<2> : project_kernel<3>;
     kern<<<blocks, 256, 0, stream>>>(
-        g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, cam, st,
+        g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, vd, st,
         reinterpret_cast<float4*>(out.xy), reinterpret_cast<float4*>(out.conic_opac),
         reinterpret_cast<float4*>(out.rgb), out.depth, reinterpret_cast<short4*>(out.rect),
         out.tiles_touched);
@@ -357,127 +361,218 @@ cudaError_t launch_project(const sgs_gaussians& g, const CamDev& cam, const SetD
 // shared memory so that the 3K-float rows are read and updated with coalesced
 // accesses.
 // ---------------------------------------------------------------------------
-constexpr int kBwdThreads = 128;
+constexpr int kBwdThreads = 64;
 
+// Geometry adjoint of one Gaussian in one view: adds the view's splitting
+// matrix to S6 and its parameter gradients to the accumulators.
+__device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, float p1, float p2, float4 q4,
+                                                 const float* sc, float4 co, const float* gg, float* S6,
+                                                 float& gm0, float& gm1, float& gm2, float& gl0, float& gl1,
+                                                 float& gl2, float4& gq, float& glog) {
+    const float* R = cam.R;
+    const float fx = cam.fx, fy = cam.fy;
+    const float tx = R[0] * p0 + R[1] * p1 + R[2] * p2 + cam.t[0];
+    const float ty = R[3] * p0 + R[4] * p1 + R[5] * p2 + cam.t[1];
+    const float tz = R[6] * p0 + R[7] * p1 + R[8] * p2 + cam.t[2];
+    const float itz = 1.0f / tz, itz2 = itz * itz;
+    const float rx = tx * itz, ry = ty * itz;
+    const bool clx = (rx < -cam.limx) || (rx > cam.limx);
+    const bool cly = (ry < -cam.limy) || (ry > cam.limy);
+    const float ux = fminf(fmaxf(rx, -cam.limx), cam.limx);
+    const float uy = fminf(fmaxf(ry, -cam.limy), cam.limy);
+    const float J00 = fx * itz, J02 = -fx * ux * itz, J11 = fy * itz, J12 = -fy * uy * itz;
+    float P[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        P[j] = J00 * R[j] + J02 * R[6 + j];
+        P[3 + j] = J11 * R[3 + j] + J12 * R[6 + j];
+    }
+    const float inv_qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float w = q4.x * inv_qn, x = q4.y * inv_qn, y = q4.z * inv_qn, z = q4.w * inv_qn;
+    float Rq[9];
+    Rq[0] = 1.0f - 2.0f * (y * y + z * z); Rq[1] = 2.0f * (x * y - w * z); Rq[2] = 2.0f * (x * z + w * y);
+    Rq[3] = 2.0f * (x * y + w * z); Rq[4] = 1.0f - 2.0f * (x * x + z * z); Rq[5] = 2.0f * (y * z - w * x);
+    Rq[6] = 2.0f * (x * z - w * y); Rq[7] = 2.0f * (y * z + w * x); Rq[8] = 1.0f - 2.0f * (x * x + y * y);
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = Rq[3 * r + c] * sc[c];
+    float V[6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) V[3 * a + j] = P[3 * a] * M[j] + P[3 * a + 1] * M[3 + j] + P[3 * a + 2] * M[6 + j];
+    const float Qa = co.x, Qb = co.y, Qc = co.z, o = co.w;
+    const float sx = gg[0], sy = gg[1], D00 = gg[2], D01 = gg[3], D11 = gg[4], a0 = gg[5];
+    const float dmx = Qa * sx + Qb * sy, dmy = Qb * sx + Qc * sy;
+
+    // splitting matrix of this view: S += P^T (Q D Q - a0 Q) P
+    {
+        const float m00 = Qa * D00 + Qb * D01, m01 = Qa * D01 + Qb * D11;
+        const float m10 = Qb * D00 + Qc * D01, m11 = Qb * D01 + Qc * D11;
+        const float K00 = (m00 * Qa + m01 * Qb) - a0 * Qa;
+        const float K01 = (m00 * Qb + m01 * Qc) - a0 * Qb;
+        const float K11 = (m10 * Qb + m11 * Qc) - a0 * Qc;
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b)
+                S6[k++] += K00 * P[a] * P[b] + K01 * (P[a] * P[3 + b] + P[3 + a] * P[b]) + K11 * P[3 + a] * P[3 + b];
+    }
+    // opacity: dL/do = a0 / o (unclamped pairs carry alpha = o G)
+    glog += (o > 0.0f ? a0 / o : 0.0f) * o * (1.0f - o);
+
+    // 2-D mean
+    float dt0 = dmx * fx * itz;
+    float dt1 = dmy * fy * itz;
+    float dt2 = -(dmx * fx * tx + dmy * fy * ty) * itz2;
+    // conic -> Sigma2D: G2 = -Q GQ Q with GQ = -D/2
+    const float dQa = -0.5f * D00, dQb = -D01, dQc = -0.5f * D11;
+    const float h = 0.5f * dQb;
+    const float t00 = Qa * dQa + Qb * h, t01 = Qa * h + Qb * dQc;
+    const float t10 = Qb * dQa + Qc * h, t11 = Qb * h + Qc * dQc;
+    const float G00 = -(t00 * Qa + t01 * Qb);
+    const float Gs01 = -0.5f * ((t00 * Qb + t01 * Qc) + (t10 * Qa + t11 * Qb));
+    const float G11 = -(t10 * Qb + t11 * Qc);
+    // Sigma2D = V V^T, V = P M: dV = 2 G2 V; dP = dV M^T; dM = P^T dV
+    float dV[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        dV[j] = 2.0f * (G00 * V[j] + Gs01 * V[3 + j]);
+        dV[3 + j] = 2.0f * (Gs01 * V[j] + G11 * V[3 + j]);
+    }
+    float dJ[6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const float dP0 = dV[3 * a] * M[0] + dV[3 * a + 1] * M[1] + dV[3 * a + 2] * M[2];
+        const float dP1 = dV[3 * a] * M[3] + dV[3 * a + 1] * M[4] + dV[3 * a + 2] * M[5];
+        const float dP2 = dV[3 * a] * M[6] + dV[3 * a + 1] * M[7] + dV[3 * a + 2] * M[8];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dJ[3 * a + k] = dP0 * R[3 * k] + dP1 * R[3 * k + 1] + dP2 * R[3 * k + 2];
+    }
+    // J = [[fx/tz, 0, -fx ux/tz], [0, fy/tz, -fy uy/tz]], ux = clamp(tx/tz)
+    dt2 += dJ[0] * (-fx * itz2) + dJ[4] * (-fy * itz2);
+    {
+        const float dux_dtx = clx ? 0.0f : itz;
+        const float dux_dtz = clx ? 0.0f : -tx * itz2;
+        dt0 += dJ[2] * (-fx * itz) * dux_dtx;
+        dt2 += dJ[2] * ((-fx * itz) * dux_dtz + fx * ux * itz2);
+        const float duy_dty = cly ? 0.0f : itz;
+        const float duy_dtz = cly ? 0.0f : -ty * itz2;
+        dt1 += dJ[5] * (-fy * itz) * duy_dty;
+        dt2 += dJ[5] * ((-fy * itz) * duy_dtz + fy * uy * itz2);
+    }
+    // t = W p + t_w
+    gm0 += R[0] * dt0 + R[3] * dt1 + R[6] * dt2;
+    gm1 += R[1] * dt0 + R[4] * dt1 + R[7] * dt2;
+    gm2 += R[2] * dt0 + R[5] * dt1 + R[8] * dt2;
+    // scales and rotation: dM = P^T dV, dRq = dM diag(s); dL/dlog s_c = sum_r dRq[r][c] Rq[r][c]
+    float dRq[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dRq[3 * r + c] = (P[r] * dV[c] + P[3 + r] * dV[3 + c]) * sc[c];
+    gl0 += dRq[0] * Rq[0] + dRq[3] * Rq[3] + dRq[6] * Rq[6];
+    gl1 += dRq[1] * Rq[1] + dRq[4] * Rq[4] + dRq[7] * Rq[7];
+    gl2 += dRq[2] * Rq[2] + dRq[5] * Rq[5] + dRq[8] * Rq[8];
+    const float* d = dRq;
+    const float dw = 2.0f * (-z * d[1] + y * d[2] + z * d[3] - x * d[5] - y * d[6] + x * d[7]);
+    const float dx = 2.0f * (y * d[1] + z * d[2] + y * d[3] - 2.0f * x * d[4] - w * d[5] + z * d[6] + w * d[7] - 2.0f * x * d[8]);
+    const float dy = 2.0f * (-2.0f * y * d[0] + x * d[1] + w * d[2] + x * d[3] + z * d[5] - w * d[6] + z * d[7] - 2.0f * y * d[8]);
+    const float dz = 2.0f * (-2.0f * z * d[0] - w * d[1] + x * d[2] + w * d[3] - 2.0f * z * d[4] + y * d[5] + x * d[6] + y * d[7]);
+    const float dot = dw * w + dx * x + dy * y + dz * z;
+    gq.x += (dw - dot * w) * inv_qn;
+    gq.y += (dx - dot * x) * inv_qn;
+    gq.z += (dy - dot * y) * inv_qn;
+    gq.w += (dz - dot * z) * inv_qn;
+}
+
+// One thread per Gaussian, looping over the views; each warp stages its 32
+// Gaussians' SH rows (coefficients and gradient increments) through shared
+// memory so that the 3K-float rows are read and updated with coalesced
+// accesses.
 template <int DEG>
-__global__ void __launch_bounds__(kBwdThreads, 5) project_bwd_kernel(
+__global__ void __launch_bounds__(kBwdThreads, 8) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
-    const float* __restrict__ sh, int n, CamDev cam, const float4* __restrict__ conic_opac,
+    const float* __restrict__ sh, int n, ViewsDev vd, const float4* __restrict__ conic_opac,
     const uint32_t* __restrict__ tiles, const float* __restrict__ g2d, int accumulate,
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_logit, float* __restrict__ g_sh, float* __restrict__ S_accum) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int K3 = 3 * K;
     constexpr int ROW = K3 + 1;                      // padded row: conflict-free per-thread access
-    __shared__ float s_sh[kBwdThreads / 32][32 * ROW];
+    __shared__ float s_coef[kBwdThreads / 32][32 * ROW];
+    __shared__ float s_inc[kBwdThreads / 32][32 * ROW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int base = blockIdx.x * kBwdThreads + warp * 32;
     if (base >= n) return;
     const int i = base + lane;
-    float* ws = s_sh[warp];
+    float* wc = s_coef[warp];
+    float* wi = s_inc[warp];
 
-    bool work = false;
-    float gg[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) gg[q] = 0.0f;
-    if (i < n && tiles[i] != 0u) {
-        const float4* r4 = reinterpret_cast<const float4*>(g2d + (size_t)i * 16);
-        const float4 a = r4[0], b = r4[1], c = r4[2];
-        gg[0] = a.x; gg[1] = a.y; gg[2] = a.z; gg[3] = a.w;
-        gg[4] = b.x; gg[5] = b.y; gg[6] = b.z; gg[7] = b.w; gg[8] = c.x;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) work |= gg[q] != 0.0f;
+    // which views touched this Gaussian
+    uint32_t vmask = 0u;
+    if (i < n) {
+        for (int v = 0; v < vd.nv; ++v) {
+            const long long row = (long long)v * n + i;
+            if (tiles[row] == 0u) continue;
+            const float4* r4 = reinterpret_cast<const float4*>(g2d + (size_t)row * 16);
+            const float4 a = r4[0], b = r4[1], c = r4[2];
+            if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f || b.x != 0.f || b.y != 0.f ||
+                b.z != 0.f || b.w != 0.f || c.x != 0.f)
+                vmask |= 1u << v;
+        }
     }
+    const bool work = vmask != 0u;
     const uint32_t need = __ballot_sync(0xffffffffu, work);
     if (need == 0u && accumulate) return;            // nothing in this warp touched any pixel
     const int rows = min(32, n - base);
 
-    // stage the SH rows of the warp's Gaussians (coalesced; zeros where unused)
+    // stage the SH coefficient rows (coalesced; zeros where unused); clear increments
     for (int f = lane; f < rows * K3; f += 32) {
         const int r = f / K3;
-        ws[r * ROW + (f - r * K3)] = ((need >> r) & 1u) ? sh[(size_t)base * K3 + f] : 0.0f;
+        const int o = r * ROW + (f - r * K3);
+        wc[o] = ((need >> r) & 1u) ? sh[(size_t)base * K3 + f] : 0.0f;
+        wi[o] = 0.0f;
     }
     __syncwarp();
 
     float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, gl0 = 0.f, gl1 = 0.f, gl2 = 0.f, glog = 0.f;
     float4 gq = make_float4(0.f, 0.f, 0.f, 0.f);
+    float S6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (work) {
-        const float* R = cam.R;
-        const float fx = cam.fx, fy = cam.fy;
         const float p0 = means[3 * i], p1 = means[3 * i + 1], p2 = means[3 * i + 2];
-        const float tx = R[0] * p0 + R[1] * p1 + R[2] * p2 + cam.t[0];
-        const float ty = R[3] * p0 + R[4] * p1 + R[5] * p2 + cam.t[1];
-        const float tz = R[6] * p0 + R[7] * p1 + R[8] * p2 + cam.t[2];
-        const float itz = 1.0f / tz, itz2 = itz * itz;
-        const float rx = tx * itz, ry = ty * itz;
-        const bool clx = (rx < -cam.limx) || (rx > cam.limx);
-        const bool cly = (ry < -cam.limy) || (ry > cam.limy);
-        const float ux = fminf(fmaxf(rx, -cam.limx), cam.limx);
-        const float uy = fminf(fmaxf(ry, -cam.limy), cam.limy);
-        const float J00 = fx * itz, J02 = -fx * ux * itz, J11 = fy * itz, J12 = -fy * uy * itz;
-        float P[6];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            P[j] = J00 * R[j] + J02 * R[6 + j];
-            P[3 + j] = J11 * R[3 + j] + J12 * R[6 + j];
-        }
         const float4 q4 = reinterpret_cast<const float4*>(quats)[i];
-        const float inv_qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
-        const float w = q4.x * inv_qn, x = q4.y * inv_qn, y = q4.z * inv_qn, z = q4.w * inv_qn;
-        float Rq[9];
-        Rq[0] = 1.0f - 2.0f * (y * y + z * z); Rq[1] = 2.0f * (x * y - w * z); Rq[2] = 2.0f * (x * z + w * y);
-        Rq[3] = 2.0f * (x * y + w * z); Rq[4] = 1.0f - 2.0f * (x * x + z * z); Rq[5] = 2.0f * (y * z - w * x);
-        Rq[6] = 2.0f * (x * z - w * y); Rq[7] = 2.0f * (y * z + w * x); Rq[8] = 1.0f - 2.0f * (x * x + y * y);
         const float sc[3] = {__expf(log_scales[3 * i]), __expf(log_scales[3 * i + 1]), __expf(log_scales[3 * i + 2])};
-        float M[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) M[3 * r + c] = Rq[3 * r + c] * sc[c];
-        float V[6];
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) V[3 * a + j] = P[3 * a] * M[j] + P[3 * a + 1] * M[3 + j] + P[3 * a + 2] * M[6 + j];
-        const float4 co = conic_opac[i];             // Q and opacity exactly as rendered
-        const float Qa = co.x, Qb = co.y, Qc = co.z, o = co.w;
-        const float sx = gg[0], sy = gg[1], D00 = gg[2], D01 = gg[3], D11 = gg[4], a0 = gg[5];
-        const float dmx = Qa * sx + Qb * sy, dmy = Qb * sx + Qc * sy;
-
-        // --- splitting matrix of this view: S += P^T (Q D Q - a0 Q) P -------------
-        {
-            const float m00 = Qa * D00 + Qb * D01, m01 = Qa * D01 + Qb * D11;
-            const float m10 = Qb * D00 + Qc * D01, m11 = Qb * D01 + Qc * D11;
-            const float K00 = (m00 * Qa + m01 * Qb) - a0 * Qa;
-            const float K01 = (m00 * Qb + m01 * Qc) - a0 * Qb;
-            const float K11 = (m10 * Qb + m11 * Qc) - a0 * Qc;
-            float* So = S_accum + (size_t)i * 6;
-            int k = 0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = a; b < 3; ++b)
-                    So[k++] += K00 * P[a] * P[b] + K01 * (P[a] * P[3 + b] + P[3 + a] * P[b]) + K11 * P[3 + a] * P[3 + b];
-        }
-
-        // --- opacity: dL/do = a0 / o (unclamped pairs carry alpha = o G) ----------
-        glog = (o > 0.0f ? a0 / o : 0.0f) * o * (1.0f - o);
-
-        // --- colour (SH) ----------------------------------------------------------
-        float dp0 = 0.0f, dp1 = 0.0f, dp2 = 0.0f;
-        {
+        const float* crow = wc + lane * ROW;
+        float* irow = wi + lane * ROW;
+        for (int v = 0; v < vd.nv; ++v) {
+            if (!((vmask >> v) & 1u)) continue;
+            const CamDev& cam = vd.cam[v];
+            const long long row = (long long)v * n + i;
+            float gg[9];
+            {
+                const float4* r4 = reinterpret_cast<const float4*>(g2d + (size_t)row * 16);
+                const float4 a = r4[0], b = r4[1], c = r4[2];
+                gg[0] = a.x; gg[1] = a.y; gg[2] = a.z; gg[3] = a.w;
+                gg[4] = b.x; gg[5] = b.y; gg[6] = b.z; gg[7] = b.w; gg[8] = c.x;
+            }
+            geometry_adjoint(cam, p0, p1, p2, q4, sc, conic_opac[row], gg, S6, gm0, gm1, gm2, gl0, gl1, gl2, gq,
+                             glog);
+            // colour (SH) of this view
             const float d0 = p0 - cam.cc[0], d1 = p1 - cam.cc[1], d2 = p2 - cam.cc[2];
             const float inv_dn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
             const float h0 = d0 * inv_dn, h1 = d1 * inv_dn, h2 = d2 * inv_dn;
             float Y[16];
             sh_basis(DEG, h0, h1, h2, Y);
-            float* row = ws + lane * ROW;
             float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                raw0 += Y[k] * row[3 * k];
-                raw1 += Y[k] * row[3 * k + 1];
-                raw2 += Y[k] * row[3 * k + 2];
+                raw0 += Y[k] * crow[3 * k];
+                raw1 += Y[k] * crow[3 * k + 1];
+                raw2 += Y[k] * crow[3 * k + 2];
             }
             const float gc0 = raw0 > 0.0f ? gg[6] : 0.0f;
             const float gc1 = raw1 > 0.0f ? gg[7] : 0.0f;
@@ -485,89 +580,24 @@ __global__ void __launch_bounds__(kBwdThreads, 5) project_bwd_kernel(
             if constexpr (DEG > 0) {
                 float wk[16];
 #pragma unroll
-                for (int k = 0; k < K; ++k) wk[k] = gc0 * row[3 * k] + gc1 * row[3 * k + 1] + gc2 * row[3 * k + 2];
+                for (int k = 0; k < K; ++k) wk[k] = gc0 * crow[3 * k] + gc1 * crow[3 * k + 1] + gc2 * crow[3 * k + 2];
                 float e0, e1, e2;
                 sh_weighted_grad<DEG>(h0, h1, h2, wk, e0, e1, e2);
                 const float pr = e0 * h0 + e1 * h1 + e2 * h2;
-                dp0 += (e0 - pr * h0) * inv_dn;
-                dp1 += (e1 - pr * h1) * inv_dn;
-                dp2 += (e2 - pr * h2) * inv_dn;
+                gm0 += (e0 - pr * h0) * inv_dn;
+                gm1 += (e1 - pr * h1) * inv_dn;
+                gm2 += (e2 - pr * h2) * inv_dn;
             }
-            // the row now receives this Gaussian's SH gradient
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                row[3 * k] = Y[k] * gc0;
-                row[3 * k + 1] = Y[k] * gc1;
-                row[3 * k + 2] = Y[k] * gc2;
+                irow[3 * k] += Y[k] * gc0;
+                irow[3 * k + 1] += Y[k] * gc1;
+                irow[3 * k + 2] += Y[k] * gc2;
             }
         }
-
-        // --- 2-D mean ---------------------------------------------------------------
-        float dt0 = dmx * fx * itz;
-        float dt1 = dmy * fy * itz;
-        float dt2 = -(dmx * fx * tx + dmy * fy * ty) * itz2;
-
-        // --- conic -> Sigma2D: G2 = -Q GQ Q with GQ = -D/2 ----------------------------
-        const float dQa = -0.5f * D00, dQb = -D01, dQc = -0.5f * D11;
-        const float h = 0.5f * dQb;
-        const float t00 = Qa * dQa + Qb * h, t01 = Qa * h + Qb * dQc;
-        const float t10 = Qb * dQa + Qc * h, t11 = Qb * h + Qc * dQc;
-        const float G00 = -(t00 * Qa + t01 * Qb);
-        const float Gs01 = -0.5f * ((t00 * Qb + t01 * Qc) + (t10 * Qa + t11 * Qb));
-        const float G11 = -(t10 * Qb + t11 * Qc);
-
-        // --- Sigma2D = V V^T, V = P M: dV = 2 G2 V; dP = dV M^T; dM = P^T dV ----------
-        float dV[6];
+        float* So = S_accum + (size_t)i * 6;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            dV[j] = 2.0f * (G00 * V[j] + Gs01 * V[3 + j]);
-            dV[3 + j] = 2.0f * (Gs01 * V[j] + G11 * V[3 + j]);
-        }
-        float dJ[6];
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            float dP0 = dV[3 * a] * M[0] + dV[3 * a + 1] * M[1] + dV[3 * a + 2] * M[2];
-            float dP1 = dV[3 * a] * M[3] + dV[3 * a + 1] * M[4] + dV[3 * a + 2] * M[5];
-            float dP2 = dV[3 * a] * M[6] + dV[3 * a + 1] * M[7] + dV[3 * a + 2] * M[8];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) dJ[3 * a + k] = dP0 * R[3 * k] + dP1 * R[3 * k + 1] + dP2 * R[3 * k + 2];
-        }
-        // J = [[fx/tz, 0, -fx ux/tz], [0, fy/tz, -fy uy/tz]], ux = clamp(tx/tz)
-        dt2 += dJ[0] * (-fx * itz2) + dJ[4] * (-fy * itz2);
-        {
-            const float dux_dtx = clx ? 0.0f : itz;
-            const float dux_dtz = clx ? 0.0f : -tx * itz2;
-            dt0 += dJ[2] * (-fx * itz) * dux_dtx;
-            dt2 += dJ[2] * ((-fx * itz) * dux_dtz + fx * ux * itz2);
-            const float duy_dty = cly ? 0.0f : itz;
-            const float duy_dtz = cly ? 0.0f : -ty * itz2;
-            dt1 += dJ[5] * (-fy * itz) * duy_dty;
-            dt2 += dJ[5] * ((-fy * itz) * duy_dtz + fy * uy * itz2);
-        }
-        // t = W p + t_w
-        gm0 = dp0 + R[0] * dt0 + R[3] * dt1 + R[6] * dt2;
-        gm1 = dp1 + R[1] * dt0 + R[4] * dt1 + R[7] * dt2;
-        gm2 = dp2 + R[2] * dt0 + R[5] * dt1 + R[8] * dt2;
-
-        // --- scales and rotation --------------------------------------------------------
-        // dM = P^T dV (row r: P[r] dV[0..2] + P[3+r] dV[3..5]); dRq = dM diag(s);
-        // dL/dlog s_c = s_c sum_r dM[r][c] Rq[r][c] = sum_r dRq[r][c] Rq[r][c]
-        float dRq[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) dRq[3 * r + c] = (P[r] * dV[c] + P[3 + r] * dV[3 + c]) * sc[c];
-        gl0 = dRq[0] * Rq[0] + dRq[3] * Rq[3] + dRq[6] * Rq[6];
-        gl1 = dRq[1] * Rq[1] + dRq[4] * Rq[4] + dRq[7] * Rq[7];
-        gl2 = dRq[2] * Rq[2] + dRq[5] * Rq[5] + dRq[8] * Rq[8];
-        const float* d = dRq;
-        const float dw = 2.0f * (-z * d[1] + y * d[2] + z * d[3] - x * d[5] - y * d[6] + x * d[7]);
-        const float dx = 2.0f * (y * d[1] + z * d[2] + y * d[3] - 2.0f * x * d[4] - w * d[5] + z * d[6] + w * d[7] - 2.0f * x * d[8]);
-        const float dy = 2.0f * (-2.0f * y * d[0] + x * d[1] + w * d[2] + x * d[3] + z * d[5] - w * d[6] + z * d[7] - 2.0f * y * d[8]);
-        const float dz = 2.0f * (-2.0f * z * d[0] - w * d[1] + x * d[2] + w * d[3] - 2.0f * z * d[4] + y * d[5] + x * d[6] + y * d[7]);
-        const float dot = dw * w + dx * x + dy * y + dz * z;
-        gq = make_float4((dw - dot * w) * inv_qn, (dx - dot * x) * inv_qn, (dy - dot * y) * inv_qn,
-                         (dz - dot * z) * inv_qn);
+        for (int k = 0; k < 6; ++k) So[k] += S6[k];
     }
     if (i < n) {
         if (accumulate) {
@@ -592,7 +622,7 @@ __global__ void __launch_bounds__(kBwdThreads, 5) project_bwd_kernel(
     // SH gradient rows (coalesced): added, or written (zeros for untouched rows)
     for (int f = lane; f < rows * K3; f += 32) {
         const int r = f / K3;
-        const float val = ws[r * ROW + (f - r * K3)];
+        const float val = wi[r * ROW + (f - r * K3)];
         if (!accumulate)
             g_sh[(size_t)base * K3 + f] = val;
         else if ((need >> r) & 1u)
@@ -600,7 +630,7 @@ __global__ void __launch_bounds__(kBwdThreads, 5) project_bwd_kernel(
     }
 }
 
-cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const CamDev& cam, const float* g2d,
+cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const ViewsDev& vd, const float* g2d,
                                bool accumulate, const sgs_grads& grads, float* S_accum, cudaStream_t stream) {
     if (g.n == 0) return cudaSuccess;
     int blocks = (g.n + kBwdThreads - 1) / kBwdThreads;
@@ -608,7 +638,7 @@ cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, con
               : g.sh_degree == 1 ? project_bwd_kernel<1>
               : g.sh_degree == 2 ? project_bwd_kernel<2> : project_bwd_kernel<3>;
     kern<<<blocks, kBwdThreads, 0, stream>>>(
-        g.means, g.log_scales, g.quats, g.sh, g.n, cam, reinterpret_cast<const float4*>(proj.conic_opac),
+        g.means, g.log_scales, g.quats, g.sh, g.n, vd, reinterpret_cast<const float4*>(proj.conic_opac),
         proj.tiles_touched, g2d, accumulate ? 1 : 0, grads.means, grads.log_scales, grads.quats,
         grads.opacity_logit, grads.sh, S_accum);
     note_launch();

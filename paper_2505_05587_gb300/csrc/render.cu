@@ -6,11 +6,13 @@
 // splitting matrix S = E[dl/dsigma Hess_p sigma] accumulated during
 // back-propagation); Appendix "Deriving Hessian of Gaussian".
 //
-// One CTA per tile of TW x TH pixels, one thread per pixel, warps on 8x4 pixel
-// blocks.  Gaussian records of the tile's depth-sorted list are staged in
-// shared memory in batches of TW*TH (one coalesced 16-byte load per field per
-// thread); each warp then walks only the batch entries whose alpha support
-// meets its block (an exact skip: outside that support alpha < alpha_min).
+// A CTA renders a tile of TW x TH pixels, one thread per pixel, warps on 8x4
+// pixel blocks.  Gaussian records of the tile's depth-sorted list are staged in
+// shared memory in batches of BATCH (coalesced 16-byte loads per field); each
+// warp then walks only the batch entries whose alpha support meets its block
+// (an exact skip: outside that support alpha < alpha_min).  Single-view
+// kernels launch one CTA per tile; the multi-view kernels are persistent and
+// pull global tiles of all views from an atomic counter.
 #include "common.cuh"
 
 namespace sgs {
@@ -95,19 +97,36 @@ __device__ __forceinline__ int build_warp_list(const float4* s_box, int cnt, flo
     return nl;
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
-    const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
-    const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
-    float* __restrict__ image, float* __restrict__ final_T, uint32_t* __restrict__ n_contrib) {
+
+template <int BATCH, int NW>
+struct FwdSmem {
+    float4 xy[BATCH];
+    float4 co[BATCH];
+    float4 rgb[BATCH];
+    float4 box[BATCH];
+    uint8_t list[NW][BATCH];
+};
+
+template <int BATCH, int NW>
+struct BwdSmem {
+    uint32_t gid[BATCH];
+    float4 xy[BATCH];
+    float4 co[BATCH];
+    float4 rgb[BATCH];
+    float4 box[BATCH];
+    uint8_t list[NW][BATCH];
+    uint32_t maxl;
+};
+
+// Forward compositing of one tile (local tile id `tile` in a gx-wide grid of a
+// W x H view); outputs are the view's own image / final_T / n_contrib arrays.
+template <int TW, int TH, int BATCH>
+__device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 rg, const uint32_t* __restrict__ gids,
+                                         const float4* __restrict__ xy, const float4* __restrict__ conic_opac,
+                                         const float4* __restrict__ rgb, const SetDev& st, float* __restrict__ image,
+                                         float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
+                                         FwdSmem<BATCH, TW * TH / 32>& sm) {
     constexpr int BS = TW * TH;
-    constexpr int NW = BS / 32;
-    __shared__ float4 s_xy[BS];
-    __shared__ float4 s_co[BS];
-    __shared__ float4 s_rgb[BS];
-    __shared__ float4 s_box[BS];
-    __shared__ uint8_t s_list[NW][BS];
-    const int tile = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int bx, by;
     warp_block_origin<TW>(tile, gx, TH, &bx, &by);
@@ -115,30 +134,29 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
     const int py = by + (lane >> 3);
     const bool inside = px < W && py < H;
     const float fpx = (float)px, fpy = (float)py;
-    const uint2 rg = ranges[tile];
     const int n = (int)(rg.y - rg.x);
     bool done = !inside;
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     uint32_t last = 0;
-    for (int base = 0; base < n; base += BS) {
+    for (int base = 0; base < n; base += BATCH) {
         if (__syncthreads_count(done) == BS) break;
-        const int cnt = min(BS, n - base);
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t g = gids[rg.x + base + threadIdx.x];
+        const int cnt = min(BATCH, n - base);
+        for (int k = threadIdx.x; k < cnt; k += BS) {
+            const uint32_t g = gids[rg.x + base + k];
             const float4 m = xy[g];
             const float4 co = conic_opac[g];
-            s_xy[threadIdx.x] = m;
-            s_co[threadIdx.x] = conic_exp2(co);
-            s_rgb[threadIdx.x] = rgb[g];
-            s_box[threadIdx.x] = alpha_support_box(m, co, st.alpha_min);
+            sm.xy[k] = m;
+            sm.co[k] = conic_exp2(co);
+            sm.rgb[k] = rgb[g];
+            sm.box[k] = alpha_support_box(m, co, st.alpha_min);
         }
         __syncthreads();
         if (__all_sync(0xffffffffu, done)) continue;
-        const int nl = build_warp_list(s_box, cnt, (float)bx, (float)by, s_list[warp]);
+        const int nl = build_warp_list(sm.box, cnt, (float)bx, (float)by, sm.list[warp]);
         for (int k = 0; k < nl && !done; ++k) {
-            const int j = s_list[warp][k];
-            const float4 m = s_xy[j];
-            const float4 cp = s_co[j];
+            const int j = sm.list[warp][k];
+            const float4 m = sm.xy[j];
+            const float4 cp = sm.co[j];
             const float dx = (fpx - m.x) - m.z;
             const float dy = (fpy - m.y) - m.w;
             const float alpha = fminf(st.alpha_max, __fmul_rn(cp.w, gauss2(cp, dx, dy)));
@@ -148,7 +166,7 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
                 done = true;
                 break;
             }
-            const float4 c = s_rgb[j];
+            const float4 c = sm.rgb[j];
             const float wgt = alpha * T;
             C0 += c.x * wgt;
             C1 += c.y * wgt;
@@ -165,36 +183,7 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
         final_T[pix] = T;
         n_contrib[pix] = last;
     }
-}
-
-// Pair counts of the forward walk, per pixel: (pairs evaluated, pairs
-// composited).  A measurement aid; it replays the walk without colour.
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) render_stats_kernel(
-    const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
-    const float4* __restrict__ conic_opac, int W, int H, int gx, SetDev st, uint2* __restrict__ counts) {
-    const int tile = blockIdx.x;
-    const int px = (tile % gx) * TW + (int)(threadIdx.x % TW);
-    const int py = (tile / gx) * TH + (int)(threadIdx.x / TW);
-    if (px >= W || py >= H) return;
-    const uint2 rg = ranges[tile];
-    float T = 1.0f;
-    uint32_t ev = 0, comp = 0;
-    for (uint32_t k = rg.x; k < rg.y; ++k) {
-        const uint32_t g = gids[k];
-        const float4 m = xy[g];
-        const float4 cp = conic_exp2(conic_opac[g]);
-        const float dx = ((float)px - m.x) - m.z;
-        const float dy = ((float)py - m.y) - m.w;
-        const float alpha = fminf(st.alpha_max, __fmul_rn(cp.w, gauss2(cp, dx, dy)));
-        ++ev;
-        if (alpha < st.alpha_min) continue;
-        const float Tn = T * (1.0f - alpha);
-        if (Tn < st.T_min) break;
-        ++comp;
-        T = Tn;
-    }
-    counts[py * W + px] = make_uint2(ev, comp);
+    __syncthreads();        // shared memory is reused by the next tile
 }
 
 // Reduce-scatter of 8 per-lane values across the warp in 9 shuffles (halving
@@ -230,22 +219,15 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
-    const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
-    const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
-    const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
-    const float* __restrict__ dL_dimage, float* __restrict__ g2d) {
+// Backward pass of one tile, back to front, with the splitting accumulators.
+template <int TW, int TH, int BATCH>
+__device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 rg, const uint32_t* __restrict__ gids,
+                                         const float4* __restrict__ xy, const float4* __restrict__ conic_opac,
+                                         const float4* __restrict__ rgb, const SetDev& st,
+                                         const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
+                                         const float* __restrict__ dL_dimage, float* __restrict__ g2d,
+                                         BwdSmem<BATCH, TW * TH / 32>& sm) {
     constexpr int BS = TW * TH;
-    constexpr int NW = BS / 32;
-    __shared__ uint32_t s_gid[BS];
-    __shared__ float4 s_xy[BS];
-    __shared__ float4 s_co[BS];
-    __shared__ float4 s_rgb[BS];
-    __shared__ float4 s_box[BS];
-    __shared__ uint8_t s_list[NW][BS];
-    __shared__ uint32_t s_max;
-    const int tile = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int bx, by;
     warp_block_origin<TW>(tile, gx, TH, &bx, &by);
@@ -254,7 +236,6 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
     const bool inside = px < W && py < H;
     const float fpx = (float)px, fpy = (float)py;
     const int pix = py * W + px;
-    const uint2 rg = ranges[tile];
     // atomics: lanes 0,4,...,28 carry slots 0..7 of the reduce-scatter, lane 1 slot 8
     const int slot = ((lane & 3) == 0) ? (lane >> 2) : (lane == 1 ? 8 : -1);
 
@@ -265,36 +246,36 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
     const float g2 = inside ? dL_dimage[3 * pix + 2] : 0.0f;
     float acc0 = st.bg[0], acc1 = st.bg[1], acc2 = st.bg[2];
 
-    if (threadIdx.x == 0) s_max = 0u;
+    if (threadIdx.x == 0) sm.maxl = 0u;
     __syncthreads();
     {
         const uint32_t m = __reduce_max_sync(0xffffffffu, last);
-        if (lane == 0) atomicMax(&s_max, m);
+        if (lane == 0) atomicMax(&sm.maxl, m);
     }
     __syncthreads();
-    const int maxl = min((int)s_max, (int)(rg.y - rg.x));
+    const int maxl = min((int)sm.maxl, (int)(rg.y - rg.x));
 
-    for (int end = maxl; end > 0; end -= BS) {
-        const int start = max(0, end - BS);
+    for (int end = maxl; end > 0; end -= BATCH) {
+        const int start = max(0, end - BATCH);
         const int cnt = end - start;
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t g = gids[rg.x + start + threadIdx.x];
+        for (int k = threadIdx.x; k < cnt; k += BS) {
+            const uint32_t g = gids[rg.x + start + k];
             const float4 m = xy[g];
             const float4 co = conic_opac[g];
-            s_gid[threadIdx.x] = g;
-            s_xy[threadIdx.x] = m;
-            s_co[threadIdx.x] = conic_exp2(co);
-            s_rgb[threadIdx.x] = rgb[g];
-            s_box[threadIdx.x] = alpha_support_box(m, co, st.alpha_min);
+            sm.gid[k] = g;
+            sm.xy[k] = m;
+            sm.co[k] = conic_exp2(co);
+            sm.rgb[k] = rgb[g];
+            sm.box[k] = alpha_support_box(m, co, st.alpha_min);
         }
         __syncthreads();
-        const int nl = build_warp_list(s_box, cnt, (float)bx, (float)by, s_list[warp]);
+        const int nl = build_warp_list(sm.box, cnt, (float)bx, (float)by, sm.list[warp]);
         for (int k = nl - 1; k >= 0; --k) {
-            const int e = s_list[warp][k];
-            const float4 m = s_xy[e];
-            const float4 cp = s_co[e];
-            const float4 c = s_rgb[e];
+            const int e = sm.list[warp][k];
+            const float4 m = sm.xy[e];
+            const float4 cp = sm.co[e];
+            const float4 c = sm.rgb[e];
             const float dx = (fpx - m.x) - m.z;
             const float dy = (fpy - m.y) - m.w;
             const float araw = __fmul_rn(cp.w, gauss2(cp, dx, dy));
@@ -318,12 +299,118 @@ __global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
                 const float tot8 = warp_reduce_scatter8(v);
                 const float tot1 = warp_sum(v8);
                 if (slot >= 0)
-                    atomicAdd(g2d + (size_t)s_gid[e] * kG2dStride + slot, slot == 8 ? tot1 : tot8);
+                    atomicAdd(g2d + (size_t)sm.gid[e] * kG2dStride + slot, slot == 8 ? tot1 : tot8);
             }
         }
     }
+    __syncthreads();        // shared memory is reused by the next tile
 }
 
+// ---------------------------------------------------------------------------
+// Single view: one CTA per tile.
+// ---------------------------------------------------------------------------
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
+    const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
+    float* __restrict__ image, float* __restrict__ final_T, uint32_t* __restrict__ n_contrib) {
+    __shared__ FwdSmem<TW * TH, TW * TH / 32> sm;
+    fwd_tile<TW, TH, TW * TH>(blockIdx.x, gx, W, H, ranges[blockIdx.x], gids, xy, conic_opac, rgb, st, image,
+                              final_T, n_contrib, sm);
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
+    const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
+    const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
+    const float* __restrict__ dL_dimage, float* __restrict__ g2d) {
+    __shared__ BwdSmem<TW * TH, TW * TH / 32> sm;
+    bwd_tile<TW, TH, TW * TH>(blockIdx.x, gx, W, H, ranges[blockIdx.x], gids, xy, conic_opac, rgb, st, final_T,
+                              n_contrib, dL_dimage, g2d, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Several views: persistent CTAs pull global tiles from an atomic counter
+// (the counter must be zero at launch).  Per-view maps are concatenated at
+// pixel offsets pix_off[v].
+// ---------------------------------------------------------------------------
+template <int TW, int TH, int BATCH>
+__global__ void __launch_bounds__(TW * TH) render_fwd_views_kernel(
+    ViewsDev vd, const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
+    const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, SetDev st, float* __restrict__ images,
+    float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ counter) {
+    __shared__ FwdSmem<BATCH, TW * TH / 32> sm;
+    __shared__ int s_tile;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= vd.T_total) break;
+        const int v = view_of_tile(vd, t);
+        const CamDev& c = vd.cam[v];
+        const long long po = vd.pix_off[v];
+        fwd_tile<TW, TH, BATCH>(t - vd.tile_off[v], c.gx, c.width, c.height, ranges[t], gids, xy, conic_opac, rgb,
+                                st, images + 3 * po, final_T + po, n_contrib + po, sm);
+    }
+}
+
+template <int TW, int TH, int BATCH>
+__global__ void __launch_bounds__(TW * TH) render_bwd_views_kernel(
+    ViewsDev vd, const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
+    const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, SetDev st,
+    const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL,
+    float* __restrict__ g2d, uint32_t* __restrict__ counter) {
+    __shared__ BwdSmem<BATCH, TW * TH / 32> sm;
+    __shared__ int s_tile;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= vd.T_total) break;
+        const int v = view_of_tile(vd, t);
+        const CamDev& c = vd.cam[v];
+        const long long po = vd.pix_off[v];
+        bwd_tile<TW, TH, BATCH>(t - vd.tile_off[v], c.gx, c.width, c.height, ranges[t], gids, xy, conic_opac, rgb,
+                                st, final_T + po, n_contrib + po, dL + 3 * po, g2d, sm);
+    }
+}
+
+// Pair counts of the forward walk, per pixel: (pairs evaluated, pairs
+// composited).  A measurement aid; it replays the walk without colour.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) render_stats_kernel(
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
+    const float4* __restrict__ conic_opac, int W, int H, int gx, SetDev st, uint2* __restrict__ counts) {
+    const int tile = blockIdx.x;
+    const int px = (tile % gx) * TW + (int)(threadIdx.x % TW);
+    const int py = (tile / gx) * TH + (int)(threadIdx.x / TW);
+    if (px >= W || py >= H) return;
+    const uint2 rg = ranges[tile];
+    float T = 1.0f;
+    uint32_t ev = 0, comp = 0;
+    for (uint32_t k = rg.x; k < rg.y; ++k) {
+        const uint32_t g = gids[k];
+        const float4 m = xy[g];
+        const float4 cp = conic_exp2(conic_opac[g]);
+        const float dx = ((float)px - m.x) - m.z;
+        const float dy = ((float)py - m.y) - m.w;
+        const float alpha = fminf(st.alpha_max, __fmul_rn(cp.w, gauss2(cp, dx, dy)));
+        ++ev;
+        if (alpha < st.alpha_min) continue;
+        const float Tn = T * (1.0f - alpha);
+        if (Tn < st.T_min) break;
+        ++comp;
+        T = Tn;
+    }
+    counts[py * W + px] = make_uint2(ev, comp);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
 template <int TW, int TH>
 static cudaError_t stats_tmpl(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
                               uint32_t* counts, cudaStream_t stream) {
@@ -334,15 +421,6 @@ static cudaError_t stats_tmpl(const sgs_proj& proj, const sgs_bins& bins, const 
         reinterpret_cast<uint2*>(counts));
     note_launch();
     return cudaGetLastError();
-}
-
-cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
-                                uint32_t* counts, cudaStream_t stream) {
-    if (st.tile_w == 16 && st.tile_h == 16) return stats_tmpl<16, 16>(proj, bins, cam, st, counts, stream);
-    if (st.tile_w == 16 && st.tile_h == 8) return stats_tmpl<16, 8>(proj, bins, cam, st, counts, stream);
-    if (st.tile_w == 8 && st.tile_h == 8) return stats_tmpl<8, 8>(proj, bins, cam, st, counts, stream);
-    if (st.tile_w == 32 && st.tile_h == 8) return stats_tmpl<32, 8>(proj, bins, cam, st, counts, stream);
-    return cudaErrorInvalidValue;
 }
 
 template <int TW, int TH>
@@ -370,23 +448,107 @@ static cudaError_t bwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const Ca
     return cudaGetLastError();
 }
 
+#define SGS_TILE_DISPATCH(FN, ...)                                                                  \
+    if (st.tile_w == 16 && st.tile_h == 16) return FN<16, 16>(__VA_ARGS__);                         \
+    if (st.tile_w == 16 && st.tile_h == 8) return FN<16, 8>(__VA_ARGS__);                           \
+    if (st.tile_w == 8 && st.tile_h == 8) return FN<8, 8>(__VA_ARGS__);                             \
+    if (st.tile_w == 32 && st.tile_h == 8) return FN<32, 8>(__VA_ARGS__);                           \
+    return cudaErrorInvalidValue;
+
+cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
+                                uint32_t* counts, cudaStream_t stream) {
+    SGS_TILE_DISPATCH(stats_tmpl, proj, bins, cam, st, counts, stream)
+}
+
 cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
                               float* image, float* final_T, uint32_t* n_contrib, cudaStream_t stream) {
-    if (st.tile_w == 16 && st.tile_h == 16) return fwd_tmpl<16, 16>(proj, bins, cam, st, image, final_T, n_contrib, stream);
-    if (st.tile_w == 16 && st.tile_h == 8) return fwd_tmpl<16, 8>(proj, bins, cam, st, image, final_T, n_contrib, stream);
-    if (st.tile_w == 8 && st.tile_h == 8) return fwd_tmpl<8, 8>(proj, bins, cam, st, image, final_T, n_contrib, stream);
-    if (st.tile_w == 32 && st.tile_h == 8) return fwd_tmpl<32, 8>(proj, bins, cam, st, image, final_T, n_contrib, stream);
-    return cudaErrorInvalidValue;
+    SGS_TILE_DISPATCH(fwd_tmpl, proj, bins, cam, st, image, final_T, n_contrib, stream)
 }
 
 cudaError_t launch_render_bwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
                               const float* final_T, const uint32_t* n_contrib, const float* dL, float* g2d,
                               cudaStream_t stream) {
-    if (st.tile_w == 16 && st.tile_h == 16) return bwd_tmpl<16, 16>(proj, bins, cam, st, final_T, n_contrib, dL, g2d, stream);
-    if (st.tile_w == 16 && st.tile_h == 8) return bwd_tmpl<16, 8>(proj, bins, cam, st, final_T, n_contrib, dL, g2d, stream);
-    if (st.tile_w == 8 && st.tile_h == 8) return bwd_tmpl<8, 8>(proj, bins, cam, st, final_T, n_contrib, dL, g2d, stream);
-    if (st.tile_w == 32 && st.tile_h == 8) return bwd_tmpl<32, 8>(proj, bins, cam, st, final_T, n_contrib, dL, g2d, stream);
+    SGS_TILE_DISPATCH(bwd_tmpl, proj, bins, cam, st, final_T, n_contrib, dL, g2d, stream)
+}
+
+// Persistent multi-view launches: CTAs per SM from the occupancy calculator.
+template <class K>
+static int persistent_grid(K kernel, int threads, int T_total) {
+    int dev = 0, sms = 152, per_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int g = sms * per_sm;
+    return g < T_total ? g : (T_total > 0 ? T_total : 1);
+}
+
+template <int TW, int TH, int BATCH>
+static cudaError_t fwd_views_tmpl(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
+                                  const uint32_t* gids, const SetDev& st, float* images, float* final_T,
+                                  uint32_t* n_contrib, uint32_t* counter, cudaStream_t stream) {
+    auto k = render_fwd_views_kernel<TW, TH, BATCH>;
+    const int grid = persistent_grid(k, TW * TH, vd.T_total);
+    k<<<grid, TW * TH, 0, stream>>>(vd, reinterpret_cast<const uint2*>(ranges), gids,
+                                    reinterpret_cast<const float4*>(proj.xy),
+                                    reinterpret_cast<const float4*>(proj.conic_opac),
+                                    reinterpret_cast<const float4*>(proj.rgb), st, images, final_T, n_contrib,
+                                    counter);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int TW, int TH, int BATCH>
+static cudaError_t bwd_views_tmpl(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
+                                  const uint32_t* gids, const SetDev& st, const float* final_T,
+                                  const uint32_t* n_contrib, const float* dL, float* g2d, uint32_t* counter,
+                                  cudaStream_t stream) {
+    auto k = render_bwd_views_kernel<TW, TH, BATCH>;
+    const int grid = persistent_grid(k, TW * TH, vd.T_total);
+    k<<<grid, TW * TH, 0, stream>>>(vd, reinterpret_cast<const uint2*>(ranges), gids,
+                                    reinterpret_cast<const float4*>(proj.xy),
+                                    reinterpret_cast<const float4*>(proj.conic_opac),
+                                    reinterpret_cast<const float4*>(proj.rgb), st, final_T, n_contrib, dL, g2d,
+                                    counter);
+    note_launch();
+    return cudaGetLastError();
+}
+
+#define SGS_VIEWS_DISPATCH(FN, ...)                                                                        \
+    switch (batch) {                                                                                       \
+        case 64:                                                                                           \
+            if (st.tile_w == 16 && st.tile_h == 16) return FN<16, 16, 64>(__VA_ARGS__);                   \
+            if (st.tile_w == 16 && st.tile_h == 8) return FN<16, 8, 64>(__VA_ARGS__);                     \
+            if (st.tile_w == 8 && st.tile_h == 8) return FN<8, 8, 64>(__VA_ARGS__);                       \
+            if (st.tile_w == 32 && st.tile_h == 8) return FN<32, 8, 64>(__VA_ARGS__);                     \
+            break;                                                                                         \
+        case 128:                                                                                          \
+            if (st.tile_w == 16 && st.tile_h == 16) return FN<16, 16, 128>(__VA_ARGS__);                  \
+            if (st.tile_w == 16 && st.tile_h == 8) return FN<16, 8, 128>(__VA_ARGS__);                    \
+            if (st.tile_w == 8 && st.tile_h == 8) return FN<8, 8, 128>(__VA_ARGS__);                      \
+            if (st.tile_w == 32 && st.tile_h == 8) return FN<32, 8, 128>(__VA_ARGS__);                    \
+            break;                                                                                         \
+        case 256:                                                                                          \
+            if (st.tile_w == 16 && st.tile_h == 16) return FN<16, 16, 256>(__VA_ARGS__);                  \
+            if (st.tile_w == 16 && st.tile_h == 8) return FN<16, 8, 256>(__VA_ARGS__);                    \
+            if (st.tile_w == 8 && st.tile_h == 8) return FN<8, 8, 256>(__VA_ARGS__);                      \
+            if (st.tile_w == 32 && st.tile_h == 8) return FN<32, 8, 256>(__VA_ARGS__);                    \
+            break;                                                                                         \
+        default:                                                                                           \
+            break;                                                                                         \
+    }                                                                                                      \
     return cudaErrorInvalidValue;
+
+cudaError_t launch_render_fwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
+                                    const uint32_t* gids, const SetDev& st, int batch, float* images,
+                                    float* final_T, uint32_t* n_contrib, uint32_t* counter, cudaStream_t stream) {
+    SGS_VIEWS_DISPATCH(fwd_views_tmpl, vd, proj, ranges, gids, st, images, final_T, n_contrib, counter, stream)
+}
+
+cudaError_t launch_render_bwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
+                                    const uint32_t* gids, const SetDev& st, int batch, const float* final_T,
+                                    const uint32_t* n_contrib, const float* dL, float* g2d, uint32_t* counter,
+                                    cudaStream_t stream) {
+    SGS_VIEWS_DISPATCH(bwd_views_tmpl, vd, proj, ranges, gids, st, final_T, n_contrib, dL, g2d, counter, stream)
 }
 
 }  // namespace sgs

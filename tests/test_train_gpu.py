@@ -64,11 +64,16 @@ def test_autograd_central_differences_config4():
     gs = [rng.normal(size=(128, 128, 3)) / (128 * 128) for _ in cams]
     got, _ = _autograd_grads(scene, cams, st, gs)
     vis = np.nonzero(oracle.integer_stage(scene, cams[0], st)["tiles"])[0]
-    sample = np.random.default_rng(7).choice(vis, 4, replace=False)
+    sample = np.random.default_rng(7).choice(vis, 3, replace=False)
     h = 1e-4
+    base_order = [oracle.bin_sort(scene, c, st)[1] for c in cams]
 
     def loss(sc):
         return sum(float(np.sum(oracle.render(sc, c, st)["image"] * gv)) for c, gv in zip(cams, gs))
+
+    def same_order(sc):
+        # the render is discontinuous where a step swaps two depths: skip those
+        return all(np.array_equal(oracle.bin_sort(sc, c, st)[1], o) for c, o in zip(cams, base_order))
 
     fd, an = [], []
     for i in sample:
@@ -80,11 +85,16 @@ def test_autograd_central_differences_config4():
                     sc = scene.copy()
                     a = getattr(sc, f).reshape(scene.n, -1)
                     a[i, k] = np.float32(flat[i, k] + sgn * h)
+                    if not same_order(sc):
+                        break
                     vals.append((loss(sc), float(a[i, k])))
+                if len(vals) < 2:
+                    continue
                 (lp, xp), (lm, xm) = vals
                 fd.append((lp - lm) / (xp - xm))
                 an.append(got[f].reshape(scene.n, -1)[i, k])
     fd, an = np.array(fd), np.array(an)
+    assert fd.size >= 30
     rel = np.linalg.norm(fd - an) / np.linalg.norm(fd)
     assert rel < 1e-4, rel
 
