@@ -142,3 +142,45 @@ def autotune(g: B.GaussianTensors, cams, targets: torch.Tensor, st, reps: int = 
         del step
         torch.cuda.empty_cache()
     return best[0], best[1], table
+
+
+def run_config3(n: int = 3_000_000, steps: int = 20, warmup: int = 3, tune: bool = True) -> dict:
+    """Batched densification step on the ring of 8 uneven views: 3M Gaussians
+    (cluster mixture, SH3).  Times the autotuned, graph-captured batched step
+    against the one-view-per-launch form of the same step."""
+    import synth
+    scene = synth.cluster_scene(0, n, 3)
+    cams = synth.ring_cameras(6.0)
+    st = synth.Settings()
+    g = B.GaussianTensors.from_scene(scene)
+    tgs = [torch.as_tensor(synth.target_image(10 + k, c.height, c.width)).cuda() for k, c in enumerate(cams)]
+    targets = concat_images(tgs)
+    del scene
+    table = []
+    if tune:
+        st_best, batch, table = autotune(g, cams, targets, st, reps=3)
+    else:
+        st_best, batch = st, 256
+    step = BatchedDensifyStep(g, cams, targets, st_best, batch=batch)
+    step.capture()
+    ms_graph = time_fn(step.replay, reps=steps, warmup=warmup)
+    ms_eager = time_fn(step.run_eager, reps=steps, warmup=warmup)
+    M = int(step.count.item())
+    n_out = int(step.db.n_out.item())
+    del step
+    torch.cuda.empty_cache()
+    plain = PlainDensifyStep(g, cams, tgs, st_best)
+    ms_plain = time_fn(plain.run, reps=steps, warmup=warmup)
+    return {"workload": "batched densification step: 3M Gaussians (cluster mixture, SH3), 8 ring views "
+                        "1957x1091, 1600x1060, 1237x822, 980x545 x2, 800x600 x3",
+            "gaussians": n, "views": len(cams), "pixels": sum(c.width * c.height for c in cams),
+            "tile": f"{st_best.tile_w}x{st_best.tile_h}", "batch": batch, "instances_M": M, "n_out": n_out,
+            "ms_batched_graph": round(ms_graph, 4), "ms_batched_eager": round(ms_eager, 4),
+            "ms_one_view_per_launch": round(ms_plain, 4), "speedup_vs_plain": round(ms_plain / ms_graph, 3),
+            "autotune": table}
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    print(json.dumps(run_config3(int(sys.argv[1]) if len(sys.argv) > 1 else 3_000_000)))

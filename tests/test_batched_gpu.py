@@ -87,12 +87,12 @@ def test_batched_equals_one_view_per_launch_and_graph_replay():
     lam_b, lam_p = step.db.lam.cpu().numpy(), plain.db.lam.cpu().numpy()
     nrm = np.linalg.norm(plain.db.S.cpu().numpy(), axis=1)
     assert np.all(np.abs(lam_b - lam_p) <= 1e-4 * np.maximum(nrm, 1e-30))
-    # graph replay equals an eager run
+    # graph replay equals an eager run (up to the order of the float atomics)
     grads_graph = [t.clone() for t in step.grads.tensors()]
     step.run_eager()
     torch.cuda.synchronize()
     for a, b in zip(grads_graph, step.grads.tensors()):
-        assert _rel(a.cpu().numpy(), b.cpu().numpy().astype(np.float64)) < 1e-6
+        assert _rel(a.cpu().numpy(), b.cpu().numpy().astype(np.float64)) < 1e-5
 
 
 def test_autotuner_picks_a_valid_configuration():
