@@ -246,6 +246,17 @@ int sgs_render_views_with_splitting(const sgs_gaussians *g, const sgs_camera *ca
                                     float *loss, const sgs_grads *grads, int32_t accumulate_grads, float *S_accum,
                                     int32_t *d_count, int64_t capacity, void *ws, size_t ws_bytes, void *stream);
 
+/* Forward-only render of a batch of views whose scenes may differ (the
+ * render-serving batch): scenes[v] is the scene of view v (sh_degree must be
+ * equal across the batch), images as in sgs_render_views_with_splitting.
+ * Each view's image is bit-identical to rendering it alone with the same
+ * settings.  d_count / capacity: instance count of the whole batch, as above. */
+int sgs_render_batch_workspace_size(const sgs_gaussians *scenes, const sgs_camera *cams, int32_t n_views,
+                                    const sgs_settings *st, int64_t capacity, size_t *bytes);
+int sgs_render_batch_fwd(const sgs_gaussians *scenes, const sgs_camera *cams, int32_t n_views,
+                         const sgs_settings *st, int32_t batch, float *images, int32_t *d_count, int64_t capacity,
+                         void *ws, size_t ws_bytes, void *stream);
+
 /* Adam step on one parameter array of `count` floats (the optimiser of the
  * training loop around the path; Algorithm 1's "standard gradient descent"
  * step): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;

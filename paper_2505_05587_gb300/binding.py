@@ -104,6 +104,10 @@ def lib():
         L.sgs_render_views_workspace_size.restype = C.c_int
         L.sgs_render_views_with_splitting.argtypes = [P, P, I32, P, I32, P, P, P, P, I32, P, P, I64, P, SZ, P]
         L.sgs_render_views_with_splitting.restype = C.c_int
+        L.sgs_render_batch_workspace_size.argtypes = [P, P, I32, P, I64, C.POINTER(SZ)]
+        L.sgs_render_batch_workspace_size.restype = C.c_int
+        L.sgs_render_batch_fwd.argtypes = [P, P, I32, P, I32, P, P, I64, P, SZ, P]
+        L.sgs_render_batch_fwd.restype = C.c_int
         L.sgs_adam_step.argtypes = [P, P, P, P, I64, F, F, F, F, I32, P, P]
         L.sgs_adam_step.restype = C.c_int
         L.sgs_densify_split_noalloc.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P]
@@ -338,6 +342,29 @@ def render_views_with_splitting(g: GaussianTensors, cams, st, batch: int, target
                                                  _p(images), _p(loss), C.byref(grc), 1 if accumulate else 0,
                                                  _p(S_accum), _p(d_count), capacity, _p(ws),
                                                  ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def _scenes_c(scenes):
+    arr = (Gaussians * len(scenes))()
+    for k, g in enumerate(scenes):
+        arr[k] = g.c()
+    return arr
+
+
+def render_batch_workspace_size(scenes, cams, st, capacity: int) -> int:
+    b = C.c_size_t()
+    sa, ca, sc = _scenes_c(scenes), cameras_c(cams), settings_c(st)
+    _check("sgs_render_batch_workspace_size",
+           lib().sgs_render_batch_workspace_size(sa, ca, len(cams), C.byref(sc), capacity, C.byref(b)))
+    return b.value
+
+
+def render_batch_fwd(scenes, cams, st, batch: int, images, d_count, capacity: int, ws, stream=None):
+    """Forward render of views of (possibly different) scenes in one pass."""
+    sa, ca, sc = _scenes_c(scenes), cameras_c(cams), settings_c(st)
+    _check("sgs_render_batch_fwd",
+           lib().sgs_render_batch_fwd(sa, ca, len(cams), C.byref(sc), batch, _p(images), _p(d_count), capacity,
+                                      _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def adam_step(param, grad, m, v, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, grad_accum=None,

@@ -31,24 +31,41 @@ CamDev make_cam(const sgs_camera& c, const sgs_settings& s) {
     return d;
 }
 
-ViewsDev make_views(const sgs_camera* cams, int nv, const sgs_settings& s) {
+ViewsDev make_views(const sgs_camera* cams, int nv, const sgs_settings& s, const int* rows_per_view, int rows_each) {
     ViewsDev vd;
     memset(&vd, 0, sizeof(vd));
     vd.nv = nv;
-    int t = 0;
+    int t = 0, r = 0;
     long long p = 0;
     for (int v = 0; v < nv; ++v) {
         vd.cam[v] = make_cam(cams[v], s);
         vd.tile_off[v] = t;
         vd.pix_off[v] = p;
+        vd.row_off[v] = r;
         t += vd.cam[v].gx * vd.cam[v].gy;
         p += (long long)cams[v].width * cams[v].height;
+        r += rows_per_view ? rows_per_view[v] : rows_each;
     }
     vd.tile_off[nv] = t;
     vd.pix_off[nv] = p;
+    vd.row_off[nv] = r;
     vd.T_total = t;
     vd.P_total = p;
     return vd;
+}
+
+ScenesDev make_scenes(const sgs_gaussians* g, int nv, bool per_view) {
+    ScenesDev sc;
+    memset(&sc, 0, sizeof(sc));
+    for (int v = 0; v < nv; ++v) {
+        const sgs_gaussians& gv = per_view ? g[v] : g[0];
+        sc.means[v] = gv.means;
+        sc.log_scales[v] = gv.log_scales;
+        sc.quats[v] = gv.quats;
+        sc.opacity_logit[v] = gv.opacity_logit;
+        sc.sh[v] = gv.sh;
+    }
+    return sc;
 }
 
 SetDev make_set(const sgs_settings& s) {
@@ -129,7 +146,8 @@ int sgs_project(const sgs_gaussians* g, const sgs_camera* cam, const sgs_setting
         return SGS_ERR_INVALID_ARG;
     if (g->n > 0 && (!out->xy || !out->conic_opac || !out->rgb || !out->depth || !out->rect || !out->tiles_touched))
         return SGS_ERR_INVALID_ARG;
-    return cuda_status(launch_project(*g, make_views(cam, 1, *st), make_set(*st), *out, (cudaStream_t)stream));
+    return cuda_status(launch_project(make_scenes(g, 1, false), g->sh_degree, make_views(cam, 1, *st, nullptr, g->n),
+                                      make_set(*st), *out, (cudaStream_t)stream));
 }
 
 int sgs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t num_tiles, size_t* bytes) {
@@ -147,9 +165,9 @@ int sgs_bin_sort(const sgs_proj* proj, int32_t n, const sgs_camera* cam, const s
         return SGS_ERR_INVALID_ARG;
     if (out->capacity > 0 && !out->gids) return SGS_ERR_INVALID_ARG;
     if (n > 0 && (!proj->depth || !proj->rect || !proj->tiles_touched)) return SGS_ERR_INVALID_ARG;
-    ViewsDev vd = make_views(cam, 1, *st);
+    ViewsDev vd = make_views(cam, 1, *st, nullptr, n);
     if (!ws || ws_bytes < bin_sort_ws_bytes(n, out->capacity, vd.T_total)) return SGS_ERR_WORKSPACE;
-    return cuda_status(launch_bin_sort(*proj, n, vd, make_set(*st), *out, ws, (cudaStream_t)stream));
+    return cuda_status(launch_bin_sort(*proj, vd, make_set(*st), *out, ws, (cudaStream_t)stream));
 }
 
 int sgs_render_fwd(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,
@@ -205,7 +223,8 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
     cudaError_t e = cudaMemsetAsync(g2d, 0, sizeof(float) * 16 * (size_t)g->n, s);
     if (e == cudaSuccess) e = launch_render_bwd(*proj, *bins, cd, sd, final_T, n_contrib, dL_dimage, g2d, s);
     if (e == cudaSuccess)
-        e = launch_project_bwd(*g, *proj, make_views(cam, 1, *st), g2d, accumulate_grads != 0, *grads, S_accum, s);
+        e = launch_project_bwd(*g, *proj, make_views(cam, 1, *st, nullptr, g->n), g2d, accumulate_grads != 0, *grads,
+                               S_accum, s);
     return cuda_status(e);
 }
 
@@ -235,10 +254,10 @@ struct ViewsWs {
     size_t bytes;
 };
 
-static ViewsWs carve_views_ws(void* base, int n, const ViewsDev& vd, int64_t capacity) {
+static ViewsWs carve_views_ws(void* base, const ViewsDev& vd, int64_t capacity, bool with_backward) {
     Carver c{reinterpret_cast<char*>(base), 0};
     ViewsWs w;
-    const size_t rows = (size_t)(n > 0 ? n : 1) * vd.nv;
+    const size_t rows = (size_t)(vd.row_off[vd.nv] > 0 ? vd.row_off[vd.nv] : 1);
     const size_t P = (size_t)(vd.P_total > 0 ? vd.P_total : 1);
     const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
     w.proj.xy = c.take<float>(4 * rows);
@@ -256,8 +275,8 @@ static ViewsWs carve_views_ws(void* base, int n, const ViewsDev& vd, int64_t cap
     w.sort_ws = c.take<char>(w.sort_bytes);
     w.final_T = c.take<float>(P);
     w.n_contrib = c.take<uint32_t>(P);
-    w.dL = c.take<float>(3 * P);
-    w.g2d = c.take<float>(16 * rows);
+    w.dL = with_backward ? c.take<float>(3 * P) : nullptr;
+    w.g2d = with_backward ? c.take<float>(16 * rows) : nullptr;
     w.counters = c.take<uint32_t>(2);
     w.bytes = c.off + 256;
     return w;
@@ -279,8 +298,8 @@ int sgs_render_views_workspace_size(int32_t n, const sgs_camera* cams, int32_t n
     if (n < 0 || capacity < 0 || capacity > ((int64_t)1 << 31) - 1 || !bytes || !valid_views(cams, n_views, st) ||
         (long long)n * n_views > ((long long)1 << 31) - 1)
         return SGS_ERR_INVALID_ARG;
-    ViewsDev vd = make_views(cams, n_views, *st);
-    *bytes = carve_views_ws(nullptr, n, vd, capacity).bytes;
+    ViewsDev vd = make_views(cams, n_views, *st, nullptr, n);
+    *bytes = carve_views_ws(nullptr, vd, capacity, true).bytes;
     return SGS_OK;
 }
 
@@ -297,16 +316,16 @@ int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* ca
     if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit || !grads->sh ||
                      !S_accum))
         return SGS_ERR_INVALID_ARG;
-    ViewsDev vd = make_views(cams, n_views, *st);
-    ViewsWs w = carve_views_ws(nullptr, g->n, vd, capacity);
+    ViewsDev vd = make_views(cams, n_views, *st, nullptr, g->n);
+    ViewsWs w = carve_views_ws(nullptr, vd, capacity, true);
     if (!ws || ws_bytes < w.bytes) return SGS_ERR_WORKSPACE;
-    w = carve_views_ws(ws, g->n, vd, capacity);
+    w = carve_views_ws(ws, vd, capacity, true);
     w.bins.count = d_count;
     const SetDev sd = make_set(*st);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t rows = (size_t)g->n * n_views;
-    cudaError_t e = launch_project(*g, vd, sd, w.proj, s);
-    if (e == cudaSuccess) e = launch_bin_sort(w.proj, g->n, vd, sd, w.bins, w.sort_ws, s);
+    cudaError_t e = launch_project(make_scenes(g, n_views, false), g->sh_degree, vd, sd, w.proj, s);
+    if (e == cudaSuccess) e = launch_bin_sort(w.proj, vd, sd, w.bins, w.sort_ws, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 2 * sizeof(uint32_t), s);
     if (e == cudaSuccess)
         e = launch_render_fwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, images, w.final_T,
@@ -317,6 +336,54 @@ int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* ca
         e = launch_render_bwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, w.final_T, w.n_contrib,
                                     w.dL, w.g2d, w.counters + 1, s);
     if (e == cudaSuccess) e = launch_project_bwd(*g, w.proj, vd, w.g2d, accumulate_grads != 0, *grads, S_accum, s);
+    return cuda_status(e);
+}
+
+// Forward-only batch of views whose scenes may differ (render serving).
+static bool valid_batch(const sgs_gaussians* scenes, const sgs_camera* cams, int32_t n_views,
+                        const sgs_settings* st, int rows[kMaxViews]) {
+    if (!scenes || !valid_views(cams, n_views, st)) return false;
+    long long total = 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (!valid_gaussians(&scenes[v]) || scenes[v].sh_degree != scenes[0].sh_degree) return false;
+        rows[v] = scenes[v].n;
+        total += scenes[v].n;
+    }
+    return total < ((long long)1 << 31);
+}
+
+int sgs_render_batch_workspace_size(const sgs_gaussians* scenes, const sgs_camera* cams, int32_t n_views,
+                                    const sgs_settings* st, int64_t capacity, size_t* bytes) {
+    int rows[kMaxViews];
+    if (!bytes || capacity < 0 || capacity > ((int64_t)1 << 31) - 1 || !valid_batch(scenes, cams, n_views, st, rows))
+        return SGS_ERR_INVALID_ARG;
+    ViewsDev vd = make_views(cams, n_views, *st, rows, 0);
+    *bytes = carve_views_ws(nullptr, vd, capacity, false).bytes;
+    return SGS_OK;
+}
+
+int sgs_render_batch_fwd(const sgs_gaussians* scenes, const sgs_camera* cams, int32_t n_views, const sgs_settings* st,
+                         int32_t batch, float* images, int32_t* d_count, int64_t capacity, void* ws, size_t ws_bytes,
+                         void* stream) {
+    int rows[kMaxViews];
+    if (!images || !d_count || capacity < 0 || capacity > ((int64_t)1 << 31) - 1 ||
+        !valid_batch(scenes, cams, n_views, st, rows))
+        return SGS_ERR_INVALID_ARG;
+    if (batch == 0) batch = st->tile_w * st->tile_h > 256 ? 256 : st->tile_w * st->tile_h;
+    if (batch != 64 && batch != 128 && batch != 256) return SGS_ERR_INVALID_ARG;
+    ViewsDev vd = make_views(cams, n_views, *st, rows, 0);
+    ViewsWs w = carve_views_ws(nullptr, vd, capacity, false);
+    if (!ws || ws_bytes < w.bytes) return SGS_ERR_WORKSPACE;
+    w = carve_views_ws(ws, vd, capacity, false);
+    w.bins.count = d_count;
+    const SetDev sd = make_set(*st);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_project(make_scenes(scenes, n_views, true), scenes[0].sh_degree, vd, sd, w.proj, s);
+    if (e == cudaSuccess) e = launch_bin_sort(w.proj, vd, sd, w.bins, w.sort_ws, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess)
+        e = launch_render_fwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, images, w.final_T,
+                                    w.n_contrib, w.counters, s);
     return cuda_status(e);
 }
 

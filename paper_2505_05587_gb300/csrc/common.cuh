@@ -61,8 +61,24 @@ struct ViewsDev {
     long long P_total;
     int tile_off[kMaxViews + 1];
     long long pix_off[kMaxViews + 1];
+    int row_off[kMaxViews + 1];     // projection rows of view v: [row_off[v], row_off[v+1])
     CamDev cam[kMaxViews];
 };
+
+// Gaussian arrays of each view's scene (all equal when the views share one).
+struct ScenesDev {
+    const float* means[kMaxViews];
+    const float* log_scales[kMaxViews];
+    const float* quats[kMaxViews];
+    const float* opacity_logit[kMaxViews];
+    const float* sh[kMaxViews];
+};
+
+__device__ __forceinline__ int view_of_row(const ViewsDev& vd, long long r) {
+    int v = 0;
+    while (v + 1 < vd.nv && r >= vd.row_off[v + 1]) ++v;
+    return v;
+}
 
 __device__ __forceinline__ int view_of_tile(const ViewsDev& vd, int t) {
     int v = 0;
@@ -92,19 +108,21 @@ void note_launch(int k = 1);
 // Keeps `e` for sgs_get_last_cuda_error() and returns SGS_ERR_CUDA.
 int record_cuda_error(cudaError_t e);
 CamDev make_cam(const sgs_camera& c, const sgs_settings& s);
-ViewsDev make_views(const sgs_camera* cams, int nv, const sgs_settings& s);
+ViewsDev make_views(const sgs_camera* cams, int nv, const sgs_settings& s, const int* rows_per_view = nullptr,
+                    int rows_each = 0);
+ScenesDev make_scenes(const sgs_gaussians* g, int nv, bool per_view);
 SetDev make_set(const sgs_settings& s);
 bool tile_supported(int tw, int th);
 
 // Launchers (host functions, enqueue on `stream`).
-cudaError_t launch_project(const sgs_gaussians& g, const ViewsDev& vd, const SetDev& st, const sgs_proj& out,
-                           cudaStream_t stream);
+cudaError_t launch_project(const ScenesDev& sc, int sh_degree, const ViewsDev& vd, const SetDev& st,
+                           const sgs_proj& out, cudaStream_t stream);
 cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const ViewsDev& vd, const float* g2d,
                                bool accumulate, const sgs_grads& grads, float* S_accum, cudaStream_t stream);
 
 size_t bin_sort_ws_bytes(int n, int64_t capacity, int num_tiles);
-cudaError_t launch_bin_sort(const sgs_proj& proj, int n_per_view, const ViewsDev& vd, const SetDev& st,
-                            const sgs_bins& out, void* ws, cudaStream_t stream);
+cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetDev& st, const sgs_bins& out, void* ws,
+                            cudaStream_t stream);
 
 cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
                               const SetDev& st, float* image, float* final_T, uint32_t* n_contrib,

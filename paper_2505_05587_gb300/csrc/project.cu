@@ -274,18 +274,21 @@ __device__ __forceinline__ void sh_weighted_grad(float x, float y, float z, cons
 // ---------------------------------------------------------------------------
 // Forward projection: one thread per Gaussian.
 // ---------------------------------------------------------------------------
+// One thread per projection row (view v, Gaussian i of view v's scene).
 template <int DEG>
-__global__ void __launch_bounds__(256) project_kernel(
-    const float* __restrict__ means, const float* __restrict__ log_scales,
-    const float* __restrict__ quats, const float* __restrict__ opacity_logit,
-    const float* __restrict__ sh, int n, ViewsDev vd, SetDev st,
+__global__ void __launch_bounds__(256) project_kernel(ScenesDev sc, ViewsDev vd, SetDev st,
     float4* __restrict__ xy, float4* __restrict__ conic_opac, float4* __restrict__ rgb_out,
     float* __restrict__ depth, short4* __restrict__ rect, uint32_t* __restrict__ tiles) {
     const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= (long long)n * vd.nv) return;
-    const int v = (int)(row / n);
-    const int i = (int)(row - (long long)v * n);
+    if (row >= vd.row_off[vd.nv]) return;
+    const int v = view_of_row(vd, row);
+    const int i = (int)(row - vd.row_off[v]);
     const CamDev& cam = vd.cam[v];
+    const float* __restrict__ means = sc.means[v];
+    const float* __restrict__ log_scales = sc.log_scales[v];
+    const float* __restrict__ quats = sc.quats[v];
+    const float* __restrict__ opacity_logit = sc.opacity_logit[v];
+    const float* __restrict__ sh = sc.sh[v];
     Stage s = integer_stage(means, log_scales, quats, i, cam, st);
     depth[row] = s.tz;
     if (s.culled) {
@@ -329,17 +332,16 @@ __global__ void __launch_bounds__(256) project_kernel(
     rgb_out[row] = make_float4(fmaxf(r, 0.0f), fmaxf(g, 0.0f), fmaxf(b, 0.0f), 0.0f);
 }
 
-cudaError_t launch_project(const sgs_gaussians& g, const ViewsDev& vd, const SetDev& st, const sgs_proj& out,
-                           cudaStream_t stream) {
-    if (g.n == 0) return cudaSuccess;
-    const long long rows = (long long)g.n * vd.nv;
+cudaError_t launch_project(const ScenesDev& sc, int sh_degree, const ViewsDev& vd, const SetDev& st,
+                           const sgs_proj& out, cudaStream_t stream) {
+    const long long rows = vd.row_off[vd.nv];
+    if (rows == 0) return cudaSuccess;
     const int blocks = (int)((rows + 255) / 256);
-    auto kern = g.sh_degree == 0 ? project_kernel<0>
-              : g.sh_degree == 1 ? project_kernel<1>
-              : g.sh_degree == 2 ? project_kernel<2> : project_kernel<3>;
+    auto kern = sh_degree == 0 ? project_kernel<0>
+              : sh_degree == 1 ? project_kernel<1>
+              : sh_degree == 2 ? project_kernel<2> : project_kernel<3>;
     kern<<<blocks, 256, 0, stream>>>(
-        g.means, g.log_scales, g.quats, g.opacity_logit, g.sh, g.n, vd, st,
-        reinterpret_cast<float4*>(out.xy), reinterpret_cast<float4*>(out.conic_opac),
+        sc, vd, st, reinterpret_cast<float4*>(out.xy), reinterpret_cast<float4*>(out.conic_opac),
         reinterpret_cast<float4*>(out.rgb), out.depth, reinterpret_cast<short4*>(out.rect),
         out.tiles_touched);
     note_launch();

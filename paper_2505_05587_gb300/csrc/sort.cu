@@ -353,17 +353,17 @@ __global__ void gather_counts_kernel(const uint32_t* __restrict__ perm, const ui
 }
 
 // One thread per depth-sorted projection row: writes the row's instances
-// (global tile id of view v = row / n_per_view, row) in row-major tile order.
+// (global tile id in the row's view, row) in row-major tile order.
 __global__ void emit_kernel(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cnt,
                             const uint32_t* __restrict__ offs, const short4* __restrict__ rect, int n_rows,
-                            int n_per_view, ViewsDev vd, int64_t cap, uint32_t* __restrict__ inst_tile,
+                            ViewsDev vd, int64_t cap, uint32_t* __restrict__ inst_tile,
                             uint32_t* __restrict__ inst_gid) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_rows) return;
     uint32_t c = cnt[j];
     if (c == 0) return;
     uint32_t g = perm[j];
-    const int v = (int)(g / (uint32_t)n_per_view);
+    const int v = view_of_row(vd, g);
     const int gx = vd.cam[v].gx;
     const uint32_t t0 = (uint32_t)vd.tile_off[v];
     short4 r = rect[g];
@@ -438,10 +438,10 @@ size_t bin_sort_ws_bytes(int n, int64_t capacity, int num_tiles) {
     return carve_bin_ws(nullptr, n, capacity).bytes;
 }
 
-cudaError_t launch_bin_sort(const sgs_proj& proj, int n_per_view, const ViewsDev& vd, const SetDev& st,
-                            const sgs_bins& out, void* ws, cudaStream_t stream) {
+cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetDev& st, const sgs_bins& out, void* ws,
+                            cudaStream_t stream) {
     (void)st;
-    const int n = n_per_view * vd.nv;           // projection rows
+    const int n = vd.row_off[vd.nv];            // projection rows
     BinWs w = carve_bin_ws(ws, n, out.capacity);
     const int T = vd.T_total;
     cudaError_t e = cudaMemsetAsync(out.ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, stream);
@@ -480,8 +480,8 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, int n_per_view, const ViewsDev
         gv[0] = w.inst_gid_tmp;
         gv[1] = out.gids;
     }
-    emit_kernel<<<nb, 256, 0, stream>>>(perm, w.cnt, w.offs, reinterpret_cast<const short4*>(proj.rect), n,
-                                        n_per_view, vd, out.capacity, gk[0], gv[0]);
+    emit_kernel<<<nb, 256, 0, stream>>>(perm, w.cnt, w.offs, reinterpret_cast<const short4*>(proj.rect), n, vd,
+                                        out.capacity, gk[0], gv[0]);
     note_launch();
     // 4. stable sort of the instances by tile id
     e = radix_sort_pairs(gk, gv, out.count, 0, out.capacity, tile_bits, w.rb, stream);

@@ -1,0 +1,241 @@
+"""Render serving with continuous batching.
+
+Scene Gaussians stay resident on the device.  Requests (scene, camera,
+resolution) arrive over time; a host scheduler forms batches of the requests
+that have arrived, up to `max_batch`, whenever a stream slot is free and the
+batch's memory fits the HBM budget (admission by free device memory), and
+launches each batch as ONE forward pass (``render_batch_fwd``: projection of
+every request's scene, one binning and depth sort, one persistent compositing
+kernel over the tiles of all its views).  Batches in flight on different
+streams overlap on the device; completions are detected with events and
+their memory is returned to the budget.  Latency = completion - arrival.
+
+``serve_one_per_launch`` is the baseline: each request alone, one launch
+sequence at a time, in arrival order.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+@dataclass
+class Job:
+    idx: int
+    arrival: float      # seconds from the start of the run
+    scene: int
+    cam: object
+
+
+@dataclass
+class _Batch:
+    jobs: list
+    stream: torch.cuda.Stream
+    event: torch.cuda.Event
+    images: torch.Tensor
+    ws: torch.Tensor
+    count: torch.Tensor
+    count_host: torch.Tensor
+    capacity: int
+    nbytes: int
+    pix_off: list
+
+
+class RenderServer:
+    def __init__(self, scenes: list[B.GaussianTensors], st, max_batch: int = 8, n_slots: int = 4,
+                 hbm_budget: int | None = None, batch_depth: int = 0, keep_images: bool = False):
+        self.scenes, self.st = scenes, st
+        self.max_batch, self.n_slots, self.batch_depth = max_batch, n_slots, batch_depth
+        self.keep_images = keep_images
+        free, _ = torch.cuda.mem_get_info()
+        self.budget = int(hbm_budget if hbm_budget is not None else 0.5 * free)
+        self.in_use = 0
+        self.streams = [torch.cuda.Stream() for _ in range(n_slots)]
+        self.m_est: dict = {}            # (scene, w, h) -> instance estimate
+        self.images: dict = {}
+        self.stats = collections.Counter()
+
+    def _est(self, j) -> int:
+        return self.m_est.get((j.scene, j.cam.width, j.cam.height), 4 * self.scenes[j.scene].n)
+
+    def _capacity(self, jobs) -> int:
+        return int(sum(self._est(j) for j in jobs)) + 4096
+
+    def _batch_bytes(self, jobs, capacity) -> int:
+        scenes = [self.scenes[j.scene] for j in jobs]
+        cams = [j.cam for j in jobs]
+        ws = B.render_batch_workspace_size(scenes, cams, self.st, capacity)
+        return ws + 12 * sum(c.width * c.height for c in cams)
+
+    def _launch(self, jobs, stream, capacity=None) -> _Batch:
+        capacity = capacity or self._capacity(jobs)
+        scenes = [self.scenes[j.scene] for j in jobs]
+        cams = [j.cam for j in jobs]
+        nbytes = self._batch_bytes(jobs, capacity)
+        P = sum(c.width * c.height for c in cams)
+        with torch.cuda.stream(stream):
+            images = torch.empty(P, 3, device="cuda")
+            ws = B.workspace(B.render_batch_workspace_size(scenes, cams, self.st, capacity))
+            count = torch.zeros(1, dtype=torch.int32, device="cuda")
+            B.render_batch_fwd(scenes, cams, self.st, self.batch_depth, images, count, capacity, ws, stream)
+            count_host = torch.empty(1, dtype=torch.int32, pin_memory=True)
+            count_host.copy_(count, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        offs = np.cumsum([0] + [c.width * c.height for c in cams]).tolist()
+        self.in_use += nbytes
+        self.stats["batches"] += 1
+        self.stats["batched_requests"] += len(jobs)
+        return _Batch(jobs, stream, ev, images, ws, count, count_host, capacity, nbytes, offs)
+
+    def _finish(self, b: _Batch, now: float, lat: dict) -> _Batch | None:
+        self.in_use -= b.nbytes
+        M = int(b.count_host.item())
+        # split the batch's instance count over its requests in proportion to
+        # their estimates, and keep ~15% headroom for the next batch
+        share = M / max(sum(self._est(j) for j in b.jobs), 1)
+        for j in b.jobs:
+            self.m_est[(j.scene, j.cam.width, j.cam.height)] = int(self._est(j) * share * 1.15) + 1024
+        if M > b.capacity:                       # instance capacity too small: rerun with room
+            self.stats["reruns"] += 1
+            return self._launch(b.jobs, b.stream, int(M * 1.1) + 4096)
+        for k, j in enumerate(b.jobs):
+            lat[j.idx] = now - j.arrival
+            if self.keep_images:
+                self.images[j.idx] = b.images[b.pix_off[k]:b.pix_off[k + 1]].reshape(j.cam.height, j.cam.width,
+                                                                                      3).clone()
+        return None
+
+    def run(self, jobs: list[Job], realtime: bool = True) -> dict:
+        """Serves the jobs (sorted by arrival); realtime=False releases every
+        job at t=0 (saturation)."""
+        jobs = sorted(jobs, key=lambda j: j.arrival)
+        if not realtime:
+            jobs = [Job(j.idx, 0.0, j.scene, j.cam) for j in jobs]
+        pending = collections.deque()
+        free_slots = list(range(self.n_slots))
+        inflight: dict = {}
+        lat: dict = {}
+        nxt = 0
+        t0 = time.perf_counter()
+        while len(lat) < len(jobs):
+            now = time.perf_counter() - t0
+            while nxt < len(jobs) and jobs[nxt].arrival <= now:
+                pending.append(jobs[nxt])
+                nxt += 1
+            # completions
+            for slot, b in list(inflight.items()):
+                if b.event.query():
+                    again = self._finish(b, time.perf_counter() - t0, lat)
+                    if again is not None:
+                        inflight[slot] = again
+                    else:
+                        del inflight[slot]
+                        free_slots.append(slot)
+            # admissions: fill free slots with batches that fit the budget
+            while free_slots and pending:
+                take = []
+                while pending and len(take) < self.max_batch:
+                    cand = take + [pending[0]]
+                    cap = self._capacity(cand)
+                    if take and self.in_use + self._batch_bytes(cand, cap) > self.budget:
+                        break
+                    take.append(pending.popleft())
+                if not take:
+                    break
+                if self.in_use + self._batch_bytes(take, self._capacity(take)) > self.budget and inflight:
+                    pending.extendleft(reversed(take))     # wait for memory to free up
+                    self.stats["admission_waits"] += 1
+                    break
+                slot = free_slots.pop()
+                inflight[slot] = self._launch(take, self.streams[slot])
+            if not inflight and not pending and nxt < len(jobs):
+                wait = jobs[nxt].arrival - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.002))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        return _summary(jobs, lat, wall, dict(self.stats))
+
+
+def serve_one_per_launch(scenes: list[B.GaussianTensors], st, jobs: list[Job], realtime: bool = True,
+                         keep_images: bool = False) -> dict:
+    """Baseline: every request alone, one launch sequence after the other."""
+    from . import pipeline as PL
+    jobs = sorted(jobs, key=lambda j: j.arrival)
+    if not realtime:
+        jobs = [Job(j.idx, 0.0, j.scene, j.cam) for j in jobs]
+    views = {}
+    lat, images = {}, {}
+    t0 = time.perf_counter()
+    for j in jobs:
+        now = time.perf_counter() - t0
+        if j.arrival > now:
+            time.sleep(j.arrival - now)
+        key = (j.scene, j.cam.width, j.cam.height)
+        g = scenes[j.scene]
+        if key not in views:
+            views[key] = PL.ViewBuffers.alloc(g.n, j.cam, st)
+        vb = views[key]
+        vb.cam = j.cam
+        PL.project_and_sort(g, vb)             # reads back M (a sync) as a per-request launch sequence does
+        B.render_fwd(vb.proj, vb.bins, j.cam, st, vb.image, vb.final_T, vb.n_contrib)
+        torch.cuda.synchronize()
+        lat[j.idx] = time.perf_counter() - t0 - j.arrival
+        if keep_images:
+            images[j.idx] = vb.image.clone()
+    wall = time.perf_counter() - t0
+    out = _summary(jobs, lat, wall, {})
+    if keep_images:
+        out["images"] = images
+    return out
+
+
+def _summary(jobs, lat, wall, stats) -> dict:
+    l = np.array([lat[j.idx] for j in jobs]) * 1e3
+    return {"requests": len(jobs), "wall_s": round(wall, 4), "frames_per_s": round(len(jobs) / wall, 2),
+            "p50_ms": round(float(np.percentile(l, 50)), 3), "p99_ms": round(float(np.percentile(l, 99)), 3),
+            "mean_ms": round(float(l.mean()), 3), "max_ms": round(float(l.max()), 3), **stats}
+
+
+def config5_jobs(seed: int = 3, n_requests: int = 4000, rate_hz: float = 200.0, n_scenes: int = 6):
+    import synth
+    reqs = synth.request_stream(seed, n_requests, rate_hz, n_scenes)
+    return [Job(k, r.arrival_s - reqs[0].arrival_s, r.scene, r.camera) for k, r in enumerate(reqs)]
+
+
+def config5_scenes(sizes=(100_000, 300_000, 1_000_000, 1_000_000, 2_000_000, 3_000_000)):
+    import synth
+    return [B.GaussianTensors.from_scene(synth.cluster_scene(10 + k, n, 3)) for k, n in enumerate(sizes)]
+
+
+def run_config5(n_requests: int = 4000, rate_hz: float = 200.0) -> dict:
+    import synth
+    st = synth.Settings()
+    scenes = config5_scenes()
+    jobs = config5_jobs(3, n_requests, rate_hz, len(scenes))
+    warm = jobs[:64]
+    RenderServer(scenes, st).run(warm, realtime=False)          # warm-up (allocator, estimates)
+    serve_one_per_launch(scenes, st, warm, realtime=False)
+    server = RenderServer(scenes, st)
+    out = {"workload": f"render serving: {n_requests} requests, Poisson {rate_hz:g} req/s, 6 resident scenes "
+                       "(100k, 300k, 1M, 1M, 2M, 3M Gaussians, SH3), 640x480 / 1237x822 / 1920x1080"}
+    out["continuous_batching_realtime"] = server.run(jobs, realtime=True)
+    out["one_per_launch_realtime"] = serve_one_per_launch(scenes, st, jobs, realtime=True)
+    sat = jobs[:1000]
+    out["continuous_batching_saturated"] = RenderServer(scenes, st).run(sat, realtime=False)
+    out["one_per_launch_saturated"] = serve_one_per_launch(scenes, st, sat, realtime=False)
+    return out
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    print(json.dumps(run_config5(int(sys.argv[1]) if len(sys.argv) > 1 else 4000)))
