@@ -100,9 +100,10 @@ class RenderServer:
         M = int(b.count_host.item())
         # split the batch's instance count over its requests in proportion to
         # their estimates, and keep ~15% headroom for the next batch
-        share = M / max(sum(self._est(j) for j in b.jobs), 1)
-        for j in b.jobs:
-            self.m_est[(j.scene, j.cam.width, j.cam.height)] = int(self._est(j) * share * 1.15) + 1024
+        ests = [self._est(j) for j in b.jobs]
+        share = M / max(sum(ests), 1)
+        for j, e in zip(b.jobs, ests):
+            self.m_est[(j.scene, j.cam.width, j.cam.height)] = int(e * share * 1.15) + 1024
         if M > b.capacity:                       # instance capacity too small: rerun with room
             self.stats["reruns"] += 1
             return self._launch(b.jobs, b.stream, int(M * 1.1) + 4096)
