@@ -37,7 +37,7 @@ class Job:
 @dataclass
 class _Batch:
     jobs: list
-    stream: torch.cuda.Stream
+    stream: int                 # slot index
     event: torch.cuda.Event
     images: torch.Tensor
     ws: torch.Tensor
@@ -58,6 +58,9 @@ class RenderServer:
         self.budget = int(hbm_budget if hbm_budget is not None else 0.5 * free)
         self.in_use = 0
         self.streams = [torch.cuda.Stream() for _ in range(n_slots)]
+        self.slot_ws = [None] * n_slots          # grow-only workspaces, one per stream slot
+        self.slot_img = [None] * n_slots
+        self.slot_cnt = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in range(n_slots)]
         self.m_est: dict = {}            # (scene, w, h) -> instance estimate
         self.images: dict = {}
         self.stats = collections.Counter()
@@ -74,16 +77,20 @@ class RenderServer:
         ws = B.render_batch_workspace_size(scenes, cams, self.st, capacity)
         return ws + 12 * sum(c.width * c.height for c in cams)
 
-    def _launch(self, jobs, stream, capacity=None) -> _Batch:
+    def _launch(self, jobs, slot, capacity=None) -> _Batch:
+        stream = self.streams[slot]
         capacity = capacity or self._capacity(jobs)
         scenes = [self.scenes[j.scene] for j in jobs]
         cams = [j.cam for j in jobs]
         nbytes = self._batch_bytes(jobs, capacity)
         P = sum(c.width * c.height for c in cams)
+        wsb = B.render_batch_workspace_size(scenes, cams, self.st, capacity)
         with torch.cuda.stream(stream):
-            images = torch.empty(P, 3, device="cuda")
-            ws = B.workspace(B.render_batch_workspace_size(scenes, cams, self.st, capacity))
-            count = torch.zeros(1, dtype=torch.int32, device="cuda")
+            if self.slot_ws[slot] is None or self.slot_ws[slot].numel() < wsb:
+                self.slot_ws[slot] = B.workspace(int(wsb * 1.25))
+            if self.slot_img[slot] is None or self.slot_img[slot].shape[0] < P:
+                self.slot_img[slot] = torch.empty(int(P * 1.25), 3, device="cuda")
+            ws, images, count = self.slot_ws[slot], self.slot_img[slot][:P], self.slot_cnt[slot]
             B.render_batch_fwd(scenes, cams, self.st, self.batch_depth, images, count, capacity, ws, stream)
             count_host = torch.empty(1, dtype=torch.int32, pin_memory=True)
             count_host.copy_(count, non_blocking=True)
@@ -93,19 +100,16 @@ class RenderServer:
         self.in_use += nbytes
         self.stats["batches"] += 1
         self.stats["batched_requests"] += len(jobs)
-        return _Batch(jobs, stream, ev, images, ws, count, count_host, capacity, nbytes, offs)
+        return _Batch(jobs, slot, ev, images, ws, count, count_host, capacity, nbytes, offs)
 
     def _finish(self, b: _Batch, now: float, lat: dict) -> _Batch | None:
         self.in_use -= b.nbytes
         M = int(b.count_host.item())
-        # split the batch's instance count over its requests in proportion to
-        # their estimates, and keep ~15% headroom for the next batch
-        ests = [self._est(j) for j in b.jobs]
-        share = M / max(sum(ests), 1)
-        for j, e in zip(b.jobs, ests):
-            self.m_est[(j.scene, j.cam.width, j.cam.height)] = int(e * share * 1.15) + 1024
         if M > b.capacity:                       # instance capacity too small: rerun with room
             self.stats["reruns"] += 1
+            ests = [self._est(j) for j in b.jobs]
+            for j, e in zip(b.jobs, ests):       # estimates only grow
+                self.m_est[(j.scene, j.cam.width, j.cam.height)] = int(1.5 * e * M / max(sum(ests), 1)) + 1024
             return self._launch(b.jobs, b.stream, int(M * 1.1) + 4096)
         for k, j in enumerate(b.jobs):
             lat[j.idx] = now - j.arrival
@@ -156,7 +160,7 @@ class RenderServer:
                     self.stats["admission_waits"] += 1
                     break
                 slot = free_slots.pop()
-                inflight[slot] = self._launch(take, self.streams[slot])
+                inflight[slot] = self._launch(take, slot)
             if not inflight and not pending and nxt < len(jobs):
                 wait = jobs[nxt].arrival - (time.perf_counter() - t0)
                 if wait > 0:
@@ -222,16 +226,18 @@ def run_config5(n_requests: int = 4000, rate_hz: float = 200.0) -> dict:
     st = synth.Settings()
     scenes = config5_scenes()
     jobs = config5_jobs(3, n_requests, rate_hz, len(scenes))
-    warm = jobs[:64]
-    RenderServer(scenes, st).run(warm, realtime=False)          # warm-up (allocator, estimates)
-    serve_one_per_launch(scenes, st, warm, realtime=False)
+    warm = jobs[:200]
     server = RenderServer(scenes, st)
+    server.run(warm, realtime=False)               # warm-up: workspaces and instance estimates
+    serve_one_per_launch(scenes, st, warm, realtime=False)
     out = {"workload": f"render serving: {n_requests} requests, Poisson {rate_hz:g} req/s, 6 resident scenes "
                        "(100k, 300k, 1M, 1M, 2M, 3M Gaussians, SH3), 640x480 / 1237x822 / 1920x1080"}
+    server.stats.clear()
     out["continuous_batching_realtime"] = server.run(jobs, realtime=True)
     out["one_per_launch_realtime"] = serve_one_per_launch(scenes, st, jobs, realtime=True)
     sat = jobs[:1000]
-    out["continuous_batching_saturated"] = RenderServer(scenes, st).run(sat, realtime=False)
+    server.stats.clear()
+    out["continuous_batching_saturated"] = server.run(sat, realtime=False)
     out["one_per_launch_saturated"] = serve_one_per_launch(scenes, st, sat, realtime=False)
     return out
 
