@@ -136,8 +136,12 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* d
 // ---------------------------------------------------------------------------
 // Binning kernels
 // ---------------------------------------------------------------------------
+// Per-tile counters live one per 128-byte line (stride kPad words) so that the
+// atomics of different tiles do not serialise on shared cache lines.
+constexpr int kPad = 32;
+
 __global__ void tile_count_kernel(const short4* __restrict__ rect, const uint32_t* __restrict__ tiles, int n_rows,
-                                  ViewsDev vd, uint32_t* __restrict__ tile_cnt) {
+                                  ViewsDev vd, uint32_t* __restrict__ tile_cnt_pad) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rows || tiles[r] == 0u) return;
     const int v = view_of_row(vd, r);
@@ -145,7 +149,12 @@ __global__ void tile_count_kernel(const short4* __restrict__ rect, const uint32_
     const int t0 = vd.tile_off[v];
     const short4 b = rect[r];
     for (int ty = b.y; ty <= b.w; ++ty)
-        for (int tx = b.x; tx <= b.z; ++tx) atomicAdd(&tile_cnt[t0 + ty * gx + tx], 1u);
+        for (int tx = b.x; tx <= b.z; ++tx) atomicAdd(&tile_cnt_pad[(size_t)(t0 + ty * gx + tx) * kPad], 1u);
+}
+
+__global__ void unpad_kernel(const uint32_t* __restrict__ pad, int T, uint32_t* __restrict__ out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T) out[t] = pad[(size_t)t * kPad];
 }
 
 __global__ void emit_kernel(const short4* __restrict__ rect, const uint32_t* __restrict__ tiles,
@@ -163,7 +172,7 @@ __global__ void emit_kernel(const short4* __restrict__ rect, const uint32_t* __r
     for (int ty = b.y; ty <= b.w; ++ty)
         for (int tx = b.x; tx <= b.z; ++tx) {
             const int t = t0 + ty * gx + tx;
-            const int64_t pos = (int64_t)tile_start[t] + atomicAdd(&tile_fill[t], 1u);
+            const int64_t pos = (int64_t)tile_start[t] + atomicAdd(&tile_fill[(size_t)t * kPad], 1u);
             if (pos < cap) bucket[pos] = key;
         }
 }
@@ -269,7 +278,7 @@ __global__ void keys_kernel(const uint2* __restrict__ ranges, int T, const uint3
 }
 
 struct BinWs {
-    uint32_t *tile_cnt, *tile_start, *tile_fill;
+    uint32_t *cnt_pad, *fill_pad, *tile_cnt, *tile_start;
     uint64_t *bucket, *tmp;
     void* scan_tmp;
     size_t bytes;
@@ -280,8 +289,9 @@ static BinWs carve_bin_ws(void* base, int64_t cap, int T) {
     BinWs w;
     const size_t tt = (size_t)(T > 0 ? T : 1);
     const size_t cc = (size_t)(cap > 0 ? cap : 1);
-    w.tile_cnt = c.take<uint32_t>(2 * tt);      // counts and fill cursors, zeroed together
-    w.tile_fill = w.tile_cnt + tt;
+    w.cnt_pad = c.take<uint32_t>(2 * tt * kPad);   // counts and fill cursors, zeroed together
+    w.fill_pad = w.cnt_pad + tt * kPad;
+    w.tile_cnt = c.take<uint32_t>(tt);
     w.tile_start = c.take<uint32_t>(tt);
     w.bucket = c.take<uint64_t>(cc);
     w.tmp = c.take<uint64_t>(cc);
@@ -301,20 +311,22 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
     const int n = vd.row_off[vd.nv];            // projection rows
     const int T = vd.T_total;
     BinWs w = carve_bin_ws(ws, out.capacity, T);
-    cudaError_t e = cudaMemsetAsync(w.tile_cnt, 0, 2 * sizeof(uint32_t) * (size_t)T, stream);
+    cudaError_t e = cudaMemsetAsync(w.cnt_pad, 0, 2 * sizeof(uint32_t) * kPad * (size_t)T, stream);
     if (e != cudaSuccess) return e;
     const int nb = (n + 255) / 256;
     const short4* rect = reinterpret_cast<const short4*>(proj.rect);
     if (n > 0) {
-        tile_count_kernel<<<nb, 256, 0, stream>>>(rect, proj.tiles_touched, n, vd, w.tile_cnt);
+        tile_count_kernel<<<nb, 256, 0, stream>>>(rect, proj.tiles_touched, n, vd, w.cnt_pad);
         note_launch();
     }
+    unpad_kernel<<<(T + 255) / 256, 256, 0, stream>>>(w.cnt_pad, T, w.tile_cnt);
+    note_launch();
     // per-tile ranges: exclusive scan of the counts; the total is M
     e = launch_exclusive_scan(w.tile_cnt, w.tile_start, reinterpret_cast<uint32_t*>(out.count), T, nullptr,
                               w.scan_tmp, stream);
     if (e != cudaSuccess) return e;
     if (n > 0) {
-        emit_kernel<<<nb, 256, 0, stream>>>(rect, proj.tiles_touched, proj.depth, n, vd, w.tile_start, w.tile_fill,
+        emit_kernel<<<nb, 256, 0, stream>>>(rect, proj.tiles_touched, proj.depth, n, vd, w.tile_start, w.fill_pad,
                                             out.capacity, w.bucket);
         note_launch();
     }
