@@ -1,16 +1,14 @@
 // Tile binning and depth sort (Section 3: "sorts points according to
 // view-dependent depth" before alpha compositing).
 //
-// Order produced: instances (row r, tile t) sorted by (t, float32 depth bits
-// of r, r), where a row is a (view, Gaussian) pair of the projection.
-// Design: a most-significant-digit pass of a radix sort on the tile id -- a
-// counting sort: per-tile counts, their exclusive scan (the per-tile ranges),
-// and emission of every instance into its tile's bucket -- followed by one CTA
-// per tile sorting its bucket by the 64-bit key (depth bits << 32 | row) in
-// shared memory (bitonic network; buckets longer than shared memory are sorted
-// in shared-memory chunks that the same CTA then merges).  The keys are
-// distinct, so the order is total and identical to one stable sort of
-// (tile << 32 | depth bits) over instances emitted in row order.
+// Order produced: instances (Gaussian i, tile t) sorted by (t, depth bits of
+// i, i).  Design: a stable LSD radix sort of the N Gaussians on their float32
+// depth bits (32 bits), emission of each Gaussian's instances in that order,
+// then a stable LSD radix sort of the M instances on the tile id only
+// (ceil(log2 T) bits).  Because the second sort is stable and its input is in
+// (depth, i) order, the result equals one stable sort of the 64-bit keys
+// (t << 32 | depth bits) emitted in Gaussian order, at a fraction of the
+// passes over the M instances.
 #include "common.cuh"
 
 namespace sgs {
@@ -134,210 +132,373 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* d
 }
 
 // ---------------------------------------------------------------------------
-// Binning kernels
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs.
+// Each of G blocks owns one contiguous chunk of the items.
+// Per pass: per-block digit histogram -> per-digit exclusive scan over blocks
+// -> stable scatter.  Inside a block, ranks come from warp-level
+// __match_any_sync over 32 consecutive items, accumulated across sub-rounds
+// and across warps in item order, which keeps equal digits in input order.
 // ---------------------------------------------------------------------------
-// Per-tile counters live one per 128-byte line (stride kPad words) so that the
-// atomics of different tiles do not serialise on shared cache lines.
-constexpr int kPad = 32;
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_MAX_BITS = 8;
+constexpr int RS_RADIX_MAX = 1 << RS_MAX_BITS;
+constexpr int RS_MAX_BLOCKS = 1024;
 
-__global__ void tile_count_kernel(const short4* __restrict__ rect, const uint32_t* __restrict__ tiles, int n_rows,
-                                  ViewsDev vd, uint32_t* __restrict__ tile_cnt_pad) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rows || tiles[r] == 0u) return;
-    const int v = view_of_row(vd, r);
-    const int gx = vd.cam[v].gx;
-    const int t0 = vd.tile_off[v];
-    const short4 b = rect[r];
-    for (int ty = b.y; ty <= b.w; ++ty)
-        for (int tx = b.x; tx <= b.z; ++tx) atomicAdd(&tile_cnt_pad[(size_t)(t0 + ty * gx + tx) * kPad], 1u);
+// Up to RS_MAX_BLOCKS blocks; each owns a contiguous chunk rounded only to
+// whole warps, so that the device-side count n (often far below n_max) still
+// spreads over every block and each SM keeps several blocks in flight.
+static int rs_blocks(int64_t n_max) {
+    int64_t b = (n_max + 255) / 256;
+    if (b < 1) b = 1;
+    if (b > RS_MAX_BLOCKS) b = RS_MAX_BLOCKS;
+    return (int)b;
 }
 
-__global__ void unpad_kernel(const uint32_t* __restrict__ pad, int T, uint32_t* __restrict__ out) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < T) out[t] = pad[(size_t)t * kPad];
+__device__ __forceinline__ void rs_chunk(int64_t n, int64_t* start, int64_t* end) {
+    int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    per = (per + 31) / 32 * 32;
+    *start = (int64_t)blockIdx.x * per;
+    *end = min(n, *start + per);
 }
 
-__global__ void emit_kernel(const short4* __restrict__ rect, const uint32_t* __restrict__ tiles,
-                            const float* __restrict__ depth, int n_rows, ViewsDev vd,
-                            const uint32_t* __restrict__ tile_start, uint32_t* __restrict__ tile_fill, int64_t cap,
-                            uint64_t* __restrict__ bucket) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rows || tiles[r] == 0u) return;
-    const int v = view_of_row(vd, r);
-    const int gx = vd.cam[v].gx;
-    const int t0 = vd.tile_off[v];
-    // depth > near_z > 0 for every visible row, so its bits order like the value
-    const uint64_t key = ((uint64_t)__float_as_uint(depth[r]) << 32) | (uint64_t)(uint32_t)r;
-    const short4 b = rect[r];
-    for (int ty = b.y; ty <= b.w; ++ty)
-        for (int tx = b.x; tx <= b.z; ++tx) {
-            const int t = t0 + ty * gx + tx;
-            const int64_t pos = (int64_t)tile_start[t] + atomicAdd(&tile_fill[(size_t)t * kPad], 1u);
-            if (pos < cap) bucket[pos] = key;
-        }
+__global__ void __launch_bounds__(RS_THREADS) radix_hist_kernel(const uint32_t* __restrict__ keys,
+                                                                const int32_t* d_n, int64_t n_host,
+                                                                int64_t cap, int shift, int bits,
+                                                                uint32_t* __restrict__ hist) {
+    __shared__ uint32_t s_cnt[RS_RADIX_MAX];
+    const int radix = 1 << bits;
+    const uint32_t mask = (uint32_t)radix - 1u;
+    for (int d = threadIdx.x; d < radix; d += blockDim.x) s_cnt[d] = 0;
+    __syncthreads();
+    int64_t n = read_n(d_n, n_host, cap), start, end;
+    rs_chunk(n, &start, &end);
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = start; base < end; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        bool valid = i < end;
+        uint32_t d = valid ? ((keys[i] >> shift) & mask) : (uint32_t)radix;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < radix; d += blockDim.x) hist[(size_t)d * gridDim.x + blockIdx.x] = s_cnt[d];
 }
 
-constexpr int TS_THREADS = 256;
-constexpr int TS_CAP = 4096;          // keys sorted at once in shared memory (32 KB)
+// One block per digit: exclusive scan of that digit's counts over the G blocks.
+__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__ hist, int G,
+                                                          uint32_t* __restrict__ digit_tot) {
+    __shared__ uint32_t s_warp[32];
+    uint32_t* h = hist + (size_t)blockIdx.x * G;
+    uint32_t v = threadIdx.x < G ? h[threadIdx.x] : 0u;
+    uint32_t inc = block_inclusive_scan(v, s_warp);
+    if (threadIdx.x < G) h[threadIdx.x] = inc - v;
+    if (threadIdx.x == blockDim.x - 1) digit_tot[blockIdx.x] = inc;
+}
 
-// Ascending bitonic sort of s[0, P) in shared memory (P a power of two).
-__device__ __forceinline__ void bitonic_sort_smem(uint64_t* s, int P) {
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int idx = threadIdx.x; idx < (P >> 1); idx += blockDim.x) {
-                const int i = 2 * idx - (idx & (j - 1));
-                const int p = i + j;
-                const uint64_t a = s[i], b = s[p];
-                const bool up = (i & k) == 0;
-                if ((a > b) == up) {
-                    s[i] = b;
-                    s[p] = a;
+__global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int32_t* d_n,
+    int64_t n_host, int64_t cap, int shift, int bits, const uint32_t* __restrict__ hist,
+    const uint32_t* __restrict__ digit_tot) {
+    __shared__ uint32_t s_warp[RS_WARPS][RS_RADIX_MAX + 1];
+    __shared__ uint32_t s_off[RS_RADIX_MAX];
+    __shared__ uint32_t s_tot[RS_RADIX_MAX];
+    __shared__ uint32_t s_scan[32];
+    const int radix = 1 << bits;
+    const uint32_t mask = (uint32_t)radix - 1u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // digit base = exclusive scan of the digit totals (radix <= RS_THREADS)
+    {
+        uint32_t v = threadIdx.x < radix ? digit_tot[threadIdx.x] : 0u;
+        // block_inclusive_scan assumes <= 32 warps; RS_THREADS = 256
+        uint32_t inc;
+        {
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += t;
+            }
+            if (lane == 31) s_scan[warp] = x;
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t w = lane < RS_WARPS ? s_scan[lane] : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+                    if (lane >= o) w += t;
                 }
+                s_scan[lane] = w;
             }
             __syncthreads();
+            inc = x + (warp > 0 ? s_scan[warp - 1] : 0u);
         }
+        if (threadIdx.x < radix)
+            s_off[threadIdx.x] = (inc - v) + hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
     }
-}
+    __syncthreads();
 
-// Sorts keys[0, L) of one tile into out[0, L) (keys may be reordered).
-// Runs of TS_CAP are sorted in shared memory, then merged pairwise by the CTA
-// (merge path: each thread finds its output range by binary search, then
-// merges serially), ping-ponging between the two buffers.
-__device__ void sort_segment(uint64_t* keys, uint64_t* tmp, int L, uint64_t* s, uint64_t** result) {
-    for (int c = 0; c < L; c += TS_CAP) {
-        const int n = min(TS_CAP, L - c);
-        int P = 1;
-        while (P < n) P <<= 1;
-        for (int k = threadIdx.x; k < P; k += blockDim.x) s[k] = k < n ? keys[c + k] : ~0ull;
+    int64_t n = read_n(d_n, n_host, cap), start, end;
+    rs_chunk(n, &start, &end);
+    for (int64_t tile = start; tile < end; tile += RS_TILE) {
+        for (int k = threadIdx.x; k < RS_WARPS * (RS_RADIX_MAX + 1); k += RS_THREADS)
+            (&s_warp[0][0])[k] = 0u;
         __syncthreads();
-        bitonic_sort_smem(s, P);
-        for (int k = threadIdx.x; k < n; k += blockDim.x) keys[c + k] = s[k];
+        uint32_t key[RS_ITEMS], val[RS_ITEMS], dig[RS_ITEMS], rank[RS_ITEMS];
+        const int64_t wbase = tile + (int64_t)warp * 32 * RS_ITEMS + lane;
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            int64_t idx = wbase + it * 32;
+            bool valid = idx < end;
+            key[it] = valid ? keys_in[idx] : 0u;
+            val[it] = valid ? vals_in[idx] : 0u;
+            dig[it] = valid ? ((key[it] >> shift) & mask) : (uint32_t)radix;
+        }
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
+            unsigned lower = peers & ((1u << lane) - 1u);
+            uint32_t base = s_warp[warp][dig[it]];
+            rank[it] = base + (uint32_t)__popc(lower);
+            __syncwarp();
+            if (lower == 0u) s_warp[warp][dig[it]] = base + (uint32_t)__popc(peers);
+            __syncwarp();
+        }
         __syncthreads();
-    }
-    uint64_t* src = keys;
-    uint64_t* dst = tmp;
-    for (int run = TS_CAP; run < L; run <<= 1) {
-        for (int a0 = 0; a0 < L; a0 += 2 * run) {
-            const int na = min(run, L - a0);
-            const int nb = max(0, min(run, L - a0 - na));
-            const uint64_t* A = src + a0;
-            const uint64_t* Bv = src + a0 + na;
-            const int total = na + nb;
-            const int per = (total + blockDim.x - 1) / blockDim.x;
-            const int k0 = min(total, (int)threadIdx.x * per), k1 = min(total, k0 + per);
-            if (k0 < k1) {
-                // merge path: i elements from A and k0 - i from B precede output k0
-                int lo = max(0, k0 - nb), hi = min(k0, na);
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (A[mid] < Bv[k0 - mid - 1]) lo = mid + 1;
-                    else hi = mid;
-                }
-                int i = lo, j = k0 - lo;
-                for (int k = k0; k < k1; ++k) {
-                    const bool takeA = j >= nb || (i < na && A[i] < Bv[j]);
-                    dst[a0 + k] = takeA ? A[i++] : Bv[j++];
-                }
+        for (int d = threadIdx.x; d < radix; d += RS_THREADS) {
+            uint32_t sum = 0;
+#pragma unroll
+            for (int w = 0; w < RS_WARPS; ++w) {
+                uint32_t c = s_warp[w][d];
+                s_warp[w][d] = sum;
+                sum += c;
+            }
+            s_tot[d] = sum;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            if (dig[it] < (uint32_t)radix) {
+                uint32_t dest = s_off[dig[it]] + s_warp[warp][dig[it]] + rank[it];
+                keys_out[dest] = key[it];
+                vals_out[dest] = val[it];
             }
         }
         __syncthreads();
-        uint64_t* t = src;
-        src = dst;
-        dst = t;
+        for (int d = threadIdx.x; d < radix; d += RS_THREADS) s_off[d] += s_tot[d];
+        __syncthreads();
     }
-    *result = src;
 }
 
-__global__ void __launch_bounds__(TS_THREADS) tile_sort_kernel(const uint32_t* __restrict__ tile_start,
-                                                               const uint32_t* __restrict__ tile_cnt, int T,
-                                                               int64_t cap, uint64_t* __restrict__ bucket,
-                                                               uint64_t* __restrict__ tmp, uint32_t* __restrict__ gids,
-                                                               uint2* __restrict__ ranges) {
-    __shared__ uint64_t s[TS_CAP];
-    const int t = blockIdx.x;
-    if (t >= T) return;
-    const int64_t start = tile_start[t];
-    int64_t end = start + tile_cnt[t];
-    if (end > cap) end = cap;                 // capacity overflow: keep every access in bounds
-    const int L = end > start ? (int)(end - start) : 0;
-    const uint32_t s0 = (uint32_t)(start < cap ? start : cap);   // [s0, s0 + L) lies within capacity
-    if (threadIdx.x == 0) ranges[t] = make_uint2(s0, s0 + (uint32_t)L);
-    if (L == 0) return;
-    uint64_t* res = nullptr;
-    sort_segment(bucket + start, tmp + start, L, s, &res);
-    for (int k = threadIdx.x; k < L; k += blockDim.x) gids[start + k] = (uint32_t)(res[k] & 0xffffffffu);
+struct RadixBufs {
+    uint32_t* hist;       // [RS_RADIX_MAX * RS_MAX_BLOCKS]
+    uint32_t* digit_tot;  // [RS_RADIX_MAX]
+};
+
+static int rs_passes(int total_bits) { return (total_bits + RS_MAX_BITS - 1) / RS_MAX_BITS; }
+
+// Sorts (k[0], v[0]) using (k[1], v[1]) as the ping-pong pair; the result is
+// in pair (passes % 2).  Bits [0, total_bits) are sorted.
+static cudaError_t radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], const int32_t* d_n, int64_t n_host,
+                                    int64_t n_max, int total_bits, const RadixBufs& rb,
+                                    cudaStream_t stream) {
+    if (total_bits <= 0) return cudaSuccess;
+    int G = rs_blocks(n_max);
+    int passes = rs_passes(total_bits);
+    int bits_per = (total_bits + passes - 1) / passes;
+    int shift = 0;
+    for (int p = 0; p < passes; ++p) {
+        int bits = min(bits_per, total_bits - shift);
+        int src = p & 1, dst = src ^ 1;
+        radix_hist_kernel<<<G, RS_THREADS, 0, stream>>>(k[src], d_n, n_host, n_max, shift, bits, rb.hist);
+        note_launch();
+        radix_scan_kernel<<<1 << bits, 1024, 0, stream>>>(rb.hist, G, rb.digit_tot);
+        note_launch();
+        radix_scatter_kernel<<<G, RS_THREADS, 0, stream>>>(k[src], v[src], k[dst], v[dst], d_n, n_host,
+                                                           n_max, shift, bits, rb.hist, rb.digit_tot);
+        note_launch();
+        shift += bits;
+    }
+    return cudaGetLastError();
 }
 
-__global__ void keys_kernel(const uint2* __restrict__ ranges, int T, const uint32_t* __restrict__ gids,
-                            const float* __restrict__ depth, uint64_t* __restrict__ keys) {
-    const int t = blockIdx.x;
-    if (t >= T) return;
-    const uint2 r = ranges[t];
-    for (uint32_t k = r.x + threadIdx.x; k < r.y; k += blockDim.x)
-        keys[k] = ((uint64_t)(uint32_t)t << 32) | (uint64_t)__float_as_uint(depth[gids[k]]);
+// ---------------------------------------------------------------------------
+// Binning kernels
+// ---------------------------------------------------------------------------
+__global__ void visible_flags_kernel(const uint32_t* __restrict__ tiles, int n, uint32_t* __restrict__ flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flag[i] = tiles[i] ? 1u : 0u;
+}
+
+// Compacts the visible Gaussians (in index order) into (depth bits, index)
+// pairs.  depth > near_z > 0 for every visible Gaussian, so its bits order like
+// the value.
+__global__ void depth_keys_kernel(const float* __restrict__ depth, const uint32_t* __restrict__ tiles,
+                                  const uint32_t* __restrict__ pos, int n, uint32_t* __restrict__ keys,
+                                  uint32_t* __restrict__ vals) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || tiles[i] == 0u) return;
+    const uint32_t p = pos[i];
+    keys[p] = __float_as_uint(depth[i]);
+    vals[p] = (uint32_t)i;
+}
+
+__global__ void gather_counts_kernel(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ tiles,
+                                     const int32_t* __restrict__ d_n, int n_max, uint32_t* __restrict__ cnt) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_max) return;
+    cnt[j] = j < *d_n ? tiles[perm[j]] : 0u;
+}
+
+// One thread per depth-sorted projection row: writes the row's instances
+// (global tile id in the row's view, row) in row-major tile order.
+__global__ void emit_kernel(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cnt,
+                            const uint32_t* __restrict__ offs, const short4* __restrict__ rect, int n_rows,
+                            ViewsDev vd, int64_t cap, uint32_t* __restrict__ inst_tile,
+                            uint32_t* __restrict__ inst_gid) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_rows) return;
+    uint32_t c = cnt[j];
+    if (c == 0) return;
+    uint32_t g = perm[j];
+    const int v = view_of_row(vd, g);
+    const int gx = vd.cam[v].gx;
+    const uint32_t t0 = (uint32_t)vd.tile_off[v];
+    short4 r = rect[g];
+    int64_t pos = offs[j];
+    for (int ty = r.y; ty <= r.w; ++ty)
+        for (int tx = r.x; tx <= r.z; ++tx) {
+            if (pos < cap) {
+                inst_tile[pos] = t0 + (uint32_t)(ty * gx + tx);
+                inst_gid[pos] = g;
+            }
+            ++pos;
+        }
+}
+
+__global__ void ranges_kernel(const uint32_t* __restrict__ tile_sorted, const int32_t* d_n, int64_t cap,
+                              uint2* __restrict__ ranges) {
+    int64_t n = read_n(d_n, 0, cap);
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t t = tile_sorted[k];
+        if (k == 0 || tile_sorted[k - 1] != t) ranges[t].x = (uint32_t)k;
+        if (k == n - 1 || tile_sorted[k + 1] != t) ranges[t].y = (uint32_t)(k + 1);
+    }
+}
+
+__global__ void keys_kernel(const uint32_t* __restrict__ tile_sorted, const uint32_t* __restrict__ gids,
+                            const float* __restrict__ depth, const int32_t* d_n, int64_t cap,
+                            uint64_t* __restrict__ keys) {
+    int64_t n = read_n(d_n, 0, cap);
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        keys[k] = ((uint64_t)tile_sorted[k] << 32) | (uint64_t)__float_as_uint(depth[gids[k]]);
+}
+
+static int ceil_log2(int64_t x) {
+    int b = 0;
+    while (((int64_t)1 << b) < x) ++b;
+    return b;
 }
 
 struct BinWs {
-    uint32_t *cnt_pad, *fill_pad, *tile_cnt, *tile_start;
-    uint64_t *bucket, *tmp;
+    uint32_t *dkey[2], *perm[2], *cnt, *offs, *inst_tile[2], *inst_gid_tmp, *n_vis;
     void* scan_tmp;
+    RadixBufs rb;
     size_t bytes;
 };
 
-static BinWs carve_bin_ws(void* base, int64_t cap, int T) {
+static BinWs carve_bin_ws(void* base, int n, int64_t cap) {
     Carver c{reinterpret_cast<char*>(base), 0};
     BinWs w;
-    const size_t tt = (size_t)(T > 0 ? T : 1);
-    const size_t cc = (size_t)(cap > 0 ? cap : 1);
-    w.cnt_pad = c.take<uint32_t>(2 * tt * kPad);   // counts and fill cursors, zeroed together
-    w.fill_pad = w.cnt_pad + tt * kPad;
-    w.tile_cnt = c.take<uint32_t>(tt);
-    w.tile_start = c.take<uint32_t>(tt);
-    w.bucket = c.take<uint64_t>(cc);
-    w.tmp = c.take<uint64_t>(cc);
-    w.scan_tmp = c.take<char>(scan_tmp_bytes(T));
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    size_t cc = (size_t)(cap > 0 ? cap : 1);
+    w.dkey[0] = c.take<uint32_t>(nn);
+    w.dkey[1] = c.take<uint32_t>(nn);
+    w.perm[0] = c.take<uint32_t>(nn);
+    w.perm[1] = c.take<uint32_t>(nn);
+    w.cnt = c.take<uint32_t>(nn);
+    w.offs = c.take<uint32_t>(nn);
+    w.inst_tile[0] = c.take<uint32_t>(cc);
+    w.inst_tile[1] = c.take<uint32_t>(cc);
+    w.inst_gid_tmp = c.take<uint32_t>(cc);
+    w.n_vis = c.take<uint32_t>(1);
+    w.scan_tmp = c.take<char>(scan_tmp_bytes(n));
+    w.rb.hist = c.take<uint32_t>((size_t)RS_RADIX_MAX * RS_MAX_BLOCKS);
+    w.rb.digit_tot = c.take<uint32_t>(RS_RADIX_MAX);
     w.bytes = c.off + 256;
     return w;
 }
 
 size_t bin_sort_ws_bytes(int n, int64_t capacity, int num_tiles) {
-    (void)n;
-    return carve_bin_ws(nullptr, capacity, num_tiles).bytes;
+    (void)num_tiles;
+    return carve_bin_ws(nullptr, n, capacity).bytes;
 }
 
 cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetDev& st, const sgs_bins& out, void* ws,
                             cudaStream_t stream) {
     (void)st;
     const int n = vd.row_off[vd.nv];            // projection rows
+    BinWs w = carve_bin_ws(ws, n, out.capacity);
     const int T = vd.T_total;
-    BinWs w = carve_bin_ws(ws, out.capacity, T);
-    cudaError_t e = cudaMemsetAsync(w.cnt_pad, 0, 2 * sizeof(uint32_t) * kPad * (size_t)T, stream);
+    cudaError_t e = cudaMemsetAsync(out.ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, stream);
     if (e != cudaSuccess) return e;
+    if (n == 0) return cudaMemsetAsync(out.count, 0, sizeof(int32_t), stream);
     const int nb = (n + 255) / 256;
-    const short4* rect = reinterpret_cast<const short4*>(proj.rect);
-    if (n > 0) {
-        tile_count_kernel<<<nb, 256, 0, stream>>>(rect, proj.tiles_touched, n, vd, w.cnt_pad);
-        note_launch();
-    }
-    unpad_kernel<<<(T + 255) / 256, 256, 0, stream>>>(w.cnt_pad, T, w.tile_cnt);
+    const int32_t* d_nvis = reinterpret_cast<const int32_t*>(w.n_vis);
+    // 1. compact the visible Gaussians, then a stable sort of them by depth bits
+    visible_flags_kernel<<<nb, 256, 0, stream>>>(proj.tiles_touched, n, w.cnt);
     note_launch();
-    // per-tile ranges: exclusive scan of the counts; the total is M
-    e = launch_exclusive_scan(w.tile_cnt, w.tile_start, reinterpret_cast<uint32_t*>(out.count), T, nullptr,
+    e = launch_exclusive_scan(w.cnt, w.offs, w.n_vis, n, nullptr, w.scan_tmp, stream);
+    if (e != cudaSuccess) return e;
+    depth_keys_kernel<<<nb, 256, 0, stream>>>(proj.depth, proj.tiles_touched, w.offs, n, w.dkey[0], w.perm[0]);
+    note_launch();
+    e = radix_sort_pairs(w.dkey, w.perm, d_nvis, 0, n, 32, w.rb, stream);
+    if (e != cudaSuccess) return e;
+    const uint32_t* perm = w.perm[rs_passes(32) & 1];
+    // 2. instance offsets in depth order, M
+    gather_counts_kernel<<<nb, 256, 0, stream>>>(perm, proj.tiles_touched, d_nvis, n, w.cnt);
+    note_launch();
+    e = launch_exclusive_scan(w.cnt, w.offs, reinterpret_cast<uint32_t*>(out.count), n, nullptr,
                               w.scan_tmp, stream);
     if (e != cudaSuccess) return e;
-    if (n > 0) {
-        emit_kernel<<<nb, 256, 0, stream>>>(rect, proj.tiles_touched, proj.depth, n, vd, w.tile_start, w.fill_pad,
-                                            out.capacity, w.bucket);
-        note_launch();
+    // 3. emit (tile, gid) instances in depth order; the tile sort's result must
+    //    land in out.gids, so pick the starting buffer by the pass parity.
+    const int tile_bits = ceil_log2(T);
+    const int tpasses = rs_passes(tile_bits);
+    uint32_t* gk[2];
+    uint32_t* gv[2];
+    gk[0] = w.inst_tile[0];
+    gk[1] = w.inst_tile[1];
+    if (tpasses % 2 == 0) {
+        gv[0] = out.gids;
+        gv[1] = w.inst_gid_tmp;
+    } else {
+        gv[0] = w.inst_gid_tmp;
+        gv[1] = out.gids;
     }
-    tile_sort_kernel<<<T, TS_THREADS, 0, stream>>>(w.tile_start, w.tile_cnt, T, out.capacity, w.bucket, w.tmp,
-                                                   out.gids, reinterpret_cast<uint2*>(out.ranges));
+    emit_kernel<<<nb, 256, 0, stream>>>(perm, w.cnt, w.offs, reinterpret_cast<const short4*>(proj.rect), n, vd,
+                                        out.capacity, gk[0], gv[0]);
     note_launch();
-    if (out.keys) {
-        keys_kernel<<<T, 128, 0, stream>>>(reinterpret_cast<const uint2*>(out.ranges), T, out.gids, proj.depth,
+    // 4. stable sort of the instances by tile id
+    e = radix_sort_pairs(gk, gv, out.count, 0, out.capacity, tile_bits, w.rb, stream);
+    if (e != cudaSuccess) return e;
+    const uint32_t* tile_sorted = gk[tpasses & 1];
+    // 5. per-tile ranges and optional 64-bit keys
+    int rb = 152 * 8;
+    ranges_kernel<<<rb, 256, 0, stream>>>(tile_sorted, out.count, out.capacity,
+                                          reinterpret_cast<uint2*>(out.ranges));
+    note_launch();
+    if (out.keys)
+        keys_kernel<<<rb, 256, 0, stream>>>(tile_sorted, out.gids, proj.depth, out.count, out.capacity,
                                             out.keys);
         note_launch();
-    }
     return cudaGetLastError();
 }
 
