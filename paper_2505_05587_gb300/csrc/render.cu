@@ -75,50 +75,10 @@ __device__ __forceinline__ float4 alpha_support_box(float4 m, float4 co, float a
     return make_float4(cx - ex, cx + ex, cy - ey, cy + ey);
 }
 
-// Support of a staged Gaussian: its ellipse d^T Q d <= m2 (m2 = 2 ln(o /
-// alpha_min), widened like the box) with the box around it.
-__device__ __forceinline__ float4 alpha_support_ellipse(float4 co, float alpha_min) {
-    const float o = co.w;
-    if (!(o >= alpha_min)) return make_float4(co.x, co.y, co.z, -1.0f);
-    if (!(alpha_min > 0.0f)) return make_float4(co.x, co.y, co.z, 1e30f);
-    return make_float4(co.x, co.y, co.z, 2.0f * logf(o / alpha_min) * 1.001f + 1e-3f);
-}
-
-// Does the ellipse d^T Q d <= m2 around (mx, my) meet the pixel box
-// [x0, x1] x [y0, y1]?  The convex quadratic's minimum over the box is 0 when
-// the centre lies inside, else it is on an edge, at the stationary point of
-// that edge clamped to it.
-__device__ __forceinline__ bool ellipse_meets_box(float4 e, float mx, float my, float x0, float x1, float y0,
-                                                  float y1) {
-    const float dx0 = x0 - mx, dx1 = x1 - mx, dy0 = y0 - my, dy1 = y1 - my;
-    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return e.w >= 0.0f;
-    const float a = e.x, b = e.y, c = e.z;
-    const float ia = 1.0f / a, ic = 1.0f / c;
-    float m = 3.0e38f;
-    {
-        const float dy = fminf(fmaxf(-b * dx0 * ic, dy0), dy1);
-        m = fminf(m, (a * dx0 + 2.0f * b * dy) * dx0 + c * dy * dy);
-    }
-    {
-        const float dy = fminf(fmaxf(-b * dx1 * ic, dy0), dy1);
-        m = fminf(m, (a * dx1 + 2.0f * b * dy) * dx1 + c * dy * dy);
-    }
-    {
-        const float dx = fminf(fmaxf(-b * dy0 * ia, dx0), dx1);
-        m = fminf(m, (a * dx + 2.0f * b * dy0) * dx + c * dy0 * dy0);
-    }
-    {
-        const float dx = fminf(fmaxf(-b * dy1 * ia, dx0), dx1);
-        m = fminf(m, (a * dx + 2.0f * b * dy1) * dx + c * dy1 * dy1);
-    }
-    return m <= e.w * 1.0001f + 1e-4f;
-}
-
-// Order-preserving list of the batch entries whose alpha support meets the
-// warp's pixel block [bx, bx+7] x [by, by+3] (box test, then the exact ellipse
-// test).  Returns the list length.
-__device__ __forceinline__ int build_warp_list(const float4* s_box, const float4* s_ell, const float4* s_xy, int cnt,
-                                               float bx, float by, uint8_t* list) {
+// Order-preserving list of the batch entries whose support box meets the
+// warp's pixel block [bx, bx+7] x [by, by+3].  Returns the list length.
+__device__ __forceinline__ int build_warp_list(const float4* s_box, int cnt, float bx, float by,
+                                               uint8_t* list) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     int nl = 0;
@@ -128,10 +88,6 @@ __device__ __forceinline__ int build_warp_list(const float4* s_box, const float4
         if (e < cnt) {
             const float4 b = s_box[e];
             hit = b.y >= bx && b.x <= bx + 7.0f && b.w >= by && b.z <= by + 3.0f;
-            if (hit) {
-                const float4 m = s_xy[e];
-                hit = ellipse_meets_box(s_ell[e], m.x + m.z, m.y + m.w, bx, bx + 7.0f, by, by + 3.0f);
-            }
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) list[nl + __popc(m & lt)] = (uint8_t)e;
@@ -141,13 +97,13 @@ __device__ __forceinline__ int build_warp_list(const float4* s_box, const float4
     return nl;
 }
 
+
 template <int BATCH, int NW>
 struct FwdSmem {
     float4 xy[BATCH];
     float4 co[BATCH];
     float4 rgb[BATCH];
     float4 box[BATCH];
-    float4 ell[BATCH];
     uint8_t list[NW][BATCH];
 };
 
@@ -158,7 +114,6 @@ struct BwdSmem {
     float4 co[BATCH];
     float4 rgb[BATCH];
     float4 box[BATCH];
-    float4 ell[BATCH];
     uint8_t list[NW][BATCH];
     uint32_t maxl;
 };
@@ -194,11 +149,10 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
             sm.co[k] = conic_exp2(co);
             sm.rgb[k] = rgb[g];
             sm.box[k] = alpha_support_box(m, co, st.alpha_min);
-            sm.ell[k] = alpha_support_ellipse(co, st.alpha_min);
         }
         __syncthreads();
         if (__all_sync(0xffffffffu, done)) continue;
-        const int nl = build_warp_list(sm.box, sm.ell, sm.xy, cnt, (float)bx, (float)by, sm.list[warp]);
+        const int nl = build_warp_list(sm.box, cnt, (float)bx, (float)by, sm.list[warp]);
         for (int k = 0; k < nl && !done; ++k) {
             const int j = sm.list[warp][k];
             const float4 m = sm.xy[j];
@@ -314,10 +268,9 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
             sm.co[k] = conic_exp2(co);
             sm.rgb[k] = rgb[g];
             sm.box[k] = alpha_support_box(m, co, st.alpha_min);
-            sm.ell[k] = alpha_support_ellipse(co, st.alpha_min);
         }
         __syncthreads();
-        const int nl = build_warp_list(sm.box, sm.ell, sm.xy, cnt, (float)bx, (float)by, sm.list[warp]);
+        const int nl = build_warp_list(sm.box, cnt, (float)bx, (float)by, sm.list[warp]);
         for (int k = nl - 1; k >= 0; --k) {
             const int e = sm.list[warp][k];
             const float4 m = sm.xy[e];
