@@ -77,7 +77,7 @@ def _load():
             lib.orc_eig3_min.argtypes = [P, C.c_double, C.c_int, P, P]
             lib.orc_jacobi3.argtypes = [P, C.c_int, P, P]
             lib.orc_split.restype = C.c_int
-            lib.orc_split.argtypes = [P, P, P, C.c_double, C.c_double, P, C.c_double,
+            lib.orc_split.argtypes = [P, P, P, C.c_double, C.c_double, P, C.c_double, C.c_int64,
                                       P, P, P, P, P, P, P]
             lib.orc_sh_basis.argtypes = [C.c_int, P, C.c_int, P, P]
             _lib = lib
@@ -257,8 +257,9 @@ def jacobi3(S):
     return ev, V
 
 
-def split(scene, lam, v, eps_split, step_scale=1.0, grad_norm=None, eps_grad=0.0):
-    """Steepest density control split and compaction (Theorem 2, Algorithm 1)."""
+def split(scene, lam, v, eps_split, step_scale=1.0, grad_norm=None, eps_grad=0.0, budget=0):
+    """Steepest density control split and compaction (Theorem 2, Algorithm 1);
+    budget > 0 keeps only the `budget` least lambda_min (Variants section)."""
     lib = _load()
     b = _Bound(scene, None, None)
     n, K = scene.n, (scene.sh_degree + 1) ** 2
@@ -271,7 +272,7 @@ def split(scene, lam, v, eps_split, step_scale=1.0, grad_norm=None, eps_grad=0.0
     v = np.ascontiguousarray(v, np.float64)
     gn = None if grad_norm is None else np.ascontiguousarray(grad_norm, np.float64)
     n_out = lib.orc_split(C.byref(b.scene), _ptr(lam), _ptr(v), float(eps_split), float(step_scale),
-                          _ptr(gn), float(eps_grad), _ptr(out["means"]), _ptr(out["log_scales"]),
+                          _ptr(gn), float(eps_grad), int(budget), _ptr(out["means"]), _ptr(out["log_scales"]),
                           _ptr(out["quats"]), _ptr(out["opacity_logit"]), _ptr(out["sh"]),
                           _ptr(out["parent"]), _ptr(flags))
     for k in list(out):

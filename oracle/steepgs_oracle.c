@@ -1056,8 +1056,19 @@ void orc_jacobi3(const double *S, int n, double *evals, double *evecs)
 /* logit(o/2) = -log(1 + 2 exp(-x)).                                         */
 /* ------------------------------------------------------------------------ */
 
+/* Increment budget (the "Densification with Increment Budget" variant): when
+ * more than `budget` Gaussians qualify, only the `budget` ones with the least
+ * lambda_min are split (ties by index). */
+static const double *g_sel_lam;
+static int sel_cmp(const void *pa, const void *pb)
+{
+    int a = *(const int *)pa, b = *(const int *)pb;
+    if (g_sel_lam[a] != g_sel_lam[b]) return g_sel_lam[a] < g_sel_lam[b] ? -1 : 1;
+    return a < b ? -1 : (a > b);
+}
+
 int orc_split(const orc_scene *sc, const double *lam, const double *v, double eps_split,
-              double step_scale, const double *grad_norm, double eps_grad,
+              double step_scale, const double *grad_norm, double eps_grad, int64_t budget,
               double *out_means, double *out_log_scales, double *out_quats,
               double *out_logit, double *out_sh, int32_t *parent, uint8_t *flags)
 {
@@ -1065,12 +1076,26 @@ int orc_split(const orc_scene *sc, const double *lam, const double *v, double ep
     int K = (sc->sh_degree + 1) * (sc->sh_degree + 1);
     int32_t *excl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     int32_t run = 0;
+    int cand = 0;
     for (int i = 0; i < n; ++i) {
         int f = lam[i] < eps_split;
         if (grad_norm) f = f && (grad_norm[i] <= eps_grad);
         flags[i] = (uint8_t)f;
+        cand += f;
+    }
+    if (budget > 0 && cand > budget) {
+        int *idx = (int *)malloc(sizeof(int) * (size_t)cand);
+        int m = 0;
+        for (int i = 0; i < n; ++i)
+            if (flags[i]) idx[m++] = i;
+        g_sel_lam = lam;
+        qsort(idx, (size_t)cand, sizeof(int), sel_cmp);
+        for (int k = (int)budget; k < cand; ++k) flags[idx[k]] = 0;
+        free(idx);
+    }
+    for (int i = 0; i < n; ++i) {
         excl[i] = run;
-        run += f;
+        run += flags[i];
     }
     for (int i = 0; i < n; ++i) {
         double p[3], e = 0.0;

@@ -517,3 +517,36 @@ def test_split_output_invariants():
     gn = np.random.default_rng(0).uniform(size=n)
     out2 = oracle.split(sc, lam, v, -1e-6, 0.5, grad_norm=gn, eps_grad=0.5)
     assert np.array_equal(out2["flags"], flags & (gn <= 0.5))
+
+
+def test_increment_budget_is_the_best_k_subset():
+    """Increment budget (Appendix, "Densification with Increment Budget"): the
+    second-order loss change of splitting Gaussian i along v_min is
+    proportional to lambda_min(S_i), so among all admissible subsets of at
+    most K candidates the chosen one has the least sum of lambda_min.  Brute
+    force over every subset of a 9-Gaussian scene, with tied values and the
+    gradient gate in play; among optimal subsets the lexicographically first
+    by index."""
+    import itertools
+    sc = synth.tiny_scene(0)
+    sc = synth.subset(sc, slice(0, 9))
+    rng = np.random.default_rng(4)
+    v = rng.normal(size=(9, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    lam = np.array([-3.0, 0.5, -1.0, -3.0, -2.0, -1.0, 0.0, -1.0, -4.0])
+    gn = np.array([0.1, 0.1, 0.1, 0.1, 0.9, 0.1, 0.1, 0.1, 0.1])
+    for eps_grad, gate in ((0.0, None), (0.5, gn)):
+        base = oracle.split(sc, lam, v, 0.0, grad_norm=gate, eps_grad=eps_grad)["flags"]
+        cand = np.nonzero(base)[0]
+        for K in range(1, len(cand) + 2):
+            got = oracle.split(sc, lam, v, 0.0, grad_norm=gate, eps_grad=eps_grad, budget=K)
+            best = None
+            for r in range(0, min(K, len(cand)) + 1):
+                for sub in itertools.combinations(cand, r):
+                    key = (lam[list(sub)].sum(), -len(sub), tuple(sub))
+                    best = key if best is None or key < best else best
+            want = np.zeros(9, bool)
+            want[list(best[2])] = True
+            assert np.array_equal(got["flags"], want), (eps_grad, K)
+            assert got["n_out"] == 9 + want.sum()
+            assert np.array_equal(got["parent"][9:], np.nonzero(want)[0])
