@@ -273,7 +273,10 @@ int sgs_densify_split_workspace_size(int32_t n, size_t *bytes);
  * "Eigendecomposition").  For each Gaussian: S_bar = S_accum * inv_T_split;
  * lambda_min, v_min by the trigonometric root formula (float32) refined by
  * one Rayleigh quotient; flag = lambda_min < eps_split, and, when grad_norm is
- * not NULL, grad_norm[i] <= eps_grad (the "compactest" condition).
+ * not NULL, grad_norm[i] <= eps_grad (the "compactest" condition).  When
+ * max_splits > 0 and more Gaussians are flagged, only the max_splits with the
+ * least lambda_min stay flagged, ties by index (the "increment budget"
+ * variant); max_splits <= 0 means no budget.
  * Output rows: row i = Gaussian i, moved to p + eps_i v_min with opacity o/2
  * when flagged; row N + excl[i] = its second offspring p - eps_i v_min with
  * opacity o/2 (excl = exclusive prefix sum of the flags); scales, rotation and
@@ -284,7 +287,7 @@ int sgs_densify_split_workspace_size(int32_t n, size_t *bytes);
  * `out` must not alias `in`.  Errors: SGS_ERR_INVALID_ARG, SGS_ERR_WORKSPACE. */
 int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, float inv_T_split,
                       float eps_split, float step_scale, const float *grad_norm, float eps_grad,
-                      const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
+                      int64_t max_splits, const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
                       int32_t *parent_index, float *lam_min_out, float *v_min_out,
                       void *ws, size_t ws_bytes, void *stream);
 
@@ -306,10 +309,10 @@ int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, float inv_T
  *     (other streams, other threads) race: serialise them.
  *   - It calls no cudaMalloc, cudaFree or allocating routine. */
 #define SGS_NOALLOC_MAX_GAUSSIANS 1000000
-#define SGS_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
+#define SGS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int sgs_densify_split_noalloc(const sgs_gaussians *in, const float *S_accum, float inv_T_split,
                               float eps_split, float step_scale, const float *grad_norm, float eps_grad,
-                              const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
+                              int64_t max_splits, const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
                               int32_t *parent_index, float *lam_min_out, float *v_min_out, void *stream);
 
 #ifdef __cplusplus

@@ -99,7 +99,7 @@ def lib():
         L.sgs_render_bwd_workspace_size.argtypes = [I32, C.POINTER(SZ)]
         L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, I32, P, P, SZ, P]
         L.sgs_densify_split_workspace_size.argtypes = [I32, C.POINTER(SZ)]
-        L.sgs_densify_split.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P, SZ, P]
+        L.sgs_densify_split.argtypes = [P, P, F, F, F, P, F, I64, P, I64, P, P, P, P, P, SZ, P]
         L.sgs_render_views_workspace_size.argtypes = [I32, P, I32, P, I64, C.POINTER(SZ)]
         L.sgs_render_views_workspace_size.restype = C.c_int
         L.sgs_render_views_with_splitting.argtypes = [P, P, I32, P, I32, P, P, P, P, I32, P, P, I64, P, SZ, P]
@@ -110,7 +110,7 @@ def lib():
         L.sgs_render_batch_fwd.restype = C.c_int
         L.sgs_adam_step.argtypes = [P, P, P, P, I64, F, F, F, F, I32, P, P]
         L.sgs_adam_step.restype = C.c_int
-        L.sgs_densify_split_noalloc.argtypes = [P, P, F, F, F, P, F, P, I64, P, P, P, P, P]
+        L.sgs_densify_split_noalloc.argtypes = [P, P, F, F, F, P, F, I64, P, I64, P, P, P, P, P]
         for name in ("sgs_project", "sgs_bin_sort_workspace_size", "sgs_bin_sort", "sgs_render_fwd",
                      "sgs_l1_loss_grad", "sgs_render_stats", "sgs_render_bwd_workspace_size", "sgs_render_bwd_with_splitting",
                      "sgs_densify_split_workspace_size", "sgs_densify_split", "sgs_densify_split_noalloc"):
@@ -382,11 +382,11 @@ def densify_split_workspace_size(n: int) -> int:
 
 def densify_split(g: GaussianTensors, S_accum, inv_T_split: float, eps_split: float, step_scale: float,
                   grad_norm, eps_grad: float, out: GaussianTensors, capacity: int, d_n_out, parent_index,
-                  lam_min_out, v_min_out, ws, stream=None):
+                  lam_min_out, v_min_out, ws, stream=None, max_splits: int = 0):
     gc, oc = g.c(), out.c_mut()
     _check("sgs_densify_split",
            lib().sgs_densify_split(C.byref(gc), _p(S_accum), inv_T_split, eps_split, step_scale, _p(grad_norm),
-                                   eps_grad, C.byref(oc), capacity, _p(d_n_out), _p(parent_index),
+                                   eps_grad, int(max_splits), C.byref(oc), capacity, _p(d_n_out), _p(parent_index),
                                    _p(lam_min_out), _p(v_min_out), _p(ws), ws.numel() * ws.element_size(),
                                    _stream(stream)))
 
@@ -398,14 +398,14 @@ def kernel_launches() -> int:
 
 def densify_split_noalloc(g: GaussianTensors, S_accum, inv_T_split: float, eps_split: float, step_scale: float,
                           grad_norm, eps_grad: float, out: GaussianTensors, capacity: int, d_n_out, parent_index,
-                          lam_min_out, v_min_out, stream=None):
+                          lam_min_out, v_min_out, stream=None, max_splits: int = 0):
     """densify_split without a workspace, for callers that cannot allocate one
     (its scratch is a fixed array inside the library; n <= 1,000,000; calls
     that overlap on the GPU race)."""
     gc, oc = g.c(), out.c_mut()
     _check("sgs_densify_split_noalloc",
            lib().sgs_densify_split_noalloc(C.byref(gc), _p(S_accum), inv_T_split, eps_split, step_scale,
-                                           _p(grad_norm), eps_grad, C.byref(oc), capacity, _p(d_n_out),
+                                           _p(grad_norm), eps_grad, int(max_splits), C.byref(oc), capacity, _p(d_n_out),
                                            _p(parent_index), _p(lam_min_out), _p(v_min_out), _stream(stream)))
 
 

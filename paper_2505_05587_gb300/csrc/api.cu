@@ -394,7 +394,8 @@ int sgs_densify_split_workspace_size(int32_t n, size_t* bytes) {
 }
 
 int sgs_densify_split(const sgs_gaussians* in, const float* S_accum, float inv_T_split, float eps_split,
-                      float step_scale, const float* grad_norm, float eps_grad, const sgs_gaussians_mut* out,
+                      float step_scale, const float* grad_norm, float eps_grad, int64_t max_splits,
+                      const sgs_gaussians_mut* out,
                       int64_t capacity, int32_t* d_n_out, int32_t* parent_index, float* lam_min_out,
                       float* v_min_out, void* ws, size_t ws_bytes, void* stream) {
     if (!valid_gaussians(in) || !out || !d_n_out || capacity < in->n || !isfinite(inv_T_split) ||
@@ -406,7 +407,8 @@ int sgs_densify_split(const sgs_gaussians* in, const float* S_accum, float inv_T
     if (in->n > 0 && (out->means == in->means || out->sh == in->sh || out->opacity_logit == in->opacity_logit))
         return SGS_ERR_INVALID_ARG;
     if (!ws || ws_bytes < densify_ws_bytes(in->n)) return SGS_ERR_WORKSPACE;
-    return cuda_status(launch_densify(*in, S_accum, inv_T_split, eps_split, step_scale, grad_norm, eps_grad, *out,
+    return cuda_status(launch_densify(*in, S_accum, inv_T_split, eps_split, step_scale, grad_norm, eps_grad,
+                                      max_splits, *out,
                                       capacity, d_n_out, parent_index, lam_min_out, v_min_out, ws,
                                       (cudaStream_t)stream));
 }

@@ -152,7 +152,7 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t co
 
 size_t densify_ws_bytes(int n);
 cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T, float eps_split,
-                           float step_scale, const float* grad_norm, float eps_grad,
+                           float step_scale, const float* grad_norm, float eps_grad, int64_t max_splits,
                            const sgs_gaussians_mut& out, int64_t capacity, int32_t* d_n_out,
                            int32_t* parent, float* lam_out, float* v_out, void* ws,
                            cudaStream_t stream);

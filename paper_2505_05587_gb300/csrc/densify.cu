@@ -119,6 +119,81 @@ __global__ void __launch_bounds__(256) eig_flag_kernel(const float* __restrict__
     flags[i] = f ? 1u : 0u;
 }
 
+// ---------------------------------------------------------------------------
+// Increment budget (the "Densification with Increment Budget" variant): when
+// more than K Gaussians are flagged, keep the K with the least lambda_min,
+// ties by index.  A 4-pass radix select (8-bit digits, most significant
+// first) over order-preserving keys of lambda finds the K-th smallest key on
+// the device; ties at that key are admitted in index order through a scan.
+// ---------------------------------------------------------------------------
+struct SelectState {
+    uint32_t active;    // 1 when the budget binds
+    uint32_t prefix;    // key digits fixed so far
+    uint32_t k_rem;     // rank still sought among keys matching the prefix
+    uint32_t pad;
+    uint32_t hist[256];
+};
+
+__device__ __forceinline__ uint32_t order_key(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void select_init_kernel(const uint32_t* __restrict__ total, int64_t K, SelectState* st) {
+    if (threadIdx.x == 0) {
+        st->active = (int64_t)(*total) > K ? 1u : 0u;
+        st->prefix = 0u;
+        st->k_rem = (uint32_t)K;
+    }
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) st->hist[b] = 0u;
+}
+
+__global__ void __launch_bounds__(256) select_hist_kernel(const float* __restrict__ lam,
+                                                          const uint32_t* __restrict__ flags, int n, int shift,
+                                                          SelectState* st) {
+    __shared__ uint32_t h[256];
+    if (!st->active) return;
+    h[threadIdx.x] = 0u;
+    __syncthreads();
+    const uint32_t hi_mask = shift + 8 >= 32 ? 0u : ~((1u << (shift + 8)) - 1u);
+    const uint32_t prefix = st->prefix;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!flags[i]) continue;
+        const uint32_t k = order_key(lam[i]);
+        if ((k & hi_mask) == (prefix & hi_mask)) atomicAdd(&h[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void select_pick_kernel(int shift, SelectState* st) {
+    if (!st->active || threadIdx.x != 0) return;
+    uint32_t before = 0u;
+    int b = 0;
+    for (; b < 255; ++b) {
+        if (before + st->hist[b] >= st->k_rem) break;
+        before += st->hist[b];
+    }
+    st->prefix |= (uint32_t)b << shift;
+    st->k_rem -= before;
+    for (int k = 0; k < 256; ++k) st->hist[k] = 0u;
+}
+
+__global__ void select_ties_kernel(const float* __restrict__ lam, const uint32_t* __restrict__ flags, int n,
+                                   const SelectState* st, uint32_t* __restrict__ tie) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    tie[i] = (st->active && flags[i] && order_key(lam[i]) == st->prefix) ? 1u : 0u;
+}
+
+__global__ void select_apply_kernel(const float* __restrict__ lam, uint32_t* __restrict__ flags, int n,
+                                    const SelectState* st, const uint32_t* __restrict__ tie_rank) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !st->active || !flags[i]) return;
+    const uint32_t k = order_key(lam[i]);
+    flags[i] = (k < st->prefix || (k == st->prefix && tie_rank[i] < st->k_rem)) ? 1u : 0u;
+}
+
 __global__ void n_out_kernel(const uint32_t* __restrict__ total, int n, int32_t* __restrict__ d_n_out) {
     *d_n_out = n + (int32_t)(*total);
 }
@@ -199,11 +274,13 @@ size_t densify_ws_bytes(int n) {
     c.take<float>(nn);          // lam (when the caller passes none)
     c.take<float>(3 * nn);      // v
     c.take<char>(scan_tmp_bytes(n));
+    c.take<uint32_t>(nn);       // ties at the budget threshold
+    c.take<SelectState>(1);
     return c.off + 256;
 }
 
 cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T, float eps_split,
-                           float step_scale, const float* grad_norm, float eps_grad,
+                           float step_scale, const float* grad_norm, float eps_grad, int64_t max_splits,
                            const sgs_gaussians_mut& out, int64_t capacity, int32_t* d_n_out, int32_t* parent,
                            float* lam_out, float* v_out, void* ws, cudaStream_t stream) {
     const int n = in.n;
@@ -215,6 +292,8 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T,
     float* lam_ws = c.take<float>(nn);
     float* v_ws = c.take<float>(3 * nn);
     void* scan_tmp = c.take<char>(scan_tmp_bytes(n));
+    uint32_t* tie = c.take<uint32_t>(nn);
+    SelectState* sel = c.take<SelectState>(1);
     float* lam = lam_out ? lam_out : lam_ws;
     float* v = v_out ? v_out : v_ws;
     if (n == 0) return cudaMemsetAsync(d_n_out, 0, sizeof(int32_t), stream);
@@ -223,6 +302,25 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T,
     note_launch();
     cudaError_t e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
     if (e != cudaSuccess) return e;
+    if (max_splits > 0) {
+        select_init_kernel<<<1, 256, 0, stream>>>(total, max_splits, sel);
+        note_launch();
+        const int hb = nb < 152 * 4 ? nb : 152 * 4;
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            select_hist_kernel<<<hb, 256, 0, stream>>>(lam, flags, n, shift, sel);
+            note_launch();
+            select_pick_kernel<<<1, 32, 0, stream>>>(shift, sel);
+            note_launch();
+        }
+        select_ties_kernel<<<nb, 256, 0, stream>>>(lam, flags, n, sel, tie);
+        note_launch();
+        e = launch_exclusive_scan(tie, excl, nullptr, n, nullptr, scan_tmp, stream);
+        if (e != cudaSuccess) return e;
+        select_apply_kernel<<<nb, 256, 0, stream>>>(lam, flags, n, sel, excl);
+        note_launch();
+        e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
+        if (e != cudaSuccess) return e;
+    }
     n_out_kernel<<<1, 1, 0, stream>>>(total, n, d_n_out);
     note_launch();
     const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;

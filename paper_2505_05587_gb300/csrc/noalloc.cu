@@ -15,8 +15,8 @@
 namespace sgs {
 
 // Scratch for sgs_densify_split_noalloc: split flags, their prefix sum, the
-// eigenpairs when the caller passes no output for them, and the scan's block
-// partials -- about 24 bytes per Gaussian.
+// eigenpairs when the caller passes no output for them, the budget's tie
+// flags and the scan's block partials -- about 28 bytes per Gaussian.
 static __device__ __align__(256) unsigned char g_densify_scratch[SGS_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
@@ -48,7 +48,8 @@ using namespace sgs;
 
 extern "C" int sgs_densify_split_noalloc(const sgs_gaussians* in, const float* S_accum, float inv_T_split,
                                          float eps_split, float step_scale, const float* grad_norm,
-                                         float eps_grad, const sgs_gaussians_mut* out, int64_t capacity,
+                                         float eps_grad, int64_t max_splits, const sgs_gaussians_mut* out,
+                                         int64_t capacity,
                                          int32_t* d_n_out, int32_t* parent_index, float* lam_min_out,
                                          float* v_min_out, void* stream) {
     if (!in || in->n < 0 || in->n > SGS_NOALLOC_MAX_GAUSSIANS) return SGS_ERR_INVALID_ARG;
@@ -56,7 +57,8 @@ extern "C" int sgs_densify_split_noalloc(const sgs_gaussians* in, const float* S
     void* ws = nullptr;
     int ce = scratch_address(&ws);
     if (ce != 0) return record_cuda_error((cudaError_t)ce);
-    return sgs_densify_split(in, S_accum, inv_T_split, eps_split, step_scale, grad_norm, eps_grad, out, capacity,
+    return sgs_densify_split(in, S_accum, inv_T_split, eps_split, step_scale, grad_norm, eps_grad, max_splits, out,
+                             capacity,
                              d_n_out, parent_index, lam_min_out, v_min_out, ws, (size_t)SGS_NOALLOC_SCRATCH_BYTES,
                              stream);
 }

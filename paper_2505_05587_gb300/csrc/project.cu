@@ -363,7 +363,6 @@ cudaError_t launch_project(const ScenesDev& sc, int sh_degree, const ViewsDev& v
 // shared memory so that the 3K-float rows are read and updated with coalesced
 // accesses.
 // ---------------------------------------------------------------------------
-constexpr int kBwdThreads = 64;
 
 // Geometry adjoint of one Gaussian in one view: adds the view's splitting
 // matrix to S6 and its parameter gradients to the accumulators.
@@ -495,29 +494,33 @@ __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, fl
 // Gaussians' SH rows (coefficients and gradient increments) through shared
 // memory so that the 3K-float rows are read and updated with coalesced
 // accesses.
-template <int DEG>
-__global__ void __launch_bounds__(kBwdThreads, 8) project_bwd_kernel(
+// MULTI = false is the single-view case: no view loop, and the SH gradient
+// increments overwrite the staged coefficients once they have been used.
+template <int DEG, bool MULTI>
+__global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ sh, int n, ViewsDev vd, const float4* __restrict__ conic_opac,
     const uint32_t* __restrict__ tiles, const float* __restrict__ g2d, int accumulate,
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_logit, float* __restrict__ g_sh, float* __restrict__ S_accum) {
+    constexpr int THREADS = MULTI ? 64 : 128;
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int K3 = 3 * K;
     constexpr int ROW = K3 + 1;                      // padded row: conflict-free per-thread access
-    __shared__ float s_coef[kBwdThreads / 32][32 * ROW];
-    __shared__ float s_inc[kBwdThreads / 32][32 * ROW];
+    __shared__ float s_coef[THREADS / 32][32 * ROW];
+    __shared__ float s_inc[MULTI ? THREADS / 32 : 1][MULTI ? 32 * ROW : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int base = blockIdx.x * kBwdThreads + warp * 32;
+    const int base = blockIdx.x * THREADS + warp * 32;
     if (base >= n) return;
     const int i = base + lane;
     float* wc = s_coef[warp];
-    float* wi = s_inc[warp];
+    float* wi = MULTI ? s_inc[warp] : s_coef[warp];
 
     // which views touched this Gaussian
     uint32_t vmask = 0u;
+    const int nv = MULTI ? vd.nv : 1;
     if (i < n) {
-        for (int v = 0; v < vd.nv; ++v) {
+        for (int v = 0; v < nv; ++v) {
             const long long row = (long long)v * n + i;
             if (tiles[row] == 0u) continue;
             const float4* r4 = reinterpret_cast<const float4*>(g2d + (size_t)row * 16);
@@ -537,7 +540,7 @@ __global__ void __launch_bounds__(kBwdThreads, 8) project_bwd_kernel(
         const int r = f / K3;
         const int o = r * ROW + (f - r * K3);
         wc[o] = ((need >> r) & 1u) ? sh[(size_t)base * K3 + f] : 0.0f;
-        wi[o] = 0.0f;
+        if constexpr (MULTI) wi[o] = 0.0f;
     }
     __syncwarp();
 
@@ -550,7 +553,7 @@ __global__ void __launch_bounds__(kBwdThreads, 8) project_bwd_kernel(
         const float sc[3] = {__expf(log_scales[3 * i]), __expf(log_scales[3 * i + 1]), __expf(log_scales[3 * i + 2])};
         const float* crow = wc + lane * ROW;
         float* irow = wi + lane * ROW;
-        for (int v = 0; v < vd.nv; ++v) {
+        for (int v = 0; v < nv; ++v) {
             if (!((vmask >> v) & 1u)) continue;
             const CamDev& cam = vd.cam[v];
             const long long row = (long long)v * n + i;
@@ -590,11 +593,20 @@ __global__ void __launch_bounds__(kBwdThreads, 8) project_bwd_kernel(
                 gm1 += (e1 - pr * h1) * inv_dn;
                 gm2 += (e2 - pr * h2) * inv_dn;
             }
+            if constexpr (MULTI) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                irow[3 * k] += Y[k] * gc0;
-                irow[3 * k + 1] += Y[k] * gc1;
-                irow[3 * k + 2] += Y[k] * gc2;
+                for (int k = 0; k < K; ++k) {
+                    irow[3 * k] += Y[k] * gc0;
+                    irow[3 * k + 1] += Y[k] * gc1;
+                    irow[3 * k + 2] += Y[k] * gc2;
+                }
+            } else {                                 // the coefficients are no longer needed
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    irow[3 * k] = Y[k] * gc0;
+                    irow[3 * k + 1] = Y[k] * gc1;
+                    irow[3 * k + 2] = Y[k] * gc2;
+                }
             }
         }
         float* So = S_accum + (size_t)i * 6;
@@ -635,11 +647,16 @@ __global__ void __launch_bounds__(kBwdThreads, 8) project_bwd_kernel(
 cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const ViewsDev& vd, const float* g2d,
                                bool accumulate, const sgs_grads& grads, float* S_accum, cudaStream_t stream) {
     if (g.n == 0) return cudaSuccess;
-    int blocks = (g.n + kBwdThreads - 1) / kBwdThreads;
-    auto kern = g.sh_degree == 0 ? project_bwd_kernel<0>
-              : g.sh_degree == 1 ? project_bwd_kernel<1>
-              : g.sh_degree == 2 ? project_bwd_kernel<2> : project_bwd_kernel<3>;
-    kern<<<blocks, kBwdThreads, 0, stream>>>(
+    const bool multi = vd.nv > 1;
+    const int threads = multi ? 64 : 128;
+    const int blocks = (g.n + threads - 1) / threads;
+    auto kern = multi ? (g.sh_degree == 0 ? project_bwd_kernel<0, true>
+                       : g.sh_degree == 1 ? project_bwd_kernel<1, true>
+                       : g.sh_degree == 2 ? project_bwd_kernel<2, true> : project_bwd_kernel<3, true>)
+                      : (g.sh_degree == 0 ? project_bwd_kernel<0, false>
+                       : g.sh_degree == 1 ? project_bwd_kernel<1, false>
+                       : g.sh_degree == 2 ? project_bwd_kernel<2, false> : project_bwd_kernel<3, false>);
+    kern<<<blocks, threads, 0, stream>>>(
         g.means, g.log_scales, g.quats, g.sh, g.n, vd, reinterpret_cast<const float4*>(proj.conic_opac),
         proj.tiles_touched, g2d, accumulate ? 1 : 0, grads.means, grads.log_scales, grads.quats,
         grads.opacity_logit, grads.sh, S_accum);

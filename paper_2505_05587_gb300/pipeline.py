@@ -113,7 +113,7 @@ class DensifyBuffers:
 
 def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: list[torch.Tensor],
                     db: DensifyBuffers, T_split: float = 1.0, eps_split: float = 0.0, step_scale: float = 1.0,
-                    grad_norm=None, eps_grad: float = 0.0, stream=None, check_capacity=True):
+                    grad_norm=None, eps_grad: float = 0.0, stream=None, check_capacity=True, max_splits: int = 0):
     """One fused fwd+bwd+splitting iteration over the views (Algorithm 1 with
     the split step taken right after accumulation)."""
     db.zero_(grads=False)
@@ -126,4 +126,4 @@ def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: lis
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, vb.cam, vb.st, vb.final_T, vb.n_contrib, vb.dL,
                                     db.grads, db.S, db.bwd_ws, stream, accumulate=k > 0)
     B.densify_split(g, db.S, 1.0 / T_split, eps_split, step_scale, grad_norm, eps_grad, db.out, db.capacity,
-                    db.n_out, db.parent, db.lam, db.v, db.split_ws, stream)
+                    db.n_out, db.parent, db.lam, db.v, db.split_ws, stream, max_splits=max_splits)

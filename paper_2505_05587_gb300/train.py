@@ -72,6 +72,7 @@ class TrainConfig:
     eps_split: float = -1e-6
     step_scale: float = 1.0
     eps_grad: float | None = None      # compactest gate ||G_bar|| <= eps_grad when set
+    max_splits: int = 0                # increment budget per densification (0: none)
     log_every: int = 10
 
 
@@ -142,7 +143,7 @@ class SteepGSTrainer:
         if cfg.eps_grad is not None:
             gn = (self.G / max(self.n_accum, 1)).norm(dim=1).contiguous()
         B.densify_split(g, self.S, 1.0 / max(self.n_accum, 1), cfg.eps_split, cfg.step_scale, gn,
-                        cfg.eps_grad or 0.0, out, 2 * n, n_out, parent, lam, vmin, ws)
+                        cfg.eps_grad or 0.0, out, 2 * n, n_out, parent, lam, vmin, ws, max_splits=cfg.max_splits)
         n2 = int(n_out.item())
         split = n2 - n
         par = parent[:n2].long()

@@ -181,15 +181,16 @@ def test_l1_loss_grad_parity():
     assert abs(loss.item() - L_ref) < 1e-5 * L_ref
 
 
-def _densify_both(scene, S_or, S_gpu, eps_split, step_scale=1.0, inv_T=1.0, grad_norm=None, eps_grad=0.0):
+def _densify_both(scene, S_or, S_gpu, eps_split, step_scale=1.0, inv_T=1.0, grad_norm=None, eps_grad=0.0,
+                  budget=0):
     g = B.GaussianTensors.from_scene(scene)
     db = PL.DensifyBuffers.alloc(g)
     gn = None if grad_norm is None else torch.as_tensor(grad_norm.astype(np.float32)).cuda()
     B.densify_split(g, S_gpu, inv_T, eps_split, step_scale, gn, eps_grad, db.out, db.capacity, db.n_out, db.parent,
-                    db.lam, db.v, db.split_ws)
+                    db.lam, db.v, db.split_ws, max_splits=budget)
     torch.cuda.synchronize()
     lam_o, v_o = oracle.eig3_min(S_or, inv_T)
-    sp = oracle.split(scene, lam_o, v_o, eps_split, step_scale, grad_norm, eps_grad)
+    sp = oracle.split(scene, lam_o, v_o, eps_split, step_scale, grad_norm, eps_grad, budget=budget)
     return db, lam_o, v_o, sp
 
 
@@ -240,6 +241,66 @@ def test_densify_gradient_gate_parity():
     flags_g = np.zeros(scene.n, bool)
     flags_g[db.parent.cpu().numpy()[scene.n:n_out]] = True
     assert np.array_equal(flags_g[decided], sp["flags"][decided])
+
+
+def _budget_scene(n=50_000, seed=7):
+    """A scene with a random symmetric S per Gaussian (about half of them
+    with lambda_min < 0) and a block of exactly repeated rows, so that the
+    budget threshold falls inside a group of equal lambda_min."""
+    scene = synth.cluster_scene(seed, n, 3)
+    rng = np.random.default_rng(seed)
+    A = rng.normal(size=(n, 3, 3))
+    S = (A + A.transpose(0, 2, 1)) * 0.5 + 0.3 * np.eye(3)
+    S[1000:1400] = S[999]                     # 401 Gaussians with the same S
+    S = S.astype(np.float32).astype(np.float64)
+    S_gpu = torch.as_tensor(_upper6(S).astype(np.float32)).cuda().contiguous()
+    return scene, S, S_gpu
+
+
+@pytest.mark.parametrize("budget", [1, 37, 1200, 10**9])
+def test_densify_budget_parity(budget):
+    scene, S_or, S_gpu = _budget_scene()
+    db, lam_o, v_o, sp = _densify_both(scene, S_or, S_gpu, 0.0, budget=budget)
+    n = scene.n
+    n_out = int(db.n_out.item())
+    flags_g = np.zeros(n, bool)
+    flags_g[db.parent.cpu().numpy()[n:n_out]] = True
+    lam_g = db.lam.cpu().numpy()
+    cand_g = lam_g < 0.0
+    # selection on the kernel's own lambda: exactly the K least, ties by index
+    K = min(budget, int(cand_g.sum()))
+    order = np.lexsort((np.arange(n), lam_g.astype(np.float64)))
+    want = np.zeros(n, bool)
+    want[[i for i in order if cand_g[i]][:K]] = True
+    assert np.array_equal(flags_g, want)
+    # against the oracle: same set wherever lambda is not within rounding of the threshold
+    nrm = np.linalg.norm(S_or.reshape(-1, 9), axis=1)
+    kept = lam_o[sp["flags"]]
+    thr = kept.max() if kept.size else -np.inf
+    near0 = np.abs(lam_o) <= 1e-4 * nrm
+    near = (np.abs(lam_o - thr) <= 1e-4 * nrm) | near0
+    assert abs(n_out - sp["n_out"]) <= int(near0.sum())
+    if budget < (lam_o < 0).sum() - near0.sum():
+        assert n_out - n == budget == sp["n_out"] - n
+    assert np.array_equal(flags_g[~near], sp["flags"][~near])
+    if np.array_equal(flags_g, sp["flags"]):
+        assert np.array_equal(db.parent.cpu().numpy()[:n_out], sp["parent"])
+
+
+def test_densify_budget_cuts_a_tie_group():
+    scene, S_or, S_gpu = _budget_scene()
+    db, _, _, _ = _densify_both(scene, S_or, S_gpu, 0.0, budget=0)
+    lam = db.lam.cpu().numpy()
+    tie = lam[999]
+    assert np.all(lam[1000:1400] == tie) and tie < 0
+    below = int(((lam < tie)).sum())
+    budget = below + 150                      # the cut falls inside the 401 equal values
+    db, _, _, _ = _densify_both(scene, S_or, S_gpu, 0.0, budget=budget)
+    n = scene.n
+    par = db.parent.cpu().numpy()[n:int(db.n_out.item())]
+    chosen = set(par.tolist())
+    assert len(chosen) == budget
+    assert chosen.issuperset(set(range(999, 1149))) and not chosen & set(range(1149, 1400))
 
 
 def test_fused_iteration_end_to_end():
