@@ -167,7 +167,7 @@ def run_gpu(args):
     for _ in range(max(args.warmup - 1, 0)):
         PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=False)
     torch.cuda.synchronize(dev)
-    M = int(vb.bins.count.item())
+    M = B.check_count(int(vb.bins.count.item()))
     n_out = int(db.n_out.item())
 
     names = ["zero_accumulators", "project", "bin_sort", "render_fwd", "l1_loss_grad",

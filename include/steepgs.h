@@ -127,7 +127,7 @@ typedef struct sgs_proj {
  *   ranges   [T,2]       per tile [start, end) into gids, T = tiles_x*tiles_y,
  *                        tile id = ty * tiles_x + tx.
  *   count    [1] int32   M, the number of instances (may exceed capacity).
- *   capacity             rows available in gids / keys. */
+ *   capacity             rows available in gids / keys (< 2^31). */
 typedef struct sgs_bins {
     uint32_t *gids;
     uint64_t *keys;

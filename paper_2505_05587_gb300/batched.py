@@ -64,7 +64,7 @@ class BatchedDensifyStep:
         """Runs once eagerly and grows the instance capacity until it holds M."""
         while True:
             self.run_eager()
-            M = int(self.count.item())
+            M = B.check_count(int(self.count.item()))
             if M <= self.capacity:
                 return M
             self._set_capacity(int(M * 1.1) + 4096)

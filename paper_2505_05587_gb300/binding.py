@@ -409,5 +409,13 @@ def densify_split_noalloc(g: GaussianTensors, S_accum, inv_T_split: float, eps_s
                                            _p(parent_index), _p(lam_min_out), _p(v_min_out), _stream(stream)))
 
 
+def check_count(M: int) -> int:
+    """Instance count read back from bin_sort / the batched entry points
+    (never negative; a negative value means corrupted device state)."""
+    if M < 0:
+        raise RuntimeError(f"sgs_bin_sort: invalid instance count {M}")
+    return M
+
+
 def workspace(nbytes: int, device="cuda") -> torch.Tensor:
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)

@@ -132,12 +132,18 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* d
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort of (uint32 key, uint32 value) pairs.
-// Each of G blocks owns one contiguous chunk of the items.
-// Per pass: per-block digit histogram -> per-digit exclusive scan over blocks
-// -> stable scatter.  Inside a block, ranks come from warp-level
-// __match_any_sync over 32 consecutive items, accumulated across sub-rounds
-// and across warps in item order, which keeps equal digits in input order.
+// Stable LSD radix passes (reduce, scan, scatter) with chunked blocks.
+//
+// A pass over n items runs G blocks (G <= SORT_G_MAX, fixed on the host); block
+// b owns the contiguous chunk [b C, min(n, (b + 1) C)), C = ceil(n / G), and
+// walks it in tiles of RS_TILE items.  hist[d][b] = count of digit d in chunk
+// b; one scan kernel turns each digit's row into exclusive prefixes over the
+// blocks and writes the digit totals; the scatter ranks each tile's items per
+// digit in item order (warp ballots + a cross-warp prefix) and writes item k of
+// digit d to  base[d] + prefix[d][b] + rank,  so the pass is stable.  The
+// scatter also counts the NEXT pass's per-block histogram from the
+// destinations it writes (the next pass's chunk of a destination is known), so
+// every pass after the first needs no separate counting kernel.
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
@@ -145,240 +151,440 @@ constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_MAX_BITS = 8;
 constexpr int RS_RADIX_MAX = 1 << RS_MAX_BITS;
-constexpr int RS_MAX_BLOCKS = 1024;
+constexpr int SORT_G_MAX = 1024;             // blocks of one pass (= threads of the scan kernel)
+constexpr int DEPTH_PASSES = 4;              // 32 depth bits
+constexpr int TILE_PASSES_MAX = 4;           // tile ids < 2^31
+constexpr int EMIT_THREADS = 256;
+constexpr int EMIT_SUB = 1024;               // rows staged per emission round
+constexpr int EMIT_G_MAX = 4096;             // emission blocks (4 per thread of the offsets scan)
+constexpr int EMIT_ROWS_PER_BLOCK = 256;     // target rows per emission block (of all rows)
+constexpr int EMIT_SPAN = 8;                 // next-pass blocks gathered in shared memory per round
+static_assert(EMIT_THREADS == RS_RADIX_MAX, "emit sums one depth digit total per thread");
+static_assert(EMIT_SUB % EMIT_THREADS == 0, "emit rows per thread");
 
-// Up to RS_MAX_BLOCKS blocks; each owns a contiguous chunk rounded only to
-// whole warps, so that the device-side count n (often far below n_max) still
-// spreads over every block and each SM keeps several blocks in flight.
-static int rs_blocks(int64_t n_max) {
-    int64_t b = (n_max + 255) / 256;
-    if (b < 1) b = 1;
-    if (b > RS_MAX_BLOCKS) b = RS_MAX_BLOCKS;
-    return (int)b;
+static int sort_blocks(int64_t n_max, int64_t per_block) {
+    int64_t g = (n_max + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > SORT_G_MAX) g = SORT_G_MAX;
+    return (int)g;
 }
 
-__device__ __forceinline__ void rs_chunk(int64_t n, int64_t* start, int64_t* end) {
-    int64_t per = (n + gridDim.x - 1) / gridDim.x;
-    per = (per + 31) / 32 * 32;
-    *start = (int64_t)blockIdx.x * per;
-    *end = min(n, *start + per);
-}
+__device__ __forceinline__ int64_t chunk_of(int64_t n, int G) { return (n + G - 1) / G; }
 
-__global__ void __launch_bounds__(RS_THREADS) radix_hist_kernel(const uint32_t* __restrict__ keys,
-                                                                const int32_t* d_n, int64_t n_host,
-                                                                int64_t cap, int shift, int bits,
-                                                                uint32_t* __restrict__ hist) {
-    __shared__ uint32_t s_cnt[RS_RADIX_MAX];
-    const int radix = 1 << bits;
-    const uint32_t mask = (uint32_t)radix - 1u;
-    for (int d = threadIdx.x; d < radix; d += blockDim.x) s_cnt[d] = 0;
-    __syncthreads();
-    int64_t n = read_n(d_n, n_host, cap), start, end;
-    rs_chunk(n, &start, &end);
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = start; base < end; base += blockDim.x) {
-        int64_t i = base + threadIdx.x;
-        bool valid = i < end;
-        uint32_t d = valid ? ((keys[i] >> shift) & mask) : (uint32_t)radix;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < radix; d += blockDim.x) hist[(size_t)d * gridDim.x + blockIdx.x] = s_cnt[d];
-}
+struct PassDesc {
+    int shift, bits;
+    uint32_t* hist;          // [1 << bits][G]: counts, then (after the scan) exclusive prefixes
+    uint32_t* tot;           // [1 << bits] digit totals (written by the scan)
+    int G;
+};
 
-// One block per digit: exclusive scan of that digit's counts over the G blocks.
-__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__ hist, int G,
-                                                          uint32_t* __restrict__ digit_tot) {
+struct NextHist {            // per-block histogram of the following pass (bits = 0: none)
+    int shift, bits;
+    uint32_t* hist;          // [1 << bits][G]
+    int G;
+};
+
+// Exclusive scan of one digit's per-block counts (one block per digit).
+__global__ void __launch_bounds__(SORT_G_MAX) pass_scan_kernel(uint32_t* __restrict__ hist, int G,
+                                                               uint32_t* __restrict__ tot) {
     __shared__ uint32_t s_warp[32];
     uint32_t* h = hist + (size_t)blockIdx.x * G;
-    uint32_t v = threadIdx.x < G ? h[threadIdx.x] : 0u;
-    uint32_t inc = block_inclusive_scan(v, s_warp);
+    const uint32_t v = threadIdx.x < G ? h[threadIdx.x] : 0u;
+    const uint32_t inc = block_inclusive_scan(v, s_warp);
     if (threadIdx.x < G) h[threadIdx.x] = inc - v;
-    if (threadIdx.x == blockDim.x - 1) digit_tot[blockIdx.x] = inc;
+    if (threadIdx.x == blockDim.x - 1) tot[blockIdx.x] = inc;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(
-    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int32_t* d_n,
-    int64_t n_host, int64_t cap, int shift, int bits, const uint32_t* __restrict__ hist,
-    const uint32_t* __restrict__ digit_tot) {
+// Lanes with the same digit as this lane (an invalid item has its own class):
+// bits ballots instead of a match instruction.
+__device__ __forceinline__ unsigned digit_peers(uint32_t dig, bool valid, int bits) {
+    unsigned m = __ballot_sync(0xffffffffu, valid);
+    m = valid ? m : ~m;
+    for (int b = 0; b < bits; ++b) {
+        const bool one = (dig >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, one);
+        m &= one ? bal : ~bal;
+    }
+    return m;
+}
+
+// Counts of the first depth pass per block over the projection rows; only rows
+// with tiles_touched > 0 are items (their float32 depth bits are the key: depth
+// > near_z > 0, so the bits order like the value).
+__global__ void __launch_bounds__(RS_THREADS) depth_hist_first_kernel(const float* __restrict__ depth,
+                                                                      const uint32_t* __restrict__ tiles_touched,
+                                                                      int64_t n_rows, PassDesc ps) {
+    __shared__ uint32_t s_h[RS_RADIX_MAX];
+    for (int k = threadIdx.x; k < RS_RADIX_MAX; k += RS_THREADS) s_h[k] = 0u;
+    __syncthreads();
+    const int64_t C = chunk_of(n_rows, ps.G);
+    const int64_t lo = (int64_t)blockIdx.x * C, hi = min(n_rows, lo + C);
+    const int lane = threadIdx.x & 31;
+    const uint32_t mask = (1u << ps.bits) - 1u;
+    for (int64_t base = lo; base < hi; base += RS_THREADS) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < hi && tiles_touched[i] != 0u;
+        const uint32_t d = valid ? ((__float_as_uint(depth[i]) >> ps.shift) & mask) : 0u;
+        const unsigned peers = digit_peers(d, valid, ps.bits);
+        if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < (1 << ps.bits); d += RS_THREADS) ps.hist[(size_t)d * ps.G + blockIdx.x] = s_h[d];
+}
+
+// Per-block digit counts of a pass whose items are keys[0, total of the
+// previous pass) (the previous pass's output).
+__global__ void __launch_bounds__(RS_THREADS) pass_hist_kernel(const uint32_t* __restrict__ keys,
+                                                               const uint32_t* __restrict__ prev_tot, int prev_radix,
+                                                               PassDesc ps) {
+    __shared__ uint32_t s_h[RS_RADIX_MAX];
+    __shared__ uint32_t s_n;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_n = 0u;
+    for (int k = threadIdx.x; k < RS_RADIX_MAX; k += RS_THREADS) s_h[k] = 0u;
+    __syncthreads();
+    {
+        uint32_t c = threadIdx.x < prev_radix ? prev_tot[threadIdx.x] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0 && c) atomicAdd(&s_n, c);
+    }
+    __syncthreads();
+    const int64_t n = s_n;
+    const int64_t C = chunk_of(n, ps.G);
+    const int64_t lo = (int64_t)blockIdx.x * C, hi = min(n, lo + C);
+    const uint32_t mask = (1u << ps.bits) - 1u;
+    for (int64_t base = lo; base < hi; base += RS_THREADS) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < hi;
+        const uint32_t d = valid ? ((keys[i] >> ps.shift) & mask) : 0u;
+        const unsigned peers = digit_peers(d, valid, ps.bits);
+        if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < (1 << ps.bits); d += RS_THREADS) ps.hist[(size_t)d * ps.G + blockIdx.x] = s_h[d];
+}
+
+// One stable pass.  FIRST: items are the projection rows [0, n_rows) (rows
+// that touch no tile are dropped), key = depth bits, value = row.  Otherwise
+// items are (keys_in, vals_in)[0, total of the pass).  keys_out may be NULL.
+// GATHER (last depth pass): also writes cnt_out[dest] = tiles_touched[value]
+// and adds it to esum[dest chunk] (the emission's per-block instance counts).
+template <bool FIRST, bool GATHER>
+__global__ void __launch_bounds__(RS_THREADS) pass_scatter_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, const float* __restrict__ depth,
+    const uint32_t* __restrict__ tiles_touched, int64_t n_rows, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, PassDesc ps, uint32_t* __restrict__ cnt_out,
+    unsigned long long* __restrict__ esum, int G_emit) {
     __shared__ uint32_t s_warp[RS_WARPS][RS_RADIX_MAX + 1];
     __shared__ uint32_t s_off[RS_RADIX_MAX];
     __shared__ uint32_t s_tot[RS_RADIX_MAX];
+    __shared__ uint32_t s_lbase[RS_RADIX_MAX];
+    __shared__ uint32_t s_key[RS_TILE];
+    __shared__ uint32_t s_val[RS_TILE];
     __shared__ uint32_t s_scan[32];
-    const int radix = 1 << bits;
+    __shared__ uint32_t s_ntile;
+    const int radix = 1 << ps.bits;
     const uint32_t mask = (uint32_t)radix - 1u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // digit base = exclusive scan of the digit totals (radix <= RS_THREADS)
-    {
-        uint32_t v = threadIdx.x < radix ? digit_tot[threadIdx.x] : 0u;
-        // block_inclusive_scan assumes <= 32 warps; RS_THREADS = 256
-        uint32_t inc;
-        {
-            uint32_t x = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += t;
-            }
-            if (lane == 31) s_scan[warp] = x;
-            __syncthreads();
-            if (warp == 0) {
-                uint32_t w = lane < RS_WARPS ? s_scan[lane] : 0u;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
-                    if (lane >= o) w += t;
-                }
-                s_scan[lane] = w;
-            }
-            __syncthreads();
-            inc = x + (warp > 0 ? s_scan[warp - 1] : 0u);
-        }
-        if (threadIdx.x < radix)
-            s_off[threadIdx.x] = (inc - v) + hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
-    }
+    // digit bases: exclusive scan of the totals (radix <= RS_THREADS)
+    const uint32_t tv = threadIdx.x < radix ? ps.tot[threadIdx.x] : 0u;
+    const uint32_t tinc = block_inclusive_scan(tv, s_scan);
+    if (threadIdx.x == RS_THREADS - 1) s_scan[31] = tinc;     // total (block_inclusive_scan ends synced)
     __syncthreads();
+    const int64_t n_out = s_scan[31];
+    const int64_t n_items = FIRST ? n_rows : n_out;
+    const int64_t C = chunk_of(n_items, ps.G);
+    const int64_t lo = (int64_t)blockIdx.x * C, hi = min(n_items, lo + C);
+    if (threadIdx.x < radix) s_off[threadIdx.x] = (tinc - tv) + ps.hist[(size_t)threadIdx.x * ps.G + blockIdx.x];
+    const uint32_t C_emit = GATHER ? (uint32_t)chunk_of(n_out, G_emit) : 1u;
 
-    int64_t n = read_n(d_n, n_host, cap), start, end;
-    rs_chunk(n, &start, &end);
-    for (int64_t tile = start; tile < end; tile += RS_TILE) {
-        for (int k = threadIdx.x; k < RS_WARPS * (RS_RADIX_MAX + 1); k += RS_THREADS)
-            (&s_warp[0][0])[k] = 0u;
+    for (int64_t tile = lo; tile < hi; tile += RS_TILE) {
+        for (int k = threadIdx.x; k < RS_WARPS * (RS_RADIX_MAX + 1); k += RS_THREADS) (&s_warp[0][0])[k] = 0u;
         __syncthreads();
         uint32_t key[RS_ITEMS], val[RS_ITEMS], dig[RS_ITEMS], rank[RS_ITEMS];
+        bool ok[RS_ITEMS];
         const int64_t wbase = tile + (int64_t)warp * 32 * RS_ITEMS + lane;
 #pragma unroll
         for (int it = 0; it < RS_ITEMS; ++it) {
-            int64_t idx = wbase + it * 32;
-            bool valid = idx < end;
-            key[it] = valid ? keys_in[idx] : 0u;
-            val[it] = valid ? vals_in[idx] : 0u;
-            dig[it] = valid ? ((key[it] >> shift) & mask) : (uint32_t)radix;
+            const int64_t idx = wbase + it * 32;
+            bool valid = idx < hi;
+            if (FIRST) {
+                valid = valid && tiles_touched[idx] != 0u;
+                key[it] = valid ? __float_as_uint(depth[idx]) : 0u;
+                val[it] = (uint32_t)idx;
+            } else {
+                key[it] = valid ? keys_in[idx] : 0u;
+                val[it] = valid ? vals_in[idx] : 0u;
+            }
+            ok[it] = valid;
+            dig[it] = (key[it] >> ps.shift) & mask;
         }
 #pragma unroll
         for (int it = 0; it < RS_ITEMS; ++it) {
-            unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
-            unsigned lower = peers & ((1u << lane) - 1u);
-            uint32_t base = s_warp[warp][dig[it]];
-            rank[it] = base + (uint32_t)__popc(lower);
+            const unsigned peers = digit_peers(dig[it], ok[it], ps.bits);
+            const unsigned lower = peers & ((1u << lane) - 1u);
+            const uint32_t slot = ok[it] ? dig[it] : (uint32_t)radix;
+            const uint32_t b = s_warp[warp][slot];
+            rank[it] = b + (uint32_t)__popc(lower);
             __syncwarp();
-            if (lower == 0u) s_warp[warp][dig[it]] = base + (uint32_t)__popc(peers);
+            if (lower == 0u) s_warp[warp][slot] = b + (uint32_t)__popc(peers);
             __syncwarp();
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < radix; d += RS_THREADS) {
-            uint32_t sum = 0;
+        uint32_t dtot = 0;
+        if (threadIdx.x < radix) {
+            const int d = threadIdx.x;
 #pragma unroll
             for (int w = 0; w < RS_WARPS; ++w) {
-                uint32_t c = s_warp[w][d];
-                s_warp[w][d] = sum;
-                sum += c;
+                const uint32_t c = s_warp[w][d];
+                s_warp[w][d] = dtot;
+                dtot += c;
             }
-            s_tot[d] = sum;
+            s_tot[d] = dtot;
         }
+        // local sort of the tile by digit in shared memory, so that the
+        // global writes below go out as runs of consecutive addresses
+        const uint32_t linc = block_inclusive_scan(dtot, s_scan);   // (ends synced)
+        if (threadIdx.x < radix) s_lbase[threadIdx.x] = linc - dtot;
+        if (threadIdx.x == RS_THREADS - 1) s_ntile = linc;
         __syncthreads();
 #pragma unroll
         for (int it = 0; it < RS_ITEMS; ++it) {
-            if (dig[it] < (uint32_t)radix) {
-                uint32_t dest = s_off[dig[it]] + s_warp[warp][dig[it]] + rank[it];
-                keys_out[dest] = key[it];
-                vals_out[dest] = val[it];
+            if (!ok[it]) continue;
+            const uint32_t lp = s_lbase[dig[it]] + s_warp[warp][dig[it]] + rank[it];
+            s_key[lp] = key[it];
+            s_val[lp] = val[it];
+        }
+        __syncthreads();
+        const uint32_t ntile = s_ntile;
+        for (uint32_t i0 = 0; i0 < ntile; i0 += RS_THREADS) {
+            const uint32_t i = i0 + threadIdx.x;
+            const bool okk = i < ntile;
+            const uint32_t k = okk ? s_key[i] : 0u;
+            const uint32_t vv = okk ? s_val[i] : 0u;
+            const uint32_t d = (k >> ps.shift) & mask;
+            const uint32_t dest = okk ? s_off[d] + (i - s_lbase[d]) : 0u;
+            if (okk) {
+                if (keys_out) keys_out[dest] = k;
+                vals_out[dest] = vv;
+            }
+            if (GATHER) {
+                // tile counts in depth order, summed per emission block; the
+                // lanes of a warp usually share the block: one add per warp
+                const uint32_t c = okk ? tiles_touched[vv] : 0u;
+                if (okk) cnt_out[dest] = c;
+                const uint32_t eb = okk ? dest / C_emit : 0xffffffffu;
+                const uint32_t eb0 = __shfl_sync(0xffffffffu, eb, 0);
+                if (__all_sync(0xffffffffu, eb == eb0 || !okk)) {
+                    unsigned long long sum = c;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                    if (lane == 0 && sum) atomicAdd(esum + eb0, sum);
+                } else if (okk && c) {
+                    atomicAdd(esum + eb, (unsigned long long)c);
+                }
             }
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < radix; d += RS_THREADS) s_off[d] += s_tot[d];
+        if (threadIdx.x < radix) s_off[threadIdx.x] += s_tot[threadIdx.x];
         __syncthreads();
     }
 }
 
-struct RadixBufs {
-    uint32_t* hist;       // [RS_RADIX_MAX * RS_MAX_BLOCKS]
-    uint32_t* digit_tot;  // [RS_RADIX_MAX]
-};
-
-static int rs_passes(int total_bits) { return (total_bits + RS_MAX_BITS - 1) / RS_MAX_BITS; }
-
-// Sorts (k[0], v[0]) using (k[1], v[1]) as the ping-pong pair; the result is
-// in pair (passes % 2).  Bits [0, total_bits) are sorted.
-static cudaError_t radix_sort_pairs(uint32_t* k[2], uint32_t* v[2], const int32_t* d_n, int64_t n_host,
-                                    int64_t n_max, int total_bits, const RadixBufs& rb,
-                                    cudaStream_t stream) {
-    if (total_bits <= 0) return cudaSuccess;
-    int G = rs_blocks(n_max);
-    int passes = rs_passes(total_bits);
-    int bits_per = (total_bits + passes - 1) / passes;
-    int shift = 0;
-    for (int p = 0; p < passes; ++p) {
-        int bits = min(bits_per, total_bits - shift);
-        int src = p & 1, dst = src ^ 1;
-        radix_hist_kernel<<<G, RS_THREADS, 0, stream>>>(k[src], d_n, n_host, n_max, shift, bits, rb.hist);
-        note_launch();
-        radix_scan_kernel<<<1 << bits, 1024, 0, stream>>>(rb.hist, G, rb.digit_tot);
-        note_launch();
-        radix_scatter_kernel<<<G, RS_THREADS, 0, stream>>>(k[src], v[src], k[dst], v[dst], d_n, n_host,
-                                                           n_max, shift, bits, rb.hist, rb.digit_tot);
-        note_launch();
-        shift += bits;
+// Exclusive scan of the emission blocks' instance counts (one block of
+// SORT_G_MAX threads, EMIT_G_MAX / SORT_G_MAX consecutive counts per thread);
+// writes M.
+__global__ void __launch_bounds__(SORT_G_MAX) emit_offsets_kernel(unsigned long long* __restrict__ esum, int G,
+                                                                  int32_t* __restrict__ d_count) {
+    constexpr int PER = EMIT_G_MAX / SORT_G_MAX;
+    __shared__ unsigned long long s_w[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long v[PER], mine = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = threadIdx.x * PER + q;
+        v[q] = i < G ? esum[i] : 0ull;
+        mine += v[q];
     }
-    return cudaGetLastError();
+    unsigned long long x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_w[lane] = w;
+    }
+    __syncthreads();
+    const unsigned long long inc = x + (warp > 0 ? s_w[warp - 1] : 0ull);
+    unsigned long long run = inc - mine;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = threadIdx.x * PER + q;
+        if (i < G) esum[i] = run;
+        run += v[q];
+    }
+    if (threadIdx.x == blockDim.x - 1) *d_count = inc > 0x7fffffffull ? 0x7fffffff : (int32_t)inc;
 }
 
-// ---------------------------------------------------------------------------
-// Binning kernels
-// ---------------------------------------------------------------------------
-__global__ void visible_flags_kernel(const uint32_t* __restrict__ tiles, int n, uint32_t* __restrict__ flag) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    flag[i] = tiles[i] ? 1u : 0u;
-}
-
-// Compacts the visible Gaussians (in index order) into (depth bits, index)
-// pairs.  depth > near_z > 0 for every visible Gaussian, so its bits order like
-// the value.
-__global__ void depth_keys_kernel(const float* __restrict__ depth, const uint32_t* __restrict__ tiles,
-                                  const uint32_t* __restrict__ pos, int n, uint32_t* __restrict__ keys,
-                                  uint32_t* __restrict__ vals) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || tiles[i] == 0u) return;
-    const uint32_t p = pos[i];
-    keys[p] = __float_as_uint(depth[i]);
-    vals[p] = (uint32_t)i;
-}
-
-__global__ void gather_counts_kernel(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ tiles,
-                                     const int32_t* __restrict__ d_n, int n_max, uint32_t* __restrict__ cnt) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_max) return;
-    cnt[j] = j < *d_n ? tiles[perm[j]] : 0u;
-}
-
-// One thread per depth-sorted projection row: writes the row's instances
-// (global tile id in the row's view, row) in row-major tile order.
-__global__ void emit_kernel(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cnt,
-                            const uint32_t* __restrict__ offs, const short4* __restrict__ rect, int n_rows,
-                            ViewsDev vd, int64_t cap, uint32_t* __restrict__ inst_tile,
-                            uint32_t* __restrict__ inst_gid) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_rows) return;
-    uint32_t c = cnt[j];
-    if (c == 0) return;
-    uint32_t g = perm[j];
-    const int v = view_of_row(vd, g);
-    const int gx = vd.cam[v].gx;
-    const uint32_t t0 = (uint32_t)vd.tile_off[v];
-    short4 r = rect[g];
-    int64_t pos = offs[j];
-    for (int ty = r.y; ty <= r.w; ++ty)
-        for (int tx = r.x; tx <= r.z; ++tx) {
-            if (pos < cap) {
-                inst_tile[pos] = t0 + (uint32_t)(ty * gx + tx);
+// Emission of the (tile, row) instances in depth order, load-balanced: block b
+// owns the depth-sorted rows of chunk b; per round of EMIT_SUB rows it scans
+// their counts into shared memory and then spreads the round's instances over
+// all threads (instance k -> its row by binary search, its tile from the
+// offset inside the row's rect, row-major), so consecutive threads write
+// consecutive positions.  At most `cap` instances are written; the first
+// tile pass's per-block histogram is counted from the written positions.
+__global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
+    const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cnt, const short4* __restrict__ rect,
+    const uint32_t* __restrict__ depth_tot, ViewsDev vd, int64_t cap, const unsigned long long* __restrict__ esum,
+    int G_emit, const int32_t* __restrict__ d_count, uint32_t* __restrict__ inst_tile,
+    uint32_t* __restrict__ inst_gid, NextHist nh) {
+    __shared__ uint32_t s_off[EMIT_SUB + 1];
+    __shared__ uint32_t s_row[EMIT_SUB];
+    __shared__ short4 s_rect[EMIT_SUB];
+    __shared__ uint32_t s_warp[EMIT_THREADS / 32];
+    __shared__ uint32_t s_nh[RS_RADIX_MAX][EMIT_SPAN];
+    __shared__ uint32_t s_nvis;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_nvis = 0u;
+    __syncthreads();
+    {
+        uint32_t c = depth_tot[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) atomicAdd(&s_nvis, c);
+    }
+    __syncthreads();
+    const int64_t n_vis = s_nvis;
+    const int64_t C = chunk_of(n_vis, G_emit);
+    const int64_t lo = (int64_t)blockIdx.x * C, hi = min(n_vis, lo + C);
+    const int64_t M = *d_count;
+    const int64_t n_written = M < cap ? M : cap;
+    const uint32_t C_next = nh.bits > 0 ? (uint32_t)chunk_of(n_written, nh.G) : 1u;
+    const uint32_t nmask = (1u << nh.bits) - 1u;
+    int64_t base = (int64_t)esum[blockIdx.x];
+    for (int64_t r0 = lo; r0 < hi; r0 += EMIT_SUB) {
+        const int rows = (int)min((int64_t)EMIT_SUB, hi - r0);
+        // counts of this round's rows: 4 consecutive rows per thread, block scan
+        uint32_t c[EMIT_SUB / EMIT_THREADS];
+        uint32_t mine = 0;
+#pragma unroll
+        for (int q = 0; q < EMIT_SUB / EMIT_THREADS; ++q) {
+            const int j = threadIdx.x * (EMIT_SUB / EMIT_THREADS) + q;
+            c[q] = j < rows ? cnt[r0 + j] : 0u;
+            mine += c[q];
+            if (j < rows) {
+                const uint32_t g = perm[r0 + j];
+                s_row[j] = g;
+                s_rect[j] = rect[g];
+            }
+        }
+        uint32_t x = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t run = 0;
+            for (int w = 0; w < EMIT_THREADS / 32; ++w) {
+                const uint32_t t = s_warp[w];
+                s_warp[w] = run;
+                run += t;
+            }
+            s_off[EMIT_SUB] = run;
+        }
+        __syncthreads();
+        {
+            uint32_t o = s_warp[warp] + x - mine;
+#pragma unroll
+            for (int q = 0; q < EMIT_SUB / EMIT_THREADS; ++q) {
+                const int j = threadIdx.x * (EMIT_SUB / EMIT_THREADS) + q;
+                if (j < rows) s_off[j] = o;
+                o += c[q];
+            }
+        }
+        const uint32_t total = s_off[EMIT_SUB];
+        // the round's positions fall in next-pass blocks [nb0, nb0 + span);
+        // with a small span their histogram is gathered in shared memory
+        const int64_t last_pos = min(base + (int64_t)total, n_written) - 1;
+        const uint32_t nb0 = base < n_written ? (uint32_t)base / C_next : 0u;
+        const int span = last_pos >= base ? (int)((uint32_t)last_pos / C_next - nb0 + 1) : 0;
+        const bool local_nh = nh.bits > 0 && span <= EMIT_SPAN;
+        if (local_nh)
+            for (int k = threadIdx.x; k < RS_RADIX_MAX * EMIT_SPAN; k += EMIT_THREADS) (&s_nh[0][0])[k] = 0u;
+        __syncthreads();
+        // thread i emits the contiguous instances [i P, (i + 1) P) of the
+        // round: one search for its first row, then a walk along the rects
+        const uint32_t P = (total + EMIT_THREADS - 1) / EMIT_THREADS;
+        uint32_t k = threadIdx.x * P;
+        const uint32_t kend = min(total, k + P);
+        if (k < kend) {
+            int a = 0, b = rows - 1;                 // last row j with s_off[j] <= k
+            while (a < b) {
+                const int mid = (a + b + 1) >> 1;
+                if (s_off[mid] <= k) a = mid;
+                else b = mid - 1;
+            }
+            uint32_t off = k - s_off[a];
+            short4 r = s_rect[a];
+            uint32_t g = s_row[a];
+            int v = view_of_row(vd, g);
+            uint32_t t0 = (uint32_t)vd.tile_off[v];
+            int gx = vd.cam[v].gx;
+            uint32_t wdt = (uint32_t)(r.z - r.x + 1);
+            int ty = r.y + (int)(off / wdt), tx = r.x + (int)(off % wdt);
+            uint32_t row_end = a + 1 < rows ? s_off[a + 1] : total;
+            for (; k < kend; ++k) {
+                while (k >= row_end) {               // next row (every visible row has instances)
+                    ++a;
+                    r = s_rect[a];
+                    g = s_row[a];
+                    v = view_of_row(vd, g);
+                    t0 = (uint32_t)vd.tile_off[v];
+                    gx = vd.cam[v].gx;
+                    ty = r.y;
+                    tx = r.x;
+                    row_end = a + 1 < rows ? s_off[a + 1] : total;
+                }
+                const int64_t pos = base + k;
+                if (pos >= cap) break;
+                const uint32_t t = t0 + (uint32_t)(ty * gx + tx);
+                inst_tile[pos] = t;
                 inst_gid[pos] = g;
+                const uint32_t nb = (uint32_t)pos / C_next;
+                if (local_nh)
+                    atomicAdd(&s_nh[(t >> nh.shift) & nmask][nb - nb0], 1u);
+                else if (nh.bits > 0)
+                    atomicAdd(nh.hist + (size_t)((t >> nh.shift) & nmask) * nh.G + nb, 1u);
+                if (++tx > r.z) {
+                    tx = r.x;
+                    ++ty;
+                }
             }
-            ++pos;
         }
+        __syncthreads();
+        if (local_nh)
+            for (int k = threadIdx.x; k < (1 << nh.bits) * span; k += EMIT_THREADS) {
+                const int d = k / span, j = k - d * span;
+                const uint32_t h = s_nh[d][j];
+                if (h) atomicAdd(nh.hist + (size_t)d * nh.G + (size_t)(nb0 + j), h);
+            }
+        base += total;
+        __syncthreads();
+    }
 }
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ tile_sorted, const int32_t* d_n, int64_t cap,
@@ -407,98 +613,179 @@ static int ceil_log2(int64_t x) {
     return b;
 }
 
+struct TileSortCfg {
+    int bits, passes, bits_per;
+};
+
+static TileSortCfg tile_sort_cfg(int num_tiles) {
+    TileSortCfg c;
+    c.bits = ceil_log2(num_tiles);
+    c.passes = (c.bits + RS_MAX_BITS - 1) / RS_MAX_BITS;
+    c.bits_per = c.passes ? (c.bits + c.passes - 1) / c.passes : 0;
+    return c;
+}
+
+struct SortGeom {
+    int G_depth, G_emit, G_tile;
+    TileSortCfg tc;
+};
+
+static SortGeom sort_geom(int n, int64_t cap, int num_tiles) {
+    SortGeom g;
+    g.G_depth = sort_blocks(n, RS_TILE);
+    int64_t ge = ((int64_t)n + EMIT_ROWS_PER_BLOCK - 1) / EMIT_ROWS_PER_BLOCK;
+    g.G_emit = (int)(ge < 1 ? 1 : (ge > EMIT_G_MAX ? EMIT_G_MAX : ge));
+    g.G_tile = sort_blocks(cap, RS_TILE);
+    g.tc = tile_sort_cfg(num_tiles > 0 ? num_tiles : 1);
+    return g;
+}
+
 struct BinWs {
-    uint32_t *dkey[2], *perm[2], *cnt, *offs, *inst_tile[2], *inst_gid_tmp, *n_vis;
-    void* scan_tmp;
-    RadixBufs rb;
+    uint32_t *dkey[2], *perm[2], *cnt, *inst_tile[2], *inst_gid_tmp;
+    // zeroed at the start of every sort (histograms built with atomics):
+    uint32_t* depth_hist;     // [DEPTH_PASSES][256][G_depth]
+    uint32_t* depth_tot;      // [DEPTH_PASSES][256]
+    uint32_t* tile_hist;      // [TILE_PASSES_MAX][256][G_tile]
+    uint32_t* tile_tot;       // [TILE_PASSES_MAX][256]
+    unsigned long long* esum; // [G_emit]
+    size_t zero_bytes;
     size_t bytes;
 };
 
-static BinWs carve_bin_ws(void* base, int n, int64_t cap) {
+static BinWs carve_bin_ws(void* base, int n, int64_t cap, int num_tiles) {
     Carver c{reinterpret_cast<char*>(base), 0};
     BinWs w;
-    size_t nn = (size_t)(n > 0 ? n : 1);
-    size_t cc = (size_t)(cap > 0 ? cap : 1);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    const size_t cc = (size_t)(cap > 0 ? cap : 1);
+    const SortGeom sg = sort_geom(n, cap, num_tiles);
     w.dkey[0] = c.take<uint32_t>(nn);
     w.dkey[1] = c.take<uint32_t>(nn);
     w.perm[0] = c.take<uint32_t>(nn);
     w.perm[1] = c.take<uint32_t>(nn);
     w.cnt = c.take<uint32_t>(nn);
-    w.offs = c.take<uint32_t>(nn);
     w.inst_tile[0] = c.take<uint32_t>(cc);
     w.inst_tile[1] = c.take<uint32_t>(cc);
     w.inst_gid_tmp = c.take<uint32_t>(cc);
-    w.n_vis = c.take<uint32_t>(1);
-    w.scan_tmp = c.take<char>(scan_tmp_bytes(n));
-    w.rb.hist = c.take<uint32_t>((size_t)RS_RADIX_MAX * RS_MAX_BLOCKS);
-    w.rb.digit_tot = c.take<uint32_t>(RS_RADIX_MAX);
+    c.off = align_up(c.off, 256);
+    const size_t z0 = c.off;
+    w.depth_hist = c.take<uint32_t>((size_t)DEPTH_PASSES * RS_RADIX_MAX * sg.G_depth);
+    w.depth_tot = c.take<uint32_t>((size_t)DEPTH_PASSES * RS_RADIX_MAX);
+    w.tile_hist = c.take<uint32_t>((size_t)TILE_PASSES_MAX * RS_RADIX_MAX * sg.G_tile);
+    w.tile_tot = c.take<uint32_t>((size_t)TILE_PASSES_MAX * RS_RADIX_MAX);
+    w.esum = c.take<unsigned long long>((size_t)sg.G_emit);
+    w.zero_bytes = c.off - z0;
     w.bytes = c.off + 256;
     return w;
 }
 
 size_t bin_sort_ws_bytes(int n, int64_t capacity, int num_tiles) {
-    (void)num_tiles;
-    return carve_bin_ws(nullptr, n, capacity).bytes;
+    return carve_bin_ws(nullptr, n, capacity, num_tiles).bytes;
 }
 
 cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetDev& st, const sgs_bins& out, void* ws,
                             cudaStream_t stream) {
     (void)st;
     const int n = vd.row_off[vd.nv];            // projection rows
-    BinWs w = carve_bin_ws(ws, n, out.capacity);
     const int T = vd.T_total;
+    BinWs w = carve_bin_ws(ws, n, out.capacity, T);
+    const SortGeom sg = sort_geom(n, out.capacity, T);
+    const TileSortCfg& tc = sg.tc;
     cudaError_t e = cudaMemsetAsync(out.ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, stream);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaMemsetAsync(out.count, 0, sizeof(int32_t), stream);
-    const int nb = (n + 255) / 256;
-    const int32_t* d_nvis = reinterpret_cast<const int32_t*>(w.n_vis);
-    // 1. compact the visible Gaussians, then a stable sort of them by depth bits
-    visible_flags_kernel<<<nb, 256, 0, stream>>>(proj.tiles_touched, n, w.cnt);
-    note_launch();
-    e = launch_exclusive_scan(w.cnt, w.offs, w.n_vis, n, nullptr, w.scan_tmp, stream);
+    e = cudaMemsetAsync(w.depth_hist, 0, w.zero_bytes, stream);
     if (e != cudaSuccess) return e;
-    depth_keys_kernel<<<nb, 256, 0, stream>>>(proj.depth, proj.tiles_touched, w.offs, n, w.dkey[0], w.perm[0]);
+    auto depth_pass = [&](int p) {
+        return PassDesc{8 * p, 8, w.depth_hist + (size_t)p * RS_RADIX_MAX * sg.G_depth,
+                        w.depth_tot + p * RS_RADIX_MAX, sg.G_depth};
+    };
+    auto tile_pass = [&](int p) {
+        const int bits = min(tc.bits_per, tc.bits - p * tc.bits_per);
+        return PassDesc{p * tc.bits_per, bits, w.tile_hist + (size_t)p * RS_RADIX_MAX * sg.G_tile,
+                        w.tile_tot + p * RS_RADIX_MAX, sg.G_tile};
+    };
+    const NextHist none{0, 0, nullptr, 1};
+    // 1. stable sort of the visible rows by depth bits (4 passes of 8 bits; the
+    //    first pass drops the rows that touch no tile, the last one also
+    //    gathers the rows' tile counts in depth order)
+    depth_hist_first_kernel<<<sg.G_depth, RS_THREADS, 0, stream>>>(proj.depth, proj.tiles_touched, n, depth_pass(0));
     note_launch();
-    e = radix_sort_pairs(w.dkey, w.perm, d_nvis, 0, n, 32, w.rb, stream);
-    if (e != cudaSuccess) return e;
-    const uint32_t* perm = w.perm[rs_passes(32) & 1];
-    // 2. instance offsets in depth order, M
-    gather_counts_kernel<<<nb, 256, 0, stream>>>(perm, proj.tiles_touched, d_nvis, n, w.cnt);
-    note_launch();
-    e = launch_exclusive_scan(w.cnt, w.offs, reinterpret_cast<uint32_t*>(out.count), n, nullptr,
-                              w.scan_tmp, stream);
-    if (e != cudaSuccess) return e;
-    // 3. emit (tile, gid) instances in depth order; the tile sort's result must
-    //    land in out.gids, so pick the starting buffer by the pass parity.
-    const int tile_bits = ceil_log2(T);
-    const int tpasses = rs_passes(tile_bits);
-    uint32_t* gk[2];
+    for (int p = 0; p < DEPTH_PASSES; ++p) {
+        const PassDesc ps = depth_pass(p);
+        const int src = (p + 1) & 1, dst = p & 1;     // pass 0 -> buffer 0 -> 1 -> 0 -> 1
+        if (p > 0) {
+            pass_hist_kernel<<<sg.G_depth, RS_THREADS, 0, stream>>>(w.dkey[src], depth_pass(p - 1).tot, RS_RADIX_MAX,
+                                                                    ps);
+            note_launch();
+        }
+        pass_scan_kernel<<<1 << ps.bits, SORT_G_MAX, 0, stream>>>(ps.hist, ps.G, ps.tot);
+        note_launch();
+        const bool last = p + 1 == DEPTH_PASSES;
+        uint32_t* kout = last ? nullptr : w.dkey[dst];
+        if (p == 0)
+            pass_scatter_kernel<true, false><<<sg.G_depth, RS_THREADS, 0, stream>>>(
+                nullptr, nullptr, proj.depth, proj.tiles_touched, n, kout, w.perm[dst], ps, nullptr, nullptr, 1);
+        else if (!last)
+            pass_scatter_kernel<false, false><<<sg.G_depth, RS_THREADS, 0, stream>>>(
+                w.dkey[src], w.perm[src], nullptr, nullptr, 0, kout, w.perm[dst], ps, nullptr, nullptr, 1);
+        else
+            pass_scatter_kernel<false, true><<<sg.G_depth, RS_THREADS, 0, stream>>>(
+                w.dkey[src], w.perm[src], nullptr, proj.tiles_touched, 0, kout, w.perm[dst], ps, w.cnt, w.esum,
+                sg.G_emit);
+        note_launch();
+    }
+    const uint32_t* perm = w.perm[(DEPTH_PASSES - 1) & 1];
+    // 2. instance offsets (M) and load-balanced emission in depth order; the
+    //    tile sort's result must land in out.gids, so pick the starting buffer
+    //    by the pass parity.
+    uint32_t* gk[2] = {w.inst_tile[0], w.inst_tile[1]};
     uint32_t* gv[2];
-    gk[0] = w.inst_tile[0];
-    gk[1] = w.inst_tile[1];
-    if (tpasses % 2 == 0) {
+    if (tc.passes % 2 == 0) {
         gv[0] = out.gids;
         gv[1] = w.inst_gid_tmp;
     } else {
         gv[0] = w.inst_gid_tmp;
         gv[1] = out.gids;
     }
-    emit_kernel<<<nb, 256, 0, stream>>>(perm, w.cnt, w.offs, reinterpret_cast<const short4*>(proj.rect), n, vd,
-                                        out.capacity, gk[0], gv[0]);
+    emit_offsets_kernel<<<1, SORT_G_MAX, 0, stream>>>(w.esum, sg.G_emit, out.count);
     note_launch();
-    // 4. stable sort of the instances by tile id
-    e = radix_sort_pairs(gk, gv, out.count, 0, out.capacity, tile_bits, w.rb, stream);
-    if (e != cudaSuccess) return e;
-    const uint32_t* tile_sorted = gk[tpasses & 1];
-    // 5. per-tile ranges and optional 64-bit keys
-    int rb = 152 * 8;
+    {
+        NextHist nh = none;
+        if (tc.passes > 0) {
+            const PassDesc q = tile_pass(0);
+            nh = NextHist{q.shift, q.bits, q.hist, q.G};
+        }
+        emit_kernel<<<sg.G_emit, EMIT_THREADS, 0, stream>>>(perm, w.cnt, reinterpret_cast<const short4*>(proj.rect),
+                                                           w.depth_tot, vd, out.capacity, w.esum, sg.G_emit,
+                                                           out.count, gk[0], gv[0], nh);
+        note_launch();
+    }
+    // 3. stable passes over the written instances by tile id (the first
+    //    pass's counts come from the emission)
+    for (int p = 0; p < tc.passes; ++p) {
+        const PassDesc ps = tile_pass(p);
+        if (p > 0) {
+            const PassDesc q = tile_pass(p - 1);
+            pass_hist_kernel<<<sg.G_tile, RS_THREADS, 0, stream>>>(gk[p & 1], q.tot, 1 << q.bits, ps);
+            note_launch();
+        }
+        pass_scan_kernel<<<1 << ps.bits, SORT_G_MAX, 0, stream>>>(ps.hist, ps.G, ps.tot);
+        note_launch();
+        pass_scatter_kernel<false, false><<<sg.G_tile, RS_THREADS, 0, stream>>>(
+            gk[p & 1], gv[p & 1], nullptr, nullptr, 0, gk[(p + 1) & 1], gv[(p + 1) & 1], ps, nullptr, nullptr, 1);
+        note_launch();
+    }
+    const uint32_t* tile_sorted = gk[tc.passes & 1];
+    // 4. per-tile ranges and optional 64-bit keys
+    const int rb = 152 * 8;
     ranges_kernel<<<rb, 256, 0, stream>>>(tile_sorted, out.count, out.capacity,
                                           reinterpret_cast<uint2*>(out.ranges));
     note_launch();
-    if (out.keys)
+    if (out.keys) {
         keys_kernel<<<rb, 256, 0, stream>>>(tile_sorted, out.gids, proj.depth, out.count, out.capacity,
                                             out.keys);
         note_launch();
+    }
     return cudaGetLastError();
 }
 

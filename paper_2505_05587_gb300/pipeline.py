@@ -61,7 +61,7 @@ def project_and_sort(g: B.GaussianTensors, vb: ViewBuffers, stream=None, check_c
     B.bin_sort(vb.proj, g.n, vb.cam, vb.st, vb.bins, vb.sort_ws, stream)
     if not check_capacity:
         return None
-    M = int(vb.bins.count.item())
+    M = B.check_count(int(vb.bins.count.item()))
     if M > vb.bins.capacity:
         vb.grow(int(M * 1.25) + 1024)
         B.bin_sort(vb.proj, g.n, vb.cam, vb.st, vb.bins, vb.sort_ws, stream)

@@ -104,7 +104,7 @@ class RenderServer:
 
     def _finish(self, b: _Batch, now: float, lat: dict) -> _Batch | None:
         self.in_use -= b.nbytes
-        M = int(b.count_host.item())
+        M = B.check_count(int(b.count_host.item()))
         if M > b.capacity:                       # instance capacity too small: rerun with room
             self.stats["reruns"] += 1
             ests = [self._est(j) for j in b.jobs]
