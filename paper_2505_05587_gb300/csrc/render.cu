@@ -280,6 +280,7 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
             const float dy = (fpy - m.y) - m.w;
             const float araw = __fmul_rn(cp.w, gauss2(cp, dx, dy));
             const bool valid = inside && (uint32_t)(start + e) < last && araw >= st.alpha_min;
+            if (!__any_sync(0xffffffffu, valid)) continue;     // nothing composited here by this warp
             const bool clamped = araw >= st.alpha_max;
             // branch-free: an invalid pair has alpha 0, leaving T, the colour
             // behind and every accumulated term unchanged
@@ -295,12 +296,9 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
             const float wdx = w * dx, wdy = w * dy;
             float v[8] = {wdx, wdy, wdx * dx, wdx * dy, wdy * dy, w, g0 * aT, g1 * aT};
             const float v8 = g2 * aT;
-            if (__any_sync(0xffffffffu, valid)) {
-                const float tot8 = warp_reduce_scatter8(v);
-                const float tot1 = warp_sum(v8);
-                if (slot >= 0)
-                    atomicAdd(g2d + (size_t)sm.gid[e] * kG2dStride + slot, slot == 8 ? tot1 : tot8);
-            }
+            const float tot8 = warp_reduce_scatter8(v);
+            const float tot1 = warp_sum(v8);
+            if (slot >= 0) atomicAdd(g2d + (size_t)sm.gid[e] * kG2dStride + slot, slot == 8 ? tot1 : tot8);
         }
     }
     __syncthreads();        // shared memory is reused by the next tile
