@@ -535,12 +535,40 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
     if (need == 0u && accumulate) return;            // nothing in this warp touched any pixel
     const int rows = min(32, n - base);
 
-    // stage the SH coefficient rows (coalesced; zeros where unused); clear increments
-    for (int f = lane; f < rows * K3; f += 32) {
-        const int r = f / K3;
-        const int o = r * ROW + (f - r * K3);
-        wc[o] = ((need >> r) & 1u) ? sh[(size_t)base * K3 + f] : 0.0f;
-        if constexpr (MULTI) wi[o] = 0.0f;
+    // parameters of this lane's Gaussian, loaded before the SH staging so that
+    // their latency overlaps it
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, ls0 = 0.f, ls1 = 0.f, ls2 = 0.f;
+    float4 q4 = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (work) {
+        p0 = means[3 * i]; p1 = means[3 * i + 1]; p2 = means[3 * i + 2];
+        q4 = reinterpret_cast<const float4*>(quats)[i];
+        ls0 = log_scales[3 * i]; ls1 = log_scales[3 * i + 1]; ls2 = log_scales[3 * i + 2];
+    }
+
+    // stage the SH coefficient rows (coalesced; zeros where unused), in
+    // batches of independent loads; clear increments
+    {
+        constexpr int UNR = 8;
+        const int nf = rows * K3;
+        for (int f0 = 0; f0 < nf; f0 += 32 * UNR) {
+            float vals[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int f = f0 + u * 32 + lane;
+                const int r = f / K3;
+                vals[u] = (f < nf && ((need >> r) & 1u)) ? sh[(size_t)base * K3 + f] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int f = f0 + u * 32 + lane;
+                if (f < nf) {
+                    const int r = f / K3;
+                    const int o = r * ROW + (f - r * K3);
+                    wc[o] = vals[u];
+                    if constexpr (MULTI) wi[o] = 0.0f;
+                }
+            }
+        }
     }
     __syncwarp();
 
@@ -548,9 +576,7 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
     float4 gq = make_float4(0.f, 0.f, 0.f, 0.f);
     float S6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (work) {
-        const float p0 = means[3 * i], p1 = means[3 * i + 1], p2 = means[3 * i + 2];
-        const float4 q4 = reinterpret_cast<const float4*>(quats)[i];
-        const float sc[3] = {__expf(log_scales[3 * i]), __expf(log_scales[3 * i + 1]), __expf(log_scales[3 * i + 2])};
+        const float sc[3] = {__expf(ls0), __expf(ls1), __expf(ls2)};
         const float* crow = wc + lane * ROW;
         float* irow = wi + lane * ROW;
         for (int v = 0; v < nv; ++v) {
