@@ -7,7 +7,8 @@ float64 for continuous quantities, compiled with ``-ffp-contract=off``).
 
 Every function cites the passage of the paper it follows in the C source.
 Inputs come from ``synth`` (seeded generators that hold none of the method's
-arithmetic).
+arithmetic).  ``oracle.ssim`` (plain float64 numpy) holds the SSIM term of the
+loss.
 """
 from __future__ import annotations
 
