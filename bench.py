@@ -53,6 +53,23 @@ def _peaks():
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
+# DRAM traffic of one render_bwd_kernel<16,16> launch on this workload, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
+# rasteriser source it was taken from (first 16 hex digits of its SHA-256).
+RENDER_BWD_TRAFFIC = {"bytes": 104_611_328 + 9_628_672, "render_cu_sha256": "a4719d80a5a175e8",
+                      "profile": "profiles/render_bwd_scene_1M_1237x822.md"}
+
+
+def _render_bwd_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2505_05587_gb300", "csrc", "render.cu")
+    try:
+        with open(path, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return RENDER_BWD_TRAFFIC["bytes"] if sha == RENDER_BWD_TRAFFIC["render_cu_sha256"] else None
+
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled while the GPU works."""
@@ -263,11 +280,28 @@ def run_gpu(args):
     else:
         dom = names.index("render_bwd_with_splitting")
         achieved = flops_bwd / (call_ms[dom] * 1e-3) / 1e12
+    # attainable FP32 rate on this GPU: FMA probe (outside the timed region)
+    probe_blocks, probe_iters = 152 * 8, 20000
+    probe_out = torch.empty(probe_blocks * 256, device=dev)
+    B.fma_probe(probe_out, probe_blocks, 2000, stream)
+    fma_ms = []
+    for _ in range(3):
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        B.fma_probe(probe_out, probe_blocks, probe_iters, stream)
+        p1.record(stream)
+        p1.synchronize()
+        fma_ms.append(p0.elapsed_time(p1))
+    fma_tflops = probe_blocks * 256 * probe_iters * 16 / (min(fma_ms) * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": names[dom], "achieved": round(achieved, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
-                "traffic": args.traffic if args.traffic is not None else None,
+                "traffic": args.traffic if args.traffic is not None else (
+                    _render_bwd_traffic() if names[dom] == "render_bwd_with_splitting" else None),
+                "traffic_unit": "bytes per render_bwd_kernel launch (ncu)",
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "peak_check": {"fma_probe_tflops": round(fma_tflops, 2),
+                               "what": "sgs_fma_probe: 1216 blocks x 256 threads x 8 independent FMA chains"},
                 "work": {"pairs_evaluated_fwd": ev_fwd, "pairs_evaluated_bwd": ev_bwd,
                          "pairs_composited": comp, "visible_gaussians": n_vis}}
     hbm = {"bytes_per_iter": alg_bytes, "achieved": round(alg_bytes / (ms_iter * 1e-3) / 1e9, 1),

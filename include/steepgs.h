@@ -192,6 +192,13 @@ int sgs_render_fwd(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera 
 int sgs_render_stats(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
                      const sgs_settings *st, uint32_t *counts, void *stream);
 
+/* FP32 FMA throughput probe (a measurement aid, not on the path): `blocks`
+ * blocks of 256 threads, each thread runs `iters` rounds of 8 independent
+ * fused multiply-adds (16 FLOP per round) and writes one float to
+ * out[blocks * 256].  Timing it gives the attainable FP32 peak that the
+ * rasteriser's ALU roofline is quoted against. */
+int sgs_fma_probe(float *out, int32_t blocks, int32_t iters, void *stream);
+
 /* L1 photometric loss (Section 3, Eq. loss, l = |.|):
  * loss += mean over pixels and channels of |image - target| / n_views and
  * dL_dimage = sign(image - target) / (3 H W n_views).  loss is one device

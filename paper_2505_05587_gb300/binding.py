@@ -110,6 +110,8 @@ def lib():
         L.sgs_render_batch_fwd.restype = C.c_int
         L.sgs_adam_step.argtypes = [P, P, P, P, I64, F, F, F, F, I32, P, P]
         L.sgs_adam_step.restype = C.c_int
+        L.sgs_fma_probe.argtypes = [P, I32, I32, P]
+        L.sgs_fma_probe.restype = C.c_int
         L.sgs_densify_split_noalloc.argtypes = [P, P, F, F, F, P, F, I64, P, I64, P, P, P, P, P]
         for name in ("sgs_project", "sgs_bin_sort_workspace_size", "sgs_bin_sort", "sgs_render_fwd",
                      "sgs_l1_loss_grad", "sgs_render_stats", "sgs_render_bwd_workspace_size", "sgs_render_bwd_with_splitting",
@@ -288,6 +290,12 @@ def render_stats(proj: ProjBuffers, bins: BinBuffers, cam, st, counts, stream=No
     pc, bc, cc, sc = proj.c(), bins.c(), camera_c(cam), settings_c(st)
     _check("sgs_render_stats", lib().sgs_render_stats(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
                                                        _p(counts), _stream(stream)))
+
+
+def fma_probe(out, blocks: int, iters: int, stream=None):
+    """FP32 FMA throughput probe: out float32 [blocks * 256]; 16 * iters FLOP
+    per thread."""
+    _check("sgs_fma_probe", lib().sgs_fma_probe(_p(out), int(blocks), int(iters), _stream(stream)))
 
 
 def l1_loss_grad(image, target, n_views: int, dL_dimage, loss, stream=None):

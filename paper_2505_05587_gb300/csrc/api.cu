@@ -188,6 +188,11 @@ int sgs_render_stats(const sgs_proj* proj, const sgs_bins* bins, const sgs_camer
                                            (cudaStream_t)stream));
 }
 
+int sgs_fma_probe(float* out, int32_t blocks, int32_t iters, void* stream) {
+    if (!out || blocks <= 0 || iters <= 0) return SGS_ERR_INVALID_ARG;
+    return cuda_status(launch_fma_probe(out, blocks, iters, (cudaStream_t)stream));
+}
+
 int sgs_l1_loss_grad(const float* image, const float* target, int32_t height, int32_t width, int32_t n_views,
                      float* dL_dimage, float* loss, void* stream) {
     if (!image || !target || height <= 0 || width <= 0 || n_views <= 0 || !dL_dimage || !loss)

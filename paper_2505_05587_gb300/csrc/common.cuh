@@ -139,6 +139,7 @@ cudaError_t launch_render_bwd_views(const ViewsDev& vd, const sgs_proj& proj, co
                                     const uint32_t* n_contrib, const float* dL, float* g2d, uint32_t* counter,
                                     cudaStream_t stream);
 
+cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t stream);
 cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
                                 const SetDev& st, uint32_t* counts, cudaStream_t stream);
 

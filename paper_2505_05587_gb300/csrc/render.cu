@@ -406,6 +406,28 @@ __global__ void __launch_bounds__(TW * TH) render_stats_kernel(
     counts[py * W + px] = make_uint2(ev, comp);
 }
 
+// FP32 FMA throughput probe (a measurement aid): eight independent FMA chains
+// per thread, `iters` rounds; the result is stored so nothing is folded.
+__global__ void __launch_bounds__(256) fma_probe_kernel(float* __restrict__ out, int iters, float b, float c) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = __fmaf_rn(a[k], b, c);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t stream) {
+    fma_probe_kernel<<<blocks, 256, 0, stream>>>(out, iters, 0.999f, 1e-3f);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
