@@ -180,14 +180,17 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     # warm-up (the first call also sizes the instance buffers)
-    PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=True)
+    PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=True,
+                       lambda_dssim=args.lambda_dssim)
     for _ in range(max(args.warmup - 1, 0)):
-        PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=False)
+        PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=False,
+                           lambda_dssim=args.lambda_dssim)
     torch.cuda.synchronize(dev)
     M = B.check_count(int(vb.bins.count.item()))
     n_out = int(db.n_out.item())
 
-    names = ["zero_accumulators", "project", "bin_sort", "render_fwd", "l1_loss_grad",
+    loss_name = "l1_loss_grad" if args.lambda_dssim is None else "ssim_l1_loss_grad"
+    names = ["zero_accumulators", "project", "bin_sort", "render_fwd", loss_name,
              "render_bwd_with_splitting", "densify_split"]
     NC = len(names)
 
@@ -202,7 +205,7 @@ def run_gpu(args):
         ev[3].record(stream)
         B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib, stream)
         ev[4].record(stream)
-        B.l1_loss_grad(vb.image, target, 1, vb.dL, db.loss, stream)
+        vb.loss_grad(target, 1, db.loss, args.lambda_dssim, stream)
         ev[5].record(stream)
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, vb.dL, db.grads,
                                     db.S, db.bwd_ws, stream, accumulate=False)
@@ -243,7 +246,8 @@ def run_gpu(args):
             for dst, src in zip(g.tensors(), host):
                 dst.copy_(src, non_blocking=True)
             target.copy_(host_tgt, non_blocking=True)
-            PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=False)
+            PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=False,
+                               lambda_dssim=args.lambda_dssim)
             loss_host.copy_(db.loss, non_blocking=True)
             nout_host.copy_(db.n_out, non_blocking=True)
             e1.record(stream)
@@ -314,6 +318,8 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
                    "sh_degree": 3, "tile": "16x16", "instances_M": M, "n_out": n_out,
+                   "loss": "L1" if args.lambda_dssim is None else f"(1-{args.lambda_dssim:g}) L1 + "
+                                                                 f"{args.lambda_dssim:g} (1-SSIM)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between iterations, outside the timed events"},
         "per_call_ms": {nm: round(float(v), 4) for nm, v in zip(names, call_ms)},
@@ -411,6 +417,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lambda-dssim", type=float, default=None,
+                    help="add the SSIM term to the loss: (1 - l) L1 + l (1 - SSIM) (default: L1 only)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()

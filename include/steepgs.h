@@ -192,6 +192,20 @@ int sgs_render_fwd(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera 
 int sgs_render_stats(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
                      const sgs_settings *st, uint32_t *counts, void *stream);
 
+/* Photometric loss with the SSIM term of Gaussian-splatting training
+ * (Section 3, Eq. loss; the paper's analysis keeps only L1, its footnote sets
+ * SSIM aside):  loss += ((1 - lambda) L1 + lambda (1 - SSIM)) / n_views, with
+ * L1 as in sgs_l1_loss_grad and SSIM after Wang et al. (2004): per channel,
+ * 11x11 Gaussian window of sigma 1.5 with zero padding, C1 = 0.01^2,
+ * C2 = 0.03^2, averaged over pixels and channels.  dL_dimage [H,W,3] is
+ * overwritten with the gradient of that loss; lambda_dssim in [0, 1]
+ * (0.2 in Gaussian-splatting training).  ws: sgs_ssim_l1_workspace_size bytes
+ * (nine float maps of H x W). */
+int sgs_ssim_l1_workspace_size(int32_t height, int32_t width, size_t *bytes);
+int sgs_ssim_l1_loss_grad(const float *image, const float *target, int32_t height, int32_t width,
+                          int32_t n_views, float lambda_dssim, float *dL_dimage, float *loss, void *ws,
+                          size_t ws_bytes, void *stream);
+
 /* FP32 FMA throughput probe (a measurement aid, not on the path): `blocks`
  * blocks of 256 threads, each thread runs `iters` rounds of 8 independent
  * fused multiply-adds (16 FLOP per round) and writes one float to

@@ -110,6 +110,10 @@ def lib():
         L.sgs_render_batch_fwd.restype = C.c_int
         L.sgs_adam_step.argtypes = [P, P, P, P, I64, F, F, F, F, I32, P, P]
         L.sgs_adam_step.restype = C.c_int
+        L.sgs_ssim_l1_workspace_size.argtypes = [I32, I32, C.POINTER(SZ)]
+        L.sgs_ssim_l1_workspace_size.restype = C.c_int
+        L.sgs_ssim_l1_loss_grad.argtypes = [P, P, I32, I32, I32, F, P, P, P, SZ, P]
+        L.sgs_ssim_l1_loss_grad.restype = C.c_int
         L.sgs_fma_probe.argtypes = [P, I32, I32, P]
         L.sgs_fma_probe.restype = C.c_int
         L.sgs_densify_split_noalloc.argtypes = [P, P, F, F, F, P, F, I64, P, I64, P, P, P, P, P]
@@ -290,6 +294,20 @@ def render_stats(proj: ProjBuffers, bins: BinBuffers, cam, st, counts, stream=No
     pc, bc, cc, sc = proj.c(), bins.c(), camera_c(cam), settings_c(st)
     _check("sgs_render_stats", lib().sgs_render_stats(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
                                                        _p(counts), _stream(stream)))
+
+
+def ssim_l1_workspace_size(height: int, width: int) -> int:
+    b = C.c_size_t()
+    _check("sgs_ssim_l1_workspace_size", lib().sgs_ssim_l1_workspace_size(int(height), int(width), C.byref(b)))
+    return b.value
+
+
+def ssim_l1_loss_grad(image, target, n_views: int, lambda_dssim: float, dL_dimage, loss, ws, stream=None):
+    """loss += ((1 - lambda) L1 + lambda (1 - SSIM)) / n_views; dL_dimage <- its gradient."""
+    H, W = int(image.shape[0]), int(image.shape[1])
+    _check("sgs_ssim_l1_loss_grad",
+           lib().sgs_ssim_l1_loss_grad(_p(image), _p(target), H, W, n_views, float(lambda_dssim), _p(dL_dimage),
+                                       _p(loss), _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def fma_probe(out, blocks: int, iters: int, stream=None):

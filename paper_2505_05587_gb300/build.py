@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsteepgs.so")
-SOURCES = ["api.cu", "project.cu", "sort.cu", "render.cu", "densify.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "project.cu", "sort.cu", "render.cu", "densify.cu", "ssim.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -188,6 +188,23 @@ int sgs_render_stats(const sgs_proj* proj, const sgs_bins* bins, const sgs_camer
                                            (cudaStream_t)stream));
 }
 
+int sgs_ssim_l1_workspace_size(int32_t height, int32_t width, size_t* bytes) {
+    if (height < 0 || width < 0 || !bytes) return SGS_ERR_INVALID_ARG;
+    *bytes = ssim_ws_bytes(height, width);
+    return SGS_OK;
+}
+
+int sgs_ssim_l1_loss_grad(const float* image, const float* target, int32_t height, int32_t width, int32_t n_views,
+                          float lambda_dssim, float* dL_dimage, float* loss, void* ws, size_t ws_bytes,
+                          void* stream) {
+    if (!image || !target || height <= 0 || width <= 0 || n_views <= 0 || !dL_dimage || !loss ||
+        !(lambda_dssim >= 0.0f && lambda_dssim <= 1.0f))
+        return SGS_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < ssim_ws_bytes(height, width)) return SGS_ERR_WORKSPACE;
+    return cuda_status(launch_ssim_l1(image, target, height, width, n_views, lambda_dssim, dL_dimage, loss, ws,
+                                      (cudaStream_t)stream));
+}
+
 int sgs_fma_probe(float* out, int32_t blocks, int32_t iters, void* stream) {
     if (!out || blocks <= 0 || iters <= 0) return SGS_ERR_INVALID_ARG;
     return cuda_status(launch_fma_probe(out, blocks, iters, (cudaStream_t)stream));

@@ -139,6 +139,9 @@ cudaError_t launch_render_bwd_views(const ViewsDev& vd, const sgs_proj& proj, co
                                     const uint32_t* n_contrib, const float* dL, float* g2d, uint32_t* counter,
                                     cudaStream_t stream);
 
+size_t ssim_ws_bytes(int H, int W);
+cudaError_t launch_ssim_l1(const float* image, const float* target, int H, int W, int n_views, float lam, float* dL,
+                           float* loss, void* ws, cudaStream_t stream);
 cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t stream);
 cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
                                 const SetDev& st, uint32_t* counts, cudaStream_t stream);

@@ -4,7 +4,7 @@ Every step runs in libsteepgs through the binding; this module only owns the
 device buffers (allocated once, reused across iterations) and orders the
 calls on one stream:
 
-    project -> bin_sort -> render_fwd -> l1_loss_grad
+    project -> bin_sort -> render_fwd -> l1_loss_grad (or ssim_l1_loss_grad)
             -> render_bwd_with_splitting (S += P^T(...)P per view)
             -> densify_split (lambda_min, v_min, split, compaction)
 
@@ -35,6 +35,18 @@ class ViewBuffers:
     dL: torch.Tensor
     sort_ws: torch.Tensor
     with_keys: bool = False
+    ssim_ws: torch.Tensor | None = None
+
+    def loss_grad(self, target, n_views: int, loss, lambda_dssim: float | None, stream=None):
+        """dL/dimage of this view into self.dL, loss accumulated: L1, or with
+        lambda_dssim set, (1 - lambda) L1 + lambda (1 - SSIM)."""
+        if lambda_dssim is None:
+            B.l1_loss_grad(self.image, target, n_views, self.dL, loss, stream)
+            return
+        if self.ssim_ws is None:
+            H, W = self.cam.height, self.cam.width
+            self.ssim_ws = B.workspace(B.ssim_l1_workspace_size(H, W), self.image.device)
+        B.ssim_l1_loss_grad(self.image, target, n_views, lambda_dssim, self.dL, loss, self.ssim_ws, stream)
 
     @staticmethod
     def alloc(n: int, cam, st, capacity: int | None = None, with_keys=False, device="cuda") -> "ViewBuffers":
@@ -113,15 +125,17 @@ class DensifyBuffers:
 
 def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: list[torch.Tensor],
                     db: DensifyBuffers, T_split: float = 1.0, eps_split: float = 0.0, step_scale: float = 1.0,
-                    grad_norm=None, eps_grad: float = 0.0, stream=None, check_capacity=True, max_splits: int = 0):
+                    grad_norm=None, eps_grad: float = 0.0, stream=None, check_capacity=True, max_splits: int = 0,
+                    lambda_dssim: float | None = None):
     """One fused fwd+bwd+splitting iteration over the views (Algorithm 1 with
-    the split step taken right after accumulation)."""
+    the split step taken right after accumulation).  lambda_dssim set: the loss
+    has the SSIM term, (1 - lambda) L1 + lambda (1 - SSIM)."""
     db.zero_(grads=False)
     V = len(views)
     for k, (vb, tgt) in enumerate(zip(views, targets)):
         project_and_sort(g, vb, stream, check_capacity)
         B.render_fwd(vb.proj, vb.bins, vb.cam, vb.st, vb.image, vb.final_T, vb.n_contrib, stream)
-        B.l1_loss_grad(vb.image, tgt, V, vb.dL, db.loss, stream)
+        vb.loss_grad(tgt, V, db.loss, lambda_dssim, stream)
         # the first view overwrites the gradients, later views add to them
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, vb.cam, vb.st, vb.final_T, vb.n_contrib, vb.dL,
                                     db.grads, db.S, db.bwd_ws, stream, accumulate=k > 0)
