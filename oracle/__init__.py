@@ -72,9 +72,9 @@ def _load():
             lib.orc_render.argtypes = [P, P, P, P, P, P, P]
             lib.orc_l1_loss_grad.restype = C.c_double
             lib.orc_l1_loss_grad.argtypes = [P, P, C.c_int, C.c_int, C.c_int, P]
-            lib.orc_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
+            lib.orc_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P]
             lib.orc_frozen_eval.restype = C.c_double
-            lib.orc_frozen_eval.argtypes = [P, P, P, C.c_int, P, P, C.c_int, P, P]
+            lib.orc_frozen_eval.argtypes = [P, P, P, C.c_int, P, P, C.c_int, P, P, C.c_double]
             lib.orc_eig3_min.argtypes = [P, C.c_double, C.c_int, P, P]
             lib.orc_jacobi3.argtypes = [P, C.c_int, P, P]
             lib.orc_split.restype = C.c_int
@@ -205,26 +205,29 @@ def l1_loss_grad(image, target, n_views=1):
 
 def backward(scene, cam, st, dL_dC, acc=None):
     """Parameter gradients and full 3x3 splitting matrices of one view
-    (Section 4.4, Algorithm 1).  Accumulates into `acc` when given."""
+    (Section 4.4, Algorithm 1), plus S_po [n,3], the position-opacity block of
+    the splitting matrix over theta = (p, o).  Accumulates into `acc` when given."""
     lib = _load()
     b = _Bound(scene, cam, st)
     n, K = scene.n, (scene.sh_degree + 1) ** 2
     if acc is None:
         acc = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
-                   opacity_logit=np.zeros(n), sh=np.zeros((n, K, 3)), S=np.zeros((n, 3, 3)))
+                   opacity_logit=np.zeros(n), sh=np.zeros((n, K, 3)), S=np.zeros((n, 3, 3)),
+                   S_po=np.zeros((n, 3)))
     grad2d = np.zeros((n, 9))
     dL = np.ascontiguousarray(dL_dC, np.float64)
     lib.orc_backward(*b.refs(), _ptr(dL), _ptr(acc["means"]), _ptr(acc["log_scales"]),
                      _ptr(acc["quats"]), _ptr(acc["opacity_logit"]), _ptr(acc["sh"]),
-                     _ptr(acc["S"]), _ptr(grad2d))
+                     _ptr(acc["S"]), _ptr(acc["S_po"]), _ptr(grad2d))
     acc["grad2d"] = grad2d
     return acc
 
 
-def frozen_eval(scene, cam, st, idx, dp=None, mix_v=None, g=None, target=None):
+def frozen_eval(scene, cam, st, idx, dp=None, mix_v=None, g=None, target=None, d_o=0.0):
     """Loss in the frozen-linearisation model (Appendix "Deriving Hessian of
-    Gaussian") with Gaussian `idx` displaced by dp or replaced by the w = 1/2
-    mixture slot at +-mix_v.  Returns sum g.C (g given) or the L1 loss."""
+    Gaussian") with Gaussian `idx` displaced by dp (opacity by d_o) or replaced
+    by the w = 1/2 mixture slot at (p +- mix_v, o +- d_o).  Returns sum g.C (g
+    given) or the L1 loss."""
     lib = _load()
     b = _Bound(scene, cam, st)
     mode = 0 if g is not None else 1
@@ -233,7 +236,7 @@ def frozen_eval(scene, cam, st, idx, dp=None, mix_v=None, g=None, target=None):
     dp_arr = None if dp is None else np.ascontiguousarray(dp, np.float64)
     mv_arr = None if mix_v is None else np.ascontiguousarray(mix_v, np.float64)
     return lib.orc_frozen_eval(*b.refs(), mode, _ptr(g_arr), _ptr(t_arr), int(idx),
-                               _ptr(dp_arr), _ptr(mv_arr))
+                               _ptr(dp_arr), _ptr(mv_arr), float(d_o))
 
 
 def eig3_min(S, scale=1.0):
@@ -279,6 +282,72 @@ def split(scene, lam, v, eps_split, step_scale=1.0, grad_norm=None, eps_grad=0.0
     for k in list(out):
         out[k] = out[k][:n_out]
     out["flags"] = flags.astype(bool)
+    out["n_out"] = n_out
+    return out
+
+
+def S4_matrix(S, S_po):
+    """Splitting matrices over theta = (p, o) (dim Theta = 4): [[S_pp, S_po],
+    [S_po^T, 0]], the opacity-opacity entry being d^2 sigma / do^2 = 0."""
+    S = np.asarray(S, np.float64)
+    S_po = np.asarray(S_po, np.float64)
+    n = S.shape[0]
+    S4 = np.zeros((n, 4, 4))
+    S4[:, :3, :3] = S
+    S4[:, :3, 3] = S_po
+    S4[:, 3, :3] = S_po
+    return S4
+
+
+def eig_min_sym(S, scale=1.0):
+    """Minimum eigenpair of symmetric matrices [n, d, d] (d small) by LAPACK's
+    symmetric solver; eigenvector sign: the component of largest magnitude is
+    positive (lowest index on ties)."""
+    w, V = np.linalg.eigh(np.asarray(S, np.float64) * scale)
+    lam = w[:, 0].copy()
+    v = V[:, :, 0].copy()
+    k = np.argmax(np.abs(v), axis=1)
+    sgn = np.where(v[np.arange(len(v)), k] < 0, -1.0, 1.0)
+    return lam, v * sgn[:, None]
+
+
+OPACITY_SPLIT_MIN, OPACITY_SPLIT_MAX = 1e-4, 1.0 - 1e-4
+
+
+def split_po(scene, lam, v4, eps_split, step_scale=1.0):
+    """Steepest split over theta = (p, o): Gaussian i with lambda_min < eps_split
+    becomes the w = 1/2 pair at theta +- eps_i v, eps_i = step_scale * max_k
+    exp(log_scale_ik); each offspring keeps half of its displaced opacity,
+    (o +- eps_i v_o) / 2 clamped to [1e-4, 1 - 1e-4]; the parent's row takes
+    the + offspring, the - offspring is appended in index order."""
+    n = scene.n
+    K = (scene.sh_degree + 1) ** 2
+    flags = np.asarray(lam) < eps_split
+    idx = np.nonzero(flags)[0]
+    n_out = n + len(idx)
+    eps = step_scale * np.exp(scene.log_scales.astype(np.float64)).max(axis=1)
+    o = 1.0 / (1.0 + np.exp(-scene.opacity_logit.astype(np.float64)))
+    out = dict(means=np.zeros((n_out, 3)), log_scales=np.zeros((n_out, 3)), quats=np.zeros((n_out, 4)),
+               opacity_logit=np.zeros(n_out), sh=np.zeros((n_out, K, 3)), parent=np.zeros(n_out, np.int32))
+    rows_p = np.arange(n)
+    out["means"][:n] = scene.means
+    out["log_scales"][:n] = scene.log_scales
+    out["quats"][:n] = scene.quats
+    out["opacity_logit"][:n] = scene.opacity_logit
+    out["sh"][:n] = scene.sh
+    out["parent"][:n] = rows_p
+    v4 = np.asarray(v4, np.float64)
+    for r, i in enumerate(idx):
+        j = n + r
+        for row, sgn in ((i, 1.0), (j, -1.0)):
+            out["means"][row] = scene.means[i].astype(np.float64) + sgn * eps[i] * v4[i, :3]
+            oj = np.clip(0.5 * (o[i] + sgn * eps[i] * v4[i, 3]), OPACITY_SPLIT_MIN, OPACITY_SPLIT_MAX)
+            out["opacity_logit"][row] = np.log(oj) - np.log1p(-oj)
+            out["log_scales"][row] = scene.log_scales[i]
+            out["quats"][row] = scene.quats[i]
+            out["sh"][row] = scene.sh[i]
+            out["parent"][row] = i
+    out["flags"] = flags
     out["n_out"] = n_out
     return out
 

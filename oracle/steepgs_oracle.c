@@ -617,7 +617,8 @@ typedef struct {
 } pair_t;
 
 static void backward_view(const orc_scene *sc, const orc_view *v, const orc_camera *cam,
-                          const orc_settings *st, const double *dL_dC, grad2d_t *g2, double *S)
+                          const orc_settings *st, const double *dL_dC, grad2d_t *g2, double *S,
+                          double *S_po)
 {
     int W = cam->width, H = cam->height;
     pair_t *list = NULL;
@@ -672,10 +673,17 @@ static void backward_view(const orc_scene *sc, const orc_view *v, const orc_came
                 gg->Q[0] += dLdG * pp->G * (-0.5 * pp->dx * pp->dx);
                 gg->Q[1] += dLdG * pp->G * (-pp->dx * pp->dy);
                 gg->Q[2] += dLdG * pp->G * (-0.5 * pp->dy * pp->dy);
+                double Y[3];
+                for (int j = 0; j < 3; ++j) Y[j] = pr->P[j] * Qd0 + pr->P[3 + j] * Qd1;
+                if (S_po) {
+                    /* mixed block of the Hessian of sigma = o G(p) w.r.t. theta = (p, o): */
+                    /* d^2 sigma / dp do = dG/dp = G Y  (d^2 sigma / do^2 = 0)               */
+                    double *So = S_po + 3 * (size_t)pp->gid;
+                    for (int a = 0; a < 3; ++a) So[a] += dLda * pp->G * Y[a];
+                }
                 if (S) {
                     /* Hessian of sigma = alpha w.r.t. p (frozen P, Sigma2D, colour) */
-                    double Y[3], PQP[9];
-                    for (int j = 0; j < 3; ++j) Y[j] = pr->P[j] * Qd0 + pr->P[3 + j] * Qd1;
+                    double PQP[9];
                     /* (P^T Q P)_ab = Q00 P0a P0b + Q01 (P0a P1b + P1a P0b) + Q11 P1a P1b */
                     for (int a = 0; a < 3; ++a)
                         for (int b = 0; b < 3; ++b)
@@ -807,16 +815,18 @@ static void chain_to_params(const orc_scene *sc, const orc_camera *cam, const or
 }
 
 /* Accumulates (+=) parameter gradients and the full 3x3 splitting matrices of
- * one view.  grad2d (optional, [N,9] = mu 2, conic a b c 3, opacity 1, rgb 3)
- * receives this view's 2-D gradients (overwritten). */
+ * one view; S_po (optional, [N,3]) accumulates the position-opacity block of
+ * the splitting matrix over theta = (p, o).  grad2d (optional, [N,9] = mu 2,
+ * conic a b c 3, opacity 1, rgb 3) receives this view's 2-D gradients
+ * (overwritten). */
 int orc_backward(const orc_scene *sc, const orc_camera *cam, const orc_settings *st,
                  const double *dL_dC, double *g_means, double *g_log_scales, double *g_quats,
-                 double *g_logit, double *g_sh, double *S, double *grad2d)
+                 double *g_logit, double *g_sh, double *S, double *S_po, double *grad2d)
 {
     orc_view v;
     view_build(sc, cam, st, &v);
     grad2d_t *g2 = (grad2d_t *)calloc((size_t)(sc->n > 0 ? sc->n : 1), sizeof(grad2d_t));
-    backward_view(sc, &v, cam, st, dL_dC, g2, S);
+    backward_view(sc, &v, cam, st, dL_dC, g2, S, S_po);
     for (int i = 0; i < sc->n; ++i) {
         if (grad2d) {
             double *o = grad2d + 9 * (size_t)i;
@@ -836,16 +846,16 @@ int orc_backward(const orc_scene *sc, const orc_camera *cam, const orc_settings 
 /* Frozen-linearisation evaluation (Appendix "Deriving Hessian of Gaussian"): */
 /* Pi is replaced by its affine approximation at the current p (mu(p') =     */
 /* mu + P (p' - p)); P, Sigma2D, colour, opacity, tile lists and order stay   */
-/* at their values at theta.  Gaussian `idx` is displaced by dp, or, when    */
-/* mix_v is given, replaced by the mixture slot                              */
-/* 0.5 sigma(p + mix_v) + 0.5 sigma(p - mix_v) (Theorem 1's w = 1/2 split with */
-/* both offspring sharing the parent's depth slot).                          */
+/* at their values at theta.  Gaussian `idx` is displaced by dp (its opacity */
+/* by d_o), or, when mix_v is given, replaced by the mixture slot            */
+/* 0.5 sigma(p + mix_v, o + d_o) + 0.5 sigma(p - mix_v, o - d_o) (Theorem 1's */
+/* w = 1/2 split with both offspring sharing the parent's depth slot).       */
 /* Returns sum g . C (mode 0) or the L1 loss against `target` (mode 1).      */
 /* ------------------------------------------------------------------------ */
 
 double orc_frozen_eval(const orc_scene *sc, const orc_camera *cam, const orc_settings *st,
                        int mode, const double *g, const float *target, int idx,
-                       const double *dp, const double *mix_v)
+                       const double *dp, const double *mix_v, double d_o)
 {
     orc_view v;
     view_build(sc, cam, st, &v);
@@ -867,11 +877,11 @@ double orc_frozen_eval(const orc_scene *sc, const orc_camera *cam, const orc_set
                     for (int a = 0; a < 2; ++a)
                         for (int j = 0; j < 3; ++j) sh1[a] += pr->P[3 * a + j] * (d1 ? d1[j] : 0.0);
                     double mu1[2] = {pr->mu[0] + sh1[0], pr->mu[1] + sh1[1]};
-                    double a1 = pr->o * gauss2d(mu1, pr->Q, px, py, &dx, &dy);
+                    double a1 = (pr->o + d_o) * gauss2d(mu1, pr->Q, px, py, &dx, &dy);
                     if (mix_v) {
                         for (int a = 0; a < 2; ++a) sh2[a] = -sh1[a];
                         double mu2[2] = {pr->mu[0] + sh2[0], pr->mu[1] + sh2[1]};
-                        double a2 = pr->o * gauss2d(mu2, pr->Q, px, py, &dx, &dy);
+                        double a2 = (pr->o - d_o) * gauss2d(mu2, pr->Q, px, py, &dx, &dy);
                         alpha = 0.5 * a1 + 0.5 * a2;
                     } else {
                         alpha = a1;

@@ -550,3 +550,89 @@ def test_increment_budget_is_the_best_k_subset():
             assert np.array_equal(got["flags"], want), (eps_grad, K)
             assert got["n_out"] == 9 + want.sum()
             assert np.array_equal(got["parent"][9:], np.nonzero(want)[0])
+
+
+# --------------------------------------------------------------------------
+# Splitting matrices over theta = (p, o) (NEXT row f3, dim Theta = 4)
+# --------------------------------------------------------------------------
+
+def _frozen_mixed(sc, cam, st, i, g, h):
+    """Central-difference d^2 (g.C) / dp_a do of the frozen model."""
+    out = np.zeros(3)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        f = lambda dp, do: oracle.frozen_eval(sc, cam, st, i, dp=dp, d_o=do, g=g)   # noqa: E731
+        out[a] = (f(e, h) - f(e, -h) - f(-e, h) + f(-e, -h)) / (4 * h * h)
+    return out
+
+
+def test_position_opacity_block_equals_frozen_hessian():
+    sc = synth.tiny_scene(0)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings().smooth()
+    g = np.random.default_rng(11).normal(size=(64, 64, 3)) / (64 * 64)
+    acc = oracle.backward(sc, cam, st, g)
+    vis = np.nonzero(oracle.integer_stage(sc, cam, st)["tiles"])[0]
+    for i in np.random.default_rng(6).choice(vis, 6, replace=False):
+        h = 2e-3
+        Hr = (4 * _frozen_mixed(sc, cam, st, i, g, h / 2) - _frozen_mixed(sc, cam, st, i, g, h)) / 3
+        rel = np.linalg.norm(Hr - acc["S_po"][i]) / np.linalg.norm(acc["S_po"][i])
+        assert rel < 1e-6, (i, rel)
+        # sigma is linear in o: the opacity-opacity entry is zero
+        f0 = oracle.frozen_eval(sc, cam, st, i, dp=np.zeros(3), g=g)
+        fp = oracle.frozen_eval(sc, cam, st, i, dp=np.zeros(3), d_o=0.05, g=g)
+        fm = oracle.frozen_eval(sc, cam, st, i, dp=np.zeros(3), d_o=-0.05, g=g)
+        assert abs(fp - 2 * f0 + fm) <= 1e-12 * (abs(fp) + abs(fm))
+
+
+def test_4d_split_predicted_decrease_interlacing_and_optimality():
+    sc, cam, st, g, tgt, S = _setup_l1(0)
+    acc = oracle.backward(sc, cam, st, g)
+    S4 = oracle.S4_matrix(acc["S"], acc["S_po"])
+    lam4, v4 = oracle.eig_min_sym(S4)
+    lam3 = np.linalg.eigvalsh(acc["S"])[:, 0]
+    # adding the opacity row and column can only lower the minimum (interlacing)
+    assert np.all(lam4 <= np.minimum(lam3, 0.0) + 1e-12 * np.abs(S4).reshape(len(S4), -1).max(1))
+    # block-diagonal special case: no mixed block -> min(lambda_min(S_pp), 0)
+    l0, _ = oracle.eig_min_sym(oracle.S4_matrix(acc["S"], np.zeros_like(acc["S_po"])))
+    np.testing.assert_allclose(l0, np.minimum(lam3, 0.0), rtol=0, atol=1e-12 * np.abs(acc["S"]).max())
+    base = oracle.frozen_eval(sc, cam, st, 0, dp=np.zeros(3), g=g)
+    scale = np.abs(S4).reshape(len(S4), -1).max(1)
+    for i in np.argsort(-scale)[:6]:
+        s_max = float(np.exp(sc.log_scales[i].astype(np.float64)).max())
+        eps = 1e-2 * s_max
+        pred = 0.5 * eps * eps * lam4[i]
+        meas = oracle.frozen_eval(sc, cam, st, i, mix_v=eps * v4[i, :3], d_o=eps * v4[i, 3], g=g) - base
+        assert abs(meas - pred) <= 1e-3 * abs(pred) + 1e-15, (i, meas, pred)
+        rng = np.random.default_rng(int(i))
+        for _ in range(60):
+            d = rng.normal(size=4)
+            d /= np.linalg.norm(d)
+            dv = oracle.frozen_eval(sc, cam, st, i, mix_v=eps * d[:3], d_o=eps * d[3], g=g) - base
+            assert dv >= meas - 1e-3 * abs(meas) - 1e-15
+
+
+def test_split_po_output_invariants():
+    sc, cam, st, g, tgt, S = _setup_l1(0)
+    acc = oracle.backward(sc, cam, st, g)
+    lam4, v4 = oracle.eig_min_sym(oracle.S4_matrix(acc["S"], acc["S_po"]))
+    out = oracle.split_po(sc, lam4, v4, eps_split=-1e-9, step_scale=0.5)
+    flags = lam4 < -1e-9
+    n = sc.n
+    assert out["n_out"] == n + flags.sum() and np.array_equal(out["flags"], flags)
+    assert np.array_equal(out["parent"][n:], np.nonzero(flags)[0])
+    o = 1 / (1 + np.exp(-sc.opacity_logit.astype(np.float64)))
+    for r, i in enumerate(np.nonzero(flags)[0]):
+        j = n + r
+        eps = 0.5 * np.exp(sc.log_scales[i].astype(np.float64)).max()
+        np.testing.assert_allclose(out["means"][i] - out["means"][j], 2 * eps * v4[i, :3], atol=1e-12)
+        o1 = 1 / (1 + np.exp(-out["opacity_logit"][i]))
+        o2 = 1 / (1 + np.exp(-out["opacity_logit"][j]))
+        want1 = np.clip(0.5 * (o[i] + eps * v4[i, 3]), 1e-4, 1 - 1e-4)
+        want2 = np.clip(0.5 * (o[i] - eps * v4[i, 3]), 1e-4, 1 - 1e-4)
+        assert abs(o1 - want1) < 1e-12 and abs(o2 - want2) < 1e-12
+        if want1 > 1e-4 and want2 > 1e-4:
+            assert abs(o1 + o2 - o[i]) < 1e-12
+    keep = ~flags
+    assert np.array_equal(out["means"][:n][keep], sc.means[keep].astype(np.float64))
