@@ -234,12 +234,17 @@ int sgs_render_bwd_workspace_size(int32_t n, size_t *bytes);
  * (every row, zeros for Gaussians this view does not reach; no prior zeroing
  * needed).  S_accum [N,6] = (xx, xy, xz, yy, yz, zz) is always accumulated
  * (+=), so calling once per view (or per training step) sums over them.
+ * S_po_accum [N,3] (may be NULL): when given, the position-opacity block of
+ * the splitting matrix over theta = (p, o) is accumulated (+=) too:
+ * sum dL/dsigma G P^T u = P^T Q (sum w (x - mu)) / o (the opacity-opacity
+ * entry is 0, sigma being linear in o); with S_accum it forms the 4x4
+ * splitting matrix [[S, S_po], [S_po^T, 0]] that sgs_densify_split takes.
  * Errors: SGS_ERR_INVALID_ARG, SGS_ERR_WORKSPACE. */
 int sgs_render_bwd_with_splitting(const sgs_gaussians *g, const sgs_proj *proj, const sgs_bins *bins,
                                   const sgs_camera *cam, const sgs_settings *st,
                                   const float *final_T, const uint32_t *n_contrib,
                                   const float *dL_dimage, const sgs_grads *grads, int32_t accumulate_grads,
-                                  float *S_accum, void *ws, size_t ws_bytes, void *stream);
+                                  float *S_accum, float *S_po_accum, void *ws, size_t ws_bytes, void *stream);
 
 /* Several views of one scene in one pass (the batched densification step):
  * projection of every (view, Gaussian) pair, one binning and depth sort over
@@ -247,7 +252,8 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians *g, const sgs_proj *proj, 
  * compositing and its backward pass as persistent kernels that pull tiles of
  * all views from a work counter, the L1 loss of every view, and the
  * projection adjoint summing each Gaussian's views: gradients overwritten
- * (accumulate_grads = 0) or added, splitting matrices added to S_accum.
+ * (accumulate_grads = 0) or added, splitting matrices added to S_accum (and
+ * the position-opacity blocks to S_po_accum when it is not NULL).
  *   cams[n_views]      host array, 1 <= n_views <= 16, resolutions may differ;
  *   batch              Gaussians staged per shared-memory batch: 64, 128 or
  *                      256 (0 = min(tile pixels, 256));
@@ -265,7 +271,8 @@ int sgs_render_views_workspace_size(int32_t n, const sgs_camera *cams, int32_t n
 int sgs_render_views_with_splitting(const sgs_gaussians *g, const sgs_camera *cams, int32_t n_views,
                                     const sgs_settings *st, int32_t batch, const float *targets, float *images,
                                     float *loss, const sgs_grads *grads, int32_t accumulate_grads, float *S_accum,
-                                    int32_t *d_count, int64_t capacity, void *ws, size_t ws_bytes, void *stream);
+                                    float *S_po_accum, int32_t *d_count, int64_t capacity, void *ws,
+                                    size_t ws_bytes, void *stream);
 
 /* Forward-only render of a batch of views whose scenes may differ (the
  * render-serving batch): scenes[v] is the scene of view v (sh_degree must be
@@ -305,8 +312,14 @@ int sgs_densify_split_workspace_size(int32_t n, size_t *bytes);
  * d_n_out (device int32) receives N + number of flags; rows at or beyond
  * `capacity` are not written.  parent_index [capacity] (int32, may be NULL),
  * lam_min_out [N] and v_min_out [N,3] (may be NULL) are written.
+ * With S_po_accum [N,3] not NULL the split runs over theta = (p, o) (dim
+ * Theta = 4): lambda_min, v_min (4 components, v_min_out [N,4]) of
+ * [[S, S_po], [S_po^T, 0]] * inv_T_split by cyclic Jacobi rotations (float32)
+ * refined by one Rayleigh quotient, same sign convention; the offspring take
+ * p +- eps_i v_p and opacities (o +- eps_i v_o) / 2, each clamped to
+ * [1e-4, 1 - 1e-4].
  * `out` must not alias `in`.  Errors: SGS_ERR_INVALID_ARG, SGS_ERR_WORKSPACE. */
-int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, float inv_T_split,
+int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, const float *S_po_accum, float inv_T_split,
                       float eps_split, float step_scale, const float *grad_norm, float eps_grad,
                       int64_t max_splits, const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
                       int32_t *parent_index, float *lam_min_out, float *v_min_out,
@@ -331,7 +344,8 @@ int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, float inv_T
  *   - It calls no cudaMalloc, cudaFree or allocating routine. */
 #define SGS_NOALLOC_MAX_GAUSSIANS 1000000
 #define SGS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
-int sgs_densify_split_noalloc(const sgs_gaussians *in, const float *S_accum, float inv_T_split,
+int sgs_densify_split_noalloc(const sgs_gaussians *in, const float *S_accum, const float *S_po_accum,
+                              float inv_T_split,
                               float eps_split, float step_scale, const float *grad_norm, float eps_grad,
                               int64_t max_splits, const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
                               int32_t *parent_index, float *lam_min_out, float *v_min_out, void *stream);

@@ -226,7 +226,8 @@ int sgs_render_bwd_workspace_size(int32_t n, size_t* bytes) {
 int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, const sgs_bins* bins,
                                   const sgs_camera* cam, const sgs_settings* st, const float* final_T,
                                   const uint32_t* n_contrib, const float* dL_dimage, const sgs_grads* grads,
-                                  int32_t accumulate_grads, float* S_accum, void* ws, size_t ws_bytes, void* stream) {
+                                  int32_t accumulate_grads, float* S_accum, float* S_po_accum, void* ws,
+                                  size_t ws_bytes, void* stream) {
     if (!valid_gaussians(g) || !proj || !bins || !valid_cam(cam) || !valid_settings(st) || !final_T ||
         !n_contrib || !dL_dimage || !grads || !tiles_fit(cam, st) || !bins->ranges)
         return SGS_ERR_INVALID_ARG;
@@ -246,7 +247,7 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
     if (e == cudaSuccess) e = launch_render_bwd(*proj, *bins, cd, sd, final_T, n_contrib, dL_dimage, g2d, s);
     if (e == cudaSuccess)
         e = launch_project_bwd(*g, *proj, make_views(cam, 1, *st, nullptr, g->n), g2d, accumulate_grads != 0, *grads,
-                               S_accum, s);
+                               S_accum, S_po_accum, s);
     return cuda_status(e);
 }
 
@@ -328,6 +329,7 @@ int sgs_render_views_workspace_size(int32_t n, const sgs_camera* cams, int32_t n
 int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* cams, int32_t n_views,
                                     const sgs_settings* st, int32_t batch, const float* targets, float* images,
                                     float* loss, const sgs_grads* grads, int32_t accumulate_grads, float* S_accum,
+                                    float* S_po_accum,
                                     int32_t* d_count, int64_t capacity, void* ws, size_t ws_bytes, void* stream) {
     if (!valid_gaussians(g) || !valid_views(cams, n_views, st) || !targets || !images || !loss || !grads ||
         !d_count || capacity < 0 || capacity > ((int64_t)1 << 31) - 1 ||
@@ -357,7 +359,8 @@ int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* ca
     if (e == cudaSuccess)
         e = launch_render_bwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, w.final_T, w.n_contrib,
                                     w.dL, w.g2d, w.counters + 1, s);
-    if (e == cudaSuccess) e = launch_project_bwd(*g, w.proj, vd, w.g2d, accumulate_grads != 0, *grads, S_accum, s);
+    if (e == cudaSuccess)
+        e = launch_project_bwd(*g, w.proj, vd, w.g2d, accumulate_grads != 0, *grads, S_accum, S_po_accum, s);
     return cuda_status(e);
 }
 
@@ -415,11 +418,10 @@ int sgs_densify_split_workspace_size(int32_t n, size_t* bytes) {
     return SGS_OK;
 }
 
-int sgs_densify_split(const sgs_gaussians* in, const float* S_accum, float inv_T_split, float eps_split,
-                      float step_scale, const float* grad_norm, float eps_grad, int64_t max_splits,
-                      const sgs_gaussians_mut* out,
-                      int64_t capacity, int32_t* d_n_out, int32_t* parent_index, float* lam_min_out,
-                      float* v_min_out, void* ws, size_t ws_bytes, void* stream) {
+int sgs_densify_split(const sgs_gaussians* in, const float* S_accum, const float* S_po_accum, float inv_T_split,
+                      float eps_split, float step_scale, const float* grad_norm, float eps_grad, int64_t max_splits,
+                      const sgs_gaussians_mut* out, int64_t capacity, int32_t* d_n_out, int32_t* parent_index,
+                      float* lam_min_out, float* v_min_out, void* ws, size_t ws_bytes, void* stream) {
     if (!valid_gaussians(in) || !out || !d_n_out || capacity < in->n || !isfinite(inv_T_split) ||
         !isfinite(step_scale))
         return SGS_ERR_INVALID_ARG;
@@ -429,10 +431,9 @@ int sgs_densify_split(const sgs_gaussians* in, const float* S_accum, float inv_T
     if (in->n > 0 && (out->means == in->means || out->sh == in->sh || out->opacity_logit == in->opacity_logit))
         return SGS_ERR_INVALID_ARG;
     if (!ws || ws_bytes < densify_ws_bytes(in->n)) return SGS_ERR_WORKSPACE;
-    return cuda_status(launch_densify(*in, S_accum, inv_T_split, eps_split, step_scale, grad_norm, eps_grad,
-                                      max_splits, *out,
-                                      capacity, d_n_out, parent_index, lam_min_out, v_min_out, ws,
-                                      (cudaStream_t)stream));
+    return cuda_status(launch_densify(*in, S_accum, S_po_accum, inv_T_split, eps_split, step_scale, grad_norm,
+                                      eps_grad, max_splits, *out, capacity, d_n_out, parent_index, lam_min_out,
+                                      v_min_out, ws, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -119,6 +119,115 @@ __global__ void __launch_bounds__(256) eig_flag_kernel(const float* __restrict__
     flags[i] = f ? 1u : 0u;
 }
 
+// Minimum eigenpair of the 4x4 splitting matrix over theta = (p, o):
+// [[S, S_po], [S_po^T, 0]] * scale.  Cyclic Jacobi rotations (each zeroes one
+// off-diagonal pair; eight sweeps, far past float32 convergence for 4x4), the
+// eigenvector the column of the accumulated rotations at the smallest
+// diagonal entry, then one Rayleigh quotient and the canonical sign (largest
+// magnitude component positive, lowest index on ties).
+struct Eig4 {
+    float lam;
+    float v[4];
+};
+
+__device__ Eig4 eig4_min(const float* s6, const float* spo, float scale) {
+    float a[4][4];
+    a[0][0] = s6[0] * scale; a[0][1] = s6[1] * scale; a[0][2] = s6[2] * scale;
+    a[1][1] = s6[3] * scale; a[1][2] = s6[4] * scale; a[2][2] = s6[5] * scale;
+    a[0][3] = spo[0] * scale; a[1][3] = spo[1] * scale; a[2][3] = spo[2] * scale; a[3][3] = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < r; ++c) a[r][c] = a[c][r];
+    float V[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) V[r][c] = r == c ? 1.0f : 0.0f;
+#pragma unroll 1
+    for (int sweep = 0; sweep < 8; ++sweep) {
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = p + 1; q < 4; ++q) {
+                const float apq = a[p][q];
+                if (apq == 0.0f) continue;
+                // rotation angle: t = tan(phi) of the smaller root of t^2 + 2 theta t - 1 = 0
+                const float theta = (a[q][q] - a[p][p]) / (2.0f * apq);
+                const float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+                const float c = rsqrtf(t * t + 1.0f), s = t * c;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {              // columns p, q
+                    const float akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - s * akq;
+                    a[k][q] = s * akp + c * akq;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {              // rows p, q
+                    const float apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - s * aqk;
+                    a[q][k] = s * apk + c * aqk;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    int m = 0;
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        if (a[k][k] < a[m][m]) m = k;
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = V[k][m];
+    const float inv = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+    int big = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] *= inv;
+        if (fabsf(v[k]) > fabsf(v[big])) big = k;
+    }
+    const float sg = v[big] < 0.0f ? -1.0f : 1.0f;
+    Eig4 e;
+    float lam = 0.0f;
+    const float b00 = s6[0] * scale, b01 = s6[1] * scale, b02 = s6[2] * scale, b11 = s6[3] * scale;
+    const float b12 = s6[4] * scale, b22 = s6[5] * scale;
+    const float c0 = spo[0] * scale, c1 = spo[1] * scale, c2 = spo[2] * scale;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) e.v[k] = sg * v[k];
+    const float Av0 = b00 * e.v[0] + b01 * e.v[1] + b02 * e.v[2] + c0 * e.v[3];
+    const float Av1 = b01 * e.v[0] + b11 * e.v[1] + b12 * e.v[2] + c1 * e.v[3];
+    const float Av2 = b02 * e.v[0] + b12 * e.v[1] + b22 * e.v[2] + c2 * e.v[3];
+    const float Av3 = c0 * e.v[0] + c1 * e.v[1] + c2 * e.v[2];
+    lam = e.v[0] * Av0 + e.v[1] * Av1 + e.v[2] * Av2 + e.v[3] * Av3;
+    e.lam = lam;
+    return e;
+}
+
+__global__ void __launch_bounds__(256) eig4_flag_kernel(const float* __restrict__ S, const float* __restrict__ S_po,
+                                                        int n, float inv_T, float eps_split,
+                                                        const float* __restrict__ grad_norm, float eps_grad,
+                                                        float* __restrict__ lam_out, float* __restrict__ v_out,
+                                                        uint32_t* __restrict__ flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s6[6], spo[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s6[k] = S[(size_t)i * 6 + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) spo[k] = S_po[(size_t)i * 3 + k];
+    const Eig4 e = eig4_min(s6, spo, inv_T);
+    lam_out[i] = e.lam;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v_out[4 * (size_t)i + k] = e.v[k];
+    bool f = e.lam < eps_split;
+    if (grad_norm) f = f && (grad_norm[i] <= eps_grad);
+    flags[i] = f ? 1u : 0u;
+}
+
 // ---------------------------------------------------------------------------
 // Increment budget (the "Densification with Increment Budget" variant): when
 // more than K Gaussians are flagged, keep the K with the least lambda_min,
@@ -204,8 +313,11 @@ __device__ __forceinline__ float half_opacity_logit(float x) {
 }
 
 // Per-Gaussian fields of the output rows: mean, scales, rotation, opacity,
-// parent index.  Row i holds Gaussian i (moved to p + eps v with o/2 when
-// flagged); row N + excl[i] holds the second offspring p - eps v.
+// parent index.  Row i holds Gaussian i (moved to p + eps v when flagged);
+// row N + excl[i] holds the second offspring p - eps v.  DIM = 3: both
+// offspring take o/2.  DIM = 4 (theta = (p, o)): v has an opacity component
+// and the offspring take (o +- eps v_o) / 2, clamped to [1e-4, 1 - 1e-4].
+template <int DIM>
 __global__ void __launch_bounds__(256) split_fields_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logit, int n, const float* __restrict__ v, const uint32_t* __restrict__ flags,
@@ -224,7 +336,9 @@ __global__ void __launch_bounds__(256) split_fields_kernel(
         eps = step_scale * expf(fmaxf(l0, fmaxf(l1, l2)));
         lg = half_opacity_logit(x);
     }
-    const float v0 = f ? v[3 * i] : 0.0f, v1 = f ? v[3 * i + 1] : 0.0f, v2 = f ? v[3 * i + 2] : 0.0f;
+    const float v0 = f ? v[DIM * i] : 0.0f, v1 = f ? v[DIM * i + 1] : 0.0f, v2 = f ? v[DIM * i + 2] : 0.0f;
+    const float vo = (DIM == 4 && f) ? v[DIM * i + 3] : 0.0f;
+    const float o = 1.0f / (1.0f + expf(-x));
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int64_t row = r == 0 ? (int64_t)i : (f ? (int64_t)n + (int64_t)excl[i] : -1);
@@ -237,7 +351,12 @@ __global__ void __launch_bounds__(256) split_fields_kernel(
         o_ls[3 * row + 1] = l1;
         o_ls[3 * row + 2] = l2;
         reinterpret_cast<float4*>(o_quats)[row] = q;
-        o_logit[row] = lg;
+        if (DIM == 4 && f) {
+            const float oj = fminf(fmaxf(0.5f * (o + sg * vo), 1e-4f), 1.0f - 1e-4f);
+            o_logit[row] = logf(oj) - log1pf(-oj);
+        } else {
+            o_logit[row] = lg;
+        }
         if (parent) parent[row] = i;
     }
 }
@@ -272,14 +391,14 @@ size_t densify_ws_bytes(int n) {
     c.take<uint32_t>(nn);       // excl
     c.take<uint32_t>(1);        // total
     c.take<float>(nn);          // lam (when the caller passes none)
-    c.take<float>(3 * nn);      // v
+    c.take<float>(4 * nn);      // v (4 components over theta = (p, o))
     c.take<char>(scan_tmp_bytes(n));
     c.take<uint32_t>(nn);       // ties at the budget threshold
     c.take<SelectState>(1);
     return c.off + 256;
 }
 
-cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T, float eps_split,
+cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float* S_po, float inv_T, float eps_split,
                            float step_scale, const float* grad_norm, float eps_grad, int64_t max_splits,
                            const sgs_gaussians_mut& out, int64_t capacity, int32_t* d_n_out, int32_t* parent,
                            float* lam_out, float* v_out, void* ws, cudaStream_t stream) {
@@ -290,7 +409,7 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T,
     uint32_t* excl = c.take<uint32_t>(nn);
     uint32_t* total = c.take<uint32_t>(1);
     float* lam_ws = c.take<float>(nn);
-    float* v_ws = c.take<float>(3 * nn);
+    float* v_ws = c.take<float>(4 * nn);
     void* scan_tmp = c.take<char>(scan_tmp_bytes(n));
     uint32_t* tie = c.take<uint32_t>(nn);
     SelectState* sel = c.take<SelectState>(1);
@@ -298,7 +417,10 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T,
     float* v = v_out ? v_out : v_ws;
     if (n == 0) return cudaMemsetAsync(d_n_out, 0, sizeof(int32_t), stream);
     const int nb = (n + 255) / 256;
-    eig_flag_kernel<<<nb, 256, 0, stream>>>(S, n, inv_T, eps_split, grad_norm, eps_grad, lam, v, flags);
+    if (S_po)
+        eig4_flag_kernel<<<nb, 256, 0, stream>>>(S, S_po, n, inv_T, eps_split, grad_norm, eps_grad, lam, v, flags);
+    else
+        eig_flag_kernel<<<nb, 256, 0, stream>>>(S, n, inv_T, eps_split, grad_norm, eps_grad, lam, v, flags);
     note_launch();
     cudaError_t e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
     if (e != cudaSuccess) return e;
@@ -324,9 +446,10 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, float inv_T,
     n_out_kernel<<<1, 1, 0, stream>>>(total, n, d_n_out);
     note_launch();
     const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;
-    split_fields_kernel<<<nb, 256, 0, stream>>>(in.means, in.log_scales, in.quats, in.opacity_logit, n, v, flags,
-                                                excl, step_scale, capacity, out.means, out.log_scales, out.quats,
-                                                out.opacity_logit, parent);
+    auto fields = S_po ? split_fields_kernel<4> : split_fields_kernel<3>;
+    fields<<<nb, 256, 0, stream>>>(in.means, in.log_scales, in.quats, in.opacity_logit, n, v, flags, excl,
+                                   step_scale, capacity, out.means, out.log_scales, out.quats, out.opacity_logit,
+                                   parent);
     note_launch();
     const bool vec4 = K3 % 4 == 0 && (reinterpret_cast<uintptr_t>(in.sh) % 16) == 0 &&
                       (reinterpret_cast<uintptr_t>(out.sh) % 16) == 0;

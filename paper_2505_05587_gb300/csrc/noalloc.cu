@@ -46,19 +46,18 @@ static int scratch_address(void** out) {
 
 using namespace sgs;
 
-extern "C" int sgs_densify_split_noalloc(const sgs_gaussians* in, const float* S_accum, float inv_T_split,
-                                         float eps_split, float step_scale, const float* grad_norm,
-                                         float eps_grad, int64_t max_splits, const sgs_gaussians_mut* out,
-                                         int64_t capacity,
-                                         int32_t* d_n_out, int32_t* parent_index, float* lam_min_out,
-                                         float* v_min_out, void* stream) {
+extern "C" int sgs_densify_split_noalloc(const sgs_gaussians* in, const float* S_accum, const float* S_po_accum,
+                                         float inv_T_split, float eps_split, float step_scale,
+                                         const float* grad_norm, float eps_grad, int64_t max_splits,
+                                         const sgs_gaussians_mut* out, int64_t capacity, int32_t* d_n_out,
+                                         int32_t* parent_index, float* lam_min_out, float* v_min_out,
+                                         void* stream) {
     if (!in || in->n < 0 || in->n > SGS_NOALLOC_MAX_GAUSSIANS) return SGS_ERR_INVALID_ARG;
     if (densify_ws_bytes(in->n) > (size_t)SGS_NOALLOC_SCRATCH_BYTES) return SGS_ERR_WORKSPACE;
     void* ws = nullptr;
     int ce = scratch_address(&ws);
     if (ce != 0) return record_cuda_error((cudaError_t)ce);
-    return sgs_densify_split(in, S_accum, inv_T_split, eps_split, step_scale, grad_norm, eps_grad, max_splits, out,
-                             capacity,
-                             d_n_out, parent_index, lam_min_out, v_min_out, ws, (size_t)SGS_NOALLOC_SCRATCH_BYTES,
-                             stream);
+    return sgs_densify_split(in, S_accum, S_po_accum, inv_T_split, eps_split, step_scale, grad_norm, eps_grad,
+                             max_splits, out, capacity, d_n_out, parent_index, lam_min_out, v_min_out, ws,
+                             (size_t)SGS_NOALLOC_SCRATCH_BYTES, stream);
 }

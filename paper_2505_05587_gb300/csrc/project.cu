@@ -367,7 +367,7 @@ cudaError_t launch_project(const ScenesDev& sc, int sh_degree, const ViewsDev& v
 // Geometry adjoint of one Gaussian in one view: adds the view's splitting
 // matrix to S6 and its parameter gradients to the accumulators.
 __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, float p1, float p2, float4 q4,
-                                                 const float* sc, float4 co, const float* gg, float* S6,
+                                                 const float* sc, float4 co, const float* gg, float* S6, float* Spo,
                                                  float& gm0, float& gm1, float& gm2, float& gl0, float& gl1,
                                                  float& gl2, float4& gq, float& glog) {
     const float* R = cam.R;
@@ -421,6 +421,13 @@ __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, fl
 #pragma unroll
             for (int b = a; b < 3; ++b)
                 S6[k++] += K00 * P[a] * P[b] + K01 * (P[a] * P[3 + b] + P[3 + a] * P[b]) + K11 * P[3 + a] * P[3 + b];
+    }
+    // position-opacity block of the splitting matrix over theta = (p, o):
+    // sum dL/dsigma G P^T Q d = P^T Q (sum w d) / o  (d^2 sigma / dp do = G Y)
+    if (Spo) {
+        const float io = o > 0.0f ? 1.0f / o : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Spo[j] += (P[j] * dmx + P[3 + j] * dmy) * io;
     }
     // opacity: dL/do = a0 / o (unclamped pairs carry alpha = o G)
     glog += (o > 0.0f ? a0 / o : 0.0f) * o * (1.0f - o);
@@ -502,7 +509,8 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
     const float* __restrict__ sh, int n, ViewsDev vd, const float4* __restrict__ conic_opac,
     const uint32_t* __restrict__ tiles, const float* __restrict__ g2d, int accumulate,
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
-    float* __restrict__ g_logit, float* __restrict__ g_sh, float* __restrict__ S_accum) {
+    float* __restrict__ g_logit, float* __restrict__ g_sh, float* __restrict__ S_accum,
+    float* __restrict__ S_po_accum) {
     constexpr int THREADS = MULTI ? 64 : 128;
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int K3 = 3 * K;
@@ -575,6 +583,7 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
     float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, gl0 = 0.f, gl1 = 0.f, gl2 = 0.f, glog = 0.f;
     float4 gq = make_float4(0.f, 0.f, 0.f, 0.f);
     float S6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float Spo[3] = {0.f, 0.f, 0.f};
     if (work) {
         const float sc[3] = {__expf(ls0), __expf(ls1), __expf(ls2)};
         const float* crow = wc + lane * ROW;
@@ -590,8 +599,8 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
                 gg[0] = a.x; gg[1] = a.y; gg[2] = a.z; gg[3] = a.w;
                 gg[4] = b.x; gg[5] = b.y; gg[6] = b.z; gg[7] = b.w; gg[8] = c.x;
             }
-            geometry_adjoint(cam, p0, p1, p2, q4, sc, conic_opac[row], gg, S6, gm0, gm1, gm2, gl0, gl1, gl2, gq,
-                             glog);
+            geometry_adjoint(cam, p0, p1, p2, q4, sc, conic_opac[row], gg, S6, S_po_accum ? Spo : nullptr, gm0,
+                             gm1, gm2, gl0, gl1, gl2, gq, glog);
             // colour (SH) of this view
             const float d0 = p0 - cam.cc[0], d1 = p1 - cam.cc[1], d2 = p2 - cam.cc[2];
             const float inv_dn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -638,6 +647,11 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
         float* So = S_accum + (size_t)i * 6;
 #pragma unroll
         for (int k = 0; k < 6; ++k) So[k] += S6[k];
+        if (S_po_accum) {
+            float* Sp = S_po_accum + (size_t)i * 3;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Sp[k] += Spo[k];
+        }
     }
     if (i < n) {
         if (accumulate) {
@@ -671,7 +685,8 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
 }
 
 cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const ViewsDev& vd, const float* g2d,
-                               bool accumulate, const sgs_grads& grads, float* S_accum, cudaStream_t stream) {
+                               bool accumulate, const sgs_grads& grads, float* S_accum, float* S_po_accum,
+                               cudaStream_t stream) {
     if (g.n == 0) return cudaSuccess;
     const bool multi = vd.nv > 1;
     const int threads = multi ? 64 : 128;
@@ -685,7 +700,7 @@ cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, con
     kern<<<blocks, threads, 0, stream>>>(
         g.means, g.log_scales, g.quats, g.sh, g.n, vd, reinterpret_cast<const float4*>(proj.conic_opac),
         proj.tiles_touched, g2d, accumulate ? 1 : 0, grads.means, grads.log_scales, grads.quats,
-        grads.opacity_logit, grads.sh, S_accum);
+        grads.opacity_logit, grads.sh, S_accum, S_po_accum);
     note_launch();
     return cudaGetLastError();
 }
