@@ -175,7 +175,7 @@ def run_gpu(args):
     g = B.GaussianTensors.from_scene(scene, dev)
     target = torch.as_tensor(target_np).to(dev)
     vb = PL.ViewBuffers.alloc(g.n, cam, st, capacity=4 * g.n, device=dev)
-    db = PL.DensifyBuffers.alloc(g)
+    db = PL.DensifyBuffers.alloc(g, dim_theta=args.dim_theta)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -208,10 +208,10 @@ def run_gpu(args):
         vb.loss_grad(target, 1, db.loss, args.lambda_dssim, stream)
         ev[5].record(stream)
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, vb.dL, db.grads,
-                                    db.S, db.bwd_ws, stream, accumulate=False)
+                                    db.S, db.bwd_ws, stream, accumulate=False, S_po=db.S_po)
         ev[6].record(stream)
         B.densify_split(g, db.S, 1.0, EPS_SPLIT, 1.0, None, 0.0, db.out, db.capacity, db.n_out, db.parent, db.lam,
-                        db.v, db.split_ws, stream)
+                        db.v, db.split_ws, stream, S_po=db.S_po)
         ev[7].record(stream)
 
     K = args.steps
@@ -318,6 +318,7 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
                    "sh_degree": 3, "tile": "16x16", "instances_M": M, "n_out": n_out,
+                   "dim_theta": args.dim_theta,
                    "loss": "L1" if args.lambda_dssim is None else f"(1-{args.lambda_dssim:g}) L1 + "
                                                                  f"{args.lambda_dssim:g} (1-SSIM)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -417,6 +418,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dim-theta", type=int, default=3, choices=[3, 4],
+                    help="splitting matrices over the position (3, the paper's experiments) or (position, opacity)")
     ap.add_argument("--lambda-dssim", type=float, default=None,
                     help="add the SSIM term to the loss: (1 - l) L1 + l (1 - SSIM) (default: L1 only)")
     ap.add_argument("--traffic", type=float, default=None,
