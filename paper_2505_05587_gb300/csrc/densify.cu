@@ -121,10 +121,11 @@ __global__ void __launch_bounds__(256) eig_flag_kernel(const float* __restrict__
 
 // Minimum eigenpair of the 4x4 splitting matrix over theta = (p, o):
 // [[S, S_po], [S_po^T, 0]] * scale.  Cyclic Jacobi rotations (each zeroes one
-// off-diagonal pair; eight sweeps, far past float32 convergence for 4x4), the
-// eigenvector the column of the accumulated rotations at the smallest
-// diagonal entry, then one Rayleigh quotient and the canonical sign (largest
-// magnitude component positive, lowest index on ties).
+// off-diagonal pair), sweeps until the off-diagonal mass is below float32
+// resolution of ||A||_F (at most eight; 4x4 converges quadratically in three or
+// four), the eigenvector the column of the accumulated rotations at the
+// smallest diagonal entry, then one Rayleigh quotient and the canonical sign
+// (largest magnitude component positive, lowest index on ties).
 struct Eig4 {
     float lam;
     float v[4];
@@ -144,8 +145,21 @@ __device__ Eig4 eig4_min(const float* s6, const float* spo, float scale) {
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) V[r][c] = r == c ? 1.0f : 0.0f;
+    // ||A||_F^2 is invariant under the rotations; stop once the off-diagonal
+    // part is below float32 resolution of it (all-zero matrices skip at once)
+    float total = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) total += a[r][c] * a[r][c];
 #pragma unroll 1
     for (int sweep = 0; sweep < 8; ++sweep) {
+        float off = 0.0f;
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = p + 1; q < 4; ++q) off += a[p][q] * a[p][q];
+        if (!(2.0f * off > 1e-14f * total)) break;
 #pragma unroll
         for (int p = 0; p < 3; ++p)
 #pragma unroll

@@ -32,6 +32,7 @@ class RenderContext:
     S: torch.Tensor            # [N,6] splitting-matrix accumulator (added to in backward)
     bwd_ws: torch.Tensor
     sh_degree: int
+    S_po: torch.Tensor | None = None   # [N,3] position-opacity block (theta = (p, o))
 
 
 class RasterizeWithSplitting(torch.autograd.Function):
@@ -55,7 +56,7 @@ class RasterizeWithSplitting(torch.autograd.Function):
         vb = rc.view
         grads = B.GaussianTensors.empty(g.n, g.sh_degree, g.means.device)
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, vb.cam, vb.st, vb.final_T, vb.n_contrib,
-                                    dL_dimage.contiguous(), grads, rc.S, rc.bwd_ws, accumulate=False)
+                                    dL_dimage.contiguous(), grads, rc.S, rc.bwd_ws, accumulate=False, S_po=rc.S_po)
         return grads.means, grads.log_scales, grads.quats, grads.opacity_logit, grads.sh, None
 
 
@@ -73,6 +74,8 @@ class TrainConfig:
     step_scale: float = 1.0
     eps_grad: float | None = None      # compactest gate ||G_bar|| <= eps_grad when set
     max_splits: int = 0                # increment budget per densification (0: none)
+    dim_theta: int = 3                 # splitting matrices over the position (3) or (position, opacity) (4)
+    lambda_dssim: float | None = None  # loss (1 - l) L1 + l (1 - SSIM) when set, else L1
     log_every: int = 10
 
 
@@ -93,11 +96,16 @@ class SteepGSTrainer:
         dev = self.params[0].device
         self.views = [PL.ViewBuffers.alloc(n, c, self.st, device=dev) for c in self.cams]
         self.S = torch.zeros(n, 6, device=dev)
+        self.S_po = torch.zeros(n, 3, device=dev) if self.cfg.dim_theta == 4 else None
         self.G = torch.zeros(n, 3, device=dev)
         self.n_accum = 0
         self.bwd_ws = B.workspace(B.render_bwd_workspace_size(n), dev)
         self.dL = [torch.empty_like(t) for t in self.targets]
         self.loss = torch.zeros(1, device=dev)
+        if self.cfg.lambda_dssim is not None and not hasattr(self, "ssim_ws"):
+            H = max(c.height for c in self.cams)
+            W = max(c.width for c in self.cams)
+            self.ssim_ws = B.workspace(B.ssim_l1_workspace_size(H, W), dev)
 
     @property
     def n(self) -> int:
@@ -108,10 +116,14 @@ class SteepGSTrainer:
 
     def step(self, t: int) -> float | None:
         k = t % len(self.cams)
-        rc = RenderContext(self.views[k], self.S, self.bwd_ws, self.sh_degree)
+        rc = RenderContext(self.views[k], self.S, self.bwd_ws, self.sh_degree, self.S_po)
         image = render(self.params, rc)
         self.loss.zero_()
-        B.l1_loss_grad(image.detach(), self.targets[k], 1, self.dL[k], self.loss)
+        if self.cfg.lambda_dssim is None:
+            B.l1_loss_grad(image.detach(), self.targets[k], 1, self.dL[k], self.loss)
+        else:
+            B.ssim_l1_loss_grad(image.detach(), self.targets[k], 1, self.cfg.lambda_dssim, self.dL[k], self.loss,
+                                self.ssim_ws)
         for p in self.params:
             p.grad = None
         image.backward(self.dL[k])
@@ -137,13 +149,14 @@ class SteepGSTrainer:
         parent = torch.empty(2 * n, dtype=torch.int32, device=dev)
         n_out = torch.zeros(1, dtype=torch.int32, device=dev)
         lam = torch.empty(n, device=dev)
-        vmin = torch.empty(n, 3, device=dev)
+        vmin = torch.empty(n, cfg.dim_theta, device=dev)
         ws = B.workspace(B.densify_split_workspace_size(n), dev)
         gn = None
         if cfg.eps_grad is not None:
             gn = (self.G / max(self.n_accum, 1)).norm(dim=1).contiguous()
         B.densify_split(g, self.S, 1.0 / max(self.n_accum, 1), cfg.eps_split, cfg.step_scale, gn,
-                        cfg.eps_grad or 0.0, out, 2 * n, n_out, parent, lam, vmin, ws, max_splits=cfg.max_splits)
+                        cfg.eps_grad or 0.0, out, 2 * n, n_out, parent, lam, vmin, ws, max_splits=cfg.max_splits,
+                        S_po=self.S_po)
         n2 = int(n_out.item())
         split = n2 - n
         par = parent[:n2].long()

@@ -112,3 +112,22 @@ def test_training_loop_densifies_and_reduces_loss():
     assert tr.n == 1024 + sum(e["split"] for e in events) and tr.n > 1024
     for p in tr.params:
         assert bool(torch.isfinite(p).all())
+
+
+@pytest.mark.parametrize("dim_theta,lam", [(4, None), (3, 0.2), (4, 0.2)])
+def test_training_loop_variants_theta4_and_ssim(dim_theta, lam):
+    """The NEXT-row variants inside Algorithm 1: splitting over (position,
+    opacity) and the SSIM term in the loss."""
+    g, cams, targets, st = TR.config4_problem(n=1024, size=64)
+    cfg = TR.TrainConfig(steps=300, start=100, T_split=100, log_every=20, dim_theta=dim_theta, lambda_dssim=lam)
+    tr = TR.SteepGSTrainer(g, cams, targets, st, cfg)
+    tr.run()
+    losses = [r["loss"] for r in tr.log if "loss" in r]
+    events = [r for r in tr.log if r.get("densify")]
+    assert len(events) == 3 and all(np.isfinite(losses))
+    assert losses[-1] < 0.95 * losses[0]
+    assert tr.n == 1024 + sum(e["split"] for e in events) and tr.n > 1024
+    for p in tr.params:
+        assert bool(torch.isfinite(p).all())
+    o = torch.sigmoid(tr.params[3])
+    assert bool(((o > 0) & (o < 1)).all())
