@@ -190,21 +190,25 @@ __device__ Eig4 eig4_min(const float* s6, const float* spo, float scale) {
                 }
             }
     }
-    int m = 0;
+    // column of the smallest diagonal entry (first on ties), selected with
+    // constant indices so that a and V stay in registers
+    float dmin = a[0][0];
+    float v[4] = {V[0][0], V[1][0], V[2][0], V[3][0]};
 #pragma unroll
-    for (int k = 1; k < 4; ++k)
-        if (a[k][k] < a[m][m]) m = k;
-    float v[4];
+    for (int k = 1; k < 4; ++k) {
+        const bool take = a[k][k] < dmin;
+        dmin = take ? a[k][k] : dmin;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = V[k][m];
+        for (int r = 0; r < 4; ++r) v[r] = take ? V[r][k] : v[r];
+    }
     const float inv = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
-    int big = 0;
+    float big = 0.0f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         v[k] *= inv;
-        if (fabsf(v[k]) > fabsf(v[big])) big = k;
+        big = fabsf(v[k]) > fabsf(big) ? v[k] : big;
     }
-    const float sg = v[big] < 0.0f ? -1.0f : 1.0f;
+    const float sg = big < 0.0f ? -1.0f : 1.0f;
     Eig4 e;
     float lam = 0.0f;
     const float b00 = s6[0] * scale, b01 = s6[1] * scale, b02 = s6[2] * scale, b11 = s6[3] * scale;
