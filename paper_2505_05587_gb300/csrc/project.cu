@@ -5,6 +5,8 @@
 // the affine-Pi footnote (Sigma2D = P Sigma P^T); Appendix "Deriving Hessian of
 // Gaussian" (Hess_p sigma = sigma (Y Y^T - P^T Sigma2D^-1 P), Y = P^T
 // Sigma2D^-1 (x - Pi(p)), with P, Sigma2D and colour frozen).
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sgs {
@@ -366,6 +368,7 @@ cudaError_t launch_project(const ScenesDev& sc, int sh_degree, const ViewsDev& v
 
 // Geometry adjoint of one Gaussian in one view: adds the view's splitting
 // matrix to S6 and its parameter gradients to the accumulators.
+template <bool PO>
 __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, float p1, float p2, float4 q4,
                                                  const float* sc, float4 co, const float* gg, float* S6, float* Spo,
                                                  float& gm0, float& gm1, float& gm2, float& gl0, float& gl1,
@@ -424,7 +427,7 @@ __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, fl
     }
     // position-opacity block of the splitting matrix over theta = (p, o):
     // sum dL/dsigma G P^T Q d = P^T Q (sum w d) / o  (d^2 sigma / dp do = G Y)
-    if (Spo) {
+    if constexpr (PO) {
         const float io = o > 0.0f ? 1.0f / o : 0.0f;
 #pragma unroll
         for (int j = 0; j < 3; ++j) Spo[j] += (P[j] * dmx + P[3 + j] * dmy) * io;
@@ -503,7 +506,7 @@ __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, fl
 // accesses.
 // MULTI = false is the single-view case: no view loop, and the SH gradient
 // increments overwrite the staged coefficients once they have been used.
-template <int DEG, bool MULTI>
+template <int DEG, bool MULTI, bool PO>
 __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ sh, int n, ViewsDev vd, const float4* __restrict__ conic_opac,
@@ -599,8 +602,8 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
                 gg[0] = a.x; gg[1] = a.y; gg[2] = a.z; gg[3] = a.w;
                 gg[4] = b.x; gg[5] = b.y; gg[6] = b.z; gg[7] = b.w; gg[8] = c.x;
             }
-            geometry_adjoint(cam, p0, p1, p2, q4, sc, conic_opac[row], gg, S6, S_po_accum ? Spo : nullptr, gm0,
-                             gm1, gm2, gl0, gl1, gl2, gq, glog);
+            geometry_adjoint<PO>(cam, p0, p1, p2, q4, sc, conic_opac[row], gg, S6, Spo, gm0, gm1, gm2, gl0, gl1,
+                                 gl2, gq, glog);
             // colour (SH) of this view
             const float d0 = p0 - cam.cc[0], d1 = p1 - cam.cc[1], d2 = p2 - cam.cc[2];
             const float inv_dn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -647,7 +650,7 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
         float* So = S_accum + (size_t)i * 6;
 #pragma unroll
         for (int k = 0; k < 6; ++k) So[k] += S6[k];
-        if (S_po_accum) {
+        if constexpr (PO) {
             float* Sp = S_po_accum + (size_t)i * 3;
 #pragma unroll
             for (int k = 0; k < 3; ++k) Sp[k] += Spo[k];
@@ -691,12 +694,18 @@ cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, con
     const bool multi = vd.nv > 1;
     const int threads = multi ? 64 : 128;
     const int blocks = (g.n + threads - 1) / threads;
-    auto kern = multi ? (g.sh_degree == 0 ? project_bwd_kernel<0, true>
-                       : g.sh_degree == 1 ? project_bwd_kernel<1, true>
-                       : g.sh_degree == 2 ? project_bwd_kernel<2, true> : project_bwd_kernel<3, true>)
-                      : (g.sh_degree == 0 ? project_bwd_kernel<0, false>
-                       : g.sh_degree == 1 ? project_bwd_kernel<1, false>
-                       : g.sh_degree == 2 ? project_bwd_kernel<2, false> : project_bwd_kernel<3, false>);
+    auto pick = [&](auto po) {
+        constexpr bool PO = decltype(po)::value;
+        return multi ? (g.sh_degree == 0 ? project_bwd_kernel<0, true, PO>
+                      : g.sh_degree == 1 ? project_bwd_kernel<1, true, PO>
+                      : g.sh_degree == 2 ? project_bwd_kernel<2, true, PO> : project_bwd_kernel<3, true, PO>)
+                     : (g.sh_degree == 0 ? project_bwd_kernel<0, false, PO>
+                      : g.sh_degree == 1 ? project_bwd_kernel<1, false, PO>
+                      : g.sh_degree == 2 ? project_bwd_kernel<2, false, PO> : project_bwd_kernel<3, false, PO>);
+    };
+    // the position-opacity block is a separate instantiation, so the common
+    // position-only kernel carries none of its code
+    auto kern = S_po_accum ? pick(std::true_type{}) : pick(std::false_type{});
     kern<<<blocks, threads, 0, stream>>>(
         g.means, g.log_scales, g.quats, g.sh, g.n, vd, reinterpret_cast<const float4*>(proj.conic_opac),
         proj.tiles_touched, g2d, accumulate ? 1 : 0, grads.means, grads.log_scales, grads.quats,

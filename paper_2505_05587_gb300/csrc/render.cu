@@ -75,8 +75,8 @@ __device__ __forceinline__ float4 alpha_support_box(float4 m, float4 co, float a
     return make_float4(cx - ex, cx + ex, cy - ey, cy + ey);
 }
 
-// Order-preserving list of the batch entries whose support box meets the
-// warp's pixel block [bx, bx+7] x [by, by+3].  Returns the list length.
+// Order-preserving list of the batch entries [0, cnt) whose support box meets
+// the warp's pixel block [bx, bx+7] x [by, by+3].  Returns the list length.
 __device__ __forceinline__ int build_warp_list(const float4* s_box, int cnt, float bx, float by,
                                                uint8_t* list) {
     const int lane = threadIdx.x & 31;
@@ -248,10 +248,11 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
 
     if (threadIdx.x == 0) sm.maxl = 0u;
     __syncthreads();
-    {
-        const uint32_t m = __reduce_max_sync(0xffffffffu, last);
-        if (lane == 0) atomicMax(&sm.maxl, m);
-    }
+    // entries at or past a pixel's last contributor composite nothing there:
+    // the tile walks up to the largest last of its pixels, each warp's list
+    // stops at the largest last of its own pixels
+    const int warp_last = (int)__reduce_max_sync(0xffffffffu, last);
+    if (lane == 0) atomicMax(&sm.maxl, (uint32_t)warp_last);
     __syncthreads();
     const int maxl = min((int)sm.maxl, (int)(rg.y - rg.x));
 
@@ -270,7 +271,8 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
             sm.box[k] = alpha_support_box(m, co, st.alpha_min);
         }
         __syncthreads();
-        const int nl = build_warp_list(sm.box, cnt, (float)bx, (float)by, sm.list[warp]);
+        const int wcnt = min(cnt, warp_last - start);    // this warp's entries end at its last contributor
+        const int nl = wcnt > 0 ? build_warp_list(sm.box, wcnt, (float)bx, (float)by, sm.list[warp]) : 0;
         for (int k = nl - 1; k >= 0; --k) {
             const int e = sm.list[warp][k];
             const float4 m = sm.xy[e];
