@@ -70,6 +70,8 @@ def _load():
             lib.orc_bin_sort.restype = C.c_int64
             lib.orc_bin_sort.argtypes = [P, P, P, P, P, P, C.c_int64]
             lib.orc_render.argtypes = [P, P, P, P, P, P, P]
+            lib.orc_render_rows.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P]
+            lib.orc_backward_rows.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P]
             lib.orc_l1_loss_grad.restype = C.c_double
             lib.orc_l1_loss_grad.argtypes = [P, P, C.c_int, C.c_int, C.c_int, P]
             lib.orc_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P]
@@ -179,16 +181,20 @@ def bin_sort(scene, cam, st):
     return keys[:M], gids[:M], ranges
 
 
-def render(scene, cam, st):
-    """Front-to-back compositing (Section 3, Eq. alpha_blend), float64."""
+def render(scene, cam, st, rows=None):
+    """Front-to-back compositing (Section 3, Eq. alpha_blend), float64.
+    rows = (y0, h): only rows [y0, y0 + h) of the same view ([h, W] outputs)."""
     lib = _load()
     b = _Bound(scene, cam, st)
-    H, W = cam.height, cam.width
+    y0, H = (0, cam.height) if rows is None else rows
+    W = cam.width
     image = np.zeros((H, W, 3))
     final_T = np.zeros((H, W))
     n_contrib = np.zeros((H, W), np.int32)
     band = np.zeros((H, W), np.uint8)
-    lib.orc_render(*b.refs(), _ptr(image), _ptr(final_T), _ptr(n_contrib), _ptr(band))
+    if lib.orc_render_rows(*b.refs(), int(y0), int(H), _ptr(image), _ptr(final_T), _ptr(n_contrib),
+                           _ptr(band)) != 0:
+        raise ValueError("rows outside the view")
     return dict(image=image, final_T=final_T, n_contrib=n_contrib, band=band.astype(bool))
 
 
@@ -203,10 +209,12 @@ def l1_loss_grad(image, target, n_views=1):
     return L, g
 
 
-def backward(scene, cam, st, dL_dC, acc=None):
+def backward(scene, cam, st, dL_dC, acc=None, rows=None):
     """Parameter gradients and full 3x3 splitting matrices of one view
     (Section 4.4, Algorithm 1), plus S_po [n,3], the position-opacity block of
-    the splitting matrix over theta = (p, o).  Accumulates into `acc` when given."""
+    the splitting matrix over theta = (p, o).  Accumulates into `acc` when given.
+    rows = (y0, h): only rows [y0, y0 + h) of the same view carry gradient
+    (dL_dC is [h, W, 3])."""
     lib = _load()
     b = _Bound(scene, cam, st)
     n, K = scene.n, (scene.sh_degree + 1) ** 2
@@ -216,9 +224,13 @@ def backward(scene, cam, st, dL_dC, acc=None):
                    S_po=np.zeros((n, 3)))
     grad2d = np.zeros((n, 9))
     dL = np.ascontiguousarray(dL_dC, np.float64)
-    lib.orc_backward(*b.refs(), _ptr(dL), _ptr(acc["means"]), _ptr(acc["log_scales"]),
-                     _ptr(acc["quats"]), _ptr(acc["opacity_logit"]), _ptr(acc["sh"]),
-                     _ptr(acc["S"]), _ptr(acc["S_po"]), _ptr(grad2d))
+    y0, h = (0, cam.height) if rows is None else rows
+    if dL.shape[:2] != (h, cam.width):
+        raise ValueError("dL_dC must cover the rows")
+    if lib.orc_backward_rows(*b.refs(), int(y0), int(h), _ptr(dL), _ptr(acc["means"]), _ptr(acc["log_scales"]),
+                             _ptr(acc["quats"]), _ptr(acc["opacity_logit"]), _ptr(acc["sh"]),
+                             _ptr(acc["S"]), _ptr(acc["S_po"]), _ptr(grad2d)) != 0:
+        raise ValueError("rows outside the view")
     acc["grad2d"] = grad2d
     return acc
 

@@ -531,11 +531,12 @@ static int near_thr(double v, double thr)
     return fabs(v - thr) <= BAND_REL * fabs(thr);
 }
 
-static void render_view(const orc_view *v, const orc_camera *cam, const orc_settings *st,
+/* Rows [y0, y1) of the view; outputs are [(y1 - y0), W] (row py at py - y0). */
+static void render_view(const orc_view *v, const orc_camera *cam, const orc_settings *st, int y0, int y1,
                         double *image, double *final_T, int32_t *n_contrib, uint8_t *band)
 {
-    int W = cam->width, H = cam->height;
-    for (int py = 0; py < H; ++py)
+    int W = cam->width;
+    for (int py = y0; py < y1; ++py)
         for (int px = 0; px < W; ++px) {
             int tile = (py / st->tile_h) * v->gx + (px / st->tile_w);
             uint32_t s = v->ranges[2 * tile], e = v->ranges[2 * tile + 1];
@@ -556,7 +557,7 @@ static void render_view(const orc_view *v, const orc_camera *cam, const orc_sett
                 T = Tn;
                 last = (int)(k - s) + 1;
             }
-            size_t pix = (size_t)py * W + px;
+            size_t pix = (size_t)(py - y0) * W + px;
             for (int ch = 0; ch < 3; ++ch) image[3 * pix + ch] = C[ch] + T * st->bg[ch];
             if (final_T) final_T[pix] = T;
             if (n_contrib) n_contrib[pix] = last;
@@ -569,7 +570,20 @@ int orc_render(const orc_scene *sc, const orc_camera *cam, const orc_settings *s
 {
     orc_view v;
     view_build(sc, cam, st, &v);
-    render_view(&v, cam, st, image, final_T, n_contrib, band);
+    render_view(&v, cam, st, 0, cam->height, image, final_T, n_contrib, band);
+    view_free(&v);
+    return 0;
+}
+
+/* Rows [y0, y0 + h) of the full view (the same projection, tiles and lists as
+ * the whole image); outputs are [h, W]. */
+int orc_render_rows(const orc_scene *sc, const orc_camera *cam, const orc_settings *st, int y0, int h,
+                    double *image, double *final_T, int32_t *n_contrib, uint8_t *band)
+{
+    if (y0 < 0 || h < 0 || y0 + h > cam->height) return -1;
+    orc_view v;
+    view_build(sc, cam, st, &v);
+    render_view(&v, cam, st, y0, y0 + h, image, final_T, n_contrib, band);
     view_free(&v);
     return 0;
 }
@@ -616,14 +630,15 @@ typedef struct {
     int clamped;
 } pair_t;
 
+/* Rows [y0, y1) of the view; dL_dC is [(y1 - y0), W, 3] (row py at py - y0). */
 static void backward_view(const orc_scene *sc, const orc_view *v, const orc_camera *cam,
-                          const orc_settings *st, const double *dL_dC, grad2d_t *g2, double *S,
+                          const orc_settings *st, int y0, int y1, const double *dL_dC, grad2d_t *g2, double *S,
                           double *S_po)
 {
-    int W = cam->width, H = cam->height;
+    int W = cam->width;
     pair_t *list = NULL;
     size_t cap = 0;
-    for (int py = 0; py < H; ++py)
+    for (int py = y0; py < y1; ++py)
         for (int px = 0; px < W; ++px) {
             int tile = (py / st->tile_h) * v->gx + (px / st->tile_w);
             uint32_t s = v->ranges[2 * tile], e = v->ranges[2 * tile + 1];
@@ -649,7 +664,7 @@ static void backward_view(const orc_scene *sc, const orc_view *v, const orc_came
                 ++nl;
                 T = Tn;
             }
-            size_t pix = (size_t)py * W + px;
+            size_t pix = (size_t)(py - y0) * W + px;
             const double *g = dL_dC + 3 * pix;
             double B[3] = {st->bg[0], st->bg[1], st->bg[2]};
             for (int k = nl - 1; k >= 0; --k) {
@@ -815,18 +830,20 @@ static void chain_to_params(const orc_scene *sc, const orc_camera *cam, const or
 }
 
 /* Accumulates (+=) parameter gradients and the full 3x3 splitting matrices of
- * one view; S_po (optional, [N,3]) accumulates the position-opacity block of
+ * rows [y0, y0 + h) of one view (dL_dC is [h, W, 3]; orc_backward: all rows),
+ * pixels outside carrying no gradient; S_po (optional, [N,3]) accumulates the position-opacity block of
  * the splitting matrix over theta = (p, o).  grad2d (optional, [N,9] = mu 2,
  * conic a b c 3, opacity 1, rgb 3) receives this view's 2-D gradients
  * (overwritten). */
-int orc_backward(const orc_scene *sc, const orc_camera *cam, const orc_settings *st,
-                 const double *dL_dC, double *g_means, double *g_log_scales, double *g_quats,
-                 double *g_logit, double *g_sh, double *S, double *S_po, double *grad2d)
+int orc_backward_rows(const orc_scene *sc, const orc_camera *cam, const orc_settings *st, int y0, int h,
+                      const double *dL_dC, double *g_means, double *g_log_scales, double *g_quats,
+                      double *g_logit, double *g_sh, double *S, double *S_po, double *grad2d)
 {
+    if (y0 < 0 || h < 0 || y0 + h > cam->height) return -1;
     orc_view v;
     view_build(sc, cam, st, &v);
     grad2d_t *g2 = (grad2d_t *)calloc((size_t)(sc->n > 0 ? sc->n : 1), sizeof(grad2d_t));
-    backward_view(sc, &v, cam, st, dL_dC, g2, S, S_po);
+    backward_view(sc, &v, cam, st, y0, y0 + h, dL_dC, g2, S, S_po);
     for (int i = 0; i < sc->n; ++i) {
         if (grad2d) {
             double *o = grad2d + 9 * (size_t)i;
@@ -840,6 +857,14 @@ int orc_backward(const orc_scene *sc, const orc_camera *cam, const orc_settings 
     free(g2);
     view_free(&v);
     return 0;
+}
+
+int orc_backward(const orc_scene *sc, const orc_camera *cam, const orc_settings *st,
+                 const double *dL_dC, double *g_means, double *g_log_scales, double *g_quats,
+                 double *g_logit, double *g_sh, double *S, double *S_po, double *grad2d)
+{
+    return orc_backward_rows(sc, cam, st, 0, cam->height, dL_dC, g_means, g_log_scales, g_quats, g_logit, g_sh,
+                             S, S_po, grad2d);
 }
 
 /* ------------------------------------------------------------------------ */

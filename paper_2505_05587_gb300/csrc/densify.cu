@@ -26,10 +26,11 @@ __device__ __forceinline__ void cross3(const float* a, const float* b, float* c)
 }
 
 // Minimum eigenpair of the symmetric matrix (xx, xy, xz, yy, yz, zz).
-// Trigonometric root formula for lambda; eigenvector from the largest cross
-// product of two rows of A - lambda I (with a repeated-root fallback); then one
-// Rayleigh quotient v^T A v, which restores full float32 accuracy of lambda
-// where the arccos loses digits (a near-repeated minimum root).
+// Trigonometric root formula; when the two smallest roots are the close pair
+// (det(B)/2 > 0) the largest, well-separated eigenpair is deflated and the
+// 2x2 block on its complement is solved in closed form; otherwise the
+// eigenvector is the largest cross product of two rows of A - lambda I (with a
+// repeated-root fallback).  Then one Rayleigh quotient v^T A v.
 __device__ Eig eig3_min(const float* s6, float scale) {
     const float a00 = s6[0] * scale, a01 = s6[1] * scale, a02 = s6[2] * scale;
     const float a11 = s6[3] * scale, a12 = s6[4] * scale, a22 = s6[5] * scale;
@@ -51,6 +52,76 @@ __device__ Eig eig3_min(const float* s6, float scale) {
                        B02 * (B01 * B12 - B11 * B02);
     const float r = fminf(fmaxf(0.5f * detB, -1.0f), 1.0f);
     const float phi = acosf(r) * (1.0f / 3.0f);
+    if (r > 0.0f) {
+        // The two smallest roots are the close pair (r -> 1 makes them equal),
+        // where arccos loses ~sqrt(eps) p and their eigenvectors mix.  Deflate
+        // the well-separated largest eigenpair and take the smaller eigenvalue
+        // of the 2x2 block on its orthogonal complement in closed form.
+        const float lmax = q + 2.0f * p * cosf(phi);
+        const float m0[3] = {a00 - lmax, a01, a02};
+        const float m1[3] = {a01, a11 - lmax, a12};
+        const float m2[3] = {a02, a12, a22 - lmax};
+        float cc[3][3];
+        cross3(m0, m1, cc[0]);
+        cross3(m0, m2, cc[1]);
+        cross3(m1, m2, cc[2]);
+        float nb = 0.0f, b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float nk = cc[k][0] * cc[k][0] + cc[k][1] * cc[k][1] + cc[k][2] * cc[k][2];
+            const bool take = nk > nb;
+            nb = take ? nk : nb;
+            b0 = take ? cc[k][0] : b0;
+            b1 = take ? cc[k][1] : b1;
+            b2 = take ? cc[k][2] : b2;
+        }
+        if (nb > 0.0f) {
+            const float in = rsqrtf(nb);
+            const float u[3] = {b0 * in, b1 * in, b2 * in};   // v_max
+            // orthonormal basis (e1, e2) of v_max's complement
+            const float au0 = fabsf(u[0]), au1 = fabsf(u[1]), au2 = fabsf(u[2]);
+            float ax[3] = {0.0f, 0.0f, 0.0f};
+            if (au0 <= au1 && au0 <= au2) ax[0] = 1.0f;
+            else if (au1 <= au2) ax[1] = 1.0f;
+            else ax[2] = 1.0f;
+            float e1[3], e2[3];
+            cross3(u, ax, e1);
+            const float i1 = rsqrtf(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+            e1[0] *= i1; e1[1] *= i1; e1[2] *= i1;
+            cross3(u, e1, e2);
+            const float A1[3] = {a00 * e1[0] + a01 * e1[1] + a02 * e1[2], a01 * e1[0] + a11 * e1[1] + a12 * e1[2],
+                                 a02 * e1[0] + a12 * e1[1] + a22 * e1[2]};
+            const float A2[3] = {a00 * e2[0] + a01 * e2[1] + a02 * e2[2], a01 * e2[0] + a11 * e2[1] + a12 * e2[2],
+                                 a02 * e2[0] + a12 * e2[1] + a22 * e2[2]};
+            const float m00 = e1[0] * A1[0] + e1[1] * A1[1] + e1[2] * A1[2];
+            const float m01 = e1[0] * A2[0] + e1[1] * A2[1] + e1[2] * A2[2];
+            const float m11 = e2[0] * A2[0] + e2[1] * A2[1] + e2[2] * A2[2];
+            const float h = 0.5f * (m00 - m11);
+            const float sq = sqrtf(h * h + m01 * m01);
+            // eigenvector of [[m00, m01], [m01, m11]] for m_mean - sq, from the
+            // better-conditioned row
+            const float w0 = h >= 0.0f ? m01 : sq - h;
+            const float w1 = h >= 0.0f ? -(h + sq) : -m01;
+            float v[3] = {w0 * e1[0] + w1 * e2[0], w0 * e1[1] + w1 * e2[1], w0 * e1[2] + w1 * e2[2]};
+            const float nv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+            if (nv > 0.0f) {
+                const float iv = rsqrtf(nv);
+                v[0] *= iv; v[1] *= iv; v[2] *= iv;
+            } else {
+                v[0] = e1[0]; v[1] = e1[1]; v[2] = e1[2];
+            }
+            float big = v[0];
+            if (fabsf(v[1]) > fabsf(big)) big = v[1];
+            if (fabsf(v[2]) > fabsf(big)) big = v[2];
+            if (big < 0.0f) { v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2]; }
+            const float Av0 = a00 * v[0] + a01 * v[1] + a02 * v[2];
+            const float Av1 = a01 * v[0] + a11 * v[1] + a12 * v[2];
+            const float Av2 = a02 * v[0] + a12 * v[1] + a22 * v[2];
+            e.lam = v[0] * Av0 + v[1] * Av1 + v[2] * Av2;
+            e.v[0] = v[0]; e.v[1] = v[1]; e.v[2] = v[2];
+            return e;
+        }
+    }
     const float lam0 = q + 2.0f * p * cosf(phi + 2.0943951023931953f);
     const float r0[3] = {a00 - lam0, a01, a02};
     const float r1[3] = {a01, a11 - lam0, a12};

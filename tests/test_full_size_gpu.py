@@ -1,0 +1,127 @@
+"""Parity at the benchmark's full size (1M Gaussians from the 64-cluster
+mixture, SH3, one 1237x822 view, 16x16 tiles) in the launch configuration the
+benchmark times (single-view project, bin_sort, render_fwd,
+render_bwd_with_splitting, densify_split):
+
+  * integer stage and binning: every row and every instance, bit for bit;
+  * colours: horizontal strips of rows that the oracle renders from the full
+    view (same projection, tiles and lists);
+  * backward: dL/dimage non-zero on those strips only, against the oracle's
+    backward of the same rows;
+  * eigenpairs and the split of all 1M Gaussians from the GPU's splitting
+    matrices.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+from paper_2505_05587_gb300 import binding as B  # noqa: E402
+from paper_2505_05587_gb300 import pipeline as PL  # noqa: E402
+
+N, W, H = 1_000_000, 1237, 822
+FIELDS = ("means", "log_scales", "quats", "opacity_logit", "sh")
+STRIPS = [(0, 16), (403, 13), (816, 6)]        # (first row, rows): tile rows, a ragged middle, the bottom edge
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+def _upper6(S):
+    return np.stack([S[:, 0, 0], S[:, 0, 1], S[:, 0, 2], S[:, 1, 1], S[:, 1, 2], S[:, 2, 2]], 1)
+
+
+@pytest.fixture(scope="module")
+def full():
+    scene = synth.cluster_scene(0, N, 3)
+    cam = synth.scene_camera(W, H)
+    st = synth.Settings()
+    g = B.GaussianTensors.from_scene(scene)
+    vb = PL.ViewBuffers.alloc(g.n, cam, st, capacity=4 * g.n, with_keys=True)
+    PL.project_and_sort(g, vb)
+    B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib)
+    torch.cuda.synchronize()
+    return scene, cam, st, g, vb
+
+
+def test_full_size_integer_stage_and_binning_bit_exact(full):
+    scene, cam, st, g, vb = full
+    ref = oracle.integer_stage(scene, cam, st)
+    tiles = vb.proj.tiles_touched.cpu().numpy().astype(np.int64)
+    assert np.array_equal(tiles, ref["tiles"])
+    vis = tiles > 0
+    rect = vb.proj.rect.cpu().numpy().reshape(N, 4).astype(np.int32)     # (x0, y0, x1, y1)
+    assert np.array_equal(rect[vis][:, [0, 2, 1, 3]], ref["rect"][vis])    # oracle: (x0, x1, y0, y1)
+    depth = vb.proj.depth.cpu().numpy()
+    assert np.array_equal(depth[vis].view(np.uint32), ref["depth"][vis].astype(np.float32).view(np.uint32))
+    keys, gids, ranges = oracle.bin_sort(scene, cam, st)
+    M = int(vb.bins.count.item())
+    assert M == len(gids)
+    assert np.array_equal(vb.bins.gids[:M].cpu().numpy().view(np.uint32), gids)
+    assert np.array_equal(vb.bins.keys[:M].cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(vb.bins.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), ranges)
+
+
+def test_full_size_colours_on_strips(full):
+    scene, cam, st, g, vb = full
+    img = vb.image.cpu().numpy().astype(np.float64)
+    for y0, h in STRIPS:
+        r = oracle.render(scene, cam, st, rows=(y0, h))
+        ok = ~r["band"]
+        assert ok.mean() > 0.999
+        d = np.abs(img[y0:y0 + h] - r["image"])[ok]
+        assert d.max() < 1e-5, (y0, d.max())
+        assert np.array_equal(vb.n_contrib.cpu().numpy()[y0:y0 + h][ok], r["n_contrib"][ok])
+
+
+def test_full_size_backward_on_strips_and_split(full):
+    scene, cam, st, g, vb = full
+    tgt = synth.target_image(1, H, W)
+    dL_full = np.zeros((H, W, 3), np.float32)
+    acc = None
+    for y0, h in STRIPS:
+        r = oracle.render(scene, cam, st, rows=(y0, h))
+        _, dL = oracle.l1_loss_grad(r["image"], tgt[y0:y0 + h])
+        dL32 = dL.astype(np.float32)
+        dL_full[y0:y0 + h] = dL32
+        acc = oracle.backward(scene, cam, st, dL32.astype(np.float64), acc, rows=(y0, h))
+    grads = g.zeros_like()
+    S = torch.zeros(N, 6, device="cuda")
+    ws = B.workspace(B.render_bwd_workspace_size(N))
+    B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib,
+                                torch.as_tensor(dL_full).cuda(), grads, S, ws, accumulate=False)
+    torch.cuda.synchronize()
+    for f, t in zip(FIELDS, grads.tensors()):
+        assert _rel(t.cpu().numpy(), acc[f]) < 1e-4, f
+    assert _rel(S.cpu().numpy(), _upper6(acc["S"])) < 1e-4
+    # eigenpairs and the split of all 1M Gaussians from the GPU's matrices
+    db = PL.DensifyBuffers.alloc(g)
+    B.densify_split(g, S, 1.0, 0.0, 1.0, None, 0.0, db.out, db.capacity, db.n_out, db.parent, db.lam, db.v,
+                    db.split_ws)
+    torch.cuda.synchronize()
+    S_in = S.cpu().numpy().astype(np.float64)
+    S_full = np.zeros((N, 3, 3))
+    iu = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    for k, (a, b) in enumerate(iu):
+        S_full[:, a, b] = S_in[:, k]
+        S_full[:, b, a] = S_in[:, k]
+    lam_o, v_o = oracle.eig3_min(S_full)
+    nrm = np.linalg.norm(S_full.reshape(N, 9), axis=1)
+    lam_g = db.lam.cpu().numpy()
+    bad = np.abs(lam_g - lam_o) > 1e-4 * np.maximum(nrm, 1e-30)
+    assert not bad.any(), (int(bad.sum()), lam_g[bad][:5], lam_o[bad][:5], nrm[bad][:5], S_in[bad][:3])
+    decided = np.abs(lam_o) > 1e-6 * np.maximum(nrm, 1e-30)
+    n_out = int(db.n_out.item())
+    flags_g = np.zeros(N, bool)
+    flags_g[db.parent.cpu().numpy()[N:n_out]] = True
+    sp = oracle.split(scene, lam_o, v_o, 0.0, 1.0)
+    assert np.array_equal(flags_g[decided], sp["flags"][decided])
+    assert flags_g.sum() > 1000
