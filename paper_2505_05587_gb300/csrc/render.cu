@@ -100,7 +100,7 @@ __device__ __forceinline__ int build_warp_list(const float4* s_box, int cnt, flo
 
 template <int BATCH, int NW>
 struct FwdSmem {
-    float4 xy[BATCH];
+    float2 xy[BATCH];      // mean relative to the tile origin
     float4 co[BATCH];
     float4 rgb[BATCH];
     float4 box[BATCH];
@@ -110,7 +110,7 @@ struct FwdSmem {
 template <int BATCH, int NW>
 struct BwdSmem {
     uint32_t gid[BATCH];
-    float4 xy[BATCH];
+    float2 xy[BATCH];      // mean relative to the tile origin
     float4 co[BATCH];
     float4 rgb[BATCH];
     float4 box[BATCH];
@@ -133,7 +133,10 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
     const int px = bx + (lane & 7);
     const int py = by + (lane >> 3);
     const bool inside = px < W && py < H;
-    const float fpx = (float)px, fpy = (float)py;
+    // offsets from the tile origin: the staged mean is tile-local, so a pair's
+    // offset is one subtraction (same bits in the forward and the backward)
+    const int ox = (tile % gx) * TW, oy = (tile / gx) * TH;
+    const float lx = (float)(px - ox), ly = (float)(py - oy);
     const int n = (int)(rg.y - rg.x);
     bool done = !inside;
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
@@ -145,7 +148,7 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
             const uint32_t g = gids[rg.x + base + k];
             const float4 m = xy[g];
             const float4 co = conic_opac[g];
-            sm.xy[k] = m;
+            sm.xy[k] = make_float2((m.x - (float)ox) + m.z, (m.y - (float)oy) + m.w);
             sm.co[k] = conic_exp2(co);
             sm.rgb[k] = rgb[g];
             sm.box[k] = alpha_support_box(m, co, st.alpha_min);
@@ -155,10 +158,10 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
         const int nl = build_warp_list(sm.box, cnt, (float)bx, (float)by, sm.list[warp]);
         for (int k = 0; k < nl && !done; ++k) {
             const int j = sm.list[warp][k];
-            const float4 m = sm.xy[j];
+            const float2 m = sm.xy[j];
             const float4 cp = sm.co[j];
-            const float dx = (fpx - m.x) - m.z;
-            const float dy = (fpy - m.y) - m.w;
+            const float dx = lx - m.x;
+            const float dy = ly - m.y;
             const float alpha = fminf(st.alpha_max, __fmul_rn(cp.w, gauss2(cp, dx, dy)));
             if (alpha < st.alpha_min) continue;
             const float Tn = T * (1.0f - alpha);
@@ -234,7 +237,8 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
     const int px = bx + (lane & 7);
     const int py = by + (lane >> 3);
     const bool inside = px < W && py < H;
-    const float fpx = (float)px, fpy = (float)py;
+    const int ox = (tile % gx) * TW, oy = (tile / gx) * TH;
+    const float lx = (float)(px - ox), ly = (float)(py - oy);
     const int pix = py * W + px;
     // atomics: lanes 0,4,...,28 carry slots 0..7 of the reduce-scatter, lane 1 slot 8
     const int slot = ((lane & 3) == 0) ? (lane >> 2) : (lane == 1 ? 8 : -1);
@@ -265,7 +269,7 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
             const float4 m = xy[g];
             const float4 co = conic_opac[g];
             sm.gid[k] = g;
-            sm.xy[k] = m;
+            sm.xy[k] = make_float2((m.x - (float)ox) + m.z, (m.y - (float)oy) + m.w);
             sm.co[k] = conic_exp2(co);
             sm.rgb[k] = rgb[g];
             sm.box[k] = alpha_support_box(m, co, st.alpha_min);
@@ -275,11 +279,11 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
         const int nl = wcnt > 0 ? build_warp_list(sm.box, wcnt, (float)bx, (float)by, sm.list[warp]) : 0;
         for (int k = nl - 1; k >= 0; --k) {
             const int e = sm.list[warp][k];
-            const float4 m = sm.xy[e];
+            const float2 m = sm.xy[e];
             const float4 cp = sm.co[e];
             const float4 c = sm.rgb[e];
-            const float dx = (fpx - m.x) - m.z;
-            const float dy = (fpy - m.y) - m.w;
+            const float dx = lx - m.x;
+            const float dy = ly - m.y;
             const float araw = __fmul_rn(cp.w, gauss2(cp, dx, dy));
             const bool valid = inside && (uint32_t)(start + e) < last && araw >= st.alpha_min;
             if (!__any_sync(0xffffffffu, valid)) continue;     // nothing composited here by this warp
@@ -319,8 +323,10 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
                               final_T, n_contrib, sm);
 }
 
+// The backward kernels are bounded to 40 resident warps per SM (48 registers):
+// their pair loop is issue-bound and hides its latencies with warps.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) render_bwd_kernel(
+__global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
@@ -357,7 +363,7 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_views_kernel(
 }
 
 template <int TW, int TH, int BATCH>
-__global__ void __launch_bounds__(TW * TH) render_bwd_views_kernel(
+__global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_views_kernel(
     ViewsDev vd, const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, SetDev st,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL,
@@ -385,9 +391,11 @@ __global__ void __launch_bounds__(TW * TH) render_stats_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, int W, int H, int gx, SetDev st, uint2* __restrict__ counts) {
     const int tile = blockIdx.x;
-    const int px = (tile % gx) * TW + (int)(threadIdx.x % TW);
-    const int py = (tile / gx) * TH + (int)(threadIdx.x / TW);
+    const int ox = (tile % gx) * TW, oy = (tile / gx) * TH;
+    const int px = ox + (int)(threadIdx.x % TW);
+    const int py = oy + (int)(threadIdx.x / TW);
     if (px >= W || py >= H) return;
+    const float lx = (float)(px - ox), ly = (float)(py - oy);
     const uint2 rg = ranges[tile];
     float T = 1.0f;
     uint32_t ev = 0, comp = 0;
@@ -395,8 +403,8 @@ __global__ void __launch_bounds__(TW * TH) render_stats_kernel(
         const uint32_t g = gids[k];
         const float4 m = xy[g];
         const float4 cp = conic_exp2(conic_opac[g]);
-        const float dx = ((float)px - m.x) - m.z;
-        const float dy = ((float)py - m.y) - m.w;
+        const float dx = lx - ((m.x - (float)ox) + m.z);
+        const float dy = ly - ((m.y - (float)oy) + m.w);
         const float alpha = fminf(st.alpha_max, __fmul_rn(cp.w, gauss2(cp, dx, dy)));
         ++ev;
         if (alpha < st.alpha_min) continue;
