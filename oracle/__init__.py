@@ -71,12 +71,12 @@ def _load():
             lib.orc_bin_sort.argtypes = [P, P, P, P, P, P, C.c_int64]
             lib.orc_render.argtypes = [P, P, P, P, P, P, P]
             lib.orc_render_rows.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P]
-            lib.orc_backward_rows.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P]
+            lib.orc_backward_rows.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P]
             lib.orc_l1_loss_grad.restype = C.c_double
             lib.orc_l1_loss_grad.argtypes = [P, P, C.c_int, C.c_int, C.c_int, P]
-            lib.orc_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P]
+            lib.orc_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P, P]
             lib.orc_frozen_eval.restype = C.c_double
-            lib.orc_frozen_eval.argtypes = [P, P, P, C.c_int, P, P, C.c_int, P, P, C.c_double]
+            lib.orc_frozen_eval.argtypes = [P, P, P, C.c_int, P, P, C.c_int, P, P, C.c_double, P]
             lib.orc_eig3_min.argtypes = [P, C.c_double, C.c_int, P, P]
             lib.orc_jacobi3.argtypes = [P, C.c_int, P, P]
             lib.orc_split.restype = C.c_int
@@ -221,7 +221,7 @@ def backward(scene, cam, st, dL_dC, acc=None, rows=None):
     if acc is None:
         acc = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
                    opacity_logit=np.zeros(n), sh=np.zeros((n, K, 3)), S=np.zeros((n, 3, 3)),
-                   S_po=np.zeros((n, 3)))
+                   S_po=np.zeros((n, 3)), S_ls=np.zeros((n, 18)))
     grad2d = np.zeros((n, 9))
     dL = np.ascontiguousarray(dL_dC, np.float64)
     y0, h = (0, cam.height) if rows is None else rows
@@ -229,17 +229,17 @@ def backward(scene, cam, st, dL_dC, acc=None, rows=None):
         raise ValueError("dL_dC must cover the rows")
     if lib.orc_backward_rows(*b.refs(), int(y0), int(h), _ptr(dL), _ptr(acc["means"]), _ptr(acc["log_scales"]),
                              _ptr(acc["quats"]), _ptr(acc["opacity_logit"]), _ptr(acc["sh"]),
-                             _ptr(acc["S"]), _ptr(acc["S_po"]), _ptr(grad2d)) != 0:
+                             _ptr(acc["S"]), _ptr(acc["S_po"]), _ptr(acc["S_ls"]), _ptr(grad2d)) != 0:
         raise ValueError("rows outside the view")
     acc["grad2d"] = grad2d
     return acc
 
 
-def frozen_eval(scene, cam, st, idx, dp=None, mix_v=None, g=None, target=None, d_o=0.0):
+def frozen_eval(scene, cam, st, idx, dp=None, mix_v=None, g=None, target=None, d_o=0.0, d_ls=None):
     """Loss in the frozen-linearisation model (Appendix "Deriving Hessian of
     Gaussian") with Gaussian `idx` displaced by dp (opacity by d_o) or replaced
-    by the w = 1/2 mixture slot at (p +- mix_v, o +- d_o).  Returns sum g.C (g
-    given) or the L1 loss."""
+    by the w = 1/2 mixture slot at (p +- mix_v, o +- d_o, log-scales +- d_ls;
+    P frozen).  Returns sum g.C (g given) or the L1 loss."""
     lib = _load()
     b = _Bound(scene, cam, st)
     mode = 0 if g is not None else 1
@@ -247,8 +247,9 @@ def frozen_eval(scene, cam, st, idx, dp=None, mix_v=None, g=None, target=None, d
     t_arr = None if target is None else np.ascontiguousarray(target, np.float32)
     dp_arr = None if dp is None else np.ascontiguousarray(dp, np.float64)
     mv_arr = None if mix_v is None else np.ascontiguousarray(mix_v, np.float64)
+    ls_arr = None if d_ls is None else np.ascontiguousarray(d_ls, np.float64)
     return lib.orc_frozen_eval(*b.refs(), mode, _ptr(g_arr), _ptr(t_arr), int(idx),
-                               _ptr(dp_arr), _ptr(mv_arr), float(d_o))
+                               _ptr(dp_arr), _ptr(mv_arr), float(d_o), _ptr(ls_arr))
 
 
 def eig3_min(S, scale=1.0):
@@ -323,12 +324,35 @@ def eig_min_sym(S, scale=1.0):
     return lam, v * sgn[:, None]
 
 
+def S7_matrix(S, S_po, S_ls):
+    """Splitting matrices over theta = (p, l, o) (dim Theta = 7, l the
+    log-scales): blocks p-p (S), p-l (S_ls[:, :9], row p), l-l (S_ls[:, 9:15],
+    xx xy xz yy yz zz), p-o (S_po), l-o (S_ls[:, 15:18]), o-o = 0."""
+    S = np.asarray(S, np.float64)
+    n = S.shape[0]
+    S7 = np.zeros((n, 7, 7))
+    S7[:, :3, :3] = S
+    pl = np.asarray(S_ls, np.float64)[:, :9].reshape(n, 3, 3)
+    S7[:, :3, 3:6] = pl
+    S7[:, 3:6, :3] = np.transpose(pl, (0, 2, 1))
+    iu = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    for q, (a, b) in enumerate(iu):
+        S7[:, 3 + a, 3 + b] = S_ls[:, 9 + q]
+        S7[:, 3 + b, 3 + a] = S_ls[:, 9 + q]
+    S7[:, :3, 6] = S_po
+    S7[:, 6, :3] = S_po
+    S7[:, 3:6, 6] = S_ls[:, 15:18]
+    S7[:, 6, 3:6] = S_ls[:, 15:18]
+    return S7
+
+
 OPACITY_SPLIT_MIN, OPACITY_SPLIT_MAX = 1e-4, 1.0 - 1e-4
 
 
 def split_po(scene, lam, v4, eps_split, step_scale=1.0):
-    """Steepest split over theta = (p, o): Gaussian i with lambda_min < eps_split
-    becomes the w = 1/2 pair at theta +- eps_i v, eps_i = step_scale * max_k
+    """Steepest split over theta = (p, o) (v4 [n, 4]) or (p, l, o) (v [n, 7],
+    l the log-scales): Gaussian i with lambda_min < eps_split becomes the
+    w = 1/2 pair at theta +- eps_i v, eps_i = step_scale * max_k
     exp(log_scale_ik); each offspring keeps half of its displaced opacity,
     (o +- eps_i v_o) / 2 clamped to [1e-4, 1 - 1e-4]; the parent's row takes
     the + offspring, the - offspring is appended in index order."""
@@ -353,9 +377,10 @@ def split_po(scene, lam, v4, eps_split, step_scale=1.0):
         j = n + r
         for row, sgn in ((i, 1.0), (j, -1.0)):
             out["means"][row] = scene.means[i].astype(np.float64) + sgn * eps[i] * v4[i, :3]
-            oj = np.clip(0.5 * (o[i] + sgn * eps[i] * v4[i, 3]), OPACITY_SPLIT_MIN, OPACITY_SPLIT_MAX)
+            oj = np.clip(0.5 * (o[i] + sgn * eps[i] * v4[i, -1]), OPACITY_SPLIT_MIN, OPACITY_SPLIT_MAX)
             out["opacity_logit"][row] = np.log(oj) - np.log1p(-oj)
-            out["log_scales"][row] = scene.log_scales[i]
+            out["log_scales"][row] = scene.log_scales[i].astype(np.float64) + (
+                sgn * eps[i] * v4[i, 3:6] if v4.shape[1] == 7 else 0.0)
             out["quats"][row] = scene.quats[i]
             out["sh"][row] = scene.sh[i]
             out["parent"][row] = i

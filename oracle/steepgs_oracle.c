@@ -515,6 +515,30 @@ static double gauss2d(const double *mu, const double *Q, double px, double py, d
     return exp(power);
 }
 
+/* Conic of Gaussian pr in the frozen model (P fixed) with its log-scales   */
+/* moved by dls: Sigma2D = P Rq diag(exp(2 (l + dls))) Rq^T P^T + dilation I. */
+static void frozen_conic(const orc_proj *pr, const orc_settings *st, const double *dls, double *Q)
+{
+    double a[2][3];
+    for (int u = 0; u < 2; ++u)
+        for (int k = 0; k < 3; ++k) {
+            double v = 0.0;
+            for (int j = 0; j < 3; ++j) v += pr->P[3 * u + j] * pr->Rq[3 * j + k];
+            a[u][k] = v;                        /* a_k = P Rq e_k, component u */
+        }
+    double S2[3] = {st->dilation, 0.0, st->dilation};
+    for (int k = 0; k < 3; ++k) {
+        double s2 = pr->s[k] * pr->s[k] * exp(2.0 * (dls ? dls[k] : 0.0));
+        S2[0] += s2 * a[0][k] * a[0][k];
+        S2[1] += s2 * a[0][k] * a[1][k];
+        S2[2] += s2 * a[1][k] * a[1][k];
+    }
+    double det = S2[0] * S2[2] - S2[1] * S2[1];
+    Q[0] = S2[2] / det;
+    Q[1] = -S2[1] / det;
+    Q[2] = S2[0] / det;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Forward compositing (Section 3, Eq. alpha_blend):                         */
 /*   alpha = min(alpha_max, o G); skipped if alpha < alpha_min; the walk stops */
@@ -633,7 +657,7 @@ typedef struct {
 /* Rows [y0, y1) of the view; dL_dC is [(y1 - y0), W, 3] (row py at py - y0). */
 static void backward_view(const orc_scene *sc, const orc_view *v, const orc_camera *cam,
                           const orc_settings *st, int y0, int y1, const double *dL_dC, grad2d_t *g2, double *S,
-                          double *S_po)
+                          double *S_po, double *S_ls)
 {
     int W = cam->width;
     pair_t *list = NULL;
@@ -690,6 +714,46 @@ static void backward_view(const orc_scene *sc, const orc_view *v, const orc_came
                 gg->Q[2] += dLdG * pp->G * (-0.5 * pp->dy * pp->dy);
                 double Y[3];
                 for (int j = 0; j < 3; ++j) Y[j] = pr->P[j] * Qd0 + pr->P[3 + j] * Qd1;
+                if (S_ls) {
+                    /* blocks of the Hessian of sigma = o exp(-d^T Q d / 2) over theta =  */
+                    /* (p, l, o), l the log-scales, P frozen: with a_k = P Rq e_k,        */
+                    /* b_k = Q a_k, t_k = b_k . d, c_kl = a_k . b_l, s2_k = exp(2 l_k):   */
+                    /*  dQ/dl_k = -2 s2_k b_k b_k^T,  dsigma/dl_k = sigma s2_k t_k^2,      */
+                    /*  d2/dp dl_k = sigma s2_k t_k^2 Y - 2 sigma s2_k t_k P^T b_k,        */
+                    /*  d2/dl_k dl_l = sigma (s2_k s2_l t_k^2 t_l^2 + 2 delta_kl s2_k t_k^2 */
+                    /*                  - 4 s2_k s2_l c_kl t_k t_l),                      */
+                    /*  d2/dl_k do = G s2_k t_k^2.                                        */
+                    /* Layout [N,18]: p-l (3x3, row p, column l), l-l (xx xy xz yy yz zz), */
+                    /* l-o (3).                                                           */
+                    double a[2][3], b[2][3], t[3], s2[3], c[3][3], Ptb[3][3];
+                    for (int k = 0; k < 3; ++k) {
+                        for (int u = 0; u < 2; ++u) {
+                            double vv = 0.0;
+                            for (int j = 0; j < 3; ++j) vv += pr->P[3 * u + j] * pr->Rq[3 * j + k];
+                            a[u][k] = vv;
+                        }
+                        b[0][k] = pr->Q[0] * a[0][k] + pr->Q[1] * a[1][k];
+                        b[1][k] = pr->Q[1] * a[0][k] + pr->Q[2] * a[1][k];
+                        t[k] = b[0][k] * pp->dx + b[1][k] * pp->dy;
+                        s2[k] = pr->s[k] * pr->s[k];
+                        for (int j = 0; j < 3; ++j) Ptb[k][j] = pr->P[j] * b[0][k] + pr->P[3 + j] * b[1][k];
+                    }
+                    for (int k = 0; k < 3; ++k)
+                        for (int l = 0; l < 3; ++l) c[k][l] = a[0][k] * b[0][l] + a[1][k] * b[1][l];
+                    double sig = pp->alpha;
+                    double *Sl = S_ls + 18 * (size_t)pp->gid;
+                    for (int j = 0; j < 3; ++j)
+                        for (int k = 0; k < 3; ++k)
+                            Sl[3 * j + k] += dLda * (sig * s2[k] * t[k] * t[k] * Y[j] -
+                                                     2.0 * sig * s2[k] * t[k] * Ptb[k][j]);
+                    int q = 9;
+                    for (int k = 0; k < 3; ++k)
+                        for (int l = k; l < 3; ++l)
+                            Sl[q++] += dLda * sig * (s2[k] * s2[l] * t[k] * t[k] * t[l] * t[l] +
+                                                     (k == l ? 2.0 * s2[k] * t[k] * t[k] : 0.0) -
+                                                     4.0 * s2[k] * s2[l] * c[k][l] * t[k] * t[l]);
+                    for (int k = 0; k < 3; ++k) Sl[15 + k] += dLda * pp->G * s2[k] * t[k] * t[k];
+                }
                 if (S_po) {
                     /* mixed block of the Hessian of sigma = o G(p) w.r.t. theta = (p, o): */
                     /* d^2 sigma / dp do = dG/dp = G Y  (d^2 sigma / do^2 = 0)               */
@@ -837,13 +901,13 @@ static void chain_to_params(const orc_scene *sc, const orc_camera *cam, const or
  * (overwritten). */
 int orc_backward_rows(const orc_scene *sc, const orc_camera *cam, const orc_settings *st, int y0, int h,
                       const double *dL_dC, double *g_means, double *g_log_scales, double *g_quats,
-                      double *g_logit, double *g_sh, double *S, double *S_po, double *grad2d)
+                      double *g_logit, double *g_sh, double *S, double *S_po, double *S_ls, double *grad2d)
 {
     if (y0 < 0 || h < 0 || y0 + h > cam->height) return -1;
     orc_view v;
     view_build(sc, cam, st, &v);
     grad2d_t *g2 = (grad2d_t *)calloc((size_t)(sc->n > 0 ? sc->n : 1), sizeof(grad2d_t));
-    backward_view(sc, &v, cam, st, y0, y0 + h, dL_dC, g2, S, S_po);
+    backward_view(sc, &v, cam, st, y0, y0 + h, dL_dC, g2, S, S_po, S_ls);
     for (int i = 0; i < sc->n; ++i) {
         if (grad2d) {
             double *o = grad2d + 9 * (size_t)i;
@@ -861,10 +925,10 @@ int orc_backward_rows(const orc_scene *sc, const orc_camera *cam, const orc_sett
 
 int orc_backward(const orc_scene *sc, const orc_camera *cam, const orc_settings *st,
                  const double *dL_dC, double *g_means, double *g_log_scales, double *g_quats,
-                 double *g_logit, double *g_sh, double *S, double *S_po, double *grad2d)
+                 double *g_logit, double *g_sh, double *S, double *S_po, double *S_ls, double *grad2d)
 {
     return orc_backward_rows(sc, cam, st, 0, cam->height, dL_dC, g_means, g_log_scales, g_quats, g_logit, g_sh,
-                             S, S_po, grad2d);
+                             S, S_po, S_ls, grad2d);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -872,15 +936,16 @@ int orc_backward(const orc_scene *sc, const orc_camera *cam, const orc_settings 
 /* Pi is replaced by its affine approximation at the current p (mu(p') =     */
 /* mu + P (p' - p)); P, Sigma2D, colour, opacity, tile lists and order stay   */
 /* at their values at theta.  Gaussian `idx` is displaced by dp (its opacity */
-/* by d_o), or, when mix_v is given, replaced by the mixture slot            */
-/* 0.5 sigma(p + mix_v, o + d_o) + 0.5 sigma(p - mix_v, o - d_o) (Theorem 1's */
+/* by d_o, its log-scales by d_ls with P frozen), or, when mix_v is given,    */
+/* replaced by the mixture slot 0.5 sigma(p + mix_v, l + d_ls, o + d_o) +     */
+/* 0.5 sigma(p - mix_v, l - d_ls, o - d_o) (Theorem 1's                       */
 /* w = 1/2 split with both offspring sharing the parent's depth slot).       */
 /* Returns sum g . C (mode 0) or the L1 loss against `target` (mode 1).      */
 /* ------------------------------------------------------------------------ */
 
 double orc_frozen_eval(const orc_scene *sc, const orc_camera *cam, const orc_settings *st,
                        int mode, const double *g, const float *target, int idx,
-                       const double *dp, const double *mix_v, double d_o)
+                       const double *dp, const double *mix_v, double d_o, const double *d_ls)
 {
     orc_view v;
     view_build(sc, cam, st, &v);
@@ -902,11 +967,17 @@ double orc_frozen_eval(const orc_scene *sc, const orc_camera *cam, const orc_set
                     for (int a = 0; a < 2; ++a)
                         for (int j = 0; j < 3; ++j) sh1[a] += pr->P[3 * a + j] * (d1 ? d1[j] : 0.0);
                     double mu1[2] = {pr->mu[0] + sh1[0], pr->mu[1] + sh1[1]};
-                    double a1 = (pr->o + d_o) * gauss2d(mu1, pr->Q, px, py, &dx, &dy);
+                    double Q1[3] = {pr->Q[0], pr->Q[1], pr->Q[2]}, Q2[3] = {pr->Q[0], pr->Q[1], pr->Q[2]};
+                    if (d_ls) {
+                        double m_ls[3] = {-d_ls[0], -d_ls[1], -d_ls[2]};
+                        frozen_conic(pr, st, d_ls, Q1);
+                        frozen_conic(pr, st, m_ls, Q2);
+                    }
+                    double a1 = (pr->o + d_o) * gauss2d(mu1, Q1, px, py, &dx, &dy);
                     if (mix_v) {
                         for (int a = 0; a < 2; ++a) sh2[a] = -sh1[a];
                         double mu2[2] = {pr->mu[0] + sh2[0], pr->mu[1] + sh2[1]};
-                        double a2 = (pr->o - d_o) * gauss2d(mu2, pr->Q, px, py, &dx, &dy);
+                        double a2 = (pr->o - d_o) * gauss2d(mu2, Q2, px, py, &dx, &dy);
                         alpha = 0.5 * a1 + 0.5 * a2;
                     } else {
                         alpha = a1;

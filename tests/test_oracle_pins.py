@@ -636,3 +636,84 @@ def test_split_po_output_invariants():
             assert abs(o1 + o2 - o[i]) < 1e-12
     keep = ~flags
     assert np.array_equal(out["means"][:n][keep], sc.means[keep].astype(np.float64))
+
+
+# --------------------------------------------------------------------------
+# Splitting matrices over theta = (p, l, o), l the log-scales (dim Theta = 7)
+# --------------------------------------------------------------------------
+
+def _fz(sc, cam, st, i, g, dp=None, dls=None, do=0.0):
+    return oracle.frozen_eval(sc, cam, st, i, dp=np.zeros(3) if dp is None else dp, d_ls=dls, d_o=do, g=g)
+
+
+def _mixed(f, u, v, h):
+    """Central-difference d^2 f / du dv for unit offsets u, v (callables of h)."""
+    return (f(u(h), v(h)) - f(u(h), v(-h)) - f(u(-h), v(h)) + f(u(-h), v(-h))) / (4 * h * h)
+
+
+def test_log_scale_blocks_equal_frozen_hessian():
+    sc = synth.tiny_scene(0)
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings().smooth()
+    g = np.random.default_rng(11).normal(size=(64, 64, 3)) / (64 * 64)
+    acc = oracle.backward(sc, cam, st, g)
+    S7 = oracle.S7_matrix(acc["S"], acc["S_po"], acc["S_ls"])
+    vis = np.nonzero(oracle.integer_stage(sc, cam, st)["tiles"])[0]
+
+    def e3(a, h):
+        v = np.zeros(3)
+        v[a] = h
+        return v
+
+    for i in np.random.default_rng(7).choice(vis, 4, replace=False):
+        H = np.zeros((7, 7))
+        for r in range(7):
+            for c in range(r, 7):
+                def f(x, y, r=r, c=c):
+                    dp, dls, do = np.zeros(3), np.zeros(3), 0.0
+                    for idx, val in ((r, x), (c, y)):
+                        if idx < 3:
+                            dp = dp + e3(idx, 1.0) * val
+                        elif idx < 6:
+                            dls = dls + e3(idx - 3, 1.0) * val
+                        else:
+                            do = do + val
+                    return _fz(sc, cam, st, i, g, dp, dls, do)
+                hr = []
+                for h in (2e-3, 1e-3):
+                    hr.append(_mixed(f, lambda t: t, lambda t: t, h) if r != c else
+                              (f(h / 2, h / 2) - 2 * f(0.0, 0.0) + f(-h / 2, -h / 2)) / (h * h))
+                H[r, c] = H[c, r] = (4 * hr[1] - hr[0]) / 3
+        rel = np.linalg.norm(H - S7[i]) / np.linalg.norm(S7[i])
+        assert rel < 1e-5, (i, rel)
+
+
+def test_7d_split_predicted_decrease_interlacing_and_optimality():
+    sc, cam, st, g, tgt, S = _setup_l1(0)
+    acc = oracle.backward(sc, cam, st, g)
+    S7 = oracle.S7_matrix(acc["S"], acc["S_po"], acc["S_ls"])
+    lam7, v7 = oracle.eig_min_sym(S7)
+    lam4, _ = oracle.eig_min_sym(oracle.S4_matrix(acc["S"], acc["S_po"]))
+    scale = np.abs(S7).reshape(len(S7), -1).max(1)
+    assert np.all(lam7 <= lam4 + 1e-12 * scale)
+    base = oracle.frozen_eval(sc, cam, st, 0, dp=np.zeros(3), g=g)
+    for i in np.argsort(-scale)[:5]:
+        s_max = float(np.exp(sc.log_scales[i].astype(np.float64)).max())
+        eps = 1e-2 * s_max
+        v = v7[i]
+        pred = 0.5 * eps * eps * lam7[i]
+        meas = oracle.frozen_eval(sc, cam, st, i, mix_v=eps * v[:3], d_ls=eps * v[3:6], d_o=eps * v[6], g=g) - base
+        assert abs(meas - pred) <= 1e-3 * abs(pred) + 1e-15, (i, meas, pred)
+        rng = np.random.default_rng(int(i))
+        for _ in range(40):
+            d = rng.normal(size=7)
+            d /= np.linalg.norm(d)
+            dv = oracle.frozen_eval(sc, cam, st, i, mix_v=eps * d[:3], d_ls=eps * d[3:6], d_o=eps * d[6],
+                                    g=g) - base
+            assert dv >= meas - 1e-3 * abs(meas) - 1e-15
+    out = oracle.split_po(sc, lam7, v7, eps_split=-1e-9, step_scale=0.5)
+    n = sc.n
+    for r, i in enumerate(np.nonzero(lam7 < -1e-9)[0][:20]):
+        eps = 0.5 * np.exp(sc.log_scales[i].astype(np.float64)).max()
+        np.testing.assert_allclose(out["log_scales"][i] - out["log_scales"][n + r], 2 * eps * v7[i, 3:6],
+                                   atol=1e-12)
