@@ -208,10 +208,10 @@ def run_gpu(args):
         vb.loss_grad(target, 1, db.loss, args.lambda_dssim, stream)
         ev[5].record(stream)
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, vb.dL, db.grads,
-                                    db.S, db.bwd_ws, stream, accumulate=False, S_po=db.S_po)
+                                    db.S, db.bwd_ws, stream, accumulate=False, S_po=db.S_po, S_ls=db.S_ls)
         ev[6].record(stream)
         B.densify_split(g, db.S, 1.0, EPS_SPLIT, 1.0, None, 0.0, db.out, db.capacity, db.n_out, db.parent, db.lam,
-                        db.v, db.split_ws, stream, S_po=db.S_po)
+                        db.v, db.split_ws, stream, S_po=db.S_po, S_ls=db.S_ls)
         ev[7].record(stream)
 
     K = args.steps
@@ -418,8 +418,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--dim-theta", type=int, default=3, choices=[3, 4],
-                    help="splitting matrices over the position (3, the paper's experiments) or (position, opacity)")
+    ap.add_argument("--dim-theta", type=int, default=3, choices=[3, 4, 7],
+                    help="splitting matrices over the position (3, the paper's experiments), (position, opacity) "
+                         "(4) or (position, log-scales, opacity) (7)")
     ap.add_argument("--lambda-dssim", type=float, default=None,
                     help="add the SSIM term to the loss: (1 - l) L1 + l (1 - SSIM) (default: L1 only)")
     ap.add_argument("--traffic", type=float, default=None,

@@ -239,12 +239,26 @@ int sgs_render_bwd_workspace_size(int32_t n, size_t *bytes);
  * sum dL/dsigma G P^T u = P^T Q (sum w (x - mu)) / o (the opacity-opacity
  * entry is 0, sigma being linear in o); with S_accum it forms the 4x4
  * splitting matrix [[S, S_po], [S_po^T, 0]] that sgs_densify_split takes.
+ * S_ls_accum [N,18] (may be NULL; requires S_po_accum): when given, the
+ * blocks of the splitting matrix over theta = (p, l, o), l the log-scales, are
+ * accumulated (+=) as well, with the projection Jacobian P held fixed (as for
+ * S): columns 0-8 the p-l block (row p, column l), 9-14 the l-l upper
+ * triangle (xx xy xz yy yz zz), 15-17 the l-o column.  With a_k = P R e_k,
+ * b_k = Q a_k, t_k = b_k . (x - mu) and s_k = exp(l_k):
+ *   p-l[j][k] = sum w (s_k^2 t_k^2 (Q P e_j).(x - mu) - 2 s_k^2 (P^T b_k)_j t_k)
+ *   l-l[k][l] = sum w (s_k^2 s_l^2 t_k^2 t_l^2 + 2 delta_kl s_k^2 t_k^2
+ *                      - 4 s_k^2 s_l^2 (a_k . b_l) t_k t_l)
+ *   l-o[k]    = sum w s_k^2 t_k^2 / o
+ * (the pixel moments of w (x - mu) up to fourth order are reduced per
+ * Gaussian in the workspace).  The multi-view entry point below has no
+ * such argument.
  * Errors: SGS_ERR_INVALID_ARG, SGS_ERR_WORKSPACE. */
 int sgs_render_bwd_with_splitting(const sgs_gaussians *g, const sgs_proj *proj, const sgs_bins *bins,
                                   const sgs_camera *cam, const sgs_settings *st,
                                   const float *final_T, const uint32_t *n_contrib,
                                   const float *dL_dimage, const sgs_grads *grads, int32_t accumulate_grads,
-                                  float *S_accum, float *S_po_accum, void *ws, size_t ws_bytes, void *stream);
+                                  float *S_accum, float *S_po_accum, float *S_ls_accum, void *ws,
+                                  size_t ws_bytes, void *stream);
 
 /* Several views of one scene in one pass (the batched densification step):
  * projection of every (view, Gaussian) pair, one binning and depth sort over
@@ -318,8 +332,15 @@ int sgs_densify_split_workspace_size(int32_t n, size_t *bytes);
  * refined by one Rayleigh quotient, same sign convention; the offspring take
  * p +- eps_i v_p and opacities (o +- eps_i v_o) / 2, each clamped to
  * [1e-4, 1 - 1e-4].
+ * With S_ls_accum [N,18] also given (layout as in
+ * sgs_render_bwd_with_splitting; requires S_po_accum) the split runs over
+ * theta = (p, l, o) (dim Theta = 7): the 7x7 matrix with blocks p-p, p-l,
+ * l-l, p-o, l-o and o-o = 0, times inv_T_split, by the same Jacobi rotations;
+ * v_min_out [N,7] = (v_p, v_l, v_o); the offspring also take log-scales
+ * l +- eps_i v_l.
  * `out` must not alias `in`.  Errors: SGS_ERR_INVALID_ARG, SGS_ERR_WORKSPACE. */
-int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, const float *S_po_accum, float inv_T_split,
+int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, const float *S_po_accum,
+                      const float *S_ls_accum, float inv_T_split,
                       float eps_split, float step_scale, const float *grad_norm, float eps_grad,
                       int64_t max_splits, const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
                       int32_t *parent_index, float *lam_min_out, float *v_min_out,
@@ -343,9 +364,9 @@ int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, const float
  *     (other streams, other threads) race: serialise them.
  *   - It calls no cudaMalloc, cudaFree or allocating routine. */
 #define SGS_NOALLOC_MAX_GAUSSIANS 1000000
-#define SGS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+#define SGS_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
 int sgs_densify_split_noalloc(const sgs_gaussians *in, const float *S_accum, const float *S_po_accum,
-                              float inv_T_split,
+                              const float *S_ls_accum, float inv_T_split,
                               float eps_split, float step_scale, const float *grad_norm, float eps_grad,
                               int64_t max_splits, const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
                               int32_t *parent_index, float *lam_min_out, float *v_min_out, void *stream);

@@ -97,9 +97,9 @@ def lib():
         L.sgs_l1_loss_grad.argtypes = [P, P, I32, I32, I32, P, P, P]
         L.sgs_render_stats.argtypes = [P, P, P, P, P, P]
         L.sgs_render_bwd_workspace_size.argtypes = [I32, C.POINTER(SZ)]
-        L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, I32, P, P, P, SZ, P]
+        L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, I32, P, P, P, P, SZ, P]
         L.sgs_densify_split_workspace_size.argtypes = [I32, C.POINTER(SZ)]
-        L.sgs_densify_split.argtypes = [P, P, P, F, F, F, P, F, I64, P, I64, P, P, P, P, P, SZ, P]
+        L.sgs_densify_split.argtypes = [P, P, P, P, F, F, F, P, F, I64, P, I64, P, P, P, P, P, SZ, P]
         L.sgs_render_views_workspace_size.argtypes = [I32, P, I32, P, I64, C.POINTER(SZ)]
         L.sgs_render_views_workspace_size.restype = C.c_int
         L.sgs_render_views_with_splitting.argtypes = [P, P, I32, P, I32, P, P, P, P, I32, P, P, P, I64, P, SZ, P]
@@ -116,7 +116,7 @@ def lib():
         L.sgs_ssim_l1_loss_grad.restype = C.c_int
         L.sgs_fma_probe.argtypes = [P, I32, I32, P]
         L.sgs_fma_probe.restype = C.c_int
-        L.sgs_densify_split_noalloc.argtypes = [P, P, P, F, F, F, P, F, I64, P, I64, P, P, P, P, P]
+        L.sgs_densify_split_noalloc.argtypes = [P, P, P, P, F, F, F, P, F, I64, P, I64, P, P, P, P, P]
         for name in ("sgs_project", "sgs_bin_sort_workspace_size", "sgs_bin_sort", "sgs_render_fwd",
                      "sgs_l1_loss_grad", "sgs_render_stats", "sgs_render_bwd_workspace_size", "sgs_render_bwd_with_splitting",
                      "sgs_densify_split_workspace_size", "sgs_densify_split", "sgs_densify_split_noalloc"):
@@ -330,15 +330,16 @@ def render_bwd_workspace_size(n: int) -> int:
 
 def render_bwd_with_splitting(g: GaussianTensors, proj: ProjBuffers, bins: BinBuffers, cam, st, final_T,
                               n_contrib, dL_dimage, grads: GaussianTensors, S_accum, ws, stream=None,
-                              accumulate: bool = True, S_po=None):
+                              accumulate: bool = True, S_po=None, S_ls=None):
     """S_po [N,3] (optional): the position-opacity block of the splitting
-    matrix over theta = (p, o) is accumulated too."""
+    matrix over theta = (p, o) is accumulated too; S_ls [N,18] (optional, with
+    S_po): the log-scale blocks over theta = (p, l, o) as well."""
     gc, pc, bc, cc, sc = g.c(), proj.c(), bins.c(), camera_c(cam), settings_c(st)
     grc = Grads(*[_p(t) for t in grads.tensors()])
     _check("sgs_render_bwd_with_splitting",
            lib().sgs_render_bwd_with_splitting(C.byref(gc), C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
                                                _p(final_T), _p(n_contrib), _p(dL_dimage), C.byref(grc),
-                                               1 if accumulate else 0, _p(S_accum), _p(S_po), _p(ws),
+                                               1 if accumulate else 0, _p(S_accum), _p(S_po), _p(S_ls), _p(ws),
                                                ws.numel() * ws.element_size(),
                                                _stream(stream)))
 
@@ -410,14 +411,14 @@ def densify_split_workspace_size(n: int) -> int:
 
 def densify_split(g: GaussianTensors, S_accum, inv_T_split: float, eps_split: float, step_scale: float,
                   grad_norm, eps_grad: float, out: GaussianTensors, capacity: int, d_n_out, parent_index,
-                  lam_min_out, v_min_out, ws, stream=None, max_splits: int = 0, S_po=None):
-    """S_po [N,3] given: split over theta = (p, o) (v_min_out [N,4])."""
+                  lam_min_out, v_min_out, ws, stream=None, max_splits: int = 0, S_po=None, S_ls=None):
+    """S_po [N,3] given: split over theta = (p, o) (v_min_out [N,4]); S_po and
+    S_ls [N,18] given: over theta = (p, l, o) (v_min_out [N,7])."""
     gc, oc = g.c(), out.c_mut()
     _check("sgs_densify_split",
-           lib().sgs_densify_split(C.byref(gc), _p(S_accum), _p(S_po), inv_T_split, eps_split, step_scale,
-                                   _p(grad_norm),
-                                   eps_grad, int(max_splits), C.byref(oc), capacity, _p(d_n_out), _p(parent_index),
-                                   _p(lam_min_out), _p(v_min_out), _p(ws), ws.numel() * ws.element_size(),
+           lib().sgs_densify_split(C.byref(gc), _p(S_accum), _p(S_po), _p(S_ls), inv_T_split, eps_split,
+                                   step_scale, _p(grad_norm), eps_grad, int(max_splits), C.byref(oc), capacity,
+                                   _p(d_n_out), _p(parent_index), _p(lam_min_out), _p(v_min_out), _p(ws), ws.numel() * ws.element_size(),
                                    _stream(stream)))
 
 
@@ -428,15 +429,15 @@ def kernel_launches() -> int:
 
 def densify_split_noalloc(g: GaussianTensors, S_accum, inv_T_split: float, eps_split: float, step_scale: float,
                           grad_norm, eps_grad: float, out: GaussianTensors, capacity: int, d_n_out, parent_index,
-                          lam_min_out, v_min_out, stream=None, max_splits: int = 0, S_po=None):
+                          lam_min_out, v_min_out, stream=None, max_splits: int = 0, S_po=None, S_ls=None):
     """densify_split without a workspace, for callers that cannot allocate one
     (its scratch is a fixed array inside the library; n <= 1,000,000; calls
     that overlap on the GPU race)."""
     gc, oc = g.c(), out.c_mut()
     _check("sgs_densify_split_noalloc",
-           lib().sgs_densify_split_noalloc(C.byref(gc), _p(S_accum), _p(S_po), inv_T_split, eps_split, step_scale,
-                                           _p(grad_norm), eps_grad, int(max_splits), C.byref(oc), capacity, _p(d_n_out),
-                                           _p(parent_index), _p(lam_min_out), _p(v_min_out), _stream(stream)))
+           lib().sgs_densify_split_noalloc(C.byref(gc), _p(S_accum), _p(S_po), _p(S_ls), inv_T_split, eps_split,
+                                           step_scale, _p(grad_norm), eps_grad, int(max_splits), C.byref(oc),
+                                           capacity, _p(d_n_out), _p(parent_index), _p(lam_min_out), _p(v_min_out), _stream(stream)))
 
 
 def check_count(M: int) -> int:

@@ -217,20 +217,24 @@ int sgs_l1_loss_grad(const float* image, const float* target, int32_t height, in
     return cuda_status(launch_l1(image, target, height, width, n_views, dL_dimage, loss, (cudaStream_t)stream));
 }
 
+// Backward workspace: per Gaussian a 16-float accumulator row, and a second
+// one for the higher moments of the log-scale blocks (used when S_ls_accum is
+// given).
 int sgs_render_bwd_workspace_size(int32_t n, size_t* bytes) {
     if (n < 0 || !bytes) return SGS_ERR_INVALID_ARG;
-    *bytes = sizeof(float) * 16 * (size_t)(n > 0 ? n : 1) + 256;
+    *bytes = sizeof(float) * 32 * (size_t)(n > 0 ? n : 1) + 256;
     return SGS_OK;
 }
 
 int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, const sgs_bins* bins,
                                   const sgs_camera* cam, const sgs_settings* st, const float* final_T,
                                   const uint32_t* n_contrib, const float* dL_dimage, const sgs_grads* grads,
-                                  int32_t accumulate_grads, float* S_accum, float* S_po_accum, void* ws,
-                                  size_t ws_bytes, void* stream) {
+                                  int32_t accumulate_grads, float* S_accum, float* S_po_accum, float* S_ls_accum,
+                                  void* ws, size_t ws_bytes, void* stream) {
     if (!valid_gaussians(g) || !proj || !bins || !valid_cam(cam) || !valid_settings(st) || !final_T ||
         !n_contrib || !dL_dimage || !grads || !tiles_fit(cam, st) || !bins->ranges)
         return SGS_ERR_INVALID_ARG;
+    if (S_ls_accum && !S_po_accum) return SGS_ERR_INVALID_ARG;      // theta = (p, l, o) includes o
     if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit ||
                      !grads->sh || !S_accum))
         return SGS_ERR_INVALID_ARG;
@@ -240,14 +244,16 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
     if (g->n == 0) return SGS_OK;
     cudaStream_t s = (cudaStream_t)stream;
     float* g2d = reinterpret_cast<float*>(align_up(reinterpret_cast<uintptr_t>(ws), 256));
-    if ((char*)g2d + sizeof(float) * 16 * (size_t)g->n > (char*)ws + ws_bytes) return SGS_ERR_WORKSPACE;
+    if ((char*)g2d + sizeof(float) * 32 * (size_t)g->n > (char*)ws + ws_bytes) return SGS_ERR_WORKSPACE;
+    float* g2d_hi = S_ls_accum ? g2d + 16 * (size_t)g->n : nullptr;
     CamDev cd = make_cam(*cam, *st);
     SetDev sd = make_set(*st);
-    cudaError_t e = cudaMemsetAsync(g2d, 0, sizeof(float) * 16 * (size_t)g->n, s);
-    if (e == cudaSuccess) e = launch_render_bwd(*proj, *bins, cd, sd, final_T, n_contrib, dL_dimage, g2d, s);
+    cudaError_t e = cudaMemsetAsync(g2d, 0, sizeof(float) * (g2d_hi ? 32 : 16) * (size_t)g->n, s);
     if (e == cudaSuccess)
-        e = launch_project_bwd(*g, *proj, make_views(cam, 1, *st, nullptr, g->n), g2d, accumulate_grads != 0, *grads,
-                               S_accum, S_po_accum, s);
+        e = launch_render_bwd(*proj, *bins, cd, sd, final_T, n_contrib, dL_dimage, g2d, g2d_hi, s);
+    if (e == cudaSuccess)
+        e = launch_project_bwd(*g, *proj, make_views(cam, 1, *st, nullptr, g->n), g2d, g2d_hi,
+                               accumulate_grads != 0, *grads, S_accum, S_po_accum, S_ls_accum, s);
     return cuda_status(e);
 }
 
@@ -360,7 +366,8 @@ int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* ca
         e = launch_render_bwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, w.final_T, w.n_contrib,
                                     w.dL, w.g2d, w.counters + 1, s);
     if (e == cudaSuccess)
-        e = launch_project_bwd(*g, w.proj, vd, w.g2d, accumulate_grads != 0, *grads, S_accum, S_po_accum, s);
+        e = launch_project_bwd(*g, w.proj, vd, w.g2d, nullptr, accumulate_grads != 0, *grads, S_accum, S_po_accum,
+                               nullptr, s);
     return cuda_status(e);
 }
 
@@ -418,8 +425,9 @@ int sgs_densify_split_workspace_size(int32_t n, size_t* bytes) {
     return SGS_OK;
 }
 
-int sgs_densify_split(const sgs_gaussians* in, const float* S_accum, const float* S_po_accum, float inv_T_split,
-                      float eps_split, float step_scale, const float* grad_norm, float eps_grad, int64_t max_splits,
+int sgs_densify_split(const sgs_gaussians* in, const float* S_accum, const float* S_po_accum,
+                      const float* S_ls_accum, float inv_T_split, float eps_split, float step_scale,
+                      const float* grad_norm, float eps_grad, int64_t max_splits,
                       const sgs_gaussians_mut* out, int64_t capacity, int32_t* d_n_out, int32_t* parent_index,
                       float* lam_min_out, float* v_min_out, void* ws, size_t ws_bytes, void* stream) {
     if (!valid_gaussians(in) || !out || !d_n_out || capacity < in->n || !isfinite(inv_T_split) ||
@@ -430,8 +438,9 @@ int sgs_densify_split(const sgs_gaussians* in, const float* S_accum, const float
         return SGS_ERR_INVALID_ARG;
     if (in->n > 0 && (out->means == in->means || out->sh == in->sh || out->opacity_logit == in->opacity_logit))
         return SGS_ERR_INVALID_ARG;
+    if (S_ls_accum && !S_po_accum) return SGS_ERR_INVALID_ARG;
     if (!ws || ws_bytes < densify_ws_bytes(in->n)) return SGS_ERR_WORKSPACE;
-    return cuda_status(launch_densify(*in, S_accum, S_po_accum, inv_T_split, eps_split, step_scale, grad_norm,
+    return cuda_status(launch_densify(*in, S_accum, S_po_accum, S_ls_accum, inv_T_split, eps_split, step_scale, grad_norm,
                                       eps_grad, max_splits, *out, capacity, d_n_out, parent_index, lam_min_out,
                                       v_min_out, ws, (cudaStream_t)stream));
 }

@@ -118,8 +118,8 @@ bool tile_supported(int tw, int th);
 cudaError_t launch_project(const ScenesDev& sc, int sh_degree, const ViewsDev& vd, const SetDev& st,
                            const sgs_proj& out, cudaStream_t stream);
 cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const ViewsDev& vd, const float* g2d,
-                               bool accumulate, const sgs_grads& grads, float* S_accum, float* S_po_accum,
-                               cudaStream_t stream);
+                               const float* g2d_hi, bool accumulate, const sgs_grads& grads, float* S_accum,
+                               float* S_po_accum, float* S_ls_accum, cudaStream_t stream);
 
 size_t bin_sort_ws_bytes(int n, int64_t capacity, int num_tiles);
 cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetDev& st, const sgs_bins& out, void* ws,
@@ -130,7 +130,7 @@ cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const 
                               cudaStream_t stream);
 cudaError_t launch_render_bwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
                               const SetDev& st, const float* final_T, const uint32_t* n_contrib,
-                              const float* dL_dimage, float* g2d, cudaStream_t stream);
+                              const float* dL_dimage, float* g2d, float* g2d_hi, cudaStream_t stream);
 
 cudaError_t launch_render_fwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                     const uint32_t* gids, const SetDev& st, int batch, float* images,
@@ -156,7 +156,8 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t co
                         float eps, int step, float* G, cudaStream_t stream);
 
 size_t densify_ws_bytes(int n);
-cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float* S_po, float inv_T, float eps_split,
+cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float* S_po, const float* S_ls, float inv_T,
+                           float eps_split,
                            float step_scale, const float* grad_norm, float eps_grad, int64_t max_splits,
                            const sgs_gaussians_mut& out, int64_t capacity, int32_t* d_n_out,
                            int32_t* parent, float* lam_out, float* v_out, void* ws,

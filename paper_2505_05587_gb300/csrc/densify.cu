@@ -190,71 +190,74 @@ __global__ void __launch_bounds__(256) eig_flag_kernel(const float* __restrict__
     flags[i] = f ? 1u : 0u;
 }
 
-// Minimum eigenpair of the 4x4 splitting matrix over theta = (p, o):
-// [[S, S_po], [S_po^T, 0]] * scale.  Cyclic Jacobi rotations (each zeroes one
-// off-diagonal pair), sweeps until the off-diagonal mass is below float32
-// resolution of ||A||_F (at most eight; 4x4 converges quadratically in three or
-// four), the eigenvector the column of the accumulated rotations at the
-// smallest diagonal entry, then one Rayleigh quotient and the canonical sign
-// (largest magnitude component positive, lowest index on ties).
-struct Eig4 {
+// Minimum eigenpair of a small symmetric matrix (the splitting matrix over
+// theta = (p, o), N = 4, or theta = (p, l, o), N = 7) by cyclic Jacobi
+// rotations (Jacobi's method; Golub & Van Loan, Matrix Computations, Sec.
+// 8.5).  Only the upper triangle is held (constant indices after unrolling, so
+// it stays in registers); each rotation zeroes one off-diagonal pair exactly.
+// Sweeps run until the off-diagonal mass is below float32 resolution of
+// ||A||_F (at most 12), the eigenvector is the column of the accumulated
+// rotations at the smallest diagonal entry, lambda the Rayleigh quotient of
+// the input matrix, sign canonical (largest magnitude component positive,
+// lowest index on ties).  entry(r, c) returns the scaled input entry, r <= c.
+template <int N>
+struct EigN {
     float lam;
-    float v[4];
+    float v[N];
 };
 
-__device__ Eig4 eig4_min(const float* s6, const float* spo, float scale) {
-    float a[4][4];
-    a[0][0] = s6[0] * scale; a[0][1] = s6[1] * scale; a[0][2] = s6[2] * scale;
-    a[1][1] = s6[3] * scale; a[1][2] = s6[4] * scale; a[2][2] = s6[5] * scale;
-    a[0][3] = spo[0] * scale; a[1][3] = spo[1] * scale; a[2][3] = spo[2] * scale; a[3][3] = 0.0f;
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < r; ++c) a[r][c] = a[c][r];
-    float V[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) V[r][c] = r == c ? 1.0f : 0.0f;
-    // ||A||_F^2 is invariant under the rotations; stop once the off-diagonal
-    // part is below float32 resolution of it (all-zero matrices skip at once)
+__host__ __device__ constexpr int upper_index(int r, int c, int n) {
+    return r <= c ? r * n - r * (r - 1) / 2 + (c - r) : c * n - c * (c - 1) / 2 + (r - c);
+}
+
+template <int N, class Entry>
+__device__ __forceinline__ EigN<N> jacobi_min(Entry entry) {
+    constexpr int NU = N * (N + 1) / 2;
+    float u[NU];
     float total = 0.0f;
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < N; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) total += a[r][c] * a[r][c];
+        for (int c = r; c < N; ++c) {
+            const float x = entry(r, c);
+            u[upper_index(r, c, N)] = x;
+            total += (r == c ? 1.0f : 2.0f) * x * x;
+        }
+    float V[N][N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c < N; ++c) V[r][c] = r == c ? 1.0f : 0.0f;
 #pragma unroll 1
-    for (int sweep = 0; sweep < 8; ++sweep) {
+    for (int sweep = 0; sweep < 12; ++sweep) {
         float off = 0.0f;
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
+        for (int p = 0; p < N - 1; ++p)
 #pragma unroll
-            for (int q = p + 1; q < 4; ++q) off += a[p][q] * a[p][q];
+            for (int q = p + 1; q < N; ++q) off += u[upper_index(p, q, N)] * u[upper_index(p, q, N)];
         if (!(2.0f * off > 1e-14f * total)) break;
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
+        for (int p = 0; p < N - 1; ++p)
 #pragma unroll
-            for (int q = p + 1; q < 4; ++q) {
-                const float apq = a[p][q];
+            for (int q = p + 1; q < N; ++q) {
+                const float apq = u[upper_index(p, q, N)];
                 if (apq == 0.0f) continue;
-                // rotation angle: t = tan(phi) of the smaller root of t^2 + 2 theta t - 1 = 0
-                const float theta = (a[q][q] - a[p][p]) / (2.0f * apq);
+                // t = tan(phi), the smaller root of t^2 + 2 theta t - 1 = 0
+                const float theta = (u[upper_index(q, q, N)] - u[upper_index(p, p, N)]) / (2.0f * apq);
                 const float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
                 const float c = rsqrtf(t * t + 1.0f), s = t * c;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {              // columns p, q
-                    const float akp = a[k][p], akq = a[k][q];
-                    a[k][p] = c * akp - s * akq;
-                    a[k][q] = s * akp + c * akq;
+                for (int k = 0; k < N; ++k) {
+                    if (k == p || k == q) continue;
+                    const float akp = u[upper_index(k, p, N)], akq = u[upper_index(k, q, N)];
+                    u[upper_index(k, p, N)] = c * akp - s * akq;
+                    u[upper_index(k, q, N)] = s * akp + c * akq;
                 }
+                u[upper_index(p, p, N)] -= t * apq;
+                u[upper_index(q, q, N)] += t * apq;
+                u[upper_index(p, q, N)] = 0.0f;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {              // rows p, q
-                    const float apk = a[p][k], aqk = a[q][k];
-                    a[p][k] = c * apk - s * aqk;
-                    a[q][k] = s * apk + c * aqk;
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < N; ++k) {
                     const float vkp = V[k][p], vkq = V[k][q];
                     V[k][p] = c * vkp - s * vkq;
                     V[k][q] = s * vkp + c * vkq;
@@ -262,56 +265,80 @@ __device__ Eig4 eig4_min(const float* s6, const float* spo, float scale) {
             }
     }
     // column of the smallest diagonal entry (first on ties), selected with
-    // constant indices so that a and V stay in registers
-    float dmin = a[0][0];
-    float v[4] = {V[0][0], V[1][0], V[2][0], V[3][0]};
+    // constant indices so that u and V stay in registers
+    float dmin = u[0];
+    float v[N];
 #pragma unroll
-    for (int k = 1; k < 4; ++k) {
-        const bool take = a[k][k] < dmin;
-        dmin = take ? a[k][k] : dmin;
+    for (int r = 0; r < N; ++r) v[r] = V[r][0];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) v[r] = take ? V[r][k] : v[r];
+    for (int k = 1; k < N; ++k) {
+        const float d = u[upper_index(k, k, N)];
+        const bool take = d < dmin;
+        dmin = take ? d : dmin;
+#pragma unroll
+        for (int r = 0; r < N; ++r) v[r] = take ? V[r][k] : v[r];
     }
-    const float inv = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+    float nrm = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) nrm += v[k] * v[k];
+    const float inv = rsqrtf(nrm);
     float big = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < N; ++k) {
         v[k] *= inv;
         big = fabsf(v[k]) > fabsf(big) ? v[k] : big;
     }
     const float sg = big < 0.0f ? -1.0f : 1.0f;
-    Eig4 e;
-    float lam = 0.0f;
-    const float b00 = s6[0] * scale, b01 = s6[1] * scale, b02 = s6[2] * scale, b11 = s6[3] * scale;
-    const float b12 = s6[4] * scale, b22 = s6[5] * scale;
-    const float c0 = spo[0] * scale, c1 = spo[1] * scale, c2 = spo[2] * scale;
+    EigN<N> e;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) e.v[k] = sg * v[k];
-    const float Av0 = b00 * e.v[0] + b01 * e.v[1] + b02 * e.v[2] + c0 * e.v[3];
-    const float Av1 = b01 * e.v[0] + b11 * e.v[1] + b12 * e.v[2] + c1 * e.v[3];
-    const float Av2 = b02 * e.v[0] + b12 * e.v[1] + b22 * e.v[2] + c2 * e.v[3];
-    const float Av3 = c0 * e.v[0] + c1 * e.v[1] + c2 * e.v[2];
-    lam = e.v[0] * Av0 + e.v[1] * Av1 + e.v[2] * Av2 + e.v[3] * Av3;
+    for (int k = 0; k < N; ++k) e.v[k] = sg * v[k];
+    float lam = 0.0f;
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        float Av = 0.0f;
+#pragma unroll
+        for (int c = 0; c < N; ++c) Av += entry(r < c ? r : c, r < c ? c : r) * e.v[c];
+        lam += e.v[r] * Av;
+    }
     e.lam = lam;
     return e;
 }
 
-__global__ void __launch_bounds__(256) eig4_flag_kernel(const float* __restrict__ S, const float* __restrict__ S_po,
-                                                        int n, float inv_T, float eps_split,
-                                                        const float* __restrict__ grad_norm, float eps_grad,
-                                                        float* __restrict__ lam_out, float* __restrict__ v_out,
-                                                        uint32_t* __restrict__ flags) {
+// Entry (r <= c) of the splitting matrix over theta = (p, o) (N = 4) or
+// theta = (p, l, o) (N = 7) from its stored blocks: s6 the p-p upper triangle
+// (xx xy xz yy yz zz), spo the p-o column, sls the p-l block (row p, column
+// l), the l-l upper triangle and the l-o column; o-o is zero.
+template <int N>
+__device__ __forceinline__ float theta_entry(const float* s6, const float* spo, const float* sls, int r, int c) {
+    constexpr int O = N - 1;
+    if (c < 3) return s6[upper_index(r, c, 3)];
+    if (c == O) return r == O ? 0.0f : (r < 3 ? spo[r] : sls[15 + r - 3]);
+    if (r < 3) return sls[3 * r + (c - 3)];
+    return sls[9 + upper_index(r - 3, c - 3, 3)];
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) eig_theta_flag_kernel(const float* __restrict__ S,
+                                                             const float* __restrict__ S_po,
+                                                             const float* __restrict__ S_ls, int n, float inv_T,
+                                                             float eps_split, const float* __restrict__ grad_norm,
+                                                             float eps_grad, float* __restrict__ lam_out,
+                                                             float* __restrict__ v_out, uint32_t* __restrict__ flags) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float s6[6], spo[3];
+    float s6[6], spo[3], sls[N == 7 ? 18 : 1];
 #pragma unroll
     for (int k = 0; k < 6; ++k) s6[k] = S[(size_t)i * 6 + k];
 #pragma unroll
     for (int k = 0; k < 3; ++k) spo[k] = S_po[(size_t)i * 3 + k];
-    const Eig4 e = eig4_min(s6, spo, inv_T);
+    if constexpr (N == 7) {
+#pragma unroll
+        for (int k = 0; k < 18; ++k) sls[k] = S_ls[(size_t)i * 18 + k];
+    }
+    const EigN<N> e = jacobi_min<N>([&](int r, int c) { return theta_entry<N>(s6, spo, sls, r, c) * inv_T; });
     lam_out[i] = e.lam;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v_out[4 * (size_t)i + k] = e.v[k];
+    for (int k = 0; k < N; ++k) v_out[N * (size_t)i + k] = e.v[k];
     bool f = e.lam < eps_split;
     if (grad_norm) f = f && (grad_norm[i] <= eps_grad);
     flags[i] = f ? 1u : 0u;
@@ -404,8 +431,10 @@ __device__ __forceinline__ float half_opacity_logit(float x) {
 // Per-Gaussian fields of the output rows: mean, scales, rotation, opacity,
 // parent index.  Row i holds Gaussian i (moved to p + eps v when flagged);
 // row N + excl[i] holds the second offspring p - eps v.  DIM = 3: both
-// offspring take o/2.  DIM = 4 (theta = (p, o)): v has an opacity component
-// and the offspring take (o +- eps v_o) / 2, clamped to [1e-4, 1 - 1e-4].
+// offspring take o/2.  DIM = 4 (theta = (p, o)) and 7 (theta = (p, l, o)): v
+// ends with an opacity component and the offspring take (o +- eps v_o) / 2,
+// clamped to [1e-4, 1 - 1e-4]; DIM = 7 also moves the log-scales by
+// +- eps v_l.
 template <int DIM>
 __global__ void __launch_bounds__(256) split_fields_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
@@ -426,7 +455,9 @@ __global__ void __launch_bounds__(256) split_fields_kernel(
         lg = half_opacity_logit(x);
     }
     const float v0 = f ? v[DIM * i] : 0.0f, v1 = f ? v[DIM * i + 1] : 0.0f, v2 = f ? v[DIM * i + 2] : 0.0f;
-    const float vo = (DIM == 4 && f) ? v[DIM * i + 3] : 0.0f;
+    const float vo = (DIM > 3 && f) ? v[DIM * i + DIM - 1] : 0.0f;
+    const float w0 = (DIM == 7 && f) ? v[DIM * i + 3] : 0.0f, w1 = (DIM == 7 && f) ? v[DIM * i + 4] : 0.0f;
+    const float w2 = (DIM == 7 && f) ? v[DIM * i + 5] : 0.0f;
     const float o = 1.0f / (1.0f + expf(-x));
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -436,11 +467,11 @@ __global__ void __launch_bounds__(256) split_fields_kernel(
         o_means[3 * row] = p0 + sg * v0;
         o_means[3 * row + 1] = p1 + sg * v1;
         o_means[3 * row + 2] = p2 + sg * v2;
-        o_ls[3 * row] = l0;
-        o_ls[3 * row + 1] = l1;
-        o_ls[3 * row + 2] = l2;
+        o_ls[3 * row] = l0 + sg * w0;
+        o_ls[3 * row + 1] = l1 + sg * w1;
+        o_ls[3 * row + 2] = l2 + sg * w2;
         reinterpret_cast<float4*>(o_quats)[row] = q;
-        if (DIM == 4 && f) {
+        if (DIM > 3 && f) {
             const float oj = fminf(fmaxf(0.5f * (o + sg * vo), 1e-4f), 1.0f - 1e-4f);
             o_logit[row] = logf(oj) - log1pf(-oj);
         } else {
@@ -480,14 +511,15 @@ size_t densify_ws_bytes(int n) {
     c.take<uint32_t>(nn);       // excl
     c.take<uint32_t>(1);        // total
     c.take<float>(nn);          // lam (when the caller passes none)
-    c.take<float>(4 * nn);      // v (4 components over theta = (p, o))
+    c.take<float>(7 * nn);      // v (up to 7 components, theta = (p, l, o))
     c.take<char>(scan_tmp_bytes(n));
     c.take<uint32_t>(nn);       // ties at the budget threshold
     c.take<SelectState>(1);
     return c.off + 256;
 }
 
-cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float* S_po, float inv_T, float eps_split,
+cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float* S_po, const float* S_ls,
+                           float inv_T, float eps_split,
                            float step_scale, const float* grad_norm, float eps_grad, int64_t max_splits,
                            const sgs_gaussians_mut& out, int64_t capacity, int32_t* d_n_out, int32_t* parent,
                            float* lam_out, float* v_out, void* ws, cudaStream_t stream) {
@@ -498,7 +530,7 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
     uint32_t* excl = c.take<uint32_t>(nn);
     uint32_t* total = c.take<uint32_t>(1);
     float* lam_ws = c.take<float>(nn);
-    float* v_ws = c.take<float>(4 * nn);
+    float* v_ws = c.take<float>(7 * nn);
     void* scan_tmp = c.take<char>(scan_tmp_bytes(n));
     uint32_t* tie = c.take<uint32_t>(nn);
     SelectState* sel = c.take<SelectState>(1);
@@ -506,8 +538,12 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
     float* v = v_out ? v_out : v_ws;
     if (n == 0) return cudaMemsetAsync(d_n_out, 0, sizeof(int32_t), stream);
     const int nb = (n + 255) / 256;
-    if (S_po)
-        eig4_flag_kernel<<<nb, 256, 0, stream>>>(S, S_po, n, inv_T, eps_split, grad_norm, eps_grad, lam, v, flags);
+    if (S_po && S_ls)
+        eig_theta_flag_kernel<7><<<nb, 256, 0, stream>>>(S, S_po, S_ls, n, inv_T, eps_split, grad_norm, eps_grad,
+                                                         lam, v, flags);
+    else if (S_po)
+        eig_theta_flag_kernel<4><<<nb, 256, 0, stream>>>(S, S_po, nullptr, n, inv_T, eps_split, grad_norm, eps_grad,
+                                                         lam, v, flags);
     else
         eig_flag_kernel<<<nb, 256, 0, stream>>>(S, n, inv_T, eps_split, grad_norm, eps_grad, lam, v, flags);
     note_launch();
@@ -535,7 +571,7 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
     n_out_kernel<<<1, 1, 0, stream>>>(total, n, d_n_out);
     note_launch();
     const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;
-    auto fields = S_po ? split_fields_kernel<4> : split_fields_kernel<3>;
+    auto fields = S_po ? (S_ls ? split_fields_kernel<7> : split_fields_kernel<4>) : split_fields_kernel<3>;
     fields<<<nb, 256, 0, stream>>>(in.means, in.log_scales, in.quats, in.opacity_logit, n, v, flags, excl,
                                    step_scale, capacity, out.means, out.log_scales, out.quats, out.opacity_logit,
                                    parent);

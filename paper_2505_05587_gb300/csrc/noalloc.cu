@@ -47,7 +47,7 @@ static int scratch_address(void** out) {
 using namespace sgs;
 
 extern "C" int sgs_densify_split_noalloc(const sgs_gaussians* in, const float* S_accum, const float* S_po_accum,
-                                         float inv_T_split, float eps_split, float step_scale,
+                                         const float* S_ls_accum, float inv_T_split, float eps_split, float step_scale,
                                          const float* grad_norm, float eps_grad, int64_t max_splits,
                                          const sgs_gaussians_mut* out, int64_t capacity, int32_t* d_n_out,
                                          int32_t* parent_index, float* lam_min_out, float* v_min_out,
@@ -57,7 +57,8 @@ extern "C" int sgs_densify_split_noalloc(const sgs_gaussians* in, const float* S
     void* ws = nullptr;
     int ce = scratch_address(&ws);
     if (ce != 0) return record_cuda_error((cudaError_t)ce);
-    return sgs_densify_split(in, S_accum, S_po_accum, inv_T_split, eps_split, step_scale, grad_norm, eps_grad,
+    return sgs_densify_split(in, S_accum, S_po_accum, S_ls_accum, inv_T_split, eps_split, step_scale, grad_norm,
+                             eps_grad,
                              max_splits, out, capacity, d_n_out, parent_index, lam_min_out, v_min_out, ws,
                              (size_t)SGS_NOALLOC_SCRATCH_BYTES, stream);
 }

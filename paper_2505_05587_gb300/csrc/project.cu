@@ -368,9 +368,10 @@ cudaError_t launch_project(const ScenesDev& sc, int sh_degree, const ViewsDev& v
 
 // Geometry adjoint of one Gaussian in one view: adds the view's splitting
 // matrix to S6 and its parameter gradients to the accumulators.
-template <bool PO>
+template <bool PO, bool LS>
 __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, float p1, float p2, float4 q4,
-                                                 const float* sc, float4 co, const float* gg, float* S6, float* Spo,
+                                                 const float* sc, float4 co, const float* gg, const float* gh,
+                                                 float* S6, float* Spo, float* Sls,
                                                  float& gm0, float& gm1, float& gm2, float& gl0, float& gl1,
                                                  float& gl2, float4& gq, float& glog) {
     const float* R = cam.R;
@@ -431,6 +432,60 @@ __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, fl
         const float io = o > 0.0f ? 1.0f / o : 0.0f;
 #pragma unroll
         for (int j = 0; j < 3; ++j) Spo[j] += (P[j] * dmx + P[3 + j] * dmy) * io;
+    }
+    // log-scale blocks of the splitting matrix over theta = (p, l, o), P
+    // frozen: with a_k = P Rq e_k, b_k = Q a_k, t_k = b_k . d, s2_k = exp(2 l_k)
+    // (dQ/dl_k = -2 s2_k b_k b_k^T), summed over the view's pixels with
+    // w = dL/dsigma sigma through the moments of w d up to fourth order:
+    //   p-l[j][k] = s2_k sum w t_k^2 (Q P e_j).d - 2 s2_k (P^T b_k)_j sum w t_k
+    //   l-l[k][l] = s2_k s2_l sum w t_k^2 t_l^2 + 2 delta_kl s2_k sum w t_k^2
+    //               - 4 s2_k s2_l (a_k . b_l) sum w t_k t_l
+    //   l-o[k]    = s2_k sum w t_k^2 / o
+    if constexpr (LS) {
+        const float T0 = gh[0], T1 = gh[1], T2 = gh[2], T3 = gh[3];             // x3 x2y xy2 y3
+        const float F0 = gh[4], F1 = gh[5], F2 = gh[6], F3 = gh[7], F4 = gh[8];  // x4 x3y x2y2 xy3 y4
+        float ak0[3], ak1[3], bk0[3], bk1[3], s2[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            ak0[k] = P[0] * Rq[k] + P[1] * Rq[3 + k] + P[2] * Rq[6 + k];
+            ak1[k] = P[3] * Rq[k] + P[4] * Rq[3 + k] + P[5] * Rq[6 + k];
+            bk0[k] = Qa * ak0[k] + Qb * ak1[k];
+            bk1[k] = Qb * ak0[k] + Qc * ak1[k];
+            s2[k] = sc[k] * sc[k];
+        }
+        auto quad = [&](float u0, float u1, float v0, float v1) {
+            return u0 * v0 * D00 + (u0 * v1 + u1 * v0) * D01 + u1 * v1 * D11;
+        };
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float q0 = Qa * P[j] + Qb * P[3 + j], q1 = Qb * P[j] + Qc * P[3 + j];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float u0 = bk0[k], u1 = bk1[k];
+                const float cubic = u0 * u0 * q0 * T0 + (u0 * u0 * q1 + 2.0f * u0 * u1 * q0) * T1 +
+                                    (2.0f * u0 * u1 * q1 + u1 * u1 * q0) * T2 + u1 * u1 * q1 * T3;
+                const float tk = u0 * sx + u1 * sy;
+                const float ptb = P[j] * u0 + P[3 + j] * u1;
+                Sls[3 * j + k] += s2[k] * cubic - 2.0f * s2[k] * ptb * tk;
+            }
+        }
+        int q = 9;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int l = k; l < 3; ++l) {
+                const float u0 = bk0[k], u1 = bk1[k], v0 = bk0[l], v1 = bk1[l];
+                const float quart = u0 * u0 * v0 * v0 * F0 + (2.0f * u0 * u0 * v0 * v1 + 2.0f * u0 * u1 * v0 * v0) * F1 +
+                                    (u0 * u0 * v1 * v1 + 4.0f * u0 * u1 * v0 * v1 + u1 * u1 * v0 * v0) * F2 +
+                                    (2.0f * u0 * u1 * v1 * v1 + 2.0f * u1 * u1 * v0 * v1) * F3 + u1 * u1 * v1 * v1 * F4;
+                const float quv = quad(u0, u1, v0, v1);
+                const float ckl = ak0[k] * v0 + ak1[k] * v1;
+                Sls[q++] += s2[k] * s2[l] * quart + (k == l ? 2.0f * s2[k] * quv : 0.0f) -
+                            4.0f * s2[k] * s2[l] * ckl * quv;
+            }
+        const float io = o > 0.0f ? 1.0f / o : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Sls[15 + k] += s2[k] * quad(bk0[k], bk1[k], bk0[k], bk1[k]) * io;
     }
     // opacity: dL/do = a0 / o (unclamped pairs carry alpha = o G)
     glog += (o > 0.0f ? a0 / o : 0.0f) * o * (1.0f - o);
@@ -506,14 +561,15 @@ __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, fl
 // accesses.
 // MULTI = false is the single-view case: no view loop, and the SH gradient
 // increments overwrite the staged coefficients once they have been used.
-template <int DEG, bool MULTI, bool PO>
-__global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_kernel(
+template <int DEG, bool MULTI, bool PO, bool LS>
+__global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 5)) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ sh, int n, ViewsDev vd, const float4* __restrict__ conic_opac,
-    const uint32_t* __restrict__ tiles, const float* __restrict__ g2d, int accumulate,
+    const uint32_t* __restrict__ tiles, const float* __restrict__ g2d, const float* __restrict__ g2d_hi,
+    int accumulate,
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_logit, float* __restrict__ g_sh, float* __restrict__ S_accum,
-    float* __restrict__ S_po_accum) {
+    float* __restrict__ S_po_accum, float* __restrict__ S_ls_accum) {
     constexpr int THREADS = MULTI ? 64 : 128;
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int K3 = 3 * K;
@@ -587,6 +643,9 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
     float4 gq = make_float4(0.f, 0.f, 0.f, 0.f);
     float S6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float Spo[3] = {0.f, 0.f, 0.f};
+    float Sls[LS ? 18 : 1];
+#pragma unroll
+    for (int k = 0; k < (LS ? 18 : 1); ++k) Sls[k] = 0.0f;
     if (work) {
         const float sc[3] = {__expf(ls0), __expf(ls1), __expf(ls2)};
         const float* crow = wc + lane * ROW;
@@ -602,8 +661,13 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
                 gg[0] = a.x; gg[1] = a.y; gg[2] = a.z; gg[3] = a.w;
                 gg[4] = b.x; gg[5] = b.y; gg[6] = b.z; gg[7] = b.w; gg[8] = c.x;
             }
-            geometry_adjoint<PO>(cam, p0, p1, p2, q4, sc, conic_opac[row], gg, S6, Spo, gm0, gm1, gm2, gl0, gl1,
-                                 gl2, gq, glog);
+            float gh[LS ? 9 : 1];
+            if constexpr (LS) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) gh[k] = g2d_hi[(size_t)row * 16 + k];
+            }
+            geometry_adjoint<PO, LS>(cam, p0, p1, p2, q4, sc, conic_opac[row], gg, gh, S6, Spo, Sls, gm0, gm1, gm2,
+                                     gl0, gl1, gl2, gq, glog);
             // colour (SH) of this view
             const float d0 = p0 - cam.cc[0], d1 = p1 - cam.cc[1], d2 = p2 - cam.cc[2];
             const float inv_dn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -655,6 +719,11 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
 #pragma unroll
             for (int k = 0; k < 3; ++k) Sp[k] += Spo[k];
         }
+        if constexpr (LS) {
+            float* Sl = S_ls_accum + (size_t)i * 18;
+#pragma unroll
+            for (int k = 0; k < 18; ++k) Sl[k] += Sls[k];
+        }
     }
     if (i < n) {
         if (accumulate) {
@@ -688,28 +757,35 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : 5) project_bwd_k
 }
 
 cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const ViewsDev& vd, const float* g2d,
-                               bool accumulate, const sgs_grads& grads, float* S_accum, float* S_po_accum,
-                               cudaStream_t stream) {
+                               const float* g2d_hi, bool accumulate, const sgs_grads& grads, float* S_accum,
+                               float* S_po_accum, float* S_ls_accum, cudaStream_t stream) {
     if (g.n == 0) return cudaSuccess;
     const bool multi = vd.nv > 1;
     const int threads = multi ? 64 : 128;
     const int blocks = (g.n + threads - 1) / threads;
     auto pick = [&](auto po) {
         constexpr bool PO = decltype(po)::value;
-        return multi ? (g.sh_degree == 0 ? project_bwd_kernel<0, true, PO>
-                      : g.sh_degree == 1 ? project_bwd_kernel<1, true, PO>
-                      : g.sh_degree == 2 ? project_bwd_kernel<2, true, PO> : project_bwd_kernel<3, true, PO>)
-                     : (g.sh_degree == 0 ? project_bwd_kernel<0, false, PO>
-                      : g.sh_degree == 1 ? project_bwd_kernel<1, false, PO>
-                      : g.sh_degree == 2 ? project_bwd_kernel<2, false, PO> : project_bwd_kernel<3, false, PO>);
+        return multi ? (g.sh_degree == 0 ? project_bwd_kernel<0, true, PO, false>
+                      : g.sh_degree == 1 ? project_bwd_kernel<1, true, PO, false>
+                      : g.sh_degree == 2 ? project_bwd_kernel<2, true, PO, false>
+                                         : project_bwd_kernel<3, true, PO, false>)
+                     : (g.sh_degree == 0 ? project_bwd_kernel<0, false, PO, false>
+                      : g.sh_degree == 1 ? project_bwd_kernel<1, false, PO, false>
+                      : g.sh_degree == 2 ? project_bwd_kernel<2, false, PO, false>
+                                         : project_bwd_kernel<3, false, PO, false>);
     };
-    // the position-opacity block is a separate instantiation, so the common
-    // position-only kernel carries none of its code
+    // the (p, o) and (p, l, o) blocks are separate instantiations, so the
+    // common position-only kernel carries none of their code; (p, l, o) is
+    // single-view only
     auto kern = S_po_accum ? pick(std::true_type{}) : pick(std::false_type{});
+    if (S_ls_accum && !multi)
+        kern = g.sh_degree == 0 ? project_bwd_kernel<0, false, true, true>
+             : g.sh_degree == 1 ? project_bwd_kernel<1, false, true, true>
+             : g.sh_degree == 2 ? project_bwd_kernel<2, false, true, true> : project_bwd_kernel<3, false, true, true>;
     kern<<<blocks, threads, 0, stream>>>(
         g.means, g.log_scales, g.quats, g.sh, g.n, vd, reinterpret_cast<const float4*>(proj.conic_opac),
-        proj.tiles_touched, g2d, accumulate ? 1 : 0, grads.means, grads.log_scales, grads.quats,
-        grads.opacity_logit, grads.sh, S_accum, S_po_accum);
+        proj.tiles_touched, g2d, g2d_hi, accumulate ? 1 : 0, grads.means, grads.log_scales, grads.quats,
+        grads.opacity_logit, grads.sh, S_accum, S_po_accum, S_ls_accum);
     note_launch();
     return cudaGetLastError();
 }

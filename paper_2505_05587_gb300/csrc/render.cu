@@ -223,13 +223,17 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Backward pass of one tile, back to front, with the splitting accumulators.
-template <int TW, int TH, int BATCH>
+// HI: also the third and fourth moments of w d (the log-scale blocks of the
+// splitting matrix over theta = (p, l, o)) into g2d_hi rows of kG2dStride:
+//  0..3 sum w (dx^3, dx^2 dy, dx dy^2, dy^3), 4..8 sum w (dx^4, dx^3 dy,
+//  dx^2 dy^2, dx dy^3, dy^4).
+template <int TW, int TH, int BATCH, bool HI>
 __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 rg, const uint32_t* __restrict__ gids,
                                          const float4* __restrict__ xy, const float4* __restrict__ conic_opac,
                                          const float4* __restrict__ rgb, const SetDev& st,
                                          const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
                                          const float* __restrict__ dL_dimage, float* __restrict__ g2d,
-                                         BwdSmem<BATCH, TW * TH / 32>& sm) {
+                                         float* __restrict__ g2d_hi, BwdSmem<BATCH, TW * TH / 32>& sm) {
     constexpr int BS = TW * TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int bx, by;
@@ -305,6 +309,15 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
             const float tot8 = warp_reduce_scatter8(v);
             const float tot1 = warp_sum(v8);
             if (slot >= 0) atomicAdd(g2d + (size_t)sm.gid[e] * kG2dStride + slot, slot == 8 ? tot1 : tot8);
+            if constexpr (HI) {
+                const float wxx = wdx * dx, wyy = wdy * dy;
+                float u[8] = {wxx * dx, wxx * dy, wyy * dx, wyy * dy, wxx * dx * dx, wxx * dx * dy, wxx * dy * dy,
+                              wyy * dx * dy};
+                const float u8 = wyy * dy * dy;
+                const float hi8 = warp_reduce_scatter8(u);
+                const float hi1 = warp_sum(u8);
+                if (slot >= 0) atomicAdd(g2d_hi + (size_t)sm.gid[e] * kG2dStride + slot, slot == 8 ? hi1 : hi8);
+            }
         }
     }
     __syncthreads();        // shared memory is reused by the next tile
@@ -325,15 +338,15 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
 
 // The backward kernels are bounded to 40 resident warps per SM (48 registers):
 // their pair loop is issue-bound and hides its latencies with warps.
-template <int TW, int TH>
+template <int TW, int TH, bool HI>
 __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
-    const float* __restrict__ dL_dimage, float* __restrict__ g2d) {
+    const float* __restrict__ dL_dimage, float* __restrict__ g2d, float* __restrict__ g2d_hi) {
     __shared__ BwdSmem<TW * TH, TW * TH / 32> sm;
-    bwd_tile<TW, TH, TW * TH>(blockIdx.x, gx, W, H, ranges[blockIdx.x], gids, xy, conic_opac, rgb, st, final_T,
-                              n_contrib, dL_dimage, g2d, sm);
+    bwd_tile<TW, TH, TW * TH, HI>(blockIdx.x, gx, W, H, ranges[blockIdx.x], gids, xy, conic_opac, rgb, st, final_T,
+                                  n_contrib, dL_dimage, g2d, g2d_hi, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -379,8 +392,9 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_views_ke
         const int v = view_of_tile(vd, t);
         const CamDev& c = vd.cam[v];
         const long long po = vd.pix_off[v];
-        bwd_tile<TW, TH, BATCH>(t - vd.tile_off[v], c.gx, c.width, c.height, ranges[t], gids, xy, conic_opac, rgb,
-                                st, final_T + po, n_contrib + po, dL + 3 * po, g2d, sm);
+        bwd_tile<TW, TH, BATCH, false>(t - vd.tile_off[v], c.gx, c.width, c.height, ranges[t], gids, xy,
+                                       conic_opac, rgb, st, final_T + po, n_contrib + po, dL + 3 * po, g2d, nullptr,
+                                       sm);
     }
 }
 
@@ -468,12 +482,13 @@ static cudaError_t fwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const Ca
 template <int TW, int TH>
 static cudaError_t bwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
                             const float* final_T, const uint32_t* n_contrib, const float* dL, float* g2d,
-                            cudaStream_t stream) {
+                            float* g2d_hi, cudaStream_t stream) {
     const int T = cam.gx * cam.gy;
-    render_bwd_kernel<TW, TH><<<T, TW * TH, 0, stream>>>(
+    auto kern = g2d_hi ? render_bwd_kernel<TW, TH, true> : render_bwd_kernel<TW, TH, false>;
+    kern<<<T, TW * TH, 0, stream>>>(
         reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
         reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
-        cam.width, cam.height, cam.gx, st, final_T, n_contrib, dL, g2d);
+        cam.width, cam.height, cam.gx, st, final_T, n_contrib, dL, g2d, g2d_hi);
     note_launch();
     return cudaGetLastError();
 }
@@ -497,8 +512,8 @@ cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const 
 
 cudaError_t launch_render_bwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
                               const float* final_T, const uint32_t* n_contrib, const float* dL, float* g2d,
-                              cudaStream_t stream) {
-    SGS_TILE_DISPATCH(bwd_tmpl, proj, bins, cam, st, final_T, n_contrib, dL, g2d, stream)
+                              float* g2d_hi, cudaStream_t stream) {
+    SGS_TILE_DISPATCH(bwd_tmpl, proj, bins, cam, st, final_T, n_contrib, dL, g2d, g2d_hi, stream)
 }
 
 // Persistent multi-view launches: CTAs per SM from the occupancy calculator.

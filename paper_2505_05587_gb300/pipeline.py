@@ -100,14 +100,16 @@ class DensifyBuffers:
     n_out: torch.Tensor
     split_ws: torch.Tensor
     capacity: int
-    S_po: torch.Tensor | None = None     # [N,3] position-opacity block (theta = (p, o)) when dim_theta = 4
+    S_po: torch.Tensor | None = None     # [N,3] position-opacity block when dim_theta = 4 or 7
+    S_ls: torch.Tensor | None = None     # [N,18] log-scale blocks (theta = (p, l, o)) when dim_theta = 7
 
     @staticmethod
     def alloc(g: B.GaussianTensors, capacity: int | None = None, dim_theta: int = 3) -> "DensifyBuffers":
         """dim_theta = 3: splitting matrices over the position (the paper's
-        experiments); 4: over (position, opacity)."""
-        if dim_theta not in (3, 4):
-            raise ValueError("dim_theta must be 3 or 4")
+        experiments); 4: over (position, opacity); 7: over (position,
+        log-scales, opacity)."""
+        if dim_theta not in (3, 4, 7):
+            raise ValueError("dim_theta must be 3, 4 or 7")
         n = g.n
         dev = g.means.device
         cap = capacity if capacity is not None else 2 * n
@@ -117,7 +119,8 @@ class DensifyBuffers:
                               torch.empty(cap, device=dev, dtype=torch.int32), torch.empty(n, device=dev),
                               torch.empty(n, dim_theta, device=dev), torch.zeros(1, device=dev, dtype=torch.int32),
                               B.workspace(B.densify_split_workspace_size(n), dev), cap,
-                              torch.zeros(n, 3, device=dev) if dim_theta == 4 else None)
+                              torch.zeros(n, 3, device=dev) if dim_theta > 3 else None,
+                              torch.zeros(n, 18, device=dev) if dim_theta == 7 else None)
 
     def zero_(self, grads: bool = True):
         """Resets the accumulators; the gradients need no reset when the first
@@ -126,8 +129,9 @@ class DensifyBuffers:
             for t in self.grads.tensors():
                 t.zero_()
         self.S.zero_()
-        if self.S_po is not None:
-            self.S_po.zero_()
+        for t in (self.S_po, self.S_ls):
+            if t is not None:
+                t.zero_()
         self.loss.zero_()
 
 
@@ -146,6 +150,8 @@ def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: lis
         vb.loss_grad(tgt, V, db.loss, lambda_dssim, stream)
         # the first view overwrites the gradients, later views add to them
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, vb.cam, vb.st, vb.final_T, vb.n_contrib, vb.dL,
-                                    db.grads, db.S, db.bwd_ws, stream, accumulate=k > 0, S_po=db.S_po)
+                                    db.grads, db.S, db.bwd_ws, stream, accumulate=k > 0, S_po=db.S_po,
+                                    S_ls=db.S_ls)
     B.densify_split(g, db.S, 1.0 / T_split, eps_split, step_scale, grad_norm, eps_grad, db.out, db.capacity,
-                    db.n_out, db.parent, db.lam, db.v, db.split_ws, stream, max_splits=max_splits, S_po=db.S_po)
+                    db.n_out, db.parent, db.lam, db.v, db.split_ws, stream, max_splits=max_splits, S_po=db.S_po,
+                    S_ls=db.S_ls)

@@ -32,7 +32,8 @@ class RenderContext:
     S: torch.Tensor            # [N,6] splitting-matrix accumulator (added to in backward)
     bwd_ws: torch.Tensor
     sh_degree: int
-    S_po: torch.Tensor | None = None   # [N,3] position-opacity block (theta = (p, o))
+    S_po: torch.Tensor | None = None   # [N,3] position-opacity block (theta = (p, o) or (p, l, o))
+    S_ls: torch.Tensor | None = None   # [N,18] log-scale blocks (theta = (p, l, o))
 
 
 class RasterizeWithSplitting(torch.autograd.Function):
@@ -56,7 +57,8 @@ class RasterizeWithSplitting(torch.autograd.Function):
         vb = rc.view
         grads = B.GaussianTensors.empty(g.n, g.sh_degree, g.means.device)
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, vb.cam, vb.st, vb.final_T, vb.n_contrib,
-                                    dL_dimage.contiguous(), grads, rc.S, rc.bwd_ws, accumulate=False, S_po=rc.S_po)
+                                    dL_dimage.contiguous(), grads, rc.S, rc.bwd_ws, accumulate=False, S_po=rc.S_po,
+                                    S_ls=rc.S_ls)
         return grads.means, grads.log_scales, grads.quats, grads.opacity_logit, grads.sh, None
 
 
@@ -74,7 +76,8 @@ class TrainConfig:
     step_scale: float = 1.0
     eps_grad: float | None = None      # compactest gate ||G_bar|| <= eps_grad when set
     max_splits: int = 0                # increment budget per densification (0: none)
-    dim_theta: int = 3                 # splitting matrices over the position (3) or (position, opacity) (4)
+    dim_theta: int = 3                 # splitting over the position (3), (position, opacity) (4) or
+    #                                    (position, log-scales, opacity) (7)
     lambda_dssim: float | None = None  # loss (1 - l) L1 + l (1 - SSIM) when set, else L1
     log_every: int = 10
 
@@ -96,7 +99,8 @@ class SteepGSTrainer:
         dev = self.params[0].device
         self.views = [PL.ViewBuffers.alloc(n, c, self.st, device=dev) for c in self.cams]
         self.S = torch.zeros(n, 6, device=dev)
-        self.S_po = torch.zeros(n, 3, device=dev) if self.cfg.dim_theta == 4 else None
+        self.S_po = torch.zeros(n, 3, device=dev) if self.cfg.dim_theta > 3 else None
+        self.S_ls = torch.zeros(n, 18, device=dev) if self.cfg.dim_theta == 7 else None
         self.G = torch.zeros(n, 3, device=dev)
         self.n_accum = 0
         self.bwd_ws = B.workspace(B.render_bwd_workspace_size(n), dev)
@@ -116,7 +120,7 @@ class SteepGSTrainer:
 
     def step(self, t: int) -> float | None:
         k = t % len(self.cams)
-        rc = RenderContext(self.views[k], self.S, self.bwd_ws, self.sh_degree, self.S_po)
+        rc = RenderContext(self.views[k], self.S, self.bwd_ws, self.sh_degree, self.S_po, self.S_ls)
         image = render(self.params, rc)
         self.loss.zero_()
         if self.cfg.lambda_dssim is None:
@@ -156,7 +160,7 @@ class SteepGSTrainer:
             gn = (self.G / max(self.n_accum, 1)).norm(dim=1).contiguous()
         B.densify_split(g, self.S, 1.0 / max(self.n_accum, 1), cfg.eps_split, cfg.step_scale, gn,
                         cfg.eps_grad or 0.0, out, 2 * n, n_out, parent, lam, vmin, ws, max_splits=cfg.max_splits,
-                        S_po=self.S_po)
+                        S_po=self.S_po, S_ls=self.S_ls)
         n2 = int(n_out.item())
         split = n2 - n
         par = parent[:n2].long()

@@ -1,0 +1,186 @@
+"""Splitting matrices over theta = (p, l, o), l the log-scales, on the GPU:
+the log-scale blocks from the backward (pixel moments of w (x - mu) up to
+fourth order, lifted in the projection adjoint), the 7x7 minimum eigenpair
+and the split that also moves the log-scales, against the float64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+from paper_2505_05587_gb300 import binding as B  # noqa: E402
+from paper_2505_05587_gb300 import pipeline as PL  # noqa: E402
+
+CASES = [
+    ("tiny", lambda: synth.tiny_scene(0), lambda: synth.camera_identity(64, 64, 64.0), synth.Settings()),
+    ("cluster_sh3_lookat", lambda: synth.cluster_scene(3, 3000, 3),
+     lambda: synth.camera_lookat((1.0, 0.5, -6.0), (0, 0, 0), 150, 101, 150.0), synth.Settings()),
+    ("tile8x8_sh1", lambda: synth.cluster_scene(5, 800, 1),
+     lambda: synth.camera_lookat((0.0, -1.0, -6.0), (0, 0, 0), 77, 59, 77.0), synth.Settings(tile_w=8, tile_h=8)),
+]
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+def _upper6(S):
+    return np.stack([S[:, 0, 0], S[:, 0, 1], S[:, 0, 2], S[:, 1, 1], S[:, 1, 2], S[:, 2, 2]], 1)
+
+
+def _backward7(scene, cam, st, accumulate_twice=False):
+    g = B.GaussianTensors.from_scene(scene)
+    vb = PL.ViewBuffers.alloc(scene.n, cam, st)
+    PL.project_and_sort(g, vb)
+    B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib)
+    ref = oracle.render(scene, cam, st)
+    _, dL_ref = oracle.l1_loss_grad(ref["image"], synth.target_image(2, cam.height, cam.width))
+    dL = torch.as_tensor(dL_ref.astype(np.float32)).cuda().contiguous()
+    grads = g.zeros_like()
+    S = torch.zeros(scene.n, 6, device="cuda")
+    S_po = torch.zeros(scene.n, 3, device="cuda")
+    S_ls = torch.zeros(scene.n, 18, device="cuda")
+    ws = B.workspace(B.render_bwd_workspace_size(scene.n))
+    for _ in range(2 if accumulate_twice else 1):
+        B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, dL, grads, S, ws,
+                                    accumulate=False, S_po=S_po, S_ls=S_ls)
+    torch.cuda.synchronize()
+    acc = oracle.backward(scene, cam, st, dL_ref.astype(np.float32).astype(np.float64))
+    return g, S, S_po, S_ls, acc
+
+
+@pytest.mark.parametrize("name,mk_scene,mk_cam,st", CASES, ids=[c[0] for c in CASES])
+def test_log_scale_blocks_parity(name, mk_scene, mk_cam, st):
+    scene, cam = mk_scene(), mk_cam()
+    _, S, S_po, S_ls, acc = _backward7(scene, cam, st)
+    got = S_ls.cpu().numpy()
+    ref = acc["S_ls"]
+    assert _rel(got, ref) < 1e-4
+    for lo, hi in ((0, 9), (9, 15), (15, 18)):       # p-l, l-l, l-o blocks on their own
+        assert _rel(got[:, lo:hi], ref[:, lo:hi]) < 1e-4, (lo, hi)
+    assert _rel(S_po.cpu().numpy(), acc["S_po"]) < 1e-4
+    assert _rel(S.cpu().numpy(), _upper6(acc["S"])) < 1e-4
+
+
+def test_log_scale_blocks_accumulate():
+    """Two calls add: the accumulators hold twice one call's blocks."""
+    scene, cam, st = CASES[0][1](), CASES[0][2](), CASES[0][3]
+    _, S, S_po, S_ls, acc = _backward7(scene, cam, st, accumulate_twice=True)
+    assert _rel(S_ls.cpu().numpy(), 2 * acc["S_ls"]) < 1e-4
+    assert _rel(S_po.cpu().numpy(), 2 * acc["S_po"]) < 1e-4
+
+
+def test_log_scales_need_opacity_block():
+    scene, cam, st = CASES[0][1](), CASES[0][2](), CASES[0][3]
+    g = B.GaussianTensors.from_scene(scene)
+    vb = PL.ViewBuffers.alloc(scene.n, cam, st)
+    PL.project_and_sort(g, vb)
+    B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib)
+    dL = torch.zeros(cam.height, cam.width, 3, device="cuda")
+    S = torch.zeros(scene.n, 6, device="cuda")
+    S_ls = torch.zeros(scene.n, 18, device="cuda")
+    ws = B.workspace(B.render_bwd_workspace_size(scene.n))
+    with pytest.raises(B.SteepGSError):
+        B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, dL, g.zeros_like(), S,
+                                    ws, accumulate=False, S_ls=S_ls)
+
+
+@pytest.mark.parametrize("name,mk_scene,mk_cam,st", CASES[:2], ids=[c[0] for c in CASES[:2]])
+def test_densify_theta7_parity(name, mk_scene, mk_cam, st):
+    scene, cam = mk_scene(), mk_cam()
+    g, _, _, _, acc = _backward7(scene, cam, st)
+    # the split reads the oracle's matrices as float32, so it is checked on its own
+    S32 = acc["S"].astype(np.float32).astype(np.float64)
+    Spo32 = acc["S_po"].astype(np.float32).astype(np.float64)
+    Sls32 = acc["S_ls"].astype(np.float32).astype(np.float64)
+    S_gpu = torch.as_tensor(_upper6(S32).astype(np.float32)).cuda().contiguous()
+    Spo_gpu = torch.as_tensor(Spo32.astype(np.float32)).cuda().contiguous()
+    Sls_gpu = torch.as_tensor(Sls32.astype(np.float32)).cuda().contiguous()
+    db = PL.DensifyBuffers.alloc(g, dim_theta=7)
+    inv_T, step = 0.5, 0.3
+    B.densify_split(g, S_gpu, inv_T, -1e-7, step, None, 0.0, db.out, db.capacity, db.n_out, db.parent, db.lam,
+                    db.v, db.split_ws, S_po=Spo_gpu, S_ls=Sls_gpu)
+    torch.cuda.synchronize()
+    S7 = oracle.S7_matrix(S32, Spo32, Sls32)
+    lam_o, v_o = oracle.eig_min_sym(S7, inv_T)
+    lam_g, v_g = db.lam.cpu().numpy(), db.v.cpu().numpy()
+    assert v_g.shape[1] == 7
+    nrm = np.linalg.norm(S7.reshape(len(S7), -1), axis=1) * inv_T
+    assert np.all(np.abs(lam_g - lam_o) <= 1e-4 * np.maximum(nrm, 1e-30))
+    ev = np.linalg.eigvalsh(S7 * inv_T)
+    gap = (ev[:, 1] - ev[:, 0]) > 1e-3 * nrm
+    assert gap.sum() > 10
+    cosang = np.abs(np.sum(v_g * v_o, 1))
+    assert np.all(1 - cosang[gap] <= 1e-4)
+    decided = np.abs(lam_o + 1e-7) > 1e-6 * np.maximum(nrm, 1e-30)
+    n = scene.n
+    n_out = int(db.n_out.item())
+    flags_g = np.zeros(n, bool)
+    flags_g[db.parent.cpu().numpy()[n:n_out]] = True
+    sp = oracle.split_po(scene, lam_o, v_o, -1e-7, step)
+    assert np.array_equal(flags_g[decided], sp["flags"][decided])
+    assert flags_g.sum() > 0
+    if np.array_equal(flags_g, sp["flags"]):
+        par = db.parent.cpu().numpy()[:n_out]
+        assert np.array_equal(par, sp["parent"])
+        ok = gap[par]                              # rows whose eigenvector is unique
+        s_max = np.exp(scene.log_scales.astype(np.float64)).max()
+        om = db.out.means[:n_out].cpu().numpy()
+        assert np.abs(om - sp["means"])[ok].max() < 1e-4 * step * s_max + 1e-6
+        ls = db.out.log_scales[:n_out].cpu().numpy()
+        assert np.abs(ls - sp["log_scales"])[ok].max() < 1e-4 * step * s_max + 1e-6
+        moved = np.abs(ls - scene.log_scales[par]).max(1) > 0
+        assert moved[n:].mean() > 0.5               # the offspring pairs move their log-scales
+        ol = db.out.opacity_logit[:n_out].cpu().numpy()
+        o_g = 1 / (1 + np.exp(-ol.astype(np.float64)))
+        o_o = 1 / (1 + np.exp(-sp["opacity_logit"]))
+        assert np.abs(o_g - o_o)[ok].max() < 1e-5
+        for f in ("quats", "sh"):
+            assert np.array_equal(getattr(db.out, f)[:n_out].cpu().numpy(), sp[f].astype(np.float32))
+
+
+def test_theta7_noalloc_equals_workspace_path():
+    scene = synth.tiny_scene(0)
+    g, S, S_po, S_ls, _ = _backward7(scene, synth.camera_identity(64, 64, 64.0), synth.Settings())
+    a = PL.DensifyBuffers.alloc(g, dim_theta=7)
+    b = PL.DensifyBuffers.alloc(g, dim_theta=7)
+    B.densify_split(g, S, 1.0, 0.0, 1.0, None, 0.0, a.out, a.capacity, a.n_out, a.parent, a.lam, a.v, a.split_ws,
+                    S_po=S_po, S_ls=S_ls)
+    B.densify_split_noalloc(g, S, 1.0, 0.0, 1.0, None, 0.0, b.out, b.capacity, b.n_out, b.parent, b.lam, b.v,
+                            S_po=S_po, S_ls=S_ls)
+    torch.cuda.synchronize()
+    assert int(a.n_out.item()) == int(b.n_out.item())
+    n2 = int(a.n_out.item())
+    assert torch.equal(a.lam, b.lam) and torch.equal(a.v, b.v)
+    for x, y in zip(a.out.tensors(), b.out.tensors()):
+        assert torch.equal(x[:n2], y[:n2])
+
+
+def test_fused_iteration_theta7_runs_and_splits():
+    """The fused iteration (project, sort, forward, loss, backward with all
+    blocks, split) over two views at dim Theta = 7: the splitting matrices
+    equal the oracle's sum over the views and the split count matches."""
+    scene = synth.cluster_scene(3, 3000, 3)
+    res = [(150, 101), (96, 64)]
+    cams = synth.ring_cameras(6.0, res)
+    st = synth.Settings()
+    tg = [synth.target_image(10 + k, h, w) for k, (w, h) in enumerate(res)]
+    g = B.GaussianTensors.from_scene(scene)
+    views = [PL.ViewBuffers.alloc(g.n, c, st) for c in cams]
+    db = PL.DensifyBuffers.alloc(g, dim_theta=7)
+    PL.fused_iteration(g, views, [torch.as_tensor(t).cuda() for t in tg], db, eps_split=-1e-7)
+    torch.cuda.synchronize()
+    acc = None
+    for c, t in zip(cams, tg):
+        r = oracle.render(scene, c, st)
+        _, dL = oracle.l1_loss_grad(r["image"], t, len(cams))
+        acc = oracle.backward(scene, c, st, dL.astype(np.float32).astype(np.float64), acc)
+    assert _rel(db.S_ls.cpu().numpy(), acc["S_ls"]) < 1e-4
+    assert _rel(db.S_po.cpu().numpy(), acc["S_po"]) < 1e-4
+    assert int(db.n_out.item()) > g.n

@@ -114,10 +114,11 @@ def test_training_loop_densifies_and_reduces_loss():
         assert bool(torch.isfinite(p).all())
 
 
-@pytest.mark.parametrize("dim_theta,lam", [(4, None), (3, 0.2), (4, 0.2)])
+@pytest.mark.parametrize("dim_theta,lam", [(4, None), (3, 0.2), (4, 0.2), (7, None)])
 def test_training_loop_variants_theta4_and_ssim(dim_theta, lam):
     """The NEXT-row variants inside Algorithm 1: splitting over (position,
-    opacity) and the SSIM term in the loss."""
+    opacity) or (position, log-scales, opacity) and the SSIM term in the
+    loss."""
     g, cams, targets, st = TR.config4_problem(n=1024, size=64)
     cfg = TR.TrainConfig(steps=300, start=100, T_split=100, log_every=20, dim_theta=dim_theta, lambda_dssim=lam)
     tr = TR.SteepGSTrainer(g, cams, targets, st, cfg)
