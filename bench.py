@@ -193,46 +193,76 @@ def run_gpu(args):
     names = ["zero_accumulators", "project", "bin_sort", "render_fwd", loss_name,
              "render_bwd_with_splitting", "densify_split"]
     NC = len(names)
+    calls = [
+        lambda s: db.zero_(grads=False, stream=s),     # S and loss; the backward overwrites the gradients
+        lambda s: B.project(g, cam, st, vb.proj, s),
+        lambda s: B.bin_sort(vb.proj, g.n, cam, st, vb.bins, vb.sort_ws, s),
+        lambda s: B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib, s),
+        lambda s: vb.loss_grad(target, 1, db.loss, args.lambda_dssim, s),
+        lambda s: B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, vb.dL,
+                                              db.grads, db.S, db.bwd_ws, s, accumulate=False, S_po=db.S_po,
+                                              S_ls=db.S_ls),
+        lambda s: B.densify_split(g, db.S, 1.0, EPS_SPLIT, 1.0, None, 0.0, db.out, db.capacity, db.n_out,
+                                  db.parent, db.lam, db.v, db.split_ws, s, S_po=db.S_po, S_ls=db.S_ls),
+    ]
 
-    def one_step(ev):
-        """One fused iteration with events around each call (on the launching stream)."""
-        ev[0].record(stream)
-        db.zero_(grads=False)               # S and loss; the backward overwrites the gradients
-        ev[1].record(stream)
-        B.project(g, cam, st, vb.proj, stream)
-        ev[2].record(stream)
-        B.bin_sort(vb.proj, g.n, cam, st, vb.bins, vb.sort_ws, stream)
-        ev[3].record(stream)
-        B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib, stream)
-        ev[4].record(stream)
-        vb.loss_grad(target, 1, db.loss, args.lambda_dssim, stream)
-        ev[5].record(stream)
-        B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, vb.dL, db.grads,
-                                    db.S, db.bwd_ws, stream, accumulate=False, S_po=db.S_po, S_ls=db.S_ls)
-        ev[6].record(stream)
-        B.densify_split(g, db.S, 1.0, EPS_SPLIT, 1.0, None, 0.0, db.out, db.capacity, db.n_out, db.parent, db.lam,
-                        db.v, db.split_ws, stream, S_po=db.S_po, S_ls=db.S_ls)
-        ev[7].record(stream)
+    # the fused iteration captured as one CUDA graph (the timed step), and each
+    # call captured as its own graph (the per-call breakdown); library launches
+    # are counted while capturing, since replays bypass the host-side counter
+    step_graph = PL.FusedIterationGraph(g, [vb], [target], db, eps_split=EPS_SPLIT,
+                                        lambda_dssim=args.lambda_dssim)
+    l1 = B.kernel_launches()
+    cap = torch.cuda.Stream(dev)
+    call_graphs = []
+    for c in calls:
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=cap):
+            c(cap)
+        call_graphs.append(cg)
+    l2 = B.kernel_launches()
+    launches_per_step = l2 - l1             # the per-call captures hold one iteration's launches
+    torch.cuda.synchronize(dev)
 
     K = args.steps
+    ev_step = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(NC + 1)] for _ in range(K)]
     sampler = ClockSampler(local)
     with sampler:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
-        launches0 = B.kernel_launches()
         wall0 = time.perf_counter()
         for k in range(K):
             flush.zero_()                     # L2 flush between iterations, outside the events
-            one_step(evs[k])
+            ev_step[k][0].record(stream)
+            step_graph.replay()
+            ev_step[k][1].record(stream)
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - wall0
-        launches = B.kernel_launches() - launches0
         if world > 1:
             dist.barrier()
+        # per-call breakdown: the same calls, one graph each, events between them
+        for k in range(K):
+            flush.zero_()
+            evs[k][0].record(stream)
+            for i, cg in enumerate(call_graphs):
+                cg.replay()
+                evs[k][i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        # the same iteration issued call by call from the host (no graph)
+        eager_ms = []
+        for k in range(max(K // 2, 3)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for c in calls:
+                c(stream)
+            e1.record(stream)
+            e1.synchronize()
+            eager_ms.append(e0.elapsed_time(e1))
 
-        # end-to-end through the public API: pinned host inputs in, loss and count out
+        # end-to-end through the public API: pinned host inputs in, the graph
+        # replayed, loss and count out
         host = [t.detach().cpu().pin_memory() for t in g.tensors()]
         host_tgt = target.detach().cpu().pin_memory()
         loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
@@ -246,8 +276,7 @@ def run_gpu(args):
             for dst, src in zip(g.tensors(), host):
                 dst.copy_(src, non_blocking=True)
             target.copy_(host_tgt, non_blocking=True)
-            PL.fused_iteration(g, [vb], [target], db, eps_split=EPS_SPLIT, stream=stream, check_capacity=False,
-                               lambda_dssim=args.lambda_dssim)
+            step_graph.replay()
             loss_host.copy_(db.loss, non_blocking=True)
             nout_host.copy_(db.n_out, non_blocking=True)
             e1.record(stream)
@@ -256,7 +285,7 @@ def run_gpu(args):
     clocks = sampler.summary()
 
     per_call = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(NC)] for k in range(K)])
-    step_ms = per_call.sum(1)
+    step_ms = np.array([ev_step[k][0].elapsed_time(ev_step[k][1]) for k in range(K)])
     ms_iter = float(step_ms.mean())
     e2e = float(np.mean(e2e_ms))
     ms_iter, e2e = max_over_ranks([ms_iter, e2e], world, dev)
@@ -323,12 +352,15 @@ def run_gpu(args):
                                                                  f"{args.lambda_dssim:g} (1-SSIM)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between iterations, outside the timed events"},
+        "timing": "each step = one replay of the fused iteration captured as a CUDA graph; per_call_ms from "
+                  "the calls captured one graph each, events between them",
         "per_call_ms": {nm: round(float(v), 4) for nm, v in zip(names, call_ms)},
+        "eager_ms_per_step": round(float(np.mean(eager_ms)), 4),
         "wall_ms_per_step": round(wall * 1e3 / K, 4),
         "roofline": roofline, "hbm_roofline": hbm,
         "e2e": {"value": round(job_value(e2e, world), 4), "unit": "ms/iter", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": 8},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(launches_per_step * K),
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

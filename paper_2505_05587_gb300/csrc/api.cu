@@ -248,7 +248,7 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
     float* g2d_hi = S_ls_accum ? g2d + 16 * (size_t)g->n : nullptr;
     CamDev cd = make_cam(*cam, *st);
     SetDev sd = make_set(*st);
-    cudaError_t e = cudaMemsetAsync(g2d, 0, sizeof(float) * (g2d_hi ? 32 : 16) * (size_t)g->n, s);
+    cudaError_t e = launch_zero_reached_rows(proj->tiles_touched, g->n, g2d, g2d_hi, s);
     if (e == cudaSuccess)
         e = launch_render_bwd(*proj, *bins, cd, sd, final_T, n_contrib, dL_dimage, g2d, g2d_hi, s);
     if (e == cudaSuccess)

@@ -128,6 +128,9 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
 cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
                               const SetDev& st, float* image, float* final_T, uint32_t* n_contrib,
                               cudaStream_t stream);
+// Zeroes the 16-float accumulator rows (and the higher-moment rows when
+// g2d_hi is not null) of the Gaussians with tiles_touched > 0.
+cudaError_t launch_zero_reached_rows(const uint32_t* tiles, int n, float* g2d, float* g2d_hi, cudaStream_t stream);
 cudaError_t launch_render_bwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
                               const SetDev& st, const float* final_T, const uint32_t* n_contrib,
                               const float* dL_dimage, float* g2d, float* g2d_hi, cudaStream_t stream);

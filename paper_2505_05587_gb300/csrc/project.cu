@@ -562,7 +562,7 @@ __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, fl
 // MULTI = false is the single-view case: no view loop, and the SH gradient
 // increments overwrite the staged coefficients once they have been used.
 template <int DEG, bool MULTI, bool PO, bool LS>
-__global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 5)) project_bwd_kernel(
+__global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 6)) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ sh, int n, ViewsDev vd, const float4* __restrict__ conic_opac,
     const uint32_t* __restrict__ tiles, const float* __restrict__ g2d, const float* __restrict__ g2d_hi,
@@ -583,27 +583,64 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 5)) pr
     float* wc = s_coef[warp];
     float* wi = MULTI ? s_inc[warp] : s_coef[warp];
 
-    // which views touched this Gaussian
-    uint32_t vmask = 0u;
+    // views whose projection reached a tile (tiles_touched > 0)
+    uint32_t tmask = 0u;
     const int nv = MULTI ? vd.nv : 1;
-    if (i < n) {
-        for (int v = 0; v < nv; ++v) {
-            const long long row = (long long)v * n + i;
-            if (tiles[row] == 0u) continue;
-            const float4* r4 = reinterpret_cast<const float4*>(g2d + (size_t)row * 16);
-            const float4 a = r4[0], b = r4[1], c = r4[2];
-            if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f || b.x != 0.f || b.y != 0.f ||
-                b.z != 0.f || b.w != 0.f || c.x != 0.f)
-                vmask |= 1u << v;
+    if (i < n)
+        for (int v = 0; v < nv; ++v)
+            if (tiles[(long long)v * n + i] != 0u) tmask |= 1u << v;
+    const uint32_t vis = __ballot_sync(0xffffffffu, tmask != 0u);
+    if (vis == 0u && accumulate) return;             // nothing in this warp reached a tile
+    const int rows = min(32, n - base);
+    if (vis == 0u) {                                 // unreached rows: zero gradients, nothing staged
+        for (int f = lane; f < 3 * rows; f += 32) {
+            g_means[3 * (size_t)base + f] = 0.0f;
+            g_ls[3 * (size_t)base + f] = 0.0f;
         }
+        if (lane < rows) {
+            reinterpret_cast<float4*>(g_quats)[base + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+            g_logit[base + lane] = 0.0f;
+        }
+        if ((K3 & 3) == 0 && (reinterpret_cast<uintptr_t>(g_sh) & 15u) == 0) {
+            float4* o4 = reinterpret_cast<float4*>(g_sh + (size_t)base * K3);
+            for (int f = lane; f < rows * K3 / 4; f += 32) o4[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            for (int f = lane; f < rows * K3; f += 32) g_sh[(size_t)base * K3 + f] = 0.0f;
+        }
+        return;
+    }
+    // stage the SH coefficient rows of the reached Gaussians with asynchronous
+    // 4-byte copies (all in flight at once, no registers), while the
+    // accumulator rows and the parameters load; clear increments
+    {
+        const int nf = rows * K3;
+        for (int f = lane; f < nf; f += 32) {
+            const int r = f / K3;
+            const int o = r * ROW + (f - r * K3);
+            if ((vis >> r) & 1u) {
+                const unsigned dst = (unsigned)__cvta_generic_to_shared(wc + o);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(sh + (size_t)base * K3 + f)
+                             : "memory");
+            }
+            if constexpr (MULTI) wi[o] = 0.0f;
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    // which views composited this Gaussian somewhere
+    uint32_t vmask = 0u;
+    for (int v = 0; v < nv; ++v) {
+        if (!((tmask >> v) & 1u)) continue;
+        const long long row = (long long)v * n + i;
+        const float4* r4 = reinterpret_cast<const float4*>(g2d + (size_t)row * 16);
+        const float4 a = r4[0], b = r4[1], c = r4[2];
+        if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f || b.x != 0.f || b.y != 0.f || b.z != 0.f ||
+            b.w != 0.f || c.x != 0.f)
+            vmask |= 1u << v;
     }
     const bool work = vmask != 0u;
     const uint32_t need = __ballot_sync(0xffffffffu, work);
-    if (need == 0u && accumulate) return;            // nothing in this warp touched any pixel
-    const int rows = min(32, n - base);
 
-    // parameters of this lane's Gaussian, loaded before the SH staging so that
-    // their latency overlaps it
+    // parameters of this lane's Gaussian (their loads overlap the SH copies)
     float p0 = 0.f, p1 = 0.f, p2 = 0.f, ls0 = 0.f, ls1 = 0.f, ls2 = 0.f;
     float4 q4 = make_float4(1.f, 0.f, 0.f, 0.f);
     if (work) {
@@ -612,31 +649,7 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 5)) pr
         ls0 = log_scales[3 * i]; ls1 = log_scales[3 * i + 1]; ls2 = log_scales[3 * i + 2];
     }
 
-    // stage the SH coefficient rows (coalesced; zeros where unused), in
-    // batches of independent loads; clear increments
-    {
-        constexpr int UNR = 8;
-        const int nf = rows * K3;
-        for (int f0 = 0; f0 < nf; f0 += 32 * UNR) {
-            float vals[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const int f = f0 + u * 32 + lane;
-                const int r = f / K3;
-                vals[u] = (f < nf && ((need >> r) & 1u)) ? sh[(size_t)base * K3 + f] : 0.0f;
-            }
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const int f = f0 + u * 32 + lane;
-                if (f < nf) {
-                    const int r = f / K3;
-                    const int o = r * ROW + (f - r * K3);
-                    wc[o] = vals[u];
-                    if constexpr (MULTI) wi[o] = 0.0f;
-                }
-            }
-        }
-    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncwarp();
 
     float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, gl0 = 0.f, gl1 = 0.f, gl2 = 0.f, glog = 0.f;
@@ -748,7 +761,7 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 5)) pr
     // SH gradient rows (coalesced): added, or written (zeros for untouched rows)
     for (int f = lane; f < rows * K3; f += 32) {
         const int r = f / K3;
-        const float val = wi[r * ROW + (f - r * K3)];
+        const float val = ((need >> r) & 1u) ? wi[r * ROW + (f - r * K3)] : 0.0f;
         if (!accumulate)
             g_sh[(size_t)base * K3 + f] = val;
         else if ((need >> r) & 1u)

@@ -323,11 +323,38 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
     __syncthreads();        // shared memory is reused by the next tile
 }
 
+// Clears the accumulator rows (and the higher-moment rows when given) of the
+// Gaussians whose projection reached a tile: the only rows the backward adds
+// to and the projection adjoint reads.
+__global__ void __launch_bounds__(256) zero_reached_rows_kernel(const uint32_t* __restrict__ tiles, int n,
+                                                                float4* __restrict__ g2d,
+                                                                float4* __restrict__ g2d_hi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || tiles[i] == 0u) return;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kG2dStride / 4; ++k) g2d[(size_t)i * (kG2dStride / 4) + k] = z;
+    if (g2d_hi) {
+#pragma unroll
+        for (int k = 0; k < kG2dStride / 4; ++k) g2d_hi[(size_t)i * (kG2dStride / 4) + k] = z;
+    }
+}
+
+cudaError_t launch_zero_reached_rows(const uint32_t* tiles, int n, float* g2d, float* g2d_hi, cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    zero_reached_rows_kernel<<<(n + 255) / 256, 256, 0, stream>>>(tiles, n, reinterpret_cast<float4*>(g2d),
+                                                                  reinterpret_cast<float4*>(g2d_hi));
+    note_launch();
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
-// Single view: one CTA per tile.
+// Single view: one CTA per tile.  The forward is bounded to 48 resident warps
+// per SM (40 registers): its per-pixel chain is latency-bound and gains from
+// the extra warps more than it loses to the two spilled words.
 // ---------------------------------------------------------------------------
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) render_fwd_kernel(
+__global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) render_fwd_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
     float* __restrict__ image, float* __restrict__ final_T, uint32_t* __restrict__ n_contrib) {

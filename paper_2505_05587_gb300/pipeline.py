@@ -11,6 +11,11 @@ calls on one stream:
 The instance count M is data dependent.  Buffers are sized with headroom; when
 a view needs more, the pipeline reads M back once, grows the buffers and
 re-runs the sort (never silently truncates).
+
+FusedIterationGraph captures one fused iteration as a CUDA graph: the ~35
+launches of an iteration then replay without host work between them (every
+library call is capture-safe: no allocation, no synchronisation, no host
+read-back inside a call).
 """
 from __future__ import annotations
 
@@ -19,6 +24,16 @@ from dataclasses import dataclass, field
 import torch
 
 from . import binding as B
+
+
+def as_stream(stream) -> torch.cuda.Stream:
+    """A torch stream for the `stream` argument of the calls: None is the
+    current stream, an int a raw cudaStream_t."""
+    if stream is None:
+        return torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return stream
+    return torch.cuda.ExternalStream(int(stream))
 
 
 @dataclass
@@ -73,6 +88,7 @@ def project_and_sort(g: B.GaussianTensors, vb: ViewBuffers, stream=None, check_c
     B.bin_sort(vb.proj, g.n, vb.cam, vb.st, vb.bins, vb.sort_ws, stream)
     if not check_capacity:
         return None
+    as_stream(stream).synchronize()          # the count is read on the host after the sort finishes
     M = B.check_count(int(vb.bins.count.item()))
     if M > vb.bins.capacity:
         vb.grow(int(M * 1.25) + 1024)
@@ -122,17 +138,19 @@ class DensifyBuffers:
                               torch.zeros(n, 3, device=dev) if dim_theta > 3 else None,
                               torch.zeros(n, 18, device=dev) if dim_theta == 7 else None)
 
-    def zero_(self, grads: bool = True):
-        """Resets the accumulators; the gradients need no reset when the first
-        backward call of an iteration overwrites them."""
-        if grads:
-            for t in self.grads.tensors():
-                t.zero_()
-        self.S.zero_()
-        for t in (self.S_po, self.S_ls):
-            if t is not None:
-                t.zero_()
-        self.loss.zero_()
+    def zero_(self, grads: bool = True, stream=None):
+        """Resets the accumulators (on `stream`, default the current one); the
+        gradients need no reset when the first backward call of an iteration
+        overwrites them."""
+        with torch.cuda.stream(as_stream(stream)):
+            if grads:
+                for t in self.grads.tensors():
+                    t.zero_()
+            self.S.zero_()
+            for t in (self.S_po, self.S_ls):
+                if t is not None:
+                    t.zero_()
+            self.loss.zero_()
 
 
 def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: list[torch.Tensor],
@@ -142,7 +160,7 @@ def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: lis
     """One fused fwd+bwd+splitting iteration over the views (Algorithm 1 with
     the split step taken right after accumulation).  lambda_dssim set: the loss
     has the SSIM term, (1 - lambda) L1 + lambda (1 - SSIM)."""
-    db.zero_(grads=False)
+    db.zero_(grads=False, stream=stream)
     V = len(views)
     for k, (vb, tgt) in enumerate(zip(views, targets)):
         project_and_sort(g, vb, stream, check_capacity)
@@ -155,3 +173,38 @@ def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: lis
     B.densify_split(g, db.S, 1.0 / T_split, eps_split, step_scale, grad_norm, eps_grad, db.out, db.capacity,
                     db.n_out, db.parent, db.lam, db.v, db.split_ws, stream, max_splits=max_splits, S_po=db.S_po,
                     S_ls=db.S_ls)
+
+
+class FusedIterationGraph:
+    """fused_iteration captured once as a CUDA graph.
+
+    The scene size, the views, the buffers and the scalar arguments are fixed
+    at capture; the VALUES in the parameter, target and gradient buffers may
+    change between replays (the graph reads and writes the same device
+    memory).  One eager iteration first sizes the instance buffers.  When the
+    parameters move, a view may need more instances than its buffers hold:
+    the sort then writes nothing out of bounds but the iteration is not valid,
+    so replay(check=True) reads the counts back and raises; grow the buffers
+    (an eager fused_iteration does) and capture again."""
+
+    def __init__(self, g: B.GaussianTensors, views: list[ViewBuffers], targets: list[torch.Tensor],
+                 db: DensifyBuffers, **kw):
+        kw.pop("stream", None)
+        kw.pop("check_capacity", None)
+        self.views = views
+        fused_iteration(g, views, targets, db, check_capacity=True, **kw)
+        torch.cuda.synchronize()
+        self.stream = torch.cuda.Stream(device=g.means.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            fused_iteration(g, views, targets, db, stream=self.stream, check_capacity=False, **kw)
+
+    def replay(self, check: bool = False):
+        """Launches the captured iteration on the current stream."""
+        self.graph.replay()
+        if check:
+            for vb in self.views:
+                M = B.check_count(int(vb.bins.count.item()))
+                if M > vb.bins.capacity:
+                    raise RuntimeError(f"a view needs {M} instances, its buffers hold {vb.bins.capacity}: "
+                                       "run fused_iteration eagerly to grow them and capture again")
