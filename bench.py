@@ -56,7 +56,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # DRAM traffic of one render_bwd_kernel<16,16> launch on this workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # rasteriser source it was taken from (first 16 hex digits of its SHA-256).
-RENDER_BWD_TRAFFIC = {"bytes": 104_611_328 + 9_628_672, "render_cu_sha256": "a4719d80a5a175e8",
+RENDER_BWD_TRAFFIC = {"bytes": 104_391_936 + 9_073_920, "render_cu_sha256": "f818065d072ce9a1",
                       "profile": "profiles/render_bwd_scene_1M_1237x822.md"}
 
 
