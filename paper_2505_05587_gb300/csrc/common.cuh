@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "steepgs.h"
 
 namespace sgs {
@@ -105,6 +107,29 @@ __device__ Stage integer_stage(const float* __restrict__ means, const float* __r
 // Host helpers (defined in api.cu)
 // Counts kernel launches issued by the library (for measurement reports).
 void note_launch(int k = 1);
+
+// Programmatic dependent launch: the kernel may be scheduled while the
+// previous kernel on the stream drains; it waits for that kernel's completion
+// (and memory) in pdl_wait_and_trigger before touching any data.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+__device__ __forceinline__ void pdl_wait_and_trigger() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" :::);
+}
 // Keeps `e` for sgs_get_last_cuda_error() and returns SGS_ERR_CUDA.
 int record_cuda_error(cudaError_t e);
 CamDev make_cam(const sgs_camera& c, const sgs_settings& s);

@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(256) eig_flag_kernel(const float* __restrict__
                                                        float eps_split, const float* __restrict__ grad_norm,
                                                        float eps_grad, float* __restrict__ lam_out,
                                                        float* __restrict__ v_out, uint32_t* __restrict__ flags) {
+    pdl_wait_and_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float s6[6];
@@ -193,8 +194,10 @@ __global__ void __launch_bounds__(256) eig_flag_kernel(const float* __restrict__
 // Minimum eigenpair of a small symmetric matrix (the splitting matrix over
 // theta = (p, o), N = 4, or theta = (p, l, o), N = 7) by cyclic Jacobi
 // rotations (Jacobi's method; Golub & Van Loan, Matrix Computations, Sec.
-// 8.5).  Only the upper triangle is held (constant indices after unrolling, so
-// it stays in registers); each rotation zeroes one off-diagonal pair exactly.
+// 8.5) in the parallel round-robin order (each round rotates disjoint pairs,
+// whose angles are independent: instruction-level parallelism for one thread).
+// Only the upper triangle is held (constant indices after unrolling, so it
+// stays in registers); each rotation zeroes one off-diagonal pair exactly.
 // Sweeps run until the off-diagonal mass is below float32 resolution of
 // ||A||_F (at most 12), the eigenvector is the column of the accumulated
 // rotations at the smallest diagonal entry, lambda the Rayleigh quotient of
@@ -210,9 +213,23 @@ __host__ __device__ constexpr int upper_index(int r, int c, int n) {
     return r <= c ? r * n - r * (r - 1) / 2 + (c - r) : c * n - c * (c - 1) / 2 + (r - c);
 }
 
+// Round-robin (circle method) pairing of M indices, M even: in round r
+// (0 <= r < M - 1) index 0 meets 1 + r and, for k = 1 .. M/2 - 1, index
+// 1 + (r + k) mod (M - 1) meets 1 + (r + M - 1 - k) mod (M - 1).  The pairs of
+// a round are disjoint and the M - 1 rounds cover every pair once.
+__host__ __device__ constexpr int rr_a(int r, int k, int M) { return k == 0 ? 0 : 1 + (r + k) % (M - 1); }
+__host__ __device__ constexpr int rr_b(int r, int k, int M) { return k == 0 ? 1 + r : 1 + (r + M - 1 - k) % (M - 1); }
+__host__ __device__ constexpr int rr_low(int r, int k, int M) {
+    return rr_a(r, k, M) < rr_b(r, k, M) ? rr_a(r, k, M) : rr_b(r, k, M);
+}
+__host__ __device__ constexpr int rr_high(int r, int k, int M) {
+    return rr_a(r, k, M) < rr_b(r, k, M) ? rr_b(r, k, M) : rr_a(r, k, M);
+}
+
 template <int N, class Entry>
 __device__ __forceinline__ EigN<N> jacobi_min(Entry entry) {
     constexpr int NU = N * (N + 1) / 2;
+    constexpr int M = N + (N & 1);
     float u[NU];
     float total = 0.0f;
 #pragma unroll
@@ -236,33 +253,46 @@ __device__ __forceinline__ EigN<N> jacobi_min(Entry entry) {
 #pragma unroll
             for (int q = p + 1; q < N; ++q) off += u[upper_index(p, q, N)] * u[upper_index(p, q, N)];
         if (!(2.0f * off > 1e-14f * total)) break;
+        // one sweep = M - 1 rounds of M / 2 disjoint pairs (round-robin order
+        // over M = N rounded up to even; pairs with the padding index skipped)
 #pragma unroll
-        for (int p = 0; p < N - 1; ++p)
+        for (int r = 0; r < M - 1; ++r) {
+            float c[M / 2], s[M / 2], t[M / 2], a[M / 2];
 #pragma unroll
-            for (int q = p + 1; q < N; ++q) {
+            for (int k = 0; k < M / 2; ++k) {           // the round's angles, independent of each other
+                const int p = rr_low(r, k, M), q = rr_high(r, k, M);
+                if (q >= N) continue;
                 const float apq = u[upper_index(p, q, N)];
-                if (apq == 0.0f) continue;
                 // t = tan(phi), the smaller root of t^2 + 2 theta t - 1 = 0
                 const float theta = (u[upper_index(q, q, N)] - u[upper_index(p, p, N)]) / (2.0f * apq);
-                const float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
-                const float c = rsqrtf(t * t + 1.0f), s = t * c;
+                const float tk = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+                t[k] = apq == 0.0f ? 0.0f : tk;
+                c[k] = rsqrtf(t[k] * t[k] + 1.0f);
+                s[k] = t[k] * c[k];
+                a[k] = apq;
+            }
 #pragma unroll
-                for (int k = 0; k < N; ++k) {
-                    if (k == p || k == q) continue;
-                    const float akp = u[upper_index(k, p, N)], akq = u[upper_index(k, q, N)];
-                    u[upper_index(k, p, N)] = c * akp - s * akq;
-                    u[upper_index(k, q, N)] = s * akp + c * akq;
+            for (int k = 0; k < M / 2; ++k) {           // disjoint rotations commute
+                const int p = rr_low(r, k, M), q = rr_high(r, k, M);
+                if (q >= N) continue;
+#pragma unroll
+                for (int m = 0; m < N; ++m) {
+                    if (m == p || m == q) continue;
+                    const float amp = u[upper_index(m, p, N)], amq = u[upper_index(m, q, N)];
+                    u[upper_index(m, p, N)] = c[k] * amp - s[k] * amq;
+                    u[upper_index(m, q, N)] = s[k] * amp + c[k] * amq;
                 }
-                u[upper_index(p, p, N)] -= t * apq;
-                u[upper_index(q, q, N)] += t * apq;
+                u[upper_index(p, p, N)] -= t[k] * a[k];
+                u[upper_index(q, q, N)] += t[k] * a[k];
                 u[upper_index(p, q, N)] = 0.0f;
 #pragma unroll
-                for (int k = 0; k < N; ++k) {
-                    const float vkp = V[k][p], vkq = V[k][q];
-                    V[k][p] = c * vkp - s * vkq;
-                    V[k][q] = s * vkp + c * vkq;
+                for (int m = 0; m < N; ++m) {
+                    const float vmp = V[m][p], vmq = V[m][q];
+                    V[m][p] = c[k] * vmp - s[k] * vmq;
+                    V[m][q] = s[k] * vmp + c[k] * vmq;
                 }
             }
+        }
     }
     // column of the smallest diagonal entry (first on ties), selected with
     // constant indices so that u and V stay in registers
@@ -324,6 +354,7 @@ __global__ void __launch_bounds__(256) eig_theta_flag_kernel(const float* __rest
                                                              float eps_split, const float* __restrict__ grad_norm,
                                                              float eps_grad, float* __restrict__ lam_out,
                                                              float* __restrict__ v_out, uint32_t* __restrict__ flags) {
+    pdl_wait_and_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float s6[6], spo[3], sls[N == 7 ? 18 : 1];
@@ -365,6 +396,7 @@ __device__ __forceinline__ uint32_t order_key(float x) {
 }
 
 __global__ void select_init_kernel(const uint32_t* __restrict__ total, int64_t K, SelectState* st) {
+    pdl_wait_and_trigger();
     if (threadIdx.x == 0) {
         st->active = (int64_t)(*total) > K ? 1u : 0u;
         st->prefix = 0u;
@@ -376,6 +408,7 @@ __global__ void select_init_kernel(const uint32_t* __restrict__ total, int64_t K
 __global__ void __launch_bounds__(256) select_hist_kernel(const float* __restrict__ lam,
                                                           const uint32_t* __restrict__ flags, int n, int shift,
                                                           SelectState* st) {
+    pdl_wait_and_trigger();
     __shared__ uint32_t h[256];
     if (!st->active) return;
     h[threadIdx.x] = 0u;
@@ -392,6 +425,7 @@ __global__ void __launch_bounds__(256) select_hist_kernel(const float* __restric
 }
 
 __global__ void select_pick_kernel(int shift, SelectState* st) {
+    pdl_wait_and_trigger();
     if (!st->active || threadIdx.x != 0) return;
     uint32_t before = 0u;
     int b = 0;
@@ -406,6 +440,7 @@ __global__ void select_pick_kernel(int shift, SelectState* st) {
 
 __global__ void select_ties_kernel(const float* __restrict__ lam, const uint32_t* __restrict__ flags, int n,
                                    const SelectState* st, uint32_t* __restrict__ tie) {
+    pdl_wait_and_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     tie[i] = (st->active && flags[i] && order_key(lam[i]) == st->prefix) ? 1u : 0u;
@@ -413,6 +448,7 @@ __global__ void select_ties_kernel(const float* __restrict__ lam, const uint32_t
 
 __global__ void select_apply_kernel(const float* __restrict__ lam, uint32_t* __restrict__ flags, int n,
                                     const SelectState* st, const uint32_t* __restrict__ tie_rank) {
+    pdl_wait_and_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !st->active || !flags[i]) return;
     const uint32_t k = order_key(lam[i]);
@@ -420,6 +456,7 @@ __global__ void select_apply_kernel(const float* __restrict__ lam, uint32_t* __r
 }
 
 __global__ void n_out_kernel(const uint32_t* __restrict__ total, int n, int32_t* __restrict__ d_n_out) {
+    pdl_wait_and_trigger();
     *d_n_out = n + (int32_t)(*total);
 }
 
@@ -442,6 +479,7 @@ __global__ void __launch_bounds__(256) split_fields_kernel(
     const uint32_t* __restrict__ excl, float step_scale, int64_t cap, float* __restrict__ o_means,
     float* __restrict__ o_ls, float* __restrict__ o_quats, float* __restrict__ o_logit,
     int32_t* __restrict__ parent) {
+    pdl_wait_and_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const bool f = flags[i] != 0u;
@@ -489,6 +527,7 @@ __global__ void __launch_bounds__(256) split_sh_kernel(const float* __restrict__
                                                        const uint32_t* __restrict__ flags,
                                                        const uint32_t* __restrict__ excl, int64_t cap,
                                                        float* __restrict__ o_sh) {
+    pdl_wait_and_trigger();
     using V = typename std::conditional<VEC == 4, float4, float>::type;
     const int64_t total = (int64_t)n * U;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -539,42 +578,43 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
     if (n == 0) return cudaMemsetAsync(d_n_out, 0, sizeof(int32_t), stream);
     const int nb = (n + 255) / 256;
     if (S_po && S_ls)
-        eig_theta_flag_kernel<7><<<nb, 256, 0, stream>>>(S, S_po, S_ls, n, inv_T, eps_split, grad_norm, eps_grad,
-                                                         lam, v, flags);
+        (void)launch_pdl(eig_theta_flag_kernel<7>, dim3(nb), dim3(256), 0, stream, S, S_po, S_ls, n, inv_T, eps_split,
+                         grad_norm, eps_grad, lam, v, flags);
     else if (S_po)
-        eig_theta_flag_kernel<4><<<nb, 256, 0, stream>>>(S, S_po, nullptr, n, inv_T, eps_split, grad_norm, eps_grad,
-                                                         lam, v, flags);
+        (void)launch_pdl(eig_theta_flag_kernel<4>, dim3(nb), dim3(256), 0, stream, S, S_po, nullptr, n, inv_T,
+                         eps_split, grad_norm, eps_grad, lam, v, flags);
     else
-        eig_flag_kernel<<<nb, 256, 0, stream>>>(S, n, inv_T, eps_split, grad_norm, eps_grad, lam, v, flags);
+        (void)launch_pdl(eig_flag_kernel, dim3(nb), dim3(256), 0, stream, S, n, inv_T, eps_split, grad_norm, eps_grad,
+                         lam, v, flags);
     note_launch();
     cudaError_t e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
     if (e != cudaSuccess) return e;
     if (max_splits > 0) {
-        select_init_kernel<<<1, 256, 0, stream>>>(total, max_splits, sel);
+        (void)launch_pdl(select_init_kernel, dim3(1), dim3(256), 0, stream, total, max_splits, sel);
         note_launch();
         const int hb = nb < 152 * 4 ? nb : 152 * 4;
         for (int shift = 24; shift >= 0; shift -= 8) {
-            select_hist_kernel<<<hb, 256, 0, stream>>>(lam, flags, n, shift, sel);
+            (void)launch_pdl(select_hist_kernel, dim3(hb), dim3(256), 0, stream, lam, flags, n, shift, sel);
             note_launch();
-            select_pick_kernel<<<1, 32, 0, stream>>>(shift, sel);
+            (void)launch_pdl(select_pick_kernel, dim3(1), dim3(32), 0, stream, shift, sel);
             note_launch();
         }
-        select_ties_kernel<<<nb, 256, 0, stream>>>(lam, flags, n, sel, tie);
+        (void)launch_pdl(select_ties_kernel, dim3(nb), dim3(256), 0, stream, lam, flags, n, sel, tie);
         note_launch();
         e = launch_exclusive_scan(tie, excl, nullptr, n, nullptr, scan_tmp, stream);
         if (e != cudaSuccess) return e;
-        select_apply_kernel<<<nb, 256, 0, stream>>>(lam, flags, n, sel, excl);
+        (void)launch_pdl(select_apply_kernel, dim3(nb), dim3(256), 0, stream, lam, flags, n, sel, excl);
         note_launch();
         e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
         if (e != cudaSuccess) return e;
     }
-    n_out_kernel<<<1, 1, 0, stream>>>(total, n, d_n_out);
+    (void)launch_pdl(n_out_kernel, dim3(1), dim3(1), 0, stream, total, n, d_n_out);
     note_launch();
     const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;
     auto fields = S_po ? (S_ls ? split_fields_kernel<7> : split_fields_kernel<4>) : split_fields_kernel<3>;
-    fields<<<nb, 256, 0, stream>>>(in.means, in.log_scales, in.quats, in.opacity_logit, n, v, flags, excl,
-                                   step_scale, capacity, out.means, out.log_scales, out.quats, out.opacity_logit,
-                                   parent);
+    (void)launch_pdl(fields, dim3(nb), dim3(256), 0, stream, in.means, in.log_scales, in.quats, in.opacity_logit, n,
+                     v, flags, excl, step_scale, capacity, out.means, out.log_scales, out.quats, out.opacity_logit,
+                     parent);
     note_launch();
     const bool vec4 = K3 % 4 == 0 && (reinterpret_cast<uintptr_t>(in.sh) % 16) == 0 &&
                       (reinterpret_cast<uintptr_t>(out.sh) % 16) == 0;
@@ -582,9 +622,11 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
     const int64_t units = (int64_t)n * U;
     const int sb = (int)std::min<int64_t>((units + 255) / 256, 152 * 16);
     if (vec4)
-        split_sh_kernel<4><<<sb, 256, 0, stream>>>(in.sh, n, U, flags, excl, capacity, out.sh);
+        (void)launch_pdl(split_sh_kernel<4>, dim3(sb), dim3(256), 0, stream, in.sh, n, U, flags, excl, capacity,
+                         out.sh);
     else
-        split_sh_kernel<1><<<sb, 256, 0, stream>>>(in.sh, n, U, flags, excl, capacity, out.sh);
+        (void)launch_pdl(split_sh_kernel<1>, dim3(sb), dim3(256), 0, stream, in.sh, n, U, flags, excl, capacity,
+                         out.sh);
     note_launch();
     return cudaGetLastError();
 }
@@ -598,6 +640,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, const 
                                                    float* __restrict__ m, float* __restrict__ v, int64_t count,
                                                    float lr, float b1, float b2, float eps, float bc1, float bc2,
                                                    float* __restrict__ G) {
+    pdl_wait_and_trigger();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
          k += (int64_t)gridDim.x * blockDim.x) {
         const float gk = g[k];
@@ -616,7 +659,8 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t co
     const float bc1 = 1.0f - powf(b1, (float)step), bc2 = 1.0f - powf(b2, (float)step);
     int64_t blocks = (count + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    adam_kernel<<<(int)blocks, 256, 0, stream>>>(p, g, m, v, count, lr, b1, b2, eps, bc1, bc2, G);
+    (void)launch_pdl(adam_kernel, dim3((int)blocks), dim3(256), 0, stream, p, g, m, v, count, lr, b1, b2, eps, bc1,
+                     bc2, G);
     note_launch();
     return cudaGetLastError();
 }
@@ -627,6 +671,7 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t co
 __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ image, const float* __restrict__ target,
                                                  int64_t count, float norm, float* __restrict__ dL,
                                                  float* __restrict__ loss) {
+    pdl_wait_and_trigger();
     __shared__ float s_part[8];
     float acc = 0.0f;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
@@ -650,6 +695,7 @@ __global__ void __launch_bounds__(256) l1_kernel(const float* __restrict__ image
 __global__ void __launch_bounds__(256) l1_views_kernel(const float* __restrict__ image,
                                                        const float* __restrict__ target, ViewsDev vd,
                                                        float* __restrict__ dL, float* __restrict__ loss) {
+    pdl_wait_and_trigger();
     __shared__ float s_part[8];
     float acc = 0.0f;
     const long long count = 3 * vd.P_total;
@@ -678,7 +724,7 @@ cudaError_t launch_l1_views(const float* image, const float* target, const Views
     if (count == 0) return cudaSuccess;
     long long blocks = (count + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    l1_views_kernel<<<(int)blocks, 256, 0, stream>>>(image, target, vd, dL, loss);
+    (void)launch_pdl(l1_views_kernel, dim3((int)blocks), dim3(256), 0, stream, image, target, vd, dL, loss);
     note_launch();
     return cudaGetLastError();
 }
@@ -690,7 +736,7 @@ cudaError_t launch_l1(const float* image, const float* target, int H, int W, int
     const float norm = (float)(1.0 / (3.0 * (double)H * (double)W * (double)n_views));
     int64_t blocks = (count + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    l1_kernel<<<(int)blocks, 256, 0, stream>>>(image, target, count, norm, dL, loss);
+    (void)launch_pdl(l1_kernel, dim3((int)blocks), dim3(256), 0, stream, image, target, count, norm, dL, loss);
     note_launch();
     return cudaGetLastError();
 }

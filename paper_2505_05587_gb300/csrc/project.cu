@@ -281,6 +281,7 @@ template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(ScenesDev sc, ViewsDev vd, SetDev st,
     float4* __restrict__ xy, float4* __restrict__ conic_opac, float4* __restrict__ rgb_out,
     float* __restrict__ depth, short4* __restrict__ rect, uint32_t* __restrict__ tiles) {
+    pdl_wait_and_trigger();
     const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= vd.row_off[vd.nv]) return;
     const int v = view_of_row(vd, row);
@@ -342,10 +343,9 @@ cudaError_t launch_project(const ScenesDev& sc, int sh_degree, const ViewsDev& v
     auto kern = sh_degree == 0 ? project_kernel<0>
               : sh_degree == 1 ? project_kernel<1>
               : sh_degree == 2 ? project_kernel<2> : project_kernel<3>;
-    kern<<<blocks, 256, 0, stream>>>(
-        sc, vd, st, reinterpret_cast<float4*>(out.xy), reinterpret_cast<float4*>(out.conic_opac),
-        reinterpret_cast<float4*>(out.rgb), out.depth, reinterpret_cast<short4*>(out.rect),
-        out.tiles_touched);
+    (void)launch_pdl(kern, dim3(blocks), dim3(256), 0, stream, sc, vd, st, reinterpret_cast<float4*>(out.xy),
+                     reinterpret_cast<float4*>(out.conic_opac), reinterpret_cast<float4*>(out.rgb), out.depth,
+                     reinterpret_cast<short4*>(out.rect), out.tiles_touched);
     note_launch();
     return cudaGetLastError();
 }
@@ -475,7 +475,8 @@ __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, fl
 #pragma unroll
             for (int l = k; l < 3; ++l) {
                 const float u0 = bk0[k], u1 = bk1[k], v0 = bk0[l], v1 = bk1[l];
-                const float quart = u0 * u0 * v0 * v0 * F0 + (2.0f * u0 * u0 * v0 * v1 + 2.0f * u0 * u1 * v0 * v0) * F1 +
+                const float quart = u0 * u0 * v0 * v0 * F0 +
+                                    (2.0f * u0 * u0 * v0 * v1 + 2.0f * u0 * u1 * v0 * v0) * F1 +
                                     (u0 * u0 * v1 * v1 + 4.0f * u0 * u1 * v0 * v1 + u1 * u1 * v0 * v0) * F2 +
                                     (2.0f * u0 * u1 * v1 * v1 + 2.0f * u1 * u1 * v0 * v1) * F3 + u1 * u1 * v1 * v1 * F4;
                 const float quv = quad(u0, u1, v0, v1);
@@ -570,6 +571,7 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 6)) pr
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_logit, float* __restrict__ g_sh, float* __restrict__ S_accum,
     float* __restrict__ S_po_accum, float* __restrict__ S_ls_accum) {
+    pdl_wait_and_trigger();
     constexpr int THREADS = MULTI ? 64 : 128;
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int K3 = 3 * K;
@@ -795,10 +797,10 @@ cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, con
         kern = g.sh_degree == 0 ? project_bwd_kernel<0, false, true, true>
              : g.sh_degree == 1 ? project_bwd_kernel<1, false, true, true>
              : g.sh_degree == 2 ? project_bwd_kernel<2, false, true, true> : project_bwd_kernel<3, false, true, true>;
-    kern<<<blocks, threads, 0, stream>>>(
-        g.means, g.log_scales, g.quats, g.sh, g.n, vd, reinterpret_cast<const float4*>(proj.conic_opac),
-        proj.tiles_touched, g2d, g2d_hi, accumulate ? 1 : 0, grads.means, grads.log_scales, grads.quats,
-        grads.opacity_logit, grads.sh, S_accum, S_po_accum, S_ls_accum);
+    (void)launch_pdl(kern, dim3(blocks), dim3(threads), 0, stream, g.means, g.log_scales, g.quats, g.sh, g.n, vd,
+                     reinterpret_cast<const float4*>(proj.conic_opac), proj.tiles_touched, g2d, g2d_hi,
+                     accumulate ? 1 : 0, grads.means, grads.log_scales, grads.quats, grads.opacity_logit, grads.sh,
+                     S_accum, S_po_accum, S_ls_accum);
     note_launch();
     return cudaGetLastError();
 }

@@ -329,6 +329,7 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
 __global__ void __launch_bounds__(256) zero_reached_rows_kernel(const uint32_t* __restrict__ tiles, int n,
                                                                 float4* __restrict__ g2d,
                                                                 float4* __restrict__ g2d_hi) {
+    pdl_wait_and_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || tiles[i] == 0u) return;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -342,8 +343,8 @@ __global__ void __launch_bounds__(256) zero_reached_rows_kernel(const uint32_t* 
 
 cudaError_t launch_zero_reached_rows(const uint32_t* tiles, int n, float* g2d, float* g2d_hi, cudaStream_t stream) {
     if (n == 0) return cudaSuccess;
-    zero_reached_rows_kernel<<<(n + 255) / 256, 256, 0, stream>>>(tiles, n, reinterpret_cast<float4*>(g2d),
-                                                                  reinterpret_cast<float4*>(g2d_hi));
+    (void)launch_pdl(zero_reached_rows_kernel, dim3((n + 255) / 256), dim3(256), 0, stream, tiles, n,
+                     reinterpret_cast<float4*>(g2d), reinterpret_cast<float4*>(g2d_hi));
     note_launch();
     return cudaGetLastError();
 }
@@ -358,6 +359,7 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) render_fwd_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
     float* __restrict__ image, float* __restrict__ final_T, uint32_t* __restrict__ n_contrib) {
+    pdl_wait_and_trigger();
     __shared__ FwdSmem<TW * TH, TW * TH / 32> sm;
     fwd_tile<TW, TH, TW * TH>(blockIdx.x, gx, W, H, ranges[blockIdx.x], gids, xy, conic_opac, rgb, st, image,
                               final_T, n_contrib, sm);
@@ -371,6 +373,7 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_kernel(
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
     const float* __restrict__ dL_dimage, float* __restrict__ g2d, float* __restrict__ g2d_hi) {
+    pdl_wait_and_trigger();
     __shared__ BwdSmem<TW * TH, TW * TH / 32> sm;
     bwd_tile<TW, TH, TW * TH, HI>(blockIdx.x, gx, W, H, ranges[blockIdx.x], gids, xy, conic_opac, rgb, st, final_T,
                                   n_contrib, dL_dimage, g2d, g2d_hi, sm);
@@ -386,6 +389,7 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_views_kernel(
     ViewsDev vd, const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, SetDev st, float* __restrict__ images,
     float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ counter) {
+    pdl_wait_and_trigger();
     __shared__ FwdSmem<BATCH, TW * TH / 32> sm;
     __shared__ int s_tile;
     for (;;) {
@@ -408,6 +412,7 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_views_ke
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, SetDev st,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL,
     float* __restrict__ g2d, uint32_t* __restrict__ counter) {
+    pdl_wait_and_trigger();
     __shared__ BwdSmem<BATCH, TW * TH / 32> sm;
     __shared__ int s_tile;
     for (;;) {
@@ -431,6 +436,7 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH) render_stats_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, int W, int H, int gx, SetDev st, uint2* __restrict__ counts) {
+    pdl_wait_and_trigger();
     const int tile = blockIdx.x;
     const int ox = (tile % gx) * TW, oy = (tile / gx) * TH;
     const int px = ox + (int)(threadIdx.x % TW);
@@ -460,6 +466,7 @@ __global__ void __launch_bounds__(TW * TH) render_stats_kernel(
 // FP32 FMA throughput probe (a measurement aid): eight independent FMA chains
 // per thread, `iters` rounds; the result is stored so nothing is folded.
 __global__ void __launch_bounds__(256) fma_probe_kernel(float* __restrict__ out, int iters, float b, float c) {
+    pdl_wait_and_trigger();
     float a[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
@@ -474,7 +481,7 @@ __global__ void __launch_bounds__(256) fma_probe_kernel(float* __restrict__ out,
 }
 
 cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t stream) {
-    fma_probe_kernel<<<blocks, 256, 0, stream>>>(out, iters, 0.999f, 1e-3f);
+    (void)launch_pdl(fma_probe_kernel, dim3(blocks), dim3(256), 0, stream, out, iters, 0.999f, 1e-3f);
     note_launch();
     return cudaGetLastError();
 }
@@ -486,10 +493,10 @@ template <int TW, int TH>
 static cudaError_t stats_tmpl(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
                               uint32_t* counts, cudaStream_t stream) {
     const int T = cam.gx * cam.gy;
-    render_stats_kernel<TW, TH><<<T, TW * TH, 0, stream>>>(
-        reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
-        reinterpret_cast<const float4*>(proj.conic_opac), cam.width, cam.height, cam.gx, st,
-        reinterpret_cast<uint2*>(counts));
+    (void)launch_pdl(render_stats_kernel<TW, TH>, dim3(T), dim3(TW * TH), 0, stream,
+                     reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
+                     reinterpret_cast<const float4*>(proj.conic_opac), cam.width, cam.height, cam.gx, st,
+                     reinterpret_cast<uint2*>(counts));
     note_launch();
     return cudaGetLastError();
 }
@@ -498,10 +505,10 @@ template <int TW, int TH>
 static cudaError_t fwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
                             float* image, float* final_T, uint32_t* n_contrib, cudaStream_t stream) {
     const int T = cam.gx * cam.gy;
-    render_fwd_kernel<TW, TH><<<T, TW * TH, 0, stream>>>(
-        reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
-        reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
-        cam.width, cam.height, cam.gx, st, image, final_T, n_contrib);
+    (void)launch_pdl(render_fwd_kernel<TW, TH>, dim3(T), dim3(TW * TH), 0, stream,
+                     reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
+                     reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
+                     cam.width, cam.height, cam.gx, st, image, final_T, n_contrib);
     note_launch();
     return cudaGetLastError();
 }
@@ -512,10 +519,10 @@ static cudaError_t bwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const Ca
                             float* g2d_hi, cudaStream_t stream) {
     const int T = cam.gx * cam.gy;
     auto kern = g2d_hi ? render_bwd_kernel<TW, TH, true> : render_bwd_kernel<TW, TH, false>;
-    kern<<<T, TW * TH, 0, stream>>>(
-        reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
-        reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
-        cam.width, cam.height, cam.gx, st, final_T, n_contrib, dL, g2d, g2d_hi);
+    (void)launch_pdl(kern, dim3(T), dim3(TW * TH), 0, stream, reinterpret_cast<const uint2*>(bins.ranges), bins.gids,
+                     reinterpret_cast<const float4*>(proj.xy), reinterpret_cast<const float4*>(proj.conic_opac),
+                     reinterpret_cast<const float4*>(proj.rgb), cam.width, cam.height, cam.gx, st, final_T, n_contrib,
+                     dL, g2d, g2d_hi);
     note_launch();
     return cudaGetLastError();
 }
@@ -560,11 +567,9 @@ static cudaError_t fwd_views_tmpl(const ViewsDev& vd, const sgs_proj& proj, cons
                                   uint32_t* n_contrib, uint32_t* counter, cudaStream_t stream) {
     auto k = render_fwd_views_kernel<TW, TH, BATCH>;
     const int grid = persistent_grid(k, TW * TH, vd.T_total);
-    k<<<grid, TW * TH, 0, stream>>>(vd, reinterpret_cast<const uint2*>(ranges), gids,
-                                    reinterpret_cast<const float4*>(proj.xy),
-                                    reinterpret_cast<const float4*>(proj.conic_opac),
-                                    reinterpret_cast<const float4*>(proj.rgb), st, images, final_T, n_contrib,
-                                    counter);
+    (void)launch_pdl(k, dim3(grid), dim3(TW * TH), 0, stream, vd, reinterpret_cast<const uint2*>(ranges), gids,
+                     reinterpret_cast<const float4*>(proj.xy), reinterpret_cast<const float4*>(proj.conic_opac),
+                     reinterpret_cast<const float4*>(proj.rgb), st, images, final_T, n_contrib, counter);
     note_launch();
     return cudaGetLastError();
 }
@@ -576,11 +581,9 @@ static cudaError_t bwd_views_tmpl(const ViewsDev& vd, const sgs_proj& proj, cons
                                   cudaStream_t stream) {
     auto k = render_bwd_views_kernel<TW, TH, BATCH>;
     const int grid = persistent_grid(k, TW * TH, vd.T_total);
-    k<<<grid, TW * TH, 0, stream>>>(vd, reinterpret_cast<const uint2*>(ranges), gids,
-                                    reinterpret_cast<const float4*>(proj.xy),
-                                    reinterpret_cast<const float4*>(proj.conic_opac),
-                                    reinterpret_cast<const float4*>(proj.rgb), st, final_T, n_contrib, dL, g2d,
-                                    counter);
+    (void)launch_pdl(k, dim3(grid), dim3(TW * TH), 0, stream, vd, reinterpret_cast<const uint2*>(ranges), gids,
+                     reinterpret_cast<const float4*>(proj.xy), reinterpret_cast<const float4*>(proj.conic_opac),
+                     reinterpret_cast<const float4*>(proj.rgb), st, final_T, n_contrib, dL, g2d, counter);
     note_launch();
     return cudaGetLastError();
 }

@@ -67,6 +67,7 @@ __device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* s
 __global__ void __launch_bounds__(SCAN_THREADS) scan_reduce_kernel(const uint32_t* __restrict__ in,
                                                                    const int32_t* d_n, int64_t n_max,
                                                                    uint32_t* __restrict__ partial) {
+    pdl_wait_and_trigger();
     __shared__ uint32_t s_warp[32];
     int64_t n = read_n(d_n, n_max, n_max);
     int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_reduce_kernel(const uint32_
 
 __global__ void __launch_bounds__(SCAN_THREADS) scan_partials_kernel(uint32_t* __restrict__ partial,
                                                                      int nb, uint32_t* __restrict__ d_total) {
+    pdl_wait_and_trigger();
     __shared__ uint32_t s_warp[32];
     uint32_t v = threadIdx.x < nb ? partial[threadIdx.x] : 0u;
     uint32_t inc = block_inclusive_scan(v, s_warp);
@@ -89,6 +91,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_partials_kernel(uint32_t* _
 __global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep_kernel(
     const uint32_t* __restrict__ in, uint32_t* __restrict__ out, const int32_t* d_n, int64_t n_max,
     const uint32_t* __restrict__ partial) {
+    pdl_wait_and_trigger();
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_carry;
     int64_t n = read_n(d_n, n_max, n_max);
@@ -122,11 +125,11 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* d
                                   const int32_t* d_n, void* tmp, cudaStream_t stream) {
     int nb = scan_blocks(n_max);
     uint32_t* partial = reinterpret_cast<uint32_t*>(tmp);
-    scan_reduce_kernel<<<nb, SCAN_THREADS, 0, stream>>>(in, d_n, n_max, partial);
+    (void)launch_pdl(scan_reduce_kernel, dim3(nb), dim3(SCAN_THREADS), 0, stream, in, d_n, n_max, partial);
     note_launch();
-    scan_partials_kernel<<<1, SCAN_THREADS, 0, stream>>>(partial, nb, d_total);
+    (void)launch_pdl(scan_partials_kernel, dim3(1), dim3(SCAN_THREADS), 0, stream, partial, nb, d_total);
     note_launch();
-    scan_downsweep_kernel<<<nb, SCAN_THREADS, 0, stream>>>(in, out, d_n, n_max, partial);
+    (void)launch_pdl(scan_downsweep_kernel, dim3(nb), dim3(SCAN_THREADS), 0, stream, in, out, d_n, n_max, partial);
     note_launch();
     return cudaGetLastError();
 }
@@ -187,6 +190,7 @@ struct NextHist {            // per-block histogram of the following pass (bits 
 // Exclusive scan of one digit's per-block counts (one block per digit).
 __global__ void __launch_bounds__(SORT_G_MAX) pass_scan_kernel(uint32_t* __restrict__ hist, int G,
                                                                uint32_t* __restrict__ tot) {
+    pdl_wait_and_trigger();
     __shared__ uint32_t s_warp[32];
     uint32_t* h = hist + (size_t)blockIdx.x * G;
     const uint32_t v = threadIdx.x < G ? h[threadIdx.x] : 0u;
@@ -214,6 +218,7 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t dig, bool valid, int bi
 __global__ void __launch_bounds__(RS_THREADS) depth_hist_first_kernel(const float* __restrict__ depth,
                                                                       const uint32_t* __restrict__ tiles_touched,
                                                                       int64_t n_rows, PassDesc ps) {
+    pdl_wait_and_trigger();
     __shared__ uint32_t s_h[RS_RADIX_MAX];
     for (int k = threadIdx.x; k < RS_RADIX_MAX; k += RS_THREADS) s_h[k] = 0u;
     __syncthreads();
@@ -237,6 +242,7 @@ __global__ void __launch_bounds__(RS_THREADS) depth_hist_first_kernel(const floa
 __global__ void __launch_bounds__(RS_THREADS) pass_hist_kernel(const uint32_t* __restrict__ keys,
                                                                const uint32_t* __restrict__ prev_tot, int prev_radix,
                                                                PassDesc ps) {
+    pdl_wait_and_trigger();
     __shared__ uint32_t s_h[RS_RADIX_MAX];
     __shared__ uint32_t s_n;
     const int lane = threadIdx.x & 31;
@@ -276,6 +282,7 @@ __global__ void __launch_bounds__(RS_THREADS) pass_scatter_kernel(
     const uint32_t* __restrict__ tiles_touched, int64_t n_rows, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, PassDesc ps, uint32_t* __restrict__ cnt_out,
     unsigned long long* __restrict__ esum, int G_emit) {
+    pdl_wait_and_trigger();
     __shared__ uint32_t s_warp[RS_WARPS][RS_RADIX_MAX + 1];
     __shared__ uint32_t s_off[RS_RADIX_MAX];
     __shared__ uint32_t s_tot[RS_RADIX_MAX];
@@ -398,6 +405,7 @@ __global__ void __launch_bounds__(RS_THREADS) pass_scatter_kernel(
 // writes M.
 __global__ void __launch_bounds__(SORT_G_MAX) emit_offsets_kernel(unsigned long long* __restrict__ esum, int G,
                                                                   int32_t* __restrict__ d_count) {
+    pdl_wait_and_trigger();
     constexpr int PER = EMIT_G_MAX / SORT_G_MAX;
     __shared__ unsigned long long s_w[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -449,6 +457,7 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
     const uint32_t* __restrict__ depth_tot, ViewsDev vd, int64_t cap, const unsigned long long* __restrict__ esum,
     int G_emit, const int32_t* __restrict__ d_count, uint32_t* __restrict__ inst_tile,
     uint32_t* __restrict__ inst_gid, NextHist nh) {
+    pdl_wait_and_trigger();
     __shared__ uint32_t s_off[EMIT_SUB + 1];
     __shared__ uint32_t s_row[EMIT_SUB];
     __shared__ short4 s_rect[EMIT_SUB];
@@ -589,6 +598,7 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ tile_sorted, const int32_t* d_n, int64_t cap,
                               uint2* __restrict__ ranges) {
+    pdl_wait_and_trigger();
     int64_t n = read_n(d_n, 0, cap);
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -601,6 +611,7 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ tile_sorted, const in
 __global__ void keys_kernel(const uint32_t* __restrict__ tile_sorted, const uint32_t* __restrict__ gids,
                             const float* __restrict__ depth, const int32_t* d_n, int64_t cap,
                             uint64_t* __restrict__ keys) {
+    pdl_wait_and_trigger();
     int64_t n = read_n(d_n, 0, cap);
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (; k < n; k += (int64_t)gridDim.x * blockDim.x)
@@ -708,30 +719,32 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
     // 1. stable sort of the visible rows by depth bits (4 passes of 8 bits; the
     //    first pass drops the rows that touch no tile, the last one also
     //    gathers the rows' tile counts in depth order)
-    depth_hist_first_kernel<<<sg.G_depth, RS_THREADS, 0, stream>>>(proj.depth, proj.tiles_touched, n, depth_pass(0));
+    (void)launch_pdl(depth_hist_first_kernel, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream, proj.depth,
+                     proj.tiles_touched, n, depth_pass(0));
     note_launch();
     for (int p = 0; p < DEPTH_PASSES; ++p) {
         const PassDesc ps = depth_pass(p);
         const int src = (p + 1) & 1, dst = p & 1;     // pass 0 -> buffer 0 -> 1 -> 0 -> 1
         if (p > 0) {
-            pass_hist_kernel<<<sg.G_depth, RS_THREADS, 0, stream>>>(w.dkey[src], depth_pass(p - 1).tot, RS_RADIX_MAX,
-                                                                    ps);
+            (void)launch_pdl(pass_hist_kernel, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream, w.dkey[src],
+                             depth_pass(p - 1).tot, RS_RADIX_MAX, ps);
             note_launch();
         }
-        pass_scan_kernel<<<1 << ps.bits, SORT_G_MAX, 0, stream>>>(ps.hist, ps.G, ps.tot);
+        (void)launch_pdl(pass_scan_kernel, dim3(1 << ps.bits), dim3(SORT_G_MAX), 0, stream, ps.hist, ps.G, ps.tot);
         note_launch();
         const bool last = p + 1 == DEPTH_PASSES;
         uint32_t* kout = last ? nullptr : w.dkey[dst];
         if (p == 0)
-            pass_scatter_kernel<true, false><<<sg.G_depth, RS_THREADS, 0, stream>>>(
-                nullptr, nullptr, proj.depth, proj.tiles_touched, n, kout, w.perm[dst], ps, nullptr, nullptr, 1);
+            (void)launch_pdl(pass_scatter_kernel<true, false>, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream, nullptr,
+                             nullptr, proj.depth, proj.tiles_touched, n, kout, w.perm[dst], ps, nullptr, nullptr, 1);
         else if (!last)
-            pass_scatter_kernel<false, false><<<sg.G_depth, RS_THREADS, 0, stream>>>(
-                w.dkey[src], w.perm[src], nullptr, nullptr, 0, kout, w.perm[dst], ps, nullptr, nullptr, 1);
+            (void)launch_pdl(pass_scatter_kernel<false, false>, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream,
+                             w.dkey[src], w.perm[src], nullptr, nullptr, 0, kout, w.perm[dst], ps, nullptr, nullptr,
+                             1);
         else
-            pass_scatter_kernel<false, true><<<sg.G_depth, RS_THREADS, 0, stream>>>(
-                w.dkey[src], w.perm[src], nullptr, proj.tiles_touched, 0, kout, w.perm[dst], ps, w.cnt, w.esum,
-                sg.G_emit);
+            (void)launch_pdl(pass_scatter_kernel<false, true>, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream,
+                             w.dkey[src], w.perm[src], nullptr, proj.tiles_touched, 0, kout, w.perm[dst], ps, w.cnt,
+                             w.esum, sg.G_emit);
         note_launch();
     }
     const uint32_t* perm = w.perm[(DEPTH_PASSES - 1) & 1];
@@ -747,7 +760,7 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
         gv[0] = w.inst_gid_tmp;
         gv[1] = out.gids;
     }
-    emit_offsets_kernel<<<1, SORT_G_MAX, 0, stream>>>(w.esum, sg.G_emit, out.count);
+    (void)launch_pdl(emit_offsets_kernel, dim3(1), dim3(SORT_G_MAX), 0, stream, w.esum, sg.G_emit, out.count);
     note_launch();
     {
         NextHist nh = none;
@@ -755,9 +768,9 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
             const PassDesc q = tile_pass(0);
             nh = NextHist{q.shift, q.bits, q.hist, q.G};
         }
-        emit_kernel<<<sg.G_emit, EMIT_THREADS, 0, stream>>>(perm, w.cnt, reinterpret_cast<const short4*>(proj.rect),
-                                                           w.depth_tot, vd, out.capacity, w.esum, sg.G_emit,
-                                                           out.count, gk[0], gv[0], nh);
+        (void)launch_pdl(emit_kernel, dim3(sg.G_emit), dim3(EMIT_THREADS), 0, stream, perm, w.cnt,
+                         reinterpret_cast<const short4*>(proj.rect), w.depth_tot, vd, out.capacity, w.esum, sg.G_emit,
+                         out.count, gk[0], gv[0], nh);
         note_launch();
     }
     // 3. stable passes over the written instances by tile id (the first
@@ -766,24 +779,25 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
         const PassDesc ps = tile_pass(p);
         if (p > 0) {
             const PassDesc q = tile_pass(p - 1);
-            pass_hist_kernel<<<sg.G_tile, RS_THREADS, 0, stream>>>(gk[p & 1], q.tot, 1 << q.bits, ps);
+            (void)launch_pdl(pass_hist_kernel, dim3(sg.G_tile), dim3(RS_THREADS), 0, stream, gk[p & 1], q.tot,
+                             1 << q.bits, ps);
             note_launch();
         }
-        pass_scan_kernel<<<1 << ps.bits, SORT_G_MAX, 0, stream>>>(ps.hist, ps.G, ps.tot);
+        (void)launch_pdl(pass_scan_kernel, dim3(1 << ps.bits), dim3(SORT_G_MAX), 0, stream, ps.hist, ps.G, ps.tot);
         note_launch();
-        pass_scatter_kernel<false, false><<<sg.G_tile, RS_THREADS, 0, stream>>>(
-            gk[p & 1], gv[p & 1], nullptr, nullptr, 0, gk[(p + 1) & 1], gv[(p + 1) & 1], ps, nullptr, nullptr, 1);
+        (void)launch_pdl(pass_scatter_kernel<false, false>, dim3(sg.G_tile), dim3(RS_THREADS), 0, stream, gk[p & 1],
+                         gv[p & 1], nullptr, nullptr, 0, gk[(p + 1) & 1], gv[(p + 1) & 1], ps, nullptr, nullptr, 1);
         note_launch();
     }
     const uint32_t* tile_sorted = gk[tc.passes & 1];
     // 4. per-tile ranges and optional 64-bit keys
     const int rb = 152 * 8;
-    ranges_kernel<<<rb, 256, 0, stream>>>(tile_sorted, out.count, out.capacity,
-                                          reinterpret_cast<uint2*>(out.ranges));
+    (void)launch_pdl(ranges_kernel, dim3(rb), dim3(256), 0, stream, tile_sorted, out.count, out.capacity,
+                     reinterpret_cast<uint2*>(out.ranges));
     note_launch();
     if (out.keys) {
-        keys_kernel<<<rb, 256, 0, stream>>>(tile_sorted, out.gids, proj.depth, out.count, out.capacity,
-                                            out.keys);
+        (void)launch_pdl(keys_kernel, dim3(rb), dim3(256), 0, stream, tile_sorted, out.gids, proj.depth, out.count,
+                         out.capacity, out.keys);
         note_launch();
     }
     return cudaGetLastError();

@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(SS_W * SS_H) ssim_moments_kernel(const float* 
                                                                    const float* __restrict__ target, int H, int W,
                                                                    float lam, float inv_views,
                                                                    float* __restrict__ coef, float* __restrict__ loss) {
+    pdl_wait_and_trigger();
     __shared__ float taps[SS_TAPS];
     __shared__ float sx[3][SS_RH][SS_RW];
     __shared__ float sy[3][SS_RH][SS_RW];
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(SS_W * SS_H) ssim_grad_kernel(const float* __r
                                                                 float lam, float inv_views,
                                                                 const float* __restrict__ coef,
                                                                 float* __restrict__ dL) {
+    pdl_wait_and_trigger();
     __shared__ float taps[SS_TAPS];
     __shared__ float sm[3][SS_RH][SS_RW];
     __shared__ float hor[3][SS_RH][SS_W];
@@ -202,9 +204,11 @@ cudaError_t launch_ssim_l1(const float* image, const float* target, int H, int W
     float* coef = reinterpret_cast<float*>(ws);
     const dim3 grid((W + SS_W - 1) / SS_W, (H + SS_H - 1) / SS_H);
     const float inv_views = 1.0f / (float)n_views;
-    ssim_moments_kernel<<<grid, SS_W * SS_H, 0, stream>>>(image, target, H, W, lam, inv_views, coef, loss);
+    (void)launch_pdl(ssim_moments_kernel, dim3(grid), dim3(SS_W * SS_H), 0, stream, image, target, H, W, lam,
+                     inv_views, coef, loss);
     note_launch();
-    ssim_grad_kernel<<<grid, SS_W * SS_H, 0, stream>>>(image, target, H, W, lam, inv_views, coef, dL);
+    (void)launch_pdl(ssim_grad_kernel, dim3(grid), dim3(SS_W * SS_H), 0, stream, image, target, H, W, lam, inv_views,
+                     coef, dL);
     note_launch();
     return cudaGetLastError();
 }
