@@ -348,16 +348,8 @@ __device__ __forceinline__ float theta_entry(const float* s6, const float* spo, 
 }
 
 template <int N>
-__global__ void __launch_bounds__(256) eig_theta_flag_kernel(const float* __restrict__ S,
-                                                             const float* __restrict__ S_po,
-                                                             const float* __restrict__ S_ls, int n, float inv_T,
-                                                             float eps_split, const float* __restrict__ grad_norm,
-                                                             float eps_grad, float* __restrict__ lam_out,
-                                                             float* __restrict__ v_out, uint32_t* __restrict__ flags) {
-    pdl_wait_and_trigger();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float s6[6], spo[3], sls[N == 7 ? 18 : 1];
+__device__ __forceinline__ void load_theta(const float* __restrict__ S, const float* __restrict__ S_po,
+                                           const float* __restrict__ S_ls, int i, float* s6, float* spo, float* sls) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) s6[k] = S[(size_t)i * 6 + k];
 #pragma unroll
@@ -366,13 +358,80 @@ __global__ void __launch_bounds__(256) eig_theta_flag_kernel(const float* __rest
 #pragma unroll
         for (int k = 0; k < 18; ++k) sls[k] = S_ls[(size_t)i * 18 + k];
     }
+}
+
+__device__ __forceinline__ void write_flag(int i, float lam, float eps_split, const float* __restrict__ grad_norm,
+                                           float eps_grad, uint32_t* __restrict__ flags) {
+    bool f = lam < eps_split;
+    if (grad_norm) f = f && (grad_norm[i] <= eps_grad);
+    flags[i] = f ? 1u : 0u;
+}
+
+// The splitting matrix of a Gaussian that no pixel reached is zero, and its
+// minimum eigenpair is (0, e_0), what the rotations return for it.  This
+// kernel writes those directly and appends the others to a work list (one
+// atomic per warp), so that the iterative solve runs in full warps.
+template <int N>
+__global__ void __launch_bounds__(256) eig_theta_triage_kernel(const float* __restrict__ S,
+                                                               const float* __restrict__ S_po,
+                                                               const float* __restrict__ S_ls, int n,
+                                                               float eps_split, const float* __restrict__ grad_norm,
+                                                               float eps_grad, float* __restrict__ lam_out,
+                                                               float* __restrict__ v_out, uint32_t* __restrict__ flags,
+                                                               uint32_t* __restrict__ work,
+                                                               uint32_t* __restrict__ n_work) {
+    pdl_wait_and_trigger();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool nz = false;
+    if (i < n) {
+        float s6[6], spo[3], sls[N == 7 ? 18 : 1];
+        load_theta<N>(S, S_po, S_ls, i, s6, spo, sls);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) nz |= s6[k] != 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) nz |= spo[k] != 0.0f;
+        if constexpr (N == 7) {
+#pragma unroll
+            for (int k = 0; k < 18; ++k) nz |= sls[k] != 0.0f;
+        }
+        if (!nz) {
+            lam_out[i] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < N; ++k) v_out[N * (size_t)i + k] = k == 0 ? 1.0f : 0.0f;
+            write_flag(i, 0.0f, eps_split, grad_norm, eps_grad, flags);
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, nz);
+    if (m == 0u) return;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(n_work, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (nz) work[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+}
+
+// Minimum eigenpair and flag of the listed (non-zero) matrices.
+template <int N>
+__global__ void __launch_bounds__(256) eig_theta_solve_kernel(const float* __restrict__ S,
+                                                              const float* __restrict__ S_po,
+                                                              const float* __restrict__ S_ls, float inv_T,
+                                                              float eps_split, const float* __restrict__ grad_norm,
+                                                              float eps_grad, float* __restrict__ lam_out,
+                                                              float* __restrict__ v_out, uint32_t* __restrict__ flags,
+                                                              const uint32_t* __restrict__ work,
+                                                              const uint32_t* __restrict__ n_work) {
+    pdl_wait_and_trigger();
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *n_work) return;
+    const int i = (int)work[t];
+    float s6[6], spo[3], sls[N == 7 ? 18 : 1];
+    load_theta<N>(S, S_po, S_ls, i, s6, spo, sls);
     const EigN<N> e = jacobi_min<N>([&](int r, int c) { return theta_entry<N>(s6, spo, sls, r, c) * inv_T; });
     lam_out[i] = e.lam;
 #pragma unroll
     for (int k = 0; k < N; ++k) v_out[N * (size_t)i + k] = e.v[k];
-    bool f = e.lam < eps_split;
-    if (grad_norm) f = f && (grad_norm[i] <= eps_grad);
-    flags[i] = f ? 1u : 0u;
+    write_flag(i, e.lam, eps_split, grad_norm, eps_grad, flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -577,16 +636,28 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
     float* v = v_out ? v_out : v_ws;
     if (n == 0) return cudaMemsetAsync(d_n_out, 0, sizeof(int32_t), stream);
     const int nb = (n + 255) / 256;
-    if (S_po && S_ls)
-        (void)launch_pdl(eig_theta_flag_kernel<7>, dim3(nb), dim3(256), 0, stream, S, S_po, S_ls, n, inv_T, eps_split,
-                         grad_norm, eps_grad, lam, v, flags);
-    else if (S_po)
-        (void)launch_pdl(eig_theta_flag_kernel<4>, dim3(nb), dim3(256), 0, stream, S, S_po, nullptr, n, inv_T,
-                         eps_split, grad_norm, eps_grad, lam, v, flags);
-    else
+    if (S_po) {
+        // triage (zero matrices answered directly) then the solve over the work
+        // list; excl and total serve as the list and its counter until the scan
+        cudaError_t z = cudaMemsetAsync(total, 0, sizeof(uint32_t), stream);
+        if (z != cudaSuccess) return z;
+        if (S_ls) {
+            (void)launch_pdl(eig_theta_triage_kernel<7>, dim3(nb), dim3(256), 0, stream, S, S_po, S_ls, n, eps_split,
+                             grad_norm, eps_grad, lam, v, flags, excl, total);
+            (void)launch_pdl(eig_theta_solve_kernel<7>, dim3(nb), dim3(256), 0, stream, S, S_po, S_ls, inv_T,
+                             eps_split, grad_norm, eps_grad, lam, v, flags, excl, total);
+        } else {
+            (void)launch_pdl(eig_theta_triage_kernel<4>, dim3(nb), dim3(256), 0, stream, S, S_po, nullptr, n,
+                             eps_split, grad_norm, eps_grad, lam, v, flags, excl, total);
+            (void)launch_pdl(eig_theta_solve_kernel<4>, dim3(nb), dim3(256), 0, stream, S, S_po, nullptr, inv_T,
+                             eps_split, grad_norm, eps_grad, lam, v, flags, excl, total);
+        }
+        note_launch(2);
+    } else {
         (void)launch_pdl(eig_flag_kernel, dim3(nb), dim3(256), 0, stream, S, n, inv_T, eps_split, grad_norm, eps_grad,
                          lam, v, flags);
-    note_launch();
+        note_launch();
+    }
     cudaError_t e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
     if (e != cudaSuccess) return e;
     if (max_splits > 0) {
