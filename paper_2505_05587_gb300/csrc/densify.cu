@@ -171,26 +171,6 @@ __device__ Eig eig3_min(const float* s6, float scale) {
     return e;
 }
 
-__global__ void __launch_bounds__(256) eig_flag_kernel(const float* __restrict__ S, int n, float inv_T,
-                                                       float eps_split, const float* __restrict__ grad_norm,
-                                                       float eps_grad, float* __restrict__ lam_out,
-                                                       float* __restrict__ v_out, uint32_t* __restrict__ flags) {
-    pdl_wait_and_trigger();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float s6[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) s6[k] = S[(size_t)i * 6 + k];
-    Eig e = eig3_min(s6, inv_T);
-    lam_out[i] = e.lam;
-    v_out[3 * (size_t)i] = e.v[0];
-    v_out[3 * (size_t)i + 1] = e.v[1];
-    v_out[3 * (size_t)i + 2] = e.v[2];
-    bool f = e.lam < eps_split;
-    if (grad_norm) f = f && (grad_norm[i] <= eps_grad);
-    flags[i] = f ? 1u : 0u;
-}
-
 // Minimum eigenpair of a small symmetric matrix (the splitting matrix over
 // theta = (p, o), N = 4, or theta = (p, l, o), N = 7) by cyclic Jacobi
 // rotations (Jacobi's method; Golub & Van Loan, Matrix Computations, Sec.
@@ -352,8 +332,10 @@ __device__ __forceinline__ void load_theta(const float* __restrict__ S, const fl
                                            const float* __restrict__ S_ls, int i, float* s6, float* spo, float* sls) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) s6[k] = S[(size_t)i * 6 + k];
+    if constexpr (N > 3) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) spo[k] = S_po[(size_t)i * 3 + k];
+        for (int k = 0; k < 3; ++k) spo[k] = S_po[(size_t)i * 3 + k];
+    }
     if constexpr (N == 7) {
 #pragma unroll
         for (int k = 0; k < 18; ++k) sls[k] = S_ls[(size_t)i * 18 + k];
@@ -368,11 +350,11 @@ __device__ __forceinline__ void write_flag(int i, float lam, float eps_split, co
 }
 
 // The splitting matrix of a Gaussian that no pixel reached is zero, and its
-// minimum eigenpair is (0, e_0), what the rotations return for it.  This
-// kernel writes those directly and appends the others to a work list (one
-// atomic per warp), so that the iterative solve runs in full warps.
+// minimum eigenpair is (0, e_0), what both solvers return for it.  This kernel
+// writes those directly and appends the others to a work list (one atomic per
+// block), so that the rotations run in full warps.
 template <int N>
-__global__ void __launch_bounds__(256) eig_theta_triage_kernel(const float* __restrict__ S,
+__global__ void __launch_bounds__(256) eig_triage_kernel(const float* __restrict__ S,
                                                                const float* __restrict__ S_po,
                                                                const float* __restrict__ S_ls, int n,
                                                                float eps_split, const float* __restrict__ grad_norm,
@@ -389,8 +371,10 @@ __global__ void __launch_bounds__(256) eig_theta_triage_kernel(const float* __re
         load_theta<N>(S, S_po, S_ls, i, s6, spo, sls);
 #pragma unroll
         for (int k = 0; k < 6; ++k) nz |= s6[k] != 0.0f;
+        if constexpr (N > 3) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) nz |= spo[k] != 0.0f;
+            for (int k = 0; k < 3; ++k) nz |= spo[k] != 0.0f;
+        }
         if constexpr (N == 7) {
 #pragma unroll
             for (int k = 0; k < 18; ++k) nz |= sls[k] != 0.0f;
@@ -402,18 +386,47 @@ __global__ void __launch_bounds__(256) eig_theta_triage_kernel(const float* __re
             write_flag(i, 0.0f, eps_split, grad_norm, eps_grad, flags);
         }
     }
+    // one atomic per block: warp counts, their prefix, then the block's base
+    __shared__ uint32_t s_cnt[8];
+    __shared__ uint32_t s_base;
+    const int warp = threadIdx.x >> 5;
     const unsigned m = __ballot_sync(0xffffffffu, nz);
-    if (m == 0u) return;
-    const int leader = __ffs(m) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(n_work, (uint32_t)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (nz) work[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+    if (lane == 0) s_cnt[warp] = (uint32_t)__popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const uint32_t c = s_cnt[w];
+            s_cnt[w] = t;
+            t += c;
+        }
+        s_base = t ? atomicAdd(n_work, t) : 0u;
+    }
+    __syncthreads();
+    if (nz) work[s_base + s_cnt[warp] + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+}
+
+// Minimum eigenpair and flag of every matrix over the position (root formula).
+__global__ void __launch_bounds__(256) eig_direct_kernel(const float* __restrict__ S, int n, float inv_T,
+                                                         float eps_split, const float* __restrict__ grad_norm,
+                                                         float eps_grad, float* __restrict__ lam_out,
+                                                         float* __restrict__ v_out, uint32_t* __restrict__ flags) {
+    pdl_wait_and_trigger();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s6[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s6[k] = S[(size_t)i * 6 + k];
+    const Eig e = eig3_min(s6, inv_T);
+    lam_out[i] = e.lam;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v_out[3 * (size_t)i + k] = e.v[k];
+    write_flag(i, e.lam, eps_split, grad_norm, eps_grad, flags);
 }
 
 // Minimum eigenpair and flag of the listed (non-zero) matrices.
 template <int N>
-__global__ void __launch_bounds__(256) eig_theta_solve_kernel(const float* __restrict__ S,
+__global__ void __launch_bounds__(256) eig_solve_kernel(const float* __restrict__ S,
                                                               const float* __restrict__ S_po,
                                                               const float* __restrict__ S_ls, float inv_T,
                                                               float eps_split, const float* __restrict__ grad_norm,
@@ -636,27 +649,32 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
     float* v = v_out ? v_out : v_ws;
     if (n == 0) return cudaMemsetAsync(d_n_out, 0, sizeof(int32_t), stream);
     const int nb = (n + 255) / 256;
-    if (S_po) {
-        // triage (zero matrices answered directly) then the solve over the work
-        // list; excl and total serve as the list and its counter until the scan
-        cudaError_t z = cudaMemsetAsync(total, 0, sizeof(uint32_t), stream);
-        if (z != cudaSuccess) return z;
-        if (S_ls) {
-            (void)launch_pdl(eig_theta_triage_kernel<7>, dim3(nb), dim3(256), 0, stream, S, S_po, S_ls, n, eps_split,
-                             grad_norm, eps_grad, lam, v, flags, excl, total);
-            (void)launch_pdl(eig_theta_solve_kernel<7>, dim3(nb), dim3(256), 0, stream, S, S_po, S_ls, inv_T,
-                             eps_split, grad_norm, eps_grad, lam, v, flags, excl, total);
-        } else {
-            (void)launch_pdl(eig_theta_triage_kernel<4>, dim3(nb), dim3(256), 0, stream, S, S_po, nullptr, n,
-                             eps_split, grad_norm, eps_grad, lam, v, flags, excl, total);
-            (void)launch_pdl(eig_theta_solve_kernel<4>, dim3(nb), dim3(256), 0, stream, S, S_po, nullptr, inv_T,
-                             eps_split, grad_norm, eps_grad, lam, v, flags, excl, total);
+    {
+        // rotations: triage (zero matrices answered directly) then the solve
+        // over the work list; excl and total serve as the list and its counter
+        // until the scan
+        if (S_po) {
+            cudaError_t z = cudaMemsetAsync(total, 0, sizeof(uint32_t), stream);
+            if (z != cudaSuccess) return z;
         }
-        note_launch(2);
-    } else {
-        (void)launch_pdl(eig_flag_kernel, dim3(nb), dim3(256), 0, stream, S, n, inv_T, eps_split, grad_norm, eps_grad,
-                         lam, v, flags);
-        note_launch();
+        auto run = [&](auto dim) {
+            constexpr int N = decltype(dim)::value;
+            (void)launch_pdl(eig_triage_kernel<N>, dim3(nb), dim3(256), 0, stream, S, S_po, S_ls, n, eps_split,
+                             grad_norm, eps_grad, lam, v, flags, excl, total);
+            (void)launch_pdl(eig_solve_kernel<N>, dim3(nb), dim3(256), 0, stream, S, S_po, S_ls, inv_T, eps_split,
+                             grad_norm, eps_grad, lam, v, flags, excl, total);
+        };
+        if (S_po && S_ls) {
+            run(std::integral_constant<int, 7>{});
+            note_launch(2);
+        } else if (S_po) {
+            run(std::integral_constant<int, 4>{});
+            note_launch(2);
+        } else {                                     // the root formula: short enough to run unsorted
+            (void)launch_pdl(eig_direct_kernel, dim3(nb), dim3(256), 0, stream, S, n, inv_T, eps_split, grad_norm,
+                             eps_grad, lam, v, flags);
+            note_launch();
+        }
     }
     cudaError_t e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
     if (e != cudaSuccess) return e;

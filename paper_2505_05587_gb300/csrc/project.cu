@@ -278,7 +278,7 @@ __device__ __forceinline__ void sh_weighted_grad(float x, float y, float z, cons
 // ---------------------------------------------------------------------------
 // One thread per projection row (view v, Gaussian i of view v's scene).
 template <int DEG>
-__global__ void __launch_bounds__(256) project_kernel(ScenesDev sc, ViewsDev vd, SetDev st,
+__global__ void __launch_bounds__(256, 6) project_kernel(ScenesDev sc, ViewsDev vd, SetDev st,
     float4* __restrict__ xy, float4* __restrict__ conic_opac, float4* __restrict__ rgb_out,
     float* __restrict__ depth, short4* __restrict__ rect, uint32_t* __restrict__ tiles) {
     pdl_wait_and_trigger();
