@@ -312,11 +312,16 @@ __global__ void __launch_bounds__(RS_THREADS) pass_scatter_kernel(
         __syncthreads();
         uint32_t key[RS_ITEMS], val[RS_ITEMS], dig[RS_ITEMS], rank[RS_ITEMS];
         bool ok[RS_ITEMS];
-        const int64_t wbase = tile + (int64_t)warp * 32 * RS_ITEMS + lane;
+        // the tile's items split into 8 contiguous warp chunks (a multiple of
+        // 32 each), so that a short tile spreads over all warps
+        const int tile_n = (int)min((int64_t)RS_TILE, hi - tile);
+        const int wchunk = (((tile_n + RS_WARPS - 1) / RS_WARPS) + 31) & ~31;
+        const int iters = wchunk >> 5;
+        const int64_t wbase = tile + (int64_t)warp * wchunk + lane;
 #pragma unroll
         for (int it = 0; it < RS_ITEMS; ++it) {
             const int64_t idx = wbase + it * 32;
-            bool valid = idx < hi;
+            bool valid = it < iters && idx < hi;
             if (FIRST) {
                 valid = valid && tiles_touched[idx] != 0u;
                 key[it] = valid ? __float_as_uint(depth[idx]) : 0u;
@@ -330,6 +335,7 @@ __global__ void __launch_bounds__(RS_THREADS) pass_scatter_kernel(
         }
 #pragma unroll
         for (int it = 0; it < RS_ITEMS; ++it) {
+            if (it >= iters) break;                     // block-uniform
             const unsigned peers = digit_peers(dig[it], ok[it], ps.bits);
             const unsigned lower = peers & ((1u << lane) - 1u);
             const uint32_t slot = ok[it] ? dig[it] : (uint32_t)radix;
