@@ -27,6 +27,13 @@
  *     code).  Argument errors are detected on the host before any launch and
  *     leave every output untouched.  SGS_ERR_CUDA means a launch failed; the
  *     CUDA error code is kept for sgs_get_last_cuda_error().
+ *   - Every call that launches work is capture-safe: it allocates nothing,
+ *     synchronises nothing and reads nothing back to the host, so a sequence
+ *     of calls can be captured into a CUDA graph and replayed (the
+ *     allocation-free variant's first call on a device is the exception, see
+ *     sgs_densify_split_noalloc).  Kernels are launched with programmatic
+ *     dependent launch: each one is scheduled while its predecessor on the
+ *     stream drains and waits for that predecessor's results before reading.
  *   - Data-dependent sizes (instance count M, split count) are written to
  *     caller-owned device integers.  When a size exceeds the caller's capacity
  *     the kernels write only within capacity (never out of bounds) and the
