@@ -134,13 +134,21 @@ typedef struct sgs_proj {
  *   ranges   [T,2]       per tile [start, end) into gids, T = tiles_x*tiles_y,
  *                        tile id = ty * tiles_x + tx.
  *   count    [1] int32   M, the number of instances (may exceed capacity).
- *   capacity             rows available in gids / keys (< 2^31). */
+ *   capacity             rows available in gids / keys (< 2^31).
+ *   order    [T]         optional (NULL to skip): every tile id once, longest
+ *                        lists first (classes floor(log2(list length)),
+ *                        descending; empty tiles last; ties by tile id).
+ *                        sgs_render_fwd and sgs_render_bwd_with_splitting
+ *                        launch their per-tile blocks in this order when it
+ *                        is given (the heavy tiles start first and the short
+ *                        ones fill the tail); results do not depend on it. */
 typedef struct sgs_bins {
     uint32_t *gids;
     uint64_t *keys;
     uint32_t *ranges;
     int32_t *count;
     int64_t capacity;
+    uint32_t *order;
 } sgs_bins;
 
 /* Parameter gradients written by sgs_render_bwd_with_splitting. */

@@ -66,7 +66,7 @@ class Proj(C.Structure):
 
 class Bins(C.Structure):
     _fields_ = [("gids", C.c_void_p), ("keys", C.c_void_p), ("ranges", C.c_void_p),
-                ("count", C.c_void_p), ("capacity", C.c_int64)]
+                ("count", C.c_void_p), ("capacity", C.c_int64), ("order", C.c_void_p)]
 
 
 class Grads(C.Structure):
@@ -234,16 +234,18 @@ class BinBuffers:
     ranges: torch.Tensor   # [T,2] i32 (uint32 in C)
     count: torch.Tensor    # [1] i32
     capacity: int
+    order: torch.Tensor | None = None   # [T] i32 (uint32 in C): tile schedule, longest lists first
 
     @staticmethod
-    def alloc(capacity: int, num_tiles: int, with_keys=False, device="cuda") -> "BinBuffers":
+    def alloc(capacity: int, num_tiles: int, with_keys=False, device="cuda", with_order=True) -> "BinBuffers":
         i32 = dict(device=device, dtype=torch.int32)
         return BinBuffers(torch.empty(max(capacity, 1), **i32),
                           torch.empty(max(capacity, 1), device=device, dtype=torch.int64) if with_keys else None,
-                          torch.empty(num_tiles, 2, **i32), torch.zeros(1, **i32), capacity)
+                          torch.empty(num_tiles, 2, **i32), torch.zeros(1, **i32), capacity,
+                          torch.empty(max(num_tiles, 1), **i32) if with_order else None)
 
     def c(self) -> Bins:
-        return Bins(_p(self.gids), _p(self.keys), _p(self.ranges), _p(self.count), self.capacity)
+        return Bins(_p(self.gids), _p(self.keys), _p(self.ranges), _p(self.count), self.capacity, _p(self.order))
 
 
 def camera_c(cam) -> Camera:

@@ -300,6 +300,7 @@ static ViewsWs carve_views_ws(void* base, const ViewsDev& vd, int64_t capacity, 
     w.bins.ranges = c.take<uint32_t>(2 * (size_t)vd.T_total);
     w.bins.count = nullptr;
     w.bins.capacity = capacity;
+    w.bins.order = c.take<uint32_t>((size_t)(vd.T_total > 0 ? vd.T_total : 1));
     w.sort_bytes = bin_sort_ws_bytes((int)rows, capacity, vd.T_total);
     w.sort_ws = c.take<char>(w.sort_bytes);
     w.final_T = c.take<float>(P);
@@ -359,12 +360,12 @@ int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* ca
     if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 2 * sizeof(uint32_t), s);
     if (e == cudaSuccess)
         e = launch_render_fwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, images, w.final_T,
-                                    w.n_contrib, w.counters, s);
+                                    w.n_contrib, w.counters, w.bins.order, s);
     if (e == cudaSuccess) e = launch_l1_views(images, targets, vd, w.dL, loss, s);
     if (e == cudaSuccess && rows > 0) e = cudaMemsetAsync(w.g2d, 0, 16 * sizeof(float) * rows, s);
     if (e == cudaSuccess)
         e = launch_render_bwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, w.final_T, w.n_contrib,
-                                    w.dL, w.g2d, w.counters + 1, s);
+                                    w.dL, w.g2d, w.counters + 1, w.bins.order, s);
     if (e == cudaSuccess)
         e = launch_project_bwd(*g, w.proj, vd, w.g2d, nullptr, accumulate_grads != 0, *grads, S_accum, S_po_accum,
                                nullptr, s);
@@ -415,7 +416,7 @@ int sgs_render_batch_fwd(const sgs_gaussians* scenes, const sgs_camera* cams, in
     if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess)
         e = launch_render_fwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, images, w.final_T,
-                                    w.n_contrib, w.counters, s);
+                                    w.n_contrib, w.counters, w.bins.order, s);
     return cuda_status(e);
 }
 

@@ -358,11 +358,12 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) render_fwd_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
-    float* __restrict__ image, float* __restrict__ final_T, uint32_t* __restrict__ n_contrib) {
+    float* __restrict__ image, float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
+    const uint32_t* __restrict__ order) {
     pdl_wait_and_trigger();
     __shared__ FwdSmem<TW * TH, TW * TH / 32> sm;
-    fwd_tile<TW, TH, TW * TH>(blockIdx.x, gx, W, H, ranges[blockIdx.x], gids, xy, conic_opac, rgb, st, image,
-                              final_T, n_contrib, sm);
+    const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    fwd_tile<TW, TH, TW * TH>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, image, final_T, n_contrib, sm);
 }
 
 // The backward kernels are bounded to 40 resident warps per SM (48 registers):
@@ -372,11 +373,13 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
-    const float* __restrict__ dL_dimage, float* __restrict__ g2d, float* __restrict__ g2d_hi) {
+    const float* __restrict__ dL_dimage, float* __restrict__ g2d, float* __restrict__ g2d_hi,
+    const uint32_t* __restrict__ order) {
     pdl_wait_and_trigger();
     __shared__ BwdSmem<TW * TH, TW * TH / 32> sm;
-    bwd_tile<TW, TH, TW * TH, HI>(blockIdx.x, gx, W, H, ranges[blockIdx.x], gids, xy, conic_opac, rgb, st, final_T,
-                                  n_contrib, dL_dimage, g2d, g2d_hi, sm);
+    const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    bwd_tile<TW, TH, TW * TH, HI>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, final_T, n_contrib,
+                                  dL_dimage, g2d, g2d_hi, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -388,16 +391,18 @@ template <int TW, int TH, int BATCH>
 __global__ void __launch_bounds__(TW * TH) render_fwd_views_kernel(
     ViewsDev vd, const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, SetDev st, float* __restrict__ images,
-    float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ counter) {
+    float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ counter,
+    const uint32_t* __restrict__ order) {
     pdl_wait_and_trigger();
     __shared__ FwdSmem<BATCH, TW * TH / 32> sm;
     __shared__ int s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
         __syncthreads();
-        const int t = s_tile;
+        const int k = s_tile;
         __syncthreads();
-        if (t >= vd.T_total) break;
+        if (k >= vd.T_total) break;
+        const int t = order ? (int)order[k] : k;
         const int v = view_of_tile(vd, t);
         const CamDev& c = vd.cam[v];
         const long long po = vd.pix_off[v];
@@ -411,16 +416,17 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_views_ke
     ViewsDev vd, const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, SetDev st,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL,
-    float* __restrict__ g2d, uint32_t* __restrict__ counter) {
+    float* __restrict__ g2d, uint32_t* __restrict__ counter, const uint32_t* __restrict__ order) {
     pdl_wait_and_trigger();
     __shared__ BwdSmem<BATCH, TW * TH / 32> sm;
     __shared__ int s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
         __syncthreads();
-        const int t = s_tile;
+        const int k = s_tile;
         __syncthreads();
-        if (t >= vd.T_total) break;
+        if (k >= vd.T_total) break;
+        const int t = order ? (int)order[k] : k;
         const int v = view_of_tile(vd, t);
         const CamDev& c = vd.cam[v];
         const long long po = vd.pix_off[v];
@@ -508,7 +514,7 @@ static cudaError_t fwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const Ca
     (void)launch_pdl(render_fwd_kernel<TW, TH>, dim3(T), dim3(TW * TH), 0, stream,
                      reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
                      reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
-                     cam.width, cam.height, cam.gx, st, image, final_T, n_contrib);
+                     cam.width, cam.height, cam.gx, st, image, final_T, n_contrib, bins.order);
     note_launch();
     return cudaGetLastError();
 }
@@ -522,7 +528,7 @@ static cudaError_t bwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const Ca
     (void)launch_pdl(kern, dim3(T), dim3(TW * TH), 0, stream, reinterpret_cast<const uint2*>(bins.ranges), bins.gids,
                      reinterpret_cast<const float4*>(proj.xy), reinterpret_cast<const float4*>(proj.conic_opac),
                      reinterpret_cast<const float4*>(proj.rgb), cam.width, cam.height, cam.gx, st, final_T, n_contrib,
-                     dL, g2d, g2d_hi);
+                     dL, g2d, g2d_hi, bins.order);
     note_launch();
     return cudaGetLastError();
 }
@@ -564,12 +570,13 @@ static int persistent_grid(K kernel, int threads, int T_total) {
 template <int TW, int TH, int BATCH>
 static cudaError_t fwd_views_tmpl(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                   const uint32_t* gids, const SetDev& st, float* images, float* final_T,
-                                  uint32_t* n_contrib, uint32_t* counter, cudaStream_t stream) {
+                                  uint32_t* n_contrib, uint32_t* counter, const uint32_t* order,
+                                  cudaStream_t stream) {
     auto k = render_fwd_views_kernel<TW, TH, BATCH>;
     const int grid = persistent_grid(k, TW * TH, vd.T_total);
     (void)launch_pdl(k, dim3(grid), dim3(TW * TH), 0, stream, vd, reinterpret_cast<const uint2*>(ranges), gids,
                      reinterpret_cast<const float4*>(proj.xy), reinterpret_cast<const float4*>(proj.conic_opac),
-                     reinterpret_cast<const float4*>(proj.rgb), st, images, final_T, n_contrib, counter);
+                     reinterpret_cast<const float4*>(proj.rgb), st, images, final_T, n_contrib, counter, order);
     note_launch();
     return cudaGetLastError();
 }
@@ -578,12 +585,12 @@ template <int TW, int TH, int BATCH>
 static cudaError_t bwd_views_tmpl(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                   const uint32_t* gids, const SetDev& st, const float* final_T,
                                   const uint32_t* n_contrib, const float* dL, float* g2d, uint32_t* counter,
-                                  cudaStream_t stream) {
+                                  const uint32_t* order, cudaStream_t stream) {
     auto k = render_bwd_views_kernel<TW, TH, BATCH>;
     const int grid = persistent_grid(k, TW * TH, vd.T_total);
     (void)launch_pdl(k, dim3(grid), dim3(TW * TH), 0, stream, vd, reinterpret_cast<const uint2*>(ranges), gids,
                      reinterpret_cast<const float4*>(proj.xy), reinterpret_cast<const float4*>(proj.conic_opac),
-                     reinterpret_cast<const float4*>(proj.rgb), st, final_T, n_contrib, dL, g2d, counter);
+                     reinterpret_cast<const float4*>(proj.rgb), st, final_T, n_contrib, dL, g2d, counter, order);
     note_launch();
     return cudaGetLastError();
 }
@@ -615,15 +622,17 @@ static cudaError_t bwd_views_tmpl(const ViewsDev& vd, const sgs_proj& proj, cons
 
 cudaError_t launch_render_fwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                     const uint32_t* gids, const SetDev& st, int batch, float* images,
-                                    float* final_T, uint32_t* n_contrib, uint32_t* counter, cudaStream_t stream) {
-    SGS_VIEWS_DISPATCH(fwd_views_tmpl, vd, proj, ranges, gids, st, images, final_T, n_contrib, counter, stream)
+                                    float* final_T, uint32_t* n_contrib, uint32_t* counter, const uint32_t* order,
+                                    cudaStream_t stream) {
+    SGS_VIEWS_DISPATCH(fwd_views_tmpl, vd, proj, ranges, gids, st, images, final_T, n_contrib, counter, order, stream)
 }
 
 cudaError_t launch_render_bwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                     const uint32_t* gids, const SetDev& st, int batch, const float* final_T,
                                     const uint32_t* n_contrib, const float* dL, float* g2d, uint32_t* counter,
-                                    cudaStream_t stream) {
-    SGS_VIEWS_DISPATCH(bwd_views_tmpl, vd, proj, ranges, gids, st, final_T, n_contrib, dL, g2d, counter, stream)
+                                    const uint32_t* order, cudaStream_t stream) {
+    SGS_VIEWS_DISPATCH(bwd_views_tmpl, vd, proj, ranges, gids, st, final_T, n_contrib, dL, g2d, counter, order,
+                       stream)
 }
 
 }  // namespace sgs

@@ -602,6 +602,70 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
     }
 }
 
+// Tile schedule: every tile id once, longest lists first.  Class of a tile =
+// 32 - (floor(log2(length)) + 1) (0 for the longest lists, 32 for empty
+// tiles); a stable counting sort by class in one block: class totals, then
+// rounds of 1024 tiles in id order, each ranked within its warp
+// (__match_any_sync) and across warps through per-warp class counts.
+constexpr int TO_THREADS = 1024;
+constexpr int TO_CLASSES = 33;
+
+__device__ __forceinline__ int tile_class(uint2 r) {
+    const uint32_t len = r.y - r.x;
+    return len ? __clz(len) : 32;
+}
+
+__global__ void __launch_bounds__(TO_THREADS) tile_order_kernel(const uint2* __restrict__ ranges, int T,
+                                                                uint32_t* __restrict__ order) {
+    pdl_wait_and_trigger();
+    __shared__ uint32_t s_base[TO_CLASSES];
+    __shared__ uint32_t s_wcnt[TO_THREADS / 32][TO_CLASSES];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < TO_CLASSES) s_base[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += TO_THREADS) atomicAdd(&s_base[tile_class(ranges[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int c = 0; c < TO_CLASSES; ++c) {
+            const uint32_t n = s_base[c];
+            s_base[c] = run;
+            run += n;
+        }
+    }
+    for (int r0 = 0; r0 < T; r0 += TO_THREADS) {
+        for (int k = threadIdx.x; k < (TO_THREADS / 32) * TO_CLASSES; k += TO_THREADS) (&s_wcnt[0][0])[k] = 0u;
+        __syncthreads();
+        const int t = r0 + threadIdx.x;
+        const bool valid = t < T;
+        const int c = valid ? tile_class(ranges[t]) : TO_CLASSES;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0u) s_wcnt[warp][c] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (threadIdx.x < TO_CLASSES) {                  // prefix over the warps, in warp order
+            uint32_t run = s_base[threadIdx.x];
+            for (int w = 0; w < TO_THREADS / 32; ++w) {
+                const uint32_t n = s_wcnt[w][threadIdx.x];
+                s_wcnt[w][threadIdx.x] = run;
+                run += n;
+            }
+            s_base[threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (valid) order[s_wcnt[warp][c] + rank] = (uint32_t)t;
+        __syncthreads();
+    }
+}
+
+static cudaError_t launch_tile_order(const sgs_bins& out, int T, cudaStream_t stream) {
+    if (!out.order || T <= 0) return cudaGetLastError();
+    (void)launch_pdl(tile_order_kernel, dim3(1), dim3(TO_THREADS), 0, stream,
+                     reinterpret_cast<const uint2*>(out.ranges), T, out.order);
+    note_launch();
+    return cudaGetLastError();
+}
+
 __global__ void ranges_kernel(const uint32_t* __restrict__ tile_sorted, const int32_t* d_n, int64_t cap,
                               uint2* __restrict__ ranges) {
     pdl_wait_and_trigger();
@@ -709,7 +773,10 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
     const TileSortCfg& tc = sg.tc;
     cudaError_t e = cudaMemsetAsync(out.ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, stream);
     if (e != cudaSuccess) return e;
-    if (n == 0) return cudaMemsetAsync(out.count, 0, sizeof(int32_t), stream);
+    if (n == 0) {
+        e = cudaMemsetAsync(out.count, 0, sizeof(int32_t), stream);
+        return e != cudaSuccess ? e : launch_tile_order(out, T, stream);
+    }
     e = cudaMemsetAsync(w.depth_hist, 0, w.zero_bytes, stream);
     if (e != cudaSuccess) return e;
     auto depth_pass = [&](int p) {
@@ -806,7 +873,7 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
                          out.capacity, out.keys);
         note_launch();
     }
-    return cudaGetLastError();
+    return launch_tile_order(out, T, stream);
 }
 
 }  // namespace sgs

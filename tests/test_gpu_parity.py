@@ -372,3 +372,45 @@ def test_invalid_arguments_rejected_on_host():
     with pytest.raises(B.SteepGSError) as e:
         B.bin_sort(vb.proj, scene.n, cam, synth.Settings(), vb.bins, B.workspace(16))
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("name,mk_scene,mk_cam,st", CASES, ids=[c[0] for c in CASES])
+def test_tile_order_is_the_longest_first_permutation(name, mk_scene, mk_cam, st):
+    """bins.order: every tile once, classes floor(log2(list length)) descending,
+    empty tiles last, ties by tile id (bit-exact against a host sort)."""
+    scene, cam = mk_scene(), mk_cam()
+    _, vb, _ = _gpu_view(scene, cam, st)
+    ranges = vb.bins.ranges.cpu().numpy().view(np.uint32).astype(np.int64)
+    length = ranges[:, 1] - ranges[:, 0]
+    cls = np.where(length > 0, 31 - np.floor(np.log2(np.maximum(length, 1))).astype(np.int64), 32)
+    expect = np.lexsort((np.arange(len(length)), cls))
+    assert np.array_equal(vb.bins.order.cpu().numpy().view(np.uint32), expect.astype(np.uint32))
+
+
+def test_results_do_not_depend_on_the_tile_order():
+    scene = synth.cluster_scene(3, 3000, 3)
+    cam = synth.camera_lookat((1.0, 0.5, -6.0), (0, 0, 0), 150, 101, 150.0)
+    st = synth.Settings()
+    g, vb, _ = _gpu_view(scene, cam, st)
+    tgt = torch.as_tensor(synth.target_image(2, cam.height, cam.width)).cuda()
+    out = {}
+    for use_order in (True, False):
+        bins = vb.bins if use_order else B.BinBuffers(vb.bins.gids, vb.bins.keys, vb.bins.ranges, vb.bins.count,
+                                                      vb.bins.capacity, None)
+        B.render_fwd(vb.proj, bins, cam, st, vb.image, vb.final_T, vb.n_contrib)
+        dL = torch.empty_like(vb.image)
+        loss = torch.zeros(1, device="cuda")
+        B.l1_loss_grad(vb.image, tgt, 1, dL, loss)
+        grads = g.zeros_like()
+        S = torch.zeros(g.n, 6, device="cuda")
+        ws = B.workspace(B.render_bwd_workspace_size(g.n))
+        B.render_bwd_with_splitting(g, vb.proj, bins, cam, st, vb.final_T, vb.n_contrib, dL, grads, S, ws,
+                                    accumulate=False)
+        torch.cuda.synchronize()
+        out[use_order] = (vb.image.clone(), vb.n_contrib.clone(), S.cpu().numpy(),
+                          [t.cpu().numpy() for t in grads.tensors()])
+    a, b = out[True], out[False]
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert _rel(a[2], b[2]) < 1e-5
+    for x, y in zip(a[3], b[3]):
+        assert _rel(x, y) < 1e-5
