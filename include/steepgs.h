@@ -136,8 +136,9 @@ typedef struct sgs_proj {
  *   count    [1] int32   M, the number of instances (may exceed capacity).
  *   capacity             rows available in gids / keys (< 2^31).
  *   order    [T]         optional (NULL to skip): every tile id once, longest
- *                        lists first (classes floor(log2(list length)),
- *                        descending; empty tiles last; ties by tile id).
+ *                        lists first (list length in quarter octaves:
+ *                        classes of the leading three bits, descending;
+ *                        empty tiles last; ties by tile id).
  *                        sgs_render_fwd and sgs_render_bwd_with_splitting
  *                        launch their per-tile blocks in this order when it
  *                        is given (the heavy tiles start first and the short

@@ -602,17 +602,21 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
     }
 }
 
-// Tile schedule: every tile id once, longest lists first.  Class of a tile =
-// 32 - (floor(log2(length)) + 1) (0 for the longest lists, 32 for empty
-// tiles); a stable counting sort by class in one block: class totals, then
+// Tile schedule: every tile id once, longest lists first.  Class of a tile:
+// its list length in quarter octaves, 4 clz(length) + 3 - (the two bits below
+// the leading one), 0 .. 127 from the longest lists down, 128 for empty
+// tiles; a stable counting sort by class in one block: class totals, then
 // rounds of 1024 tiles in id order, each ranked within its warp
 // (__match_any_sync) and across warps through per-warp class counts.
 constexpr int TO_THREADS = 1024;
-constexpr int TO_CLASSES = 33;
+constexpr int TO_CLASSES = 129;
 
 __device__ __forceinline__ int tile_class(uint2 r) {
     const uint32_t len = r.y - r.x;
-    return len ? __clz(len) : 32;
+    if (!len) return TO_CLASSES - 1;
+    const int z = __clz(len);
+    const uint32_t next2 = z <= 29 ? (len << (z + 1)) >> 30 : (z == 30 ? ((len & 1u) << 1) : 0u);
+    return 4 * z + 3 - (int)next2;
 }
 
 __global__ void __launch_bounds__(TO_THREADS) tile_order_kernel(const uint2* __restrict__ ranges, int T,

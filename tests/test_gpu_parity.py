@@ -376,13 +376,19 @@ def test_invalid_arguments_rejected_on_host():
 
 @pytest.mark.parametrize("name,mk_scene,mk_cam,st", CASES, ids=[c[0] for c in CASES])
 def test_tile_order_is_the_longest_first_permutation(name, mk_scene, mk_cam, st):
-    """bins.order: every tile once, classes floor(log2(list length)) descending,
-    empty tiles last, ties by tile id (bit-exact against a host sort)."""
+    """bins.order: every tile once, list lengths in quarter octaves (the leading
+    three bits) descending, empty tiles last, ties by tile id (bit-exact
+    against a host sort)."""
     scene, cam = mk_scene(), mk_cam()
     _, vb, _ = _gpu_view(scene, cam, st)
     ranges = vb.bins.ranges.cpu().numpy().view(np.uint32).astype(np.int64)
     length = ranges[:, 1] - ranges[:, 0]
-    cls = np.where(length > 0, 31 - np.floor(np.log2(np.maximum(length, 1))).astype(np.int64), 32)
+    cls = np.full(len(length), 128, np.int64)
+    for t, n in enumerate(length):
+        if n > 0:
+            k = int(n).bit_length() - 1                   # floor(log2 n)
+            next2 = (int(n) >> (k - 2)) & 3 if k >= 2 else ((int(n) & 1) << 1 if k == 1 else 0)
+            cls[t] = 4 * (31 - k) + 3 - next2
     expect = np.lexsort((np.arange(len(length)), cls))
     assert np.array_equal(vb.bins.order.cpu().numpy().view(np.uint32), expect.astype(np.uint32))
 
