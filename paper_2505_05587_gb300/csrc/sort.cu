@@ -155,6 +155,7 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_MAX_BITS = 8;
 constexpr int RS_RADIX_MAX = 1 << RS_MAX_BITS;
 constexpr int SORT_G_MAX = 1024;             // blocks of one pass (= threads of the scan kernel)
+constexpr int kSortPdlMaxRows = 4 << 20;     // dependent launches for sorts of at most this many rows
 constexpr int DEPTH_PASSES = 4;              // 32 depth bits
 constexpr int TILE_PASSES_MAX = 4;           // tile ids < 2^31
 constexpr int EMIT_THREADS = 256;
@@ -605,10 +606,12 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
 // Tile schedule: every tile id once, longest lists first.  Class of a tile:
 // its list length in quarter octaves, 4 clz(length) + 3 - (the two bits below
 // the leading one), 0 .. 127 from the longest lists down, 128 for empty
-// tiles; a stable counting sort by class in one block: class totals, then
-// rounds of 1024 tiles in id order, each ranked within its warp
-// (__match_any_sync) and across warps through per-warp class counts.
+// tiles.  A stable counting sort by class in one block: warp w owns the
+// contiguous tiles [w C, (w + 1) C) and walks them 32 at a time, ranking equal
+// classes with __match_any_sync; per-warp class counts, their prefix in
+// (class, warp) order, then a second walk writes every tile at its place.
 constexpr int TO_THREADS = 1024;
+constexpr int TO_WARPS = TO_THREADS / 32;
 constexpr int TO_CLASSES = 129;
 
 __device__ __forceinline__ int tile_class(uint2 r) {
@@ -622,50 +625,61 @@ __device__ __forceinline__ int tile_class(uint2 r) {
 __global__ void __launch_bounds__(TO_THREADS) tile_order_kernel(const uint2* __restrict__ ranges, int T,
                                                                 uint32_t* __restrict__ order) {
     pdl_wait_and_trigger();
-    __shared__ uint32_t s_base[TO_CLASSES];
-    __shared__ uint32_t s_wcnt[TO_THREADS / 32][TO_CLASSES];
+    __shared__ uint32_t s_cnt[TO_WARPS][TO_CLASSES];
+    __shared__ uint32_t s_tot[TO_CLASSES];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < TO_CLASSES) s_base[threadIdx.x] = 0u;
+    for (int k = threadIdx.x; k < TO_WARPS * TO_CLASSES; k += TO_THREADS) (&s_cnt[0][0])[k] = 0u;
     __syncthreads();
-    for (int t = threadIdx.x; t < T; t += TO_THREADS) atomicAdd(&s_base[tile_class(ranges[t])], 1u);
+    const int C = (T + TO_WARPS - 1) / TO_WARPS;
+    const int lo = warp * C, hi = min(T, lo + C);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int b = lo; b < hi; b += 32) {                  // per-warp class counts
+        const int t = b + lane;
+        const int c = t < hi ? tile_class(ranges[t]) : TO_CLASSES;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        if (c < TO_CLASSES && (peers & lt) == 0u) s_cnt[warp][c] += (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < TO_CLASSES) {
+        uint32_t tot = 0;
+        for (int w = 0; w < TO_WARPS; ++w) tot += s_cnt[w][threadIdx.x];
+        s_tot[threadIdx.x] = tot;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
         for (int c = 0; c < TO_CLASSES; ++c) {
-            const uint32_t n = s_base[c];
-            s_base[c] = run;
+            const uint32_t n = s_tot[c];
+            s_tot[c] = run;
             run += n;
         }
     }
-    for (int r0 = 0; r0 < T; r0 += TO_THREADS) {
-        for (int k = threadIdx.x; k < (TO_THREADS / 32) * TO_CLASSES; k += TO_THREADS) (&s_wcnt[0][0])[k] = 0u;
-        __syncthreads();
-        const int t = r0 + threadIdx.x;
-        const bool valid = t < T;
-        const int c = valid ? tile_class(ranges[t]) : TO_CLASSES;
-        const unsigned peers = __match_any_sync(0xffffffffu, c);
-        const uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
-        if (valid && rank == 0u) s_wcnt[warp][c] = (uint32_t)__popc(peers);
-        __syncthreads();
-        if (threadIdx.x < TO_CLASSES) {                  // prefix over the warps, in warp order
-            uint32_t run = s_base[threadIdx.x];
-            for (int w = 0; w < TO_THREADS / 32; ++w) {
-                const uint32_t n = s_wcnt[w][threadIdx.x];
-                s_wcnt[w][threadIdx.x] = run;
-                run += n;
-            }
-            s_base[threadIdx.x] = run;
+    __syncthreads();
+    if (threadIdx.x < TO_CLASSES) {                     // place of each (class, warp) run
+        uint32_t run = s_tot[threadIdx.x];
+        for (int w = 0; w < TO_WARPS; ++w) {
+            const uint32_t n = s_cnt[w][threadIdx.x];
+            s_cnt[w][threadIdx.x] = run;
+            run += n;
         }
-        __syncthreads();
-        if (valid) order[s_wcnt[warp][c] + rank] = (uint32_t)t;
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int b = lo; b < hi; b += 32) {                  // same walk: write every tile at its place
+        const int t = b + lane;
+        const int c = t < hi ? tile_class(ranges[t]) : TO_CLASSES;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        if (c < TO_CLASSES) order[s_cnt[warp][c] + (uint32_t)__popc(peers & lt)] = (uint32_t)t;
+        __syncwarp();
+        if (c < TO_CLASSES && (peers & lt) == 0u) s_cnt[warp][c] += (uint32_t)__popc(peers);
+        __syncwarp();
     }
 }
 
-static cudaError_t launch_tile_order(const sgs_bins& out, int T, cudaStream_t stream) {
+static cudaError_t launch_tile_order(const sgs_bins& out, int T, bool pdl, cudaStream_t stream) {
     if (!out.order || T <= 0) return cudaGetLastError();
-    (void)launch_pdl(tile_order_kernel, dim3(1), dim3(TO_THREADS), 0, stream,
-                     reinterpret_cast<const uint2*>(out.ranges), T, out.order);
+    (void)launch_pdl_if(pdl, tile_order_kernel, dim3(1), dim3(TO_THREADS), 0, stream,
+                        reinterpret_cast<const uint2*>(out.ranges), T, out.order);
     note_launch();
     return cudaGetLastError();
 }
@@ -771,6 +785,10 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
                             cudaStream_t stream) {
     (void)st;
     const int n = vd.row_off[vd.nv];            // projection rows
+    // dependent launches between the sort's kernels measured faster up to a
+    // few million rows (one view) and slower on the multi-view sorts of tens
+    // of millions of rows, so they are used up to kSortPdlMaxRows
+    const bool pdl = n <= kSortPdlMaxRows;
     const int T = vd.T_total;
     BinWs w = carve_bin_ws(ws, n, out.capacity, T);
     const SortGeom sg = sort_geom(n, out.capacity, T);
@@ -779,7 +797,7 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
     if (e != cudaSuccess) return e;
     if (n == 0) {
         e = cudaMemsetAsync(out.count, 0, sizeof(int32_t), stream);
-        return e != cudaSuccess ? e : launch_tile_order(out, T, stream);
+        return e != cudaSuccess ? e : launch_tile_order(out, T, pdl, stream);
     }
     e = cudaMemsetAsync(w.depth_hist, 0, w.zero_bytes, stream);
     if (e != cudaSuccess) return e;
@@ -796,32 +814,34 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
     // 1. stable sort of the visible rows by depth bits (4 passes of 8 bits; the
     //    first pass drops the rows that touch no tile, the last one also
     //    gathers the rows' tile counts in depth order)
-    (void)launch_pdl(depth_hist_first_kernel, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream, proj.depth,
-                     proj.tiles_touched, n, depth_pass(0));
+    (void)launch_pdl_if(pdl, depth_hist_first_kernel, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream, proj.depth,
+                        proj.tiles_touched, n, depth_pass(0));
     note_launch();
     for (int p = 0; p < DEPTH_PASSES; ++p) {
         const PassDesc ps = depth_pass(p);
         const int src = (p + 1) & 1, dst = p & 1;     // pass 0 -> buffer 0 -> 1 -> 0 -> 1
         if (p > 0) {
-            (void)launch_pdl(pass_hist_kernel, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream, w.dkey[src],
-                             depth_pass(p - 1).tot, RS_RADIX_MAX, ps);
+            (void)launch_pdl_if(pdl, pass_hist_kernel, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream, w.dkey[src],
+                                depth_pass(p - 1).tot, RS_RADIX_MAX, ps);
             note_launch();
         }
-        (void)launch_pdl(pass_scan_kernel, dim3(1 << ps.bits), dim3(SORT_G_MAX), 0, stream, ps.hist, ps.G, ps.tot);
+        (void)launch_pdl_if(pdl, pass_scan_kernel, dim3(1 << ps.bits), dim3(SORT_G_MAX), 0, stream, ps.hist, ps.G,
+                            ps.tot);
         note_launch();
         const bool last = p + 1 == DEPTH_PASSES;
         uint32_t* kout = last ? nullptr : w.dkey[dst];
         if (p == 0)
-            (void)launch_pdl(pass_scatter_kernel<true, false>, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream, nullptr,
-                             nullptr, proj.depth, proj.tiles_touched, n, kout, w.perm[dst], ps, nullptr, nullptr, 1);
+            (void)launch_pdl_if(pdl, pass_scatter_kernel<true, false>, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream,
+                                nullptr, nullptr, proj.depth, proj.tiles_touched, n, kout, w.perm[dst], ps, nullptr,
+                                nullptr, 1);
         else if (!last)
-            (void)launch_pdl(pass_scatter_kernel<false, false>, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream,
-                             w.dkey[src], w.perm[src], nullptr, nullptr, 0, kout, w.perm[dst], ps, nullptr, nullptr,
-                             1);
+            (void)launch_pdl_if(pdl, pass_scatter_kernel<false, false>, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream,
+                                w.dkey[src], w.perm[src], nullptr, nullptr, 0, kout, w.perm[dst], ps, nullptr,
+                                nullptr, 1);
         else
-            (void)launch_pdl(pass_scatter_kernel<false, true>, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream,
-                             w.dkey[src], w.perm[src], nullptr, proj.tiles_touched, 0, kout, w.perm[dst], ps, w.cnt,
-                             w.esum, sg.G_emit);
+            (void)launch_pdl_if(pdl, pass_scatter_kernel<false, true>, dim3(sg.G_depth), dim3(RS_THREADS), 0, stream,
+                                w.dkey[src], w.perm[src], nullptr, proj.tiles_touched, 0, kout, w.perm[dst], ps,
+                                w.cnt, w.esum, sg.G_emit);
         note_launch();
     }
     const uint32_t* perm = w.perm[(DEPTH_PASSES - 1) & 1];
@@ -837,7 +857,7 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
         gv[0] = w.inst_gid_tmp;
         gv[1] = out.gids;
     }
-    (void)launch_pdl(emit_offsets_kernel, dim3(1), dim3(SORT_G_MAX), 0, stream, w.esum, sg.G_emit, out.count);
+    (void)launch_pdl_if(pdl, emit_offsets_kernel, dim3(1), dim3(SORT_G_MAX), 0, stream, w.esum, sg.G_emit, out.count);
     note_launch();
     {
         NextHist nh = none;
@@ -845,9 +865,9 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
             const PassDesc q = tile_pass(0);
             nh = NextHist{q.shift, q.bits, q.hist, q.G};
         }
-        (void)launch_pdl(emit_kernel, dim3(sg.G_emit), dim3(EMIT_THREADS), 0, stream, perm, w.cnt,
-                         reinterpret_cast<const short4*>(proj.rect), w.depth_tot, vd, out.capacity, w.esum, sg.G_emit,
-                         out.count, gk[0], gv[0], nh);
+        (void)launch_pdl_if(pdl, emit_kernel, dim3(sg.G_emit), dim3(EMIT_THREADS), 0, stream, perm, w.cnt,
+                            reinterpret_cast<const short4*>(proj.rect), w.depth_tot, vd, out.capacity, w.esum,
+                            sg.G_emit, out.count, gk[0], gv[0], nh);
         note_launch();
     }
     // 3. stable passes over the written instances by tile id (the first
@@ -856,28 +876,30 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
         const PassDesc ps = tile_pass(p);
         if (p > 0) {
             const PassDesc q = tile_pass(p - 1);
-            (void)launch_pdl(pass_hist_kernel, dim3(sg.G_tile), dim3(RS_THREADS), 0, stream, gk[p & 1], q.tot,
-                             1 << q.bits, ps);
+            (void)launch_pdl_if(pdl, pass_hist_kernel, dim3(sg.G_tile), dim3(RS_THREADS), 0, stream, gk[p & 1], q.tot,
+                                1 << q.bits, ps);
             note_launch();
         }
-        (void)launch_pdl(pass_scan_kernel, dim3(1 << ps.bits), dim3(SORT_G_MAX), 0, stream, ps.hist, ps.G, ps.tot);
+        (void)launch_pdl_if(pdl, pass_scan_kernel, dim3(1 << ps.bits), dim3(SORT_G_MAX), 0, stream, ps.hist, ps.G,
+                            ps.tot);
         note_launch();
-        (void)launch_pdl(pass_scatter_kernel<false, false>, dim3(sg.G_tile), dim3(RS_THREADS), 0, stream, gk[p & 1],
-                         gv[p & 1], nullptr, nullptr, 0, gk[(p + 1) & 1], gv[(p + 1) & 1], ps, nullptr, nullptr, 1);
+        (void)launch_pdl_if(pdl, pass_scatter_kernel<false, false>, dim3(sg.G_tile), dim3(RS_THREADS), 0, stream,
+                            gk[p & 1], gv[p & 1], nullptr, nullptr, 0, gk[(p + 1) & 1], gv[(p + 1) & 1], ps, nullptr,
+                            nullptr, 1);
         note_launch();
     }
     const uint32_t* tile_sorted = gk[tc.passes & 1];
     // 4. per-tile ranges and optional 64-bit keys
     const int rb = 152 * 8;
-    (void)launch_pdl(ranges_kernel, dim3(rb), dim3(256), 0, stream, tile_sorted, out.count, out.capacity,
-                     reinterpret_cast<uint2*>(out.ranges));
+    (void)launch_pdl_if(pdl, ranges_kernel, dim3(rb), dim3(256), 0, stream, tile_sorted, out.count, out.capacity,
+                        reinterpret_cast<uint2*>(out.ranges));
     note_launch();
     if (out.keys) {
-        (void)launch_pdl(keys_kernel, dim3(rb), dim3(256), 0, stream, tile_sorted, out.gids, proj.depth, out.count,
-                         out.capacity, out.keys);
+        (void)launch_pdl_if(pdl, keys_kernel, dim3(rb), dim3(256), 0, stream, tile_sorted, out.gids, proj.depth,
+                            out.count, out.capacity, out.keys);
         note_launch();
     }
-    return launch_tile_order(out, T, stream);
+    return launch_tile_order(out, T, pdl, stream);
 }
 
 }  // namespace sgs
