@@ -208,3 +208,62 @@ class FusedIterationGraph:
                 if M > vb.bins.capacity:
                     raise RuntimeError(f"a view needs {M} instances, its buffers hold {vb.bins.capacity}: "
                                        "run fused_iteration eagerly to grow them and capture again")
+
+
+class PrefetchedIterations:
+    """Fused iterations fed from page-locked host memory with the inputs of
+    iteration k + 1 copied (on a copy stream) while iteration k computes: two
+    device copies of the parameters and the targets, one captured graph for
+    each, and events that order every copy after the last iteration that read
+    its buffers and every iteration after its own copy.  The views' and the
+    densification buffers are shared (the iterations run in order on one
+    stream); each iteration's loss and split count are read back to host.
+
+    run(host_params, host_targets, k_steps) -> (loss[k], n_out[k]) host arrays;
+    host_params / host_targets: per iteration, or one set reused."""
+
+    def __init__(self, g: B.GaussianTensors, views: list[ViewBuffers], targets: list[torch.Tensor],
+                 db: DensifyBuffers, **kw):
+        self.sets = [(g, targets)]
+        g2 = B.GaussianTensors(*[t.clone() for t in g.tensors()], g.sh_degree)
+        self.sets.append((g2, [t.clone() for t in targets]))
+        self.graphs = [FusedIterationGraph(gs, views, ts, db, **kw) for gs, ts in self.sets]
+        self.db = db
+        dev = g.means.device
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.copied = [torch.cuda.Event(), torch.cuda.Event()]
+        self.done = [torch.cuda.Event(), torch.cuda.Event()]
+        self.loss_host = torch.empty(2, dtype=torch.float32).pin_memory()
+        self.nout_host = torch.empty(2, dtype=torch.int32).pin_memory()
+
+    def _copy(self, s: int, params_host, targets_host, after_done: bool):
+        gs, ts = self.sets[s]
+        with torch.cuda.stream(self.copy_stream):
+            if after_done:
+                self.copy_stream.wait_event(self.done[s])       # the buffers' last reader finished
+            for dst, src in zip(gs.tensors(), params_host):
+                dst.copy_(src, non_blocking=True)
+            for dst, src in zip(ts, targets_host):
+                dst.copy_(src, non_blocking=True)
+            self.copied[s].record(self.copy_stream)
+
+    def run(self, host_params, host_targets, k_steps: int, stream=None):
+        """Issues k_steps iterations; returns the pinned per-iteration loss and
+        split count arrays (valid once `stream` has been synchronised)."""
+        stream = as_stream(stream)
+        per_step = isinstance(host_params[0], (list, tuple))
+        pick = (lambda seq, k: seq[k]) if per_step else (lambda seq, k: seq)
+        loss = torch.empty(k_steps, dtype=torch.float32).pin_memory()
+        nout = torch.empty(k_steps, dtype=torch.int32).pin_memory()
+        self._copy(0, pick(host_params, 0), pick(host_targets, 0), after_done=False)
+        for k in range(k_steps):
+            s = k & 1
+            if k + 1 < k_steps:
+                self._copy(1 - s, pick(host_params, k + 1), pick(host_targets, k + 1), after_done=k >= 1)
+            stream.wait_event(self.copied[s])
+            with torch.cuda.stream(stream):
+                self.graphs[s].replay()
+                loss[k:k + 1].copy_(self.db.loss, non_blocking=True)
+                nout[k:k + 1].copy_(self.db.n_out, non_blocking=True)
+            self.done[s].record(stream)
+        return loss, nout

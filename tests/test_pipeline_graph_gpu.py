@@ -94,3 +94,26 @@ def test_zero_on_a_side_stream_orders_with_the_calls():
     PL.fused_iteration(g, views, tg, db, eps_split=-1e-7)
     torch.cuda.synchronize()
     assert _rel(ref, db.S) < 1e-5
+
+
+def test_prefetched_iterations_match_eager_ones():
+    """Streamed iterations (inputs of k + 1 copied during k) give each
+    iteration's loss and split count as the eager calls on the same inputs."""
+    g, views, tg, db = _setup()
+    host_sets, host_tgts, ref = [], [], []
+    for k in range(4):                                # four different parameter sets
+        gk = B.GaussianTensors(*[t.clone() for t in g.tensors()], g.sh_degree)
+        with torch.no_grad():
+            gk.means.add_(0.003 * k)
+            gk.opacity_logit.mul_(1.0 - 0.05 * k)
+        PL.fused_iteration(gk, views, tg, db, eps_split=-1e-7)
+        torch.cuda.synchronize()
+        ref.append((float(db.loss.item()), int(db.n_out.item())))
+        host_sets.append([t.cpu().pin_memory() for t in gk.tensors()])
+        host_tgts.append([t.cpu().pin_memory() for t in tg])
+    pre = PL.PrefetchedIterations(g, views, tg, db, eps_split=-1e-7)
+    loss, nout = pre.run(host_sets, host_tgts, 4)
+    torch.cuda.synchronize()
+    for k in range(4):
+        assert abs(float(loss[k]) - ref[k][0]) <= 1e-5 * abs(ref[k][0])
+        assert abs(int(nout[k]) - ref[k][1]) <= 2
