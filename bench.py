@@ -189,16 +189,21 @@ def run_gpu(args):
     M = B.check_count(int(vb.bins.count.item()))
     n_out = int(db.n_out.item())
 
-    loss_name = "l1_loss_grad" if args.lambda_dssim is None else "ssim_l1_loss_grad"
-    names = ["zero_accumulators", "project", "bin_sort", "render_fwd", loss_name,
-             "render_bwd_with_splitting", "densify_split"]
+    if args.lambda_dssim is None:                      # the L1 loss fused into the forward kernel
+        fwd_names = ["render_fwd_l1"]
+        fwd_calls = [lambda s: B.render_fwd_l1(vb.proj, vb.bins, cam, st, target, 1, vb.image, vb.final_T,
+                                               vb.n_contrib, vb.dL, db.loss, s)]
+    else:
+        fwd_names = ["render_fwd", "ssim_l1_loss_grad"]
+        fwd_calls = [lambda s: B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib, s),
+                     lambda s: vb.loss_grad(target, 1, db.loss, args.lambda_dssim, s)]
+    names = ["zero_accumulators", "project", "bin_sort", *fwd_names, "render_bwd_with_splitting", "densify_split"]
     NC = len(names)
     calls = [
         lambda s: db.zero_(grads=False, stream=s),     # S and loss; the backward overwrites the gradients
         lambda s: B.project(g, cam, st, vb.proj, s),
         lambda s: B.bin_sort(vb.proj, g.n, cam, st, vb.bins, vb.sort_ws, s),
-        lambda s: B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib, s),
-        lambda s: vb.loss_grad(target, 1, db.loss, args.lambda_dssim, s),
+        *fwd_calls,
         lambda s: B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, vb.dL,
                                               db.grads, db.S, db.bwd_ws, s, accumulate=False, S_po=db.S_po,
                                               S_ls=db.S_ls),
@@ -319,7 +324,7 @@ def run_gpu(args):
     T = B.num_tiles(cam, st)
     P = WIDTH * HEIGHT
     alg_bytes = algorithmic_bytes(N_GAUSS, M, P, T)
-    if names[dom] == "render_fwd":
+    if names[dom] in ("render_fwd", "render_fwd_l1"):
         achieved = flops_fwd / (call_ms[dom] * 1e-3) / 1e12
     else:
         dom = names.index("render_bwd_with_splitting")

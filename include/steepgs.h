@@ -202,6 +202,15 @@ int sgs_render_fwd(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera 
                    const sgs_settings *st, float *image, float *final_T, uint32_t *n_contrib,
                    void *stream);
 
+/* sgs_render_fwd and sgs_l1_loss_grad in one kernel (the loss in the
+ * compositing epilogue): the same image, final_T and n_contrib, dL_dimage
+ * [H,W,3] = sign(image - target) / (3 H W n_views) bit for bit, and loss +=
+ * mean |image - target| / n_views (summed per tile, one atomic each, so the
+ * float sum may round differently from sgs_l1_loss_grad's). */
+int sgs_render_fwd_l1(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
+                      const sgs_settings *st, const float *target, int32_t n_views, float *image,
+                      float *final_T, uint32_t *n_contrib, float *dL_dimage, float *loss, void *stream);
+
 /* Pair counts of the forward walk (a measurement aid, not on the path):
  * counts [H,W,2] uint32 = (pairs evaluated, pairs composited) per pixel, the
  * work units behind the rasteriser's algorithmic FLOP count. */

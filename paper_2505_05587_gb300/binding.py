@@ -94,6 +94,7 @@ def lib():
         L.sgs_bin_sort_workspace_size.argtypes = [I32, I64, I32, C.POINTER(SZ)]
         L.sgs_bin_sort.argtypes = [P, I32, P, P, P, P, SZ, P]
         L.sgs_render_fwd.argtypes = [P, P, P, P, P, P, P, P]
+        L.sgs_render_fwd_l1.argtypes = [P, P, P, P, P, I32, P, P, P, P, P, P]
         L.sgs_l1_loss_grad.argtypes = [P, P, I32, I32, I32, P, P, P]
         L.sgs_render_stats.argtypes = [P, P, P, P, P, P]
         L.sgs_render_bwd_workspace_size.argtypes = [I32, C.POINTER(SZ)]
@@ -289,6 +290,15 @@ def render_fwd(proj: ProjBuffers, bins: BinBuffers, cam, st, image, final_T, n_c
     pc, bc, cc, sc = proj.c(), bins.c(), camera_c(cam), settings_c(st)
     _check("sgs_render_fwd", lib().sgs_render_fwd(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc), _p(image),
                                                    _p(final_T), _p(n_contrib), _stream(stream)))
+
+
+def render_fwd_l1(proj: ProjBuffers, bins: BinBuffers, cam, st, target, n_views: int, image, final_T, n_contrib,
+                  dL_dimage, loss, stream=None):
+    """render_fwd with the L1 loss and its gradient in the same kernel."""
+    pc, bc, cc, sc = proj.c(), bins.c(), camera_c(cam), settings_c(st)
+    _check("sgs_render_fwd_l1", lib().sgs_render_fwd_l1(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
+                                                         _p(target), int(n_views), _p(image), _p(final_T),
+                                                         _p(n_contrib), _p(dL_dimage), _p(loss), _stream(stream)))
 
 
 def render_stats(proj: ProjBuffers, bins: BinBuffers, cam, st, counts, stream=None):

@@ -176,7 +176,17 @@ int sgs_render_fwd(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera*
         !tiles_fit(cam, st) || !bins->ranges)
         return SGS_ERR_INVALID_ARG;
     return cuda_status(launch_render_fwd(*proj, *bins, make_cam(*cam, *st), make_set(*st), image, final_T,
-                                         n_contrib, (cudaStream_t)stream));
+                                         n_contrib, nullptr, 1, nullptr, nullptr, (cudaStream_t)stream));
+}
+
+int sgs_render_fwd_l1(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,
+                      const float* target, int32_t n_views, float* image, float* final_T, uint32_t* n_contrib,
+                      float* dL_dimage, float* loss, void* stream) {
+    if (!proj || !bins || !valid_cam(cam) || !valid_settings(st) || !image || !final_T || !n_contrib ||
+        !tiles_fit(cam, st) || !bins->ranges || !target || n_views <= 0 || !dL_dimage || !loss)
+        return SGS_ERR_INVALID_ARG;
+    return cuda_status(launch_render_fwd(*proj, *bins, make_cam(*cam, *st), make_set(*st), image, final_T,
+                                         n_contrib, target, n_views, dL_dimage, loss, (cudaStream_t)stream));
 }
 
 int sgs_render_stats(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,

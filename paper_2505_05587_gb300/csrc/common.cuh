@@ -157,9 +157,10 @@ size_t bin_sort_ws_bytes(int n, int64_t capacity, int num_tiles);
 cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetDev& st, const sgs_bins& out, void* ws,
                             cudaStream_t stream);
 
+// target != null: the L1 loss is fused into the epilogue (dL overwritten, loss +=).
 cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
                               const SetDev& st, float* image, float* final_T, uint32_t* n_contrib,
-                              cudaStream_t stream);
+                              const float* target, int n_views, float* dL, float* loss, cudaStream_t stream);
 // Zeroes the 16-float accumulator rows (and the higher-moment rows when
 // g2d_hi is not null) of the Gaussians with tiles_touched > 0.
 cudaError_t launch_zero_reached_rows(const uint32_t* tiles, int n, float* g2d, float* g2d_hi, cudaStream_t stream);

@@ -105,6 +105,16 @@ struct FwdSmem {
     float4 rgb[BATCH];
     float4 box[BATCH];
     uint8_t list[NW][BATCH];
+    float l1_part[NW];
+};
+
+// L1 loss fused into the forward epilogue: dL = sign(C - target) norm,
+// loss += norm sum |C - target|, norm = 1 / (3 H W n_views).
+struct L1Out {
+    const float* target;
+    float* dL;
+    float* loss;
+    float norm;
 };
 
 template <int BATCH, int NW>
@@ -125,7 +135,7 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
                                          const float4* __restrict__ xy, const float4* __restrict__ conic_opac,
                                          const float4* __restrict__ rgb, const SetDev& st, float* __restrict__ image,
                                          float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
-                                         FwdSmem<BATCH, TW * TH / 32>& sm) {
+                                         FwdSmem<BATCH, TW * TH / 32>& sm, const L1Out* l1 = nullptr) {
     constexpr int BS = TW * TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int bx, by;
@@ -178,13 +188,33 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
             last = (uint32_t)(base + j + 1);
         }
     }
+    float l1_sum = 0.0f;
     if (inside) {
         const int pix = py * W + px;
-        image[3 * pix] = C0 + T * st.bg[0];
-        image[3 * pix + 1] = C1 + T * st.bg[1];
-        image[3 * pix + 2] = C2 + T * st.bg[2];
+        const float c[3] = {C0 + T * st.bg[0], C1 + T * st.bg[1], C2 + T * st.bg[2]};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) image[3 * pix + ch] = c[ch];
         final_T[pix] = T;
         n_contrib[pix] = last;
+        if (l1) {                                   // the L1 loss and its gradient at this pixel
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float r = c[ch] - l1->target[3 * pix + ch];
+                l1_sum += fabsf(r);
+                l1->dL[3 * pix + ch] = r > 0.0f ? l1->norm : (r < 0.0f ? -l1->norm : 0.0f);
+            }
+        }
+    }
+    if (l1) {                                       // one atomic per tile for the loss
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l1_sum += __shfl_xor_sync(0xffffffffu, l1_sum, o);
+        if (lane == 0) sm.l1_part[warp] = l1_sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int w = 0; w < BS / 32; ++w) t += sm.l1_part[w];
+            if (t != 0.0f) atomicAdd(l1->loss, t * l1->norm);
+        }
     }
     __syncthreads();        // shared memory is reused by the next tile
 }
@@ -354,16 +384,17 @@ cudaError_t launch_zero_reached_rows(const uint32_t* tiles, int n, float* g2d, f
 // per SM (40 registers): its per-pixel chain is latency-bound and gains from
 // the extra warps more than it loses to the two spilled words.
 // ---------------------------------------------------------------------------
-template <int TW, int TH>
+template <int TW, int TH, bool L1>
 __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) render_fwd_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
     float* __restrict__ image, float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
-    const uint32_t* __restrict__ order) {
+    const uint32_t* __restrict__ order, L1Out l1) {
     pdl_wait_and_trigger();
     __shared__ FwdSmem<TW * TH, TW * TH / 32> sm;
     const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
-    fwd_tile<TW, TH, TW * TH>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, image, final_T, n_contrib, sm);
+    fwd_tile<TW, TH, TW * TH>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, image, final_T, n_contrib, sm,
+                              L1 ? &l1 : nullptr);
 }
 
 // The backward kernels are bounded to 40 resident warps per SM (48 registers):
@@ -509,12 +540,14 @@ static cudaError_t stats_tmpl(const sgs_proj& proj, const sgs_bins& bins, const 
 
 template <int TW, int TH>
 static cudaError_t fwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
-                            float* image, float* final_T, uint32_t* n_contrib, cudaStream_t stream) {
+                            float* image, float* final_T, uint32_t* n_contrib, const L1Out& l1,
+                            cudaStream_t stream) {
     const int T = cam.gx * cam.gy;
-    (void)launch_pdl(render_fwd_kernel<TW, TH>, dim3(T), dim3(TW * TH), 0, stream,
+    (void)launch_pdl(l1.target ? render_fwd_kernel<TW, TH, true> : render_fwd_kernel<TW, TH, false>, dim3(T),
+                     dim3(TW * TH), 0, stream,
                      reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
                      reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
-                     cam.width, cam.height, cam.gx, st, image, final_T, n_contrib, bins.order);
+                     cam.width, cam.height, cam.gx, st, image, final_T, n_contrib, bins.order, l1);
     note_launch();
     return cudaGetLastError();
 }
@@ -546,8 +579,12 @@ cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, cons
 }
 
 cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
-                              float* image, float* final_T, uint32_t* n_contrib, cudaStream_t stream) {
-    SGS_TILE_DISPATCH(fwd_tmpl, proj, bins, cam, st, image, final_T, n_contrib, stream)
+                              float* image, float* final_T, uint32_t* n_contrib, const float* target, int n_views,
+                              float* dL, float* loss, cudaStream_t stream) {
+    L1Out l1{target, dL, loss, 0.0f};
+    if (target)
+        l1.norm = (float)(1.0 / (3.0 * (double)cam.height * (double)cam.width * (double)n_views));
+    SGS_TILE_DISPATCH(fwd_tmpl, proj, bins, cam, st, image, final_T, n_contrib, l1, stream)
 }
 
 cudaError_t launch_render_bwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,

@@ -164,8 +164,12 @@ def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: lis
     V = len(views)
     for k, (vb, tgt) in enumerate(zip(views, targets)):
         project_and_sort(g, vb, stream, check_capacity)
-        B.render_fwd(vb.proj, vb.bins, vb.cam, vb.st, vb.image, vb.final_T, vb.n_contrib, stream)
-        vb.loss_grad(tgt, V, db.loss, lambda_dssim, stream)
+        if lambda_dssim is None:                    # L1: the loss is fused into the forward kernel
+            B.render_fwd_l1(vb.proj, vb.bins, vb.cam, vb.st, tgt, V, vb.image, vb.final_T, vb.n_contrib, vb.dL,
+                            db.loss, stream)
+        else:
+            B.render_fwd(vb.proj, vb.bins, vb.cam, vb.st, vb.image, vb.final_T, vb.n_contrib, stream)
+            vb.loss_grad(tgt, V, db.loss, lambda_dssim, stream)
         # the first view overwrites the gradients, later views add to them
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, vb.cam, vb.st, vb.final_T, vb.n_contrib, vb.dL,
                                     db.grads, db.S, db.bwd_ws, stream, accumulate=k > 0, S_po=db.S_po,

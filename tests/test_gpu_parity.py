@@ -420,3 +420,25 @@ def test_results_do_not_depend_on_the_tile_order():
     assert _rel(a[2], b[2]) < 1e-5
     for x, y in zip(a[3], b[3]):
         assert _rel(x, y) < 1e-5
+
+
+@pytest.mark.parametrize("name,mk_scene,mk_cam,st", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_forward_with_fused_l1_equals_forward_then_l1(name, mk_scene, mk_cam, st):
+    """render_fwd_l1: image, final_T, n_contrib and dL bit for bit as
+    render_fwd followed by l1_loss_grad; the loss to float summation order."""
+    scene, cam = mk_scene(), mk_cam()
+    _, vb, _ = _gpu_view(scene, cam, st)
+    tgt = torch.as_tensor(synth.target_image(4, cam.height, cam.width)).cuda()
+    B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib)
+    dL1 = torch.empty_like(vb.image)
+    loss1 = torch.zeros(1, device="cuda")
+    B.l1_loss_grad(vb.image, tgt, 2, dL1, loss1)
+    ref = (vb.image.clone(), vb.final_T.clone(), vb.n_contrib.clone())
+    dL2 = torch.full_like(vb.image, 7.0)
+    loss2 = torch.full((1,), 0.25, device="cuda")
+    img = torch.full_like(vb.image, -1.0)
+    B.render_fwd_l1(vb.proj, vb.bins, cam, st, tgt, 2, img, vb.final_T, vb.n_contrib, dL2, loss2)
+    torch.cuda.synchronize()
+    assert torch.equal(img, ref[0]) and torch.equal(vb.final_T, ref[1]) and torch.equal(vb.n_contrib, ref[2])
+    assert torch.equal(dL2, dL1)
+    assert abs(float(loss2.item()) - 0.25 - float(loss1.item())) <= 1e-6 * float(loss1.item()) + 1e-9
