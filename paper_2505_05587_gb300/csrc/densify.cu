@@ -406,22 +406,65 @@ __global__ void __launch_bounds__(256) eig_triage_kernel(const float* __restrict
     if (nz) work[s_base + s_cnt[warp] + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
 }
 
-// Minimum eigenpair and flag of every matrix over the position (root formula).
+// Minimum eigenpair and flag of every matrix over the position (root
+// formula).  A zero matrix (a Gaussian no pixel reached) gets (0, e_0), what
+// the formula returns for it; the block's non-zero matrices are first packed
+// into its leading threads through shared memory, so that the solve runs in
+// full warps.
 __global__ void __launch_bounds__(256) eig_direct_kernel(const float* __restrict__ S, int n, float inv_T,
                                                          float eps_split, const float* __restrict__ grad_norm,
                                                          float eps_grad, float* __restrict__ lam_out,
                                                          float* __restrict__ v_out, uint32_t* __restrict__ flags) {
     pdl_wait_and_trigger();
+    __shared__ float s_m[256][7];                     // packed matrices (6 floats, padded)
+    __shared__ int s_idx[256];
+    __shared__ uint32_t s_wcnt[8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float s6[6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float s6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool nz = false;
+    if (i < n) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) s6[k] = S[(size_t)i * 6 + k];
-    const Eig e = eig3_min(s6, inv_T);
-    lam_out[i] = e.lam;
+        for (int k = 0; k < 6; ++k) {
+            s6[k] = S[(size_t)i * 6 + k];
+            nz |= s6[k] != 0.0f;
+        }
+        if (!nz) {
+            lam_out[i] = 0.0f;
+            v_out[3 * (size_t)i] = 1.0f;
+            v_out[3 * (size_t)i + 1] = 0.0f;
+            v_out[3 * (size_t)i + 2] = 0.0f;
+            write_flag(i, 0.0f, eps_split, grad_norm, eps_grad, flags);
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, nz);
+    if (lane == 0) s_wcnt[warp] = (uint32_t)__popc(m);
+    __syncthreads();
+    uint32_t before = 0, count = 0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v_out[3 * (size_t)i + k] = e.v[k];
-    write_flag(i, e.lam, eps_split, grad_norm, eps_grad, flags);
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t c = s_wcnt[w];
+        before += w < warp ? c : 0u;
+        count += c;
+    }
+    if (nz) {
+        const uint32_t slot = before + (uint32_t)__popc(m & ((1u << lane) - 1u));
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s_m[slot][k] = s6[k];
+        s_idx[slot] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x < count) {
+        float a6[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a6[k] = s_m[threadIdx.x][k];
+        const int j = s_idx[threadIdx.x];
+        const Eig e = eig3_min(a6, inv_T);
+        lam_out[j] = e.lam;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v_out[3 * (size_t)j + k] = e.v[k];
+        write_flag(j, e.lam, eps_split, grad_norm, eps_grad, flags);
+    }
 }
 
 // Minimum eigenpair and flag of the listed (non-zero) matrices.

@@ -563,7 +563,7 @@ __device__ __forceinline__ void geometry_adjoint(const CamDev& cam, float p0, fl
 // MULTI = false is the single-view case: no view loop, and the SH gradient
 // increments overwrite the staged coefficients once they have been used.
 template <int DEG, bool MULTI, bool PO, bool LS>
-__global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 6)) project_bwd_kernel(
+__global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 7)) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ sh, int n, ViewsDev vd, const float4* __restrict__ conic_opac,
     const uint32_t* __restrict__ tiles, const float* __restrict__ g2d, const float* __restrict__ g2d_hi,
