@@ -332,6 +332,11 @@ int sgs_render_batch_fwd(const sgs_gaussians *scenes, const sgs_camera *cams, in
  * G <- G + grad).  step >= 1. */
 int sgs_adam_step(float *param, const float *grad, float *m, float *v, int64_t count, float lr, float beta1,
                   float beta2, float eps, int32_t step, float *grad_accum, void *stream);
+/* The same update with the step count read from device memory (d_step, one
+ * int32 >= 1 when the kernel runs), so that a captured graph can replay it
+ * while the caller advances the count on the device. */
+int sgs_adam_step_dev(float *param, const float *grad, float *m, float *v, int64_t count, float lr, float beta1,
+                      float beta2, float eps, const int32_t *d_step, float *grad_accum, void *stream);
 
 /* Workspace bytes for sgs_densify_split with n Gaussians. */
 int sgs_densify_split_workspace_size(int32_t n, size_t *bytes);

@@ -110,6 +110,7 @@ def lib():
         L.sgs_render_batch_fwd.argtypes = [P, P, I32, P, I32, P, P, I64, P, SZ, P]
         L.sgs_render_batch_fwd.restype = C.c_int
         L.sgs_adam_step.argtypes = [P, P, P, P, I64, F, F, F, F, I32, P, P]
+        L.sgs_adam_step_dev.argtypes = [P, P, P, P, I64, F, F, F, F, P, P, P]
         L.sgs_adam_step.restype = C.c_int
         L.sgs_ssim_l1_workspace_size.argtypes = [I32, I32, C.POINTER(SZ)]
         L.sgs_ssim_l1_workspace_size.restype = C.c_int
@@ -413,6 +414,13 @@ def adam_step(param, grad, m, v, lr: float, step: int, beta1=0.9, beta2=0.999, e
     """In-place Adam update of one float32 parameter tensor."""
     _check("sgs_adam_step", lib().sgs_adam_step(_p(param), _p(grad), _p(m), _p(v), param.numel(), lr, beta1, beta2,
                                                  eps, step, _p(grad_accum), _stream(stream)))
+
+
+def adam_step_dev(param, grad, m, v, lr: float, d_step, beta1=0.9, beta2=0.999, eps=1e-8, grad_accum=None,
+                  stream=None):
+    """adam_step with the step count read from the device int32 tensor d_step."""
+    _check("sgs_adam_step_dev", lib().sgs_adam_step_dev(_p(param), _p(grad), _p(m), _p(v), param.numel(), lr, beta1,
+                                                         beta2, eps, _p(d_step), _p(grad_accum), _stream(stream)))
 
 
 def densify_split_workspace_size(n: int) -> int:

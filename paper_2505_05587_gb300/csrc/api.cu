@@ -273,7 +273,17 @@ int sgs_adam_step(float* param, const float* grad, float* m, float* v, int64_t c
         !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
         return SGS_ERR_INVALID_ARG;
     if (count > 0 && (!param || !grad || !m || !v)) return SGS_ERR_INVALID_ARG;
-    return cuda_status(launch_adam(param, grad, m, v, count, lr, beta1, beta2, eps, step, grad_accum,
+    return cuda_status(launch_adam(param, grad, m, v, count, lr, beta1, beta2, eps, step, nullptr, grad_accum,
+                                   (cudaStream_t)stream));
+}
+
+int sgs_adam_step_dev(float* param, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
+                      float beta2, float eps, const int32_t* d_step, float* grad_accum, void* stream) {
+    if (count < 0 || !d_step || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return SGS_ERR_INVALID_ARG;
+    if (count > 0 && (!param || !grad || !m || !v)) return SGS_ERR_INVALID_ARG;
+    return cuda_status(launch_adam(param, grad, m, v, count, lr, beta1, beta2, eps, 1, d_step, grad_accum,
                                    (cudaStream_t)stream));
 }
 

@@ -190,7 +190,7 @@ cudaError_t launch_l1(const float* image, const float* target, int H, int W, int
                       float* dL, float* loss, cudaStream_t stream);
 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, float lr, float b1, float b2,
-                        float eps, int step, float* G, cudaStream_t stream);
+                        float eps, int step, const int32_t* d_step, float* G, cudaStream_t stream);
 
 size_t densify_ws_bytes(int n);
 cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float* S_po, const float* S_ls, float inv_T,

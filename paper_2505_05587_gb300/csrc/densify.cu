@@ -771,8 +771,13 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
 __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, const float* __restrict__ g,
                                                    float* __restrict__ m, float* __restrict__ v, int64_t count,
                                                    float lr, float b1, float b2, float eps, float bc1, float bc2,
-                                                   float* __restrict__ G) {
+                                                   float* __restrict__ G, const int32_t* __restrict__ d_step) {
     pdl_wait_and_trigger();
+    if (d_step) {                                    // step count from device memory (graph replays)
+        const float t = (float)*d_step;
+        bc1 = 1.0f - powf(b1, t);
+        bc2 = 1.0f - powf(b2, t);
+    }
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
          k += (int64_t)gridDim.x * blockDim.x) {
         const float gk = g[k];
@@ -786,13 +791,14 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, const 
 }
 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, float lr, float b1, float b2,
-                        float eps, int step, float* G, cudaStream_t stream) {
+                        float eps, int step, const int32_t* d_step, float* G, cudaStream_t stream) {
     if (count == 0) return cudaSuccess;
-    const float bc1 = 1.0f - powf(b1, (float)step), bc2 = 1.0f - powf(b2, (float)step);
+    const float bc1 = d_step ? 1.0f : 1.0f - powf(b1, (float)step);
+    const float bc2 = d_step ? 1.0f : 1.0f - powf(b2, (float)step);
     int64_t blocks = (count + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     (void)launch_pdl(adam_kernel, dim3((int)blocks), dim3(256), 0, stream, p, g, m, v, count, lr, b1, b2, eps, bc1,
-                     bc2, G);
+                     bc2, G, d_step);
     note_launch();
     return cudaGetLastError();
 }

@@ -80,10 +80,20 @@ class TrainConfig:
     #                                    (position, log-scales, opacity) (7)
     lambda_dssim: float | None = None  # loss (1 - l) L1 + l (1 - SSIM) when set, else L1
     log_every: int = 10
+    graphs: bool = True                # each training step replayed as captured CUDA graphs (else autograd)
 
 
 class SteepGSTrainer:
-    """Algorithm 1 on one GPU: one view per step (cycled), L1 loss, Adam."""
+    """Algorithm 1 on one GPU: one view per step (cycled), L1 loss, Adam.
+
+    With cfg.graphs (the default) a step is two captured CUDA graphs per view:
+    (projection, binning) and (forward with the loss, backward with the
+    splitting accumulators, Adam on every parameter, the device step count);
+    between them the view's instance count is read back, and when it
+    outgrows the buffers they grow and the graphs are captured again, so no
+    step runs on truncated lists.  The graphs are captured again after every
+    densification (the number of Gaussians changes).  Without graphs a step
+    runs through the autograd Function above."""
 
     def __init__(self, g: B.GaussianTensors, cams, targets: list[torch.Tensor], st, cfg: TrainConfig):
         self.cams, self.targets, self.st, self.cfg = cams, targets, st, cfg
@@ -94,6 +104,7 @@ class SteepGSTrainer:
         self.m = [torch.zeros_like(p) for p in self.params]
         self.v = [torch.zeros_like(p) for p in self.params]
         self.adam_t = 0
+        self.step_graphs = None
 
     def _alloc(self, n: int):
         dev = self.params[0].device
@@ -118,8 +129,69 @@ class SteepGSTrainer:
     def gaussians(self) -> B.GaussianTensors:
         return B.GaussianTensors(*[p.detach() for p in self.params], self.sh_degree)
 
+    def _capture(self):
+        """Captures the (projection, binning) and (forward, loss, backward,
+        Adam) graphs of every view for the current buffers."""
+        cfg = self.cfg
+        dev = self.params[0].device
+        g = self.gaussians()
+        self.grads = B.GaussianTensors.empty(g.n, self.sh_degree, dev)
+        self.d_step = torch.full((1,), self.adam_t, dtype=torch.int32, device=dev)
+        for vb in self.views:                       # size the instance buffers (no side effects)
+            PL.project_and_sort(g, vb)
+        torch.cuda.synchronize()
+        cs = torch.cuda.Stream(device=dev)
+        self.step_graphs = []
+        for k, vb in enumerate(self.views):
+            ga, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+            with torch.cuda.graph(ga, stream=cs):
+                PL.project_and_sort(g, vb, cs, check_capacity=False)
+            with torch.cuda.graph(gb, stream=cs):
+                self.loss.zero_()
+                if cfg.lambda_dssim is None:
+                    B.render_fwd_l1(vb.proj, vb.bins, vb.cam, vb.st, self.targets[k], 1, vb.image, vb.final_T,
+                                    vb.n_contrib, self.dL[k], self.loss, cs)
+                else:
+                    B.render_fwd(vb.proj, vb.bins, vb.cam, vb.st, vb.image, vb.final_T, vb.n_contrib, cs)
+                    B.ssim_l1_loss_grad(vb.image, self.targets[k], 1, cfg.lambda_dssim, self.dL[k], self.loss,
+                                        self.ssim_ws, cs)
+                B.render_bwd_with_splitting(g, vb.proj, vb.bins, vb.cam, vb.st, vb.final_T, vb.n_contrib, self.dL[k],
+                                            self.grads, self.S, self.bwd_ws, cs, accumulate=False, S_po=self.S_po,
+                                            S_ls=self.S_ls)
+                self.d_step.add_(1)
+                for i, (p, gr) in enumerate(zip(self.params, self.grads.tensors())):
+                    B.adam_step_dev(p.data, gr, self.m[i], self.v[i], cfg.lr, self.d_step,
+                                    grad_accum=self.G if i == 0 else None, stream=cs)
+            self.step_graphs.append((ga, gb))
+
+    def _graph_step(self, k: int):
+        if self.step_graphs is None:
+            self._capture()
+        ga, gb = self.step_graphs[k]
+        vb = self.views[k]
+        ga.replay()
+        M = B.check_count(int(vb.bins.count.item()))
+        if M > vb.bins.capacity:                    # grow, capture again, redo the binning
+            vb.grow(int(M * 1.25) + 1024)
+            self.step_graphs = None
+            self._capture()
+            ga, gb = self.step_graphs[k]
+            ga.replay()
+        gb.replay()
+
     def step(self, t: int) -> float | None:
         k = t % len(self.cams)
+        if self.cfg.graphs:
+            self._graph_step(k)
+            self.adam_t += 1
+            self.n_accum += 1
+            loss = None
+            if t % self.cfg.log_every == 0 or t == 1:
+                loss = float(self.loss.item())
+                self.log.append({"step": t, "loss": loss, "gaussians": self.n})
+            if t >= self.cfg.start and t % self.cfg.T_split == 0:
+                self.densify(t)
+            return loss
         rc = RenderContext(self.views[k], self.S, self.bwd_ws, self.sh_degree, self.S_po, self.S_ls)
         image = render(self.params, rc)
         self.loss.zero_()
@@ -178,6 +250,7 @@ class SteepGSTrainer:
         self.log.append({"step": t, "densify": True, "split": split, "gaussians": n2,
                          "lambda_min_min": float(lam.min().item()) if n else 0.0})
         self._alloc(n2)
+        self.step_graphs = None                     # captured again for the new buffers
 
     def run(self, steps: int | None = None, log_path: str | None = None):
         steps = steps or self.cfg.steps

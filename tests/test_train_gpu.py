@@ -132,3 +132,22 @@ def test_training_loop_variants_theta4_and_ssim(dim_theta, lam):
         assert bool(torch.isfinite(p).all())
     o = torch.sigmoid(tr.params[3])
     assert bool(((o > 0) & (o < 1)).all())
+
+
+def test_graphed_steps_follow_the_autograd_steps():
+    """The trainer's captured-graph step and its autograd step take the same
+    Adam trajectory (bias corrections and loss sums may round differently)."""
+    runs = []
+    for graphs in (False, True):
+        g, cams, targets, st = TR.config4_problem(n=1024, size=64)
+        cfg = TR.TrainConfig(steps=40, start=1000, T_split=100, log_every=10, graphs=graphs)
+        tr = TR.SteepGSTrainer(g, cams, targets, st, cfg)
+        tr.run()
+        runs.append(tr)
+    a, b = runs
+    for pa, pb in zip(a.params, b.params):
+        d = (pa.detach() - pb.detach()).double().norm() / pa.detach().double().norm()
+        assert float(d) < 1e-4
+    la = [r["loss"] for r in a.log if "loss" in r]
+    lb = [r["loss"] for r in b.log if "loss" in r]
+    assert len(la) == len(lb) and all(abs(x - y) <= 1e-4 * abs(x) for x, y in zip(la, lb))
