@@ -12,7 +12,10 @@
 // warp then walks only the batch entries whose alpha support meets its block
 // (an exact skip: outside that support alpha < alpha_min).  Single-view
 // kernels launch one CTA per tile; the multi-view kernels are persistent and
-// pull global tiles of all views from an atomic counter.
+// pull global tiles of all views from an atomic counter.  Both take their
+// tiles in the schedule bin_sort writes (longest lists first), so that the
+// heaviest tiles do not run alone at the end of a launch.  The forward can
+// carry the L1 loss in its epilogue.
 #include "common.cuh"
 
 namespace sgs {
