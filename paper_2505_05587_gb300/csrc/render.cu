@@ -396,6 +396,7 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) render_fwd_kernel(
     pdl_wait_and_trigger();
     __shared__ FwdSmem<TW * TH, TW * TH / 32> sm;
     const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    if ((unsigned)t >= gridDim.x) return;      // a schedule that is not a permutation of the tiles
     fwd_tile<TW, TH, TW * TH>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, image, final_T, n_contrib, sm,
                               L1 ? &l1 : nullptr);
 }
@@ -412,6 +413,7 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_kernel(
     pdl_wait_and_trigger();
     __shared__ BwdSmem<TW * TH, TW * TH / 32> sm;
     const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    if ((unsigned)t >= gridDim.x) return;      // a schedule that is not a permutation of the tiles
     bwd_tile<TW, TH, TW * TH, HI>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, final_T, n_contrib,
                                   dL_dimage, g2d, g2d_hi, sm);
 }
@@ -437,6 +439,7 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_views_kernel(
         __syncthreads();
         if (k >= vd.T_total) break;
         const int t = order ? (int)order[k] : k;
+        if ((unsigned)t >= (unsigned)vd.T_total) continue;
         const int v = view_of_tile(vd, t);
         const CamDev& c = vd.cam[v];
         const long long po = vd.pix_off[v];
@@ -461,6 +464,7 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_views_ke
         __syncthreads();
         if (k >= vd.T_total) break;
         const int t = order ? (int)order[k] : k;
+        if ((unsigned)t >= (unsigned)vd.T_total) continue;
         const int v = view_of_tile(vd, t);
         const CamDev& c = vd.cam[v];
         const long long po = vd.pix_off[v];

@@ -442,3 +442,27 @@ def test_forward_with_fused_l1_equals_forward_then_l1(name, mk_scene, mk_cam, st
     assert torch.equal(img, ref[0]) and torch.equal(vb.final_T, ref[1]) and torch.equal(vb.n_contrib, ref[2])
     assert torch.equal(dL2, dL1)
     assert abs(float(loss2.item()) - 0.25 - float(loss1.item())) <= 1e-6 * float(loss1.item()) + 1e-9
+
+
+def test_schedule_entries_out_of_range_are_skipped():
+    """The render kernels bound every schedule entry by the tile count: a
+    schedule holding out-of-range ids renders nothing for them (no access
+    outside the buffers) and leaves the valid tiles exact."""
+    scene, cam, st = CASES[0][1](), CASES[0][2](), CASES[0][3]
+    g, vb, _ = _gpu_view(scene, cam, st)
+    B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib)
+    ref = vb.image.clone()
+    T = B.num_tiles(cam, st)
+    bad = vb.bins.order.clone()
+    bad[: T // 2] = T + 7                            # first half of the schedule out of range
+    bins = B.BinBuffers(vb.bins.gids, vb.bins.keys, vb.bins.ranges, vb.bins.count, vb.bins.capacity, bad)
+    img = torch.full_like(vb.image, -1.0)
+    B.render_fwd(vb.proj, bins, cam, st, img, vb.final_T, vb.n_contrib)
+    torch.cuda.synchronize()
+    kept = vb.bins.order[T // 2:].cpu().numpy()
+    gx = (cam.width + st.tile_w - 1) // st.tile_w
+    for t in kept[:8]:
+        ty, tx = divmod(int(t), gx)
+        ys, xs = slice(ty * st.tile_h, (ty + 1) * st.tile_h), slice(tx * st.tile_w, (tx + 1) * st.tile_w)
+        assert torch.equal(img[ys, xs], ref[ys, xs])
+    assert bool((img == -1.0).any())                  # the skipped tiles stay unwritten
