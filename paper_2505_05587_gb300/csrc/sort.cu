@@ -471,9 +471,26 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
     __shared__ uint32_t s_warp[EMIT_THREADS / 32];
     __shared__ uint32_t s_nh[RS_RADIX_MAX][EMIT_SPAN];
     __shared__ uint32_t s_nvis;
+    // per-view row bounds, tile offsets and tile-grid widths in shared memory:
+    // the rows of one round come from different views, and indexing the kernel
+    // parameters with a lane-dependent view serialises the constant loads
+    __shared__ int s_rowoff[kMaxViews + 1];
+    __shared__ uint32_t s_tileoff[kMaxViews];
+    __shared__ int s_gx[kMaxViews];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_nvis = 0u;
+    if (threadIdx.x <= vd.nv) s_rowoff[threadIdx.x] = (int)vd.row_off[threadIdx.x];
+    if (threadIdx.x < vd.nv) {
+        s_tileoff[threadIdx.x] = (uint32_t)vd.tile_off[threadIdx.x];
+        s_gx[threadIdx.x] = vd.cam[threadIdx.x].gx;
+    }
     __syncthreads();
+    const int nv = vd.nv;
+    auto view_of = [&](uint32_t row) {
+        int v = 0;
+        while (v + 1 < nv && (int)row >= s_rowoff[v + 1]) ++v;
+        return v;
+    };
     {
         uint32_t c = depth_tot[threadIdx.x];
 #pragma unroll
@@ -557,9 +574,9 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
             uint32_t off = k - s_off[a];
             short4 r = s_rect[a];
             uint32_t g = s_row[a];
-            int v = view_of_row(vd, g);
-            uint32_t t0 = (uint32_t)vd.tile_off[v];
-            int gx = vd.cam[v].gx;
+            int v = view_of(g);
+            uint32_t t0 = s_tileoff[v];
+            int gx = s_gx[v];
             uint32_t wdt = (uint32_t)(r.z - r.x + 1);
             int ty = r.y + (int)(off / wdt), tx = r.x + (int)(off % wdt);
             uint32_t row_end = a + 1 < rows ? s_off[a + 1] : total;
@@ -568,9 +585,9 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
                     ++a;
                     r = s_rect[a];
                     g = s_row[a];
-                    v = view_of_row(vd, g);
-                    t0 = (uint32_t)vd.tile_off[v];
-                    gx = vd.cam[v].gx;
+                    v = view_of(g);
+                    t0 = s_tileoff[v];
+                    gx = s_gx[v];
                     ty = r.y;
                     tx = r.x;
                     row_end = a + 1 < rows ? s_off[a + 1] : total;
