@@ -56,7 +56,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # DRAM traffic of one render_bwd_kernel<16,16> launch on this workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # rasteriser source it was taken from (first 16 hex digits of its SHA-256).
-RENDER_BWD_TRAFFIC = {"bytes": 103_409_152 + 9_349_120, "render_cu_sha256": "43bd8cddde47bc48",
+RENDER_BWD_TRAFFIC = {"bytes": 103_380_480 + 9_347_072, "render_cu_sha256": "84602c17738c286d",
                       "profile": "profiles/render_bwd_scene_1M_1237x822.md"}
 
 
