@@ -125,3 +125,35 @@ def test_full_size_backward_on_strips_and_split(full):
     sp = oracle.split(scene, lam_o, v_o, 0.0, 1.0)
     assert np.array_equal(flags_g[decided], sp["flags"][decided])
     assert flags_g.sum() > 1000
+
+
+def test_full_size_graph_replay_equals_eager_iteration():
+    """The benchmark's launch configuration (the fused iteration captured as
+    one CUDA graph: fused forward+L1, tile schedule, backward with splitting,
+    split) against the same calls issued eagerly at the full size: images and
+    maps bit for bit, loss, gradients and splitting matrices to atomics
+    reordering, split counts equal up to lambda ~ 0 flips."""
+    scene = synth.cluster_scene(0, N, 3)
+    cam = synth.scene_camera(W, H)
+    st = synth.Settings()
+    g = B.GaussianTensors.from_scene(scene)
+    target = torch.as_tensor(synth.target_image(1, H, W)).cuda()
+    vb = PL.ViewBuffers.alloc(g.n, cam, st, capacity=4 * g.n)
+    db = PL.DensifyBuffers.alloc(g)
+    PL.fused_iteration(g, [vb], [target], db, eps_split=0.0)
+    torch.cuda.synchronize()
+    ref = dict(image=vb.image.clone(), T=vb.final_T.clone(), nc=vb.n_contrib.clone(), S=db.S.clone(),
+               loss=float(db.loss.item()), n_out=int(db.n_out.item()),
+               grads=[t.clone() for t in db.grads.tensors()])
+    graph = PL.FusedIterationGraph(g, [vb], [target], db, eps_split=0.0)
+    vb.image.fill_(-1.0)
+    db.S.fill_(5.0)
+    graph.replay(check=True)
+    torch.cuda.synchronize()
+    assert torch.equal(vb.image, ref["image"]) and torch.equal(vb.final_T, ref["T"])
+    assert torch.equal(vb.n_contrib, ref["nc"])
+    assert abs(float(db.loss.item()) - ref["loss"]) <= 1e-5 * ref["loss"]
+    assert _rel(db.S.cpu().numpy(), ref["S"].cpu().numpy()) < 1e-5
+    for a, b in zip(db.grads.tensors(), ref["grads"]):          # the gradients' parity bar (atomics order)
+        assert _rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-4
+    assert abs(int(db.n_out.item()) - ref["n_out"]) <= 500          # of ~276k splits, decided at lambda ~ 0
