@@ -2,8 +2,9 @@
 package docstring for who may import it).
 
 Section 3 (Eq. loss and its footnote) sets the per-pixel error to L1 and sets
-the SSIM term of 3D Gaussian Splatting aside for the analysis; the NEXT rows of
-this build add it back.  The paper names SSIM (Wang et al., 2004) as a metric
+the SSIM term of 3D Gaussian Splatting aside for the analysis; the training
+objective of 3D Gaussian Splatting keeps it, and so does this module.  The
+paper names SSIM (Wang et al., 2004) as a metric
 but fixes none of its constants, so this module takes the published
 definition: per channel,
 

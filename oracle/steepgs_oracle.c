@@ -30,8 +30,8 @@
  * degree-7 Taylor polynomial), so that it is a fixed sequence of IEEE
  * operations too.
  *
- * Readings of points the paper leaves open are listed in the design doc; the ones
- * that change arithmetic are repeated at the code that implements them.
+ * Where the paper leaves a point open, the reading taken is stated at the
+ * code that implements it.
  * Parity status: every exported function here is pinned by a CPU test
  * (tests/test_oracle_*.py) against finite differences, closed forms, library
  * routines or brute force.

@@ -61,7 +61,10 @@ class Camera:
 
 @dataclass
 class Settings:
-    """Rasterisation constants; defaults follow the readings listed in the design doc."""
+    """Rasterisation constants (3D Gaussian Splatting conventions where the
+    paper is silent): 16x16 tiles, alpha clamped to [1/255, 0.99], compositing
+    stops below transmittance 1e-4, 3-sigma radius, 0.3 px^2 dilation, the
+    projection Jacobian clamped at 1.3 x the half field of view."""
     tile_w: int = 16
     tile_h: int = 16
     alpha_min: float = 1.0 / 255.0
