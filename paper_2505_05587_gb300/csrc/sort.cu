@@ -144,7 +144,7 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* d
 // blocks and writes the digit totals; the scatter ranks each tile's items per
 // digit in item order (warp ballots + a cross-warp prefix) and writes item k of
 // digit d to  base[d] + prefix[d][b] + rank,  so the pass is stable.  The
-// scatter also counts the NEXT pass's per-block histogram from the
+// scatter also counts the next pass's per-block histogram from the
 // destinations it writes (the next pass's chunk of a destination is known), so
 // every pass after the first needs no separate counting kernel.
 // ---------------------------------------------------------------------------

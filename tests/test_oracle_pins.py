@@ -553,7 +553,7 @@ def test_increment_budget_is_the_best_k_subset():
 
 
 # --------------------------------------------------------------------------
-# Splitting matrices over theta = (p, o) (NEXT row f3, dim Theta = 4)
+# Splitting matrices over theta = (p, o) (dim Theta = 4)
 # --------------------------------------------------------------------------
 
 def _frozen_mixed(sc, cam, st, i, g, h):

@@ -116,7 +116,7 @@ def test_training_loop_densifies_and_reduces_loss():
 
 @pytest.mark.parametrize("dim_theta,lam", [(4, None), (3, 0.2), (4, 0.2), (7, None)])
 def test_training_loop_variants_theta4_and_ssim(dim_theta, lam):
-    """The NEXT-row variants inside Algorithm 1: splitting over (position,
+    """Variants inside Algorithm 1: splitting over (position,
     opacity) or (position, log-scales, opacity) and the SSIM term in the
     loss."""
     g, cams, targets, st = TR.config4_problem(n=1024, size=64)
