@@ -125,9 +125,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# Algorithmic bytes of one fused iteration at SH degree 3 (236 B of parameters
+# per Gaussian): every array the method needs, read or written once.  Atomics,
+# extra sort passes and re-reads are implementation cost and are not counted.
+# Rows: (stage, bytes per Gaussian, per instance, per pixel, per tile).
+ALGORITHMIC_BYTES = (
+    ("project: parameters read (236), projected state written (48)", 284, 0, 0, 0),
+    ("instance offsets: tile counts read, offsets written", 8, 0, 0, 0),
+    ("keys: (tile, depth) key and id written", 0, 12, 0, 0),
+    ("sort: one read and one write of each key-id pair", 0, 24, 0, 0),
+    ("tile ranges: keys read, [start, end) per tile written", 0, 8, 0, 8),
+    ("forward: instance record read (40); colour, T, last contributor written (20)", 0, 40, 20, 0),
+    ("L1 loss: colour and target read, dL/dC written", 0, 0, 36, 0),
+    ("backward: instance record read; dL/dC, T, last contributor read; 2-D gradients (36) and "
+     "splitting moments (16) written", 52, 40, 20, 0),
+    ("projection adjoint and lift: parameters, projected state, 2-D sums read (336); gradients (236) "
+     "and the splitting matrix (24) written", 596, 0, 0, 0),
+)
+
+
 def algorithmic_bytes(n, m, p, t):
-    """Bytes each array of the iteration is read or written once (SH degree 3)."""
-    return 932 * n + 124 * m + 88 * p + 8 * t
+    """Bytes each array of the iteration is read or written once (SH degree 3):
+    940 n + 124 m + 76 p + 8 t for n Gaussians, m instances, p pixels, t tiles."""
+    per = [sum(row[k] for row in ALGORITHMIC_BYTES) for k in (1, 2, 3, 4)]
+    return per[0] * n + per[1] * m + per[2] * p + per[3] * t
 
 
 def max_over_ranks(values, world, device):

@@ -83,6 +83,13 @@ class TrainConfig:
     graphs: bool = True                # each training step replayed as captured CUDA graphs (else autograd)
 
 
+def densify_due(t: int, cfg: TrainConfig) -> bool:
+    """Whether step t (1-based) ends with a densification: every T_split steps
+    from step `start` on (Section 5, implementation details: every 100 steps
+    from the 500th)."""
+    return t >= cfg.start and t % cfg.T_split == 0
+
+
 class SteepGSTrainer:
     """Algorithm 1 on one GPU: one view per step (cycled), L1 loss, Adam.
 
@@ -189,7 +196,7 @@ class SteepGSTrainer:
             if t % self.cfg.log_every == 0 or t == 1:
                 loss = float(self.loss.item())
                 self.log.append({"step": t, "loss": loss, "gaussians": self.n})
-            if t >= self.cfg.start and t % self.cfg.T_split == 0:
+            if densify_due(t, self.cfg):
                 self.densify(t)
             return loss
         rc = RenderContext(self.views[k], self.S, self.bwd_ws, self.sh_degree, self.S_po, self.S_ls)
@@ -212,7 +219,7 @@ class SteepGSTrainer:
         if t % self.cfg.log_every == 0 or t == 1:
             loss = float(self.loss.item())
             self.log.append({"step": t, "loss": loss, "gaussians": self.n})
-        if t >= self.cfg.start and t % self.cfg.T_split == 0:
+        if densify_due(t, self.cfg):
             self.densify(t)
         return loss
 
