@@ -65,6 +65,11 @@ extern "C" {
 #define SGS_ERR_CUDA 4
 #define SGS_ERR_TIMEOUT 5
 #define SGS_ERR_UNSUPPORTED 6
+/* Codes 3, 5 and 6 are reserved; no call of this version returns them: a
+ * capacity overflow is reported through the data-dependent counts (see the
+ * conventions above), no kernel waits on another agent (every loop is bounded
+ * by its input sizes), and settings outside what the kernels handle are
+ * argument errors (SGS_ERR_INVALID_ARG). */
 
 /* Gaussian parameters theta^(i) = (p, Sigma via quaternion + log-scale, o, SH
  * colour) (Section 3, "Scene Representation").  Read-only input. */
