@@ -144,6 +144,37 @@ def _p(t):
     return t.data_ptr()
 
 
+F32 = (torch.float32,)
+I16 = (torch.int16,)
+I32 = tuple(d for d in (torch.int32, getattr(torch, "uint32", None)) if d is not None)
+I64 = tuple(d for d in (torch.int64, getattr(torch, "uint64", None)) if d is not None)
+
+
+def _check_arr(t, name: str, dtypes, numel: int = 0):
+    """Checks the element type of `t` (None passes) and that it holds at least
+    `numel` elements.  The library receives bare pointers and cannot check the
+    arrays behind them, so a tensor too small for the call is refused here,
+    before anything is launched."""
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name}: dtype {t.dtype}, expected {' or '.join(str(d) for d in dtypes)}")
+    if t.numel() < numel:
+        raise ValueError(f"{name}: {t.numel()} elements, the call needs at least {numel}")
+
+
+def _arr(t, name: str, dtypes, numel: int = 0):
+    """Device pointer of `t` (None passes through) after _check_arr."""
+    _check_arr(t, name, dtypes, numel)
+    return _p(t)
+
+
+def _pixels(cam) -> int:
+    return int(cam.width) * int(cam.height)
+
+
 def _stream(stream):
     if stream is None:
         return C.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -168,16 +199,30 @@ class GaussianTensors:
     def n(self) -> int:
         return int(self.means.shape[0])
 
-    def c(self) -> Gaussians:
-        for t in (self.means, self.log_scales, self.quats, self.opacity_logit, self.sh):
-            if t.dtype != torch.float32:
-                raise TypeError("Gaussian parameters must be float32")
-        return Gaussians(_p(self.means), _p(self.log_scales), _p(self.quats), _p(self.opacity_logit),
-                         _p(self.sh), self.n, self.sh_degree)
+    def ptrs(self, rows: int | None = None, what: str = "") -> tuple:
+        """Device pointers of the five arrays, each checked to hold `rows`
+        (default n) Gaussians of this SH degree."""
+        r = self.n if rows is None else int(rows)
+        if not 0 <= self.sh_degree <= 3:
+            raise ValueError(f"sh_degree {self.sh_degree} outside 0..3")
+        K = (self.sh_degree + 1) ** 2
+        arrays = ((self.means, "means", 3 * r), (self.log_scales, "log_scales", 3 * r), (self.quats, "quats", 4 * r),
+                  (self.opacity_logit, "opacity_logit", r), (self.sh, "sh", 3 * K * r))
+        for t, name, k in arrays:
+            _check_arr(t, what + name, F32, k)
+        return tuple(_p(t) for t, _, _ in arrays)
 
-    def c_mut(self) -> GaussiansMut:
-        return GaussiansMut(_p(self.means), _p(self.log_scales), _p(self.quats), _p(self.opacity_logit),
-                            _p(self.sh))
+    def c(self) -> Gaussians:
+        return Gaussians(*self.ptrs(), self.n, self.sh_degree)
+
+    def c_mut(self, rows: int | None = None) -> GaussiansMut:
+        return GaussiansMut(*self.ptrs(rows, "out."))
+
+    def grads_c(self, g: "GaussianTensors") -> "Grads":
+        """These tensors as the gradient arrays of the Gaussians `g`."""
+        if self.sh_degree != g.sh_degree:
+            raise ValueError("gradients and Gaussians differ in SH degree")
+        return Grads(*self.ptrs(g.n, "grads."))
 
     @staticmethod
     def empty(n: int, sh_degree: int, device="cuda") -> "GaussianTensors":
@@ -224,9 +269,12 @@ class ProjBuffers:
                            torch.empty(n, **f), torch.empty(n, 4, device=device, dtype=torch.int16),
                            torch.empty(n, device=device, dtype=torch.int32))
 
-    def c(self) -> Proj:
-        return Proj(_p(self.xy), _p(self.conic_opac), _p(self.rgb), _p(self.depth), _p(self.rect),
-                    _p(self.tiles_touched))
+    def c(self, rows: int | None = None) -> Proj:
+        """Checked for `rows` Gaussians (default: the rows of `depth`)."""
+        r = int(self.depth.shape[0]) if rows is None else int(rows)
+        return Proj(_arr(self.xy, "proj.xy", F32, 4 * r), _arr(self.conic_opac, "proj.conic_opac", F32, 4 * r),
+                    _arr(self.rgb, "proj.rgb", F32, 4 * r), _arr(self.depth, "proj.depth", F32, r),
+                    _arr(self.rect, "proj.rect", I16, 4 * r), _arr(self.tiles_touched, "proj.tiles_touched", I32, r))
 
 
 @dataclass
@@ -246,8 +294,14 @@ class BinBuffers:
                           torch.empty(num_tiles, 2, **i32), torch.zeros(1, **i32), capacity,
                           torch.empty(max(num_tiles, 1), **i32) if with_order else None)
 
-    def c(self) -> Bins:
-        return Bins(_p(self.gids), _p(self.keys), _p(self.ranges), _p(self.count), self.capacity, _p(self.order))
+    def c(self, num_tiles: int | None = None) -> Bins:
+        """Checked for `capacity` instances and `num_tiles` tiles (default:
+        the rows of `ranges`)."""
+        T = int(self.ranges.shape[0]) if num_tiles is None else int(num_tiles)
+        cap = int(self.capacity)
+        return Bins(_arr(self.gids, "bins.gids", I32, cap), _arr(self.keys, "bins.keys", I64, cap),
+                    _arr(self.ranges, "bins.ranges", I32, 2 * T), _arr(self.count, "bins.count", I32, 1), cap,
+                    _arr(self.order, "bins.order", I32, T))
 
 
 def camera_c(cam) -> Camera:
@@ -271,7 +325,7 @@ def num_tiles(cam, st) -> int:
 # Entry points (same names as the C ABI)
 # --------------------------------------------------------------------------
 def project(g: GaussianTensors, cam, st, out: ProjBuffers, stream=None):
-    gc, cc, sc, oc = g.c(), camera_c(cam), settings_c(st), out.c()
+    gc, cc, sc, oc = g.c(), camera_c(cam), settings_c(st), out.c(g.n)
     _check("sgs_project", lib().sgs_project(C.byref(gc), C.byref(cc), C.byref(sc), C.byref(oc), _stream(stream)))
 
 
@@ -282,31 +336,40 @@ def bin_sort_workspace_size(n: int, capacity: int, tiles: int) -> int:
 
 
 def bin_sort(proj: ProjBuffers, n: int, cam, st, out: BinBuffers, ws: torch.Tensor, stream=None):
-    pc, cc, sc, oc = proj.c(), camera_c(cam), settings_c(st), out.c()
+    pc, cc, sc, oc = proj.c(n), camera_c(cam), settings_c(st), out.c(num_tiles(cam, st))
     _check("sgs_bin_sort", lib().sgs_bin_sort(C.byref(pc), n, C.byref(cc), C.byref(sc), C.byref(oc), _p(ws),
                                                ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def render_fwd(proj: ProjBuffers, bins: BinBuffers, cam, st, image, final_T, n_contrib, stream=None):
-    pc, bc, cc, sc = proj.c(), bins.c(), camera_c(cam), settings_c(st)
-    _check("sgs_render_fwd", lib().sgs_render_fwd(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc), _p(image),
-                                                   _p(final_T), _p(n_contrib), _stream(stream)))
+    pc, bc, cc, sc = proj.c(), bins.c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
+    P = _pixels(cam)
+    _check("sgs_render_fwd", lib().sgs_render_fwd(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
+                                                   _arr(image, "image", F32, 3 * P),
+                                                   _arr(final_T, "final_T", F32, P),
+                                                   _arr(n_contrib, "n_contrib", I32, P), _stream(stream)))
 
 
 def render_fwd_l1(proj: ProjBuffers, bins: BinBuffers, cam, st, target, n_views: int, image, final_T, n_contrib,
                   dL_dimage, loss, stream=None):
     """render_fwd with the L1 loss and its gradient in the same kernel."""
-    pc, bc, cc, sc = proj.c(), bins.c(), camera_c(cam), settings_c(st)
+    pc, bc, cc, sc = proj.c(), bins.c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
+    P = _pixels(cam)
     _check("sgs_render_fwd_l1", lib().sgs_render_fwd_l1(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
-                                                         _p(target), int(n_views), _p(image), _p(final_T),
-                                                         _p(n_contrib), _p(dL_dimage), _p(loss), _stream(stream)))
+                                                         _arr(target, "target", F32, 3 * P), int(n_views),
+                                                         _arr(image, "image", F32, 3 * P),
+                                                         _arr(final_T, "final_T", F32, P),
+                                                         _arr(n_contrib, "n_contrib", I32, P),
+                                                         _arr(dL_dimage, "dL_dimage", F32, 3 * P),
+                                                         _arr(loss, "loss", F32, 1), _stream(stream)))
 
 
 def render_stats(proj: ProjBuffers, bins: BinBuffers, cam, st, counts, stream=None):
     """counts: int32 [H,W,2] <- (pairs evaluated, pairs composited) per pixel."""
-    pc, bc, cc, sc = proj.c(), bins.c(), camera_c(cam), settings_c(st)
+    pc, bc, cc, sc = proj.c(), bins.c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
     _check("sgs_render_stats", lib().sgs_render_stats(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
-                                                       _p(counts), _stream(stream)))
+                                                       _arr(counts, "counts", I32, 2 * _pixels(cam)),
+                                                       _stream(stream)))
 
 
 def ssim_l1_workspace_size(height: int, width: int) -> int:
@@ -317,22 +380,33 @@ def ssim_l1_workspace_size(height: int, width: int) -> int:
 
 def ssim_l1_loss_grad(image, target, n_views: int, lambda_dssim: float, dL_dimage, loss, ws, stream=None):
     """loss += ((1 - lambda) L1 + lambda (1 - SSIM)) / n_views; dL_dimage <- its gradient."""
-    H, W = int(image.shape[0]), int(image.shape[1])
+    H, W = _image_hw(image)
     _check("sgs_ssim_l1_loss_grad",
-           lib().sgs_ssim_l1_loss_grad(_p(image), _p(target), H, W, n_views, float(lambda_dssim), _p(dL_dimage),
-                                       _p(loss), _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
+           lib().sgs_ssim_l1_loss_grad(_arr(image, "image", F32, 3 * H * W), _arr(target, "target", F32, 3 * H * W),
+                                       H, W, n_views, float(lambda_dssim),
+                                       _arr(dL_dimage, "dL_dimage", F32, 3 * H * W), _arr(loss, "loss", F32, 1),
+                                       _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def fma_probe(out, blocks: int, iters: int, stream=None):
     """FP32 FMA throughput probe: out float32 [blocks * 256]; 16 * iters FLOP
     per thread."""
-    _check("sgs_fma_probe", lib().sgs_fma_probe(_p(out), int(blocks), int(iters), _stream(stream)))
+    _check("sgs_fma_probe", lib().sgs_fma_probe(_arr(out, "out", F32, int(blocks) * 256), int(blocks), int(iters),
+                                                 _stream(stream)))
+
+
+def _image_hw(image) -> tuple[int, int]:
+    if not isinstance(image, torch.Tensor) or image.dim() != 3 or image.shape[2] != 3:
+        raise ValueError("image: expected a [H, W, 3] tensor")
+    return int(image.shape[0]), int(image.shape[1])
 
 
 def l1_loss_grad(image, target, n_views: int, dL_dimage, loss, stream=None):
-    H, W = int(image.shape[0]), int(image.shape[1])
-    _check("sgs_l1_loss_grad", lib().sgs_l1_loss_grad(_p(image), _p(target), H, W, n_views, _p(dL_dimage),
-                                                       _p(loss), _stream(stream)))
+    H, W = _image_hw(image)
+    _check("sgs_l1_loss_grad", lib().sgs_l1_loss_grad(_arr(image, "image", F32, 3 * H * W),
+                                                       _arr(target, "target", F32, 3 * H * W), H, W, n_views,
+                                                       _arr(dL_dimage, "dL_dimage", F32, 3 * H * W),
+                                                       _arr(loss, "loss", F32, 1), _stream(stream)))
 
 
 def render_bwd_workspace_size(n: int) -> int:
@@ -347,12 +421,15 @@ def render_bwd_with_splitting(g: GaussianTensors, proj: ProjBuffers, bins: BinBu
     """S_po [N,3] (optional): the position-opacity block of the splitting
     matrix over theta = (p, o) is accumulated too; S_ls [N,18] (optional, with
     S_po): the log-scale blocks over theta = (p, l, o) as well."""
-    gc, pc, bc, cc, sc = g.c(), proj.c(), bins.c(), camera_c(cam), settings_c(st)
-    grc = Grads(*[_p(t) for t in grads.tensors()])
+    gc, pc, bc, cc, sc = g.c(), proj.c(g.n), bins.c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
+    grc = grads.grads_c(g)
+    n, P = g.n, _pixels(cam)
     _check("sgs_render_bwd_with_splitting",
            lib().sgs_render_bwd_with_splitting(C.byref(gc), C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
-                                               _p(final_T), _p(n_contrib), _p(dL_dimage), C.byref(grc),
-                                               1 if accumulate else 0, _p(S_accum), _p(S_po), _p(S_ls), _p(ws),
+                                               _arr(final_T, "final_T", F32, P), _arr(n_contrib, "n_contrib", I32, P),
+                                               _arr(dL_dimage, "dL_dimage", F32, 3 * P), C.byref(grc),
+                                               1 if accumulate else 0, _arr(S_accum, "S_accum", F32, 6 * n),
+                                               _arr(S_po, "S_po", F32, 3 * n), _arr(S_ls, "S_ls", F32, 18 * n), _p(ws),
                                                ws.numel() * ws.element_size(),
                                                _stream(stream)))
 
@@ -378,11 +455,15 @@ def render_views_with_splitting(g: GaussianTensors, cams, st, batch: int, target
     """All views in one pass: project, bin/sort, persistent forward, L1,
     persistent backward, projection adjoint (see sgs_render_views_with_splitting)."""
     gc, arr, sc = g.c(), cameras_c(cams), settings_c(st)
-    grc = Grads(*[_p(t) for t in grads.tensors()])
+    grc = grads.grads_c(g)
+    n, P = g.n, sum(_pixels(c) for c in cams)
     _check("sgs_render_views_with_splitting",
-           lib().sgs_render_views_with_splitting(C.byref(gc), arr, len(cams), C.byref(sc), batch, _p(targets),
-                                                 _p(images), _p(loss), C.byref(grc), 1 if accumulate else 0,
-                                                 _p(S_accum), _p(S_po), _p(d_count), capacity, _p(ws),
+           lib().sgs_render_views_with_splitting(C.byref(gc), arr, len(cams), C.byref(sc), batch,
+                                                 _arr(targets, "targets", F32, 3 * P),
+                                                 _arr(images, "images", F32, 3 * P), _arr(loss, "loss", F32, 1),
+                                                 C.byref(grc), 1 if accumulate else 0,
+                                                 _arr(S_accum, "S_accum", F32, 6 * n), _arr(S_po, "S_po", F32, 3 * n),
+                                                 _arr(d_count, "d_count", I32, 1), capacity, _p(ws),
                                                  ws.numel() * ws.element_size(), _stream(stream)))
 
 
@@ -404,23 +485,40 @@ def render_batch_workspace_size(scenes, cams, st, capacity: int) -> int:
 def render_batch_fwd(scenes, cams, st, batch: int, images, d_count, capacity: int, ws, stream=None):
     """Forward render of views of (possibly different) scenes in one pass."""
     sa, ca, sc = _scenes_c(scenes), cameras_c(cams), settings_c(st)
+    P = sum(_pixels(c) for c in cams)
     _check("sgs_render_batch_fwd",
-           lib().sgs_render_batch_fwd(sa, ca, len(cams), C.byref(sc), batch, _p(images), _p(d_count), capacity,
+           lib().sgs_render_batch_fwd(sa, ca, len(cams), C.byref(sc), batch, _arr(images, "images", F32, 3 * P),
+                                      _arr(d_count, "d_count", I32, 1), capacity,
                                       _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def adam_step(param, grad, m, v, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, grad_accum=None,
               stream=None):
     """In-place Adam update of one float32 parameter tensor."""
-    _check("sgs_adam_step", lib().sgs_adam_step(_p(param), _p(grad), _p(m), _p(v), param.numel(), lr, beta1, beta2,
-                                                 eps, step, _p(grad_accum), _stream(stream)))
+    k = param.numel()
+    _check("sgs_adam_step", lib().sgs_adam_step(_arr(param, "param", F32), _arr(grad, "grad", F32, k),
+                                                 _arr(m, "m", F32, k), _arr(v, "v", F32, k), k, lr, beta1, beta2,
+                                                 eps, step, _arr(grad_accum, "grad_accum", F32, k), _stream(stream)))
 
 
 def adam_step_dev(param, grad, m, v, lr: float, d_step, beta1=0.9, beta2=0.999, eps=1e-8, grad_accum=None,
                   stream=None):
     """adam_step with the step count read from the device int32 tensor d_step."""
-    _check("sgs_adam_step_dev", lib().sgs_adam_step_dev(_p(param), _p(grad), _p(m), _p(v), param.numel(), lr, beta1,
-                                                         beta2, eps, _p(d_step), _p(grad_accum), _stream(stream)))
+    k = param.numel()
+    _check("sgs_adam_step_dev", lib().sgs_adam_step_dev(_arr(param, "param", F32), _arr(grad, "grad", F32, k),
+                                                         _arr(m, "m", F32, k), _arr(v, "v", F32, k), k, lr, beta1,
+                                                         beta2, eps, _arr(d_step, "d_step", I32, 1),
+                                                         _arr(grad_accum, "grad_accum", F32, k), _stream(stream)))
+
+
+def _split_arrays(n, S_accum, S_po, S_ls):
+    return (_arr(S_accum, "S_accum", F32, 6 * n), _arr(S_po, "S_po", F32, 3 * n), _arr(S_ls, "S_ls", F32, 18 * n))
+
+
+def _split_outputs(n, capacity, S_po, S_ls, d_n_out, parent_index, lam_min_out, v_min_out):
+    d = 7 if S_ls is not None else (4 if S_po is not None else 3)
+    return (_arr(d_n_out, "d_n_out", I32, 1), _arr(parent_index, "parent_index", I32, capacity),
+            _arr(lam_min_out, "lam_min_out", F32, n), _arr(v_min_out, "v_min_out", F32, d * n))
 
 
 def densify_split_workspace_size(n: int) -> int:
@@ -434,11 +532,13 @@ def densify_split(g: GaussianTensors, S_accum, inv_T_split: float, eps_split: fl
                   lam_min_out, v_min_out, ws, stream=None, max_splits: int = 0, S_po=None, S_ls=None):
     """S_po [N,3] given: split over theta = (p, o) (v_min_out [N,4]); S_po and
     S_ls [N,18] given: over theta = (p, l, o) (v_min_out [N,7])."""
-    gc, oc = g.c(), out.c_mut()
+    gc, oc = g.c(), out.c_mut(capacity)
     _check("sgs_densify_split",
-           lib().sgs_densify_split(C.byref(gc), _p(S_accum), _p(S_po), _p(S_ls), inv_T_split, eps_split,
-                                   step_scale, _p(grad_norm), eps_grad, int(max_splits), C.byref(oc), capacity,
-                                   _p(d_n_out), _p(parent_index), _p(lam_min_out), _p(v_min_out), _p(ws), ws.numel() * ws.element_size(),
+           lib().sgs_densify_split(C.byref(gc), *_split_arrays(g.n, S_accum, S_po, S_ls), inv_T_split,
+                                   eps_split, step_scale, _arr(grad_norm, "grad_norm", F32, g.n), eps_grad,
+                                   int(max_splits), C.byref(oc), capacity,
+                                   *_split_outputs(g.n, capacity, S_po, S_ls, d_n_out, parent_index, lam_min_out,
+                                                   v_min_out), _p(ws), ws.numel() * ws.element_size(),
                                    _stream(stream)))
 
 
@@ -453,11 +553,14 @@ def densify_split_noalloc(g: GaussianTensors, S_accum, inv_T_split: float, eps_s
     """densify_split without a workspace, for callers that cannot allocate one
     (its scratch is a fixed array inside the library; n <= 1,000,000; calls
     that overlap on the GPU race)."""
-    gc, oc = g.c(), out.c_mut()
+    gc, oc = g.c(), out.c_mut(capacity)
     _check("sgs_densify_split_noalloc",
-           lib().sgs_densify_split_noalloc(C.byref(gc), _p(S_accum), _p(S_po), _p(S_ls), inv_T_split, eps_split,
-                                           step_scale, _p(grad_norm), eps_grad, int(max_splits), C.byref(oc),
-                                           capacity, _p(d_n_out), _p(parent_index), _p(lam_min_out), _p(v_min_out), _stream(stream)))
+           lib().sgs_densify_split_noalloc(C.byref(gc), *_split_arrays(g.n, S_accum, S_po, S_ls),
+                                           inv_T_split, eps_split, step_scale,
+                                           _arr(grad_norm, "grad_norm", F32, g.n), eps_grad, int(max_splits),
+                                           C.byref(oc), capacity,
+                                           *_split_outputs(g.n, capacity, S_po, S_ls, d_n_out, parent_index,
+                                                           lam_min_out, v_min_out), _stream(stream)))
 
 
 def check_count(M: int) -> int:
