@@ -200,6 +200,53 @@ def test_rect_covers_three_sigma_ellipse_and_is_tight():
         assert yl == max(0, math.floor((my - r) / 16)) and yh == min(3, math.floor((my + r) / 16))
 
 
+def test_equal_depths_sort_by_gaussian_index():
+    """Copies of one Gaussian share tiles and depth bits; within a tile they
+    follow each other in increasing index (the stable order over instances
+    emitted in index order), between the neighbours of their depth."""
+    sc = synth.tiny_scene(2, 60)
+    for i in (41, 7, 23):                            # copies of Gaussian 12, placed at shuffled indices
+        for f in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+            getattr(sc, f)[i] = getattr(sc, f)[12]
+    cam = synth.camera_identity(64, 64, 64.0)
+    st = synth.Settings()
+    isg = oracle.integer_stage(sc, cam, st)
+    assert isg["tiles"][12] > 0
+    keys, gids, ranges = oracle.bin_sort(sc, cam, st)
+    copies = [7, 12, 23, 41]
+    for t in range(len(ranges)):
+        a, b = ranges[t]
+        g = gids[a:b].tolist()
+        if 12 not in g:
+            continue
+        pos = [g.index(c) for c in copies]
+        assert pos == list(range(pos[0], pos[0] + 4))   # adjacent, in index order
+        d = [int(k & np.uint64(0xFFFFFFFF)) for k in keys[a:b]]
+        assert d == sorted(d)
+
+
+def test_near_plane_culls_and_renders_nothing():
+    """A Gaussian whose camera depth is at or in front of the near plane
+    (t_z <= 0.2) touches no tile and leaves the background; just behind it
+    the same Gaussian is binned and drawn."""
+    st = synth.Settings(bg=(0.1, 0.2, 0.3))
+    cam = synth.camera_identity(64, 64, 64.0)
+    near = np.float32(cam.near_z)
+    for z, visible in ((0.15, False), (float(near), False), (float(np.nextafter(near, np.float32(1))), True),
+                       (0.5, True)):
+        sc = _one_gaussian([0.0, 0.0, z], [-3.0] * 3, 2.0, [1.0, 1.0, 1.0])
+        isg = oracle.integer_stage(sc, cam, st)
+        img = oracle.render(sc, cam, st)["image"]
+        keys, _, _ = oracle.bin_sort(sc, cam, st)
+        if visible:
+            assert isg["tiles"][0] > 0 and len(keys) == isg["tiles"][0]
+            assert np.abs(img - np.array(st.bg)).max() > 1e-3
+        else:
+            assert isg["tiles"][0] == 0 and len(keys) == 0
+            bg = np.array(st.bg, np.float32).astype(np.float64)     # the settings carry float32
+            assert np.array_equal(img, np.broadcast_to(bg, img.shape))
+
+
 # --------------------------------------------------------------------------
 # Gradients: central finite differences on the full model (smooth mode)
 # --------------------------------------------------------------------------
