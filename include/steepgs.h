@@ -202,7 +202,11 @@ int sgs_bin_sort(const sgs_proj *proj, int32_t n, const sgs_camera *cam, const s
  * tile's list: C = sum c_i alpha_i T_i + T_final bg.
  * Outputs image [H,W,3], final_T [H,W] (transmittance after the last
  * composited Gaussian) and n_contrib [H,W] (1 + list position of the last
- * composited Gaussian, 0 if none), the two maps the backward pass needs. */
+ * composited Gaussian, 0 if none), the two maps the backward pass needs.
+ * proj and bins are the same view's sgs_project / sgs_bin_sort outputs.
+ * Errors: SGS_ERR_INVALID_ARG on a NULL struct or array, an invalid camera or
+ * settings, or a tile grid that does not fit; SGS_ERR_CUDA if the launch
+ * fails. */
 int sgs_render_fwd(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
                    const sgs_settings *st, float *image, float *final_T, uint32_t *n_contrib,
                    void *stream);
@@ -211,14 +215,17 @@ int sgs_render_fwd(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera 
  * compositing epilogue): the same image, final_T and n_contrib, dL_dimage
  * [H,W,3] = sign(image - target) / (3 H W n_views) bit for bit, and loss +=
  * mean |image - target| / n_views (summed per tile, one atomic each, so the
- * float sum may round differently from sgs_l1_loss_grad's). */
+ * float sum may round differently from sgs_l1_loss_grad's).  target [H,W,3]
+ * is read; loss is one device float.  Errors: as sgs_render_fwd, and
+ * SGS_ERR_INVALID_ARG on a NULL target, dL_dimage or loss or n_views < 1. */
 int sgs_render_fwd_l1(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
                       const sgs_settings *st, const float *target, int32_t n_views, float *image,
                       float *final_T, uint32_t *n_contrib, float *dL_dimage, float *loss, void *stream);
 
 /* Pair counts of the forward walk (a measurement aid, not on the path):
  * counts [H,W,2] uint32 = (pairs evaluated, pairs composited) per pixel, the
- * work units behind the rasteriser's algorithmic FLOP count. */
+ * work units behind the rasteriser's algorithmic FLOP count.  Errors: as
+ * sgs_render_fwd. */
 int sgs_render_stats(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
                      const sgs_settings *st, uint32_t *counts, void *stream);
 
@@ -230,7 +237,10 @@ int sgs_render_stats(const sgs_proj *proj, const sgs_bins *bins, const sgs_camer
  * C2 = 0.03^2, averaged over pixels and channels.  dL_dimage [H,W,3] is
  * overwritten with the gradient of that loss; lambda_dssim in [0, 1]
  * (0.2 in Gaussian-splatting training).  ws: sgs_ssim_l1_workspace_size bytes
- * (nine float maps of H x W). */
+ * (nine float maps of H x W).  Errors: SGS_ERR_INVALID_ARG on NULL arrays,
+ * non-positive sizes, n_views < 1 or lambda_dssim outside [0, 1];
+ * SGS_ERR_WORKSPACE when ws_bytes is too small; SGS_ERR_CUDA if a launch
+ * fails. */
 int sgs_ssim_l1_workspace_size(int32_t height, int32_t width, size_t *bytes);
 int sgs_ssim_l1_loss_grad(const float *image, const float *target, int32_t height, int32_t width,
                           int32_t n_views, float lambda_dssim, float *dL_dimage, float *loss, void *ws,
@@ -240,13 +250,16 @@ int sgs_ssim_l1_loss_grad(const float *image, const float *target, int32_t heigh
  * blocks of 256 threads, each thread runs `iters` rounds of 8 independent
  * fused multiply-adds (16 FLOP per round) and writes one float to
  * out[blocks * 256].  Timing it gives the attainable FP32 peak that the
- * rasteriser's ALU roofline is quoted against. */
+ * rasteriser's ALU roofline is quoted against.  Errors: SGS_ERR_INVALID_ARG
+ * on a NULL out or non-positive blocks or iters. */
 int sgs_fma_probe(float *out, int32_t blocks, int32_t iters, void *stream);
 
 /* L1 photometric loss (Section 3, Eq. loss, l = |.|):
  * loss += mean over pixels and channels of |image - target| / n_views and
  * dL_dimage = sign(image - target) / (3 H W n_views).  loss is one device
- * float, accumulated (+=); dL_dimage [H,W,3] is overwritten. */
+ * float, accumulated (+=); dL_dimage [H,W,3] is overwritten.  Errors:
+ * SGS_ERR_INVALID_ARG on NULL arrays, non-positive sizes or n_views < 1;
+ * SGS_ERR_CUDA if the launch fails. */
 int sgs_l1_loss_grad(const float *image, const float *target, int32_t height, int32_t width,
                      int32_t n_views, float *dL_dimage, float *loss, void *stream);
 
@@ -322,7 +335,9 @@ int sgs_render_views_with_splitting(const sgs_gaussians *g, const sgs_camera *ca
  * render-serving batch): scenes[v] is the scene of view v (sh_degree must be
  * equal across the batch), images as in sgs_render_views_with_splitting.
  * Each view's image is bit-identical to rendering it alone with the same
- * settings.  d_count / capacity: instance count of the whole batch, as above. */
+ * settings.  d_count / capacity: instance count of the whole batch, as above.
+ * Errors: SGS_ERR_INVALID_ARG (also when the scenes' SH degrees differ),
+ * SGS_ERR_WORKSPACE, SGS_ERR_CUDA. */
 int sgs_render_batch_workspace_size(const sgs_gaussians *scenes, const sgs_camera *cams, int32_t n_views,
                                     const sgs_settings *st, int64_t capacity, size_t *bytes);
 int sgs_render_batch_fwd(const sgs_gaussians *scenes, const sgs_camera *cams, int32_t n_views,
@@ -334,12 +349,15 @@ int sgs_render_batch_fwd(const sgs_gaussians *scenes, const sgs_camera *cams, in
  * step): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
  * When grad_accum is not NULL it also adds g into it (Algorithm 1's
- * G <- G + grad).  step >= 1. */
+ * G <- G + grad).  step >= 1.  Errors: SGS_ERR_INVALID_ARG on count < 0,
+ * step < 1, lr < 0, beta outside [0, 1), eps <= 0 or a NULL array when
+ * count > 0; SGS_ERR_CUDA if the launch fails. */
 int sgs_adam_step(float *param, const float *grad, float *m, float *v, int64_t count, float lr, float beta1,
                   float beta2, float eps, int32_t step, float *grad_accum, void *stream);
 /* The same update with the step count read from device memory (d_step, one
  * int32 >= 1 when the kernel runs), so that a captured graph can replay it
- * while the caller advances the count on the device. */
+ * while the caller advances the count on the device.  Errors: as
+ * sgs_adam_step, with a NULL d_step in place of step < 1. */
 int sgs_adam_step_dev(float *param, const float *grad, float *m, float *v, int64_t count, float lr, float beta1,
                       float beta2, float eps, const int32_t *d_step, float *grad_accum, void *stream);
 
