@@ -144,7 +144,7 @@ def autotune(g: B.GaussianTensors, cams, targets: torch.Tensor, st, reps: int = 
     return best[0], best[1], table
 
 
-def run_config3(n: int = 3_000_000, steps: int = 20, warmup: int = 3, tune: bool = True) -> dict:
+def run_ring_densify(n: int = 3_000_000, steps: int = 20, warmup: int = 3, tune: bool = True) -> dict:
     """Batched densification step on the ring of 8 uneven views: 3M Gaussians
     (cluster mixture, SH3).  Times the autotuned, graph-captured batched step
     against the one-view-per-launch form of the same step."""
@@ -183,4 +183,4 @@ def run_config3(n: int = 3_000_000, steps: int = 20, warmup: int = 3, tune: bool
 if __name__ == "__main__":
     import json
     import sys
-    print(json.dumps(run_config3(int(sys.argv[1]) if len(sys.argv) > 1 else 3_000_000)))
+    print(json.dumps(run_ring_densify(int(sys.argv[1]) if len(sys.argv) > 1 else 3_000_000)))

@@ -210,22 +210,22 @@ def _summary(jobs, lat, wall, stats) -> dict:
             "mean_ms": round(float(l.mean()), 3), "max_ms": round(float(l.max()), 3), **stats}
 
 
-def config5_jobs(seed: int = 3, n_requests: int = 4000, rate_hz: float = 200.0, n_scenes: int = 6):
+def serving_requests(seed: int = 3, n_requests: int = 4000, rate_hz: float = 200.0, n_scenes: int = 6):
     import synth
     reqs = synth.request_stream(seed, n_requests, rate_hz, n_scenes)
     return [Job(k, r.arrival_s - reqs[0].arrival_s, r.scene, r.camera) for k, r in enumerate(reqs)]
 
 
-def config5_scenes(sizes=(100_000, 300_000, 1_000_000, 1_000_000, 2_000_000, 3_000_000)):
+def resident_scenes(sizes=(100_000, 300_000, 1_000_000, 1_000_000, 2_000_000, 3_000_000)):
     import synth
     return [B.GaussianTensors.from_scene(synth.cluster_scene(10 + k, n, 3)) for k, n in enumerate(sizes)]
 
 
-def run_config5(n_requests: int = 4000, rate_hz: float = 200.0) -> dict:
+def run_serving(n_requests: int = 4000, rate_hz: float = 200.0) -> dict:
     import synth
     st = synth.Settings()
-    scenes = config5_scenes()
-    jobs = config5_jobs(3, n_requests, rate_hz, len(scenes))
+    scenes = resident_scenes()
+    jobs = serving_requests(3, n_requests, rate_hz, len(scenes))
     warm = jobs[:200]
     server = RenderServer(scenes, st)
     server.run(warm, realtime=False)               # warm-up: workspaces and instance estimates
@@ -245,4 +245,4 @@ def run_config5(n_requests: int = 4000, rate_hz: float = 200.0) -> dict:
 if __name__ == "__main__":
     import json
     import sys
-    print(json.dumps(run_config5(int(sys.argv[1]) if len(sys.argv) > 1 else 4000)))
+    print(json.dumps(run_serving(int(sys.argv[1]) if len(sys.argv) > 1 else 4000)))

@@ -273,7 +273,7 @@ class SteepGSTrainer:
         return wall
 
 
-def config4_problem(n: int = 4096, size: int = 128, device="cuda"):
+def offset_views_problem(n: int = 4096, size: int = 128, device="cuda"):
     """Differentiation/training workload: tiny-scene distributions with n
     Gaussians, four size x size views at the origin shifted by (+-0.25,
     +-0.25, 0), targets rendered from a hidden scene (seed 1) of the same size."""
@@ -290,8 +290,8 @@ def config4_problem(n: int = 4096, size: int = 128, device="cuda"):
     return B.GaussianTensors.from_scene(scene, device), cams, targets, st
 
 
-def run_config4(steps: int = 2000, log_path: str | None = None, **cfg_kw) -> dict:
-    g, cams, targets, st = config4_problem()
+def run_training(steps: int = 2000, log_path: str | None = None, **cfg_kw) -> dict:
+    g, cams, targets, st = offset_views_problem()
     tr = SteepGSTrainer(g, cams, targets, st, TrainConfig(steps=steps, **cfg_kw))
     wall = tr.run(steps, log_path)
     losses = [r["loss"] for r in tr.log if "loss" in r]
@@ -303,6 +303,6 @@ def run_config4(steps: int = 2000, log_path: str | None = None, **cfg_kw) -> dic
 
 if __name__ == "__main__":
     import sys
-    out = run_config4(int(sys.argv[1]) if len(sys.argv) > 1 else 2000,
+    out = run_training(int(sys.argv[1]) if len(sys.argv) > 1 else 2000,
                       sys.argv[2] if len(sys.argv) > 2 else None)
     print(json.dumps(out))

@@ -35,7 +35,7 @@ def _autograd_grads(scene, cams, st, gs):
     return {f: p.grad.cpu().numpy().astype(np.float64) for f, p in zip(FIELDS, params)}, S.cpu().numpy()
 
 
-def test_autograd_matches_oracle_gradient_config4():
+def test_autograd_matches_oracle_gradient_offset_views():
     scene = synth.tiny_scene(0, 4096)
     cams = synth.offset_cameras(128, 128, 128.0)
     st = synth.Settings()
@@ -53,7 +53,7 @@ def test_autograd_matches_oracle_gradient_config4():
     assert np.linalg.norm(S - up) / np.linalg.norm(up) < 1e-4
 
 
-def test_autograd_central_differences_config4():
+def test_autograd_central_differences_offset_views():
     """h = 1e-4 central differences of the float64 oracle render (smooth mode)
     against the float32 autograd gradient, on every parameter of a sample of
     Gaussians."""
@@ -100,7 +100,7 @@ def test_autograd_central_differences_config4():
 
 
 def test_training_loop_densifies_and_reduces_loss():
-    g, cams, targets, st = TR.config4_problem(n=1024, size=64)
+    g, cams, targets, st = TR.offset_views_problem(n=1024, size=64)
     cfg = TR.TrainConfig(steps=400, start=200, T_split=100, log_every=20)
     tr = TR.SteepGSTrainer(g, cams, targets, st, cfg)
     tr.run()
@@ -119,7 +119,7 @@ def test_training_loop_variants_theta4_and_ssim(dim_theta, lam):
     """Variants inside Algorithm 1: splitting over (position,
     opacity) or (position, log-scales, opacity) and the SSIM term in the
     loss."""
-    g, cams, targets, st = TR.config4_problem(n=1024, size=64)
+    g, cams, targets, st = TR.offset_views_problem(n=1024, size=64)
     cfg = TR.TrainConfig(steps=300, start=100, T_split=100, log_every=20, dim_theta=dim_theta, lambda_dssim=lam)
     tr = TR.SteepGSTrainer(g, cams, targets, st, cfg)
     tr.run()
@@ -139,7 +139,7 @@ def test_graphed_steps_follow_the_autograd_steps():
     Adam trajectory (bias corrections and loss sums may round differently)."""
     runs = []
     for graphs in (False, True):
-        g, cams, targets, st = TR.config4_problem(n=1024, size=64)
+        g, cams, targets, st = TR.offset_views_problem(n=1024, size=64)
         cfg = TR.TrainConfig(steps=40, start=1000, T_split=100, log_every=10, graphs=graphs)
         tr = TR.SteepGSTrainer(g, cams, targets, st, cfg)
         tr.run()
