@@ -130,6 +130,48 @@ def test_two_gaussians_composite_by_hand():
         assert np.abs(r["image"][32, 32] - expect).max() < 1e-12
 
 
+def test_projection_against_pinhole_jacobian_and_library_rotation():
+    """EWA projection by an independent route (Section 3, Eq. sigma_3D /
+    sigma_2D): the 2-D mean is the pinhole map of R p + t, P its Jacobian
+    with respect to p by central differences, Sigma_3D built with SciPy's
+    quaternion rotation, Sigma_2D = P Sigma_3D P^T + 0.3 I and the conic its
+    inverse; opacity is the logistic of the logit."""
+    from scipy.spatial.transform import Rotation
+    sc = synth.cluster_scene(4, 400, 0)
+    cam = synth.camera_lookat((0.5, -0.3, -6.0), (0, 0, 0), 160, 120, 160.0)
+    st = synth.Settings()
+    pr = oracle.project(sc, cam, st)
+    R = cam.R.astype(np.float64)
+    t = cam.t.astype(np.float64)
+
+    def pix(p):
+        x, y, z = R @ p + t
+        return np.array([cam.fx * x / z + cam.cx, cam.fy * y / z + cam.cy])
+
+    lim_x, lim_y = 1.3 * 0.5 * cam.width / cam.fx, 1.3 * 0.5 * cam.height / cam.fy
+    checked = 0
+    for i in range(sc.n):
+        p = sc.means[i].astype(np.float64)
+        x, y, z = R @ p + t
+        if pr["tiles"][i] == 0 or abs(x / z) >= lim_x or abs(y / z) >= lim_y:
+            continue                                   # culled, or the Jacobian clamp is active
+        checked += 1
+        assert np.allclose(pr["mean2d"][i], pix(p), rtol=0, atol=1e-9)
+        assert abs(pr["depth"][i] - z) < 1e-12
+        h = 1e-5
+        P = np.stack([(pix(p + h * e) - pix(p - h * e)) / (2 * h) for e in np.eye(3)], axis=1)
+        assert np.allclose(pr["P"][i], P, rtol=1e-7, atol=1e-7 * np.abs(P).max())
+        w, qx, qy, qz = sc.quats[i].astype(np.float64)
+        Rq = Rotation.from_quat([qx, qy, qz, w]).as_matrix()           # SciPy: scalar last
+        S3 = Rq @ np.diag(np.exp(2.0 * sc.log_scales[i].astype(np.float64))) @ Rq.T
+        S2 = pr["P"][i] @ S3 @ pr["P"][i].T + float(np.float32(st.dilation)) * np.eye(2)   # settings are float32
+        Q = np.linalg.inv(S2)
+        assert np.allclose(pr["conic"][i], [Q[0, 0], Q[0, 1], Q[1, 1]], rtol=1e-9, atol=0)
+        o = 1.0 / (1.0 + math.exp(-float(sc.opacity_logit[i])))
+        assert abs(pr["opacity"][i] - o) < 1e-12
+    assert checked > 100
+
+
 # --------------------------------------------------------------------------
 # Integer stages: brute force (binning, sort, ranges, rect coverage)
 # --------------------------------------------------------------------------
