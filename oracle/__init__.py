@@ -81,7 +81,7 @@ def _load():
             lib.orc_jacobi3.argtypes = [P, C.c_int, P, P]
             lib.orc_split.restype = C.c_int
             lib.orc_split.argtypes = [P, P, P, C.c_double, C.c_double, P, C.c_double, C.c_int64,
-                                      P, P, P, P, P, P, P]
+                                      P, P, P, P, P, P, P, P]
             lib.orc_sh_basis.argtypes = [C.c_int, P, C.c_int, P, P]
             _lib = lib
     return _lib
@@ -274,9 +274,11 @@ def jacobi3(S):
     return ev, V
 
 
-def split(scene, lam, v, eps_split, step_scale=1.0, grad_norm=None, eps_grad=0.0, budget=0):
+def split(scene, lam, v, eps_split, step_scale=1.0, grad_norm=None, eps_grad=0.0, budget=0, flags=None):
     """Steepest density control split and compaction (Theorem 2, Algorithm 1);
-    budget > 0 keeps only the `budget` least lambda_min (Variants section)."""
+    budget > 0 keeps only the `budget` least lambda_min (Variants section).
+    `flags` (bool [n]), when given, replaces the split rule: the exclusive
+    scan, parent indices and offspring follow from those decisions."""
     lib = _load()
     b = _Bound(scene, None, None)
     n, K = scene.n, (scene.sh_degree + 1) ** 2
@@ -284,14 +286,17 @@ def split(scene, lam, v, eps_split, step_scale=1.0, grad_norm=None, eps_grad=0.0
     out = dict(means=np.zeros((cap, 3)), log_scales=np.zeros((cap, 3)), quats=np.zeros((cap, 4)),
                opacity_logit=np.zeros(cap), sh=np.zeros((cap, K, 3)),
                parent=np.zeros(cap, np.int32))
-    flags = np.zeros(n, np.uint8)
+    flags_in, flags = flags, np.zeros(n, np.uint8)
     lam = np.ascontiguousarray(lam, np.float64)
     v = np.ascontiguousarray(v, np.float64)
     gn = None if grad_norm is None else np.ascontiguousarray(grad_norm, np.float64)
+    f_in = None if flags_in is None else np.ascontiguousarray(np.asarray(flags_in, bool).astype(np.uint8))
+    if f_in is not None and f_in.shape != (n,):
+        raise ValueError("flags must hold one decision per Gaussian")
     n_out = lib.orc_split(C.byref(b.scene), _ptr(lam), _ptr(v), float(eps_split), float(step_scale),
                           _ptr(gn), float(eps_grad), int(budget), _ptr(out["means"]), _ptr(out["log_scales"]),
                           _ptr(out["quats"]), _ptr(out["opacity_logit"]), _ptr(out["sh"]),
-                          _ptr(out["parent"]), _ptr(flags))
+                          _ptr(out["parent"]), _ptr(flags), _ptr(f_in))
     for k in list(out):
         out[k] = out[k][:n_out]
     out["flags"] = flags.astype(bool)
@@ -349,16 +354,19 @@ def S7_matrix(S, S_po, S_ls):
 OPACITY_SPLIT_MIN, OPACITY_SPLIT_MAX = 1e-4, 1.0 - 1e-4
 
 
-def split_po(scene, lam, v4, eps_split, step_scale=1.0):
+def split_po(scene, lam, v4, eps_split, step_scale=1.0, flags=None):
     """Steepest split over theta = (p, o) (v4 [n, 4]) or (p, l, o) (v [n, 7],
     l the log-scales): Gaussian i with lambda_min < eps_split becomes the
     w = 1/2 pair at theta +- eps_i v, eps_i = step_scale * max_k
     exp(log_scale_ik); each offspring keeps half of its displaced opacity,
     (o +- eps_i v_o) / 2 clamped to [1e-4, 1 - 1e-4]; the parent's row takes
-    the + offspring, the - offspring is appended in index order."""
+    the + offspring, the - offspring is appended in index order.  `flags`
+    (bool [n]), when given, replaces the rule lambda_min < eps_split."""
     n = scene.n
     K = (scene.sh_degree + 1) ** 2
-    flags = np.asarray(lam) < eps_split
+    flags = np.asarray(lam) < eps_split if flags is None else np.asarray(flags, bool).copy()
+    if flags.shape != (n,):
+        raise ValueError("flags must hold one decision per Gaussian")
     idx = np.nonzero(flags)[0]
     n_out = n + len(idx)
     eps = step_scale * np.exp(scene.log_scales.astype(np.float64)).max(axis=1)

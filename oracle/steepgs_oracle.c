@@ -1164,7 +1164,14 @@ void orc_jacobi3(const double *S, int n, double *evals, double *evecs)
 
 /* Increment budget (the "Densification with Increment Budget" variant): when
  * more than `budget` Gaussians qualify, only the `budget` ones with the least
- * lambda_min are split (ties by index). */
+ * lambda_min are split (ties by index).
+ *
+ * flags_in, when not NULL, gives the split decisions instead of the rule
+ * above (no gate, no budget): the exclusive scan and the offspring rows then
+ * follow from those flags alone.  A decision taken in float32 can differ from
+ * the float64 one only where lambda_min lies within rounding of eps_split;
+ * handing the other side's flags to this scan keeps the compaction indices
+ * and offspring comparable everywhere. */
 static const double *g_sel_lam;
 static int sel_cmp(const void *pa, const void *pb)
 {
@@ -1176,7 +1183,8 @@ static int sel_cmp(const void *pa, const void *pb)
 int orc_split(const orc_scene *sc, const double *lam, const double *v, double eps_split,
               double step_scale, const double *grad_norm, double eps_grad, int64_t budget,
               double *out_means, double *out_log_scales, double *out_quats,
-              double *out_logit, double *out_sh, int32_t *parent, uint8_t *flags)
+              double *out_logit, double *out_sh, int32_t *parent, uint8_t *flags,
+              const uint8_t *flags_in)
 {
     int n = sc->n;
     int K = (sc->sh_degree + 1) * (sc->sh_degree + 1);
@@ -1184,12 +1192,17 @@ int orc_split(const orc_scene *sc, const double *lam, const double *v, double ep
     int32_t run = 0;
     int cand = 0;
     for (int i = 0; i < n; ++i) {
-        int f = lam[i] < eps_split;
-        if (grad_norm) f = f && (grad_norm[i] <= eps_grad);
+        int f;
+        if (flags_in) {
+            f = flags_in[i] != 0;
+        } else {
+            f = lam[i] < eps_split;
+            if (grad_norm) f = f && (grad_norm[i] <= eps_grad);
+        }
         flags[i] = (uint8_t)f;
         cand += f;
     }
-    if (budget > 0 && cand > budget) {
+    if (!flags_in && budget > 0 && cand > budget) {
         int *idx = (int *)malloc(sizeof(int) * (size_t)cand);
         int m = 0;
         for (int i = 0; i < n; ++i)

@@ -608,6 +608,49 @@ def test_split_output_invariants():
     assert np.array_equal(out2["flags"], flags & (gn <= 0.5))
 
 
+def test_split_with_given_flags_is_the_scan_of_those_flags():
+    """The split driven by a given flag vector (how GPU decisions are handed
+    to the oracle's scan): with the rule's own flags it reproduces the rule's
+    output exactly; with arbitrary flags the appended rows are the flagged
+    indices in increasing order (the exclusive scan), each pair sits
+    symmetrically about its parent at distance eps_i along v, and unflagged
+    rows are copied."""
+    sc, cam, st, g, tgt, S = _setup_l1(0)
+    lam, v = oracle.eig3_min(S)
+    n = sc.n
+    rule = oracle.split(sc, lam, v, eps_split=-1e-6, step_scale=0.5)
+    same = oracle.split(sc, lam, v, eps_split=-1e-6, step_scale=0.5, flags=rule["flags"])
+    for k in ("means", "log_scales", "quats", "opacity_logit", "sh", "parent", "flags"):
+        assert np.array_equal(same[k], rule[k]), k
+    rng = np.random.default_rng(9)
+    for p_flag in (0.0, 0.3, 1.0):
+        f = rng.uniform(size=n) < p_flag
+        out = oracle.split(sc, lam, v, eps_split=-1e-6, step_scale=0.5, flags=f)
+        assert out["n_out"] == n + f.sum() and np.array_equal(out["flags"], f)
+        par = out["parent"]
+        assert np.array_equal(par[:n], np.arange(n))
+        assert list(par[n:]) == [i for i in range(n) if f[i]]
+        for r, i in enumerate(np.nonzero(f)[0]):
+            j = n + r
+            eps = 0.5 * np.exp(sc.log_scales[i].astype(np.float64)).max()
+            np.testing.assert_allclose(out["means"][i] - out["means"][j], 2 * eps * v[i], atol=1e-12)
+            np.testing.assert_allclose(out["means"][i] + out["means"][j], 2 * sc.means[i].astype(np.float64),
+                                       atol=1e-12)
+        keep = ~f
+        assert np.array_equal(out["means"][:n][keep], sc.means[keep].astype(np.float64))
+        assert np.array_equal(out["opacity_logit"][:n][keep], sc.opacity_logit[keep].astype(np.float64))
+    # the (p, o) split takes given flags the same way
+    acc = oracle.backward(sc, cam, st, g)
+    lam4, v4 = oracle.eig_min_sym(oracle.S4_matrix(acc["S"], acc["S_po"]))
+    r4 = oracle.split_po(sc, lam4, v4, -1e-9, 0.5)
+    s4 = oracle.split_po(sc, lam4, v4, -1e-9, 0.5, flags=r4["flags"])
+    for k in ("means", "opacity_logit", "parent", "flags"):
+        assert np.array_equal(s4[k], r4[k]), k
+    f = rng.uniform(size=n) < 0.4
+    o4 = oracle.split_po(sc, lam4, v4, -1e-9, 0.5, flags=f)
+    assert list(o4["parent"][n:]) == [i for i in range(n) if f[i]]
+
+
 def test_increment_budget_is_the_best_k_subset():
     """Increment budget (Appendix, "Densification with Increment Budget"): the
     second-order loss change of splitting Gaussian i along v_min is
