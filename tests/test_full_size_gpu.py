@@ -9,7 +9,9 @@ render_bwd_with_splitting, densify_split):
   * backward: dL/dimage non-zero on those strips only, against the oracle's
     backward of the same rows;
   * eigenpairs and the split of all 1M Gaussians from the GPU's splitting
-    matrices.
+    matrices: decisions against the oracle's outside the band, and the
+    compaction indices and offspring rows against the oracle's scan of the
+    GPU's own decisions.
 """
 import numpy as np
 import pytest
@@ -25,6 +27,8 @@ if not torch.cuda.is_available():
 
 from paper_2505_05587_gb300 import binding as B  # noqa: E402
 from paper_2505_05587_gb300 import pipeline as PL  # noqa: E402
+
+import split_parity as SP  # noqa: E402
 
 N, W, H = 1_000_000, 1237, 822
 FIELDS = ("means", "log_scales", "quats", "opacity_logit", "sh")
@@ -120,10 +124,14 @@ def test_full_size_backward_on_strips_and_split(full):
     assert not bad.any(), (int(bad.sum()), lam_g[bad][:5], lam_o[bad][:5], nrm[bad][:5], S_in[bad][:3])
     decided = np.abs(lam_o) > 1e-6 * np.maximum(nrm, 1e-30)
     n_out = int(db.n_out.item())
-    flags_g = np.zeros(N, bool)
-    flags_g[db.parent.cpu().numpy()[N:n_out]] = True
-    sp = oracle.split(scene, lam_o, v_o, 0.0, 1.0)
-    assert np.array_equal(flags_g[decided], sp["flags"][decided])
+    ev = np.linalg.eigvalsh(S_full)
+    gap = (ev[:, 1] - ev[:, 0]) > 1e-3 * nrm
+    v_g = db.v.cpu().numpy()
+    assert np.all(1 - np.abs(np.sum(v_g * v_o, 1))[gap] <= 1e-4)
+    flags_rule = lam_o < 0.0
+    # compaction indices and every offspring row of all 1M Gaussians, from the GPU's own decisions
+    flags_g = SP.check_split(scene, SP.gpu_out(db, n_out), db.parent.cpu().numpy(), n_out, lam_o, v_o,
+                             flags_rule, decided, gap, 0.0, 1.0, v_gpu=v_g)
     assert flags_g.sum() > 1000
 
 

@@ -17,6 +17,8 @@ from paper_2505_05587_gb300 import batched as BT  # noqa: E402
 from paper_2505_05587_gb300 import binding as B  # noqa: E402
 from paper_2505_05587_gb300 import pipeline as PL  # noqa: E402
 
+import split_parity as SP  # noqa: E402
+
 CASES = [
     ("tiny", lambda: synth.tiny_scene(0), lambda: synth.camera_identity(64, 64, 64.0), synth.Settings()),
     ("cluster_sh3_lookat", lambda: synth.cluster_scene(3, 3000, 3),
@@ -88,24 +90,11 @@ def test_densify_theta4_parity(name, mk_scene, mk_cam, st):
     decided = np.abs(lam_o + 1e-7) > 1e-6 * np.maximum(nrm, 1e-30)
     n = scene.n
     n_out = int(db.n_out.item())
-    flags_g = np.zeros(n, bool)
-    flags_g[db.parent.cpu().numpy()[n:n_out]] = True
     sp = oracle.split_po(scene, lam_o, v_o, -1e-7, step)
-    assert np.array_equal(flags_g[decided], sp["flags"][decided])
+    out = SP.gpu_out(db, n_out)
+    flags_g = SP.check_split(scene, out, db.parent.cpu().numpy(), n_out, lam_o, v_o, sp["flags"], decided, gap,
+                             -1e-7, step, dim=4, v_gpu=v_g)
     assert flags_g.sum() > 0
-    if np.array_equal(flags_g, sp["flags"]):
-        par = db.parent.cpu().numpy()[:n_out]
-        assert np.array_equal(par, sp["parent"])
-        ok = gap[par]                              # rows whose eigenvector is unique
-        om = db.out.means[:n_out].cpu().numpy()
-        s_max = np.exp(scene.log_scales.astype(np.float64)).max()
-        assert np.abs(om - sp["means"])[ok].max() < 1e-4 * step * s_max + 1e-6
-        ol = db.out.opacity_logit[:n_out].cpu().numpy()
-        o_g = 1 / (1 + np.exp(-ol.astype(np.float64)))
-        o_o = 1 / (1 + np.exp(-sp["opacity_logit"]))
-        assert np.abs(o_g - o_o)[ok].max() < 1e-5
-        for f in ("log_scales", "quats", "sh"):
-            assert np.array_equal(getattr(db.out, f)[:n_out].cpu().numpy(), sp[f].astype(np.float32))
 
 
 def test_theta4_multi_view_sums_views():
