@@ -218,16 +218,16 @@ def run_gpu(args):
         fwd_names = ["render_fwd", "ssim_l1_loss_grad"]
         fwd_calls = [lambda s: B.render_fwd(vb.proj, vb.bins, cam, st, vb.image, vb.final_T, vb.n_contrib, s),
                      lambda s: vb.loss_grad(target, 1, db.loss, args.lambda_dssim, s)]
-    names = ["zero_accumulators", "project", "bin_sort", *fwd_names, "render_bwd_with_splitting", "densify_split"]
+    names = ["clear_loss", "project", "bin_sort", *fwd_names, "render_bwd_with_splitting", "densify_split"]
     NC = len(names)
     calls = [
-        lambda s: db.zero_(grads=False, stream=s),     # S and loss; the backward overwrites the gradients
+        lambda s: db.zero_(grads=False, S=False, stream=s),   # the loss (a memset); the backward writes grads and S
         lambda s: B.project(g, cam, st, vb.proj, s),
         lambda s: B.bin_sort(vb.proj, g.n, cam, st, vb.bins, vb.sort_ws, s),
         *fwd_calls,
         lambda s: B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, vb.dL,
                                               db.grads, db.S, db.bwd_ws, s, accumulate=False, S_po=db.S_po,
-                                              S_ls=db.S_ls),
+                                              S_ls=db.S_ls, reset_S=True),
         lambda s: B.densify_split(g, db.S, 1.0, EPS_SPLIT, 1.0, None, 0.0, db.out, db.capacity, db.n_out,
                                   db.parent, db.lam, db.v, db.split_ws, s, S_po=db.S_po, S_ls=db.S_ls),
     ]

@@ -175,6 +175,12 @@ int sgs_version(void);
 /* Number of CUDA kernel launches this library has issued since it was loaded
  * (all threads), for measurement reports.  Memsets are not counted. */
 uint64_t sgs_kernel_launches(void);
+/* Clears `bytes` bytes of caller device memory at dst on the stream (a
+ * memset, no kernel launch; capture-safe): for the accumulators the entry
+ * points add into, such as the loss of sgs_render_fwd_l1 / sgs_l1_loss_grad
+ * and S_accum when no backward call resets it.  Errors:
+ * SGS_ERR_INVALID_ARG on a NULL dst with bytes > 0; SGS_ERR_CUDA. */
+int sgs_clear(void *dst, size_t bytes, void *stream);
 
 /* Projection (Section 3, Eq. sigma_2D and the affine-Pi footnote; Pi is the
  * pinhole map, linearised at p as P = J W for the 2-D covariance).
@@ -222,13 +228,6 @@ int sgs_render_fwd_l1(const sgs_proj *proj, const sgs_bins *bins, const sgs_came
                       const sgs_settings *st, const float *target, int32_t n_views, float *image,
                       float *final_T, uint32_t *n_contrib, float *dL_dimage, float *loss, void *stream);
 
-/* Pair counts of the forward walk (a measurement aid, not on the path):
- * counts [H,W,2] uint32 = (pairs evaluated, pairs composited) per pixel, the
- * work units behind the rasteriser's algorithmic FLOP count.  Errors: as
- * sgs_render_fwd. */
-int sgs_render_stats(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
-                     const sgs_settings *st, uint32_t *counts, void *stream);
-
 /* Photometric loss with the SSIM term of Gaussian-splatting training
  * (Section 3, Eq. loss; the paper's analysis keeps only L1, its footnote sets
  * SSIM aside):  loss += ((1 - lambda) L1 + lambda (1 - SSIM)) / n_views, with
@@ -245,14 +244,6 @@ int sgs_ssim_l1_workspace_size(int32_t height, int32_t width, size_t *bytes);
 int sgs_ssim_l1_loss_grad(const float *image, const float *target, int32_t height, int32_t width,
                           int32_t n_views, float lambda_dssim, float *dL_dimage, float *loss, void *ws,
                           size_t ws_bytes, void *stream);
-
-/* FP32 FMA throughput probe (a measurement aid, not on the path): `blocks`
- * blocks of 256 threads, each thread runs `iters` rounds of 8 independent
- * fused multiply-adds (16 FLOP per round) and writes one float to
- * out[blocks * 256].  Timing it gives the attainable FP32 peak that the
- * rasteriser's ALU roofline is quoted against.  Errors: SGS_ERR_INVALID_ARG
- * on a NULL out or non-positive blocks or iters. */
-int sgs_fma_probe(float *out, int32_t blocks, int32_t iters, void *stream);
 
 /* L1 photometric loss (Section 3, Eq. loss, l = |.|):
  * loss += mean over pixels and channels of |image - target| / n_views and
@@ -273,10 +264,22 @@ int sgs_render_bwd_workspace_size(int32_t n, size_t *bytes);
  * u = Q (x - mu) per composited, unclamped pair, the splitting matrix of this
  * view is S += P^T (sum w u u^T - (sum w) Q) P (the Appendix's Hessian
  * sigma (Y Y^T - P^T Q P), Y = P^T u, summed over pixels).
- * grads are accumulated (+=) when accumulate_grads != 0, else overwritten
- * (every row, zeros for Gaussians this view does not reach; no prior zeroing
- * needed).  S_accum [N,6] = (xx, xy, xz, yy, yz, zz) is always accumulated
- * (+=), so calling once per view (or per training step) sums over them.
+ * flags (a bit set; 0 = overwrite the gradients, add to S):
+ *   SGS_BWD_ACCUMULATE_GRADS  grads are accumulated (+=); without it they are
+ *                             overwritten (every row, zeros for Gaussians
+ *                             this view does not reach; no prior zeroing
+ *                             needed);
+ *   SGS_BWD_RESET_S           this call starts a new accumulation period of
+ *                             the splitting matrices (Algorithm 1 resets S
+ *                             after each densification): S_accum (and
+ *                             S_po_accum, S_ls_accum when given) are
+ *                             overwritten with this call's matrices, zeros
+ *                             where nothing composited; no prior zeroing
+ *                             needed.
+ *   Other bits: SGS_ERR_INVALID_ARG.
+ * Without SGS_BWD_RESET_S, S_accum [N,6] = (xx, xy, xz, yy, yz, zz) is
+ * accumulated (+=), so calling once per view (or per training step) sums over
+ * them.
  * S_po_accum [N,3] (may be NULL): when given, the position-opacity block of
  * the splitting matrix over theta = (p, o) is accumulated (+=) too:
  * sum dL/dsigma G P^T u = P^T Q (sum w (x - mu)) / o (the opacity-opacity
@@ -299,9 +302,11 @@ int sgs_render_bwd_workspace_size(int32_t n, size_t *bytes);
 int sgs_render_bwd_with_splitting(const sgs_gaussians *g, const sgs_proj *proj, const sgs_bins *bins,
                                   const sgs_camera *cam, const sgs_settings *st,
                                   const float *final_T, const uint32_t *n_contrib,
-                                  const float *dL_dimage, const sgs_grads *grads, int32_t accumulate_grads,
+                                  const float *dL_dimage, const sgs_grads *grads, int32_t flags,
                                   float *S_accum, float *S_po_accum, float *S_ls_accum, void *ws,
                                   size_t ws_bytes, void *stream);
+#define SGS_BWD_ACCUMULATE_GRADS 1
+#define SGS_BWD_RESET_S 2
 
 /* Several views of one scene in one pass (the batched densification step):
  * projection of every (view, Gaussian) pair, one binning and depth sort over
@@ -309,8 +314,9 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians *g, const sgs_proj *proj, 
  * compositing and its backward pass as persistent kernels that pull tiles of
  * all views from a work counter, the L1 loss of every view, and the
  * projection adjoint summing each Gaussian's views: gradients overwritten
- * (accumulate_grads = 0) or added, splitting matrices added to S_accum (and
- * the position-opacity blocks to S_po_accum when it is not NULL).
+ * or added and splitting matrices added to S_accum (and the position-opacity
+ * blocks to S_po_accum when it is not NULL) or written, by `flags` as in
+ * sgs_render_bwd_with_splitting.
  *   cams[n_views]      host array, 1 <= n_views <= 16, resolutions may differ;
  *   batch              Gaussians staged per shared-memory batch: 64, 128 or
  *                      256 (0 = min(tile pixels, 256));
@@ -327,7 +333,7 @@ int sgs_render_views_workspace_size(int32_t n, const sgs_camera *cams, int32_t n
                                     int64_t capacity, size_t *bytes);
 int sgs_render_views_with_splitting(const sgs_gaussians *g, const sgs_camera *cams, int32_t n_views,
                                     const sgs_settings *st, int32_t batch, const float *targets, float *images,
-                                    float *loss, const sgs_grads *grads, int32_t accumulate_grads, float *S_accum,
+                                    float *loss, const sgs_grads *grads, int32_t flags, float *S_accum,
                                     float *S_po_accum, int32_t *d_count, int64_t capacity, void *ws,
                                     size_t ws_bytes, void *stream);
 
@@ -414,7 +420,13 @@ int sgs_densify_split(const sgs_gaussians *in, const float *S_accum, const float
  *     device looks up the array's device address (cudaGetSymbolAddress) and
  *     caches it; make that first call before any stream capture begins.
  *   - Every call shares the one array, so calls whose work overlaps on the GPU
- *     (other streams, other threads) race: serialise them.
+ *     (other streams, other threads) race: serialise them.  The array keeps the
+ *     last call's contents; the call clears what it needs cleared itself.
+ *   - The cached address belongs to the device's current context: do not use
+ *     this entry point on a device after cudaDeviceReset in the same process.
+ *   - Scratch: 44 bytes per Gaussian plus the scan's partials (about 44 MB at
+ *     the maximum n); a build whose workspace layout outgrew the array returns
+ *     SGS_ERR_WORKSPACE for every call.
  *   - It calls no cudaMalloc, cudaFree or allocating routine. */
 #define SGS_NOALLOC_MAX_GAUSSIANS 1000000
 #define SGS_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
@@ -423,6 +435,25 @@ int sgs_densify_split_noalloc(const sgs_gaussians *in, const float *S_accum, con
                               float eps_split, float step_scale, const float *grad_norm, float eps_grad,
                               int64_t max_splits, const sgs_gaussians_mut *out, int64_t capacity, int32_t *d_n_out,
                               int32_t *parent_index, float *lam_min_out, float *v_min_out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Measurement instrumentation.  Not steps of the method and not used by its
+ * path: the benchmark calls them to count the rasteriser's work units and to
+ * measure the FP32 roofline it quotes.
+ * ------------------------------------------------------------------------ */
+
+/* Pair counts of the forward walk: counts [H,W,2] uint32 = (pairs evaluated,
+ * pairs composited) per pixel, the work units behind the rasteriser's
+ * algorithmic FLOP count.  Errors: as sgs_render_fwd. */
+int sgs_render_stats(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
+                     const sgs_settings *st, uint32_t *counts, void *stream);
+
+/* FP32 FMA throughput probe: `blocks` blocks of 256 threads, each thread runs
+ * `iters` rounds of 8 independent fused multiply-adds (16 FLOP per round) and
+ * writes one float to out[blocks * 256].  Timing it gives the attainable FP32
+ * peak that the rasteriser's ALU roofline is quoted against.  Errors:
+ * SGS_ERR_INVALID_ARG on a NULL out or non-positive blocks or iters. */
+int sgs_fma_probe(float *out, int32_t blocks, int32_t iters, void *stream);
 
 #ifdef __cplusplus
 }

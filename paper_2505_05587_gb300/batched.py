@@ -52,10 +52,10 @@ class BatchedDensifyStep:
         self.graph = None
 
     def run_eager(self, stream=None):
-        self.S.zero_()
-        self.loss.zero_()
+        B.clear(self.loss, stream)          # the projection adjoint writes the gradients and S (reset)
         B.render_views_with_splitting(self.g, self.cams, self.st, self.batch, self.targets, self.images, self.loss,
-                                      self.grads, False, self.S, self.count, self.capacity, self.ws, stream)
+                                      self.grads, False, self.S, self.count, self.capacity, self.ws, stream,
+                                      reset_S=True)
         db = self.db
         B.densify_split(self.g, self.S, 1.0, self.eps_split, self.step_scale, None, 0.0, db.out, db.capacity,
                         db.n_out, db.parent, db.lam, db.v, db.split_ws, stream)

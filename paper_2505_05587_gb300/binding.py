@@ -119,6 +119,8 @@ def lib():
         L.sgs_fma_probe.argtypes = [P, I32, I32, P]
         L.sgs_fma_probe.restype = C.c_int
         L.sgs_densify_split_noalloc.argtypes = [P, P, P, P, F, F, F, P, F, I64, P, I64, P, P, P, P, P]
+        L.sgs_clear.argtypes = [P, SZ, P]
+        L.sgs_clear.restype = C.c_int
         for name in ("sgs_project", "sgs_bin_sort_workspace_size", "sgs_bin_sort", "sgs_render_fwd",
                      "sgs_l1_loss_grad", "sgs_render_stats", "sgs_render_bwd_workspace_size", "sgs_render_bwd_with_splitting",
                      "sgs_densify_split_workspace_size", "sgs_densify_split", "sgs_densify_split_noalloc"):
@@ -415,12 +417,27 @@ def render_bwd_workspace_size(n: int) -> int:
     return b.value
 
 
+BWD_ACCUMULATE_GRADS, BWD_RESET_S = 1, 2
+
+
+def _bwd_flags(accumulate: bool, reset_S: bool) -> int:
+    return (BWD_ACCUMULATE_GRADS if accumulate else 0) | (BWD_RESET_S if reset_S else 0)
+
+
+def clear(t: torch.Tensor, stream=None):
+    """Zeroes a contiguous device tensor with a memset on `stream` (no kernel)."""
+    if not t.is_contiguous():
+        raise ValueError("clear: tensor must be contiguous")
+    _check("sgs_clear", lib().sgs_clear(_p(t), t.numel() * t.element_size(), _stream(stream)))
+
+
 def render_bwd_with_splitting(g: GaussianTensors, proj: ProjBuffers, bins: BinBuffers, cam, st, final_T,
                               n_contrib, dL_dimage, grads: GaussianTensors, S_accum, ws, stream=None,
-                              accumulate: bool = True, S_po=None, S_ls=None):
+                              accumulate: bool = True, S_po=None, S_ls=None, reset_S: bool = False):
     """S_po [N,3] (optional): the position-opacity block of the splitting
     matrix over theta = (p, o) is accumulated too; S_ls [N,18] (optional, with
-    S_po): the log-scale blocks over theta = (p, l, o) as well."""
+    S_po): the log-scale blocks over theta = (p, l, o) as well.  reset_S: the
+    call starts a new accumulation period (S, S_po, S_ls overwritten)."""
     gc, pc, bc, cc, sc = g.c(), proj.c(g.n), bins.c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
     grc = grads.grads_c(g)
     n, P = g.n, _pixels(cam)
@@ -428,7 +445,7 @@ def render_bwd_with_splitting(g: GaussianTensors, proj: ProjBuffers, bins: BinBu
            lib().sgs_render_bwd_with_splitting(C.byref(gc), C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
                                                _arr(final_T, "final_T", F32, P), _arr(n_contrib, "n_contrib", I32, P),
                                                _arr(dL_dimage, "dL_dimage", F32, 3 * P), C.byref(grc),
-                                               1 if accumulate else 0, _arr(S_accum, "S_accum", F32, 6 * n),
+                                               _bwd_flags(accumulate, reset_S), _arr(S_accum, "S_accum", F32, 6 * n),
                                                _arr(S_po, "S_po", F32, 3 * n), _arr(S_ls, "S_ls", F32, 18 * n), _p(ws),
                                                ws.numel() * ws.element_size(),
                                                _stream(stream)))
@@ -451,9 +468,10 @@ def render_views_workspace_size(n: int, cams, st, capacity: int) -> int:
 
 def render_views_with_splitting(g: GaussianTensors, cams, st, batch: int, targets, images, loss,
                                 grads: GaussianTensors, accumulate: bool, S_accum, d_count, capacity: int, ws,
-                                stream=None, S_po=None):
+                                stream=None, S_po=None, reset_S: bool = False):
     """All views in one pass: project, bin/sort, persistent forward, L1,
-    persistent backward, projection adjoint (see sgs_render_views_with_splitting)."""
+    persistent backward, projection adjoint (see sgs_render_views_with_splitting);
+    reset_S: S (and S_po) overwritten instead of added to."""
     gc, arr, sc = g.c(), cameras_c(cams), settings_c(st)
     grc = grads.grads_c(g)
     n, P = g.n, sum(_pixels(c) for c in cams)
@@ -461,7 +479,7 @@ def render_views_with_splitting(g: GaussianTensors, cams, st, batch: int, target
            lib().sgs_render_views_with_splitting(C.byref(gc), arr, len(cams), C.byref(sc), batch,
                                                  _arr(targets, "targets", F32, 3 * P),
                                                  _arr(images, "images", F32, 3 * P), _arr(loss, "loss", F32, 1),
-                                                 C.byref(grc), 1 if accumulate else 0,
+                                                 C.byref(grc), _bwd_flags(accumulate, reset_S),
                                                  _arr(S_accum, "S_accum", F32, 6 * n), _arr(S_po, "S_po", F32, 3 * n),
                                                  _arr(d_count, "d_count", I32, 1), capacity, _p(ws),
                                                  ws.numel() * ws.element_size(), _stream(stream)))

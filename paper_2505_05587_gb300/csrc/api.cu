@@ -140,6 +140,12 @@ int sgs_version(void) { return 100; }
 
 uint64_t sgs_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
+int sgs_clear(void* dst, size_t bytes, void* stream) {
+    if (bytes == 0) return SGS_OK;
+    if (!dst) return SGS_ERR_INVALID_ARG;
+    return cuda_status(cudaMemsetAsync(dst, 0, bytes, (cudaStream_t)stream));
+}
+
 int sgs_project(const sgs_gaussians* g, const sgs_camera* cam, const sgs_settings* st, const sgs_proj* out,
                 void* stream) {
     if (!valid_gaussians(g) || !valid_cam(cam) || !valid_settings(st) || !out || !tiles_fit(cam, st))
@@ -239,8 +245,9 @@ int sgs_render_bwd_workspace_size(int32_t n, size_t* bytes) {
 int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, const sgs_bins* bins,
                                   const sgs_camera* cam, const sgs_settings* st, const float* final_T,
                                   const uint32_t* n_contrib, const float* dL_dimage, const sgs_grads* grads,
-                                  int32_t accumulate_grads, float* S_accum, float* S_po_accum, float* S_ls_accum,
+                                  int32_t flags, float* S_accum, float* S_po_accum, float* S_ls_accum,
                                   void* ws, size_t ws_bytes, void* stream) {
+    if (flags & ~(SGS_BWD_ACCUMULATE_GRADS | SGS_BWD_RESET_S)) return SGS_ERR_INVALID_ARG;
     if (!valid_gaussians(g) || !proj || !bins || !valid_cam(cam) || !valid_settings(st) || !final_T ||
         !n_contrib || !dL_dimage || !grads || !tiles_fit(cam, st) || !bins->ranges)
         return SGS_ERR_INVALID_ARG;
@@ -262,8 +269,8 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
     if (e == cudaSuccess)
         e = launch_render_bwd(*proj, *bins, cd, sd, final_T, n_contrib, dL_dimage, g2d, g2d_hi, s);
     if (e == cudaSuccess)
-        e = launch_project_bwd(*g, *proj, make_views(cam, 1, *st, nullptr, g->n), g2d, g2d_hi,
-                               accumulate_grads != 0, *grads, S_accum, S_po_accum, S_ls_accum, s);
+        e = launch_project_bwd(*g, *proj, make_views(cam, 1, *st, nullptr, g->n), g2d, g2d_hi, flags, *grads,
+                               S_accum, S_po_accum, S_ls_accum, s);
     return cuda_status(e);
 }
 
@@ -355,9 +362,10 @@ int sgs_render_views_workspace_size(int32_t n, const sgs_camera* cams, int32_t n
 
 int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* cams, int32_t n_views,
                                     const sgs_settings* st, int32_t batch, const float* targets, float* images,
-                                    float* loss, const sgs_grads* grads, int32_t accumulate_grads, float* S_accum,
+                                    float* loss, const sgs_grads* grads, int32_t flags, float* S_accum,
                                     float* S_po_accum,
                                     int32_t* d_count, int64_t capacity, void* ws, size_t ws_bytes, void* stream) {
+    if (flags & ~(SGS_BWD_ACCUMULATE_GRADS | SGS_BWD_RESET_S)) return SGS_ERR_INVALID_ARG;
     if (!valid_gaussians(g) || !valid_views(cams, n_views, st) || !targets || !images || !loss || !grads ||
         !d_count || capacity < 0 || capacity > ((int64_t)1 << 31) - 1 ||
         (long long)g->n * n_views > ((long long)1 << 31) - 1)
@@ -387,8 +395,7 @@ int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* ca
         e = launch_render_bwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, w.final_T, w.n_contrib,
                                     w.dL, w.g2d, w.counters + 1, w.bins.order, s);
     if (e == cudaSuccess)
-        e = launch_project_bwd(*g, w.proj, vd, w.g2d, nullptr, accumulate_grads != 0, *grads, S_accum, S_po_accum,
-                               nullptr, s);
+        e = launch_project_bwd(*g, w.proj, vd, w.g2d, nullptr, flags, *grads, S_accum, S_po_accum, nullptr, s);
     return cuda_status(e);
 }
 

@@ -146,11 +146,15 @@ ScenesDev make_scenes(const sgs_gaussians* g, int nv, bool per_view);
 SetDev make_set(const sgs_settings& s);
 bool tile_supported(int tw, int th);
 
+// Flags of the projection adjoint (the backward entry points' `flags`).
+constexpr int kBwdAccumulateGrads = SGS_BWD_ACCUMULATE_GRADS;
+constexpr int kBwdResetS = SGS_BWD_RESET_S;
+
 // Launchers (host functions, enqueue on `stream`).
 cudaError_t launch_project(const ScenesDev& sc, int sh_degree, const ViewsDev& vd, const SetDev& st,
                            const sgs_proj& out, cudaStream_t stream);
 cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const ViewsDev& vd, const float* g2d,
-                               const float* g2d_hi, bool accumulate, const sgs_grads& grads, float* S_accum,
+                               const float* g2d_hi, int flags, const sgs_grads& grads, float* S_accum,
                                float* S_po_accum, float* S_ls_accum, cudaStream_t stream);
 
 size_t bin_sort_ws_bytes(int n, int64_t capacity, int num_tiles);

@@ -15,8 +15,12 @@
 namespace sgs {
 
 // Scratch for sgs_densify_split_noalloc: split flags, their prefix sum, the
-// eigenpairs when the caller passes no output for them, the budget's tie
-// flags and the scan's block partials -- about 28 bytes per Gaussian.
+// eigenvalue and the (up to 7-component) eigenvector when the caller passes no
+// output for them, and the budget's tie flags -- 4 + 4 + 4 + 28 + 4 = 44 bytes
+// per Gaussian -- plus the scan's block partials and 256-byte alignment of
+// each region: about 44 MB at SGS_NOALLOC_MAX_GAUSSIANS.  Every call checks
+// that the largest allowed n still fits, so a change of the workspace layout
+// cannot silently shrink the documented limit.
 static __device__ __align__(256) unsigned char g_densify_scratch[SGS_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
@@ -25,7 +29,9 @@ static std::mutex g_scratch_mu;
 
 // Device address of the scratch array on the calling thread's current device.
 // Host code cannot use the array's name as a device address, so the address is
-// looked up once per device (with that device current) and cached.
+// looked up once per device (with that device current) and cached for the life
+// of the process: a device reset (cudaDeviceReset) reloads the library's device
+// image elsewhere, after which the cached address is stale.
 static int scratch_address(void** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -52,6 +58,7 @@ extern "C" int sgs_densify_split_noalloc(const sgs_gaussians* in, const float* S
                                          const sgs_gaussians_mut* out, int64_t capacity, int32_t* d_n_out,
                                          int32_t* parent_index, float* lam_min_out, float* v_min_out,
                                          void* stream) {
+    if (densify_ws_bytes(SGS_NOALLOC_MAX_GAUSSIANS) > (size_t)SGS_NOALLOC_SCRATCH_BYTES) return SGS_ERR_WORKSPACE;
     if (!in || in->n < 0 || in->n > SGS_NOALLOC_MAX_GAUSSIANS) return SGS_ERR_INVALID_ARG;
     if (densify_ws_bytes(in->n) > (size_t)SGS_NOALLOC_SCRATCH_BYTES) return SGS_ERR_WORKSPACE;
     void* ws = nullptr;

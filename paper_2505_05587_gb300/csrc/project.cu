@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 7)) pr
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ sh, int n, ViewsDev vd, const float4* __restrict__ conic_opac,
     const uint32_t* __restrict__ tiles, const float* __restrict__ g2d, const float* __restrict__ g2d_hi,
-    int accumulate,
+    int flags,
     float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
     float* __restrict__ g_logit, float* __restrict__ g_sh, float* __restrict__ S_accum,
     float* __restrict__ S_po_accum, float* __restrict__ S_ls_accum) {
@@ -592,8 +592,18 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 7)) pr
         for (int v = 0; v < nv; ++v)
             if (tiles[(long long)v * n + i] != 0u) tmask |= 1u << v;
     const uint32_t vis = __ballot_sync(0xffffffffu, tmask != 0u);
-    if (vis == 0u && accumulate) return;             // nothing in this warp reached a tile
+    const bool accumulate = (flags & kBwdAccumulateGrads) != 0;
+    const bool reset_S = (flags & kBwdResetS) != 0;
+    if (vis == 0u && accumulate && !reset_S) return;  // nothing in this warp reached a tile
     const int rows = min(32, n - base);
+    if (vis == 0u && reset_S) {                      // unreached rows of a reset: zero splitting matrices
+        for (int f = lane; f < 6 * rows; f += 32) S_accum[6 * (size_t)base + f] = 0.0f;
+        if constexpr (PO)
+            for (int f = lane; f < 3 * rows; f += 32) S_po_accum[3 * (size_t)base + f] = 0.0f;
+        if constexpr (LS)
+            for (int f = lane; f < 18 * rows; f += 32) S_ls_accum[18 * (size_t)base + f] = 0.0f;
+        if (accumulate) return;
+    }
     if (vis == 0u) {                                 // unreached rows: zero gradients, nothing staged
         for (int f = lane; f < 3 * rows; f += 32) {
             g_means[3 * (size_t)base + f] = 0.0f;
@@ -726,18 +736,22 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 7)) pr
                 }
             }
         }
+    }
+    // splitting matrices: added (Algorithm 1 sums them over views and steps),
+    // or, on a reset, written for every row (zeros where nothing composited)
+    if (i < n && (work || reset_S)) {
         float* So = S_accum + (size_t)i * 6;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) So[k] += S6[k];
+        for (int k = 0; k < 6; ++k) So[k] = reset_S ? S6[k] : So[k] + S6[k];
         if constexpr (PO) {
             float* Sp = S_po_accum + (size_t)i * 3;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) Sp[k] += Spo[k];
+            for (int k = 0; k < 3; ++k) Sp[k] = reset_S ? Spo[k] : Sp[k] + Spo[k];
         }
         if constexpr (LS) {
             float* Sl = S_ls_accum + (size_t)i * 18;
 #pragma unroll
-            for (int k = 0; k < 18; ++k) Sl[k] += Sls[k];
+            for (int k = 0; k < 18; ++k) Sl[k] = reset_S ? Sls[k] : Sl[k] + Sls[k];
         }
     }
     if (i < n) {
@@ -772,7 +786,7 @@ __global__ void __launch_bounds__(MULTI ? 64 : 128, MULTI ? 8 : (LS ? 3 : 7)) pr
 }
 
 cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, const ViewsDev& vd, const float* g2d,
-                               const float* g2d_hi, bool accumulate, const sgs_grads& grads, float* S_accum,
+                               const float* g2d_hi, int flags, const sgs_grads& grads, float* S_accum,
                                float* S_po_accum, float* S_ls_accum, cudaStream_t stream) {
     if (g.n == 0) return cudaSuccess;
     const bool multi = vd.nv > 1;
@@ -799,7 +813,7 @@ cudaError_t launch_project_bwd(const sgs_gaussians& g, const sgs_proj& proj, con
              : g.sh_degree == 2 ? project_bwd_kernel<2, false, true, true> : project_bwd_kernel<3, false, true, true>;
     (void)launch_pdl(kern, dim3(blocks), dim3(threads), 0, stream, g.means, g.log_scales, g.quats, g.sh, g.n, vd,
                      reinterpret_cast<const float4*>(proj.conic_opac), proj.tiles_touched, g2d, g2d_hi,
-                     accumulate ? 1 : 0, grads.means, grads.log_scales, grads.quats, grads.opacity_logit, grads.sh,
+                     flags, grads.means, grads.log_scales, grads.quats, grads.opacity_logit, grads.sh,
                      S_accum, S_po_accum, S_ls_accum);
     note_launch();
     return cudaGetLastError();

@@ -138,19 +138,18 @@ class DensifyBuffers:
                               torch.zeros(n, 3, device=dev) if dim_theta > 3 else None,
                               torch.zeros(n, 18, device=dev) if dim_theta == 7 else None)
 
-    def zero_(self, grads: bool = True, stream=None):
-        """Resets the accumulators (on `stream`, default the current one); the
-        gradients need no reset when the first backward call of an iteration
-        overwrites them."""
-        with torch.cuda.stream(as_stream(stream)):
-            if grads:
-                for t in self.grads.tensors():
-                    t.zero_()
-            self.S.zero_()
-            for t in (self.S_po, self.S_ls):
-                if t is not None:
-                    t.zero_()
-            self.loss.zero_()
+    def zero_(self, grads: bool = True, S: bool = True, stream=None):
+        """Resets the accumulators with library memsets on `stream` (default
+        the current one).  The gradients need no reset when the first backward
+        call of an iteration overwrites them, nor the splitting matrices when
+        it resets them (reset_S)."""
+        ts = [self.loss]
+        if grads:
+            ts += list(self.grads.tensors())
+        if S:
+            ts += [t for t in (self.S, self.S_po, self.S_ls) if t is not None]
+        for t in ts:
+            B.clear(t, stream)
 
 
 def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: list[torch.Tensor],
@@ -160,7 +159,7 @@ def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: lis
     """One fused fwd+bwd+splitting iteration over the views (Algorithm 1 with
     the split step taken right after accumulation).  lambda_dssim set: the loss
     has the SSIM term, (1 - lambda) L1 + lambda (1 - SSIM)."""
-    db.zero_(grads=False, stream=stream)
+    db.zero_(grads=False, S=False, stream=stream)    # the loss; the first backward writes grads and S
     V = len(views)
     for k, (vb, tgt) in enumerate(zip(views, targets)):
         project_and_sort(g, vb, stream, check_capacity)
@@ -170,10 +169,11 @@ def fused_iteration(g: B.GaussianTensors, views: list[ViewBuffers], targets: lis
         else:
             B.render_fwd(vb.proj, vb.bins, vb.cam, vb.st, vb.image, vb.final_T, vb.n_contrib, stream)
             vb.loss_grad(tgt, V, db.loss, lambda_dssim, stream)
-        # the first view overwrites the gradients, later views add to them
+        # the first view overwrites the gradients and starts the splitting
+        # matrices' accumulation; later views add to both
         B.render_bwd_with_splitting(g, vb.proj, vb.bins, vb.cam, vb.st, vb.final_T, vb.n_contrib, vb.dL,
                                     db.grads, db.S, db.bwd_ws, stream, accumulate=k > 0, S_po=db.S_po,
-                                    S_ls=db.S_ls)
+                                    S_ls=db.S_ls, reset_S=k == 0)
     B.densify_split(g, db.S, 1.0 / T_split, eps_split, step_scale, grad_norm, eps_grad, db.out, db.capacity,
                     db.n_out, db.parent, db.lam, db.v, db.split_ws, stream, max_splits=max_splits, S_po=db.S_po,
                     S_ls=db.S_ls)

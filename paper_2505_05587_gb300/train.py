@@ -154,7 +154,7 @@ class SteepGSTrainer:
             with torch.cuda.graph(ga, stream=cs):
                 PL.project_and_sort(g, vb, cs, check_capacity=False)
             with torch.cuda.graph(gb, stream=cs):
-                self.loss.zero_()
+                B.clear(self.loss, cs)
                 if cfg.lambda_dssim is None:
                     B.render_fwd_l1(vb.proj, vb.bins, vb.cam, vb.st, self.targets[k], 1, vb.image, vb.final_T,
                                     vb.n_contrib, self.dL[k], self.loss, cs)
@@ -201,7 +201,7 @@ class SteepGSTrainer:
             return loss
         rc = RenderContext(self.views[k], self.S, self.bwd_ws, self.sh_degree, self.S_po, self.S_ls)
         image = render(self.params, rc)
-        self.loss.zero_()
+        B.clear(self.loss)
         if self.cfg.lambda_dssim is None:
             B.l1_loss_grad(image.detach(), self.targets[k], 1, self.dL[k], self.loss)
         else:

@@ -9,7 +9,11 @@ threshold (the band).  The check therefore:
      Gaussians) and requires parent[:n] = 0..n-1 and parent[n:] strictly
      increasing;
   2. requires the GPU flags to equal the oracle's rule outside the band, and
-     the mismatches (all inside it) to number at most ceil(1e-4 n);
+     the mismatches (all inside it) to number at most ceil(1e-4 n), not
+     counting Gaussians whose lambda_min sits exactly at the threshold in
+     exact arithmetic (`structural`: on one view S = P^T M P has rank <= 2,
+     so lambda_min = 0 wherever M is positive semidefinite, and at
+     eps_split = 0 both sides then decide on the sign of rounding error);
   3. hands the GPU's flags to the oracle's scan (Theorem 2, Algorithm 1:
      exclusive scan of the flags, the + offspring in the parent's row, the -
      offspring appended in index order) and compares every output row:
@@ -38,8 +42,15 @@ def gpu_flags(parent, n, n_out):
     return f
 
 
+def structural_zeros(lam_exact, nrm_exact, eps_split, rel=1e-12):
+    """Gaussians whose lambda_min, from the float64 oracle's own splitting
+    matrices, equals eps_split up to float64 rounding: their decision is not
+    determined by the method, only by rounding."""
+    return np.abs(np.asarray(lam_exact) - eps_split) <= rel * np.maximum(np.asarray(nrm_exact), 1e-300)
+
+
 def check_split(scene, out, parent, n_out, lam_o, v_o, flags_rule, decided, gap, eps_split, step_scale,
-                dim=3, v_gpu=None):
+                dim=3, v_gpu=None, structural=None):
     """Compare the GPU split (output fields `out` as numpy arrays, `parent`,
     `n_out`) with the oracle's split of the GPU's own flags.
 
@@ -52,7 +63,9 @@ def check_split(scene, out, parent, n_out, lam_o, v_o, flags_rule, decided, gap,
     flags_g = gpu_flags(parent, n, n_out)
     mism = flags_g != np.asarray(flags_rule, bool)
     assert not (mism & decided).any(), f"{int((mism & decided).sum())} split decisions differ outside the band"
-    assert mism.sum() <= math.ceil(1e-4 * n), f"{int(mism.sum())} banded decisions differ"
+    counted = mism if structural is None else mism & ~np.asarray(structural, bool)
+    assert counted.sum() <= math.ceil(1e-4 * n), \
+        f"{int(counted.sum())} banded decisions differ ({int(mism.sum())} with those at exactly the threshold)"
     if dim == 3:
         sp = oracle.split(scene, lam_o, v_o, eps_split, step_scale, flags=flags_g)
     else:

@@ -96,6 +96,14 @@ def test_backward_checks(lib):
     base = [C.byref(g), C.byref(p), C.byref(b), C.byref(cam), C.byref(st), _ptr(1), _ptr(2), _ptr(3),
             C.byref(grads), 0, _ptr(4), None, None, _ptr(7), need.value, None]
     assert lib.sgs_render_bwd_with_splitting(*base) == NO_DEVICE
+    for flags in (1, 2, 3):                                                     # accumulate grads, reset S, both
+        a = list(base)
+        a[9] = flags
+        assert lib.sgs_render_bwd_with_splitting(*a) == NO_DEVICE
+    for flags in (4, -1):                                                       # undefined flag bits
+        a = list(base)
+        a[9] = flags
+        assert lib.sgs_render_bwd_with_splitting(*a) == INVALID
     a = list(base)
     a[12] = _ptr(6)                                                             # S_ls without S_po
     assert lib.sgs_render_bwd_with_splitting(*a) == INVALID
@@ -136,6 +144,17 @@ def test_densify_checks(lib):
     big = _gauss(1_000_001)                                                     # beyond the fixed scratch
     assert lib.sgs_densify_split_noalloc(C.byref(big), _ptr(1), None, None, 1.0, 0.0, 1.0, None, 0.0, 0,
                                          C.byref(out), 2_000_002, _ptr(2), None, None, None, None) == INVALID
+    # the largest allowed n passes every size check (its workspace fits the
+    # fixed array) and fails only for want of a device
+    top = _gauss(1_000_000)
+    assert lib.sgs_densify_split_noalloc(C.byref(top), _ptr(1), None, None, 1.0, 0.0, 1.0, None, 0.0, 0,
+                                         C.byref(out), 2_000_000, _ptr(2), None, None, None, None) == NO_DEVICE
+
+
+def test_clear_checks(lib):
+    assert lib.sgs_clear(None, 0, None) == 0                                   # nothing to clear
+    assert lib.sgs_clear(None, 16, None) == INVALID
+    assert lib.sgs_clear(_ptr(1), 16, None) == NO_DEVICE
 
 
 def test_adam_and_probe_checks(lib):
@@ -168,6 +187,9 @@ def test_batched_checks(lib):
     base = [C.byref(g), cams, 2, C.byref(st), 128, _ptr(1), _ptr(2), _ptr(3), C.byref(grads), 0, _ptr(4), None,
             _ptr(5), 1000, _ptr(6), sz.value, None]
     assert lib.sgs_render_views_with_splitting(*base) == NO_DEVICE
+    a = list(base)
+    a[9] = 8                                                                    # undefined flag bit
+    assert lib.sgs_render_views_with_splitting(*a) == INVALID
     a = list(base)
     a[4] = 100                                                                  # batch not 64/128/256
     assert lib.sgs_render_views_with_splitting(*a) == INVALID

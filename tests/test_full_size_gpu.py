@@ -129,9 +129,11 @@ def test_full_size_backward_on_strips_and_split(full):
     v_g = db.v.cpu().numpy()
     assert np.all(1 - np.abs(np.sum(v_g * v_o, 1))[gap] <= 1e-4)
     flags_rule = lam_o < 0.0
+    lam_x, _ = oracle.eig3_min(acc["S"])                  # the oracle's own float64 matrices
+    structural = SP.structural_zeros(lam_x, np.linalg.norm(acc["S"].reshape(N, 9), axis=1), 0.0)
     # compaction indices and every offspring row of all 1M Gaussians, from the GPU's own decisions
     flags_g = SP.check_split(scene, SP.gpu_out(db, n_out), db.parent.cpu().numpy(), n_out, lam_o, v_o,
-                             flags_rule, decided, gap, 0.0, 1.0, v_gpu=v_g)
+                             flags_rule, decided, gap, 0.0, 1.0, v_gpu=v_g, structural=structural)
     assert flags_g.sum() > 1000
 
 

@@ -141,7 +141,10 @@ def test_eigenpairs_and_split(gold, run):
     decided = np.abs(lam_o - gold["workload"]["eps_split"]) > 1e-6
     assert decided.sum() > 0.8 * n
     assert np.array_equal(flags_g[decided], flags_o[decided])
-    assert int(np.sum(flags_g != flags_o)) <= int(np.ceil(1e-4 * n))
+    # decisions at exactly the threshold in exact arithmetic (a rank-2 single-view S with lambda_min = 0)
+    # are the sign of rounding on both sides and are not counted
+    structural = np.abs(lam_o - gold["workload"]["eps_split"]) <= 1e-12 * np.abs(lam_o).max()
+    assert int(np.sum((flags_g != flags_o) & ~structural)) <= int(np.ceil(1e-4 * n))
     # the compaction is the exclusive scan of the GPU's own flags: the first n
     # rows in place, the split Gaussians appended once each in index order
     par = np.asarray(run["parent"][:run["n_out"]])

@@ -168,6 +168,63 @@ def test_backward_overwrite_and_accumulate_modes():
     assert _rel(S.cpu().numpy(), 2.0 * _upper6(acc["S"])) < 1e-4
 
 
+def test_backward_reset_of_splitting_matrices():
+    """reset_S: the call writes S (every row, zeros where nothing composited)
+    instead of adding, whatever S held before; with gradients accumulated or
+    overwritten; a following call without it adds.  Single view at dim
+    Theta 3 and 4, and the multi-view pass."""
+    scene = synth.cluster_scene(3, 3000, 3)
+    cam = synth.camera_lookat((1.0, 0.5, -6.0), (0, 0, 0), 150, 101, 150.0)
+    st = synth.Settings()
+    grads_ref, S_ref, acc, _, _ = _backward_both(scene, cam, st)
+    g, vb = _render_gpu(scene, cam, st)
+    ref = oracle.render(scene, cam, st)
+    _, dL_ref = oracle.l1_loss_grad(ref["image"], synth.target_image(2, cam.height, cam.width))
+    dL = torch.as_tensor(dL_ref.astype(np.float32)).cuda().contiguous()
+    ws = B.workspace(B.render_bwd_workspace_size(scene.n))
+    for accumulate in (False, True):
+        grads = g.zeros_like()
+        S = torch.full((scene.n, 6), 7.25, device="cuda")          # stale contents everywhere
+        S_po = torch.full((scene.n, 3), -3.5, device="cuda")
+        B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, dL, grads, S, ws,
+                                    accumulate=accumulate, S_po=S_po, reset_S=True)
+        torch.cuda.synchronize()
+        assert _rel(S.cpu().numpy(), _upper6(acc["S"])) < 1e-4
+        assert _rel(S_po.cpu().numpy(), acc["S_po"]) < 1e-4
+        unreached = vb.proj.tiles_touched.cpu().numpy() == 0
+        assert unreached.sum() > 0 and np.all(S.cpu().numpy()[unreached] == 0.0)
+        assert np.all(S_po.cpu().numpy()[unreached] == 0.0)
+        for f, t in zip(FIELDS, grads.tensors()):
+            assert _rel(t.cpu().numpy(), acc[f]) < 1e-4, f
+        B.render_bwd_with_splitting(g, vb.proj, vb.bins, cam, st, vb.final_T, vb.n_contrib, dL, grads, S, ws,
+                                    accumulate=True, S_po=S_po)
+        torch.cuda.synchronize()
+        assert _rel(S.cpu().numpy(), 2.0 * _upper6(acc["S"])) < 1e-4
+        assert _rel(S_po.cpu().numpy(), 2.0 * acc["S_po"]) < 1e-4
+
+
+def test_multi_view_reset_of_splitting_matrices():
+    from paper_2505_05587_gb300 import batched as BT
+    scene = synth.cluster_scene(3, 3000, 3)
+    res = [(150, 101), (96, 64)]
+    cams = synth.ring_cameras(6.0, res)
+    st = synth.Settings()
+    tg = [torch.as_tensor(synth.target_image(10 + k, h, w)).cuda() for k, (w, h) in enumerate(res)]
+    g = B.GaussianTensors.from_scene(scene)
+    step = BT.BatchedDensifyStep(g, cams, BT.concat_images(tg), st, batch=128)
+    step.fit_capacity()
+    S_add = torch.zeros(scene.n, 6, device="cuda")
+    S_set = torch.full((scene.n, 6), 11.0, device="cuda")
+    for S, reset in ((S_add, False), (S_set, True)):
+        step.loss.zero_()
+        B.render_views_with_splitting(g, cams, st, 128, step.targets, step.images, step.loss, step.grads, False, S,
+                                      step.count, step.capacity, step.ws, reset_S=reset)
+    torch.cuda.synchronize()
+    unreached = (S_add == 0).all(dim=1)
+    assert bool(unreached.any()) and bool((S_set[unreached] == 0).all())
+    assert _rel(S_set.cpu().numpy(), S_add.cpu().numpy()) < 1e-5     # atomics may add in another order
+
+
 def test_l1_loss_grad_parity():
     rng = np.random.default_rng(0)
     img = rng.uniform(size=(37, 53, 3)).astype(np.float32)
@@ -215,8 +272,10 @@ def test_densify_split_parity(name, mk_scene, mk_cam, st):
         assert np.all(1 - cosang[gap] <= 1e-4)
         decided = np.abs(lam_o - eps_split) > max(1e-6, 0.0)
         n_out = int(db.n_out.item())
+        lam_x, _ = oracle.eig3_min(acc["S"], 0.5)
+        structural = SP.structural_zeros(lam_x, nrm, eps_split)
         SP.check_split(scene, SP.gpu_out(db, n_out), db.parent.cpu().numpy(), n_out, lam_o, v_o, sp["flags"],
-                       decided, gap, eps_split, 0.5, v_gpu=v_g)
+                       decided, gap, eps_split, 0.5, v_gpu=v_g, structural=structural)
 
 
 def test_densify_gradient_gate_parity():
@@ -232,8 +291,10 @@ def test_densify_gradient_gate_parity():
     nrm = np.linalg.norm(S_or.reshape(-1, 9), axis=1)
     ev = np.linalg.eigvalsh(S_or)
     gap = (ev[:, 1] - ev[:, 0]) > 1e-3 * nrm
+    lam_x, _ = oracle.eig3_min(acc["S"])
     flags_g = SP.check_split(scene, SP.gpu_out(db, n_out), db.parent.cpu().numpy(), n_out, lam_o, v_o,
-                             sp["flags"], decided, gap, -1e-6, 1.0, v_gpu=db.v.cpu().numpy())
+                             sp["flags"], decided, gap, -1e-6, 1.0, v_gpu=db.v.cpu().numpy(),
+                             structural=SP.structural_zeros(lam_x, nrm, -1e-6))
     assert flags_g.sum() < (lam_o < -1e-6).sum()        # the gate removed some splits
 
 

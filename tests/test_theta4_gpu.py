@@ -92,8 +92,11 @@ def test_densify_theta4_parity(name, mk_scene, mk_cam, st):
     n_out = int(db.n_out.item())
     sp = oracle.split_po(scene, lam_o, v_o, -1e-7, step)
     out = SP.gpu_out(db, n_out)
+    Sx = oracle.S4_matrix(acc["S"], acc["S_po"])                 # the oracle's own float64 matrices
+    lam_x, _ = oracle.eig_min_sym(Sx, inv_T)
+    structural = SP.structural_zeros(lam_x, np.linalg.norm(Sx.reshape(n, -1), axis=1) * inv_T, -1e-7)
     flags_g = SP.check_split(scene, out, db.parent.cpu().numpy(), n_out, lam_o, v_o, sp["flags"], decided, gap,
-                             -1e-7, step, dim=4, v_gpu=v_g)
+                             -1e-7, step, dim=4, v_gpu=v_g, structural=structural)
     assert flags_g.sum() > 0
 
 

@@ -2,8 +2,10 @@
 library a workspace (code where cudaMalloc is not allowed or would stall the
 device, or hosts that own every device allocation).  Its scratch is a fixed
 array inside the library; this test checks, through the C ABI, that two calls
-in a row give the same results as the workspace entry point, and that sizes
-beyond the array's limit are refused before anything runs."""
+in a row give the same results as the workspace entry point, that the
+largest allowed size with every scratch region in use (7-D eigenpairs held in
+the scratch, the increment budget) does too, and that sizes beyond the
+array's limit are refused before anything runs."""
 import numpy as np
 import pytest
 
@@ -65,6 +67,58 @@ def test_noalloc_matches_workspace_entry_point_two_calls():
     got2 = _run(True, g2, S2, gn2, -1e-6, 0.5, 0.25)
     _compare(ref2, got2, S2, 0.25)
     assert int(got1.n_out.item()) > g1.n and int(got2.n_out.item()) > g2.n
+
+
+def _split_both(g, S, eps_split, step, budget, S_po=None, S_ls=None, eig_out=True):
+    """The workspace entry point and the allocation-free one on the same inputs."""
+    dim = 3 if S_po is None else (4 if S_ls is None else 7)
+    res = []
+    for noalloc in (False, True):
+        db = PL.DensifyBuffers.alloc(g, dim_theta=dim)
+        lam, v = (db.lam, db.v) if eig_out else (None, None)
+        if noalloc:
+            B.densify_split_noalloc(g, S, 1.0, eps_split, step, None, 0.0, db.out, db.capacity, db.n_out, db.parent,
+                                    lam, v, max_splits=budget, S_po=S_po, S_ls=S_ls)
+        else:
+            B.densify_split(g, S, 1.0, eps_split, step, None, 0.0, db.out, db.capacity, db.n_out, db.parent, lam,
+                            v, db.split_ws, max_splits=budget, S_po=S_po, S_ls=S_ls)
+        torch.cuda.synchronize()
+        res.append(db)
+    return res
+
+
+def _same_split(a, b):
+    n_out = int(a.n_out.item())
+    assert int(b.n_out.item()) == n_out
+    assert torch.equal(a.parent[:n_out], b.parent[:n_out])
+    for f in ("means", "log_scales", "opacity_logit"):
+        assert float((getattr(a.out, f)[:n_out] - getattr(b.out, f)[:n_out]).abs().max()) <= 1e-6, f
+    for f in ("quats", "sh"):
+        assert torch.equal(getattr(a.out, f)[:n_out], getattr(b.out, f)[:n_out])
+    return n_out
+
+
+def test_noalloc_largest_size_theta7_budget_scratch_eigenpairs():
+    """The worst case of the fixed scratch: n at its limit (1,000,000), the
+    7-component eigenvectors and the eigenvalues kept in the scratch (no
+    caller outputs for them), and the increment budget's tie flags and select
+    state in use."""
+    n = 1_000_000
+    g, S, _ = _inputs(2, n, 0)
+    rng = np.random.default_rng(5)
+    S_po = torch.as_tensor(rng.normal(0.0, 1e-2, (n, 3)).astype(np.float32)).cuda()
+    S_ls = torch.as_tensor(rng.normal(0.0, 1e-2, (n, 18)).astype(np.float32)).cuda()
+    a, b = _split_both(g, S, 0.0, 0.5, 4096, S_po=S_po, S_ls=S_ls, eig_out=False)
+    assert _same_split(a, b) == n + 4096
+
+
+def test_noalloc_theta4_with_budget_and_eigen_outputs():
+    g, S, _ = _inputs(3, 30000, 2)
+    rng = np.random.default_rng(6)
+    S_po = torch.as_tensor(rng.normal(0.0, 1e-2, (g.n, 3)).astype(np.float32)).cuda()
+    a, b = _split_both(g, S, -1e-6, 0.3, 1000, S_po=S_po)
+    assert _same_split(a, b) == g.n + 1000
+    assert torch.equal(a.lam, b.lam) and torch.equal(a.v, b.v)
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch():
