@@ -120,6 +120,14 @@ struct L1Out {
     float norm;
 };
 
+// Per-warp transposed reduction buffer of the backward pass: 18 rows of the
+// warp's 32 per-pixel values (9 per entry, two entries per flush; or the 18
+// values of one entry with the higher moments), each row padded to 36 floats
+// so that the writes (one row per value, a lane per column) and the 16-byte
+// reads of the summing lanes (a row per lane) are free of bank conflicts.
+constexpr int kRedRows = 18;
+constexpr int kRedStride = 36;
+
 template <int BATCH, int NW>
 struct BwdSmem {
     uint32_t gid[BATCH];
@@ -129,6 +137,7 @@ struct BwdSmem {
     float4 box[BATCH];
     uint8_t list[NW][BATCH];
     uint32_t maxl;
+    alignas(16) float red[NW][kRedRows * kRedStride];
 };
 
 // Forward compositing of one tile (local tile id `tile` in a gx-wide grid of a
@@ -222,37 +231,30 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
     __syncthreads();        // shared memory is reused by the next tile
 }
 
-// Reduce-scatter of 8 per-lane values across the warp in 9 shuffles (halving
-// exchanges at strides 16, 8, 4, then pair sums at 2 and 1).  Lane l returns
-// the warp total of slot (l >> 2) & 7.
-__device__ __forceinline__ float warp_reduce_scatter8(float (&v)[8]) {
-    const int lane = threadIdx.x & 31;
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float send = b4 ? v[k] : v[k + 4];
-        const float keep = b4 ? v[k + 4] : v[k];
-        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float send = b3 ? v[k] : v[k + 2];
-        const float keep = b3 ? v[k + 2] : v[k];
-        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    {
-        const float send = b2 ? v[0] : v[1];
-        const float keep = b2 ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+// Sum of the 32 floats of one 16-byte aligned row: eight 16-byte loads and a
+// tree of packed two-lane float32 additions (add.rn.f32x2).
+__device__ __forceinline__ unsigned long long add_f32x2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+__device__ __forceinline__ float row_sum32(const float* row) {
+    const ulonglong2* r = reinterpret_cast<const ulonglong2*>(row);
+    unsigned long long s[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int k = 0; k < 4; ++k) {
+        const ulonglong2 a = r[2 * k], b = r[2 * k + 1];
+        s[2 * k] = add_f32x2(a.x, b.x);
+        s[2 * k + 1] = add_f32x2(a.y, b.y);
+    }
+#pragma unroll
+    for (int w = 4; w > 0; w >>= 1)
+#pragma unroll
+        for (int k = 0; k < w; ++k) s[k] = add_f32x2(s[k], s[k + w]);
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(s[0]));
+    return lo + hi;
 }
 
 // Backward pass of one tile, back to front, with the splitting accumulators.
@@ -277,8 +279,6 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
     const int ox = (tile % gx) * TW, oy = (tile / gx) * TH;
     const float lx = (float)(px - ox), ly = (float)(py - oy);
     const int pix = py * W + px;
-    // atomics: lanes 0,4,...,28 carry slots 0..7 of the reduce-scatter, lane 1 slot 8
-    const int slot = ((lane & 3) == 0) ? (lane >> 2) : (lane == 1 ? 8 : -1);
 
     float T = inside ? final_T[pix] : 1.0f;
     const uint32_t last = inside ? n_contrib[pix] : 0u;
@@ -286,6 +286,26 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
     const float g1 = inside ? dL_dimage[3 * pix + 1] : 0.0f;
     const float g2 = inside ? dL_dimage[3 * pix + 2] : 0.0f;
     float acc0 = st.bg[0], acc1 = st.bg[1], acc2 = st.bg[2];
+
+    // transposed reduction: a reduced entry's per-pixel values go to rows of
+    // this warp's buffer; every EPF entries (two, or one with the higher
+    // moments) the first 18 lanes each sum one row and add it to the entry's
+    // accumulator with one atomic
+    constexpr int EPF = HI ? 1 : 2;
+    float* red = sm.red[warp];
+    int pend = 0;                       // entries waiting in the buffer (warp-uniform)
+    uint32_t gid_a = 0u;                // the first waiting entry's Gaussian
+    auto flush = [&](uint32_t gid_b, int rows) {
+        __syncwarp();
+        if (lane < rows) {
+            const float t = row_sum32(red + lane * kRedStride);
+            if constexpr (HI)
+                atomicAdd((lane < 9 ? g2d : g2d_hi) + (size_t)gid_b * kG2dStride + (lane < 9 ? lane : lane - 9), t);
+            else
+                atomicAdd(g2d + (size_t)(lane < 9 ? gid_a : gid_b) * kG2dStride + (lane < 9 ? lane : lane - 9), t);
+        }
+        __syncwarp();
+    };
 
     if (threadIdx.x == 0) sm.maxl = 0u;
     __syncthreads();
@@ -337,22 +357,39 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
             const float aT = ae * T;
             const float w = (clamped ? 0.0f : ae) * dLda;   // dL/dsigma * sigma
             const float wdx = w * dx, wdy = w * dy;
-            float v[8] = {wdx, wdy, wdx * dx, wdx * dy, wdy * dy, w, g0 * aT, g1 * aT};
-            const float v8 = g2 * aT;
-            const float tot8 = warp_reduce_scatter8(v);
-            const float tot1 = warp_sum(v8);
-            if (slot >= 0) atomicAdd(g2d + (size_t)sm.gid[e] * kG2dStride + slot, slot == 8 ? tot1 : tot8);
+            float* rb = red + pend * 9 * kRedStride + lane;
+            rb[0 * kRedStride] = wdx;
+            rb[1 * kRedStride] = wdy;
+            rb[2 * kRedStride] = wdx * dx;
+            rb[3 * kRedStride] = wdx * dy;
+            rb[4 * kRedStride] = wdy * dy;
+            rb[5 * kRedStride] = w;
+            rb[6 * kRedStride] = g0 * aT;
+            rb[7 * kRedStride] = g1 * aT;
+            rb[8 * kRedStride] = g2 * aT;
             if constexpr (HI) {
                 const float wxx = wdx * dx, wyy = wdy * dy;
-                float u[8] = {wxx * dx, wxx * dy, wyy * dx, wyy * dy, wxx * dx * dx, wxx * dx * dy, wxx * dy * dy,
-                              wyy * dx * dy};
-                const float u8 = wyy * dy * dy;
-                const float hi8 = warp_reduce_scatter8(u);
-                const float hi1 = warp_sum(u8);
-                if (slot >= 0) atomicAdd(g2d_hi + (size_t)sm.gid[e] * kG2dStride + slot, slot == 8 ? hi1 : hi8);
+                rb[9 * kRedStride] = wxx * dx;
+                rb[10 * kRedStride] = wxx * dy;
+                rb[11 * kRedStride] = wyy * dx;
+                rb[12 * kRedStride] = wyy * dy;
+                rb[13 * kRedStride] = wxx * dx * dx;
+                rb[14 * kRedStride] = wxx * dx * dy;
+                rb[15 * kRedStride] = wxx * dy * dy;
+                rb[16 * kRedStride] = wyy * dx * dy;
+                rb[17 * kRedStride] = wyy * dy * dy;
+            }
+            const uint32_t gid = sm.gid[e];
+            if (pend + 1 == EPF) {
+                flush(gid, kRedRows);
+                pend = 0;
+            } else {
+                gid_a = gid;
+                ++pend;
             }
         }
     }
+    if (pend > 0) flush(gid_a, 9);      // an odd entry left waiting (two-entry flushes only)
     __syncthreads();        // shared memory is reused by the next tile
 }
 
