@@ -195,7 +195,7 @@ def run_gpu(args):
     target_np = synth.target_image(TARGET_SEED, HEIGHT, WIDTH)
     g = B.GaussianTensors.from_scene(scene, dev)
     target = torch.as_tensor(target_np).to(dev)
-    vb = PL.ViewBuffers.alloc(g.n, cam, st, capacity=4 * g.n, device=dev)
+    vb = PL.ViewBuffers.alloc(g.n, cam, st, capacity=4 * g.n, device=dev, walk=not args.no_walk)
     db = PL.DensifyBuffers.alloc(g, dim_theta=args.dim_theta)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -387,6 +387,7 @@ def run_gpu(args):
                    "dim_theta": args.dim_theta,
                    "loss": "L1" if args.lambda_dssim is None else f"(1-{args.lambda_dssim:g}) L1 + "
                                                                  f"{args.lambda_dssim:g} (1-SSIM)",
+                   "backward_walk": "culled list entries" if args.no_walk else "forward's walk lists",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between iterations, outside the timed events"},
         "timing": "each step = one replay of the fused iteration captured as a CUDA graph; per_call_ms from "
@@ -496,6 +497,9 @@ def main():
                          "(4) or (position, log-scales, opacity) (7)")
     ap.add_argument("--lambda-dssim", type=float, default=None,
                     help="add the SSIM term to the loss: (1 - l) L1 + l (1 - SSIM) (default: L1 only)")
+    ap.add_argument("--no-walk", action="store_true",
+                    help="no walk lists: the backward culls every list entry itself instead of following the "
+                         "forward's per-warp lists of composited entries")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()

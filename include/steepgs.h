@@ -147,7 +147,23 @@ typedef struct sgs_proj {
  *                        sgs_render_fwd and sgs_render_bwd_with_splitting
  *                        launch their per-tile blocks in this order when it
  *                        is given (the heavy tiles start first and the short
- *                        ones fill the tail); results do not depend on it. */
+ *                        ones fill the tail); results do not depend on it.
+ *   walk     [W*capacity]  optional (NULL with walk_count): the forward
+ *                        pass's walk lists, W = tile pixels / 32 warps per
+ *                        tile.  sgs_render_fwd / sgs_render_fwd_l1 write, for
+ *                        warp w of tile t (8x4 pixel blocks in row-major
+ *                        order within the tile), the positions in t's list
+ *                        of the entries it composited in at least one pixel,
+ *                        front to back, from element W*start_t +
+ *                        w*(end_t - start_t); walk_count [T*W] holds their
+ *                        numbers.  Given them,
+ *                        sgs_render_bwd_with_splitting walks only those
+ *                        entries (recomputing the transmittance back to
+ *                        front as always) instead of every entry whose alpha
+ *                        support meets the block; its results are the same.
+ *                        They must come from the forward pass over the same
+ *                        proj, bins and settings.  Not written by
+ *                        sgs_bin_sort, ignored by the multi-view calls. */
 typedef struct sgs_bins {
     uint32_t *gids;
     uint64_t *keys;
@@ -155,6 +171,8 @@ typedef struct sgs_bins {
     int32_t *count;
     int64_t capacity;
     uint32_t *order;
+    uint32_t *walk;
+    uint32_t *walk_count;
 } sgs_bins;
 
 /* Parameter gradients written by sgs_render_bwd_with_splitting. */
@@ -444,9 +462,12 @@ int sgs_densify_split_noalloc(const sgs_gaussians *in, const float *S_accum, con
 
 /* Pair counts of the forward walk: counts [H,W,2] uint32 = (pairs evaluated,
  * pairs composited) per pixel, the work units behind the rasteriser's
- * algorithmic FLOP count.  Errors: as sgs_render_fwd. */
+ * algorithmic FLOP count; warp_union [T * tile pixels / 32] (may be NULL): per
+ * 8x4 pixel block of each tile, the number of list entries at least one of
+ * its pixels composites (what the forward's walk lists hold).  A walk over
+ * every list entry without culling.  Errors: as sgs_render_fwd. */
 int sgs_render_stats(const sgs_proj *proj, const sgs_bins *bins, const sgs_camera *cam,
-                     const sgs_settings *st, uint32_t *counts, void *stream);
+                     const sgs_settings *st, uint32_t *counts, uint32_t *warp_union, void *stream);
 
 /* FP32 FMA throughput probe: `blocks` blocks of 256 threads, each thread runs
  * `iters` rounds of 8 independent fused multiply-adds (16 FLOP per round) and

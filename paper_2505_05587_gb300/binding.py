@@ -66,7 +66,8 @@ class Proj(C.Structure):
 
 class Bins(C.Structure):
     _fields_ = [("gids", C.c_void_p), ("keys", C.c_void_p), ("ranges", C.c_void_p),
-                ("count", C.c_void_p), ("capacity", C.c_int64), ("order", C.c_void_p)]
+                ("count", C.c_void_p), ("capacity", C.c_int64), ("order", C.c_void_p),
+                ("walk", C.c_void_p), ("walk_count", C.c_void_p)]
 
 
 class Grads(C.Structure):
@@ -96,7 +97,7 @@ def lib():
         L.sgs_render_fwd.argtypes = [P, P, P, P, P, P, P, P]
         L.sgs_render_fwd_l1.argtypes = [P, P, P, P, P, I32, P, P, P, P, P, P]
         L.sgs_l1_loss_grad.argtypes = [P, P, I32, I32, I32, P, P, P]
-        L.sgs_render_stats.argtypes = [P, P, P, P, P, P]
+        L.sgs_render_stats.argtypes = [P, P, P, P, P, P, P]
         L.sgs_render_bwd_workspace_size.argtypes = [I32, C.POINTER(SZ)]
         L.sgs_render_bwd_with_splitting.argtypes = [P, P, P, P, P, P, P, P, P, I32, P, P, P, P, SZ, P]
         L.sgs_densify_split_workspace_size.argtypes = [I32, C.POINTER(SZ)]
@@ -287,23 +288,40 @@ class BinBuffers:
     count: torch.Tensor    # [1] i32
     capacity: int
     order: torch.Tensor | None = None   # [T] i32 (uint32 in C): tile schedule, longest lists first
+    walk: torch.Tensor | None = None        # [W*cap] i32: the forward's walk lists (W warps per tile)
+    walk_count: torch.Tensor | None = None  # [T*W] i32
+    walk_warps: int = 0
 
     @staticmethod
-    def alloc(capacity: int, num_tiles: int, with_keys=False, device="cuda", with_order=True) -> "BinBuffers":
+    def alloc(capacity: int, num_tiles: int, with_keys=False, device="cuda", with_order=True,
+              walk_warps: int = 0) -> "BinBuffers":
+        """walk_warps > 0 (tile pixels / 32): room for the forward pass's walk
+        lists, which the backward pass then follows."""
         i32 = dict(device=device, dtype=torch.int32)
-        return BinBuffers(torch.empty(max(capacity, 1), **i32),
-                          torch.empty(max(capacity, 1), device=device, dtype=torch.int64) if with_keys else None,
+        cap = max(capacity, 1)
+        return BinBuffers(torch.empty(cap, **i32),
+                          torch.empty(cap, device=device, dtype=torch.int64) if with_keys else None,
                           torch.empty(num_tiles, 2, **i32), torch.zeros(1, **i32), capacity,
-                          torch.empty(max(num_tiles, 1), **i32) if with_order else None)
+                          torch.empty(max(num_tiles, 1), **i32) if with_order else None,
+                          torch.empty(walk_warps * cap, **i32) if walk_warps else None,
+                          torch.zeros(max(num_tiles * walk_warps, 1), **i32) if walk_warps else None, walk_warps)
 
     def c(self, num_tiles: int | None = None) -> Bins:
         """Checked for `capacity` instances and `num_tiles` tiles (default:
         the rows of `ranges`)."""
         T = int(self.ranges.shape[0]) if num_tiles is None else int(num_tiles)
         cap = int(self.capacity)
+        Wn = int(self.walk_warps)
         return Bins(_arr(self.gids, "bins.gids", I32, cap), _arr(self.keys, "bins.keys", I64, cap),
                     _arr(self.ranges, "bins.ranges", I32, 2 * T), _arr(self.count, "bins.count", I32, 1), cap,
-                    _arr(self.order, "bins.order", I32, T))
+                    _arr(self.order, "bins.order", I32, T), _arr(self.walk, "bins.walk", I32, Wn * cap),
+                    _arr(self.walk_count, "bins.walk_count", I32, T * Wn))
+
+    def for_settings(self, st) -> "BinBuffers":
+        """Checks that the walk lists were sized for the tile shape of `st`."""
+        if self.walk is not None and self.walk_warps != st.tile_w * st.tile_h // 32:
+            raise ValueError("bins: walk lists sized for another tile shape")
+        return self
 
 
 def camera_c(cam) -> Camera:
@@ -344,7 +362,7 @@ def bin_sort(proj: ProjBuffers, n: int, cam, st, out: BinBuffers, ws: torch.Tens
 
 
 def render_fwd(proj: ProjBuffers, bins: BinBuffers, cam, st, image, final_T, n_contrib, stream=None):
-    pc, bc, cc, sc = proj.c(), bins.c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
+    pc, bc, cc, sc = proj.c(), bins.for_settings(st).c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
     P = _pixels(cam)
     _check("sgs_render_fwd", lib().sgs_render_fwd(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
                                                    _arr(image, "image", F32, 3 * P),
@@ -355,7 +373,7 @@ def render_fwd(proj: ProjBuffers, bins: BinBuffers, cam, st, image, final_T, n_c
 def render_fwd_l1(proj: ProjBuffers, bins: BinBuffers, cam, st, target, n_views: int, image, final_T, n_contrib,
                   dL_dimage, loss, stream=None):
     """render_fwd with the L1 loss and its gradient in the same kernel."""
-    pc, bc, cc, sc = proj.c(), bins.c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
+    pc, bc, cc, sc = proj.c(), bins.for_settings(st).c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
     P = _pixels(cam)
     _check("sgs_render_fwd_l1", lib().sgs_render_fwd_l1(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
                                                          _arr(target, "target", F32, 3 * P), int(n_views),
@@ -366,12 +384,15 @@ def render_fwd_l1(proj: ProjBuffers, bins: BinBuffers, cam, st, target, n_views:
                                                          _arr(loss, "loss", F32, 1), _stream(stream)))
 
 
-def render_stats(proj: ProjBuffers, bins: BinBuffers, cam, st, counts, stream=None):
-    """counts: int32 [H,W,2] <- (pairs evaluated, pairs composited) per pixel."""
-    pc, bc, cc, sc = proj.c(), bins.c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
+def render_stats(proj: ProjBuffers, bins: BinBuffers, cam, st, counts, stream=None, warp_union=None):
+    """counts: int32 [H,W,2] <- (pairs evaluated, pairs composited) per pixel;
+    warp_union (optional) int32 [T * tile pixels / 32] <- per 8x4 block, the
+    list entries at least one of its pixels composites."""
+    pc, bc, cc, sc = proj.c(), bins.for_settings(st).c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
+    nw = num_tiles(cam, st) * (st.tile_w * st.tile_h // 32)
     _check("sgs_render_stats", lib().sgs_render_stats(C.byref(pc), C.byref(bc), C.byref(cc), C.byref(sc),
                                                        _arr(counts, "counts", I32, 2 * _pixels(cam)),
-                                                       _stream(stream)))
+                                                       _arr(warp_union, "warp_union", I32, nw), _stream(stream)))
 
 
 def ssim_l1_workspace_size(height: int, width: int) -> int:
@@ -438,7 +459,8 @@ def render_bwd_with_splitting(g: GaussianTensors, proj: ProjBuffers, bins: BinBu
     matrix over theta = (p, o) is accumulated too; S_ls [N,18] (optional, with
     S_po): the log-scale blocks over theta = (p, l, o) as well.  reset_S: the
     call starts a new accumulation period (S, S_po, S_ls overwritten)."""
-    gc, pc, bc, cc, sc = g.c(), proj.c(g.n), bins.c(num_tiles(cam, st)), camera_c(cam), settings_c(st)
+    gc, pc, bc, cc, sc = g.c(), proj.c(g.n), bins.for_settings(st).c(num_tiles(cam, st)), camera_c(cam), \
+        settings_c(st)
     grc = grads.grads_c(g)
     n, P = g.n, _pixels(cam)
     _check("sgs_render_bwd_with_splitting",

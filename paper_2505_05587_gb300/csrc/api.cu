@@ -176,10 +176,17 @@ int sgs_bin_sort(const sgs_proj* proj, int32_t n, const sgs_camera* cam, const s
     return cuda_status(launch_bin_sort(*proj, vd, make_set(*st), *out, ws, (cudaStream_t)stream));
 }
 
+// Walk lists come as a pair (both given or both NULL), with a capacity whose
+// rows (warps per tile x capacity) fit a 64-bit index.
+static bool walk_ok(const sgs_bins* b) {
+    if ((b->walk == nullptr) != (b->walk_count == nullptr)) return false;
+    return b->walk == nullptr || (b->capacity >= 0 && b->capacity <= ((int64_t)1 << 31) - 1);
+}
+
 int sgs_render_fwd(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,
                    float* image, float* final_T, uint32_t* n_contrib, void* stream) {
     if (!proj || !bins || !valid_cam(cam) || !valid_settings(st) || !image || !final_T || !n_contrib ||
-        !tiles_fit(cam, st) || !bins->ranges)
+        !tiles_fit(cam, st) || !bins->ranges || !walk_ok(bins))
         return SGS_ERR_INVALID_ARG;
     return cuda_status(launch_render_fwd(*proj, *bins, make_cam(*cam, *st), make_set(*st), image, final_T,
                                          n_contrib, nullptr, 1, nullptr, nullptr, (cudaStream_t)stream));
@@ -189,18 +196,18 @@ int sgs_render_fwd_l1(const sgs_proj* proj, const sgs_bins* bins, const sgs_came
                       const float* target, int32_t n_views, float* image, float* final_T, uint32_t* n_contrib,
                       float* dL_dimage, float* loss, void* stream) {
     if (!proj || !bins || !valid_cam(cam) || !valid_settings(st) || !image || !final_T || !n_contrib ||
-        !tiles_fit(cam, st) || !bins->ranges || !target || n_views <= 0 || !dL_dimage || !loss)
+        !tiles_fit(cam, st) || !bins->ranges || !walk_ok(bins) || !target || n_views <= 0 || !dL_dimage || !loss)
         return SGS_ERR_INVALID_ARG;
     return cuda_status(launch_render_fwd(*proj, *bins, make_cam(*cam, *st), make_set(*st), image, final_T,
                                          n_contrib, target, n_views, dL_dimage, loss, (cudaStream_t)stream));
 }
 
 int sgs_render_stats(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,
-                     uint32_t* counts, void* stream) {
+                     uint32_t* counts, uint32_t* warp_union, void* stream) {
     if (!proj || !bins || !valid_cam(cam) || !valid_settings(st) || !counts || !tiles_fit(cam, st) ||
         !bins->ranges)
         return SGS_ERR_INVALID_ARG;
-    return cuda_status(launch_render_stats(*proj, *bins, make_cam(*cam, *st), make_set(*st), counts,
+    return cuda_status(launch_render_stats(*proj, *bins, make_cam(*cam, *st), make_set(*st), counts, warp_union,
                                            (cudaStream_t)stream));
 }
 
@@ -249,7 +256,7 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
                                   void* ws, size_t ws_bytes, void* stream) {
     if (flags & ~(SGS_BWD_ACCUMULATE_GRADS | SGS_BWD_RESET_S)) return SGS_ERR_INVALID_ARG;
     if (!valid_gaussians(g) || !proj || !bins || !valid_cam(cam) || !valid_settings(st) || !final_T ||
-        !n_contrib || !dL_dimage || !grads || !tiles_fit(cam, st) || !bins->ranges)
+        !n_contrib || !dL_dimage || !grads || !tiles_fit(cam, st) || !bins->ranges || !walk_ok(bins))
         return SGS_ERR_INVALID_ARG;
     if (S_ls_accum && !S_po_accum) return SGS_ERR_INVALID_ARG;      // theta = (p, l, o) includes o
     if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit ||
@@ -312,7 +319,7 @@ struct ViewsWs {
 
 static ViewsWs carve_views_ws(void* base, const ViewsDev& vd, int64_t capacity, bool with_backward) {
     Carver c{reinterpret_cast<char*>(base), 0};
-    ViewsWs w;
+    ViewsWs w{};                                    // no walk lists: the multi-view kernels cull per batch
     const size_t rows = (size_t)(vd.row_off[vd.nv] > 0 ? vd.row_off[vd.nv] : 1);
     const size_t P = (size_t)(vd.P_total > 0 ? vd.P_total : 1);
     const size_t cap = (size_t)(capacity > 0 ? capacity : 1);

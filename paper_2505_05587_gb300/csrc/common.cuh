@@ -186,7 +186,7 @@ cudaError_t launch_ssim_l1(const float* image, const float* target, int H, int W
                            float* loss, void* ws, cudaStream_t stream);
 cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t stream);
 cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam,
-                                const SetDev& st, uint32_t* counts, cudaStream_t stream);
+                                const SetDev& st, uint32_t* counts, uint32_t* warp_union, cudaStream_t stream);
 
 cudaError_t launch_l1_views(const float* image, const float* target, const ViewsDev& vd, float* dL, float* loss,
                             cudaStream_t stream);

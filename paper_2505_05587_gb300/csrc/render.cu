@@ -108,6 +108,7 @@ struct FwdSmem {
     float4 rgb[BATCH];
     float4 box[BATCH];
     uint8_t list[NW][BATCH];
+    uint8_t hit[NW][BATCH];  // walk recording: list slot composited by some pixel of the warp
     float l1_part[NW];
 };
 
@@ -142,12 +143,24 @@ struct BwdSmem {
 
 // Forward compositing of one tile (local tile id `tile` in a gx-wide grid of a
 // W x H view); outputs are the view's own image / final_T / n_contrib arrays.
-template <int TW, int TH, int BATCH>
+// Walk lists written by the forward pass (REC): for warp w of a tile with list
+// [start, end), entries NW*start + w*(end - start) on of `walk` hold the list
+// positions it composited in some pixel, front to back; walk_count[tile*NW + w]
+// their number.
+struct WalkOut {
+    uint32_t* walk;
+    uint32_t* count;
+    long long cap;          // entries of walk
+};
+
+template <int TW, int TH, int BATCH, bool REC = false>
 __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 rg, const uint32_t* __restrict__ gids,
                                          const float4* __restrict__ xy, const float4* __restrict__ conic_opac,
                                          const float4* __restrict__ rgb, const SetDev& st, float* __restrict__ image,
                                          float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
-                                         FwdSmem<BATCH, TW * TH / 32>& sm, const L1Out* l1 = nullptr) {
+                                         FwdSmem<BATCH, TW * TH / 32>& sm, const L1Out* l1 = nullptr,
+                                         WalkOut wo = WalkOut{nullptr, nullptr, 0}) {
+    constexpr int NW = TW * TH / 32;
     constexpr int BS = TW * TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int bx, by;
@@ -163,6 +176,15 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
     bool done = !inside;
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     uint32_t last = 0;
+    uint32_t* wp = nullptr;                         // this warp's list
+    uint32_t wroom = 0;                             // rows left in `walk` from wp on
+    uint32_t wcnt = 0;                              // entries recorded by this warp
+    if constexpr (REC) {
+        const long long wbase = (long long)NW * rg.x + (long long)warp * n;
+        wp = wo.walk + wbase;
+        wroom = (uint32_t)max(0LL, min(wo.cap - wbase, (long long)n));
+        for (int k = threadIdx.x; k < NW * BATCH; k += BS) (&sm.hit[0][0])[k] = 0;   // read after a barrier
+    }
     for (int base = 0; base < n; base += BATCH) {
         if (__syncthreads_count(done) == BS) break;
         const int cnt = min(BATCH, n - base);
@@ -198,7 +220,27 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
             C2 += c.z * wgt;
             T = Tn;
             last = (uint32_t)(base + j + 1);
+            if constexpr (REC) sm.hit[warp][k] = 1;  // lanes at one k store the same byte
         }
+        if constexpr (REC) {                        // append the composited slots, in list order
+            __syncwarp();
+            const unsigned lt = (1u << lane) - 1u;
+            for (int c = 0; c < nl; c += 32) {
+                const int k = c + lane;
+                const bool h = k < nl && sm.hit[warp][k] != 0;
+                const unsigned m = __ballot_sync(0xffffffffu, h);
+                if (h) {
+                    sm.hit[warp][k] = 0;
+                    const uint32_t at = wcnt + __popc(m & lt);
+                    if (at < wroom) wp[at] = (uint32_t)(base + sm.list[warp][k]);
+                }
+                wcnt += __popc(m);
+            }
+            __syncwarp();
+        }
+    }
+    if constexpr (REC) {
+        if (lane == 0) wo.count[(long long)tile * NW + warp] = wcnt;
     }
     float l1_sum = 0.0f;
     if (inside) {
@@ -393,6 +435,140 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
     __syncthreads();        // shared memory is reused by the next tile
 }
 
+// Backward pass of one tile over the forward pass's walk lists: each warp
+// steps back to front through the entries it composited in some pixel (never
+// the others), staging 32 of them at a time in its own shared-memory slots, so
+// that the warps of a tile never wait for one another.  Per pixel, the
+// transmittance is recovered by division and the compositing decision
+// recomputed exactly as in bwd_tile.
+template <int NW>
+struct BwdWalkSmem {
+    float4 ent[NW][3][32];  // per warp: (tile-local mean, gid bits, position bits), conic (exp2 form), colour
+    alignas(16) float red[NW][kRedRows * kRedStride];
+};
+
+template <int TW, int TH, bool HI>
+__device__ __forceinline__ void bwd_tile_walk(int tile, int gx, int W, int H, uint2 rg,
+                                              const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
+                                              const float4* __restrict__ conic_opac, const float4* __restrict__ rgb,
+                                              const SetDev& st, const float* __restrict__ final_T,
+                                              const uint32_t* __restrict__ n_contrib,
+                                              const float* __restrict__ dL_dimage, const uint32_t* __restrict__ walk,
+                                              const uint32_t* __restrict__ walk_count, long long walk_cap,
+                                              float* __restrict__ g2d, float* __restrict__ g2d_hi,
+                                              BwdWalkSmem<TW * TH / 32>& sm) {
+    constexpr int NW = TW * TH / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long L = (long long)rg.y - (long long)rg.x;
+    const long long wbase = (long long)NW * rg.x + (long long)warp * L;
+    long long cnt = walk_count[(long long)tile * NW + warp];
+    cnt = min(cnt, L);
+    cnt = min(cnt, walk_cap - wbase);               // in bounds whatever the counts say
+    if (cnt <= 0) return;
+    int bx, by;
+    warp_block_origin<TW>(tile, gx, TH, &bx, &by);
+    const int px = bx + (lane & 7);
+    const int py = by + (lane >> 3);
+    const bool inside = px < W && py < H;
+    const int ox = (tile % gx) * TW, oy = (tile / gx) * TH;
+    const float lx = (float)(px - ox), ly = (float)(py - oy);
+    const int pix = py * W + px;
+    float T = inside ? final_T[pix] : 1.0f;
+    const uint32_t last = inside ? n_contrib[pix] : 0u;
+    const float g0 = inside ? dL_dimage[3 * pix] : 0.0f;
+    const float g1 = inside ? dL_dimage[3 * pix + 1] : 0.0f;
+    const float g2 = inside ? dL_dimage[3 * pix + 2] : 0.0f;
+    float acc0 = st.bg[0], acc1 = st.bg[1], acc2 = st.bg[2];
+
+    constexpr int EPF = HI ? 1 : 2;
+    float* red = sm.red[warp];
+    int pend = 0;
+    uint32_t gid_a = 0u;
+    auto flush = [&](uint32_t gid_b, int rows) {
+        __syncwarp();
+        if (lane < rows) {
+            const float t = row_sum32(red + lane * kRedStride);
+            if constexpr (HI)
+                atomicAdd((lane < 9 ? g2d : g2d_hi) + (size_t)gid_b * kG2dStride + (lane < 9 ? lane : lane - 9), t);
+            else
+                atomicAdd(g2d + (size_t)(lane < 9 ? gid_a : gid_b) * kG2dStride + (lane < 9 ? lane : lane - 9), t);
+        }
+        __syncwarp();
+    };
+
+    float4* e_mu = sm.ent[warp][0];
+    float4* e_co = sm.ent[warp][1];
+    float4* e_c = sm.ent[warp][2];
+    for (int end = (int)cnt; end > 0; end -= 32) {
+        const int start = max(0, end - 32);
+        const int c = end - start;
+        __syncwarp();                               // the previous chunk's slots are free
+        if (lane < c) {
+            uint32_t pos = walk[wbase + start + lane];
+            // a position past the list composites nowhere (pos >= L >= every last)
+            const uint32_t g = gids[rg.x + ((long long)pos < L ? pos : 0u)];
+            if ((long long)pos > L) pos = (uint32_t)L;
+            const float4 m = xy[g];
+            e_mu[lane] = make_float4((m.x - (float)ox) + m.z, (m.y - (float)oy) + m.w, __uint_as_float(g),
+                                     __uint_as_float(pos));
+            e_co[lane] = conic_exp2(conic_opac[g]);
+            e_c[lane] = rgb[g];
+        }
+        __syncwarp();
+        for (int k = c - 1; k >= 0; --k) {
+            const float4 m = e_mu[k];
+            const float4 cp = e_co[k];
+            const float4 col = e_c[k];
+            const float dx = lx - m.x;
+            const float dy = ly - m.y;
+            const float araw = __fmul_rn(cp.w, gauss2(cp, dx, dy));
+            const bool valid = __float_as_uint(m.w) < last && araw >= st.alpha_min;
+            const bool clamped = araw >= st.alpha_max;
+            const float ae = valid ? (clamped ? st.alpha_max : araw) : 0.0f;
+            const float one_m = 1.0f - ae;
+            T = __fdividef(T, one_m);                 // transmittance in front of this Gaussian
+            const float dLda = T * (g0 * (col.x - acc0) + g1 * (col.y - acc1) + g2 * (col.z - acc2));
+            acc0 += ae * (col.x - acc0);
+            acc1 += ae * (col.y - acc1);
+            acc2 += ae * (col.z - acc2);
+            const float aT = ae * T;
+            const float w = (clamped ? 0.0f : ae) * dLda;   // dL/dsigma * sigma
+            const float wdx = w * dx, wdy = w * dy;
+            float* rb = red + pend * 9 * kRedStride + lane;
+            rb[0 * kRedStride] = wdx;
+            rb[1 * kRedStride] = wdy;
+            rb[2 * kRedStride] = wdx * dx;
+            rb[3 * kRedStride] = wdx * dy;
+            rb[4 * kRedStride] = wdy * dy;
+            rb[5 * kRedStride] = w;
+            rb[6 * kRedStride] = g0 * aT;
+            rb[7 * kRedStride] = g1 * aT;
+            rb[8 * kRedStride] = g2 * aT;
+            if constexpr (HI) {
+                const float wxx = wdx * dx, wyy = wdy * dy;
+                rb[9 * kRedStride] = wxx * dx;
+                rb[10 * kRedStride] = wxx * dy;
+                rb[11 * kRedStride] = wyy * dx;
+                rb[12 * kRedStride] = wyy * dy;
+                rb[13 * kRedStride] = wxx * dx * dx;
+                rb[14 * kRedStride] = wxx * dx * dy;
+                rb[15 * kRedStride] = wxx * dy * dy;
+                rb[16 * kRedStride] = wyy * dx * dy;
+                rb[17 * kRedStride] = wyy * dy * dy;
+            }
+            const uint32_t gid = __float_as_uint(m.z);
+            if (pend + 1 == EPF) {
+                flush(gid, kRedRows);
+                pend = 0;
+            } else {
+                gid_a = gid;
+                ++pend;
+            }
+        }
+    }
+    if (pend > 0) flush(gid_a, 9);
+}
+
 // Clears the accumulator rows (and the higher-moment rows when given) of the
 // Gaussians whose projection reached a tile: the only rows the backward adds
 // to and the projection adjoint reads.
@@ -424,18 +600,18 @@ cudaError_t launch_zero_reached_rows(const uint32_t* tiles, int n, float* g2d, f
 // per SM (40 registers): its per-pixel chain is latency-bound and gains from
 // the extra warps more than it loses to the two spilled words.
 // ---------------------------------------------------------------------------
-template <int TW, int TH, bool L1>
+template <int TW, int TH, bool L1, bool REC>
 __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) render_fwd_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
     float* __restrict__ image, float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
-    const uint32_t* __restrict__ order, L1Out l1) {
+    const uint32_t* __restrict__ order, L1Out l1, WalkOut wo) {
     pdl_wait_and_trigger();
     __shared__ FwdSmem<TW * TH, TW * TH / 32> sm;
     const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     if ((unsigned)t >= gridDim.x) return;      // a schedule that is not a permutation of the tiles
-    fwd_tile<TW, TH, TW * TH>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, image, final_T, n_contrib, sm,
-                              L1 ? &l1 : nullptr);
+    fwd_tile<TW, TH, TW * TH, REC>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, image, final_T, n_contrib,
+                                   sm, L1 ? &l1 : nullptr, wo);
 }
 
 // The backward kernels are bounded to 40 resident warps per SM (48 registers):
@@ -453,6 +629,23 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_kernel(
     if ((unsigned)t >= gridDim.x) return;      // a schedule that is not a permutation of the tiles
     bwd_tile<TW, TH, TW * TH, HI>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, final_T, n_contrib,
                                   dL_dimage, g2d, g2d_hi, sm);
+}
+
+// The backward pass over the forward's walk lists (same residency bound).
+template <int TW, int TH, bool HI>
+__global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_walk_kernel(
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
+    const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
+    const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
+    const float* __restrict__ dL_dimage, const uint32_t* __restrict__ walk,
+    const uint32_t* __restrict__ walk_count, long long walk_cap, float* __restrict__ g2d,
+    float* __restrict__ g2d_hi, const uint32_t* __restrict__ order) {
+    pdl_wait_and_trigger();
+    __shared__ BwdWalkSmem<TW * TH / 32> sm;
+    const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    if ((unsigned)t >= gridDim.x) return;      // a schedule that is not a permutation of the tiles
+    bwd_tile_walk<TW, TH, HI>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, final_T, n_contrib, dL_dimage,
+                              walk, walk_count, walk_cap, g2d, g2d_hi, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -512,36 +705,56 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_views_ke
 }
 
 // Pair counts of the forward walk, per pixel: (pairs evaluated, pairs
-// composited).  A measurement aid; it replays the walk without colour.
+// composited), and, when warp_union is given, per 8x4 pixel block of each tile
+// (the warps of the compositing kernels) the number of list entries that at
+// least one of its pixels composites.  A measurement aid: it replays the walk
+// over every list entry, without colour and without culling.
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH) render_stats_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
-    const float4* __restrict__ conic_opac, int W, int H, int gx, SetDev st, uint2* __restrict__ counts) {
+    const float4* __restrict__ conic_opac, int W, int H, int gx, SetDev st, uint2* __restrict__ counts,
+    uint32_t* __restrict__ warp_union) {
     pdl_wait_and_trigger();
+    constexpr int NW = TW * TH / 32;
     const int tile = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int bx, by;
+    warp_block_origin<TW>(tile, gx, TH, &bx, &by);
+    const int px = bx + (lane & 7);
+    const int py = by + (lane >> 3);
+    const bool inside = px < W && py < H;
     const int ox = (tile % gx) * TW, oy = (tile / gx) * TH;
-    const int px = ox + (int)(threadIdx.x % TW);
-    const int py = oy + (int)(threadIdx.x / TW);
-    if (px >= W || py >= H) return;
     const float lx = (float)(px - ox), ly = (float)(py - oy);
     const uint2 rg = ranges[tile];
     float T = 1.0f;
-    uint32_t ev = 0, comp = 0;
+    bool stop = !inside;
+    uint32_t ev = 0, comp = 0, uni = 0;
     for (uint32_t k = rg.x; k < rg.y; ++k) {
-        const uint32_t g = gids[k];
-        const float4 m = xy[g];
-        const float4 cp = conic_exp2(conic_opac[g]);
-        const float dx = lx - ((m.x - (float)ox) + m.z);
-        const float dy = ly - ((m.y - (float)oy) + m.w);
-        const float alpha = fminf(st.alpha_max, __fmul_rn(cp.w, gauss2(cp, dx, dy)));
-        ++ev;
-        if (alpha < st.alpha_min) continue;
-        const float Tn = T * (1.0f - alpha);
-        if (Tn < st.T_min) break;
-        ++comp;
-        T = Tn;
+        if (__all_sync(0xffffffffu, stop)) break;
+        bool c = false;
+        if (!stop) {
+            const uint32_t g = gids[k];
+            const float4 m = xy[g];
+            const float4 cp = conic_exp2(conic_opac[g]);
+            const float dx = lx - ((m.x - (float)ox) + m.z);
+            const float dy = ly - ((m.y - (float)oy) + m.w);
+            const float alpha = fminf(st.alpha_max, __fmul_rn(cp.w, gauss2(cp, dx, dy)));
+            ++ev;
+            if (alpha >= st.alpha_min) {
+                const float Tn = T * (1.0f - alpha);
+                if (Tn < st.T_min) {
+                    stop = true;
+                } else {
+                    ++comp;
+                    T = Tn;
+                    c = true;
+                }
+            }
+        }
+        uni += __ballot_sync(0xffffffffu, c) != 0u;
     }
-    counts[py * W + px] = make_uint2(ev, comp);
+    if (inside) counts[py * W + px] = make_uint2(ev, comp);
+    if (warp_union && lane == 0) warp_union[(long long)tile * NW + warp] = uni;
 }
 
 // FP32 FMA throughput probe (a measurement aid): eight independent FMA chains
@@ -572,12 +785,12 @@ cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t str
 // ---------------------------------------------------------------------------
 template <int TW, int TH>
 static cudaError_t stats_tmpl(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
-                              uint32_t* counts, cudaStream_t stream) {
+                              uint32_t* counts, uint32_t* warp_union, cudaStream_t stream) {
     const int T = cam.gx * cam.gy;
     (void)launch_pdl(render_stats_kernel<TW, TH>, dim3(T), dim3(TW * TH), 0, stream,
                      reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
                      reinterpret_cast<const float4*>(proj.conic_opac), cam.width, cam.height, cam.gx, st,
-                     reinterpret_cast<uint2*>(counts));
+                     reinterpret_cast<uint2*>(counts), warp_union);
     note_launch();
     return cudaGetLastError();
 }
@@ -587,11 +800,15 @@ static cudaError_t fwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const Ca
                             float* image, float* final_T, uint32_t* n_contrib, const L1Out& l1,
                             cudaStream_t stream) {
     const int T = cam.gx * cam.gy;
-    (void)launch_pdl(l1.target ? render_fwd_kernel<TW, TH, true> : render_fwd_kernel<TW, TH, false>, dim3(T),
-                     dim3(TW * TH), 0, stream,
+    const bool rec = bins.walk != nullptr;
+    const WalkOut wo{bins.walk, bins.walk_count,
+                     (long long)(TW * TH / 32) * (long long)bins.capacity};
+    auto kern = l1.target ? (rec ? render_fwd_kernel<TW, TH, true, true> : render_fwd_kernel<TW, TH, true, false>)
+                          : (rec ? render_fwd_kernel<TW, TH, false, true> : render_fwd_kernel<TW, TH, false, false>);
+    (void)launch_pdl(kern, dim3(T), dim3(TW * TH), 0, stream,
                      reinterpret_cast<const uint2*>(bins.ranges), bins.gids, reinterpret_cast<const float4*>(proj.xy),
                      reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
-                     cam.width, cam.height, cam.gx, st, image, final_T, n_contrib, bins.order, l1);
+                     cam.width, cam.height, cam.gx, st, image, final_T, n_contrib, bins.order, l1, wo);
     note_launch();
     return cudaGetLastError();
 }
@@ -601,6 +818,16 @@ static cudaError_t bwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const Ca
                             const float* final_T, const uint32_t* n_contrib, const float* dL, float* g2d,
                             float* g2d_hi, cudaStream_t stream) {
     const int T = cam.gx * cam.gy;
+    if (bins.walk) {                            // the forward's walk lists: composited entries only
+        auto kern = g2d_hi ? render_bwd_walk_kernel<TW, TH, true> : render_bwd_walk_kernel<TW, TH, false>;
+        (void)launch_pdl(kern, dim3(T), dim3(TW * TH), 0, stream, reinterpret_cast<const uint2*>(bins.ranges),
+                         bins.gids, reinterpret_cast<const float4*>(proj.xy),
+                         reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
+                         cam.width, cam.height, cam.gx, st, final_T, n_contrib, dL, bins.walk, bins.walk_count,
+                         (long long)(TW * TH / 32) * (long long)bins.capacity, g2d, g2d_hi, bins.order);
+        note_launch();
+        return cudaGetLastError();
+    }
     auto kern = g2d_hi ? render_bwd_kernel<TW, TH, true> : render_bwd_kernel<TW, TH, false>;
     (void)launch_pdl(kern, dim3(T), dim3(TW * TH), 0, stream, reinterpret_cast<const uint2*>(bins.ranges), bins.gids,
                      reinterpret_cast<const float4*>(proj.xy), reinterpret_cast<const float4*>(proj.conic_opac),
@@ -618,8 +845,8 @@ static cudaError_t bwd_tmpl(const sgs_proj& proj, const sgs_bins& bins, const Ca
     return cudaErrorInvalidValue;
 
 cudaError_t launch_render_stats(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,
-                                uint32_t* counts, cudaStream_t stream) {
-    SGS_TILE_DISPATCH(stats_tmpl, proj, bins, cam, st, counts, stream)
+                                uint32_t* counts, uint32_t* warp_union, cudaStream_t stream) {
+    SGS_TILE_DISPATCH(stats_tmpl, proj, bins, cam, st, counts, warp_union, stream)
 }
 
 cudaError_t launch_render_fwd(const sgs_proj& proj, const sgs_bins& bins, const CamDev& cam, const SetDev& st,

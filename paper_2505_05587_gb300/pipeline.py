@@ -64,12 +64,17 @@ class ViewBuffers:
         B.ssim_l1_loss_grad(self.image, target, n_views, lambda_dssim, self.dL, loss, self.ssim_ws, stream)
 
     @staticmethod
-    def alloc(n: int, cam, st, capacity: int | None = None, with_keys=False, device="cuda") -> "ViewBuffers":
+    def alloc(n: int, cam, st, capacity: int | None = None, with_keys=False, device="cuda",
+              walk: bool = True) -> "ViewBuffers":
+        """walk: room for the forward pass's walk lists (the backward pass then
+        visits only the entries each warp composited)."""
         T = B.num_tiles(cam, st)
         cap = capacity if capacity is not None else max(4 * n, 1024)
         H, W = cam.height, cam.width
         f = dict(device=device, dtype=torch.float32)
-        return ViewBuffers(cam, st, n, B.ProjBuffers.alloc(n, device), B.BinBuffers.alloc(cap, T, with_keys, device),
+        ww = st.tile_w * st.tile_h // 32 if walk else 0
+        return ViewBuffers(cam, st, n, B.ProjBuffers.alloc(n, device),
+                           B.BinBuffers.alloc(cap, T, with_keys, device, walk_warps=ww),
                            torch.empty(H, W, 3, **f), torch.empty(H, W, **f),
                            torch.empty(H, W, device=device, dtype=torch.int32), torch.empty(H, W, 3, **f),
                            B.workspace(B.bin_sort_workspace_size(n, cap, T), device), with_keys)
@@ -77,7 +82,7 @@ class ViewBuffers:
     def grow(self, capacity: int):
         T = B.num_tiles(self.cam, self.st)
         dev = self.image.device
-        self.bins = B.BinBuffers.alloc(capacity, T, self.with_keys, dev)
+        self.bins = B.BinBuffers.alloc(capacity, T, self.with_keys, dev, walk_warps=self.bins.walk_warps)
         self.sort_ws = B.workspace(B.bin_sort_workspace_size(self.n, capacity, T), dev)
 
 

@@ -62,6 +62,11 @@ def test_render_fwd_checks(lib):
     assert lib.sgs_render_fwd(*ok) == NO_DEVICE
     nr = _bins(ranges=False)
     assert lib.sgs_render_fwd(ok[0], C.byref(nr), *ok[2:]) == INVALID          # no tile ranges
+    wb = _bins()
+    wb.walk, wb.walk_count = DUMMY + 40960, DUMMY + 45056                       # walk lists: both given
+    assert lib.sgs_render_fwd(ok[0], C.byref(wb), *ok[2:]) == NO_DEVICE
+    wb.walk_count = None                                                        # one without the other
+    assert lib.sgs_render_fwd(ok[0], C.byref(wb), *ok[2:]) == INVALID
     assert lib.sgs_render_fwd(*ok[:4], None, *ok[5:]) == INVALID                # no image
     cam12, st12 = _view(tile=12)
     assert lib.sgs_render_fwd(ok[0], ok[1], C.byref(cam12), C.byref(st12), *ok[4:]) == INVALID   # tile 12x12
@@ -70,7 +75,9 @@ def test_render_fwd_checks(lib):
     assert lib.sgs_render_fwd(ok[0], ok[1], C.byref(bad_cam), *ok[3:]) == INVALID
     assert lib.sgs_render_fwd_l1(*ok[:4], _ptr(4), 0, _ptr(1), _ptr(2), _ptr(3), _ptr(5), _ptr(6),
                                  None) == INVALID                               # n_views < 1
-    assert lib.sgs_render_stats(*ok[:4], None, None) == INVALID                 # no counts
+    assert lib.sgs_render_stats(*ok[:4], None, None, None) == INVALID           # no counts
+    assert lib.sgs_render_stats(*ok[:4], _ptr(9), None, None) == NO_DEVICE
+    assert lib.sgs_render_stats(*ok[:4], _ptr(9), _ptr(10), None) == NO_DEVICE    # with per-block counts
 
 
 def test_loss_checks(lib):
@@ -96,6 +103,13 @@ def test_backward_checks(lib):
     base = [C.byref(g), C.byref(p), C.byref(b), C.byref(cam), C.byref(st), _ptr(1), _ptr(2), _ptr(3),
             C.byref(grads), 0, _ptr(4), None, None, _ptr(7), need.value, None]
     assert lib.sgs_render_bwd_with_splitting(*base) == NO_DEVICE
+    wb = _bins()
+    wb.walk = DUMMY + 40960                                                     # walk without its counts
+    a = list(base)
+    a[2] = C.byref(wb)
+    assert lib.sgs_render_bwd_with_splitting(*a) == INVALID
+    wb.walk_count = DUMMY + 45056
+    assert lib.sgs_render_bwd_with_splitting(*a) == NO_DEVICE
     for flags in (1, 2, 3):                                                     # accumulate grads, reset S, both
         a = list(base)
         a[9] = flags
