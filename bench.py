@@ -405,12 +405,97 @@ def run_gpu(args):
         "gpu_launches": int(launches_per_step * K),
         "clocks": clocks,
     }
+    if rank == 0 and world == 1 and not args.no_serving:
+        result["serving"] = bench_serving(local, args.serve_requests)
+    if rank == 0 and world == 1 and not args.no_batched:
+        result["batched"] = bench_batched(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_full()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# The metric's second half (render serving) and the batched densification
+# step, each with its own clock record
+# ---------------------------------------------------------------------------
+def bench_serving(local: int, n_requests: int) -> dict:
+    """Render serving: Poisson arrivals at 200 req/s over the 6 resident scenes
+    (100k-3M Gaussians, SH3) at 640x480 / 1237x822 / 1920x1080; continuous
+    batching against one request per launch, in real time (the configured
+    load) and saturated (every request released at once)."""
+    import torch
+
+    from paper_2505_05587_gb300 import serve as SV
+    st = synth.Settings()
+    scenes = SV.resident_scenes()
+    jobs = SV.serving_requests(3, n_requests, 200.0, len(scenes))
+    warm = SV.serving_requests(99, 200, 200.0, len(scenes))
+    server = SV.RenderServer(scenes, st)
+    server.run(warm, realtime=False)                # warm-up: buffers, instance estimates
+    SV.serve_one_per_launch(scenes, st, warm, realtime=False)
+    torch.cuda.synchronize()
+    out = {"workload": f"render serving: {n_requests} requests (Poisson 200 req/s, seed 3), 6 resident scenes "
+                       "(100k, 300k, 1M, 1M, 2M, 3M Gaussians, SH3), 640x480 / 1237x822 / 1920x1080, 16x16 tiles",
+           "latency": "arrival to completion on the host clock; p50/p99 over the requests"}
+    sat = jobs[:max(n_requests // 2, 1)]
+    for name, fn in (("continuous_batching_realtime", lambda: server.run(jobs, realtime=True)),
+                     ("one_per_launch_realtime", lambda: SV.serve_one_per_launch(scenes, st, jobs, realtime=True)),
+                     ("continuous_batching_saturated", lambda: server.run(sat, realtime=False)),
+                     ("one_per_launch_saturated", lambda: SV.serve_one_per_launch(scenes, st, sat,
+                                                                                   realtime=False))):
+        server.stats.clear()
+        sampler = ClockSampler(local)
+        with sampler:
+            r = fn()
+        r["clocks"] = sampler.summary()
+        out[name] = r
+    out["saturated_speedup"] = round(out["continuous_batching_saturated"]["frames_per_s"] /
+                                     out["one_per_launch_saturated"]["frames_per_s"], 3)
+    del server, scenes
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_batched(local: int, steps: int = 20, warmup: int = 3) -> dict:
+    """Batched densification step: 3M Gaussians, 8 ring views of uneven
+    resolution, one persistent pass per step replayed as a CUDA graph, against
+    the same step one view per launch sequence.  Tile 16x16 and staging batch
+    128, the autotuner's choice on this workload (python -m
+    paper_2505_05587_gb300.batched runs the tuner)."""
+    import torch
+
+    from paper_2505_05587_gb300 import batched as BT
+    from paper_2505_05587_gb300 import binding as B
+    scene = synth.cluster_scene(0, 3_000_000, 3)
+    cams = synth.ring_cameras(6.0)
+    st = synth.Settings()
+    g = B.GaussianTensors.from_scene(scene)
+    del scene
+    tgs = [torch.as_tensor(synth.target_image(10 + k, c.height, c.width)).cuda() for k, c in enumerate(cams)]
+    step = BT.BatchedDensifyStep(g, cams, BT.concat_images(tgs), st, batch=128)
+    step.capture()
+    sampler = ClockSampler(local)
+    with sampler:
+        ms_graph = BT.time_fn(step.replay, reps=steps, warmup=warmup)
+    clk_b = sampler.summary()
+    M, n_out = int(step.count.item()), int(step.db.n_out.item())
+    del step
+    torch.cuda.empty_cache()
+    plain = BT.PlainDensifyStep(g, cams, tgs, st)
+    sampler = ClockSampler(local)
+    with sampler:
+        ms_plain = BT.time_fn(plain.run, reps=steps, warmup=warmup)
+    clk_p = sampler.summary()
+    del plain, g
+    torch.cuda.empty_cache()
+    return {"workload": "batched densification step: 3M Gaussians (cluster mixture, SH3), 8 ring views 1957x1091, "
+                        "1600x1060, 1237x822, 980x545 x2, 800x600 x3 (7,356,101 pixels), 16x16 tiles, batch 128",
+            "instances_M": M, "n_out": n_out, "unit": "ms/step", "steps": steps, "warmup": warmup,
+            "batched_graph_ms": round(ms_graph, 4), "one_view_per_launch_ms": round(ms_plain, 4),
+            "speedup": round(ms_plain / ms_graph, 3), "clocks": {"batched": clk_b, "one_view_per_launch": clk_p}}
 
 
 # ---------------------------------------------------------------------------
@@ -492,6 +577,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the render-serving measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched densification step")
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="requests in the real-time serving stream (the saturated run takes half of them)")
     ap.add_argument("--dim-theta", type=int, default=3, choices=[3, 4, 7],
                     help="splitting matrices over the position (3, the paper's experiments), (position, opacity) "
                          "(4) or (position, log-scales, opacity) (7)")

@@ -1,6 +1,7 @@
 """Serving pattern: continuous batching of render requests of different
 scenes and resolutions.  Each result is the same alone and in the mix
-(bit-identical: the batched forward runs the same per-tile computation)."""
+(bit-identical: the batched forward runs the same per-tile computation, and
+a batch of one request runs the single-view calls)."""
 import numpy as np
 import pytest
 
@@ -45,6 +46,10 @@ def test_each_result_same_alone_and_in_the_mix(realtime):
     for j in jobs:
         assert torch.equal(server.images[j.idx], _alone(scenes, j, st)), j.idx
     assert out["p99_ms"] >= out["p50_ms"] > 0
+    # batches of one request take the single-view calls, larger ones the batched pass
+    assert out["batched_requests"] > out.get("single_view_batches", 0)
+    if realtime:                                  # requests arriving one at a time: both paths ran
+        assert out.get("single_view_batches", 0) > 0
 
 
 def test_admission_waits_for_memory_and_completes():
