@@ -31,9 +31,10 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-fopenmp",
                "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        if subprocess.run(cmd).returncode != 0:          # no OpenMP: the all-core variants run on one thread
+            subprocess.run([c for c in cmd if c != "-fopenmp"], check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -72,6 +73,9 @@ def _load():
             lib.orc_render.argtypes = [P, P, P, P, P, P, P]
             lib.orc_render_rows.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P]
             lib.orc_backward_rows.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P]
+            lib.orc_render_rows_mt.argtypes = lib.orc_render_rows.argtypes
+            lib.orc_backward_rows_mt.argtypes = lib.orc_backward_rows.argtypes
+            lib.orc_threads.restype = C.c_int
             lib.orc_l1_loss_grad.restype = C.c_double
             lib.orc_l1_loss_grad.argtypes = [P, P, C.c_int, C.c_int, C.c_int, P]
             lib.orc_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P, P]
@@ -181,9 +185,16 @@ def bin_sort(scene, cam, st):
     return keys[:M], gids[:M], ranges
 
 
-def render(scene, cam, st, rows=None):
+def threads() -> int:
+    """Host threads the all-core variants use (OpenMP; 1 without it)."""
+    return int(_load().orc_threads())
+
+
+def render(scene, cam, st, rows=None, all_cores=False):
     """Front-to-back compositing (Section 3, Eq. alpha_blend), float64.
-    rows = (y0, h): only rows [y0, y0 + h) of the same view ([h, W] outputs)."""
+    rows = (y0, h): only rows [y0, y0 + h) of the same view ([h, W] outputs).
+    all_cores: the same per-pixel computation with rows dealt to all host
+    threads (identical results; a timing baseline)."""
     lib = _load()
     b = _Bound(scene, cam, st)
     y0, H = (0, cam.height) if rows is None else rows
@@ -192,8 +203,8 @@ def render(scene, cam, st, rows=None):
     final_T = np.zeros((H, W))
     n_contrib = np.zeros((H, W), np.int32)
     band = np.zeros((H, W), np.uint8)
-    if lib.orc_render_rows(*b.refs(), int(y0), int(H), _ptr(image), _ptr(final_T), _ptr(n_contrib),
-                           _ptr(band)) != 0:
+    fn = lib.orc_render_rows_mt if all_cores else lib.orc_render_rows
+    if fn(*b.refs(), int(y0), int(H), _ptr(image), _ptr(final_T), _ptr(n_contrib), _ptr(band)) != 0:
         raise ValueError("rows outside the view")
     return dict(image=image, final_T=final_T, n_contrib=n_contrib, band=band.astype(bool))
 
@@ -209,12 +220,15 @@ def l1_loss_grad(image, target, n_views=1):
     return L, g
 
 
-def backward(scene, cam, st, dL_dC, acc=None, rows=None):
+def backward(scene, cam, st, dL_dC, acc=None, rows=None, all_cores=False, blocks=True):
     """Parameter gradients and full 3x3 splitting matrices of one view
     (Section 4.4, Algorithm 1), plus S_po [n,3], the position-opacity block of
     the splitting matrix over theta = (p, o).  Accumulates into `acc` when given.
     rows = (y0, h): only rows [y0, y0 + h) of the same view carry gradient
-    (dL_dC is [h, W, 3])."""
+    (dL_dC is [h, W, 3]).  all_cores: rows dealt to all host threads, each
+    summing into its own copy, the copies added at the end (the same terms in
+    another order; a timing baseline).  blocks=False leaves out S_po and S_ls
+    (the splitting matrix over the position only, as the paper's experiments)."""
     lib = _load()
     b = _Bound(scene, cam, st)
     n, K = scene.n, (scene.sh_degree + 1) ** 2
@@ -227,9 +241,11 @@ def backward(scene, cam, st, dL_dC, acc=None, rows=None):
     y0, h = (0, cam.height) if rows is None else rows
     if dL.shape[:2] != (h, cam.width):
         raise ValueError("dL_dC must cover the rows")
-    if lib.orc_backward_rows(*b.refs(), int(y0), int(h), _ptr(dL), _ptr(acc["means"]), _ptr(acc["log_scales"]),
-                             _ptr(acc["quats"]), _ptr(acc["opacity_logit"]), _ptr(acc["sh"]),
-                             _ptr(acc["S"]), _ptr(acc["S_po"]), _ptr(acc["S_ls"]), _ptr(grad2d)) != 0:
+    fn = lib.orc_backward_rows_mt if all_cores else lib.orc_backward_rows
+    if fn(*b.refs(), int(y0), int(h), _ptr(dL), _ptr(acc["means"]), _ptr(acc["log_scales"]),
+          _ptr(acc["quats"]), _ptr(acc["opacity_logit"]), _ptr(acc["sh"]),
+          _ptr(acc["S"]), _ptr(acc["S_po"] if blocks else None), _ptr(acc["S_ls"] if blocks else None),
+          _ptr(grad2d)) != 0:
         raise ValueError("rows outside the view")
     acc["grad2d"] = grad2d
     return acc

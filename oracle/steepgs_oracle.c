@@ -40,6 +40,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define PI_D 3.14159265358979323846
 
@@ -929,6 +932,108 @@ int orc_backward(const orc_scene *sc, const orc_camera *cam, const orc_settings 
 {
     return orc_backward_rows(sc, cam, st, 0, cam->height, dL_dC, g_means, g_log_scales, g_quats, g_logit, g_sh,
                              S, S_po, S_ls, grad2d);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same render and backward on all host cores (a timing baseline; the    */
+/* single-thread functions above are the pinned reference).  Rows are dealt  */
+/* to threads one at a time, each thread runs render_view / backward_view on */
+/* its rows exactly as above, into its own copy of the per-Gaussian sums,    */
+/* and the copies are added at the end: the same terms, summed in another    */
+/* order.  Without OpenMP these run on one thread.                           */
+/* ------------------------------------------------------------------------ */
+
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static void view_build_mt(const orc_scene *sc, const orc_camera *cam, const orc_settings *st, orc_view *v)
+{
+    v->n = sc->n;
+    v->gx = (cam->width + st->tile_w - 1) / st->tile_w;
+    v->gy = (cam->height + st->tile_h - 1) / st->tile_h;
+    v->ntiles = v->gx * v->gy;
+    v->pr = (orc_proj *)malloc(sizeof(orc_proj) * (size_t)(sc->n > 0 ? sc->n : 1));
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < sc->n; ++i) project_one(sc, cam, st, i, &v->pr[i]);
+    v->M = orc_bin_sort(sc, cam, st, NULL, NULL, NULL, 0);
+    uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(v->M > 0 ? v->M : 1));
+    v->gids = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(v->M > 0 ? v->M : 1));
+    v->ranges = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)v->ntiles);
+    orc_bin_sort(sc, cam, st, keys, v->gids, v->ranges, v->M);
+    free(keys);
+}
+
+int orc_render_rows_mt(const orc_scene *sc, const orc_camera *cam, const orc_settings *st, int y0, int h,
+                       double *image, double *final_T, int32_t *n_contrib, uint8_t *band)
+{
+    if (y0 < 0 || h < 0 || y0 + h > cam->height) return -1;
+    orc_view v;
+    view_build_mt(sc, cam, st, &v);
+    const size_t W = (size_t)cam->width;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < h; ++r)
+        render_view(&v, cam, st, y0 + r, y0 + r + 1, image + 3 * W * r, final_T ? final_T + W * r : NULL,
+                    n_contrib ? n_contrib + W * r : NULL, band ? band + W * r : NULL);
+    view_free(&v);
+    return 0;
+}
+
+int orc_backward_rows_mt(const orc_scene *sc, const orc_camera *cam, const orc_settings *st, int y0, int h,
+                         const double *dL_dC, double *g_means, double *g_log_scales, double *g_quats,
+                         double *g_logit, double *g_sh, double *S, double *S_po, double *S_ls, double *grad2d)
+{
+    if (y0 < 0 || h < 0 || y0 + h > cam->height) return -1;
+    orc_view v;
+    view_build_mt(sc, cam, st, &v);
+    const size_t n = (size_t)(sc->n > 0 ? sc->n : 1), W = (size_t)cam->width;
+    const int T = orc_threads();
+    grad2d_t *g2 = (grad2d_t *)calloc(n * (size_t)T, sizeof(grad2d_t));
+    double *St = S ? (double *)calloc(9 * n * (size_t)T, sizeof(double)) : NULL;
+    double *Pt = S_po ? (double *)calloc(3 * n * (size_t)T, sizeof(double)) : NULL;
+    double *Lt = S_ls ? (double *)calloc(18 * n * (size_t)T, sizeof(double)) : NULL;
+#pragma omp parallel
+    {
+#ifdef _OPENMP
+        const size_t t = (size_t)omp_get_thread_num();
+#else
+        const size_t t = 0;
+#endif
+#pragma omp for schedule(dynamic, 1)
+        for (int r = 0; r < h; ++r)
+            backward_view(sc, &v, cam, st, y0 + r, y0 + r + 1, dL_dC + 3 * W * r, g2 + n * t,
+                          St ? St + 9 * n * t : NULL, Pt ? Pt + 3 * n * t : NULL, Lt ? Lt + 18 * n * t : NULL);
+    }
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < sc->n; ++i) {
+        grad2d_t sum;
+        memset(&sum, 0, sizeof sum);
+        for (int t = 0; t < T; ++t) {
+            const grad2d_t *q = g2 + n * (size_t)t + i;
+            sum.mu[0] += q->mu[0]; sum.mu[1] += q->mu[1];
+            for (int k = 0; k < 3; ++k) { sum.Q[k] += q->Q[k]; sum.rgb[k] += q->rgb[k]; }
+            sum.o += q->o;
+            if (S) for (int k = 0; k < 9; ++k) S[9 * (size_t)i + k] += St[9 * (n * t + i) + k];
+            if (S_po) for (int k = 0; k < 3; ++k) S_po[3 * (size_t)i + k] += Pt[3 * (n * t + i) + k];
+            if (S_ls) for (int k = 0; k < 18; ++k) S_ls[18 * (size_t)i + k] += Lt[18 * (n * t + i) + k];
+        }
+        if (grad2d) {
+            double *o = grad2d + 9 * (size_t)i;
+            o[0] = sum.mu[0]; o[1] = sum.mu[1];
+            o[2] = sum.Q[0]; o[3] = sum.Q[1]; o[4] = sum.Q[2];
+            o[5] = sum.o; o[6] = sum.rgb[0]; o[7] = sum.rgb[1]; o[8] = sum.rgb[2];
+        }
+        if (!v.pr[i].is.culled)
+            chain_to_params(sc, cam, &v.pr[i], &sum, i, g_means, g_log_scales, g_quats, g_logit, g_sh);
+    }
+    free(g2); free(St); free(Pt); free(Lt);
+    view_free(&v);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

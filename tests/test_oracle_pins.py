@@ -849,3 +849,27 @@ def test_7d_split_predicted_decrease_interlacing_and_optimality():
         eps = 0.5 * np.exp(sc.log_scales[i].astype(np.float64)).max()
         np.testing.assert_allclose(out["log_scales"][i] - out["log_scales"][n + r], 2 * eps * v7[i, 3:6],
                                    atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# The all-core variants (a timing baseline) against the single-thread oracle
+# --------------------------------------------------------------------------
+
+def test_all_core_render_and_backward_equal_the_single_thread_oracle():
+    sc = synth.cluster_scene(3, 3000, 3)
+    cam = synth.camera_lookat((1.0, 0.5, -6.0), (0, 0, 0), 150, 101, 150.0)
+    st = synth.Settings()
+    r1 = oracle.render(sc, cam, st)
+    rm = oracle.render(sc, cam, st, all_cores=True)
+    for k in ("image", "final_T", "n_contrib", "band"):
+        assert np.array_equal(r1[k], rm[k]), k
+    _, g = oracle.l1_loss_grad(r1["image"], synth.target_image(2, cam.height, cam.width))
+    a1 = oracle.backward(sc, cam, st, g)
+    am = oracle.backward(sc, cam, st, g, all_cores=True)
+    for k in ("means", "log_scales", "quats", "opacity_logit", "sh", "S", "S_po", "S_ls", "grad2d"):
+        d = np.linalg.norm(a1[k] - am[k]) / max(np.linalg.norm(a1[k]), 1e-300)
+        assert d < 1e-12, (k, d)
+    # a row window, and accumulation into an existing acc
+    acc = oracle.backward(sc, cam, st, g[40:57], rows=(40, 17))
+    accm = oracle.backward(sc, cam, st, g[40:57], rows=(40, 17), all_cores=True)
+    assert np.linalg.norm(acc["S"] - accm["S"]) <= 1e-12 * np.linalg.norm(acc["S"])
