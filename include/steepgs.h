@@ -355,6 +355,18 @@ int sgs_render_views_with_splitting(const sgs_gaussians *g, const sgs_camera *ca
                                     float *S_po_accum, int32_t *d_count, int64_t capacity, void *ws,
                                     size_t ws_bytes, void *stream);
 
+/* The binning that the last sgs_render_views_with_splitting call with the
+ * same n, cameras, settings and capacity left in `ws`, for inspection (no
+ * work is launched): out->gids [capacity] projection rows v*n + i in (global
+ * tile id, float32 depth bits, row) order, out->ranges [T_total, 2] per global
+ * tile (view v's tiles follow view v-1's), out->order the tile schedule,
+ * out->capacity; out->keys, out->count, out->walk and out->walk_count are
+ * NULL.  The pointers point into ws and stay valid while ws holds that call's
+ * results.  Errors: SGS_ERR_INVALID_ARG as sgs_render_views_workspace_size,
+ * or a NULL out; SGS_ERR_WORKSPACE when ws_bytes is too small. */
+int sgs_render_views_bins(int32_t n, const sgs_camera *cams, int32_t n_views, const sgs_settings *st,
+                          int64_t capacity, void *ws, size_t ws_bytes, sgs_bins *out);
+
 /* Forward-only render of a batch of views whose scenes may differ (the
  * render-serving batch): scenes[v] is the scene of view v (sh_degree must be
  * equal across the batch), images as in sgs_render_views_with_splitting.

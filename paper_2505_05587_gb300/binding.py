@@ -120,6 +120,8 @@ def lib():
         L.sgs_fma_probe.argtypes = [P, I32, I32, P]
         L.sgs_fma_probe.restype = C.c_int
         L.sgs_densify_split_noalloc.argtypes = [P, P, P, P, F, F, F, P, F, I64, P, I64, P, P, P, P, P]
+        L.sgs_render_views_bins.argtypes = [I32, P, I32, P, I64, P, SZ, P]
+        L.sgs_render_views_bins.restype = C.c_int
         L.sgs_clear.argtypes = [P, SZ, P]
         L.sgs_clear.restype = C.c_int
         for name in ("sgs_project", "sgs_bin_sort_workspace_size", "sgs_bin_sort", "sgs_render_fwd",
@@ -505,6 +507,29 @@ def render_views_with_splitting(g: GaussianTensors, cams, st, batch: int, target
                                                  _arr(S_accum, "S_accum", F32, 6 * n), _arr(S_po, "S_po", F32, 3 * n),
                                                  _arr(d_count, "d_count", I32, 1), capacity, _p(ws),
                                                  ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def render_views_bins(n: int, cams, st, capacity: int, ws: torch.Tensor, count: torch.Tensor) -> BinBuffers:
+    """The binning the last render_views_with_splitting call left in `ws`
+    (gids = projection rows v*n + i, ranges over global tile ids), as tensor
+    views into ws (valid while ws holds that call's results)."""
+    arr, sc = cameras_c(cams), settings_c(st)
+    b = Bins()
+    _check("sgs_render_views_bins",
+           lib().sgs_render_views_bins(n, arr, len(cams), C.byref(sc), capacity, _p(ws),
+                                       ws.numel() * ws.element_size(), C.byref(b)))
+    T = sum(num_tiles(c, st) for c in cams)
+    base = ws.data_ptr()
+    nbytes = ws.numel() * ws.element_size()
+
+    def view(ptr, count_):
+        off = int(ptr) - base
+        if off < 0 or off + 4 * count_ > nbytes:
+            raise RuntimeError("sgs_render_views_bins: pointer outside the workspace")
+        return ws[off:off + 4 * count_].view(torch.int32)
+
+    return BinBuffers(view(b.gids, max(capacity, 1)), None, view(b.ranges, 2 * T).view(T, 2), count, capacity,
+                      view(b.order, max(T, 1)))
 
 
 def _scenes_c(scenes):

@@ -367,6 +367,19 @@ int sgs_render_views_workspace_size(int32_t n, const sgs_camera* cams, int32_t n
     return SGS_OK;
 }
 
+int sgs_render_views_bins(int32_t n, const sgs_camera* cams, int32_t n_views, const sgs_settings* st,
+                          int64_t capacity, void* ws, size_t ws_bytes, sgs_bins* out) {
+    if (n < 0 || capacity < 0 || capacity > ((int64_t)1 << 31) - 1 || !out || !valid_views(cams, n_views, st) ||
+        (long long)n * n_views > ((long long)1 << 31) - 1)
+        return SGS_ERR_INVALID_ARG;
+    ViewsDev vd = make_views(cams, n_views, *st, nullptr, n);
+    ViewsWs w = carve_views_ws(nullptr, vd, capacity, true);
+    if (!ws || ws_bytes < w.bytes) return SGS_ERR_WORKSPACE;
+    w = carve_views_ws(ws, vd, capacity, true);
+    *out = w.bins;
+    return SGS_OK;
+}
+
 int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* cams, int32_t n_views,
                                     const sgs_settings* st, int32_t batch, const float* targets, float* images,
                                     float* loss, const sgs_grads* grads, int32_t flags, float* S_accum,

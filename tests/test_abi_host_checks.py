@@ -210,5 +210,14 @@ def test_batched_checks(lib):
     a = list(base)
     a[15] = sz.value - 1
     assert lib.sgs_render_views_with_splitting(*a) == WORKSPACE
+    # the binning inside the workspace: pointers into ws, no launch, no device needed
+    b = B.Bins()
+    assert lib.sgs_render_views_bins(10, cams, 2, C.byref(st), 1000, _ptr(6), sz.value - 1, C.byref(b)) == WORKSPACE
+    assert lib.sgs_render_views_bins(10, cams, 2, C.byref(st), 1000, _ptr(6), sz.value, None) == INVALID
+    assert lib.sgs_render_views_bins(10, cams, 2, C.byref(st), 1000, _ptr(6), sz.value, C.byref(b)) == 0
+    lo, hi = DUMMY + 4096 * 6, DUMMY + 4096 * 6 + sz.value
+    for p in (b.gids, b.ranges, b.order):
+        assert lo <= p < hi
+    assert b.capacity == 1000 and not b.keys and not b.count and not b.walk
     scenes = (B.Gaussians * 2)(_gauss(10, 0), _gauss(10, 1))                    # SH degrees differ
     assert lib.sgs_render_batch_workspace_size(scenes, cams, 2, C.byref(st), 1000, C.byref(sz)) == INVALID
