@@ -480,9 +480,7 @@ __device__ __forceinline__ void bwd_tile_walk(int tile, int gx, int W, int H, ui
     const float g2 = inside ? dL_dimage[3 * pix + 2] : 0.0f;
     float acc0 = st.bg[0], acc1 = st.bg[1], acc2 = st.bg[2];
 
-    constexpr int EPF = HI ? 1 : 2;
     float* red = sm.red[warp];
-    int pend = 0;
     uint32_t gid_a = 0u;
     auto flush = [&](uint32_t gid_b, int rows) {
         __syncwarp();
@@ -499,6 +497,67 @@ __device__ __forceinline__ void bwd_tile_walk(int tile, int gx, int W, int H, ui
     float4* e_mu = sm.ent[warp][0];
     float4* e_co = sm.ent[warp][1];
     float4* e_c = sm.ent[warp][2];
+    // an entry's per-pixel quantities that do not depend on the entries behind it
+    struct Staged {
+        float dx, dy, araw, c0, c1, c2;
+        uint32_t gid, pos;
+    };
+    auto stage = [&](int k) {
+        const float4 m = e_mu[k];
+        const float4 cp = e_co[k];
+        const float4 col = e_c[k];
+        Staged a;
+        a.dx = lx - m.x;
+        a.dy = ly - m.y;
+        a.araw = __fmul_rn(cp.w, gauss2(cp, a.dx, a.dy));
+        a.c0 = col.x;
+        a.c1 = col.y;
+        a.c2 = col.z;
+        a.gid = __float_as_uint(m.z);
+        a.pos = __float_as_uint(m.w);
+        return a;
+    };
+    // back to front through one entry: transmittance in front of it, its
+    // dL/dalpha, the colour behind, and its per-pixel values into buffer slot
+    // `slot` (rows 9 slot .. 9 slot + 8, and the higher moments in rows 9..17)
+    auto composite = [&](const Staged& a, int slot) {
+        const bool valid = a.pos < last && a.araw >= st.alpha_min;
+        const bool clamped = a.araw >= st.alpha_max;
+        const float ae = valid ? (clamped ? st.alpha_max : a.araw) : 0.0f;
+        const float one_m = 1.0f - ae;
+        T = __fdividef(T, one_m);                     // transmittance in front of this Gaussian
+        const float dLda = T * (g0 * (a.c0 - acc0) + g1 * (a.c1 - acc1) + g2 * (a.c2 - acc2));
+        acc0 += ae * (a.c0 - acc0);
+        acc1 += ae * (a.c1 - acc1);
+        acc2 += ae * (a.c2 - acc2);
+        const float aT = ae * T;
+        const float w = (clamped ? 0.0f : ae) * dLda;   // dL/dsigma * sigma
+        const float dx = a.dx, dy = a.dy;
+        const float wdx = w * dx, wdy = w * dy;
+        float* rb = red + slot * 9 * kRedStride + lane;
+        rb[0 * kRedStride] = wdx;
+        rb[1 * kRedStride] = wdy;
+        rb[2 * kRedStride] = wdx * dx;
+        rb[3 * kRedStride] = wdx * dy;
+        rb[4 * kRedStride] = wdy * dy;
+        rb[5 * kRedStride] = w;
+        rb[6 * kRedStride] = g0 * aT;
+        rb[7 * kRedStride] = g1 * aT;
+        rb[8 * kRedStride] = g2 * aT;
+        if constexpr (HI) {
+            const float wxx = wdx * dx, wyy = wdy * dy;
+            rb[9 * kRedStride] = wxx * dx;
+            rb[10 * kRedStride] = wxx * dy;
+            rb[11 * kRedStride] = wyy * dx;
+            rb[12 * kRedStride] = wyy * dy;
+            rb[13 * kRedStride] = wxx * dx * dx;
+            rb[14 * kRedStride] = wxx * dx * dy;
+            rb[15 * kRedStride] = wxx * dy * dy;
+            rb[16 * kRedStride] = wyy * dx * dy;
+            rb[17 * kRedStride] = wyy * dy * dy;
+        }
+        return a.gid;
+    };
     for (int end = (int)cnt; end > 0; end -= 32) {
         const int start = max(0, end - 32);
         const int c = end - start;
@@ -515,58 +574,28 @@ __device__ __forceinline__ void bwd_tile_walk(int tile, int gx, int W, int H, ui
             e_c[lane] = rgb[g];
         }
         __syncwarp();
-        for (int k = c - 1; k >= 0; --k) {
-            const float4 m = e_mu[k];
-            const float4 cp = e_co[k];
-            const float4 col = e_c[k];
-            const float dx = lx - m.x;
-            const float dy = ly - m.y;
-            const float araw = __fmul_rn(cp.w, gauss2(cp, dx, dy));
-            const bool valid = __float_as_uint(m.w) < last && araw >= st.alpha_min;
-            const bool clamped = araw >= st.alpha_max;
-            const float ae = valid ? (clamped ? st.alpha_max : araw) : 0.0f;
-            const float one_m = 1.0f - ae;
-            T = __fdividef(T, one_m);                 // transmittance in front of this Gaussian
-            const float dLda = T * (g0 * (col.x - acc0) + g1 * (col.y - acc1) + g2 * (col.z - acc2));
-            acc0 += ae * (col.x - acc0);
-            acc1 += ae * (col.y - acc1);
-            acc2 += ae * (col.z - acc2);
-            const float aT = ae * T;
-            const float w = (clamped ? 0.0f : ae) * dLda;   // dL/dsigma * sigma
-            const float wdx = w * dx, wdy = w * dy;
-            float* rb = red + pend * 9 * kRedStride + lane;
-            rb[0 * kRedStride] = wdx;
-            rb[1 * kRedStride] = wdy;
-            rb[2 * kRedStride] = wdx * dx;
-            rb[3 * kRedStride] = wdx * dy;
-            rb[4 * kRedStride] = wdy * dy;
-            rb[5 * kRedStride] = w;
-            rb[6 * kRedStride] = g0 * aT;
-            rb[7 * kRedStride] = g1 * aT;
-            rb[8 * kRedStride] = g2 * aT;
-            if constexpr (HI) {
-                const float wxx = wdx * dx, wyy = wdy * dy;
-                rb[9 * kRedStride] = wxx * dx;
-                rb[10 * kRedStride] = wxx * dy;
-                rb[11 * kRedStride] = wyy * dx;
-                rb[12 * kRedStride] = wyy * dy;
-                rb[13 * kRedStride] = wxx * dx * dx;
-                rb[14 * kRedStride] = wxx * dx * dy;
-                rb[15 * kRedStride] = wxx * dy * dy;
-                rb[16 * kRedStride] = wyy * dx * dy;
-                rb[17 * kRedStride] = wyy * dy * dy;
+        if constexpr (HI) {
+            for (int k = c - 1; k >= 0; --k) {
+                const Staged a = stage(k);
+                flush(composite(a, 0), kRedRows);
             }
-            const uint32_t gid = __float_as_uint(m.z);
-            if (pend + 1 == EPF) {
-                flush(gid, kRedRows);
-                pend = 0;
-            } else {
-                gid_a = gid;
-                ++pend;
+        } else {
+            // two entries at a time: their alpha evaluations are independent
+            // (only the transmittance and the colour behind are carried from
+            // one entry to the next), and the pair fills one 18-row flush
+            int k = c - 1;
+            for (; k >= 1; k -= 2) {
+                const Staged a = stage(k);
+                const Staged b = stage(k - 1);
+                gid_a = composite(a, 0);
+                flush(composite(b, 1), kRedRows);
+            }
+            if (k == 0) {
+                gid_a = composite(stage(0), 0);
+                flush(gid_a, 9);
             }
         }
     }
-    if (pend > 0) flush(gid_a, 9);
 }
 
 // Clears the accumulator rows (and the higher-moment rows when given) of the
@@ -631,9 +660,10 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_kernel(
                                   dL_dimage, g2d, g2d_hi, sm);
 }
 
-// The backward pass over the forward's walk lists (same residency bound).
+// The backward pass over the forward's walk lists, bounded to 32 resident
+// warps per SM (64 registers): the two-entry steps need the registers.
 template <int TW, int TH, bool HI>
-__global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_walk_kernel(
+__global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) render_bwd_walk_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, int W, int H, int gx, SetDev st,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
