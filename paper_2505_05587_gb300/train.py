@@ -12,6 +12,8 @@ splitting matrices and gradients accumulated every step, and every T_split
 steps from `start` on, the steepest-density-control split: lambda_min, v_min
 of S / (steps accumulated), offspring p +- eps v_min with opacity o/2.
 Offspring get zeroed Adam moments; S and G are reset after each split.
+The trainer's state between steps can be saved and restored (``save``,
+``restore``, ``run(first_step=...)``).
 """
 from __future__ import annotations
 
@@ -259,11 +261,58 @@ class SteepGSTrainer:
         self._alloc(n2)
         self.step_graphs = None                     # captured again for the new buffers
 
-    def run(self, steps: int | None = None, log_path: str | None = None):
+    # -- checkpoint / resume ------------------------------------------------
+    # The state between two steps of Algorithm 1: the Gaussians, their Adam
+    # moments and step count, the splitting-matrix and gradient accumulators
+    # with the number of steps they hold, and the log.  The loop draws no
+    # random numbers, so this is all a resumed run needs.
+    _FIELDS = ("params", "m", "v")
+
+    def state_dict(self) -> dict:
+        c = lambda t: None if t is None else t.detach().clone()    # noqa: E731
+        return {"params": [c(p) for p in self.params], "m": [c(t) for t in self.m], "v": [c(t) for t in self.v],
+                "adam_t": self.adam_t, "S": c(self.S), "S_po": c(self.S_po), "S_ls": c(self.S_ls),
+                "G": c(self.G), "n_accum": self.n_accum, "log": [dict(r) for r in self.log],
+                "sh_degree": self.sh_degree, "dim_theta": self.cfg.dim_theta}
+
+    def load_state_dict(self, sd: dict):
+        if sd["sh_degree"] != self.sh_degree or sd["dim_theta"] != self.cfg.dim_theta:
+            raise ValueError("checkpoint: SH degree or dim Theta differs from this trainer's")
+        dev = self.params[0].device
+        self.params = [p.to(dev).clone().requires_grad_(True) for p in sd["params"]]
+        self._alloc(self.n)
+        self.m = [t.to(dev).clone() for t in sd["m"]]
+        self.v = [t.to(dev).clone() for t in sd["v"]]
+        self.adam_t = int(sd["adam_t"])
+        for name in ("S", "S_po", "S_ls", "G"):
+            if sd[name] is not None:
+                getattr(self, name).copy_(sd[name].to(dev))
+        self.n_accum = int(sd["n_accum"])
+        self.log = [dict(r) for r in sd["log"]]
+        self.step_graphs = None                     # captured again for these buffers
+
+    def save(self, path: str, step: int):
+        """Checkpoint after `step` (1-based) steps."""
+        torch.save({"step": int(step), "state": self.state_dict()}, path)
+
+    def restore(self, path: str) -> int:
+        """Loads a checkpoint; returns the number of steps it holds (resume at
+        that step + 1)."""
+        ck = torch.load(path, map_location=self.params[0].device, weights_only=False)
+        self.load_state_dict(ck["state"])
+        return int(ck["step"])
+
+    def run(self, steps: int | None = None, log_path: str | None = None, first_step: int = 1,
+            checkpoint_path: str | None = None, checkpoint_every: int = 0):
+        """Steps first_step .. steps (1-based; first_step > 1 after restore);
+        with checkpoint_path and checkpoint_every, a checkpoint is written after
+        every checkpoint_every-th step."""
         steps = steps or self.cfg.steps
         t0 = time.perf_counter()
-        for t in range(1, steps + 1):
+        for t in range(first_step, steps + 1):
             self.step(t)
+            if checkpoint_path and checkpoint_every and t % checkpoint_every == 0:
+                self.save(checkpoint_path, t)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         if log_path:
