@@ -128,6 +128,11 @@ struct L1Out {
 // reads of the summing lanes (a row per lane) are free of bank conflicts.
 constexpr int kRedRows = 18;
 constexpr int kRedStride = 36;
+// Half rows of the walk backward: after one shuffle exchange between lanes
+// 16 apart, each of the nine values of an entry is carried by 16 lanes; rows
+// of 16 floats on a 20-float stride keep both the writes (rows j and j + 4
+// from the two lane halves at once) and the 16-byte row reads conflict-free.
+constexpr int kHalfStride = 20;
 
 template <int BATCH, int NW>
 struct BwdSmem {
@@ -279,6 +284,18 @@ __device__ __forceinline__ unsigned long long add_f32x2(unsigned long long a, un
     unsigned long long d;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
+}
+
+// Sum of the 16 floats of one 16-byte aligned row (four 16-byte loads).
+__device__ __forceinline__ float row_sum16(const float* row) {
+    const ulonglong2* r = reinterpret_cast<const ulonglong2*>(row);
+    const ulonglong2 a = r[0], b = r[1], c = r[2], d = r[3];
+    unsigned long long s0 = add_f32x2(add_f32x2(a.x, b.x), add_f32x2(c.x, d.x));
+    const unsigned long long s1 = add_f32x2(add_f32x2(a.y, b.y), add_f32x2(c.y, d.y));
+    s0 = add_f32x2(s0, s1);
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(s0));
+    return lo + hi;
 }
 
 __device__ __forceinline__ float row_sum32(const float* row) {
@@ -485,11 +502,13 @@ __device__ __forceinline__ void bwd_tile_walk(int tile, int gx, int W, int H, ui
     auto flush = [&](uint32_t gid_b, int rows) {
         __syncwarp();
         if (lane < rows) {
-            const float t = row_sum32(red + lane * kRedStride);
-            if constexpr (HI)
+            if constexpr (HI) {
+                const float t = row_sum32(red + lane * kRedStride);
                 atomicAdd((lane < 9 ? g2d : g2d_hi) + (size_t)gid_b * kG2dStride + (lane < 9 ? lane : lane - 9), t);
-            else
+            } else {
+                const float t = row_sum16(red + lane * kHalfStride);
                 atomicAdd(g2d + (size_t)(lane < 9 ? gid_a : gid_b) * kG2dStride + (lane < 9 ? lane : lane - 9), t);
+            }
         }
         __syncwarp();
     };
@@ -534,6 +553,24 @@ __device__ __forceinline__ void bwd_tile_walk(int tile, int gx, int W, int H, ui
         const float w = (clamped ? 0.0f : ae) * dLda;   // dL/dsigma * sigma
         const float dx = a.dx, dy = a.dy;
         const float wdx = w * dx, wdy = w * dy;
+        if constexpr (!HI) {
+            // lanes 16 apart exchange halves: lanes 0-15 keep values 0-3, lanes
+            // 16-31 values 4-7, each summed over the pair; value 8 is summed by
+            // both and written by the lower half
+            const float v[8] = {wdx, wdy, wdx * dx, wdx * dy, wdy * dy, w, g0 * aT, g1 * aT};
+            const bool up = lane & 16;
+            float* rb = red + (slot * 9 + (up ? 4 : 0)) * kHalfStride + (lane & 15);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float send = up ? v[j] : v[j + 4];
+                const float keep = up ? v[j + 4] : v[j];
+                rb[j * kHalfStride] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
+            const float v8 = g2 * aT;
+            const float s8 = v8 + __shfl_xor_sync(0xffffffffu, v8, 16);
+            if (!up) red[(slot * 9 + 8) * kHalfStride + lane] = s8;
+            return a.gid;
+        }
         float* rb = red + slot * 9 * kRedStride + lane;
         rb[0 * kRedStride] = wdx;
         rb[1 * kRedStride] = wdy;
