@@ -314,12 +314,16 @@ struct ViewsWs {
     float* dL;
     float* g2d;
     uint32_t* counters;
+    WalkLists wl;
     size_t bytes;
 };
 
-static ViewsWs carve_views_ws(void* base, const ViewsDev& vd, int64_t capacity, bool with_backward) {
+// The workspace of a multi-view pass.  With the backward it also holds the
+// forward's walk lists (warps per tile x capacity entries, and a count per
+// warp of every tile), which the backward then follows.
+static ViewsWs carve_views_ws(void* base, const ViewsDev& vd, int64_t capacity, bool with_backward, int nw = 8) {
     Carver c{reinterpret_cast<char*>(base), 0};
-    ViewsWs w{};                                    // no walk lists: the multi-view kernels cull per batch
+    ViewsWs w{};
     const size_t rows = (size_t)(vd.row_off[vd.nv] > 0 ? vd.row_off[vd.nv] : 1);
     const size_t P = (size_t)(vd.P_total > 0 ? vd.P_total : 1);
     const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
@@ -342,6 +346,11 @@ static ViewsWs carve_views_ws(void* base, const ViewsDev& vd, int64_t capacity, 
     w.dL = with_backward ? c.take<float>(3 * P) : nullptr;
     w.g2d = with_backward ? c.take<float>(16 * rows) : nullptr;
     w.counters = c.take<uint32_t>(2);
+    if (with_backward) {
+        w.wl.cap = (long long)nw * (long long)cap;
+        w.wl.walk = c.take<uint32_t>((size_t)w.wl.cap);
+        w.wl.count = c.take<uint32_t>((size_t)nw * (size_t)(vd.T_total > 0 ? vd.T_total : 1));
+    }
     w.bytes = c.off + 256;
     return w;
 }
@@ -363,7 +372,7 @@ int sgs_render_views_workspace_size(int32_t n, const sgs_camera* cams, int32_t n
         (long long)n * n_views > ((long long)1 << 31) - 1)
         return SGS_ERR_INVALID_ARG;
     ViewsDev vd = make_views(cams, n_views, *st, nullptr, n);
-    *bytes = carve_views_ws(nullptr, vd, capacity, true).bytes;
+    *bytes = carve_views_ws(nullptr, vd, capacity, true, st->tile_w * st->tile_h / 32).bytes;
     return SGS_OK;
 }
 
@@ -373,9 +382,10 @@ int sgs_render_views_bins(int32_t n, const sgs_camera* cams, int32_t n_views, co
         (long long)n * n_views > ((long long)1 << 31) - 1)
         return SGS_ERR_INVALID_ARG;
     ViewsDev vd = make_views(cams, n_views, *st, nullptr, n);
-    ViewsWs w = carve_views_ws(nullptr, vd, capacity, true);
+    const int nw = st->tile_w * st->tile_h / 32;
+    ViewsWs w = carve_views_ws(nullptr, vd, capacity, true, nw);
     if (!ws || ws_bytes < w.bytes) return SGS_ERR_WORKSPACE;
-    w = carve_views_ws(ws, vd, capacity, true);
+    w = carve_views_ws(ws, vd, capacity, true, nw);
     *out = w.bins;
     return SGS_OK;
 }
@@ -396,9 +406,10 @@ int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* ca
                      !S_accum))
         return SGS_ERR_INVALID_ARG;
     ViewsDev vd = make_views(cams, n_views, *st, nullptr, g->n);
-    ViewsWs w = carve_views_ws(nullptr, vd, capacity, true);
+    const int nw = st->tile_w * st->tile_h / 32;
+    ViewsWs w = carve_views_ws(nullptr, vd, capacity, true, nw);
     if (!ws || ws_bytes < w.bytes) return SGS_ERR_WORKSPACE;
-    w = carve_views_ws(ws, vd, capacity, true);
+    w = carve_views_ws(ws, vd, capacity, true, nw);
     w.bins.count = d_count;
     const SetDev sd = make_set(*st);
     cudaStream_t s = (cudaStream_t)stream;
@@ -408,12 +419,12 @@ int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* ca
     if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 2 * sizeof(uint32_t), s);
     if (e == cudaSuccess)
         e = launch_render_fwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, images, w.final_T,
-                                    w.n_contrib, w.counters, w.bins.order, s);
+                                    w.n_contrib, w.counters, w.bins.order, w.wl, s);
     if (e == cudaSuccess) e = launch_l1_views(images, targets, vd, w.dL, loss, s);
     if (e == cudaSuccess && rows > 0) e = cudaMemsetAsync(w.g2d, 0, 16 * sizeof(float) * rows, s);
     if (e == cudaSuccess)
         e = launch_render_bwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, w.final_T, w.n_contrib,
-                                    w.dL, w.g2d, w.counters + 1, w.bins.order, s);
+                                    w.dL, w.g2d, w.counters + 1, w.bins.order, w.wl, s);
     if (e == cudaSuccess)
         e = launch_project_bwd(*g, w.proj, vd, w.g2d, nullptr, flags, *grads, S_accum, S_po_accum, nullptr, s);
     return cuda_status(e);
@@ -463,7 +474,7 @@ int sgs_render_batch_fwd(const sgs_gaussians* scenes, const sgs_camera* cams, in
     if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess)
         e = launch_render_fwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, images, w.final_T,
-                                    w.n_contrib, w.counters, w.bins.order, s);
+                                    w.n_contrib, w.counters, w.bins.order, WalkLists{nullptr, nullptr, 0}, s);
     return cuda_status(e);
 }
 

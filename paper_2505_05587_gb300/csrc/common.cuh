@@ -172,14 +172,21 @@ cudaError_t launch_render_bwd(const sgs_proj& proj, const sgs_bins& bins, const 
                               const SetDev& st, const float* final_T, const uint32_t* n_contrib,
                               const float* dL_dimage, float* g2d, float* g2d_hi, cudaStream_t stream);
 
+// Walk lists of a multi-view pass (all null: none; the kernels then cull
+// every list entry themselves): walk [cap] u32, count [T_total * warps per tile].
+struct WalkLists {
+    uint32_t* walk;
+    uint32_t* count;
+    long long cap;
+};
 cudaError_t launch_render_fwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                     const uint32_t* gids, const SetDev& st, int batch, float* images,
                                     float* final_T, uint32_t* n_contrib, uint32_t* counter, const uint32_t* order,
-                                    cudaStream_t stream);
+                                    const WalkLists& wl, cudaStream_t stream);
 cudaError_t launch_render_bwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                     const uint32_t* gids, const SetDev& st, int batch, const float* final_T,
                                     const uint32_t* n_contrib, const float* dL, float* g2d, uint32_t* counter,
-                                    const uint32_t* order, cudaStream_t stream);
+                                    const uint32_t* order, const WalkLists& wl, cudaStream_t stream);
 
 size_t ssim_ws_bytes(int H, int W);
 cudaError_t launch_ssim_l1(const float* image, const float* target, int H, int W, int n_views, float lam, float* dL,

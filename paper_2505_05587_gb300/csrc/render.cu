@@ -465,7 +465,7 @@ struct BwdWalkSmem {
 };
 
 template <int TW, int TH, bool HI>
-__device__ __forceinline__ void bwd_tile_walk(int tile, int gx, int W, int H, uint2 rg,
+__device__ __forceinline__ void bwd_tile_walk(int tile, int wb, int gx, int W, int H, uint2 rg,
                                               const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
                                               const float4* __restrict__ conic_opac, const float4* __restrict__ rgb,
                                               const SetDev& st, const float* __restrict__ final_T,
@@ -475,15 +475,15 @@ __device__ __forceinline__ void bwd_tile_walk(int tile, int gx, int W, int H, ui
                                               float* __restrict__ g2d, float* __restrict__ g2d_hi,
                                               BwdWalkSmem<TW * TH / 32>& sm) {
     constexpr int NW = TW * TH / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // `warp`: this warp's shared-memory slot
     const long long L = (long long)rg.y - (long long)rg.x;
-    const long long wbase = (long long)NW * rg.x + (long long)warp * L;
-    long long cnt = walk_count[(long long)tile * NW + warp];
+    const long long wbase = (long long)NW * rg.x + (long long)wb * L;
+    long long cnt = walk_count[(long long)tile * NW + wb];
     cnt = min(cnt, L);
     cnt = min(cnt, walk_cap - wbase);               // in bounds whatever the counts say
     if (cnt <= 0) return;
-    int bx, by;
-    warp_block_origin<TW>(tile, gx, TH, &bx, &by);
+    const int bx = (tile % gx) * TW + (wb % (TW / 8)) * 8;   // the tile's 8x4 block wb
+    const int by = (tile / gx) * TH + (wb / (TW / 8)) * 4;
     const int px = bx + (lane & 7);
     const int py = by + (lane >> 3);
     const bool inside = px < W && py < H;
@@ -711,8 +711,8 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) render_bwd_walk_ker
     __shared__ BwdWalkSmem<TW * TH / 32> sm;
     const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     if ((unsigned)t >= gridDim.x) return;      // a schedule that is not a permutation of the tiles
-    bwd_tile_walk<TW, TH, HI>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, final_T, n_contrib, dL_dimage,
-                              walk, walk_count, walk_cap, g2d, g2d_hi, sm);
+    bwd_tile_walk<TW, TH, HI>(t, threadIdx.x >> 5, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, final_T,
+                              n_contrib, dL_dimage, walk, walk_count, walk_cap, g2d, g2d_hi, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -720,14 +720,15 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) render_bwd_walk_ker
 // (the counter must be zero at launch).  Per-view maps are concatenated at
 // pixel offsets pix_off[v].
 // ---------------------------------------------------------------------------
-template <int TW, int TH, int BATCH>
+template <int TW, int TH, int BATCH, bool REC>
 __global__ void __launch_bounds__(TW * TH) render_fwd_views_kernel(
     ViewsDev vd, const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, SetDev st, float* __restrict__ images,
     float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ counter,
-    const uint32_t* __restrict__ order) {
+    const uint32_t* __restrict__ order, WalkOut wo) {
     pdl_wait_and_trigger();
-    __shared__ FwdSmem<BATCH, TW * TH / 32> sm;
+    constexpr int NW = TW * TH / 32;
+    __shared__ FwdSmem<BATCH, NW> sm;
     __shared__ int s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
@@ -740,9 +741,35 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_views_kernel(
         const int v = view_of_tile(vd, t);
         const CamDev& c = vd.cam[v];
         const long long po = vd.pix_off[v];
-        fwd_tile<TW, TH, BATCH>(t - vd.tile_off[v], c.gx, c.width, c.height, ranges[t], gids, xy, conic_opac, rgb,
-                                st, images + 3 * po, final_T + po, n_contrib + po, sm);
+        // walk lists index the global list (rows NW*start + ...) and count per
+        // global tile: the view's counts start at its first global tile
+        const WalkOut wv{wo.walk, wo.count ? wo.count + (long long)vd.tile_off[v] * NW : nullptr, wo.cap};
+        fwd_tile<TW, TH, BATCH, REC>(t - vd.tile_off[v], c.gx, c.width, c.height, ranges[t], gids, xy, conic_opac,
+                                     rgb, st, images + 3 * po, final_T + po, n_contrib + po, sm, nullptr, wv);
     }
+}
+
+// The backward pass of several views over the forward's walk lists: a block
+// per global tile in the schedule's order, each warp stepping through its own
+// list (as render_bwd_walk_kernel).
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) render_bwd_views_walk_kernel(
+    ViewsDev vd, const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
+    const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, SetDev st,
+    const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL,
+    const uint32_t* __restrict__ walk, const uint32_t* __restrict__ walk_count, long long walk_cap,
+    float* __restrict__ g2d, const uint32_t* __restrict__ order) {
+    pdl_wait_and_trigger();
+    constexpr int NW = TW * TH / 32;
+    __shared__ BwdWalkSmem<NW> sm;
+    const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    if ((unsigned)t >= (unsigned)vd.T_total) return;
+    const int v = view_of_tile(vd, t);
+    const CamDev& c = vd.cam[v];
+    const long long po = vd.pix_off[v];
+    bwd_tile_walk<TW, TH, false>(t - vd.tile_off[v], threadIdx.x >> 5, c.gx, c.width, c.height, ranges[t], gids, xy,
+                                 conic_opac, rgb, st, final_T + po, n_contrib + po, dL + 3 * po, walk,
+                                 walk_count + (long long)vd.tile_off[v] * NW, walk_cap, g2d, nullptr, sm);
 }
 
 template <int TW, int TH, int BATCH>
@@ -946,12 +973,13 @@ template <int TW, int TH, int BATCH>
 static cudaError_t fwd_views_tmpl(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                   const uint32_t* gids, const SetDev& st, float* images, float* final_T,
                                   uint32_t* n_contrib, uint32_t* counter, const uint32_t* order,
-                                  cudaStream_t stream) {
-    auto k = render_fwd_views_kernel<TW, TH, BATCH>;
+                                  const WalkLists& wl, cudaStream_t stream) {
+    auto k = wl.walk ? render_fwd_views_kernel<TW, TH, BATCH, true> : render_fwd_views_kernel<TW, TH, BATCH, false>;
     const int grid = persistent_grid(k, TW * TH, vd.T_total);
+    const WalkOut wo{wl.walk, wl.count, wl.cap};
     (void)launch_pdl(k, dim3(grid), dim3(TW * TH), 0, stream, vd, reinterpret_cast<const uint2*>(ranges), gids,
                      reinterpret_cast<const float4*>(proj.xy), reinterpret_cast<const float4*>(proj.conic_opac),
-                     reinterpret_cast<const float4*>(proj.rgb), st, images, final_T, n_contrib, counter, order);
+                     reinterpret_cast<const float4*>(proj.rgb), st, images, final_T, n_contrib, counter, order, wo);
     note_launch();
     return cudaGetLastError();
 }
@@ -960,7 +988,16 @@ template <int TW, int TH, int BATCH>
 static cudaError_t bwd_views_tmpl(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                   const uint32_t* gids, const SetDev& st, const float* final_T,
                                   const uint32_t* n_contrib, const float* dL, float* g2d, uint32_t* counter,
-                                  const uint32_t* order, cudaStream_t stream) {
+                                  const uint32_t* order, const WalkLists& wl, cudaStream_t stream) {
+    if (wl.walk) {
+        auto k = render_bwd_views_walk_kernel<TW, TH>;
+        (void)launch_pdl(k, dim3(vd.T_total > 0 ? vd.T_total : 1), dim3(TW * TH), 0, stream, vd,
+                         reinterpret_cast<const uint2*>(ranges), gids, reinterpret_cast<const float4*>(proj.xy),
+                         reinterpret_cast<const float4*>(proj.conic_opac), reinterpret_cast<const float4*>(proj.rgb),
+                         st, final_T, n_contrib, dL, wl.walk, wl.count, wl.cap, g2d, order);
+        note_launch();
+        return cudaGetLastError();
+    }
     auto k = render_bwd_views_kernel<TW, TH, BATCH>;
     const int grid = persistent_grid(k, TW * TH, vd.T_total);
     (void)launch_pdl(k, dim3(grid), dim3(TW * TH), 0, stream, vd, reinterpret_cast<const uint2*>(ranges), gids,
@@ -998,15 +1035,16 @@ static cudaError_t bwd_views_tmpl(const ViewsDev& vd, const sgs_proj& proj, cons
 cudaError_t launch_render_fwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                     const uint32_t* gids, const SetDev& st, int batch, float* images,
                                     float* final_T, uint32_t* n_contrib, uint32_t* counter, const uint32_t* order,
-                                    cudaStream_t stream) {
-    SGS_VIEWS_DISPATCH(fwd_views_tmpl, vd, proj, ranges, gids, st, images, final_T, n_contrib, counter, order, stream)
+                                    const WalkLists& wl, cudaStream_t stream) {
+    SGS_VIEWS_DISPATCH(fwd_views_tmpl, vd, proj, ranges, gids, st, images, final_T, n_contrib, counter, order, wl,
+                       stream)
 }
 
 cudaError_t launch_render_bwd_views(const ViewsDev& vd, const sgs_proj& proj, const uint32_t* ranges,
                                     const uint32_t* gids, const SetDev& st, int batch, const float* final_T,
                                     const uint32_t* n_contrib, const float* dL, float* g2d, uint32_t* counter,
-                                    const uint32_t* order, cudaStream_t stream) {
-    SGS_VIEWS_DISPATCH(bwd_views_tmpl, vd, proj, ranges, gids, st, final_T, n_contrib, dL, g2d, counter, order,
+                                    const uint32_t* order, const WalkLists& wl, cudaStream_t stream) {
+    SGS_VIEWS_DISPATCH(bwd_views_tmpl, vd, proj, ranges, gids, st, final_T, n_contrib, dL, g2d, counter, order, wl,
                        stream)
 }
 
