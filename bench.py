@@ -53,22 +53,32 @@ def _peaks():
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
-# DRAM traffic of one render_bwd_kernel<16,16> launch on this workload, from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
-# rasteriser source it was taken from (first 16 hex digits of its SHA-256).
-RENDER_BWD_TRAFFIC = {"bytes": 103_380_480 + 9_347_072, "render_cu_sha256": "84602c17738c286d",
+# DRAM traffic of one render_bwd_with_splitting call on this workload (its three
+# launches: zero_reached_rows_kernel, render_bwd_walk_kernel<16,16,0> and
+# project_bwd_kernel<3,0,0,0>), dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture, valid only for the sources it was taken from (first 16 hex
+# digits of the SHA-256 of render.cu, project.cu and api.cu, concatenated).
+RENDER_BWD_TRAFFIC = {"bytes": (4_012_288 + 182_016) + (121_667_584 + 10_877_184) + (173_860_352 + 209_018_624),
+                      "sources_sha256": "db0e2d3ab059b8e4",
                       "profile": "profiles/render_bwd_scene_1M_1237x822.md"}
+TRAFFIC_SOURCES = ("render.cu", "project.cu", "api.cu")
+
+
+def _sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2505_05587_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _render_bwd_traffic():
-    import hashlib
-    path = os.path.join(ROOT, "paper_2505_05587_gb300", "csrc", "render.cu")
     try:
-        with open(path, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        sha = _sources_sha()
     except OSError:
         return None
-    return RENDER_BWD_TRAFFIC["bytes"] if sha == RENDER_BWD_TRAFFIC["render_cu_sha256"] else None
+    return RENDER_BWD_TRAFFIC["bytes"] if sha == RENDER_BWD_TRAFFIC["sources_sha256"] else None
 
 
 class ClockSampler:
@@ -368,7 +378,7 @@ def run_gpu(args):
                 "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
                 "traffic": args.traffic if args.traffic is not None else (
                     _render_bwd_traffic() if names[dom] == "render_bwd_with_splitting" else None),
-                "traffic_unit": "bytes per render_bwd_kernel launch (ncu)",
+                "traffic_unit": "DRAM bytes per render_bwd_with_splitting call (ncu: its three launches)",
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                 "peak_check": {"fma_probe_tflops": round(fma_tflops, 2),
                                "what": "sgs_fma_probe: 1216 blocks x 256 threads x 8 independent FMA chains"},

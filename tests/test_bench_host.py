@@ -37,14 +37,16 @@ def test_clock_summary_without_samples():
     assert c["sm_mhz"] is None and c["samples"] == 0 and c["reasons"] == []
 
 
-def test_traffic_figure_only_for_the_profiled_source():
-    """The ncu DRAM traffic is reported only while the rasteriser source is
-    the one it was captured from (first 16 hex digits of its SHA-256)."""
-    path = os.path.join(bench.ROOT, "paper_2505_05587_gb300", "csrc", "render.cu")
-    with open(path, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+def test_traffic_figure_only_for_the_profiled_sources():
+    """The ncu DRAM traffic of the backward call is reported only while the
+    sources of its three kernels and their launcher are the ones it was
+    captured from (first 16 hex digits of their concatenated SHA-256)."""
+    h = hashlib.sha256()
+    for name in ("render.cu", "project.cu", "api.cu"):
+        with open(os.path.join(bench.ROOT, "paper_2505_05587_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     got = bench._render_bwd_traffic()
-    if sha == bench.RENDER_BWD_TRAFFIC["render_cu_sha256"]:
+    if h.hexdigest()[:16] == bench.RENDER_BWD_TRAFFIC["sources_sha256"]:
         assert got == bench.RENDER_BWD_TRAFFIC["bytes"]
     else:
         assert got is None
