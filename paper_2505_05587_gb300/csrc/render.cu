@@ -62,26 +62,67 @@ __device__ __forceinline__ void warp_block_origin(int tile, int gx, int TH_, int
     *by = (tile / gx) * TH_ + (warp / (TW / 8)) * 4;
 }
 
-// Axis-aligned box of the region where alpha = o G can reach alpha_min:
-// d^T Q d <= 2 ln(o / alpha_min) (widened by a small safety margin, so the box
-// is conservative against float rounding).  Empty when o < alpha_min; the
-// whole plane when alpha_min = 0.
-__device__ __forceinline__ float4 alpha_support_box(float4 m, float4 co, float alpha_min) {
+// Per column strip of a tile (the 8 pixel-centre columns of one column of
+// warp blocks, NS = TW / 8 strips), the rows where alpha = o G can reach
+// alpha_min.  That region is the ellipse d^T Q d <= M, M = 2 ln(o /
+// alpha_min); its part inside a strip is convex, so its rows form one
+// interval and a warp's 8x4 block meets the region iff the block's rows meet
+// its strip's interval (an exact test, where an axis-aligned box of the whole
+// ellipse also passes blocks in the box's empty corners).  On the ellipse's
+// boundary at column offset u, dy = (-b u +- sqrt(c M - det u^2)) / c; the
+// upper branch (concave) peaks at the ellipse's top, u_t = -b e_y / a with
+// e_y = sqrt(M a / det), the lower branch (convex) bottoms out at -u_t, so
+// the interval's ends are the branches at u_t and -u_t clamped into the
+// strip.  Conservative against float32 rounding, including that of the
+// compositing kernels' own evaluation of d^T Q d at a pixel (cancellation
+// there is at most about 16 eps (a + c)^2 / det of M near the boundary): M
+// is widened by that term and 1e-3 relative, the strips and intervals by
+// 0.01 pixel, and det = ac - b^2 is taken with the rounding error of b^2
+// compensated.  Empty intervals when o < alpha_min; whole columns when
+// alpha_min = 0 or the conic is not positive definite.  yr[s * stride] gets
+// strip s's interval (lo, hi) in view rows.
+template <int NS>
+__device__ __forceinline__ void alpha_support_strips(float4 m, float4 co, float alpha_min, float ox, float2* yr,
+                                                     int stride) {
     const float o = co.w;
-    if (!(o >= alpha_min)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);
-    if (!(alpha_min > 0.0f)) return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);
-    const float m2 = 2.0f * logf(o / alpha_min) * 1.001f + 1e-3f;
-    const float det = co.x * co.z - co.y * co.y;
-    const float ex = sqrtf(m2 * co.z / det) + 0.01f;
-    const float ey = sqrtf(m2 * co.x / det) + 0.01f;
+    const float a = co.x, b = co.y, c = co.z;
+    const float bb = b * b;
+    const float det = __fmaf_rn(a, c, -bb) - __fmaf_rn(b, b, -bb);
+    if (!(o >= alpha_min)) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) yr[s * stride] = make_float2(1e30f, -1e30f);
+        return;
+    }
+    if (!(alpha_min > 0.0f) || !(det > 0.0f) || !(a > 0.0f) || !(c > 0.0f)) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) yr[s * stride] = make_float2(-1e30f, 1e30f);
+        return;
+    }
+    const float sa = a + c;
+    const float M = 2.0f * logf(o / alpha_min) * (1.001f + 1e-6f * (sa * sa / det)) + 1e-3f;
+    const float cM = c * M, ic = 1.0f / c;
+    const float ex = sqrtf(cM / det);
+    const float ut = -b * sqrtf(M * a / det) / a;
     const float cx = m.x + m.z, cy = m.y + m.w;
-    return make_float4(cx - ex, cx + ex, cy - ey, cy + ey);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const float xa = (ox + (float)(8 * s)) - cx - 0.01f, xb = xa + 7.02f;
+        float2 r = make_float2(1e30f, -1e30f);
+        if (xb >= -ex && xa <= ex) {
+            const float u = fminf(fmaxf(ut, xa), xb);
+            const float v = fminf(fmaxf(-ut, xa), xb);
+            const float hi = (sqrtf(fmaxf(0.0f, cM - det * u * u)) - b * u) * ic;
+            const float lo = (-sqrtf(fmaxf(0.0f, cM - det * v * v)) - b * v) * ic;
+            r = make_float2(cy + lo - 0.01f, cy + hi + 0.01f);
+        }
+        yr[s * stride] = r;
+    }
 }
 
-// Order-preserving list of the batch entries [0, cnt) whose support box meets
-// the warp's pixel block [bx, bx+7] x [by, by+3].  Returns the list length.
-__device__ __forceinline__ int build_warp_list(const float4* s_box, int cnt, float bx, float by,
-                                               uint8_t* list) {
+// Order-preserving list of the batch entries [0, cnt) whose support meets the
+// warp's pixel rows [by, by+3] within its strip (s_yr: the strip's intervals).
+// Returns the list length.
+__device__ __forceinline__ int build_warp_list(const float2* s_yr, int cnt, float by, uint8_t* list) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     int nl = 0;
@@ -89,8 +130,8 @@ __device__ __forceinline__ int build_warp_list(const float4* s_box, int cnt, flo
         const int e = c + lane;
         bool hit = false;
         if (e < cnt) {
-            const float4 b = s_box[e];
-            hit = b.y >= bx && b.x <= bx + 7.0f && b.w >= by && b.z <= by + 3.0f;
+            const float2 r = s_yr[e];
+            hit = r.y >= by && r.x <= by + 3.0f;
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) list[nl + __popc(m & lt)] = (uint8_t)e;
@@ -101,12 +142,12 @@ __device__ __forceinline__ int build_warp_list(const float4* s_box, int cnt, flo
 }
 
 
-template <int BATCH, int NW>
+template <int BATCH, int NW, int NS>
 struct FwdSmem {
     float2 xy[BATCH];      // mean relative to the tile origin
     float4 co[BATCH];
     float4 rgb[BATCH];
-    float4 box[BATCH];
+    float2 yr[NS][BATCH];  // per column strip: rows of the alpha support
     uint8_t list[NW][BATCH];
     uint8_t hit[NW][BATCH];  // walk recording: list slot composited by some pixel of the warp
     float l1_part[NW];
@@ -134,13 +175,13 @@ constexpr int kRedStride = 36;
 // from the two lane halves at once) and the 16-byte row reads conflict-free.
 constexpr int kHalfStride = 20;
 
-template <int BATCH, int NW>
+template <int BATCH, int NW, int NS>
 struct BwdSmem {
     uint32_t gid[BATCH];
     float2 xy[BATCH];      // mean relative to the tile origin
     float4 co[BATCH];
     float4 rgb[BATCH];
-    float4 box[BATCH];
+    float2 yr[NS][BATCH];  // per column strip: rows of the alpha support
     uint8_t list[NW][BATCH];
     uint32_t maxl;
     alignas(16) float red[NW][kRedRows * kRedStride];
@@ -163,7 +204,7 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
                                          const float4* __restrict__ xy, const float4* __restrict__ conic_opac,
                                          const float4* __restrict__ rgb, const SetDev& st, float* __restrict__ image,
                                          float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
-                                         FwdSmem<BATCH, TW * TH / 32>& sm, const L1Out* l1 = nullptr,
+                                         FwdSmem<BATCH, TW * TH / 32, TW / 8>& sm, const L1Out* l1 = nullptr,
                                          WalkOut wo = WalkOut{nullptr, nullptr, 0}) {
     constexpr int NW = TW * TH / 32;
     constexpr int BS = TW * TH;
@@ -200,11 +241,11 @@ __device__ __forceinline__ void fwd_tile(int tile, int gx, int W, int H, uint2 r
             sm.xy[k] = make_float2((m.x - (float)ox) + m.z, (m.y - (float)oy) + m.w);
             sm.co[k] = conic_exp2(co);
             sm.rgb[k] = rgb[g];
-            sm.box[k] = alpha_support_box(m, co, st.alpha_min);
+            alpha_support_strips<TW / 8>(m, co, st.alpha_min, (float)ox, &sm.yr[0][k], BATCH);
         }
         __syncthreads();
         if (__all_sync(0xffffffffu, done)) continue;
-        const int nl = build_warp_list(sm.box, cnt, (float)bx, (float)by, sm.list[warp]);
+        const int nl = build_warp_list(sm.yr[warp % (TW / 8)], cnt, (float)by, sm.list[warp]);
         for (int k = 0; k < nl && !done; ++k) {
             const int j = sm.list[warp][k];
             const float2 m = sm.xy[j];
@@ -327,7 +368,7 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
                                          const float4* __restrict__ rgb, const SetDev& st,
                                          const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib,
                                          const float* __restrict__ dL_dimage, float* __restrict__ g2d,
-                                         float* __restrict__ g2d_hi, BwdSmem<BATCH, TW * TH / 32>& sm) {
+                                         float* __restrict__ g2d_hi, BwdSmem<BATCH, TW * TH / 32, TW / 8>& sm) {
     constexpr int BS = TW * TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int bx, by;
@@ -388,11 +429,11 @@ __device__ __forceinline__ void bwd_tile(int tile, int gx, int W, int H, uint2 r
             sm.xy[k] = make_float2((m.x - (float)ox) + m.z, (m.y - (float)oy) + m.w);
             sm.co[k] = conic_exp2(co);
             sm.rgb[k] = rgb[g];
-            sm.box[k] = alpha_support_box(m, co, st.alpha_min);
+            alpha_support_strips<TW / 8>(m, co, st.alpha_min, (float)ox, &sm.yr[0][k], BATCH);
         }
         __syncthreads();
         const int wcnt = min(cnt, warp_last - start);    // this warp's entries end at its last contributor
-        const int nl = wcnt > 0 ? build_warp_list(sm.box, wcnt, (float)bx, (float)by, sm.list[warp]) : 0;
+        const int nl = wcnt > 0 ? build_warp_list(sm.yr[warp % (TW / 8)], wcnt, (float)by, sm.list[warp]) : 0;
         for (int k = nl - 1; k >= 0; --k) {
             const int e = sm.list[warp][k];
             const float2 m = sm.xy[e];
@@ -673,7 +714,7 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) render_fwd_kernel(
     float* __restrict__ image, float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
     const uint32_t* __restrict__ order, L1Out l1, WalkOut wo) {
     pdl_wait_and_trigger();
-    __shared__ FwdSmem<TW * TH, TW * TH / 32> sm;
+    __shared__ FwdSmem<TW * TH, TW * TH / 32, TW / 8> sm;
     const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     if ((unsigned)t >= gridDim.x) return;      // a schedule that is not a permutation of the tiles
     fwd_tile<TW, TH, TW * TH, REC>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, image, final_T, n_contrib,
@@ -690,7 +731,7 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_kernel(
     const float* __restrict__ dL_dimage, float* __restrict__ g2d, float* __restrict__ g2d_hi,
     const uint32_t* __restrict__ order) {
     pdl_wait_and_trigger();
-    __shared__ BwdSmem<TW * TH, TW * TH / 32> sm;
+    __shared__ BwdSmem<TW * TH, TW * TH / 32, TW / 8> sm;
     const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     if ((unsigned)t >= gridDim.x) return;      // a schedule that is not a permutation of the tiles
     bwd_tile<TW, TH, TW * TH, HI>(t, gx, W, H, ranges[t], gids, xy, conic_opac, rgb, st, final_T, n_contrib,
@@ -728,7 +769,7 @@ __global__ void __launch_bounds__(TW * TH) render_fwd_views_kernel(
     const uint32_t* __restrict__ order, WalkOut wo) {
     pdl_wait_and_trigger();
     constexpr int NW = TW * TH / 32;
-    __shared__ FwdSmem<BATCH, NW> sm;
+    __shared__ FwdSmem<BATCH, NW, TW / 8> sm;
     __shared__ int s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
@@ -779,7 +820,7 @@ __global__ void __launch_bounds__(TW * TH, 1280 / (TW * TH)) render_bwd_views_ke
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ dL,
     float* __restrict__ g2d, uint32_t* __restrict__ counter, const uint32_t* __restrict__ order) {
     pdl_wait_and_trigger();
-    __shared__ BwdSmem<BATCH, TW * TH / 32> sm;
+    __shared__ BwdSmem<BATCH, TW * TH / 32, TW / 8> sm;
     __shared__ int s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
