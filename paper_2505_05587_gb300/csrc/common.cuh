@@ -217,6 +217,11 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
 size_t scan_tmp_bytes(int64_t n_max);
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* d_total,
                                   int64_t n_max, const int32_t* d_n, void* tmp, cudaStream_t stream);
+// The same scan of n values whose producer already wrote the sum of every
+// 256-value block (bcount[b] = sum of in[256 b, 256 b + 256)), so that no
+// reduction pass over `in` is needed.
+cudaError_t launch_exclusive_scan_counted(const uint32_t* in, uint32_t* out, uint32_t* d_total, int64_t n,
+                                          const uint32_t* bcount, void* tmp, cudaStream_t stream);
 
 constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

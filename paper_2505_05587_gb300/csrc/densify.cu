@@ -342,11 +342,12 @@ __device__ __forceinline__ void load_theta(const float* __restrict__ S, const fl
     }
 }
 
-__device__ __forceinline__ void write_flag(int i, float lam, float eps_split, const float* __restrict__ grad_norm,
+__device__ __forceinline__ bool write_flag(int i, float lam, float eps_split, const float* __restrict__ grad_norm,
                                            float eps_grad, uint32_t* __restrict__ flags) {
     bool f = lam < eps_split;
     if (grad_norm) f = f && (grad_norm[i] <= eps_grad);
     flags[i] = f ? 1u : 0u;
+    return f;
 }
 
 // The splitting matrix of a Gaussian that no pixel reached is zero, and its
@@ -410,11 +411,13 @@ __global__ void __launch_bounds__(256) eig_triage_kernel(const float* __restrict
 // formula).  A zero matrix (a Gaussian no pixel reached) gets (0, e_0), what
 // the formula returns for it; the block's non-zero matrices are first packed
 // into its leading threads through shared memory, so that the solve runs in
-// full warps.
+// full warps.  bcount[block] = the block's number of flags (the sums the
+// compaction's scan starts from).
 __global__ void __launch_bounds__(256) eig_direct_kernel(const float* __restrict__ S, int n, float inv_T,
                                                          float eps_split, const float* __restrict__ grad_norm,
                                                          float eps_grad, float* __restrict__ lam_out,
-                                                         float* __restrict__ v_out, uint32_t* __restrict__ flags) {
+                                                         float* __restrict__ v_out, uint32_t* __restrict__ flags,
+                                                         uint32_t* __restrict__ bcount) {
     pdl_wait_and_trigger();
     __shared__ float s_m[256][7];                     // packed matrices (6 floats, padded)
     __shared__ int s_idx[256];
@@ -422,7 +425,7 @@ __global__ void __launch_bounds__(256) eig_direct_kernel(const float* __restrict
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float s6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bool nz = false;
+    bool nz = false, f0 = false, f1 = false;
     if (i < n) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(256) eig_direct_kernel(const float* __restrict
             v_out[3 * (size_t)i] = 1.0f;
             v_out[3 * (size_t)i + 1] = 0.0f;
             v_out[3 * (size_t)i + 2] = 0.0f;
-            write_flag(i, 0.0f, eps_split, grad_norm, eps_grad, flags);
+            f0 = write_flag(i, 0.0f, eps_split, grad_norm, eps_grad, flags);
         }
     }
     const unsigned m = __ballot_sync(0xffffffffu, nz);
@@ -463,8 +466,10 @@ __global__ void __launch_bounds__(256) eig_direct_kernel(const float* __restrict
         lam_out[j] = e.lam;
 #pragma unroll
         for (int k = 0; k < 3; ++k) v_out[3 * (size_t)j + k] = e.v[k];
-        write_flag(j, e.lam, eps_split, grad_norm, eps_grad, flags);
+        f1 = write_flag(j, e.lam, eps_split, grad_norm, eps_grad, flags);
     }
+    const int c = __syncthreads_count(f0) + __syncthreads_count(f1);
+    if (bcount && threadIdx.x == 0) bcount[blockIdx.x] = (uint32_t)c;
 }
 
 // Minimum eigenpair and flag of the listed (non-zero) matrices.
@@ -570,11 +575,6 @@ __global__ void select_apply_kernel(const float* __restrict__ lam, uint32_t* __r
     flags[i] = (k < st->prefix || (k == st->prefix && tie_rank[i] < st->k_rem)) ? 1u : 0u;
 }
 
-__global__ void n_out_kernel(const uint32_t* __restrict__ total, int n, int32_t* __restrict__ d_n_out) {
-    pdl_wait_and_trigger();
-    *d_n_out = n + (int32_t)(*total);
-}
-
 // logit(sigmoid(x) / 2) = -log(1 + 2 exp(-x)), evaluated without overflow.
 __device__ __forceinline__ float half_opacity_logit(float x) {
     return x > 0.0f ? -log1pf(2.0f * expf(-x)) : x - logf(expf(x) + 2.0f);
@@ -588,14 +588,12 @@ __device__ __forceinline__ float half_opacity_logit(float x) {
 // clamped to [1e-4, 1 - 1e-4]; DIM = 7 also moves the log-scales by
 // +- eps v_l.
 template <int DIM>
-__global__ void __launch_bounds__(256) split_fields_kernel(
-    const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
+__device__ __forceinline__ void split_fields(
+    int i, const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logit, int n, const float* __restrict__ v, const uint32_t* __restrict__ flags,
     const uint32_t* __restrict__ excl, float step_scale, int64_t cap, float* __restrict__ o_means,
     float* __restrict__ o_ls, float* __restrict__ o_quats, float* __restrict__ o_logit,
     int32_t* __restrict__ parent) {
-    pdl_wait_and_trigger();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const bool f = flags[i] != 0u;
     const float l0 = log_scales[3 * i], l1 = log_scales[3 * i + 1], l2 = log_scales[3 * i + 2];
@@ -638,15 +636,12 @@ __global__ void __launch_bounds__(256) split_fields_kernel(
 // VEC floats): reads and the writes of row i are coalesced, and the second
 // offspring of consecutive flagged Gaussians land in consecutive rows.
 template <int VEC>
-__global__ void __launch_bounds__(256) split_sh_kernel(const float* __restrict__ sh, int n, int U,
-                                                       const uint32_t* __restrict__ flags,
-                                                       const uint32_t* __restrict__ excl, int64_t cap,
-                                                       float* __restrict__ o_sh) {
-    pdl_wait_and_trigger();
+__device__ __forceinline__ void split_sh(int64_t first, int64_t stride, const float* __restrict__ sh, int n, int U,
+                                         const uint32_t* __restrict__ flags, const uint32_t* __restrict__ excl,
+                                         int64_t cap, float* __restrict__ o_sh) {
     using V = typename std::conditional<VEC == 4, float4, float>::type;
     const int64_t total = (int64_t)n * U;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = first; t < total; t += stride) {
         const int64_t i = t / U;
         const int u = (int)(t - i * U);
         const V val = reinterpret_cast<const V*>(sh)[t];
@@ -655,6 +650,29 @@ __global__ void __launch_bounds__(256) split_sh_kernel(const float* __restrict__
             const int64_t row = (int64_t)n + (int64_t)excl[i];
             if (row < cap) reinterpret_cast<V*>(o_sh)[row * U + u] = val;
         }
+    }
+}
+
+// The split in one launch: blocks [0, nbf) write the per-Gaussian fields (one
+// thread per Gaussian; the first also writes n_out = n + number flagged), the
+// other blocks copy the SH rows (grid-stride over the vector units), so the
+// two streams of rows run side by side.
+template <int DIM, int VEC>
+__global__ void __launch_bounds__(256) split_kernel(
+    const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
+    const float* __restrict__ logit, const float* __restrict__ sh, int n, int U, int nbf,
+    const float* __restrict__ v, const uint32_t* __restrict__ flags, const uint32_t* __restrict__ excl,
+    const uint32_t* __restrict__ total, float step_scale, int64_t cap, float* __restrict__ o_means,
+    float* __restrict__ o_ls, float* __restrict__ o_quats, float* __restrict__ o_logit, float* __restrict__ o_sh,
+    int32_t* __restrict__ parent, int32_t* __restrict__ d_n_out) {
+    pdl_wait_and_trigger();
+    if ((int)blockIdx.x < nbf) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *d_n_out = n + (int32_t)(*total);
+        split_fields<DIM>((int)blockIdx.x * 256 + (int)threadIdx.x, means, log_scales, quats, logit, n, v, flags,
+                          excl, step_scale, cap, o_means, o_ls, o_quats, o_logit, parent);
+    } else {
+        split_sh<VEC>((int64_t)(blockIdx.x - nbf) * 256 + threadIdx.x, (int64_t)(gridDim.x - nbf) * 256, sh, n, U,
+                      flags, excl, cap, o_sh);
     }
 }
 
@@ -714,12 +732,15 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
             run(std::integral_constant<int, 4>{});
             note_launch(2);
         } else {                                     // the root formula: short enough to run unsorted
+            // its per-block flag counts go to `tie` (free until the budget's
+            // tie ranks) and spare the scan its reduction pass
             (void)launch_pdl(eig_direct_kernel, dim3(nb), dim3(256), 0, stream, S, n, inv_T, eps_split, grad_norm,
-                             eps_grad, lam, v, flags);
+                             eps_grad, lam, v, flags, tie);
             note_launch();
         }
     }
-    cudaError_t e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
+    cudaError_t e = S_po ? launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream)
+                         : launch_exclusive_scan_counted(flags, excl, total, n, tie, scan_tmp, stream);
     if (e != cudaSuccess) return e;
     if (max_splits > 0) {
         (void)launch_pdl(select_init_kernel, dim3(1), dim3(256), 0, stream, total, max_splits, sel);
@@ -740,25 +761,20 @@ cudaError_t launch_densify(const sgs_gaussians& in, const float* S, const float*
         e = launch_exclusive_scan(flags, excl, total, n, nullptr, scan_tmp, stream);
         if (e != cudaSuccess) return e;
     }
-    (void)launch_pdl(n_out_kernel, dim3(1), dim3(1), 0, stream, total, n, d_n_out);
-    note_launch();
     const int K3 = (in.sh_degree + 1) * (in.sh_degree + 1) * 3;
-    auto fields = S_po ? (S_ls ? split_fields_kernel<7> : split_fields_kernel<4>) : split_fields_kernel<3>;
-    (void)launch_pdl(fields, dim3(nb), dim3(256), 0, stream, in.means, in.log_scales, in.quats, in.opacity_logit, n,
-                     v, flags, excl, step_scale, capacity, out.means, out.log_scales, out.quats, out.opacity_logit,
-                     parent);
-    note_launch();
     const bool vec4 = K3 % 4 == 0 && (reinterpret_cast<uintptr_t>(in.sh) % 16) == 0 &&
                       (reinterpret_cast<uintptr_t>(out.sh) % 16) == 0;
     const int U = vec4 ? K3 / 4 : K3;
     const int64_t units = (int64_t)n * U;
     const int sb = (int)std::min<int64_t>((units + 255) / 256, 152 * 16);
-    if (vec4)
-        (void)launch_pdl(split_sh_kernel<4>, dim3(sb), dim3(256), 0, stream, in.sh, n, U, flags, excl, capacity,
-                         out.sh);
-    else
-        (void)launch_pdl(split_sh_kernel<1>, dim3(sb), dim3(256), 0, stream, in.sh, n, U, flags, excl, capacity,
-                         out.sh);
+    auto pick = [&](auto vec) {
+        constexpr int VEC = decltype(vec)::value;
+        return S_po ? (S_ls ? split_kernel<7, VEC> : split_kernel<4, VEC>) : split_kernel<3, VEC>;
+    };
+    auto kern = vec4 ? pick(std::integral_constant<int, 4>{}) : pick(std::integral_constant<int, 1>{});
+    (void)launch_pdl(kern, dim3(nb + sb), dim3(256), 0, stream, in.means, in.log_scales, in.quats,
+                     in.opacity_logit, in.sh, n, U, nb, v, flags, excl, total, step_scale, capacity, out.means,
+                     out.log_scales, out.quats, out.opacity_logit, out.sh, parent, d_n_out);
     note_launch();
     return cudaGetLastError();
 }

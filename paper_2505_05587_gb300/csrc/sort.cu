@@ -90,12 +90,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_partials_kernel(uint32_t* _
 
 __global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep_kernel(
     const uint32_t* __restrict__ in, uint32_t* __restrict__ out, const int32_t* d_n, int64_t n_max,
-    const uint32_t* __restrict__ partial) {
+    const uint32_t* __restrict__ partial, int64_t fixed_chunk) {
     pdl_wait_and_trigger();
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_carry;
     int64_t n = read_n(d_n, n_max, n_max);
-    int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    int64_t chunk = fixed_chunk > 0 ? fixed_chunk : (n + gridDim.x - 1) / gridDim.x;
     int64_t start = (int64_t)blockIdx.x * chunk, end = min(n, start + chunk);
     if (threadIdx.x == 0) s_carry = partial[blockIdx.x];
     __syncthreads();
@@ -129,7 +129,42 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* d
     note_launch();
     (void)launch_pdl(scan_partials_kernel, dim3(1), dim3(SCAN_THREADS), 0, stream, partial, nb, d_total);
     note_launch();
-    (void)launch_pdl(scan_downsweep_kernel, dim3(nb), dim3(SCAN_THREADS), 0, stream, in, out, d_n, n_max, partial);
+    (void)launch_pdl(scan_downsweep_kernel, dim3(nb), dim3(SCAN_THREADS), 0, stream, in, out, d_n, n_max, partial,
+                     (int64_t)0);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Chunk sums from the producer's 256-value block sums: chunk c covers blocks
+// [c per, (c + 1) per); exclusive prefixes over the chunks and the total.
+__global__ void __launch_bounds__(SCAN_THREADS) scan_partials_counted_kernel(
+    const uint32_t* __restrict__ bcount, int nbe, int per, uint32_t* __restrict__ partial, int nb,
+    uint32_t* __restrict__ d_total) {
+    pdl_wait_and_trigger();
+    __shared__ uint32_t s_warp[32];
+    uint32_t v = 0u;
+    if ((int)threadIdx.x < nb) {
+        const int b0 = (int)threadIdx.x * per, b1 = min(nbe, b0 + per);
+        for (int b = b0; b < b1; ++b) v += bcount[b];
+    }
+    const uint32_t inc = block_inclusive_scan(v, s_warp);
+    if ((int)threadIdx.x < nb) partial[threadIdx.x] = inc - v;
+    if (threadIdx.x == blockDim.x - 1 && d_total) *d_total = inc;
+}
+
+cudaError_t launch_exclusive_scan_counted(const uint32_t* in, uint32_t* out, uint32_t* d_total, int64_t n,
+                                          const uint32_t* bcount, void* tmp, cudaStream_t stream) {
+    const int64_t nbe = (n + 255) / 256;
+    const int nb_max = scan_blocks(n);          // chunks: at most the plain scan's, so tmp suffices
+    int64_t per = (nbe + nb_max - 1) / nb_max;
+    if (per < SCAN_TILE / 256) per = SCAN_TILE / 256;
+    const int nb = (int)((nbe + per - 1) / per);
+    uint32_t* partial = reinterpret_cast<uint32_t*>(tmp);
+    (void)launch_pdl(scan_partials_counted_kernel, dim3(1), dim3(SCAN_THREADS), 0, stream, bcount, (int)nbe,
+                     (int)per, partial, nb, d_total);
+    note_launch();
+    (void)launch_pdl(scan_downsweep_kernel, dim3(nb), dim3(SCAN_THREADS), 0, stream, in, out, nullptr, n, partial,
+                     per * 256);
     note_launch();
     return cudaGetLastError();
 }
@@ -143,10 +178,9 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t* d
 // b; one scan kernel turns each digit's row into exclusive prefixes over the
 // blocks and writes the digit totals; the scatter ranks each tile's items per
 // digit in item order (warp ballots + a cross-warp prefix) and writes item k of
-// digit d to  base[d] + prefix[d][b] + rank,  so the pass is stable.  The
-// scatter also counts the next pass's per-block histogram from the
-// destinations it writes (the next pass's chunk of a destination is known), so
-// every pass after the first needs no separate counting kernel.
+// digit d to  base[d] + prefix[d][b] + rank,  so the pass is stable.  Each
+// pass's per-block counts come from a counting kernel over its input (the
+// first tile pass's from the emission, which writes that input).
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
@@ -227,12 +261,24 @@ __global__ void __launch_bounds__(RS_THREADS) depth_hist_first_kernel(const floa
     const int64_t lo = (int64_t)blockIdx.x * C, hi = min(n_rows, lo + C);
     const int lane = threadIdx.x & 31;
     const uint32_t mask = (1u << ps.bits) - 1u;
-    for (int64_t base = lo; base < hi; base += RS_THREADS) {
-        const int64_t i = base + threadIdx.x;
-        const bool valid = i < hi && tiles_touched[i] != 0u;
-        const uint32_t d = valid ? ((__float_as_uint(depth[i]) >> ps.shift) & mask) : 0u;
-        const unsigned peers = digit_peers(d, valid, ps.bits);
-        if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+    // RS_ITEMS rows per thread loaded before any is counted (one memory
+    // round trip per RS_TILE rows instead of one per RS_THREADS)
+    for (int64_t base = lo; base < hi; base += RS_TILE) {
+        uint32_t t[RS_ITEMS], b[RS_ITEMS];
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            const int64_t i = base + it * RS_THREADS + threadIdx.x;
+            t[it] = i < hi ? tiles_touched[i] : 0u;
+            b[it] = i < hi ? __float_as_uint(depth[i]) : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            if (base + it * RS_THREADS >= hi) break;    // block-uniform
+            const bool valid = t[it] != 0u;
+            const uint32_t d = valid ? ((b[it] >> ps.shift) & mask) : 0u;
+            const unsigned peers = digit_peers(d, valid, ps.bits);
+            if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+        }
     }
     __syncthreads();
     for (int d = threadIdx.x; d < (1 << ps.bits); d += RS_THREADS) ps.hist[(size_t)d * ps.G + blockIdx.x] = s_h[d];
@@ -261,12 +307,21 @@ __global__ void __launch_bounds__(RS_THREADS) pass_hist_kernel(const uint32_t* _
     const int64_t C = chunk_of(n, ps.G);
     const int64_t lo = (int64_t)blockIdx.x * C, hi = min(n, lo + C);
     const uint32_t mask = (1u << ps.bits) - 1u;
-    for (int64_t base = lo; base < hi; base += RS_THREADS) {
-        const int64_t i = base + threadIdx.x;
-        const bool valid = i < hi;
-        const uint32_t d = valid ? ((keys[i] >> ps.shift) & mask) : 0u;
-        const unsigned peers = digit_peers(d, valid, ps.bits);
-        if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+    for (int64_t base = lo; base < hi; base += RS_TILE) {
+        uint32_t k[RS_ITEMS];
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            const int64_t i = base + it * RS_THREADS + threadIdx.x;
+            k[it] = i < hi ? keys[i] : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            if (base + it * RS_THREADS >= hi) break;    // block-uniform
+            const bool valid = base + it * RS_THREADS + threadIdx.x < hi;
+            const uint32_t d = valid ? ((k[it] >> ps.shift) & mask) : 0u;
+            const unsigned peers = digit_peers(d, valid, ps.bits);
+            if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+        }
     }
     __syncthreads();
     for (int d = threadIdx.x; d < (1 << ps.bits); d += RS_THREADS) ps.hist[(size_t)d * ps.G + blockIdx.x] = s_h[d];
