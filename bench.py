@@ -58,8 +58,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # project_bwd_kernel<3,0,0,0>), dram__bytes_read.sum + dram__bytes_write.sum from
 # one ncu capture, valid only for the sources it was taken from (first 16 hex
 # digits of the SHA-256 of render.cu, project.cu and api.cu, concatenated).
-RENDER_BWD_TRAFFIC = {"bytes": (4_012_288 + 182_016) + (121_667_584 + 10_877_184) + (173_860_352 + 209_018_624),
-                      "sources_sha256": "db0e2d3ab059b8e4",
+RENDER_BWD_TRAFFIC = {"bytes": (4_007_936 + 154_624) + (121_745_408 + 7_674_368) + (174_042_112 + 206_420_736),
+                      "sources_sha256": "febd8d816fdaf0fa",
                       "profile": "profiles/render_bwd_scene_1M_1237x822.md"}
 TRAFFIC_SOURCES = ("render.cu", "project.cu", "api.cu")
 
@@ -546,6 +546,50 @@ def cpu_baseline_full():
                               "sample": "the same full iteration on one thread"}}
 
 
+def oracle_workloads(n_requests: int = 20) -> dict:
+    """The float64 oracle, on all host threads, on the two other workloads:
+    the batched densification step (3M Gaussians, the 8 ring views rendered,
+    L1 over the views, the backward with the splitting matrices summed over
+    them, the eigenpairs and the split) once, and `n_requests` requests of
+    the serving stream (seed 3: scene, pose and resolution drawn as the GPU
+    run draws them) rendered one by one.  Timings only (nothing is compared):
+    the CPU baselines beside the GPU figures."""
+    import oracle
+    st = synth.Settings()
+    scene = synth.cluster_scene(0, 3_000_000, 3)
+    cams = synth.ring_cameras(6.0)
+    tgs = [synth.target_image(10 + k, c.height, c.width) for k, c in enumerate(cams)]
+    t0 = time.perf_counter()
+    acc = None
+    for cam, tgt in zip(cams, tgs):
+        r = oracle.render(scene, cam, st, all_cores=True)
+        _, g = oracle.l1_loss_grad(r["image"], tgt, n_views=len(cams))
+        acc = oracle.backward(scene, cam, st, g, acc=acc, all_cores=True, blocks=False)
+    lam, v = oracle.eig3_min(acc["S"])
+    oracle.split(scene, lam, v, EPS_SPLIT, 1.0)
+    t_batched = time.perf_counter() - t0
+    del scene, acc
+    sizes = (100_000, 300_000, 1_000_000, 1_000_000, 2_000_000, 3_000_000)
+    reqs = synth.request_stream(3, n_requests, 200.0, len(sizes))
+    used = sorted({r.scene for r in reqs})
+    scenes = {k: synth.cluster_scene(10 + k, sizes[k], 3) for k in used}
+    per = []
+    for r in reqs:
+        t0 = time.perf_counter()
+        oracle.render(scenes[r.scene], r.camera, st, all_cores=True)
+        per.append(time.perf_counter() - t0)
+    return {"kind": "oracle", "cores": oracle.threads(), "nproc": os.cpu_count(),
+            "batched_step": {"value": round(t_batched, 2), "unit": "s/step",
+                             "sample": "the whole step once: 3M Gaussians, 8 ring views (1957x1091, 1600x1060, "
+                                       "1237x822, 980x545 x2, 800x600 x3), render, L1, backward with splitting "
+                                       "matrices, eigenpairs, split (projection and binning serial)"},
+            "serving": {"value": round(1e3 * float(np.mean(per)), 1), "unit": "ms/frame",
+                        "requests": n_requests, "min_ms": round(1e3 * min(per), 1),
+                        "max_ms": round(1e3 * max(per), 1),
+                        "sample": f"the first {n_requests} requests of the serving stream (seed 3), each "
+                                  "rendered alone (forward only)"}}
+
+
 def run_reference(args):
     """Oracle arm, on all host cores: one full iteration measured, then each
     step runs the oracle's fused iteration on the full scene for a horizontal
@@ -615,11 +659,16 @@ def main():
     ap.add_argument("--no-walk", action="store_true",
                     help="no walk lists: the backward culls every list entry itself instead of following the "
                          "forward's per-warp lists of composited entries")
+    ap.add_argument("--oracle-workloads", action="store_true",
+                    help="time the float64 oracle (all host threads) on the batched step and on 20 serving requests, "
+                         "print one JSON line and exit (no GPU work)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
+    if args.oracle_workloads:
+        print(json.dumps({"oracle_workloads": oracle_workloads()}), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
