@@ -421,6 +421,8 @@ def run_gpu(args):
         result["batched"] = bench_batched(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_full()
+        if not (args.no_serving and args.no_batched):
+            result["cpu_baseline"]["workloads"] = oracle_workloads()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
