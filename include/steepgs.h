@@ -122,7 +122,10 @@ typedef struct sgs_settings {
  *   depth       [N]   camera-space z, float32 (the depth sort key).
  *   rect        [N,4] int16 (x_lo, y_lo, x_hi, y_hi), inclusive tile rect;
  *               (0,0,-1,-1) for a culled Gaussian.
- *   tiles_touched [N] number of tiles in rect (0 = culled). */
+ *   tiles_touched [N] number of tiles in rect (0 = culled).
+ * xy, conic_opac and rgb are written only for rows with tiles_touched > 0
+ * (the only rows an instance refers to); depth, rect and tiles_touched for
+ * every row. */
 typedef struct sgs_proj {
     float *xy;
     float *conic_opac;

@@ -421,7 +421,9 @@ int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* ca
         e = launch_render_fwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, images, w.final_T,
                                     w.n_contrib, w.counters, w.bins.order, w.wl, s);
     if (e == cudaSuccess) e = launch_l1_views(images, targets, vd, w.dL, loss, s);
-    if (e == cudaSuccess && rows > 0) e = cudaMemsetAsync(w.g2d, 0, 16 * sizeof(float) * rows, s);
+    // the backward adds into the accumulator rows of reached (view, Gaussian)
+    // pairs only, and the adjoint reads only those: clear just them
+    if (e == cudaSuccess) e = launch_zero_reached_rows(w.proj.tiles_touched, (int)rows, w.g2d, nullptr, s);
     if (e == cudaSuccess)
         e = launch_render_bwd_views(vd, w.proj, w.bins.ranges, w.bins.gids, sd, batch, w.final_T, w.n_contrib,
                                     w.dL, w.g2d, w.counters + 1, w.bins.order, w.wl, s);

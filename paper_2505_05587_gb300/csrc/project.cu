@@ -276,30 +276,20 @@ __device__ __forceinline__ void sh_weighted_grad(float x, float y, float z, cons
 // ---------------------------------------------------------------------------
 // Forward projection: one thread per Gaussian.
 // ---------------------------------------------------------------------------
-// One thread per projection row (view v, Gaussian i of view v's scene).
+// Projected state of Gaussian i in one view, written to projection row `row`.
 template <int DEG>
-__global__ void __launch_bounds__(256, 6) project_kernel(ScenesDev sc, ViewsDev vd, SetDev st,
-    float4* __restrict__ xy, float4* __restrict__ conic_opac, float4* __restrict__ rgb_out,
-    float* __restrict__ depth, short4* __restrict__ rect, uint32_t* __restrict__ tiles) {
-    pdl_wait_and_trigger();
-    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= vd.row_off[vd.nv]) return;
-    const int v = view_of_row(vd, row);
-    const int i = (int)(row - vd.row_off[v]);
-    const CamDev& cam = vd.cam[v];
-    const float* __restrict__ means = sc.means[v];
-    const float* __restrict__ log_scales = sc.log_scales[v];
-    const float* __restrict__ quats = sc.quats[v];
-    const float* __restrict__ opacity_logit = sc.opacity_logit[v];
-    const float* __restrict__ sh = sc.sh[v];
+__device__ __forceinline__ void project_one(const float* __restrict__ means, const float* __restrict__ log_scales,
+                                            const float* __restrict__ quats,
+                                            const float* __restrict__ opacity_logit, const float* __restrict__ sh,
+                                            int i, long long row, const CamDev& cam, const SetDev& st,
+                                            float4* __restrict__ xy, float4* __restrict__ conic_opac,
+                                            float4* __restrict__ rgb_out, float* __restrict__ depth,
+                                            short4* __restrict__ rect, uint32_t* __restrict__ tiles) {
     Stage s = integer_stage(means, log_scales, quats, i, cam, st);
     depth[row] = s.tz;
-    if (s.culled) {
+    if (s.culled) {              // no instance reads this row's mean, conic or colour
         tiles[row] = 0;
         rect[row] = make_short4(0, 0, -1, -1);
-        xy[row] = make_float4(0.f, 0.f, 0.f, 0.f);
-        conic_opac[row] = make_float4(0.f, 0.f, 0.f, 0.f);
-        rgb_out[row] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     tiles[row] = (uint32_t)((s.x_hi - s.x_lo + 1) * (s.y_hi - s.y_lo + 1));
@@ -335,17 +325,64 @@ __global__ void __launch_bounds__(256, 6) project_kernel(ScenesDev sc, ViewsDev 
     rgb_out[row] = make_float4(fmaxf(r, 0.0f), fmaxf(g, 0.0f), fmaxf(b, 0.0f), 0.0f);
 }
 
+// One thread per projection row (view v, Gaussian i of view v's scene).
+template <int DEG>
+__global__ void __launch_bounds__(256, 6) project_kernel(ScenesDev sc, ViewsDev vd, SetDev st,
+    float4* __restrict__ xy, float4* __restrict__ conic_opac, float4* __restrict__ rgb_out,
+    float* __restrict__ depth, short4* __restrict__ rect, uint32_t* __restrict__ tiles) {
+    pdl_wait_and_trigger();
+    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= vd.row_off[vd.nv]) return;
+    const int v = view_of_row(vd, row);
+    const int i = (int)(row - vd.row_off[v]);
+    project_one<DEG>(sc.means[v], sc.log_scales[v], sc.quats[v], sc.opacity_logit[v], sc.sh[v], i, row, vd.cam[v],
+                     st, xy, conic_opac, rgb_out, depth, rect, tiles);
+}
+
+// Views that share one scene of n Gaussians (rows v n + i): one thread per
+// Gaussian walks all the views, so that its parameters and SH row come from
+// DRAM once and from the caches for the other views (the per-row kernel
+// streams every view's rows, and the scene with them, one view after another).
+template <int DEG>
+__global__ void __launch_bounds__(256, 4) project_views_kernel(ScenesDev sc, ViewsDev vd, SetDev st, int n,
+    float4* __restrict__ xy, float4* __restrict__ conic_opac, float4* __restrict__ rgb_out,
+    float* __restrict__ depth, short4* __restrict__ rect, uint32_t* __restrict__ tiles) {
+    pdl_wait_and_trigger();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int v = 0; v < vd.nv; ++v)
+        project_one<DEG>(sc.means[0], sc.log_scales[0], sc.quats[0], sc.opacity_logit[0], sc.sh[0], i,
+                         (long long)v * n + i, vd.cam[v], st, xy, conic_opac, rgb_out, depth, rect, tiles);
+}
+
 cudaError_t launch_project(const ScenesDev& sc, int sh_degree, const ViewsDev& vd, const SetDev& st,
                            const sgs_proj& out, cudaStream_t stream) {
     const long long rows = vd.row_off[vd.nv];
     if (rows == 0) return cudaSuccess;
-    const int blocks = (int)((rows + 255) / 256);
-    auto kern = sh_degree == 0 ? project_kernel<0>
-              : sh_degree == 1 ? project_kernel<1>
-              : sh_degree == 2 ? project_kernel<2> : project_kernel<3>;
-    (void)launch_pdl(kern, dim3(blocks), dim3(256), 0, stream, sc, vd, st, reinterpret_cast<float4*>(out.xy),
-                     reinterpret_cast<float4*>(out.conic_opac), reinterpret_cast<float4*>(out.rgb), out.depth,
-                     reinterpret_cast<short4*>(out.rect), out.tiles_touched);
+    // several views of one scene with the same rows each: the per-Gaussian form
+    bool shared = vd.nv > 1;
+    const int n = vd.row_off[1] - vd.row_off[0];
+    for (int v = 1; v < vd.nv && shared; ++v)
+        shared = vd.row_off[v + 1] - vd.row_off[v] == n && sc.means[v] == sc.means[0] &&
+                 sc.log_scales[v] == sc.log_scales[0] && sc.quats[v] == sc.quats[0] &&
+                 sc.opacity_logit[v] == sc.opacity_logit[0] && sc.sh[v] == sc.sh[0];
+    if (shared) {
+        auto kern = sh_degree == 0 ? project_views_kernel<0>
+                  : sh_degree == 1 ? project_views_kernel<1>
+                  : sh_degree == 2 ? project_views_kernel<2> : project_views_kernel<3>;
+        (void)launch_pdl(kern, dim3((n + 255) / 256), dim3(256), 0, stream, sc, vd, st, n,
+                         reinterpret_cast<float4*>(out.xy), reinterpret_cast<float4*>(out.conic_opac),
+                         reinterpret_cast<float4*>(out.rgb), out.depth, reinterpret_cast<short4*>(out.rect),
+                         out.tiles_touched);
+    } else {
+        const int blocks = (int)((rows + 255) / 256);
+        auto kern = sh_degree == 0 ? project_kernel<0>
+                  : sh_degree == 1 ? project_kernel<1>
+                  : sh_degree == 2 ? project_kernel<2> : project_kernel<3>;
+        (void)launch_pdl(kern, dim3(blocks), dim3(256), 0, stream, sc, vd, st, reinterpret_cast<float4*>(out.xy),
+                         reinterpret_cast<float4*>(out.conic_opac), reinterpret_cast<float4*>(out.rgb), out.depth,
+                         reinterpret_cast<short4*>(out.rect), out.tiles_touched);
+    }
     note_launch();
     return cudaGetLastError();
 }

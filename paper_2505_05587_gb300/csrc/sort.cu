@@ -197,6 +197,8 @@ constexpr int EMIT_SUB = 1024;               // rows staged per emission round
 constexpr int EMIT_G_MAX = 4096;             // emission blocks (4 per thread of the offsets scan)
 constexpr int EMIT_ROWS_PER_BLOCK = 256;     // target rows per emission block (of all rows)
 constexpr int EMIT_SPAN = 8;                 // next-pass blocks gathered in shared memory per round
+constexpr int EMIT_STAGE = 2048;             // instances staged in shared memory per write-out
+constexpr int EMIT_DIRECT_MAX = 4 * EMIT_THREADS;   // rounds up to this many instances write directly
 static_assert(EMIT_THREADS == RS_RADIX_MAX, "emit sums one depth digit total per thread");
 static_assert(EMIT_SUB % EMIT_THREADS == 0, "emit rows per thread");
 
@@ -514,6 +516,7 @@ __global__ void __launch_bounds__(SORT_G_MAX) emit_offsets_kernel(unsigned long 
 // offset inside the row's rect, row-major), so consecutive threads write
 // consecutive positions.  At most `cap` instances are written; the first
 // tile pass's per-block histogram is counted from the written positions.
+template <bool STAGED>
 __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
     const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cnt, const short4* __restrict__ rect,
     const uint32_t* __restrict__ depth_tot, ViewsDev vd, int64_t cap, const unsigned long long* __restrict__ esum,
@@ -525,6 +528,8 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
     __shared__ short4 s_rect[EMIT_SUB];
     __shared__ uint32_t s_warp[EMIT_THREADS / 32];
     __shared__ uint32_t s_nh[RS_RADIX_MAX][EMIT_SPAN];
+    __shared__ uint32_t s_et[STAGED ? EMIT_STAGE : 1];   // a chunk's tile ids and rows, written out coalesced
+    __shared__ uint32_t s_eg[STAGED ? EMIT_STAGE : 1];
     __shared__ uint32_t s_nvis;
     // per-view row bounds, tile offsets and tile-grid widths in shared memory:
     // the rows of one round come from different views, and indexing the kernel
@@ -614,12 +619,13 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
         if (local_nh)
             for (int k = threadIdx.x; k < RS_RADIX_MAX * EMIT_SPAN; k += EMIT_THREADS) (&s_nh[0][0])[k] = 0u;
         __syncthreads();
-        // thread i emits the contiguous instances [i P, (i + 1) P) of the
-        // round: one search for its first row, then a walk along the rects
-        const uint32_t P = (total + EMIT_THREADS - 1) / EMIT_THREADS;
-        uint32_t k = threadIdx.x * P;
-        const uint32_t kend = min(total, k + P);
-        if (k < kend) {
+        // thread i emits the contiguous instances [i P, (i + 1) P) of a range
+        // of the round: one search for its first row, then a walk along the
+        // rects.  A round of few instances per thread writes them directly
+        // (neighbouring threads' runs are close together); a larger one goes
+        // in chunks of EMIT_STAGE through shared memory and the block writes
+        // each chunk out with coalesced stores.
+        auto walk = [&](uint32_t k, uint32_t kend, uint32_t c0, bool staged) {
             int a = 0, b = rows - 1;                 // last row j with s_off[j] <= k
             while (a < b) {
                 const int mid = (a + b + 1) >> 1;
@@ -635,6 +641,10 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
             uint32_t wdt = (uint32_t)(r.z - r.x + 1);
             int ty = r.y + (int)(off / wdt), tx = r.x + (int)(off % wdt);
             uint32_t row_end = a + 1 < rows ? s_off[a + 1] : total;
+            // next-pass block of the current position, advanced incrementally
+            // (positions grow by one per instance)
+            uint32_t nb = (uint32_t)(base + k) / C_next;
+            uint64_t nb_end = (uint64_t)(nb + 1) * C_next;
             for (; k < kend; ++k) {
                 while (k >= row_end) {               // next row (every visible row has instances)
                     ++a;
@@ -650,9 +660,17 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
                 const int64_t pos = base + k;
                 if (pos >= cap) break;
                 const uint32_t t = t0 + (uint32_t)(ty * gx + tx);
-                inst_tile[pos] = t;
-                inst_gid[pos] = g;
-                const uint32_t nb = (uint32_t)pos / C_next;
+                if (STAGED && staged) {
+                    s_et[k - c0] = t;
+                    s_eg[k - c0] = g;
+                } else {
+                    inst_tile[pos] = t;
+                    inst_gid[pos] = g;
+                }
+                if ((uint64_t)pos >= nb_end) {
+                    ++nb;
+                    nb_end += C_next;
+                }
                 if (local_nh)
                     atomicAdd(&s_nh[(t >> nh.shift) & nmask][nb - nb0], 1u);
                 else if (nh.bits > 0)
@@ -661,6 +679,27 @@ __global__ void __launch_bounds__(EMIT_THREADS) emit_kernel(
                     tx = r.x;
                     ++ty;
                 }
+            }
+        };
+        if (!STAGED || total <= EMIT_DIRECT_MAX) {
+            const uint32_t P = (total + EMIT_THREADS - 1) / EMIT_THREADS;
+            const uint32_t k = threadIdx.x * P;
+            if (k < total) walk(k, min(total, k + P), 0u, false);
+        } else {
+            for (uint32_t c0 = 0; c0 < total; c0 += EMIT_STAGE) {
+                const uint32_t cn = min((uint32_t)EMIT_STAGE, total - c0);
+                const uint32_t P = (cn + EMIT_THREADS - 1) / EMIT_THREADS;
+                const uint32_t k = c0 + threadIdx.x * P;
+                if (k < c0 + cn) walk(k, min(c0 + cn, k + P), c0, true);
+                __syncthreads();
+                for (uint32_t j = threadIdx.x; j < cn; j += EMIT_THREADS) {
+                    const int64_t pos = base + c0 + j;
+                    if (pos < cap) {
+                        inst_tile[pos] = s_et[j];
+                        inst_gid[pos] = s_eg[j];
+                    }
+                }
+                __syncthreads();
             }
         }
         __syncthreads();
@@ -937,7 +976,11 @@ cudaError_t launch_bin_sort(const sgs_proj& proj, const ViewsDev& vd, const SetD
             const PassDesc q = tile_pass(0);
             nh = NextHist{q.shift, q.bits, q.hist, q.G};
         }
-        (void)launch_pdl_if(pdl, emit_kernel, dim3(sg.G_emit), dim3(EMIT_THREADS), 0, stream, perm, w.cnt,
+        // blocks of many rows (the emission grid at its cap) stage their
+        // instances for coalesced writes; short blocks write directly
+        const bool staged = (int64_t)n > (int64_t)EMIT_G_MAX * EMIT_ROWS_PER_BLOCK;
+        (void)launch_pdl_if(pdl, staged ? emit_kernel<true> : emit_kernel<false>, dim3(sg.G_emit),
+                            dim3(EMIT_THREADS), 0, stream, perm, w.cnt,
                             reinterpret_cast<const short4*>(proj.rect), w.depth_tot, vd, out.capacity, w.esum,
                             sg.G_emit, out.count, gk[0], gv[0], nh);
         note_launch();
