@@ -180,7 +180,27 @@ def run_ring_densify(n: int = 3_000_000, steps: int = 20, warmup: int = 3, tune:
             "autotune": table}
 
 
+def run_eager_steps(steps: int = 3, n: int = 3_000_000, tile=(16, 16), batch: int = 128) -> dict:
+    """A few eager batched steps on the ring workload with a fixed tile shape
+    and batch depth (no tuning, no graph): the command a per-launch profile of
+    the batched step runs."""
+    import synth
+    scene = synth.cluster_scene(0, n, 3)
+    cams = synth.ring_cameras(6.0)
+    st = dataclasses.replace(synth.Settings(), tile_w=tile[0], tile_h=tile[1])
+    g = B.GaussianTensors.from_scene(scene)
+    del scene
+    tgs = [torch.as_tensor(synth.target_image(10 + k, c.height, c.width)).cuda() for k, c in enumerate(cams)]
+    step = BatchedDensifyStep(g, cams, concat_images(tgs), st, batch=batch)
+    M = step.fit_capacity()
+    ms = time_fn(step.run_eager, reps=steps, warmup=0)
+    return {"steps": steps, "instances_M": M, "ms_eager": round(ms, 4)}
+
+
 if __name__ == "__main__":
     import json
     import sys
-    print(json.dumps(run_ring_densify(int(sys.argv[1]) if len(sys.argv) > 1 else 3_000_000)))
+    if len(sys.argv) > 2 and sys.argv[1] == "--eager":
+        print(json.dumps(run_eager_steps(int(sys.argv[2]))))
+    else:
+        print(json.dumps(run_ring_densify(int(sys.argv[1]) if len(sys.argv) > 1 else 3_000_000)))
