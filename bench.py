@@ -58,8 +58,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # project_bwd_kernel<3,0,0,0>), dram__bytes_read.sum + dram__bytes_write.sum from
 # one ncu capture, valid only for the sources it was taken from (first 16 hex
 # digits of the SHA-256 of render.cu, project.cu and api.cu, concatenated).
-RENDER_BWD_TRAFFIC = {"bytes": (4_007_936 + 154_624) + (121_745_408 + 7_674_368) + (174_042_112 + 206_420_736),
-                      "sources_sha256": "febd8d816fdaf0fa",
+RENDER_BWD_TRAFFIC = {"bytes": (4_008_960 + 165_888) + (121_690_880 + 7_526_400) + (174_166_784 + 206_474_496),
+                      "sources_sha256": "35e49fbf61ce64bb",
                       "profile": "profiles/render_bwd_scene_1M_1237x822.md"}
 TRAFFIC_SOURCES = ("render.cu", "project.cu", "api.cu")
 
@@ -475,7 +475,7 @@ def bench_batched(local: int, steps: int = 20, warmup: int = 3) -> dict:
     """Batched densification step: 3M Gaussians, 8 ring views of uneven
     resolution, one persistent pass per step replayed as a CUDA graph, against
     the same step one view per launch sequence.  Tile 16x16 and staging batch
-    128, the autotuner's choice on this workload (python -m
+    256, the autotuner's choice on this workload (python -m
     paper_2505_05587_gb300.batched runs the tuner)."""
     import torch
 
@@ -487,7 +487,7 @@ def bench_batched(local: int, steps: int = 20, warmup: int = 3) -> dict:
     g = B.GaussianTensors.from_scene(scene)
     del scene
     tgs = [torch.as_tensor(synth.target_image(10 + k, c.height, c.width)).cuda() for k, c in enumerate(cams)]
-    step = BT.BatchedDensifyStep(g, cams, BT.concat_images(tgs), st, batch=128)
+    step = BT.BatchedDensifyStep(g, cams, BT.concat_images(tgs), st, batch=256)
     step.capture()
     sampler = ClockSampler(local)
     with sampler:
@@ -504,7 +504,7 @@ def bench_batched(local: int, steps: int = 20, warmup: int = 3) -> dict:
     del plain, g
     torch.cuda.empty_cache()
     return {"workload": "batched densification step: 3M Gaussians (cluster mixture, SH3), 8 ring views 1957x1091, "
-                        "1600x1060, 1237x822, 980x545 x2, 800x600 x3 (7,356,101 pixels), 16x16 tiles, batch 128",
+                        "1600x1060, 1237x822, 980x545 x2, 800x600 x3 (7,356,101 pixels), 16x16 tiles, batch 256",
             "instances_M": M, "n_out": n_out, "unit": "ms/step", "steps": steps, "warmup": warmup,
             "batched_graph_ms": round(ms_graph, 4), "one_view_per_launch_ms": round(ms_plain, 4),
             "speedup": round(ms_plain / ms_graph, 3), "clocks": {"batched": clk_b, "one_view_per_launch": clk_p}}
