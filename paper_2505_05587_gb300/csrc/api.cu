@@ -141,6 +141,7 @@ int sgs_version(void) { return 100; }
 uint64_t sgs_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 int sgs_clear(void* dst, size_t bytes, void* stream) {
+    SGS_NVTX_RANGE();
     if (bytes == 0) return SGS_OK;
     if (!dst) return SGS_ERR_INVALID_ARG;
     return cuda_status(cudaMemsetAsync(dst, 0, bytes, (cudaStream_t)stream));
@@ -148,6 +149,7 @@ int sgs_clear(void* dst, size_t bytes, void* stream) {
 
 int sgs_project(const sgs_gaussians* g, const sgs_camera* cam, const sgs_settings* st, const sgs_proj* out,
                 void* stream) {
+    SGS_NVTX_RANGE();
     if (!valid_gaussians(g) || !valid_cam(cam) || !valid_settings(st) || !out || !tiles_fit(cam, st))
         return SGS_ERR_INVALID_ARG;
     if (g->n > 0 && (!out->xy || !out->conic_opac || !out->rgb || !out->depth || !out->rect || !out->tiles_touched))
@@ -165,6 +167,7 @@ int sgs_bin_sort_workspace_size(int32_t n, int64_t capacity, int32_t num_tiles, 
 
 int sgs_bin_sort(const sgs_proj* proj, int32_t n, const sgs_camera* cam, const sgs_settings* st,
                  const sgs_bins* out, void* ws, size_t ws_bytes, void* stream) {
+    SGS_NVTX_RANGE();
     if (!proj || n < 0 || !valid_cam(cam) || !valid_settings(st) || !out || !tiles_fit(cam, st))
         return SGS_ERR_INVALID_ARG;
     if (!out->ranges || !out->count || out->capacity < 0 || out->capacity > ((int64_t)1 << 31) - 1)
@@ -185,6 +188,7 @@ static bool walk_ok(const sgs_bins* b) {
 
 int sgs_render_fwd(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,
                    float* image, float* final_T, uint32_t* n_contrib, void* stream) {
+    SGS_NVTX_RANGE();
     if (!proj || !bins || !valid_cam(cam) || !valid_settings(st) || !image || !final_T || !n_contrib ||
         !tiles_fit(cam, st) || !bins->ranges || !walk_ok(bins))
         return SGS_ERR_INVALID_ARG;
@@ -195,6 +199,7 @@ int sgs_render_fwd(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera*
 int sgs_render_fwd_l1(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,
                       const float* target, int32_t n_views, float* image, float* final_T, uint32_t* n_contrib,
                       float* dL_dimage, float* loss, void* stream) {
+    SGS_NVTX_RANGE();
     if (!proj || !bins || !valid_cam(cam) || !valid_settings(st) || !image || !final_T || !n_contrib ||
         !tiles_fit(cam, st) || !bins->ranges || !walk_ok(bins) || !target || n_views <= 0 || !dL_dimage || !loss)
         return SGS_ERR_INVALID_ARG;
@@ -204,6 +209,7 @@ int sgs_render_fwd_l1(const sgs_proj* proj, const sgs_bins* bins, const sgs_came
 
 int sgs_render_stats(const sgs_proj* proj, const sgs_bins* bins, const sgs_camera* cam, const sgs_settings* st,
                      uint32_t* counts, uint32_t* warp_union, void* stream) {
+    SGS_NVTX_RANGE();
     if (!proj || !bins || !valid_cam(cam) || !valid_settings(st) || !counts || !tiles_fit(cam, st) ||
         !bins->ranges)
         return SGS_ERR_INVALID_ARG;
@@ -220,6 +226,7 @@ int sgs_ssim_l1_workspace_size(int32_t height, int32_t width, size_t* bytes) {
 int sgs_ssim_l1_loss_grad(const float* image, const float* target, int32_t height, int32_t width, int32_t n_views,
                           float lambda_dssim, float* dL_dimage, float* loss, void* ws, size_t ws_bytes,
                           void* stream) {
+    SGS_NVTX_RANGE();
     if (!image || !target || height <= 0 || width <= 0 || n_views <= 0 || !dL_dimage || !loss ||
         !(lambda_dssim >= 0.0f && lambda_dssim <= 1.0f))
         return SGS_ERR_INVALID_ARG;
@@ -229,12 +236,14 @@ int sgs_ssim_l1_loss_grad(const float* image, const float* target, int32_t heigh
 }
 
 int sgs_fma_probe(float* out, int32_t blocks, int32_t iters, void* stream) {
+    SGS_NVTX_RANGE();
     if (!out || blocks <= 0 || iters <= 0) return SGS_ERR_INVALID_ARG;
     return cuda_status(launch_fma_probe(out, blocks, iters, (cudaStream_t)stream));
 }
 
 int sgs_l1_loss_grad(const float* image, const float* target, int32_t height, int32_t width, int32_t n_views,
                      float* dL_dimage, float* loss, void* stream) {
+    SGS_NVTX_RANGE();
     if (!image || !target || height <= 0 || width <= 0 || n_views <= 0 || !dL_dimage || !loss)
         return SGS_ERR_INVALID_ARG;
     return cuda_status(launch_l1(image, target, height, width, n_views, dL_dimage, loss, (cudaStream_t)stream));
@@ -254,6 +263,7 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
                                   const uint32_t* n_contrib, const float* dL_dimage, const sgs_grads* grads,
                                   int32_t flags, float* S_accum, float* S_po_accum, float* S_ls_accum,
                                   void* ws, size_t ws_bytes, void* stream) {
+    SGS_NVTX_RANGE();
     if (flags & ~(SGS_BWD_ACCUMULATE_GRADS | SGS_BWD_RESET_S)) return SGS_ERR_INVALID_ARG;
     if (!valid_gaussians(g) || !proj || !bins || !valid_cam(cam) || !valid_settings(st) || !final_T ||
         !n_contrib || !dL_dimage || !grads || !tiles_fit(cam, st) || !bins->ranges || !walk_ok(bins))
@@ -283,6 +293,7 @@ int sgs_render_bwd_with_splitting(const sgs_gaussians* g, const sgs_proj* proj, 
 
 int sgs_adam_step(float* param, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
                   float beta2, float eps, int32_t step, float* grad_accum, void* stream) {
+    SGS_NVTX_RANGE();
     if (count < 0 || step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
         !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
         return SGS_ERR_INVALID_ARG;
@@ -293,6 +304,7 @@ int sgs_adam_step(float* param, const float* grad, float* m, float* v, int64_t c
 
 int sgs_adam_step_dev(float* param, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
                       float beta2, float eps, const int32_t* d_step, float* grad_accum, void* stream) {
+    SGS_NVTX_RANGE();
     if (count < 0 || !d_step || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
         !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
         return SGS_ERR_INVALID_ARG;
@@ -395,6 +407,7 @@ int sgs_render_views_with_splitting(const sgs_gaussians* g, const sgs_camera* ca
                                     float* loss, const sgs_grads* grads, int32_t flags, float* S_accum,
                                     float* S_po_accum,
                                     int32_t* d_count, int64_t capacity, void* ws, size_t ws_bytes, void* stream) {
+    SGS_NVTX_RANGE();
     if (flags & ~(SGS_BWD_ACCUMULATE_GRADS | SGS_BWD_RESET_S)) return SGS_ERR_INVALID_ARG;
     if (!valid_gaussians(g) || !valid_views(cams, n_views, st) || !targets || !images || !loss || !grads ||
         !d_count || capacity < 0 || capacity > ((int64_t)1 << 31) - 1 ||
@@ -458,6 +471,7 @@ int sgs_render_batch_workspace_size(const sgs_gaussians* scenes, const sgs_camer
 int sgs_render_batch_fwd(const sgs_gaussians* scenes, const sgs_camera* cams, int32_t n_views, const sgs_settings* st,
                          int32_t batch, float* images, int32_t* d_count, int64_t capacity, void* ws, size_t ws_bytes,
                          void* stream) {
+    SGS_NVTX_RANGE();
     int rows[kMaxViews];
     if (!images || !d_count || capacity < 0 || capacity > ((int64_t)1 << 31) - 1 ||
         !valid_batch(scenes, cams, n_views, st, rows))
@@ -491,6 +505,7 @@ int sgs_densify_split(const sgs_gaussians* in, const float* S_accum, const float
                       const float* grad_norm, float eps_grad, int64_t max_splits,
                       const sgs_gaussians_mut* out, int64_t capacity, int32_t* d_n_out, int32_t* parent_index,
                       float* lam_min_out, float* v_min_out, void* ws, size_t ws_bytes, void* stream) {
+    SGS_NVTX_RANGE();
     if (!valid_gaussians(in) || !out || !d_n_out || capacity < in->n || !isfinite(inv_T_split) ||
         !isfinite(step_scale))
         return SGS_ERR_INVALID_ARG;

@@ -7,6 +7,8 @@
 
 #include <utility>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "steepgs.h"
 
 namespace sgs {
@@ -103,6 +105,17 @@ struct SetDev {
 __device__ Stage integer_stage(const float* __restrict__ means, const float* __restrict__ log_scales,
                                const float* __restrict__ quats, int i, const CamDev& cam,
                                const SetDev& st);
+
+// NVTX range named after the entry point, for the duration of the host call:
+// a profiler's timeline shows each call's launches under it.  Without a tool
+// attached, push and pop are a pointer check each.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define SGS_NVTX_RANGE() ::sgs::NvtxRange sgs_nvtx_range_(__func__)
 
 // Host helpers (defined in api.cu)
 // Counts kernel launches issued by the library (for measurement reports).

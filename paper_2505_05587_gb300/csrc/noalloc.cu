@@ -58,6 +58,7 @@ extern "C" int sgs_densify_split_noalloc(const sgs_gaussians* in, const float* S
                                          const sgs_gaussians_mut* out, int64_t capacity, int32_t* d_n_out,
                                          int32_t* parent_index, float* lam_min_out, float* v_min_out,
                                          void* stream) {
+    SGS_NVTX_RANGE();
     if (densify_ws_bytes(SGS_NOALLOC_MAX_GAUSSIANS) > (size_t)SGS_NOALLOC_SCRATCH_BYTES) return SGS_ERR_WORKSPACE;
     if (!in || in->n < 0 || in->n > SGS_NOALLOC_MAX_GAUSSIANS) return SGS_ERR_INVALID_ARG;
     if (densify_ws_bytes(in->n) > (size_t)SGS_NOALLOC_SCRATCH_BYTES) return SGS_ERR_WORKSPACE;
