@@ -58,7 +58,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # project_bwd_kernel<3,0,0,0>), dram__bytes_read.sum + dram__bytes_write.sum from
 # one ncu capture, valid only for the sources it was taken from (first 16 hex
 # digits of the SHA-256 of render.cu, project.cu and api.cu, concatenated).
-RENDER_BWD_TRAFFIC = {"bytes": (4_008_960 + 165_888) + (121_690_880 + 7_526_400) + (174_166_784 + 206_474_496),
+RENDER_BWD_TRAFFIC = {"bytes": (4_010_240 + 156_416) + (121_663_744 + 7_563_264) + (173_928_192 + 205_738_752),
                       "sources_sha256": "00008c25ca11c16f",
                       "profile": "profiles/render_bwd_scene_1M_1237x822.md"}
 TRAFFIC_SOURCES = ("render.cu", "project.cu", "api.cu")
