@@ -758,12 +758,27 @@ __global__ void __launch_bounds__(TO_THREADS) tile_order_kernel(const uint2* __r
         s_tot[threadIdx.x] = tot;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int c = 0; c < TO_CLASSES; ++c) {
-            const uint32_t n = s_tot[c];
-            s_tot[c] = run;
-            run += n;
+    if (warp == 0) {                                    // exclusive scan of the class totals
+        constexpr int PER = (TO_CLASSES + 31) / 32;
+        uint32_t v[PER], mine = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int c = lane * PER + q;
+            v[q] = c < TO_CLASSES ? s_tot[c] : 0u;
+            mine += v[q];
+        }
+        uint32_t x = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        uint32_t run = x - mine;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int c = lane * PER + q;
+            if (c < TO_CLASSES) s_tot[c] = run;
+            run += v[q];
         }
     }
     __syncthreads();
