@@ -597,9 +597,9 @@ def run_reference(args):
     fits about three minutes (the first full iteration tells), every step is
     one full fused iteration of the oracle, timed as it runs.  Otherwise each
     step runs the oracle's fused iteration on the full scene for a horizontal
-    strip of rows, and the per-iteration time of a step is extrapolated with
-    t(rows) = a + b rows, a measured on a one-row strip, beside the measured
-    full iteration."""
+    strip of rows, and the per-iteration time of a step is extrapolated along
+    the line t(rows) = c + b rows through a one-row strip's time and the
+    step's own, beside the measured full iteration."""
     import oracle
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -639,10 +639,10 @@ def run_reference(args):
             _oracle_iteration(scene, cam, st, tgt, rows=(y0, rows), all_cores=True)
             dt = time.perf_counter() - t0
             if k >= args.warmup:
-                est.append(a + (dt - a) * HEIGHT / rows)
+                est.append(a + (dt - a) * (HEIGHT - 1) / max(rows - 1, 1))
         v = float(np.mean(est)) * 1e3
         sample = (f"per step: full scene, rows of the view ({rows} per step, rotating), all host threads; "
-                  f"t(rows) = a + b rows extrapolated to {HEIGHT} rows, a = {a:.2f} s from a one-row strip")
+                  f"t(rows) = c + b rows through a one-row strip ({a:.2f} s) and the step, extrapolated to {HEIGHT} rows")
     out = {"metric": METRIC, "value": round(v, 1), "unit": "ms/iter", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",

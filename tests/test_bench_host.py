@@ -65,3 +65,51 @@ def test_algorithmic_bytes_per_unit():
     unit = [bench.algorithmic_bytes(*e) for e in ((1, 0, 0, 0), (0, 1, 0, 0), (0, 0, 1, 0), (0, 0, 0, 1))]
     assert unit == [940, 124, 76, 8]
     assert bench.algorithmic_bytes(2, 3, 5, 7) == 2 * 940 + 3 * 124 + 5 * 76 + 7 * 8
+
+
+def _reference_line(monkeypatch, per_full_s, steps=2, warmup=3):
+    """The oracle arm's JSON line with the oracle replaced by a clock: a full
+    iteration advances it by per_full_s, a strip of h rows by
+    per_full_s * (0.05 + 0.95 h / HEIGHT)."""
+    import contextlib
+    import io
+    import json
+    t = [0.0]
+
+    def fake_iteration(scene, cam, st, target, rows=None, all_cores=False):
+        frac = 1.0 if rows is None else 0.05 + 0.95 * rows[1] / bench.HEIGHT
+        t[0] += per_full_s * frac
+
+    class Scene:
+        n = 4
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(bench, "_oracle_iteration", fake_iteration)
+    monkeypatch.setattr(bench.time, "perf_counter", lambda: t[0])
+    monkeypatch.setattr(bench.synth, "cluster_scene", lambda *a, **k: Scene())
+    monkeypatch.setattr(bench.synth, "target_image", lambda *a, **k: None)
+
+    class Args:
+        pass
+
+    Args.steps, Args.warmup = steps, warmup
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(Args())
+    return json.loads(buf.getvalue().strip().splitlines()[-1])
+
+
+def test_reference_arm_times_whole_iterations_when_they_fit(monkeypatch):
+    out = _reference_line(monkeypatch, per_full_s=2.0)
+    assert out["impl"] == "reference" and out["cpu_baseline"]["measured"] is True
+    assert abs(out["value"] - 2000.0) < 1e-6
+    assert out["e2e"]["value"] == out["value"] and out["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_extrapolates_strips_when_whole_iterations_do_not_fit(monkeypatch):
+    out = _reference_line(monkeypatch, per_full_s=100.0, steps=5, warmup=3)
+    assert out["cpu_baseline"]["measured"] is False
+    assert "extrapolated" in out["cpu_baseline"]["sample"]
+    # the fake's strip cost is linear in the rows, so the extrapolation is exact
+    assert abs(out["value"] - 100_000.0) < 1e-3 * 100_000.0
