@@ -180,13 +180,13 @@ def run_ring_densify(n: int = 3_000_000, steps: int = 20, warmup: int = 3, tune:
             "autotune": table}
 
 
-def run_eager_steps(steps: int = 3, n: int = 3_000_000, tile=(16, 16), batch: int = 128) -> dict:
+def run_eager_steps(steps: int = 3, n: int = 3_000_000, tile=(16, 16), batch: int = 128, views: int = 8) -> dict:
     """A few eager batched steps on the ring workload with a fixed tile shape
-    and batch depth (no tuning, no graph): the command a per-launch profile of
-    the batched step runs."""
+    and batch depth (no tuning, no graph), over its first `views` views: the
+    command a per-launch profile of the batched step runs."""
     import synth
     scene = synth.cluster_scene(0, n, 3)
-    cams = synth.ring_cameras(6.0)
+    cams = synth.ring_cameras(6.0)[:views]
     st = dataclasses.replace(synth.Settings(), tile_w=tile[0], tile_h=tile[1])
     g = B.GaussianTensors.from_scene(scene)
     del scene
@@ -200,7 +200,8 @@ def run_eager_steps(steps: int = 3, n: int = 3_000_000, tile=(16, 16), batch: in
 if __name__ == "__main__":
     import json
     import sys
-    if len(sys.argv) > 2 and sys.argv[1] == "--eager":
-        print(json.dumps(run_eager_steps(int(sys.argv[2]))))
+    if len(sys.argv) > 2 and sys.argv[1] == "--eager":        # --eager STEPS [VIEWS [GAUSSIANS]]
+        print(json.dumps(run_eager_steps(int(sys.argv[2]), views=int(sys.argv[3]) if len(sys.argv) > 3 else 8,
+                                         n=int(sys.argv[4]) if len(sys.argv) > 4 else 3_000_000)))
     else:
         print(json.dumps(run_ring_densify(int(sys.argv[1]) if len(sys.argv) > 1 else 3_000_000)))

@@ -759,10 +759,13 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) render_bwd_walk_ker
 // ---------------------------------------------------------------------------
 // Several views: persistent CTAs pull global tiles from an atomic counter
 // (the counter must be zero at launch).  Per-view maps are concatenated at
-// pixel offsets pix_off[v].
+// pixel offsets pix_off[v].  The forward is bounded, as the single-view one,
+// to 48 resident warps per SM (40 registers): unbounded it took 55 registers
+// and 4 CTAs per SM, and its warps waited at the batch barriers with the
+// issue slots two-thirds busy.
 // ---------------------------------------------------------------------------
 template <int TW, int TH, int BATCH, bool REC>
-__global__ void __launch_bounds__(TW * TH) render_fwd_views_kernel(
+__global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) render_fwd_views_kernel(
     ViewsDev vd, const uint2* __restrict__ ranges, const uint32_t* __restrict__ gids, const float4* __restrict__ xy,
     const float4* __restrict__ conic_opac, const float4* __restrict__ rgb, SetDev st, float* __restrict__ images,
     float* __restrict__ final_T, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ counter,
