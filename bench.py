@@ -58,8 +58,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # project_bwd_kernel<3,0,0,0>), dram__bytes_read.sum + dram__bytes_write.sum from
 # one ncu capture, valid only for the sources it was taken from (first 16 hex
 # digits of the SHA-256 of render.cu, project.cu and api.cu, concatenated).
-RENDER_BWD_TRAFFIC = {"bytes": (4_010_240 + 156_416) + (121_663_744 + 7_563_264) + (173_928_192 + 205_738_752),
-                      "sources_sha256": "00008c25ca11c16f",
+RENDER_BWD_TRAFFIC = {"bytes": (4_009_472 + 149_760) + (121_743_104 + 7_667_712) + (173_870_080 + 205_750_016),
+                      "sources_sha256": "0b68179a1da1023d",
                       "profile": "profiles/render_bwd_scene_1M_1237x822.md"}
 TRAFFIC_SOURCES = ("render.cu", "project.cu", "api.cu")
 
