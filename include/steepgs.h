@@ -34,6 +34,9 @@
  *     sgs_densify_split_noalloc).  Kernels are launched with programmatic
  *     dependent launch: each one is scheduled while its predecessor on the
  *     stream drains and waits for that predecessor's results before reading.
+ *   - Every call that launches work opens an NVTX range named after itself
+ *     for the duration of the host call, so a profiler's timeline groups its
+ *     launches; without a tool attached the range costs a pointer check.
  *   - Data-dependent sizes (instance count M, split count) are written to
  *     caller-owned device integers.  When a size exceeds the caller's capacity
  *     the kernels write only within capacity (never out of bounds) and the
